@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Benchmark: 3D free-space Stokeslet DMK near-field pass on GB300.
+
+Workload (one rank = one independent system, weak scaling): N = 1e6 points from
+a mixture of 8 isotropic Gaussians (sigma = 0.02, centres uniform in
+[0.2, 0.8]^3, clipped to the unit cube, shifted to [-1/2, 1/2]^3), forces
+N(0, 1), eps = 1e-6 (3c/pi = 17, Table 2), leaf capacity n_s = 1200 (the
+paper's 3D value for eps = 1e-6, Sec. 8).
+
+One step = dmk_stokes_plan (kernel tables, Morton sort, adaptive tree, level
+restriction, near lists, tiles) + dmk_stokes_eval (near field + self term) +
+dmk_stokes_destroy, mixed precision.  value = targets / s over the timed
+steps; the L2 is flushed (256 MB write) before every timed step.  The FP64
+path is measured on the same workload and reported beside it.
+
+--impl reference times the FP64 CPU oracle (plain numpy, one thread) on a
+bounded sample of the same recipe.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "3D Stokeslet DMK targets/s at eps=1e-6 (near-field pass incl. tree build), mixed precision"
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--leaf-capacity", type=int, default=0, help="0 = paper's n_s for eps")
+    ap.add_argument("--cpu-sample", type=int, default=4000, help="points in the oracle's bounded sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, ns):
+    return {"workload": "3d-free-stokeslet-clustered-8gauss",
+            "n_points": args.n, "sigma": 0.02, "eps": args.eps, "leaf_capacity": ns,
+            "kernels": "stokeslet", "rhs": 1, "l2": "flushed (256 MB write) before every timed step"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        import statistics
+        reasons = set()
+        for r in rows:
+            if r["hw"].lower().startswith("active"):
+                reasons.add("hw_slowdown")
+            if r["hwt"].lower().startswith("active"):
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"].lower().startswith("active"):
+                reasons.add("sw_thermal_slowdown")
+            if r["pcap"].lower().startswith("active"):
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+# ------------------------------------------------------------ reference arm
+def oracle_sample(n_sample, eps, ns, seed_extra=0):
+    """Times the FP64 oracle (tree + near pass) on the same recipe at n_sample points."""
+    import numpy as np
+    from paper_2509_21471_gb300 import workloads as wl
+    from oracle import near as onear
+    from oracle.tree import Tree
+    from oracle.window import ProlateWindow
+    from oracle.params import bandlimit_c
+    rng = wl.rng_for(1, extra=10 + seed_extra)
+    x = wl.gaussian_mixture_points(rng, n_sample, 3, 8, 0.02)
+    f = wl.forces(rng, n_sample, 3)
+    win = ProlateWindow(bandlimit_c(eps))
+    t0 = time.perf_counter()
+    tr = Tree(x, ns)
+    onear.near_lists(tr, dict(win=win, stokeslet=True), f=f)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    ns = args.leaf_capacity or 1200
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_sample(max(200, args.cpu_sample // 10), args.eps, ns)
+    times = [oracle_sample(args.cpu_sample, args.eps, ns, k) for k in range(args.steps)]
+    t = sum(times)
+    v = args.cpu_sample * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "targets/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, ns),
+            "cpu_baseline": {"value": v, "unit": "targets/s", "cores": 1, "kind": "oracle",
+                             "sample": f"same 8-Gaussian recipe at N={args.cpu_sample} points per step "
+                                       f"(oracle tree + near pass, numpy, 1 thread)"},
+            "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    from paper_2509_21471_gb300 import dmk, workloads as wl
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    x_np, f_np = wl.clustered_3d(n=args.n, sigma=0.02, seed_index=1 + 100 * rank)
+    N = x_np.shape[0]
+    x_h = torch.from_numpy(x_np).pin_memory()
+    f_h = torch.from_numpy(f_np).pin_memory()
+    u_h = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+    x_d = x_h.to("cuda")
+    f_d = f_h.to("cuda")
+    u_d = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ns = args.leaf_capacity or 0
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    def step(prec):
+        p = dmk.Plan(x_d, eps=args.eps, precision=prec, leaf_capacity=ns)
+        p.eval(f_d, out=u_d)
+        p.close()
+
+    def timed(fn, k):
+        ms = []
+        for _ in range(k):
+            flush()
+            barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    # ---- warm-up (both precisions: first-use costs of pools and kernels)
+    for _ in range(args.warmup):
+        step(dmk.MIXED)
+    step(dmk.FP64)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    ms_mixed = timed(lambda: step(dmk.MIXED), args.steps)
+    clocks = sampler.stop()
+    t_mixed = max_over_ranks(sum(ms_mixed) / 1e3)
+    value = world * N * args.steps / t_mixed
+
+    ms_fp64 = timed(lambda: step(dmk.FP64), max(1, args.steps // 2))
+    t_fp64 = max_over_ranks(sum(ms_fp64) / 1e3) / len(ms_fp64)
+
+    # ---- near-field kernel alone (plan reused), both precisions
+    near = {}
+    launches = None
+    for name, prec in (("mixed", dmk.MIXED), ("fp64", dmk.FP64)):
+        p = dmk.Plan(x_d, eps=args.eps, precision=prec, leaf_capacity=ns)
+        l0 = p.stats()["launches"]
+        p.eval(f_d, out=u_d)
+        torch.cuda.synchronize()
+        st = p.stats()
+        if prec == dmk.MIXED:
+            # kernels of one step: plan build + one eval (the pair count is not part of a step)
+            launches = l0 + (st["launches"] - l0 - 1)
+        ms = timed(lambda: p.eval(f_d, out=u_d), args.steps)
+        t = max_over_ranks(sum(ms) / len(ms) / 1e3)
+        near[name] = dict(ms=1e3 * t, issued_pairs=st["issued_pairs"], useful_pairs=st["useful_pairs"],
+                          gpairs_issued=st["issued_pairs"] / t / 1e9, gpairs_useful=st["useful_pairs"] / t / 1e9,
+                          leaves=st["leaves"], max_level=st["max_level"], tiles=st["tiles"],
+                          leaf_capacity=st["leaf_capacity"])
+        p.close()
+    ns_used = near["mixed"]["leaf_capacity"]
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    def e2e_step():
+        x_d.copy_(x_h, non_blocking=True)
+        f_d.copy_(f_h, non_blocking=True)
+        step(dmk.MIXED)
+        u_h.copy_(u_d, non_blocking=True)
+    ms_e2e = timed(e2e_step, args.steps)
+    t_e2e = max_over_ranks(sum(ms_e2e) / 1e3)
+    e2e = {"value": world * N * args.steps / t_e2e, "unit": "targets/s",
+           "h2d_bytes_per_step": int(x_h.numel() * 8 + f_h.numel() * 8), "d2h_bytes_per_step": int(u_h.numel() * 8)}
+
+    # ---- roofline of the dominant kernel (mixed near field): FP32 ALU bound
+    c32 = [len(dmk.kernel_table(3, args.eps, w, fp32=True)[2]) for w in (0, 1)]
+    flops_per_pair = 40 + 2 * (c32[0] - 1) + 2 * (c32[1] - 1)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = near["mixed"]["useful_pairs"] * flops_per_pair / (near["mixed"]["ms"] / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "kernel": "k_near_mixed3 (near field, mixed precision)",
+                "flops_per_useful_pair": flops_per_pair,
+                "peak_basis": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                              "(max SM clock of MEASURED_PEAKS.json)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = oracle_sample(args.cpu_sample, args.eps, ns_used)
+        cpu = {"value": args.cpu_sample / t, "unit": "targets/s", "cores": 1, "kind": "oracle",
+               "sample": f"same 8-Gaussian recipe at N={args.cpu_sample} points (oracle tree + near pass, "
+                         f"numpy, 1 thread), {t:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32-compensated (f64 self term, output)",
+                "data": "synthetic", "config": workload_config(args, ns_used),
+                "fp64": {"value": N * world / t_fp64, "unit": "targets/s", "ms_per_step": 1e3 * t_fp64},
+                "speedup_mixed_over_fp64": t_fp64 / (t_mixed / args.steps),
+                "near_field": near, "e2e": e2e, "gpu_launches": launches,
+                "gpu_launches_note": "our kernels per step (plan + eval); CUB sort/scan kernels not counted",
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * dmk_stokes.h -- C ABI of the GB300 near-field library for the DMK method for
+ * Stokes potentials (Jiang, Tornberg et al., arXiv 2509.21471).
+ *
+ * What it computes (the "near" component of the DMK sum, Sec. 5.3 Eq.
+ * (three_part_sum) and Step 4 of Sec. 6.1): for every point t of a point set in
+ * the unit box [lo, lo+1]^d (Sec. 1), d = 2 or 3, with sources == targets,
+ *
+ *   u_t = sum_{s near t, 0 < r < nu_ts}  S_R,nu_ts(x_t - x_s) f_s      (Stokeslet)
+ *       + sum_{s near t, 0 < r < nu_ts}  T_R,nu_ts(x_t - x_s) g_s n_s  (stresslet)
+ *       + u_self(t)
+ *
+ * with the prolate-split residual kernels S_R, T_R of Sec. 5.2 (Eqs.
+ * (res_stokeslet), (Soffdiag), (res_stresslet), (T-offd)) at the residual scale
+ *   nu_ts = 2^-(min(L_t, L_s) + 1),   L = level of the point's leaf,
+ * and the Stokeslet self term u_self = -phi(0)/(2 pi nu_t) f_t (Eq. (S_self),
+ * nu_t = 2^-(L_t+1); the stresslet's is zero).  "near" = the sources of the
+ * leaves touching t's leaf in the adaptive, level-restricted tree of Step 1
+ * (periodic images included in the periodic case, Sec. 6.2).  In the periodic
+ * stresslet case the k = 0 term u0(x_t) = -sum_s (x_t - x_s)(g_s . n_s)
+ * (Sec. 5.3, after Eq. (ewald_far)) is added as well.
+ *
+ * Conventions
+ *   - Every array argument is a DEVICE pointer owned by the caller, row-major,
+ *     float64, on the device current when the plan was made.
+ *   - Calls are asynchronous on the given CUDA stream (NULL = legacy default
+ *     stream).  Argument errors are returned synchronously.  Errors found on the
+ *     device (a free-space point outside the box, a non-finite coordinate) are
+ *     latched in the plan and returned by dmk_stokes_sync_status().
+ *   - Outputs are in the caller's original point order.
+ *   - The plan copies everything it needs from the coordinates; the caller may
+ *     reuse the coordinate buffer when dmk_stokes_plan has returned (it
+ *     synchronises its stream before returning).
+ *   - The stream given to dmk_stokes_plan must stay valid until
+ *     dmk_stokes_destroy (device memory is released on it, after the work of
+ *     the last stream an evaluation was queued on).
+ *   - Functions are not thread-safe on the same plan.
+ */
+#ifndef DMK_STOKES_H_
+#define DMK_STOKES_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dmk_stokes_plan_s* dmk_stokes_plan_t; /* opaque, owned by the library */
+
+typedef enum {
+  DMK_OK = 0,
+  DMK_ERR_INVALID_ARG = 1,  /* bad option, null pointer, size or NaN */
+  DMK_ERR_OUT_OF_RANGE = 2, /* free-space point outside [lo, lo+1]^d */
+  DMK_ERR_UNSUPPORTED = 3,  /* valid but not provided by this library */
+  DMK_ERR_NOMEM = 4,        /* device allocation failed */
+  DMK_ERR_CUDA = 5,         /* a CUDA runtime call failed */
+  DMK_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+  DMK_ERR_BAD_PLAN = 7      /* null, destroyed or foreign plan handle */
+} dmk_status_t;
+
+enum { DMK_KERNEL_STOKESLET = 1, DMK_KERNEL_STRESSLET = 2 };
+enum { DMK_PRECISION_FP64 = 0, DMK_PRECISION_MIXED = 1 };
+enum { DMK_COMPONENTS_ALL = 0, DMK_COMPONENTS_NEAR = 1 };
+
+typedef struct {
+  int32_t dim;           /* 2 or 3 */
+  int32_t periodic;      /* 0 free space; 1 periodic unit cell (Sec. 6.2) */
+  int32_t kernels;       /* bitmask DMK_KERNEL_*; the stresslet needs n_rhs == 1 */
+  int32_t precision;     /* DMK_PRECISION_FP64: all arithmetic in float64.
+                            DMK_PRECISION_MIXED: pair terms in float32 with
+                            leaf-relative coordinates and compensated (two-sum)
+                            accumulation; self term and output in float64. */
+  int32_t components;    /* DMK_COMPONENTS_NEAR (the far field is not provided:
+                            DMK_COMPONENTS_ALL returns DMK_ERR_UNSUPPORTED) */
+  int32_t leaf_capacity; /* n_s, max points per leaf; 0 = the paper's value for
+                            eps (Sec. 8: 3D 600..3000, 2D 120..480) */
+  int32_t n_rhs;         /* force columns, 1..16 */
+  int32_t reserved;      /* must be 0 */
+  double eps;            /* tolerance in [1e-12, 1e-3]; selects the prolate
+                            bandlimit c from Table 2 (3c/pi interpolated in
+                            log10 eps and rounded up) */
+  double box_lo[3];      /* lower corner lo of the unit box (side 1) */
+} dmk_stokes_opts_t;
+
+/* Builds the plan: Morton keys, sort, adaptive tree (leaves hold <= n_s points,
+ * Step 1(a)), level restriction (Step 1(b)), near lists and tiles, and the
+ * polynomial kernel tables for the bandlimit c of eps (remark closing Sec. 5.2).
+ *   n_src   number of points (>= 0, < 2^31)
+ *   d_src   [n_src][dim] coordinates
+ *   n_trg, d_trg: separate targets are not provided; pass n_trg == n_src and
+ *           d_trg == NULL (targets are the sources) else DMK_ERR_UNSUPPORTED.
+ *   stream  cudaStream_t or NULL
+ *   out     receives the plan handle (set to NULL on failure)
+ * Host-synchronises the stream a few times (tree sizes are read back). */
+dmk_status_t dmk_stokes_plan(const dmk_stokes_opts_t* opts, int64_t n_src, const double* d_src,
+                             int64_t n_trg, const double* d_trg, void* stream,
+                             dmk_stokes_plan_t* out);
+
+/* Same for n_sys independent systems (each its own unit box, tree and sums)
+ * stored back to back: system i owns points [h_offsets[i], h_offsets[i+1]).
+ * h_offsets is a HOST array of n_sys + 1 nondecreasing values, h_offsets[0] = 0.
+ * No paper counterpart (batching of many small systems).  eval / eval_grad /
+ * destroy work on the result as on any plan. */
+dmk_status_t dmk_stokes_plan_batched(const dmk_stokes_opts_t* opts, int32_t n_sys,
+                                     const int64_t* h_offsets, const double* d_src, void* stream,
+                                     dmk_stokes_plan_t* out);
+
+/* Evaluates the near component (definition at the top of this file).
+ *   d_f  [n][dim][n_rhs] Stokeslet forces (required if the Stokeslet bit is set)
+ *   d_g  [n][dim] stresslet strengths, d_n [n][dim] orientation vectors
+ *        (required if the stresslet bit is set; rho_s = g_s (x) n_s, Eq. (stokes_stress_sum))
+ *   d_u  [n][dim][n_rhs] output, overwritten
+ * Does not allocate; may be captured in a CUDA graph. */
+dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
+                             const double* d_n, double* d_u, void* stream);
+
+/* Velocity gradient of the Stokeslet near component (the stresslet gradient is
+ * not provided: DMK_ERR_UNSUPPORTED):
+ *   d_gradu [n][dim][dim][n_rhs], gradu[t][j][m] = d u_j / d x_m at x_t with the
+ *   tree (and so every nu_ts) held fixed; the self term does not depend on x.
+ *   d_u may be NULL; if not NULL it receives the velocity as dmk_stokes_eval does.
+ * The derivative of Eq. (res_stokeslet) is derived in the library docs. */
+dmk_status_t dmk_stokes_eval_grad(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
+                                  const double* d_n, double* d_u, double* d_gradu, void* stream);
+
+/* Synchronises the plan's last stream and returns the latched device status
+ * (DMK_OK, DMK_ERR_OUT_OF_RANGE, DMK_ERR_INVALID_ARG for a non-finite point). */
+dmk_status_t dmk_stokes_sync_status(dmk_stokes_plan_t plan);
+
+/* Tree statistics (host values, valid after dmk_stokes_plan returned DMK_OK):
+ *   stats[0] leaves, [1] max leaf level, [2] near-list entries,
+ *   [3] tiles, [4] issued pairs (sum over targets of the points in their
+ *   near leaves, the target itself excluded), [5] bandlimit c (as integer
+ *   3c/pi), [6] leaf capacity n_s, [7] points,
+ *   [8] useful pairs (0 < r < nu_ts, decided in float64; counted by a GPU
+ *   kernel on the first call), [9] kernel launches issued by this library for
+ *   this plan so far (plan build, evaluations and the pair count).
+ * Host-synchronises. */
+dmk_status_t dmk_stokes_plan_stats(dmk_stokes_plan_t plan, int64_t stats[10]);
+
+/* Copies the plan's tree to HOST arrays (any pointer may be NULL):
+ *   perm[n]        sorted position -> original index
+ *   leaf_level[L], leaf_start[L], leaf_count[L], leaf_coords[L][dim] (box
+ *   coordinates at the leaf's level), near_off[L+1], near_leaf[E],
+ *   near_q[E][dim] (periodic image offsets q, displacement (w_t - w_s) + q).
+ * Sizes L, E from dmk_stokes_plan_stats.  Host-synchronises. */
+dmk_status_t dmk_stokes_plan_tree(dmk_stokes_plan_t plan, int32_t* perm, int32_t* leaf_level,
+                                  int32_t* leaf_start, int32_t* leaf_count, int64_t* leaf_coords,
+                                  int32_t* near_off, int32_t* near_leaf, int32_t* near_q);
+
+/* Host-only query of the kernel tables for (dim, eps, kernels): bandlimit c,
+ * phi(0) and the polynomial coefficients (monomials in t = 2 rho^2 - 1) of the
+ * residual functions; no GPU needed.
+ *   out_c, out_phi0   scalars (may be NULL)
+ *   which             0 gS, 1 hS, 2 pT, 3 qT, 4 dgS/ds, 5 dhS/ds
+ *   fp32              0 the float64 table, 1 the float32 table
+ *   coef, max_terms   output buffer; returns the number of terms in *n_terms. */
+dmk_status_t dmk_stokes_kernel_table(int32_t dim, double eps, int32_t kernels, int32_t which,
+                                     int32_t fp32, double* out_c, double* out_phi0,
+                                     double* coef, int32_t max_terms, int32_t* n_terms);
+
+/* Releases the plan (device memory is freed on the plan's stream). NULL is ignored. */
+void dmk_stokes_destroy(dmk_stokes_plan_t plan);
+
+/* Message of the last error on this plan, or of the last failed call on this
+ * thread when plan == NULL.  The string is owned by the library. */
+const char* dmk_stokes_last_error(dmk_stokes_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMK_STOKES_H_ */

@@ -1,0 +1,342 @@
+// C ABI of the DMK Stokes near-field library (see include/dmk_stokes.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+#include <vector>
+
+#include "common.cuh"
+
+namespace dmk {
+size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N);
+}
+
+struct dmk_stokes_plan_s {
+  dmk::Plan p;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+dmk_status_t set_err(dmk_stokes_plan_t plan, dmk_status_t code, const std::string& msg) {
+  g_last_error = msg;
+  if (plan) plan->p.last_error = msg;
+  return code;
+}
+
+bool valid_plan(dmk_stokes_plan_t plan) { return plan && plan->p.magic == dmk::kPlanMagic; }
+
+dmk_status_t validate_opts(const dmk_stokes_opts_t* o, std::string& msg) {
+  if (!o) { msg = "opts is NULL"; return DMK_ERR_INVALID_ARG; }
+  if (o->dim != 2 && o->dim != 3) { msg = "dim must be 2 or 3"; return DMK_ERR_INVALID_ARG; }
+  if (o->periodic != 0 && o->periodic != 1) { msg = "periodic must be 0 or 1"; return DMK_ERR_INVALID_ARG; }
+  if (o->kernels < 1 || o->kernels > 3) { msg = "kernels must be a nonzero mask of 1|2"; return DMK_ERR_INVALID_ARG; }
+  if (o->precision != 0 && o->precision != 1) { msg = "precision must be 0 or 1"; return DMK_ERR_INVALID_ARG; }
+  if (o->components != DMK_COMPONENTS_ALL && o->components != DMK_COMPONENTS_NEAR) {
+    msg = "components must be 0 or 1";
+    return DMK_ERR_INVALID_ARG;
+  }
+  if (o->leaf_capacity < 0 || o->leaf_capacity > (1 << 20)) { msg = "leaf_capacity out of range"; return DMK_ERR_INVALID_ARG; }
+  if (o->n_rhs < 1 || o->n_rhs > 16) { msg = "n_rhs must be in 1..16"; return DMK_ERR_INVALID_ARG; }
+  if (o->reserved != 0) { msg = "reserved must be 0"; return DMK_ERR_INVALID_ARG; }
+  if (!(o->eps >= 1e-12 * (1 - 1e-9) && o->eps <= 1e-3 * (1 + 1e-9))) {
+    msg = "eps must lie in [1e-12, 1e-3] (Table 2 range)";
+    return DMK_ERR_INVALID_ARG;
+  }
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(o->box_lo[a])) { msg = "box_lo not finite"; return DMK_ERR_INVALID_ARG; }
+  if (o->components == DMK_COMPONENTS_ALL) {
+    msg = "the far field is not provided: use components = DMK_COMPONENTS_NEAR";
+    return DMK_ERR_UNSUPPORTED;
+  }
+  if (o->dim == 2) { msg = "2D kernels are not provided by this library version"; return DMK_ERR_UNSUPPORTED; }
+  if (o->n_rhs != 1) { msg = "n_rhs > 1 is not provided by this library version"; return DMK_ERR_UNSUPPORTED; }
+  return DMK_OK;
+}
+
+void configure_pool(int dev) {
+  static std::mutex mu;
+  static std::set<int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(dev)) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;   // keep freed blocks cached in the pool
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done.insert(dev);
+}
+
+void release(dmk::Plan& p) {
+  cudaStream_t s = p.stream;
+  dmk::free_tree(p.tree, s);
+  dmk::dfree(p.fsorted, s);
+  dmk::dfree(p.reduce_buf, s);
+  dmk::dfree(p.status, s);
+  if (p.h_status) cudaFreeHost(p.h_status);
+  p.h_status = nullptr;
+}
+
+dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64_t* h_offsets,
+                       const double* d_src, void* stream, dmk_stokes_plan_t* out) {
+  if (!out) return set_err(nullptr, DMK_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::string msg;
+  dmk_status_t st = validate_opts(opts, msg);
+  if (st != DMK_OK) return set_err(nullptr, st, msg);
+  if (n_sys < 1 || !h_offsets) return set_err(nullptr, DMK_ERR_INVALID_ARG, "bad system offsets");
+  if (h_offsets[0] != 0) return set_err(nullptr, DMK_ERR_INVALID_ARG, "h_offsets[0] must be 0");
+  for (int k = 0; k < n_sys; ++k)
+    if (h_offsets[k + 1] < h_offsets[k]) return set_err(nullptr, DMK_ERR_INVALID_ARG, "h_offsets decreasing");
+  const int64_t N = h_offsets[n_sys];
+  if (N >= (int64_t(1) << 31)) return set_err(nullptr, DMK_ERR_INVALID_ARG, "too many points (>= 2^31)");
+  if (N > 0 && !d_src) return set_err(nullptr, DMK_ERR_INVALID_ARG, "d_src is NULL");
+
+  dmk_stokes_plan_t plan = new (std::nothrow) dmk_stokes_plan_s();
+  if (!plan) return set_err(nullptr, DMK_ERR_NOMEM, "host allocation failed");
+  dmk::Plan& p = plan->p;
+  p.opts = *opts;
+  p.stream = static_cast<cudaStream_t>(stream);
+  plan->last_stream = p.stream;
+  try {
+    DMK_CUDA_TRY(cudaGetDevice(&p.device));
+    configure_pool(p.device);
+    double c = dmk::bandlimit_for_eps(opts->eps, opts->kernels);
+    if (c <= 0) throw dmk::Error{DMK_ERR_INVALID_ARG, "eps outside Table 2 range"};
+    double fp32_tol = std::max(opts->eps / 100.0, 1e-8);
+    if (dmk::build_tables(opts->dim, c, fp32_tol, &p.tables) != 0)
+      throw dmk::Error{DMK_ERR_UNSUPPORTED, "kernel tables could not be built for this dimension"};
+    p.leaf_capacity = opts->leaf_capacity > 0 ? opts->leaf_capacity
+                                              : dmk::leaf_capacity_for_eps(opts->eps, opts->dim);
+    p.tree.N = N;
+    p.tree.n_sys = n_sys;
+    p.status = dmk::dalloc<int>(1, p.stream);
+    DMK_CUDA_TRY(cudaMemsetAsync(p.status, 0, sizeof(int), p.stream));
+    DMK_CUDA_TRY(cudaMallocHost(&p.h_status, sizeof(int)));
+    dmk::build_tree(p, d_src, h_offsets);
+    p.fsorted_bytes = dmk::eval_workspace_bytes(p.opts, N);
+    p.fsorted = dmk::dalloc<char>(p.fsorted_bytes, p.stream);
+    p.reduce_buf = dmk::dalloc<double>(4 * n_sys, p.stream);
+    DMK_CUDA_TRY(cudaGetLastError());
+    // everything above is complete when the call returns: the plan may then be
+    // used from any stream and the coordinate buffer reused
+    DMK_CUDA_TRY(cudaStreamSynchronize(p.stream));
+  } catch (const dmk::Error& e) {
+    release(p);
+    delete plan;
+    return set_err(nullptr, e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    release(p);
+    delete plan;
+    return set_err(nullptr, DMK_ERR_NOMEM, "host allocation failed");
+  }
+  p.magic = dmk::kPlanMagic;
+  *out = plan;
+  return DMK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dmk_status_t dmk_stokes_plan(const dmk_stokes_opts_t* opts, int64_t n_src, const double* d_src,
+                             int64_t n_trg, const double* d_trg, void* stream, dmk_stokes_plan_t* out) {
+  if (out) *out = nullptr;
+  if (n_src < 0) return set_err(nullptr, DMK_ERR_INVALID_ARG, "n_src < 0");
+  if (d_trg != nullptr || n_trg != n_src)
+    return set_err(nullptr, DMK_ERR_UNSUPPORTED, "separate targets are not provided (pass d_trg = NULL, n_trg = n_src)");
+  int64_t offs[2] = {0, n_src};
+  return make_plan(opts, 1, offs, d_src, stream, out);
+}
+
+dmk_status_t dmk_stokes_plan_batched(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64_t* h_offsets,
+                                     const double* d_src, void* stream, dmk_stokes_plan_t* out) {
+  if (out) *out = nullptr;
+  if (n_sys > 65535) return set_err(nullptr, DMK_ERR_INVALID_ARG, "n_sys > 65535");
+  return make_plan(opts, n_sys, h_offsets, d_src, stream, out);
+}
+
+static dmk_status_t run_eval(dmk_stokes_plan_t plan, const double* d_f, const double* d_g, const double* d_n,
+                             double* d_u, double* d_gradu, void* stream) {
+  if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
+  dmk::Plan& p = plan->p;
+  const int64_t N = p.tree.N;
+  const bool want_s = p.opts.kernels & DMK_KERNEL_STOKESLET;
+  const bool want_t = p.opts.kernels & DMK_KERNEL_STRESSLET;
+  if (N > 0) {
+    if (want_s && !d_f) return set_err(plan, DMK_ERR_INVALID_ARG, "d_f is NULL but the Stokeslet is requested");
+    if (want_t && (!d_g || !d_n)) return set_err(plan, DMK_ERR_INVALID_ARG, "d_g / d_n NULL but the stresslet is requested");
+    if (!d_u && !d_gradu) return set_err(plan, DMK_ERR_INVALID_ARG, "d_u is NULL");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  plan->last_stream = s;
+  try {
+    dmk::launch_near(p, want_s ? d_f : nullptr, want_t ? d_g : nullptr, want_t ? d_n : nullptr, d_u, d_gradu, s);
+  } catch (const dmk::Error& e) {
+    return set_err(plan, e.code, e.msg);
+  }
+  return DMK_OK;
+}
+
+dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const double* d_g, const double* d_n,
+                             double* d_u, void* stream) {
+  if (valid_plan(plan) && plan->p.tree.N > 0 && !d_u)
+    return set_err(plan, DMK_ERR_INVALID_ARG, "d_u is NULL");
+  return run_eval(plan, d_f, d_g, d_n, d_u, nullptr, stream);
+}
+
+dmk_status_t dmk_stokes_eval_grad(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
+                                  const double* d_n, double* d_u, double* d_gradu, void* stream) {
+  if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
+  if (plan->p.opts.kernels != DMK_KERNEL_STOKESLET)
+    return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient is provided for the Stokeslet only");
+  if (plan->p.tree.N > 0 && !d_gradu) return set_err(plan, DMK_ERR_INVALID_ARG, "d_gradu is NULL");
+  (void)d_g;
+  (void)d_n;
+  return run_eval(plan, d_f, nullptr, nullptr, d_u, d_gradu, stream);
+}
+
+dmk_status_t dmk_stokes_sync_status(dmk_stokes_plan_t plan) {
+  if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
+  dmk::Plan& p = plan->p;
+  cudaError_t e = cudaStreamSynchronize(plan->last_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
+  if (e != cudaSuccess) return set_err(plan, DMK_ERR_CUDA, cudaGetErrorString(e));
+  e = cudaMemcpy(p.h_status, p.status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_err(plan, DMK_ERR_CUDA, cudaGetErrorString(e));
+  int st = *p.h_status;
+  if (st & dmk::ST_NONFINITE) return set_err(plan, DMK_ERR_INVALID_ARG, "non-finite coordinate");
+  if (st & dmk::ST_OUT_OF_RANGE) return set_err(plan, DMK_ERR_OUT_OF_RANGE, "point outside the unit box");
+  if (st & (dmk::ST_NEAR_OVERFLOW | dmk::ST_TREE_INCONSISTENT))
+    return set_err(plan, DMK_ERR_CUDA, "internal tree inconsistency");
+  return DMK_OK;
+}
+
+dmk_status_t dmk_stokes_plan_stats(dmk_stokes_plan_t plan, int64_t stats[10]) {
+  if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
+  if (!stats) return set_err(plan, DMK_ERR_INVALID_ARG, "stats is NULL");
+  dmk::Plan& p = plan->p;
+  const dmk::DeviceTree& T = p.tree;
+  std::vector<int32_t> lvl(T.n_leaf), cnt(T.n_leaf), off(T.n_leaf + 1), nl(T.n_near);
+  cudaStream_t s = p.stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return set_err(plan, DMK_ERR_CUDA, "stream sync failed");
+  if (T.n_leaf > 0) {
+    cudaMemcpy(lvl.data(), T.leaf_level, T.n_leaf * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaMemcpy(cnt.data(), T.leaf_count, T.n_leaf * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaMemcpy(off.data(), T.near_off, (T.n_leaf + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  }
+  if (T.n_near > 0) cudaMemcpy(nl.data(), T.near_leaf, T.n_near * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  int64_t issued = 0;
+  int maxl = 0;
+  for (int i = 0; i < T.n_leaf; ++i) {
+    maxl = std::max(maxl, lvl[i]);
+    int64_t src = 0;
+    for (int e = off[i]; e < off[i + 1]; ++e) src += cnt[nl[e]];
+    issued += int64_t(cnt[i]) * src - cnt[i];
+  }
+  stats[0] = T.n_leaf;
+  stats[1] = maxl;
+  stats[2] = T.n_near;
+  stats[3] = T.n_tile;
+  stats[4] = issued;
+  stats[5] = static_cast<int64_t>(std::lround(p.tables.c * 3.0 / M_PI));
+  stats[6] = p.leaf_capacity;
+  stats[7] = T.N;
+  if (p.useful_pairs < 0) {
+    try {
+      p.useful_pairs = dmk::count_useful_pairs(p);
+    } catch (const dmk::Error& e) {
+      return set_err(plan, e.code, e.msg);
+    }
+  }
+  stats[8] = p.useful_pairs;
+  stats[9] = p.launches;
+  return DMK_OK;
+}
+
+dmk_status_t dmk_stokes_plan_tree(dmk_stokes_plan_t plan, int32_t* perm, int32_t* leaf_level, int32_t* leaf_start,
+                                  int32_t* leaf_count, int64_t* leaf_coords, int32_t* near_off,
+                                  int32_t* near_leaf, int32_t* near_q) {
+  if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
+  dmk::Plan& p = plan->p;
+  const dmk::DeviceTree& T = p.tree;
+  const int D = p.opts.dim;
+  if (cudaStreamSynchronize(p.stream) != cudaSuccess) return set_err(plan, DMK_ERR_CUDA, "stream sync failed");
+  auto cp = [](void* dst, const void* src, size_t bytes) {
+    if (dst && bytes) cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+  };
+  cp(perm, T.perm, T.N * sizeof(int32_t));
+  cp(leaf_level, T.leaf_level, T.n_leaf * sizeof(int32_t));
+  cp(leaf_start, T.leaf_start, T.n_leaf * sizeof(int32_t));
+  cp(leaf_count, T.leaf_count, T.n_leaf * sizeof(int32_t));
+  cp(near_off, T.near_off, (T.n_leaf + 1) * sizeof(int32_t));
+  cp(near_leaf, T.near_leaf, T.n_near * sizeof(int32_t));
+  if (leaf_coords) {
+    std::vector<uint64_t> anc(T.n_leaf);
+    std::vector<int32_t> lv(T.n_leaf);
+    cp(anc.data(), T.leaf_anchor, T.n_leaf * sizeof(uint64_t));
+    cp(lv.data(), T.leaf_level, T.n_leaf * sizeof(int32_t));
+    for (int i = 0; i < T.n_leaf; ++i) {
+      int64_t c[3];
+      if (D == 3) dmk::leaf_coords<3>(anc[i], lv[i], T.M, c);
+      else dmk::leaf_coords<2>(anc[i], lv[i], T.M, c);
+      for (int a = 0; a < D; ++a) leaf_coords[int64_t(i) * D + a] = c[a];
+    }
+  }
+  if (near_q) {
+    std::vector<int32_t> q(T.n_near);
+    cp(q.data(), T.near_q, T.n_near * sizeof(int32_t));
+    for (int64_t e = 0; e < T.n_near; ++e)
+      for (int a = 0; a < D; ++a) near_q[e * D + a] = dmk::unpack_q(q[e], a);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(plan, DMK_ERR_CUDA, cudaGetErrorString(e));
+  return DMK_OK;
+}
+
+dmk_status_t dmk_stokes_kernel_table(int32_t dim, double eps, int32_t kernels, int32_t which, int32_t fp32,
+                                     double* out_c, double* out_phi0, double* coef, int32_t max_terms,
+                                     int32_t* n_terms) {
+  if (dim != 3) return set_err(nullptr, DMK_ERR_UNSUPPORTED, "2D tables are not provided by this library version");
+  if (which < 0 || which >= dmk::P_COUNT) return set_err(nullptr, DMK_ERR_INVALID_ARG, "bad table id");
+  double c = dmk::bandlimit_for_eps(eps, kernels);
+  if (c <= 0) return set_err(nullptr, DMK_ERR_INVALID_ARG, "eps outside Table 2 range");
+  static thread_local dmk::KernelTables tb;
+  if (dmk::build_tables(dim, c, std::max(eps / 100.0, 1e-8), &tb) != 0)
+    return set_err(nullptr, DMK_ERR_UNSUPPORTED, "table build failed");
+  if (out_c) *out_c = tb.c;
+  if (out_phi0) *out_phi0 = tb.phi0;
+  int n = fp32 ? tb.n32[which] : tb.n64[which];
+  if (n_terms) *n_terms = n;
+  if (coef)
+    for (int k = 0; k < std::min(n, max_terms); ++k) coef[k] = fp32 ? tb.p32[which][k] : tb.p64[which][k];
+  return DMK_OK;
+}
+
+void dmk_stokes_destroy(dmk_stokes_plan_t plan) {
+  if (!valid_plan(plan)) return;
+  // frees go on the plan's stream; order them after work queued on the last
+  // stream an evaluation used
+  if (plan->last_stream != plan->p.stream) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(ev, plan->last_stream);
+      cudaStreamWaitEvent(plan->p.stream, ev, 0);
+      cudaEventDestroy(ev);
+    }
+  }
+  plan->p.magic = 0;
+  release(plan->p);
+  delete plan;
+}
+
+const char* dmk_stokes_last_error(dmk_stokes_plan_t plan) {
+  if (valid_plan(plan)) return plan->p.last_error.c_str();
+  return g_last_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,210 @@
+// Shared definitions of the DMK Stokes near-field library (device + host).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/dmk_stokes.h"
+#include "tables.h"
+
+namespace dmk {
+
+constexpr int kTile = 32;        // points per target / source tile (one warp)
+constexpr int kMaxNear = 64;     // upper bound of a near list (57 in 3D)
+
+// ----------------------------------------------------------------- errors
+struct Error {
+  dmk_status_t code;
+  std::string msg;
+};
+
+#define DMK_CUDA_TRY(expr)                                                         \
+  do {                                                                             \
+    cudaError_t _e = (expr);                                                       \
+    if (_e != cudaSuccess)                                                         \
+      throw ::dmk::Error{_e == cudaErrorMemoryAllocation ? DMK_ERR_NOMEM : DMK_ERR_CUDA,     \
+                         std::string(#expr) + ": " + cudaGetErrorString(_e)};             \
+  } while (0)
+
+// Device status word bits (latched; read by dmk_stokes_sync_status)
+enum : int {
+  ST_OUT_OF_RANGE = 1,      // free-space point outside the unit box
+  ST_NONFINITE = 2,         // NaN / Inf coordinate
+  ST_NEAR_OVERFLOW = 4,     // near list longer than kMaxNear (tree not level-restricted)
+  ST_TREE_INCONSISTENT = 8  // a fine neighbour expected to be a leaf was not
+};
+
+// ------------------------------------------------------------ Morton keys
+// Bits of axis a at level-M resolution sit at positions d*b + a (axis 0 least
+// significant within each group).
+__host__ __device__ inline uint64_t spread3(uint64_t v) {   // 21 bits -> every 3rd
+  v &= 0x1fffffULL;
+  v = (v | (v << 32)) & 0x1f00000000ffffULL;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+  v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+  v = (v | (v << 2)) & 0x1249249249249249ULL;
+  return v;
+}
+__host__ __device__ inline uint64_t compact3(uint64_t v) {
+  v &= 0x1249249249249249ULL;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ULL;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00fULL;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffULL;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffULL;
+  v = (v ^ (v >> 32)) & 0x1fffffULL;
+  return v;
+}
+__host__ __device__ inline uint64_t spread2(uint64_t v) {   // 32 bits -> every 2nd
+  v &= 0xffffffffULL;
+  v = (v | (v << 16)) & 0x0000ffff0000ffffULL;
+  v = (v | (v << 8)) & 0x00ff00ff00ff00ffULL;
+  v = (v | (v << 4)) & 0x0f0f0f0f0f0f0f0fULL;
+  v = (v | (v << 2)) & 0x3333333333333333ULL;
+  v = (v | (v << 1)) & 0x5555555555555555ULL;
+  return v;
+}
+__host__ __device__ inline uint64_t compact2(uint64_t v) {
+  v &= 0x5555555555555555ULL;
+  v = (v ^ (v >> 1)) & 0x3333333333333333ULL;
+  v = (v ^ (v >> 2)) & 0x0f0f0f0f0f0f0f0fULL;
+  v = (v ^ (v >> 4)) & 0x00ff00ff00ff00ffULL;
+  v = (v ^ (v >> 8)) & 0x0000ffff0000ffffULL;
+  v = (v ^ (v >> 16)) & 0x00000000ffffffffULL;
+  return v;
+}
+
+template <int D>
+__host__ __device__ inline uint64_t morton(const int64_t* c) {
+  if (D == 3) return spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2);
+  return spread2(c[0]) | (spread2(c[1]) << 1);
+}
+template <int D>
+__host__ __device__ inline void demorton(uint64_t k, int64_t* c) {
+  if (D == 3) {
+    c[0] = compact3(k);
+    c[1] = compact3(k >> 1);
+    c[2] = compact3(k >> 2);
+  } else {
+    c[0] = compact2(k);
+    c[1] = compact2(k >> 1);
+  }
+}
+
+// integer box coordinates of a leaf at its own level
+template <int D>
+__host__ __device__ inline void leaf_coords(uint64_t anchor, int lev, int M, int64_t* c) {
+  demorton<D>(anchor, c);
+  for (int a = 0; a < D; ++a) c[a] >>= (M - lev);
+}
+
+template <int D>
+__host__ __device__ inline uint64_t box_anchor(const int64_t* c, int lev, int M) {
+  int64_t cc[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) cc[a] = c[a] << (M - lev);
+  return morton<D>(cc);
+}
+
+template <int D> struct MaxLevel;
+template <> struct MaxLevel<3> { static constexpr int value = 21; };
+template <> struct MaxLevel<2> { static constexpr int value = 31; };
+
+// q offsets of a near-list entry, packed 8 bits per axis (values -1, 0, 1)
+__host__ __device__ inline int32_t pack_q(int q0, int q1, int q2) {
+  return (q0 & 0xff) | ((q1 & 0xff) << 8) | ((q2 & 0xff) << 16);
+}
+__host__ __device__ inline int unpack_q(int32_t p, int a) {
+  return static_cast<int>(static_cast<int8_t>((p >> (8 * a)) & 0xff));
+}
+
+// ----------------------------------------------------------------- plan
+struct DeviceTree {
+  int dim = 3;
+  int M = 21;                 // key bits per axis
+  int periodic = 0;
+  int n_sys = 1;
+  int64_t N = 0;              // points (sources == targets)
+  // points, sorted order
+  int32_t* perm = nullptr;    // sorted index -> original index
+  double* w = nullptr;        // in-cell coordinates, SoA [dim][N]
+  float4* rel = nullptr;      // FP32 leaf-centre-relative coordinates, [N]
+  int32_t* point_sys = nullptr;
+  // leaves (sorted by (system, Morton anchor))
+  int32_t n_leaf = 0;
+  uint64_t* leaf_anchor = nullptr;
+  int32_t* leaf_level = nullptr;
+  int32_t* leaf_start = nullptr;
+  int32_t* leaf_count = nullptr;
+  int32_t* leaf_sys = nullptr;
+  int32_t* sys_leaf_begin = nullptr;   // [n_sys + 1]
+  // near lists (CSR)
+  int32_t* near_off = nullptr;         // [n_leaf + 1]
+  int32_t* near_leaf = nullptr;
+  int32_t* near_q = nullptr;
+  int64_t n_near = 0;
+  // tiles
+  int32_t n_tile = 0;
+  int32_t* tile_leaf = nullptr;
+  int32_t* tile_start = nullptr;
+  int32_t* tile_count = nullptr;
+  float4* tile_lo = nullptr;           // bounding box in the leaf-relative frame
+  float4* tile_hi = nullptr;
+  int32_t* leaf_tile0 = nullptr;       // first tile of each leaf
+  int32_t* leaf_ntile = nullptr;
+};
+
+struct Plan {
+  dmk_stokes_opts_t opts{};
+  int leaf_capacity = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  KernelTables tables;
+  DeviceTree tree;
+  // eval workspace (owned by the plan)
+  void* fsorted = nullptr;     // sorted forces (FP32 float4 or FP64 SoA), n_rhs columns
+  size_t fsorted_bytes = 0;
+  double* gn_sorted = nullptr; // stresslet: sorted g (SoA) , n (SoA), g.n
+  double* reduce_buf = nullptr;
+  int* status = nullptr;       // device status word
+  int* h_status = nullptr;     // pinned host mirror
+  std::string last_error;
+  int64_t useful_pairs = -1;   // cached by dmk_stokes_plan_stats
+  mutable int64_t launches = 0;  // kernels launched by this library for this plan
+  uint32_t magic = 0;
+};
+
+constexpr uint32_t kPlanMagic = 0xD3C5A17Bu;
+
+// tree.cu
+void build_tree(Plan& p, const double* d_src, const int64_t* h_offsets);
+void free_tree(DeviceTree& t, cudaStream_t s);
+
+// near.cu
+void launch_near(const Plan& p, const double* d_f, const double* d_g, const double* d_n,
+                 double* d_u, double* d_gradu, cudaStream_t s);
+
+int64_t count_useful_pairs(const Plan& p);
+
+// device memory helper (stream-ordered pool)
+template <typename T>
+T* dalloc(size_t n, cudaStream_t s) {
+  void* ptr = nullptr;
+  if (n == 0) n = 1;
+  DMK_CUDA_TRY(cudaMallocAsync(&ptr, n * sizeof(T), s));
+  return static_cast<T*>(ptr);
+}
+template <typename T>
+void dfree(T*& ptr, cudaStream_t s) {
+  if (ptr) cudaFreeAsync(ptr, s);
+  ptr = nullptr;
+}
+
+inline int grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > (1 << 30)) g = (1 << 30);
+  return static_cast<int>(g);
+}
+
+}  // namespace dmk

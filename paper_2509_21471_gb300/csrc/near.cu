@@ -1,0 +1,295 @@
+// Near-field dispatch, force permutation and the periodic stresslet zero mode.
+#include "near_kernel.cuh"
+
+namespace dmk {
+
+#define DMK_EXT_M(KM, GR, NT) extern template void run_near_mixed3<KM, GR, NT>(const NearParams&, cudaStream_t);
+#define DMK_EXT_M_NT(NT) DMK_FOR_EACH_VARIANT(DMK_EXT_M, NT)
+DMK_NT_MIXED(DMK_EXT_M_NT)
+#define DMK_EXT_D(KM, GR, NT) extern template void run_near_fp64_3<KM, GR, NT>(const NearParams&, cudaStream_t);
+#define DMK_EXT_D_NT(NT) DMK_FOR_EACH_VARIANT(DMK_EXT_D, NT)
+DMK_NT_FP64(DMK_EXT_D_NT)
+
+namespace {
+
+// sorted FP32 copy of a [N][3] FP64 array: out[i] = in[perm[i]]
+__global__ void k_perm_f32(int64_t N, const int32_t* __restrict__ perm, const double* __restrict__ in,
+                           float4* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int64_t o = perm[i];
+  out[i] = make_float4(static_cast<float>(in[o * 3]), static_cast<float>(in[o * 3 + 1]),
+                       static_cast<float>(in[o * 3 + 2]), 0.f);
+}
+
+// sorted orientation vectors with .w = g.n (g.n in FP64, then rounded)
+__global__ void k_perm_n32(int64_t N, const int32_t* __restrict__ perm, const double* __restrict__ g,
+                           const double* __restrict__ n, float4* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int64_t o = perm[i];
+  double gn = g[o * 3] * n[o * 3] + g[o * 3 + 1] * n[o * 3 + 1] + g[o * 3 + 2] * n[o * 3 + 2];
+  out[i] = make_float4(static_cast<float>(n[o * 3]), static_cast<float>(n[o * 3 + 1]),
+                       static_cast<float>(n[o * 3 + 2]), static_cast<float>(gn));
+}
+
+// sorted SoA FP64 copy: out[a*N + i] = in[perm[i]*D + a]
+__global__ void k_perm_soa(int64_t N, int D, const int32_t* __restrict__ perm, const double* __restrict__ in,
+                           double* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int64_t o = perm[i];
+  for (int a = 0; a < D; ++a) out[a * N + i] = in[o * D + a];
+}
+
+__global__ void k_gn64(int64_t N, int D, const double* __restrict__ g, double* __restrict__ n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double s = 0.0;
+  for (int a = 0; a < D; ++a) s += g[a * N + i] * n[a * N + i];
+  n[D * N + i] = s;
+}
+
+// Periodic stresslet k = 0 term (Sec. 5.3, after Eq. (ewald_far)):
+//   u0(x_t) = -sum_s (w_t - w_s)(g_s . n_s) = -( w_t G - W ),
+//   G = sum_s g_s.n_s,  W = sum_s w_s (g_s.n_s), per system.
+__global__ void k_zero_reduce(int64_t N, int D, const double* __restrict__ w, const double* __restrict__ n64,
+                              const int32_t* __restrict__ psys, double* __restrict__ sums) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double gn = n64[D * N + i];
+  double* s = sums + 4 * psys[i];
+  atomicAdd(s, gn);
+  for (int a = 0; a < D; ++a) atomicAdd(s + 1 + a, w[a * N + i] * gn);
+}
+
+__global__ void k_zero_apply(int64_t N, int D, const double* __restrict__ w, const int32_t* __restrict__ perm,
+                             const int32_t* __restrict__ psys, const double* __restrict__ sums,
+                             double* __restrict__ u) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double* s = sums + 4 * psys[i];
+  int64_t o = perm[i];
+  for (int a = 0; a < D; ++a) u[o * D + a] -= w[a * N + i] * s[0] - s[1 + a];
+}
+
+// Number of pairs (t, s) with 0 < r2 < nu_ts^2, decided in float64 exactly as
+// the FP64 kernel does (one warp per target tile; no culling, so it also checks
+// that culling never drops an included pair: compare with the kernels' sums).
+template <int D>
+__global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned long long* out) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * 4 + wid;
+  if (tile >= P.n_tile) return;
+  const int64_t N = P.N;
+  const int B = P.tile_leaf[tile];
+  const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
+  const int LB = P.leaf_level[B];
+  const bool on = lane < nt;
+  double wt[3] = {0.0, 0.0, 0.0};
+  if (on)
+    for (int a = 0; a < D; ++a) wt[a] = P.w[a * N + t0 + lane];
+  unsigned long long cnt = 0;
+  for (int e = P.near_off[B]; e < P.near_off[B + 1]; ++e) {
+    const int X = P.near_leaf[e];
+    const int32_t qp = P.near_q[e];
+    const int Lmin = min(LB, P.leaf_level[X]);
+    const double nu = ldexp(1.0, -(Lmin + 1));
+    const double nu2 = nu * nu;
+    double q[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < D; ++a) q[a] = unpack_q(qp, a);
+    const int U0 = P.leaf_tile0[X], U1 = U0 + P.leaf_ntile[X];
+    if (!on) continue;
+    for (int U = U0; U < U1; ++U) {
+      const int s0 = P.tile_start[U], ns = P.tile_count[U];
+      for (int j = 0; j < ns; ++j) {
+        double r2 = 0.0;
+        for (int a = 0; a < D; ++a) {
+          const double d = __dadd_rn(__dsub_rn(wt[a], P.w[a * N + s0 + j]), q[a]);
+          r2 = __dadd_rn(r2, __dmul_rn(d, d));
+        }
+        if (r2 < nu2 && r2 > 0.0) ++cnt;
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if (lane == 0 && cnt) atomicAdd(out, cnt);
+}
+
+int pick_nt(const int* set, int n, int need) {
+  for (int i = 0; i < n; ++i)
+    if (set[i] >= need) return set[i];
+  return -1;
+}
+
+void dispatch_mixed3(int km, bool grad, int nt, const NearParams& P, cudaStream_t s) {
+#define DMK_CASE(KM, GR, NT) \
+  if (km == KM && grad == GR && nt == NT) { run_near_mixed3<KM, GR, NT>(P, s); return; }
+#define DMK_CASE_NT(NT) DMK_FOR_EACH_VARIANT(DMK_CASE, NT)
+  DMK_NT_MIXED(DMK_CASE_NT)
+#undef DMK_CASE
+#undef DMK_CASE_NT
+  throw Error{DMK_ERR_UNSUPPORTED, "no mixed kernel for this table size"};
+}
+
+void dispatch_fp64_3(int km, bool grad, int nt, const NearParams& P, cudaStream_t s) {
+#define DMK_CASE(KM, GR, NT) \
+  if (km == KM && grad == GR && nt == NT) { run_near_fp64_3<KM, GR, NT>(P, s); return; }
+#define DMK_CASE_NT(NT) DMK_FOR_EACH_VARIANT(DMK_CASE, NT)
+  DMK_NT_FP64(DMK_CASE_NT)
+#undef DMK_CASE
+#undef DMK_CASE_NT
+  throw Error{DMK_ERR_UNSUPPORTED, "no FP64 kernel for this table size"};
+}
+
+}  // namespace
+
+void launch_near(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u,
+                 double* d_gradu, cudaStream_t s) {
+  const DeviceTree& T = p.tree;
+  const int64_t N = T.N;
+  const int D = p.opts.dim;
+  if (D != 3) throw Error{DMK_ERR_UNSUPPORTED, "2D near field is not built in this library version"};
+  const bool mixed = p.opts.precision == DMK_PRECISION_MIXED;
+  const int km = (d_f ? 1 : 0) | (d_g ? 2 : 0);
+  const bool grad = d_gradu != nullptr;
+  if (N == 0) return;
+  const int B = 256;
+
+  NearParams P{};
+  P.N = N;
+  P.n_tile = T.n_tile;
+  P.M = T.M;
+  P.tile_leaf = T.tile_leaf;
+  P.tile_start = T.tile_start;
+  P.tile_count = T.tile_count;
+  P.tile_lo = T.tile_lo;
+  P.tile_hi = T.tile_hi;
+  P.leaf_anchor = T.leaf_anchor;
+  P.leaf_level = T.leaf_level;
+  P.leaf_tile0 = T.leaf_tile0;
+  P.leaf_ntile = T.leaf_ntile;
+  P.near_off = T.near_off;
+  P.near_leaf = T.near_leaf;
+  P.near_q = T.near_q;
+  P.perm = T.perm;
+  P.rel = T.rel;
+  P.w = T.w;
+  P.f_orig = d_f;
+  P.u = d_u;
+  P.gradu = d_gradu;
+  P.self_base = -p.tables.phi0 / (2.0 * M_PI);
+
+  // sorted copies of the densities (plan-owned workspace)
+  char* ws = static_cast<char*>(p.fsorted);
+  if (mixed) {
+    float4* f32 = reinterpret_cast<float4*>(ws);
+    float4* g32 = f32 + N;
+    float4* n32 = g32 + N;
+    if (km & 1) {
+      k_perm_f32<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_f, f32);
+      ++p.launches;
+    }
+    if (km & 2) {
+      k_perm_f32<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_g, g32);
+      ++p.launches;
+      k_perm_n32<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_g, d_n, n32);
+      ++p.launches;
+    }
+    P.f32 = f32;
+    P.g32 = g32;
+    P.n32 = n32;
+  }
+  double* f64 = reinterpret_cast<double*>(ws + (mixed ? 3 * N * sizeof(float4) : 0));
+  double* g64 = f64 + 3 * N;
+  double* n64 = g64 + 3 * N;
+  const bool need64 = !mixed || ((km & 2) && p.opts.periodic);
+  if (need64) {
+    if (km & 1) {
+      k_perm_soa<<<grid_for(N, B), B, 0, s>>>(N, 3, T.perm, d_f, f64);
+      ++p.launches;
+    }
+    if (km & 2) {
+      k_perm_soa<<<grid_for(N, B), B, 0, s>>>(N, 3, T.perm, d_g, g64);
+      ++p.launches;
+      k_perm_soa<<<grid_for(N, B), B, 0, s>>>(N, 3, T.perm, d_n, n64);
+      ++p.launches;
+      k_gn64<<<grid_for(N, B), B, 0, s>>>(N, 3, g64, n64);
+      ++p.launches;
+    }
+  }
+  P.f64 = f64;
+  P.g64 = g64;
+  P.n64 = n64;
+  DMK_CUDA_TRY(cudaGetLastError());
+
+  const KernelTables& tb = p.tables;
+  int need = 1;
+  const int ids[4] = {(km & 1) ? P_GS : -1, (km & 1) ? P_HS : -1, (km & 2) ? P_PT : -1, (km & 2) ? P_QT : -1};
+  for (int id : ids)
+    if (id >= 0) need = std::max(need, mixed ? tb.n32[id] : tb.n64[id]);
+  if (grad) need = std::max(need, std::max(mixed ? tb.n32[P_DGS] : tb.n64[P_DGS], mixed ? tb.n32[P_DHS] : tb.n64[P_DHS]));
+  static const int kSetM[] = {8, 12, 16, 20, 24};
+  static const int kSetD[] = {16, 20, 24, 28, 32};
+  int nt = mixed ? pick_nt(kSetM, 5, need) : pick_nt(kSetD, 5, need);
+  if (nt < 0) throw Error{DMK_ERR_UNSUPPORTED, "kernel table longer than the compiled kernels"};
+  for (int id = 0; id < P_COUNT; ++id)
+    for (int k = 0; k < kPolyCap; ++k) {
+      P.c32[id][k] = k < tb.n32[id] ? tb.p32[id][k] : 0.f;
+      P.c64[id][k] = k < tb.n64[id] ? tb.p64[id][k] : 0.0;
+    }
+  if (T.n_tile > 0) {
+    if (mixed) dispatch_mixed3(km, grad, nt, P, s);
+    else dispatch_fp64_3(km, grad, nt, P, s);
+    ++p.launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+  }
+
+  if ((km & 2) && p.opts.periodic && d_u) {
+    DMK_CUDA_TRY(cudaMemsetAsync(p.reduce_buf, 0, 4 * sizeof(double) * T.n_sys, s));
+    k_zero_reduce<<<grid_for(N, B), B, 0, s>>>(N, 3, T.w, n64, T.point_sys, p.reduce_buf);
+    ++p.launches;
+    k_zero_apply<<<grid_for(N, B), B, 0, s>>>(N, 3, T.w, T.perm, T.point_sys, p.reduce_buf, d_u);
+    ++p.launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+  }
+}
+
+int64_t count_useful_pairs(const Plan& p) {
+  const DeviceTree& T = p.tree;
+  if (T.N == 0 || T.n_tile == 0) return 0;
+  NearParams P{};
+  P.N = T.N;
+  P.n_tile = T.n_tile;
+  P.tile_leaf = T.tile_leaf;
+  P.tile_start = T.tile_start;
+  P.tile_count = T.tile_count;
+  P.leaf_level = T.leaf_level;
+  P.leaf_tile0 = T.leaf_tile0;
+  P.leaf_ntile = T.leaf_ntile;
+  P.near_off = T.near_off;
+  P.near_leaf = T.near_leaf;
+  P.near_q = T.near_q;
+  P.w = T.w;
+  unsigned long long* d = dalloc<unsigned long long>(1, p.stream);
+  DMK_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), p.stream));
+  if (p.opts.dim == 3) k_count_useful<3><<<(T.n_tile + 3) / 4, 128, 0, p.stream>>>(P, d);
+  else k_count_useful<2><<<(T.n_tile + 3) / 4, 128, 0, p.stream>>>(P, d);
+  ++p.launches;
+  DMK_CUDA_TRY(cudaGetLastError());
+  unsigned long long h = 0;
+  DMK_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, p.stream));
+  DMK_CUDA_TRY(cudaStreamSynchronize(p.stream));
+  dfree(d, p.stream);
+  return static_cast<int64_t>(h);
+}
+
+size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N) {
+  const bool mixed = o.precision == DMK_PRECISION_MIXED;
+  size_t b = 0;
+  if (mixed) b += 3 * N * sizeof(float4);
+  b += (3 + 3 + 4) * N * sizeof(double);
+  return b;
+}
+
+}  // namespace dmk

@@ -1,0 +1,409 @@
+// Near-field (residual + self) kernels, 3D.
+//
+// Sec. 5.2, Eqs. (res_stokeslet), (Soffdiag), (res_stresslet), (T-offd), with
+// the length-scale remark closing Sec. 5.2 (real-space functions at rho = r/nu).
+// With the even polynomials gS, hS, pT, qT of s = rho^2 (tables.h) and r < nu:
+//
+//   S_R f  = [ (1/r + gS/nu) f + (1/r^3 + hS/(nu r^2)) (x.f) x ] / (8 pi)
+//   T_R:(g n) = [ pT/(nu r^2) (g (x.n) + x (g.n) + n (x.g))
+//                 - 6 (1/r^5 + qT/(nu r^4)) x (x.g)(x.n) ] / (8 pi)
+//
+// Gradient (Stokeslet; derivative of Eq. (res_stokeslet), tree held fixed):
+//   d_m (S_R f)_j = A1 x_m f_j + C1 x_m x_j (x.f) + C (delta_jm (x.f) + x_j f_m)
+//   A1 = (-1/r^3 + 2 gS'/nu^3) / 8pi,
+//   C1 = (-3/r^5 + 2 hS'/(nu^3 r^2) - 2 hS/(nu r^4)) / 8pi,   ' = d/ds.
+//
+// Work decomposition: one warp per target tile (<= 32 points of one leaf, one
+// target per lane).  The warp walks its leaf's near list (leaf X, image offset
+// q, scale nu = 2^-(min(L_B, L_X)+1)), skips source tiles whose bounding box
+// is farther than nu from the target tile's box, stages the surviving source
+// tile in shared memory and sums the included pairs (0 < r^2 < nu^2).
+//
+// MIXED: coordinates are FP32 offsets from the leaf centre; a source is moved
+// into the target leaf's frame by the exact dyadic offset (c_X - c_B - q),
+// computed in integers.  Pair terms are FP32 (rsqrt + one Newton step), each
+// source tile's partial sum is added to a two-sum (hi, lo) accumulator.
+// FP64: coordinates are the in-cell FP64 values; the pair displacement is
+// (w_t - w_s) + q and r^2 = (dx*dx + dy*dy) + dz*dz without fused operations,
+// so the r < nu decision is the same as in a plain FP64 evaluation.
+#pragma once
+#include "common.cuh"
+
+namespace dmk {
+
+constexpr int kPolyCap = 32;
+
+struct NearParams {
+  int64_t N;
+  int n_tile;
+  int M;
+  const int32_t* tile_leaf;
+  const int32_t* tile_start;
+  const int32_t* tile_count;
+  const float4* tile_lo;
+  const float4* tile_hi;
+  const uint64_t* leaf_anchor;
+  const int32_t* leaf_level;
+  const int32_t* leaf_tile0;
+  const int32_t* leaf_ntile;
+  const int32_t* near_off;
+  const int32_t* near_leaf;
+  const int32_t* near_q;
+  const int32_t* perm;
+  const float4* rel;     // mixed: leaf-relative FP32 coordinates (sorted)
+  const double* w;       // FP64 in-cell coordinates, SoA [3][N] (sorted)
+  const float4* f32;     // mixed, sorted Stokeslet forces
+  const float4* g32;     // mixed, sorted stresslet strengths
+  const float4* n32;     // mixed, sorted orientations, .w = g.n
+  const double* f64;     // FP64 sorted forces SoA [3][N]
+  const double* g64;     // FP64 sorted strengths SoA [3][N]
+  const double* n64;     // FP64 sorted orientations SoA [3][N] (+ [3] g.n)
+  const double* f_orig;  // caller's forces [N][3] (self term)
+  double* u;             // [N][3] caller order (may be null for grad-only)
+  double* gradu;         // [N][3][3] caller order
+  double self_base;      // -phi(0) / (2 pi)
+  float c32[P_COUNT][kPolyCap];
+  double c64[P_COUNT][kPolyCap];
+};
+
+template <int NT, typename T>
+__device__ __forceinline__ T horner(const T (&c)[kPolyCap], T t) {
+  T v = c[NT - 1];
+#pragma unroll
+  for (int k = NT - 2; k >= 0; --k) v = fma(v, t, c[k]);
+  return v;
+}
+
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+  float s = hi + x;
+  float bp = s - hi;
+  float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+
+constexpr double kInv8Pi = 0.039788735772973836;   // 1 / (8 pi)
+
+// ---------------------------------------------------------------- mixed
+template <int KM, bool GRAD, int NT>
+__global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ NearParams P) {
+  constexpr int D = 3;
+  __shared__ float4 s_pos[4][kTile];
+  __shared__ float4 s_f[(KM & 1) ? 4 : 1][kTile];
+  __shared__ float4 s_g[(KM & 2) ? 4 : 1][kTile];
+  __shared__ float4 s_n[(KM & 2) ? 4 : 1][kTile];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * 4 + wid;
+  if (tile >= P.n_tile) return;
+  const int B = P.tile_leaf[tile];
+  const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
+  const int LB = P.leaf_level[B];
+  int64_t cB[3];
+  leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
+  const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
+  const bool on = lane < nt;
+  const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+
+  float uh[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
+  float Gh[GRAD ? 9 : 1], Gl[GRAD ? 9 : 1];
+#pragma unroll
+  for (int k = 0; k < (GRAD ? 9 : 1); ++k) Gh[k] = Gl[k] = 0.f;
+
+  const int e1 = P.near_off[B + 1];
+  for (int e = P.near_off[B]; e < e1; ++e) {
+    const int X = P.near_leaf[e];
+    const int32_t qp = P.near_q[e];
+    const int LX = P.leaf_level[X];
+    const int Lmin = min(LB, LX), Lmax = max(LB, LX);
+    const float nuinv = ldexpf(1.f, Lmin + 1);
+    const float nu = ldexpf(1.f, -(Lmin + 1));
+    const float nu2 = nu * nu;
+    const float tscale = 2.f * nuinv * nuinv;
+    int64_t cX[3];
+    leaf_coords<D>(P.leaf_anchor[X], LX, P.M, cX);
+    float off[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int64_t v = ((2 * cX[a] + 1) << (Lmax - LX)) - ((2 * cB[a] + 1) << (Lmax - LB)) -
+                  (static_cast<int64_t>(unpack_q(qp, a)) << (Lmax + 1));
+      off[a] = ldexpf(static_cast<float>(v), -(Lmax + 1));
+    }
+    const float cull = nu2 * 1.0001f;
+    const int U0 = P.leaf_tile0[X], U1 = U0 + P.leaf_ntile[X];
+    for (int U = U0; U < U1; ++U) {
+      const float4 slo = P.tile_lo[U], shi = P.tile_hi[U];
+      float gx = fmaxf(fmaxf(slo.x + off[0] - thi.x, tlo.x - (shi.x + off[0])), 0.f);
+      float gy = fmaxf(fmaxf(slo.y + off[1] - thi.y, tlo.y - (shi.y + off[1])), 0.f);
+      float gz = fmaxf(fmaxf(slo.z + off[2] - thi.z, tlo.z - (shi.z + off[2])), 0.f);
+      if (gx * gx + gy * gy + gz * gz >= cull) continue;
+      const int s0 = P.tile_start[U], ns = P.tile_count[U];
+      __syncwarp();
+      if (lane < ns) {
+        const float4 r = P.rel[s0 + lane];
+        s_pos[wid][lane] = make_float4(r.x + off[0], r.y + off[1], r.z + off[2], 0.f);
+        if (KM & 1) s_f[(KM & 1) ? wid : 0][lane] = P.f32[s0 + lane];
+        if (KM & 2) {
+          s_g[(KM & 2) ? wid : 0][lane] = P.g32[s0 + lane];
+          s_n[(KM & 2) ? wid : 0][lane] = P.n32[s0 + lane];
+        }
+      }
+      __syncwarp();
+      if (!on) continue;
+      float p[3] = {0.f, 0.f, 0.f};
+      float pg[GRAD ? 9 : 1];
+#pragma unroll
+      for (int k = 0; k < (GRAD ? 9 : 1); ++k) pg[k] = 0.f;
+      for (int j = 0; j < ns; ++j) {
+        const float4 sp = s_pos[wid][j];
+        const float dx = xt.x - sp.x, dy = xt.y - sp.y, dz = xt.z - sp.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (r2 < nu2 && r2 > 0.f) {
+          float ri = rsqrtf(r2);
+          ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);      // one Newton step
+          const float t = fmaf(r2, tscale, -1.f);
+          const float ri2 = ri * ri;
+          if (KM & 1) {
+            const float g = horner<NT>(P.c32[P_GS], t);
+            const float h = horner<NT>(P.c32[P_HS], t);
+            const float A = fmaf(g, nuinv, ri);
+            const float C = ri2 * fmaf(h, nuinv, ri);
+            const float4 fs = s_f[(KM & 1) ? wid : 0][j];
+            const float xf = fmaf(dx, fs.x, fmaf(dy, fs.y, dz * fs.z));
+            const float Cx = C * xf;
+            p[0] = fmaf(A, fs.x, fmaf(Cx, dx, p[0]));
+            p[1] = fmaf(A, fs.y, fmaf(Cx, dy, p[1]));
+            p[2] = fmaf(A, fs.z, fmaf(Cx, dz, p[2]));
+            if (GRAD) {
+              const float dg = horner<NT>(P.c32[P_DGS], t);
+              const float dh = horner<NT>(P.c32[P_DHS], t);
+              const float nu3i = nuinv * nuinv * nuinv;
+              const float ri3 = ri2 * ri;
+              const float A1 = fmaf(2.f * dg, nu3i, -ri3);
+              const float C1 = fmaf(-3.f * ri3, ri2, ri2 * fmaf(2.f * dh, nu3i, -2.f * h * nuinv * ri2));
+              const float xv[3] = {dx, dy, dz};
+              const float fv[3] = {fs.x, fs.y, fs.z};
+#pragma unroll
+              for (int jj = 0; jj < 3; ++jj) {
+                const float a1 = fmaf(A1, fv[jj], C1 * xv[jj] * xf);
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                  float v = fmaf(a1, xv[m], C * xv[jj] * fv[m]);
+                  if (jj == m) v = fmaf(C, xf, v);
+                  pg[jj * 3 + m] += v;
+                }
+              }
+            }
+          }
+          if (KM & 2) {
+            const float pt = horner<NT>(P.c32[P_PT], t);
+            const float qt = horner<NT>(P.c32[P_QT], t);
+            const float4 gs = s_g[(KM & 2) ? wid : 0][j];
+            const float4 nsv = s_n[(KM & 2) ? wid : 0][j];
+            const float xn = fmaf(dx, nsv.x, fmaf(dy, nsv.y, dz * nsv.z));
+            const float xg = fmaf(dx, gs.x, fmaf(dy, gs.y, dz * gs.z));
+            const float Dc = pt * nuinv * ri2;
+            const float Ec = -6.f * ri2 * ri2 * fmaf(qt, nuinv, ri);
+            const float Ex = Ec * xg * xn + Dc * nsv.w;      // coefficient of x
+            p[0] += fmaf(Dc, fmaf(gs.x, xn, nsv.x * xg), Ex * dx);
+            p[1] += fmaf(Dc, fmaf(gs.y, xn, nsv.y * xg), Ex * dy);
+            p[2] += fmaf(Dc, fmaf(gs.z, xn, nsv.z * xg), Ex * dz);
+          }
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) two_sum_add(uh[a], ul[a], p[a]);
+      if (GRAD) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) two_sum_add(Gh[k], Gl[k], pg[k]);
+      }
+    }
+  }
+  if (!on) return;
+  const int64_t o = P.perm[t0 + lane];
+  const double nutinv = ldexp(1.0, LB + 1);
+  if (P.u) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double v = (static_cast<double>(uh[a]) + static_cast<double>(ul[a])) * kInv8Pi;
+      if (KM & 1) v += P.self_base * nutinv * P.f_orig[o * 3 + a];
+      P.u[o * 3 + a] = v;
+    }
+  }
+  if (GRAD) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+      P.gradu[o * 9 + k] = (static_cast<double>(Gh[k]) + static_cast<double>(Gl[k])) * kInv8Pi;
+  }
+}
+
+// ----------------------------------------------------------------- FP64
+template <int KM, bool GRAD, int NT>
+__global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ NearParams P) {
+  constexpr int D = 3;
+  constexpr int NF = 3 + ((KM & 1) ? 3 : 0) + ((KM & 2) ? 7 : 0);
+  __shared__ double s_src[4][NF][kTile];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * 4 + wid;
+  if (tile >= P.n_tile) return;
+  const int64_t N = P.N;
+  const int B = P.tile_leaf[tile];
+  const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
+  const int LB = P.leaf_level[B];
+  int64_t cB[3];
+  leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
+  const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
+  const bool on = lane < nt;
+  double wt[3] = {0.0, 0.0, 0.0};
+  if (on)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) wt[a] = P.w[a * N + t0 + lane];
+
+  double acc[3] = {0.0, 0.0, 0.0};
+  double G[GRAD ? 9 : 1];
+#pragma unroll
+  for (int k = 0; k < (GRAD ? 9 : 1); ++k) G[k] = 0.0;
+
+  const int e1 = P.near_off[B + 1];
+  for (int e = P.near_off[B]; e < e1; ++e) {
+    const int X = P.near_leaf[e];
+    const int32_t qp = P.near_q[e];
+    const int LX = P.leaf_level[X];
+    const int Lmin = min(LB, LX), Lmax = max(LB, LX);
+    const double nuinv = ldexp(1.0, Lmin + 1);
+    const double nu = ldexp(1.0, -(Lmin + 1));
+    const double nu2 = nu * nu;
+    const double tscale = 2.0 * nuinv * nuinv;
+    const double q[3] = {static_cast<double>(unpack_q(qp, 0)), static_cast<double>(unpack_q(qp, 1)),
+                         static_cast<double>(unpack_q(qp, 2))};
+    int64_t cX[3];
+    leaf_coords<D>(P.leaf_anchor[X], LX, P.M, cX);
+    float off[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int64_t v = ((2 * cX[a] + 1) << (Lmax - LX)) - ((2 * cB[a] + 1) << (Lmax - LB)) -
+                  (static_cast<int64_t>(unpack_q(qp, a)) << (Lmax + 1));
+      off[a] = ldexpf(static_cast<float>(v), -(Lmax + 1));
+    }
+    const float cull = static_cast<float>(nu2) * 1.0001f;
+    const int U0 = P.leaf_tile0[X], U1 = U0 + P.leaf_ntile[X];
+    for (int U = U0; U < U1; ++U) {
+      const float4 slo = P.tile_lo[U], shi = P.tile_hi[U];
+      float gx = fmaxf(fmaxf(slo.x + off[0] - thi.x, tlo.x - (shi.x + off[0])), 0.f);
+      float gy = fmaxf(fmaxf(slo.y + off[1] - thi.y, tlo.y - (shi.y + off[1])), 0.f);
+      float gz = fmaxf(fmaxf(slo.z + off[2] - thi.z, tlo.z - (shi.z + off[2])), 0.f);
+      if (gx * gx + gy * gy + gz * gz >= cull) continue;
+      const int s0 = P.tile_start[U], ns = P.tile_count[U];
+      __syncwarp();
+      if (lane < ns) {
+        const int64_t sidx = s0 + lane;
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s_src[wid][k++][lane] = P.w[a * N + sidx];
+        if (KM & 1)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) s_src[wid][k++][lane] = P.f64[a * N + sidx];
+        if (KM & 2) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) s_src[wid][k++][lane] = P.g64[a * N + sidx];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) s_src[wid][k++][lane] = P.n64[a * N + sidx];
+        }
+      }
+      __syncwarp();
+      if (!on) continue;
+      for (int j = 0; j < ns; ++j) {
+        const double dx = __dadd_rn(__dsub_rn(wt[0], s_src[wid][0][j]), q[0]);
+        const double dy = __dadd_rn(__dsub_rn(wt[1], s_src[wid][1][j]), q[1]);
+        const double dz = __dadd_rn(__dsub_rn(wt[2], s_src[wid][2][j]), q[2]);
+        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        if (r2 < nu2 && r2 > 0.0) {
+          const double ri = 1.0 / sqrt(r2);
+          const double t = fma(r2, tscale, -1.0);
+          const double ri2 = ri * ri;
+          int k = 3;
+          if (KM & 1) {
+            const double g = horner<NT>(P.c64[P_GS], t);
+            const double h = horner<NT>(P.c64[P_HS], t);
+            const double A = fma(g, nuinv, ri);
+            const double C = ri2 * fma(h, nuinv, ri);
+            const double fx = s_src[wid][k][j], fy = s_src[wid][k + 1][j], fz = s_src[wid][k + 2][j];
+            k += 3;
+            const double xf = fma(dx, fx, fma(dy, fy, dz * fz));
+            const double Cx = C * xf;
+            acc[0] = fma(A, fx, fma(Cx, dx, acc[0]));
+            acc[1] = fma(A, fy, fma(Cx, dy, acc[1]));
+            acc[2] = fma(A, fz, fma(Cx, dz, acc[2]));
+            if (GRAD) {
+              const double dg = horner<NT>(P.c64[P_DGS], t);
+              const double dh = horner<NT>(P.c64[P_DHS], t);
+              const double nu3i = nuinv * nuinv * nuinv;
+              const double ri3 = ri2 * ri;
+              const double A1 = fma(2.0 * dg, nu3i, -ri3);
+              const double C1 = fma(-3.0 * ri3, ri2, ri2 * fma(2.0 * dh, nu3i, -2.0 * h * nuinv * ri2));
+              const double xv[3] = {dx, dy, dz};
+              const double fv[3] = {fx, fy, fz};
+#pragma unroll
+              for (int jj = 0; jj < 3; ++jj) {
+                const double a1 = fma(A1, fv[jj], C1 * xv[jj] * xf);
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                  double v = fma(a1, xv[m], C * xv[jj] * fv[m]);
+                  if (jj == m) v = fma(C, xf, v);
+                  G[jj * 3 + m] += v;
+                }
+              }
+            }
+          }
+          if (KM & 2) {
+            const double pt = horner<NT>(P.c64[P_PT], t);
+            const double qt = horner<NT>(P.c64[P_QT], t);
+            const double gx_ = s_src[wid][k][j], gy_ = s_src[wid][k + 1][j], gz_ = s_src[wid][k + 2][j];
+            const double nx = s_src[wid][k + 3][j], ny = s_src[wid][k + 4][j], nz = s_src[wid][k + 5][j];
+            const double gn = s_src[wid][k + 6][j];
+            const double xn = fma(dx, nx, fma(dy, ny, dz * nz));
+            const double xg = fma(dx, gx_, fma(dy, gy_, dz * gz_));
+            const double Dc = pt * nuinv * ri2;
+            const double Ec = -6.0 * ri2 * ri2 * fma(qt, nuinv, ri);
+            const double Ex = Ec * xg * xn + Dc * gn;
+            acc[0] += fma(Dc, fma(gx_, xn, nx * xg), Ex * dx);
+            acc[1] += fma(Dc, fma(gy_, xn, ny * xg), Ex * dy);
+            acc[2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
+          }
+        }
+      }
+    }
+  }
+  if (!on) return;
+  const int64_t o = P.perm[t0 + lane];
+  const double nutinv = ldexp(1.0, LB + 1);
+  if (P.u) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double v = acc[a] * kInv8Pi;
+      if (KM & 1) v += P.self_base * nutinv * P.f_orig[o * 3 + a];
+      P.u[o * 3 + a] = v;
+    }
+  }
+  if (GRAD) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) P.gradu[o * 9 + k] = G[k] * kInv8Pi;
+  }
+}
+
+template <int KM, bool GRAD, int NT>
+void run_near_mixed3(const NearParams& P, cudaStream_t s) {
+  k_near_mixed3<KM, GRAD, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P);
+}
+template <int KM, bool GRAD, int NT>
+void run_near_fp64_3(const NearParams& P, cudaStream_t s) {
+  k_near_fp64_3<KM, GRAD, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P);
+}
+
+// instantiation lists (near_mixed.cu, near_fp64.cu)
+#define DMK_FOR_EACH_VARIANT(M, NT) \
+  M(1, false, NT) M(2, false, NT) M(3, false, NT) M(1, true, NT)
+
+#define DMK_NT_MIXED(X) X(8) X(12) X(16) X(20) X(24)
+#define DMK_NT_FP64(X) X(16) X(20) X(24) X(28) X(32)
+
+}  // namespace dmk

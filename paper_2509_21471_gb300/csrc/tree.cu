@@ -1,0 +1,600 @@
+// GPU adaptive, level-restricted quad/oct-tree with near lists and tiles.
+//
+// Sec. 6.1 Step 1: (a) split boxes until a leaf holds at most n_s points;
+// (b) level-restrict: leaves that share a boundary point differ by at most one
+// level (in the periodic case across the wrap too, Fig. 2 / Sec. 6.2).
+// Near list of a leaf = the leaves sharing a boundary point with it (colleague,
+// coarse and fine neighbours, itself included), with periodic image offsets q
+// (pair displacement (w_t - w_s) + q).  This is the FMM list 1 of the remark
+// after Step 4.
+//
+// Representation: a linear quad/oct-tree.  Points are sorted by Morton key of
+// their finest-level cell (M = 21 bits per axis in 3D, 31 in 2D); a leaf is the
+// pair (anchor key, level) and owns a contiguous range of sorted points.
+// Leaves are kept sorted by (system, anchor), so "the leaf containing cell k"
+// is the last leaf whose anchor is <= k (binary search).
+//
+// Coordinates: w = x - lo; periodic: w -= floor(w); cell = min(floor(w 2^M),
+// 2^M - 1) per axis (the top face belongs to the last box).
+#include <cub/cub.cuh>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace dmk {
+namespace {
+
+struct LeafArrays {
+  uint64_t* anchor = nullptr;
+  int32_t* level = nullptr;
+  int32_t* start = nullptr;
+  int32_t* count = nullptr;
+  int32_t* sys = nullptr;
+};
+
+void alloc_leaves(LeafArrays& L, int64_t n, cudaStream_t s) {
+  L.anchor = dalloc<uint64_t>(n, s);
+  L.level = dalloc<int32_t>(n, s);
+  L.start = dalloc<int32_t>(n, s);
+  L.count = dalloc<int32_t>(n, s);
+  L.sys = dalloc<int32_t>(n, s);
+}
+void free_leaves(LeafArrays& L, cudaStream_t s) {
+  dfree(L.anchor, s);
+  dfree(L.level, s);
+  dfree(L.start, s);
+  dfree(L.count, s);
+  dfree(L.sys, s);
+}
+
+template <int D>
+__device__ inline double in_cell(double x, double lo, int periodic) {
+  double w = x - lo;
+  if (periodic) w = w - floor(w);
+  return w;
+}
+
+template <int D>
+__global__ void k_keys(int64_t N, const double* __restrict__ x, double lo0, double lo1, double lo2,
+                       int periodic, int M, uint64_t* __restrict__ key, int32_t* __restrict__ idx,
+                       int* __restrict__ status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double lo[3] = {lo0, lo1, lo2};
+  const double scale = ldexp(1.0, M);
+  const int64_t cmax = (int64_t(1) << M) - 1;
+  int64_t c[3] = {0, 0, 0};
+  for (int a = 0; a < D; ++a) {
+    double xa = x[i * D + a];
+    if (!isfinite(xa)) {
+      atomicOr(status, ST_NONFINITE);
+      xa = lo[a];
+    }
+    double w = in_cell<D>(xa, lo[a], periodic);
+    if (!periodic && (w < 0.0 || w > 1.0)) {
+      atomicOr(status, ST_OUT_OF_RANGE);
+      w = fmin(fmax(w, 0.0), 1.0);
+    }
+    int64_t ci = static_cast<int64_t>(floor(w * scale));
+    c[a] = ci < 0 ? 0 : (ci > cmax ? cmax : ci);
+  }
+  key[i] = morton<D>(c);
+  idx[i] = static_cast<int32_t>(i);
+}
+
+template <int D>
+__global__ void k_gather_w(int64_t N, const double* __restrict__ x, const int32_t* __restrict__ perm,
+                           double lo0, double lo1, double lo2, int periodic, double* __restrict__ w) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double lo[3] = {lo0, lo1, lo2};
+  int64_t o = perm[i];
+  for (int a = 0; a < D; ++a) {
+    double xa = x[o * D + a];
+    if (!isfinite(xa)) xa = lo[a];
+    double v = in_cell<D>(xa, lo[a], periodic);
+    if (!periodic) v = fmin(fmax(v, 0.0), 1.0);
+    w[a * N + i] = v;
+  }
+}
+
+__global__ void k_init_roots(int n_sys, const int32_t* __restrict__ offs, LeafArrays L) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_sys) return;
+  L.anchor[k] = 0;
+  L.level[k] = 0;
+  L.start[k] = offs[k];
+  L.count[k] = offs[k + 1] - offs[k];
+  L.sys[k] = k;
+}
+
+template <int D>
+__global__ void k_split_flags(int n, LeafArrays L, int ns, int M, const int32_t* __restrict__ flag,
+                              int32_t* __restrict__ nchild) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool split = flag ? (flag[i] != 0) : (L.count[i] > ns && L.level[i] < M);
+  nchild[i] = split ? (1 << D) : 1;
+}
+
+__device__ inline int32_t lower_bound_key(const uint64_t* __restrict__ keys, int32_t lo, int32_t hi,
+                                          uint64_t k) {
+  while (lo < hi) {
+    int32_t mid = lo + ((hi - lo) >> 1);
+    if (keys[mid] < k) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+template <int D>
+__global__ void k_refine(int n, LeafArrays in, const int32_t* __restrict__ nchild,
+                         const int32_t* __restrict__ pos, LeafArrays out,
+                         const uint64_t* __restrict__ skeys, int M) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t p = pos[i];
+  if (nchild[i] == 1) {
+    out.anchor[p] = in.anchor[i];
+    out.level[p] = in.level[i];
+    out.start[p] = in.start[i];
+    out.count[p] = in.count[i];
+    out.sys[p] = in.sys[i];
+    return;
+  }
+  int lev = in.level[i];
+  int sh = D * (M - lev - 1);
+  uint64_t span = uint64_t(1) << sh;
+  int32_t s0 = in.start[i], s1 = in.start[i] + in.count[i];
+  int32_t b = s0;
+  for (int j = 0; j < (1 << D); ++j) {
+    uint64_t ca = in.anchor[i] + (uint64_t(j) << sh);
+    int32_t e = (j == (1 << D) - 1) ? s1 : lower_bound_key(skeys, b, s1, ca + span);
+    out.anchor[p + j] = ca;
+    out.level[p + j] = lev + 1;
+    out.start[p + j] = b;
+    out.count[p + j] = e - b;
+    out.sys[p + j] = in.sys[i];
+    b = e;
+  }
+}
+
+__global__ void k_sys_begin(int n, int n_sys, const int32_t* __restrict__ sys, int32_t* __restrict__ begin) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (i == 0 || sys[i] != sys[i - 1]) begin[sys[i]] = i;
+  if (i == n - 1) begin[n_sys] = n;
+}
+
+// last leaf in [b, e) with anchor <= key
+__device__ inline int32_t find_leaf(const uint64_t* __restrict__ anchor, int32_t b, int32_t e, uint64_t key) {
+  int32_t lo = b, hi = e;   // first index with anchor > key
+  while (lo < hi) {
+    int32_t mid = lo + ((hi - lo) >> 1);
+    if (anchor[mid] <= key) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
+}
+
+template <int D>
+__device__ inline bool neighbour(const int64_t* c, const int* dl, int lev, int periodic, int64_t* nb, int* q) {
+  const int64_t n = int64_t(1) << lev;
+  for (int a = 0; a < D; ++a) {
+    int64_t v = c[a] + dl[a];
+    q[a] = 0;
+    if (v < 0 || v >= n) {
+      if (!periodic) return false;
+      if (v < 0) { v += n; q[a] = 1; }        // image shifted by -1: q = +1
+      else { v -= n; q[a] = -1; }
+    }
+    nb[a] = v;
+  }
+  return true;
+}
+
+template <int D>
+__global__ void k_balance(int n, LeafArrays L, const int32_t* __restrict__ begin, int M, int periodic,
+                          int32_t* __restrict__ flag, int* __restrict__ any) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int lev = L.level[i];
+  if (lev < 2) return;
+  int64_t c[3];
+  leaf_coords<D>(L.anchor[i], lev, M, c);
+  int32_t b = begin[L.sys[i]], e = begin[L.sys[i] + 1];
+  const int ndir = (D == 3) ? 27 : 9;
+  for (int k = 0; k < ndir; ++k) {
+    int dl[3] = {k % 3 - 1, (k / 3) % 3 - 1, (k / 9) % 3 - 1};
+    if (dl[0] == 0 && dl[1] == 0 && (D == 2 || dl[2] == 0)) continue;
+    int64_t nb[3];
+    int q[3];
+    if (!neighbour<D>(c, dl, lev, periodic, nb, q)) continue;
+    int32_t X = find_leaf(L.anchor, b, e, box_anchor<D>(nb, lev, M));
+    if (L.level[X] < lev - 1) {
+      flag[X] = 1;
+      *any = 1;
+    }
+  }
+}
+
+// Enumerates the near list of leaf i; calls emit(X, qpacked) for each entry.
+template <int D, typename F>
+__device__ inline int near_entries(int i, const LeafArrays& L, const int32_t* __restrict__ begin, int M,
+                                   int periodic, int* status, F emit) {
+  int lev = L.level[i];
+  int64_t c[3];
+  leaf_coords<D>(L.anchor[i], lev, M, c);
+  int32_t b = begin[L.sys[i]], e = begin[L.sys[i] + 1];
+  int32_t got_leaf[kMaxNear];
+  int32_t got_q[kMaxNear];
+  int cnt = 0;
+  const int ndir = (D == 3) ? 27 : 9;
+  for (int k = 0; k < ndir; ++k) {
+    int dl[3] = {k % 3 - 1, (k / 3) % 3 - 1, D == 3 ? (k / 9) % 3 - 1 : 0};
+    int64_t nb[3];
+    int q[3];
+    if (!neighbour<D>(c, dl, lev, periodic, nb, q)) continue;
+    int32_t qp = pack_q(q[0], q[1], D == 3 ? q[2] : 0);
+    int32_t X = find_leaf(L.anchor, b, e, box_anchor<D>(nb, lev, M));
+    int32_t cand[4];
+    int nc = 0;
+    if (L.level[X] <= lev) {
+      cand[nc++] = X;
+    } else {
+      for (int j = 0; j < (1 << D); ++j) {
+        int o[3] = {j & 1, (j >> 1) & 1, (j >> 2) & 1};
+        bool ok = true;
+        for (int a = 0; a < D; ++a) {
+          if (dl[a] == 1 && o[a] != 0) ok = false;
+          if (dl[a] == -1 && o[a] != 1) ok = false;
+        }
+        if (!ok) continue;
+        int64_t ch[3];
+        for (int a = 0; a < D; ++a) ch[a] = 2 * nb[a] + o[a];
+        uint64_t ca = box_anchor<D>(ch, lev + 1, M);
+        int32_t Y = find_leaf(L.anchor, b, e, ca);
+        if (L.level[Y] != lev + 1 || L.anchor[Y] != ca) {
+          atomicOr(status, ST_TREE_INCONSISTENT);
+          continue;
+        }
+        if (nc < 4) cand[nc++] = Y;
+      }
+    }
+    for (int m = 0; m < nc; ++m) {
+      bool dup = false;
+      for (int r = 0; r < cnt; ++r)
+        if (got_leaf[r] == cand[m] && got_q[r] == qp) dup = true;
+      if (dup) continue;
+      if (cnt >= kMaxNear) {
+        atomicOr(status, ST_NEAR_OVERFLOW);
+        continue;
+      }
+      got_leaf[cnt] = cand[m];
+      got_q[cnt] = qp;
+      emit(cnt, cand[m], qp);
+      ++cnt;
+    }
+  }
+  return cnt;
+}
+
+template <int D>
+__global__ void k_near_count(int n, LeafArrays L, const int32_t* __restrict__ begin, int M, int periodic,
+                             int32_t* __restrict__ cnt_out, int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cnt_out[i] = near_entries<D>(i, L, begin, M, periodic, status, [](int, int32_t, int32_t) {});
+}
+
+template <int D>
+__global__ void k_near_fill(int n, LeafArrays L, const int32_t* __restrict__ begin, int M, int periodic,
+                            const int32_t* __restrict__ off, int32_t* __restrict__ nl,
+                            int32_t* __restrict__ nq, int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t o = off[i];
+  near_entries<D>(i, L, begin, M, periodic, status, [&](int r, int32_t X, int32_t qp) {
+    nl[o + r] = X;
+    nq[o + r] = qp;
+  });
+}
+
+__global__ void k_tile_count(int n, const int32_t* __restrict__ count, int32_t* __restrict__ ntile) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ntile[i] = (count[i] + kTile - 1) / kTile;
+}
+
+__global__ void k_tile_fill(int n, const int32_t* __restrict__ start, const int32_t* __restrict__ count,
+                            const int32_t* __restrict__ tile0, int32_t* __restrict__ tleaf,
+                            int32_t* __restrict__ tstart, int32_t* __restrict__ tcount) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int nt = (count[i] + kTile - 1) / kTile;
+  for (int k = 0; k < nt; ++k) {
+    int t = tile0[i] + k;
+    tleaf[t] = i;
+    tstart[t] = start[i] + k * kTile;
+    tcount[t] = min(kTile, count[i] - k * kTile);
+  }
+}
+
+// one warp per tile: leaf-relative FP32 coordinates and the tile bounding box
+template <int D>
+__global__ void k_rel_bbox(int n_tile, int64_t N, const int32_t* __restrict__ tleaf,
+                           const int32_t* __restrict__ tstart, const int32_t* __restrict__ tcount,
+                           const uint64_t* __restrict__ anchor, const int32_t* __restrict__ level,
+                           const double* __restrict__ w, int M, float4* __restrict__ rel,
+                           float4* __restrict__ tlo, float4* __restrict__ thi) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (warp >= n_tile) return;
+  int leaf = tleaf[warp];
+  int lev = level[leaf];
+  int64_t c[3] = {0, 0, 0};
+  leaf_coords<D>(anchor[leaf], lev, M, c);
+  const double h = ldexp(1.0, -lev);
+  float v[3] = {0.f, 0.f, 0.f};
+  bool on = lane < tcount[warp];
+  if (on) {
+    int64_t p = tstart[warp] + lane;
+    for (int a = 0; a < D; ++a) {
+      double centre = (static_cast<double>(c[a]) + 0.5) * h;
+      v[a] = __double2float_rn(w[a * N + p] - centre);
+    }
+    rel[p] = make_float4(v[0], v[1], v[2], 0.f);
+  }
+  float lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = on ? v[a] : 3.0e38f;
+    hi[a] = on ? v[a] : -3.0e38f;
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+      hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+    }
+  }
+  if (lane == 0) {
+    tlo[warp] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    thi[warp] = make_float4(hi[0], hi[1], hi[2], 0.f);
+  }
+}
+
+__global__ void k_set_value(int32_t* dst, int32_t v) { *dst = v; }
+
+__global__ void k_point_sys(int n_sys, const int32_t* __restrict__ offs, int32_t* __restrict__ ps) {
+  int k = blockIdx.y;
+  int64_t i = offs[k] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < n_sys && i < offs[k + 1]) ps[i] = k;
+}
+
+// exclusive scan of n int32 values; returns the total (host-synchronising)
+int64_t scan_total(const int32_t* in, int32_t* out, int n, cudaStream_t s, int32_t* h_pinned) {
+  if (n == 0) return 0;
+  size_t bytes = 0;
+  DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, n, s));
+  void* tmp = dalloc<char>(bytes, s);
+  DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, bytes, in, out, n, s));
+  dfree(tmp, s);
+  DMK_CUDA_TRY(cudaMemcpyAsync(h_pinned, out + (n - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DMK_CUDA_TRY(cudaMemcpyAsync(h_pinned + 1, in + (n - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DMK_CUDA_TRY(cudaStreamSynchronize(s));
+  return static_cast<int64_t>(h_pinned[0]) + h_pinned[1];
+}
+
+template <int D>
+void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
+  DeviceTree& T = p.tree;
+  cudaStream_t s = p.stream;
+  const int M = MaxLevel<D>::value;
+  T.dim = D;
+  T.M = M;
+  T.periodic = p.opts.periodic;
+  const int64_t N = T.N;
+  const int n_sys = T.n_sys;
+  const int B = 256;
+  const double lo0 = p.opts.box_lo[0], lo1 = p.opts.box_lo[1], lo2 = D == 3 ? p.opts.box_lo[2] : 0.0;
+
+  int32_t* h_pin = nullptr;
+  DMK_CUDA_TRY(cudaMallocHost(&h_pin, 4 * sizeof(int32_t)));
+  struct PinGuard { int32_t* q; ~PinGuard() { cudaFreeHost(q); } } pin_guard{h_pin};
+
+  // system offsets on the device
+  std::vector<int32_t> offs32(n_sys + 1);
+  for (int k = 0; k <= n_sys; ++k) offs32[k] = static_cast<int32_t>(h_offsets[k]);
+  int32_t* d_offs = dalloc<int32_t>(n_sys + 1, s);
+  DMK_CUDA_TRY(cudaMemcpyAsync(d_offs, offs32.data(), (n_sys + 1) * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s));
+
+  // ---- keys and sort -------------------------------------------------------
+  uint64_t* key_in = dalloc<uint64_t>(N, s);
+  uint64_t* skeys = dalloc<uint64_t>(N, s);
+  int32_t* idx_in = dalloc<int32_t>(N, s);
+  T.perm = dalloc<int32_t>(N, s);
+  if (N > 0) {
+    k_keys<D><<<grid_for(N, B), B, 0, s>>>(N, d_src, lo0, lo1, lo2, T.periodic, M, key_in, idx_in, p.status);
+    ++p.launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+    size_t bytes = 0;
+    if (n_sys == 1) {
+      DMK_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, bytes, key_in, skeys, idx_in, T.perm,
+                                                   static_cast<int>(N), 0, D * M, s));
+      void* tmp = dalloc<char>(bytes, s);
+      DMK_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, bytes, key_in, skeys, idx_in, T.perm,
+                                                   static_cast<int>(N), 0, D * M, s));
+      dfree(tmp, s);
+    } else {
+      DMK_CUDA_TRY(cub::DeviceSegmentedRadixSort::SortPairs(
+          nullptr, bytes, key_in, skeys, idx_in, T.perm, static_cast<int>(N), n_sys, d_offs, d_offs + 1,
+          0, D * M, s));
+      void* tmp = dalloc<char>(bytes, s);
+      DMK_CUDA_TRY(cub::DeviceSegmentedRadixSort::SortPairs(
+          tmp, bytes, key_in, skeys, idx_in, T.perm, static_cast<int>(N), n_sys, d_offs, d_offs + 1,
+          0, D * M, s));
+      dfree(tmp, s);
+    }
+  }
+  dfree(key_in, s);
+  dfree(idx_in, s);
+  T.w = dalloc<double>(N * D, s);
+  if (N > 0) {
+    k_gather_w<D><<<grid_for(N, B), B, 0, s>>>(N, d_src, T.perm, lo0, lo1, lo2, T.periodic, T.w);
+    ++p.launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+  }
+  T.point_sys = dalloc<int32_t>(N, s);
+  if (N > 0) {
+    int64_t maxn = 0;
+    for (int k = 0; k < n_sys; ++k) maxn = std::max<int64_t>(maxn, h_offsets[k + 1] - h_offsets[k]);
+    dim3 g(grid_for(std::max<int64_t>(maxn, 1), B), n_sys);
+    k_point_sys<<<g, B, 0, s>>>(n_sys, d_offs, T.point_sys);
+    ++p.launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+  }
+
+  // ---- (a) adaptive refinement -------------------------------------------
+  LeafArrays cur, nxt;
+  int64_t n_leaf = n_sys;
+  alloc_leaves(cur, n_leaf, s);
+  k_init_roots<<<grid_for(n_sys, B), B, 0, s>>>(n_sys, d_offs, cur);
+  ++p.launches;
+  DMK_CUDA_TRY(cudaGetLastError());
+  int32_t* begin = dalloc<int32_t>(n_sys + 1, s);
+
+  auto refine = [&](const int32_t* flag) -> bool {
+    int32_t* nch = dalloc<int32_t>(n_leaf, s);
+    int32_t* pos = dalloc<int32_t>(n_leaf, s);
+    k_split_flags<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, p.leaf_capacity, M,
+                                                       flag, nch);
+    ++p.launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+    int64_t total = scan_total(nch, pos, static_cast<int>(n_leaf), s, h_pin);
+    bool changed = total != n_leaf;
+    if (changed) {
+      if (total >= (int64_t(1) << 31)) throw Error{DMK_ERR_NOMEM, "tree too large"};
+      alloc_leaves(nxt, total, s);
+      k_refine<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, nch, pos, nxt, skeys, M);
+      ++p.launches;
+      DMK_CUDA_TRY(cudaGetLastError());
+      free_leaves(cur, s);
+      cur = nxt;
+      nxt = LeafArrays();
+      n_leaf = total;
+    }
+    dfree(nch, s);
+    dfree(pos, s);
+    return changed;
+  };
+
+  for (int it = 0; it <= M; ++it)
+    if (!refine(nullptr)) break;
+
+  // ---- (b) level restriction --------------------------------------------
+  int* d_any = dalloc<int>(1, s);
+  for (int it = 0; it < 4 * M + 8; ++it) {
+    k_sys_begin<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), n_sys, cur.sys, begin);
+    ++p.launches;
+    int32_t* flag = dalloc<int32_t>(n_leaf, s);
+    DMK_CUDA_TRY(cudaMemsetAsync(flag, 0, n_leaf * sizeof(int32_t), s));
+    DMK_CUDA_TRY(cudaMemsetAsync(d_any, 0, sizeof(int), s));
+    k_balance<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
+                                                   flag, d_any);
+    ++p.launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+    DMK_CUDA_TRY(cudaMemcpyAsync(h_pin + 2, d_any, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DMK_CUDA_TRY(cudaStreamSynchronize(s));
+    bool any = h_pin[2] != 0;
+    if (any) refine(flag);
+    dfree(flag, s);
+    if (!any) break;
+  }
+  dfree(d_any, s);
+  k_sys_begin<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), n_sys, cur.sys, begin);
+  ++p.launches;
+  DMK_CUDA_TRY(cudaGetLastError());
+
+  T.n_leaf = static_cast<int32_t>(n_leaf);
+  T.leaf_anchor = cur.anchor;
+  T.leaf_level = cur.level;
+  T.leaf_start = cur.start;
+  T.leaf_count = cur.count;
+  T.leaf_sys = cur.sys;
+  T.sys_leaf_begin = begin;
+
+  // ---- near lists ------------------------------------------------------------
+  int32_t* ncount = dalloc<int32_t>(n_leaf, s);
+  T.near_off = dalloc<int32_t>(n_leaf + 1, s);
+  k_near_count<D><<<grid_for(n_leaf, 128), 128, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
+                                                        ncount, p.status);
+  ++p.launches;
+  DMK_CUDA_TRY(cudaGetLastError());
+  T.n_near = scan_total(ncount, T.near_off, static_cast<int>(n_leaf), s, h_pin);
+  k_set_value<<<1, 1, 0, s>>>(T.near_off + n_leaf, static_cast<int32_t>(T.n_near));
+  ++p.launches;
+  DMK_CUDA_TRY(cudaGetLastError());
+  T.near_leaf = dalloc<int32_t>(T.n_near, s);
+  T.near_q = dalloc<int32_t>(T.n_near, s);
+  k_near_fill<D><<<grid_for(n_leaf, 128), 128, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
+                                                       T.near_off, T.near_leaf, T.near_q, p.status);
+  ++p.launches;
+  DMK_CUDA_TRY(cudaGetLastError());
+  dfree(ncount, s);
+
+  // ---- tiles, leaf-relative FP32 coordinates, bounding boxes ---------------------
+  T.leaf_ntile = dalloc<int32_t>(n_leaf, s);
+  T.leaf_tile0 = dalloc<int32_t>(n_leaf, s);
+  k_tile_count<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur.count, T.leaf_ntile);
+  ++p.launches;
+  DMK_CUDA_TRY(cudaGetLastError());
+  T.n_tile = static_cast<int32_t>(scan_total(T.leaf_ntile, T.leaf_tile0, static_cast<int>(n_leaf), s, h_pin));
+  T.tile_leaf = dalloc<int32_t>(T.n_tile, s);
+  T.tile_start = dalloc<int32_t>(T.n_tile, s);
+  T.tile_count = dalloc<int32_t>(T.n_tile, s);
+  T.tile_lo = dalloc<float4>(T.n_tile, s);
+  T.tile_hi = dalloc<float4>(T.n_tile, s);
+  T.rel = dalloc<float4>(N, s);
+  k_tile_fill<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur.start, cur.count, T.leaf_tile0,
+                                                T.tile_leaf, T.tile_start, T.tile_count);
+  ++p.launches;
+  DMK_CUDA_TRY(cudaGetLastError());
+  if (T.n_tile > 0) {
+    k_rel_bbox<D><<<grid_for(int64_t(T.n_tile) * 32, 256), 256, 0, s>>>(
+        T.n_tile, N, T.tile_leaf, T.tile_start, T.tile_count, T.leaf_anchor, T.leaf_level, T.w, M, T.rel,
+        T.tile_lo, T.tile_hi);
+    ++p.launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+  }
+  dfree(skeys, s);
+  dfree(d_offs, s);
+}
+
+}  // namespace
+
+void build_tree(Plan& p, const double* d_src, const int64_t* h_offsets) {
+  if (p.opts.dim == 3) build_tree_t<3>(p, d_src, h_offsets);
+  else build_tree_t<2>(p, d_src, h_offsets);
+}
+
+void free_tree(DeviceTree& t, cudaStream_t s) {
+  dfree(t.perm, s);
+  dfree(t.w, s);
+  dfree(t.rel, s);
+  dfree(t.point_sys, s);
+  dfree(t.leaf_anchor, s);
+  dfree(t.leaf_level, s);
+  dfree(t.leaf_start, s);
+  dfree(t.leaf_count, s);
+  dfree(t.leaf_sys, s);
+  dfree(t.sys_leaf_begin, s);
+  dfree(t.near_off, s);
+  dfree(t.near_leaf, s);
+  dfree(t.near_q, s);
+  dfree(t.tile_leaf, s);
+  dfree(t.tile_start, s);
+  dfree(t.tile_count, s);
+  dfree(t.tile_lo, s);
+  dfree(t.tile_hi, s);
+  dfree(t.leaf_tile0, s);
+  dfree(t.leaf_ntile, s);
+}
+
+}  // namespace dmk

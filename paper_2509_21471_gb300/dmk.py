@@ -1,0 +1,242 @@
+"""Thin Python binding of the C ABI in include/dmk_stokes.h (ctypes).
+
+Argument marshalling only: every step of the near-field pass runs in the CUDA
+library libdmk_stokes.so.  Importing this module fails loudly if the library
+has not been built (``python -c "import __graft_entry__ as g; g.build()"``).
+Torch is used for device memory and streams only.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdmk_stokes.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (paper_2509_21471_gb300/build.py)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+DMK_OK = 0
+STATUS_NAMES = {0: "DMK_OK", 1: "DMK_ERR_INVALID_ARG", 2: "DMK_ERR_OUT_OF_RANGE", 3: "DMK_ERR_UNSUPPORTED",
+                4: "DMK_ERR_NOMEM", 5: "DMK_ERR_CUDA", 6: "DMK_ERR_TIMEOUT", 7: "DMK_ERR_BAD_PLAN"}
+STOKESLET, STRESSLET = 1, 2
+FP64, MIXED = 0, 1
+ALL, NEAR = 0, 1
+
+
+class DMKError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("periodic", ctypes.c_int32), ("kernels", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("components", ctypes.c_int32),
+                ("leaf_capacity", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("box_lo", ctypes.c_double * 3)]
+
+
+_P = ctypes.c_void_p
+_lib.dmk_stokes_plan.argtypes = [ctypes.POINTER(Opts), ctypes.c_int64, _P, ctypes.c_int64, _P, _P,
+                                 ctypes.POINTER(_P)]
+_lib.dmk_stokes_plan_batched.argtypes = [ctypes.POINTER(Opts), ctypes.c_int32, _P, _P, _P, ctypes.POINTER(_P)]
+_lib.dmk_stokes_eval.argtypes = [_P, _P, _P, _P, _P, _P]
+_lib.dmk_stokes_eval_grad.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+_lib.dmk_stokes_sync_status.argtypes = [_P]
+_lib.dmk_stokes_plan_stats.argtypes = [_P, _P]
+_lib.dmk_stokes_plan_tree.argtypes = [_P] + [_P] * 8
+_lib.dmk_stokes_kernel_table.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P]
+_lib.dmk_stokes_destroy.argtypes = [_P]
+_lib.dmk_stokes_destroy.restype = None
+_lib.dmk_stokes_last_error.argtypes = [_P]
+_lib.dmk_stokes_last_error.restype = ctypes.c_char_p
+for _name in ("dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_grad",
+              "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree",
+              "dmk_stokes_kernel_table"):
+    getattr(_lib, _name).restype = ctypes.c_int
+
+EXPORTED = ["dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_grad",
+            "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree", "dmk_stokes_kernel_table",
+            "dmk_stokes_destroy", "dmk_stokes_last_error"]
+
+
+def _check(code, handle=None):
+    if code != DMK_OK:
+        msg = _lib.dmk_stokes_last_error(handle)
+        raise DMKError(code, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _as_dev(t, dim, name, device):
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t, dtype=np.float64))
+    t = t.to(device=device, dtype=torch.float64).contiguous()
+    if t.dim() != 2 or t.shape[1] != dim:
+        raise ValueError(f"{name} must have shape [n, {dim}]")
+    return t
+
+
+def make_opts(dim=3, periodic=False, kernels=STOKESLET, precision=MIXED, components=NEAR,
+              leaf_capacity=0, n_rhs=1, eps=1e-6, box_lo=None):
+    o = Opts()
+    o.dim, o.periodic, o.kernels, o.precision = dim, int(bool(periodic)), kernels, precision
+    o.components, o.leaf_capacity, o.n_rhs, o.reserved = components, leaf_capacity, n_rhs, 0
+    o.eps = eps
+    lo = [-0.5] * 3 if box_lo is None else list(box_lo) + [-0.5] * (3 - len(box_lo))
+    for a in range(3):
+        o.box_lo[a] = lo[a]
+    return o
+
+
+class Plan:
+    """dmk_stokes_plan / dmk_stokes_plan_batched on CUDA tensors."""
+
+    def __init__(self, x, eps=1e-6, dim=None, periodic=False, kernels=STOKESLET, precision=MIXED,
+                 leaf_capacity=0, n_rhs=1, box_lo=None, offsets=None, stream=None, device=None):
+        device = device or (x.device if isinstance(x, torch.Tensor) and x.is_cuda else torch.device("cuda"))
+        dim = dim or (x.shape[1])
+        self.dim = dim
+        self.kernels = kernels
+        self.n_rhs = n_rhs
+        self.device = device
+        self._x = _as_dev(x, dim, "x", device)
+        self.n = self._x.shape[0]
+        self.opts = make_opts(dim, periodic, kernels, precision, NEAR, leaf_capacity, n_rhs, eps, box_lo)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(device):
+            sp = _stream_ptr(stream)
+            if offsets is None:
+                code = _lib.dmk_stokes_plan(ctypes.byref(self.opts), self.n, _ptr(self._x), self.n, None, sp,
+                                            ctypes.byref(self._h))
+            else:
+                offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+                self._offs = offs
+                code = _lib.dmk_stokes_plan_batched(ctypes.byref(self.opts), len(offs) - 1,
+                                                    offs.ctypes.data_as(ctypes.c_void_p), _ptr(self._x), sp,
+                                                    ctypes.byref(self._h))
+        _check(code, None)
+
+    # ------------------------------------------------------------------
+    def eval(self, f=None, g=None, n=None, out=None, stream=None):
+        """dmk_stokes_eval: near component u [n, dim] (float64, caller order)."""
+        f = None if f is None else _as_dev(f, self.dim, "f", self.device)
+        g = None if g is None else _as_dev(g, self.dim, "g", self.device)
+        n = None if n is None else _as_dev(n, self.dim, "n", self.device)
+        if out is None:
+            out = torch.empty((self.n, self.dim), dtype=torch.float64, device=self.device)
+        code = _lib.dmk_stokes_eval(self._h, _ptr(f), _ptr(g), _ptr(n), _ptr(out), _stream_ptr(stream))
+        _check(code, self._h)
+        return out
+
+    def eval_grad(self, f, want_u=False, stream=None):
+        """dmk_stokes_eval_grad: gradu [n, dim, dim] (and u if want_u)."""
+        f = _as_dev(f, self.dim, "f", self.device)
+        gu = torch.empty((self.n, self.dim, self.dim), dtype=torch.float64, device=self.device)
+        u = torch.empty((self.n, self.dim), dtype=torch.float64, device=self.device) if want_u else None
+        code = _lib.dmk_stokes_eval_grad(self._h, _ptr(f), None, None, _ptr(u), _ptr(gu), _stream_ptr(stream))
+        _check(code, self._h)
+        return (u, gu) if want_u else gu
+
+    def sync_status(self):
+        _check(_lib.dmk_stokes_sync_status(self._h), self._h)
+
+    def stats(self):
+        s = (ctypes.c_int64 * 10)()
+        _check(_lib.dmk_stokes_plan_stats(self._h, ctypes.cast(s, ctypes.c_void_p)), self._h)
+        keys = ["leaves", "max_level", "near_entries", "tiles", "issued_pairs", "three_c_over_pi",
+                "leaf_capacity", "points", "useful_pairs", "launches"]
+        return dict(zip(keys, [int(v) for v in s]))
+
+    def tree(self):
+        """Host copy of the tree: dict of numpy arrays."""
+        st = self.stats()
+        L, E, N, d = st["leaves"], st["near_entries"], st["points"], self.dim
+        arr = dict(perm=np.zeros(N, np.int32), leaf_level=np.zeros(L, np.int32), leaf_start=np.zeros(L, np.int32),
+                   leaf_count=np.zeros(L, np.int32), leaf_coords=np.zeros((L, d), np.int64),
+                   near_off=np.zeros(L + 1, np.int32), near_leaf=np.zeros(E, np.int32),
+                   near_q=np.zeros((E, d), np.int32))
+        ptrs = [arr[k].ctypes.data_as(ctypes.c_void_p) for k in
+                ("perm", "leaf_level", "leaf_start", "leaf_count", "leaf_coords", "near_off", "near_leaf", "near_q")]
+        _check(_lib.dmk_stokes_plan_tree(self._h, *ptrs), self._h)
+        return arr
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.dmk_stokes_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def kernel_table(dim, eps, which, fp32=False, kernels=STOKESLET):
+    """dmk_stokes_kernel_table (host only): (c, phi0, coefficients)."""
+    c = ctypes.c_double()
+    phi0 = ctypes.c_double()
+    buf = np.zeros(64, np.float64)
+    nt = ctypes.c_int32()
+    _check(_lib.dmk_stokes_kernel_table(dim, eps, kernels, which, int(fp32), ctypes.byref(c), ctypes.byref(phi0),
+                                        buf.ctypes.data_as(ctypes.c_void_p), 64, ctypes.byref(nt)))
+    return c.value, phi0.value, buf[: nt.value].copy()
+
+
+def eval(x, f=None, g=None, n=None, **plan_kwargs):
+    """One-shot plan + eval (allocates a plan per call)."""
+    p = Plan(x, **plan_kwargs)
+    try:
+        return p.eval(f, g, n)
+    finally:
+        p.close()
+
+
+class DMKStokesFn(torch.autograd.Function):
+    """u = near-field Stokeslet(x, f) with gradients for f and x.
+
+    Backward (the tree, hence every residual scale, is held fixed):
+      dL/df = S[w]                   (S_R is even and symmetric, so the transpose is itself)
+      dL/dx_k = (grad u_k)^T w_k + (grad v_k)^T f_k,  v = S[w]
+    computed with two eval_grad calls; no pair terms are stored.
+    """
+
+    @staticmethod
+    def forward(ctx, x, f, plan):
+        ctx.plan = plan
+        ctx.save_for_backward(x, f)
+        return plan.eval(f.detach())
+
+    @staticmethod
+    def backward(ctx, w):
+        x, f = ctx.saved_tensors
+        plan = ctx.plan
+        w = w.contiguous()
+        grad_f = grad_x = None
+        if ctx.needs_input_grad[1] or ctx.needs_input_grad[0]:
+            v, gv = plan.eval_grad(w, want_u=True)
+            grad_f = v
+        if ctx.needs_input_grad[0]:
+            gu = plan.eval_grad(f.detach())
+            grad_x = torch.einsum("tjm,tj->tm", gu, w) + torch.einsum("tjm,tj->tm", gv, f.detach())
+        return grad_x, (grad_f if ctx.needs_input_grad[1] else None), None
+
+
+def near_stokeslet(x, f, plan):
+    """Differentiable near-field Stokeslet velocity (autograd through DMKStokesFn)."""
+    return DMKStokesFn.apply(x, f, plan)
