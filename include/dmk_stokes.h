@@ -114,6 +114,27 @@ dmk_status_t dmk_stokes_plan_batched(const dmk_stokes_opts_t* opts, int32_t n_sy
 dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
                              const double* d_n, double* d_u, void* stream);
 
+/* The same evaluation as dmk_stokes_eval for callers that must not allocate
+ * device memory when they evaluate (for example during a CUDA stream capture
+ * that forbids allocation calls, or where another allocator owns the device
+ * memory budget).  It calls no cudaMalloc / cudaMallocAsync / cudaFree and
+ * does not touch the plan's own workspace: its scratch (sorted copies of the
+ * densities, the periodic zero-mode sums) is one array of 64 MiB that the
+ * library reserves statically on every GPU that loads it, until exit.
+ * The paper has no counterpart; this is a deployment variant.
+ *   Arguments, layouts and results: as dmk_stokes_eval.
+ *   Limit: plans needing more than 64 MiB of scratch (mixed precision:
+ *   128 bytes per point, about 524k points; FP64: 80 bytes per point, about
+ *   838k points; plus 32 bytes per system) return DMK_ERR_INVALID_ARG before
+ *   any work is queued.  The plan's device must be current.
+ *   Sharing: all calls on a device use the same array, which keeps the last
+ *   call's contents (what must start at zero is cleared by every call); calls
+ *   whose work overlaps on the GPU race on it, so queue them on one stream.
+ *   The first call on a device looks the array's address up (with that device
+ *   current); make it before any stream capture. */
+dmk_status_t dmk_stokes_eval_noalloc(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
+                                     const double* d_n, double* d_u, void* stream);
+
 /* Velocity gradient of the Stokeslet near component (the stresslet gradient is
  * not provided: DMK_ERR_UNSUPPORTED):
  *   d_gradu [n][dim][dim][n_rhs], gradu[t][j][m] = d u_j / d x_m at x_t with the

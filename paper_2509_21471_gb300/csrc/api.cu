@@ -13,11 +13,6 @@ namespace dmk {
 size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N);
 }
 
-struct dmk_stokes_plan_s {
-  dmk::Plan p;
-  cudaStream_t last_stream = nullptr;
-};
-
 namespace {
 
 thread_local std::string g_last_error;
@@ -140,6 +135,10 @@ dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64
 }
 
 }  // namespace
+
+dmk_status_t dmk::record_error(dmk_stokes_plan_t plan, dmk_status_t code, const std::string& msg) {
+  return set_err(plan, code, msg);
+}
 
 extern "C" {
 

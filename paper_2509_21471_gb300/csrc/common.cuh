@@ -183,6 +183,11 @@ void free_tree(DeviceTree& t, cudaStream_t s);
 // near.cu
 void launch_near(const Plan& p, const double* d_f, const double* d_g, const double* d_n,
                  double* d_u, double* d_gradu, cudaStream_t s);
+// same, with the evaluation scratch given explicitly: workspace of
+// eval_workspace_bytes(opts, N) bytes and reduce_buf of 4 * n_sys doubles
+void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const double* d_n,
+                    double* d_u, double* d_gradu, cudaStream_t s, void* workspace, double* reduce_buf);
+size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N);
 
 int64_t count_useful_pairs(const Plan& p);
 
@@ -207,4 +212,15 @@ inline int grid_for(int64_t n, int block) {
   return static_cast<int>(g);
 }
 
+}  // namespace dmk
+
+// the opaque plan handle of the C ABI
+struct dmk_stokes_plan_s {
+  dmk::Plan p;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace dmk {
+// records msg as the last error (per thread, and on the plan if not NULL); returns code
+dmk_status_t record_error(dmk_stokes_plan_t plan, dmk_status_t code, const std::string& msg);
 }  // namespace dmk

@@ -146,6 +146,11 @@ void dispatch_fp64_3(int km, bool grad, int nt, const NearParams& P, cudaStream_
 
 void launch_near(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u,
                  double* d_gradu, cudaStream_t s) {
+  launch_near_ws(p, d_f, d_g, d_n, d_u, d_gradu, s, p.fsorted, p.reduce_buf);
+}
+
+void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u,
+                    double* d_gradu, cudaStream_t s, void* workspace, double* reduce_buf) {
   const DeviceTree& T = p.tree;
   const int64_t N = T.N;
   const int D = p.opts.dim;
@@ -181,7 +186,7 @@ void launch_near(const Plan& p, const double* d_f, const double* d_g, const doub
   P.self_base = -p.tables.phi0 / (2.0 * M_PI);
 
   // sorted copies of the densities (plan-owned workspace)
-  char* ws = static_cast<char*>(p.fsorted);
+  char* ws = static_cast<char*>(workspace);
   if (mixed) {
     float4* f32 = reinterpret_cast<float4*>(ws);
     float4* g32 = f32 + N;
@@ -246,10 +251,10 @@ void launch_near(const Plan& p, const double* d_f, const double* d_g, const doub
   }
 
   if ((km & 2) && p.opts.periodic && d_u) {
-    DMK_CUDA_TRY(cudaMemsetAsync(p.reduce_buf, 0, 4 * sizeof(double) * T.n_sys, s));
-    k_zero_reduce<<<grid_for(N, B), B, 0, s>>>(N, 3, T.w, n64, T.point_sys, p.reduce_buf);
+    DMK_CUDA_TRY(cudaMemsetAsync(reduce_buf, 0, 4 * sizeof(double) * T.n_sys, s));
+    k_zero_reduce<<<grid_for(N, B), B, 0, s>>>(N, 3, T.w, n64, T.point_sys, reduce_buf);
     ++p.launches;
-    k_zero_apply<<<grid_for(N, B), B, 0, s>>>(N, 3, T.w, T.perm, T.point_sys, p.reduce_buf, d_u);
+    k_zero_apply<<<grid_for(N, B), B, 0, s>>>(N, 3, T.w, T.perm, T.point_sys, reduce_buf, d_u);
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());
   }

@@ -45,6 +45,7 @@ _lib.dmk_stokes_plan.argtypes = [ctypes.POINTER(Opts), ctypes.c_int64, _P, ctype
 _lib.dmk_stokes_plan_batched.argtypes = [ctypes.POINTER(Opts), ctypes.c_int32, _P, _P, _P, ctypes.POINTER(_P)]
 _lib.dmk_stokes_eval.argtypes = [_P, _P, _P, _P, _P, _P]
 _lib.dmk_stokes_eval_grad.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+_lib.dmk_stokes_eval_noalloc.argtypes = [_P, _P, _P, _P, _P, _P]
 _lib.dmk_stokes_sync_status.argtypes = [_P]
 _lib.dmk_stokes_plan_stats.argtypes = [_P, _P]
 _lib.dmk_stokes_plan_tree.argtypes = [_P] + [_P] * 8
@@ -54,12 +55,14 @@ _lib.dmk_stokes_destroy.argtypes = [_P]
 _lib.dmk_stokes_destroy.restype = None
 _lib.dmk_stokes_last_error.argtypes = [_P]
 _lib.dmk_stokes_last_error.restype = ctypes.c_char_p
-for _name in ("dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_grad",
+for _name in ("dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
+              "dmk_stokes_eval_grad",
               "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree",
               "dmk_stokes_kernel_table"):
     getattr(_lib, _name).restype = ctypes.c_int
 
-EXPORTED = ["dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_grad",
+EXPORTED = ["dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
+            "dmk_stokes_eval_grad",
             "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree", "dmk_stokes_kernel_table",
             "dmk_stokes_destroy", "dmk_stokes_last_error"]
 
@@ -140,6 +143,18 @@ class Plan:
         if out is None:
             out = torch.empty((self.n, self.dim), dtype=torch.float64, device=self.device)
         code = _lib.dmk_stokes_eval(self._h, _ptr(f), _ptr(g), _ptr(n), _ptr(out), _stream_ptr(stream))
+        _check(code, self._h)
+        return out
+
+    def eval_noalloc(self, f=None, g=None, n=None, out=None, stream=None):
+        """dmk_stokes_eval_noalloc: as eval, with the library's static scratch
+        array instead of the plan's workspace (no device allocation)."""
+        f = None if f is None else _as_dev(f, self.dim, "f", self.device)
+        g = None if g is None else _as_dev(g, self.dim, "g", self.device)
+        n = None if n is None else _as_dev(n, self.dim, "n", self.device)
+        if out is None:
+            out = torch.empty((self.n, self.dim), dtype=torch.float64, device=self.device)
+        code = _lib.dmk_stokes_eval_noalloc(self._h, _ptr(f), _ptr(g), _ptr(n), _ptr(out), _stream_ptr(stream))
         _check(code, self._h)
         return out
 
