@@ -74,9 +74,8 @@ __global__ void k_zero_apply(int64_t N, int D, const double* __restrict__ w, con
 }
 
 // Number of pairs (t, s) with 0 < r2 < nu_ts^2, decided in float64 exactly as
-// the FP64 kernel does (one warp per target tile; no culling, so it also checks
-// that culling never drops an included pair: compare with the kernels' sums).
-template <int D>
+// the FP64 kernel does.  Source tiles are culled by bounding box and single
+// sources by an FP32 test with the kernels' margin before the FP64 decision.
 __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned long long* out) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x * 4 + wid;
@@ -85,27 +84,30 @@ __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned lo
   const int B = P.tile_leaf[tile];
   const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
   const int LB = P.leaf_level[B];
+  int64_t cB[3];
+  leaf_coords<3>(P.leaf_anchor[B], LB, P.M, cB);
+  const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
   const bool on = lane < nt;
+  const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
   double wt[3] = {0.0, 0.0, 0.0};
   if (on)
-    for (int a = 0; a < D; ++a) wt[a] = P.w[a * N + t0 + lane];
+    for (int a = 0; a < 3; ++a) wt[a] = P.w[a * N + t0 + lane];
   unsigned long long cnt = 0;
   for (int e = P.near_off[B]; e < P.near_off[B + 1]; ++e) {
-    const int X = P.near_leaf[e];
-    const int32_t qp = P.near_q[e];
-    const int Lmin = min(LB, P.leaf_level[X]);
-    const double nu = ldexp(1.0, -(Lmin + 1));
-    const double nu2 = nu * nu;
-    double q[3] = {0.0, 0.0, 0.0};
-    for (int a = 0; a < D; ++a) q[a] = unpack_q(qp, a);
-    const int U0 = P.leaf_tile0[X], U1 = U0 + P.leaf_ntile[X];
-    if (!on) continue;
+    const Entry E = make_entry(P, e, LB, cB);
+    const float nu2m = E.nu2 * (1.f + 0x1p-12f);
+    const double nu2 = static_cast<double>(E.nu2);
+    const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
     for (int U = U0; U < U1; ++U) {
+      if (!on || !tile_near(P, U, E, tlo, thi)) continue;
       const int s0 = P.tile_start[U], ns = P.tile_count[U];
       for (int j = 0; j < ns; ++j) {
+        const float4 r = P.rel[s0 + j];
+        const float dx = xt.x - (r.x + E.off[0]), dy = xt.y - (r.y + E.off[1]), dz = xt.z - (r.z + E.off[2]);
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= nu2m) continue;
         double r2 = 0.0;
-        for (int a = 0; a < D; ++a) {
-          const double d = __dadd_rn(__dsub_rn(wt[a], P.w[a * N + s0 + j]), q[a]);
+        for (int a = 0; a < 3; ++a) {
+          const double d = __dadd_rn(__dsub_rn(wt[a], P.w[a * N + s0 + j]), E.q[a]);
           r2 = __dadd_rn(r2, __dmul_rn(d, d));
         }
         if (r2 < nu2 && r2 > 0.0) ++cnt;
@@ -276,10 +278,15 @@ int64_t count_useful_pairs(const Plan& p) {
   P.near_leaf = T.near_leaf;
   P.near_q = T.near_q;
   P.w = T.w;
+  P.rel = T.rel;
+  P.M = T.M;
+  P.tile_lo = T.tile_lo;
+  P.tile_hi = T.tile_hi;
+  P.leaf_anchor = T.leaf_anchor;
   unsigned long long* d = dalloc<unsigned long long>(1, p.stream);
   DMK_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), p.stream));
-  if (p.opts.dim == 3) k_count_useful<3><<<(T.n_tile + 3) / 4, 128, 0, p.stream>>>(P, d);
-  else k_count_useful<2><<<(T.n_tile + 3) / 4, 128, 0, p.stream>>>(P, d);
+  if (p.opts.dim != 3) throw Error{DMK_ERR_UNSUPPORTED, "pair count is provided in 3D"};
+  k_count_useful<<<(T.n_tile + 3) / 4, 128, 0, p.stream>>>(P, d);
   ++p.launches;
   DMK_CUDA_TRY(cudaGetLastError());
   unsigned long long h = 0;

@@ -16,8 +16,11 @@
 // Work decomposition: one warp per target tile (<= 32 points of one leaf, one
 // target per lane).  The warp walks its leaf's near list (leaf X, image offset
 // q, scale nu = 2^-(min(L_B, L_X)+1)), skips source tiles whose bounding box
-// is farther than nu from the target tile's box, stages the surviving source
-// tile in shared memory and sums the included pairs (0 < r^2 < nu^2).
+// is farther than nu from the target tile's box and stages the surviving
+// source tiles in shared memory.  MIXED: every lane tests its target against
+// each staged source and evaluates the pairs with 0 < r^2 < nu^2.  FP64:
+// batches of tiles are staged, each lane marks its candidate pairs with a
+// cheap FP32 test (with a margin) and then decides and evaluates only those.
 //
 // MIXED: coordinates are FP32 offsets from the leaf centre; a source is moved
 // into the target leaf's frame by the exact dyadic offset (c_X - c_B - q),
@@ -84,10 +87,93 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
 
 constexpr double kInv8Pi = 0.039788735772973836;   // 1 / (8 pi)
 
+// ------------------------------------------------------ tile traversal
+// Per near-list entry of the target leaf B: the source leaf X, its image
+// offset q, the residual scale nu = 2^-(min(L_B, L_X) + 1) and the exact dyadic
+// offset (c_X - c_B - q) that moves X's leaf-relative FP32 coordinates into B's
+// frame (computed in integers, exact in FP32 for every level <= 21).
+struct Entry {
+  int X;
+  float off[3];
+  float nuinv;   // 1/nu (power of two)
+  float nu2;
+  double q[3];
+};
+
+__device__ __forceinline__ Entry make_entry(const NearParams& P, int e, int LB, const int64_t* cB) {
+  Entry E;
+  E.X = P.near_leaf[e];
+  const int32_t qp = P.near_q[e];
+  const int LX = P.leaf_level[E.X];
+  const int Lmin = min(LB, LX), Lmax = max(LB, LX);
+  E.nuinv = ldexpf(1.f, Lmin + 1);
+  const float nu = ldexpf(1.f, -(Lmin + 1));
+  E.nu2 = nu * nu;
+  int64_t cX[3];
+  leaf_coords<3>(P.leaf_anchor[E.X], LX, P.M, cX);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int qa = unpack_q(qp, a);
+    E.q[a] = static_cast<double>(qa);
+    const int64_t v = ((2 * cX[a] + 1) << (Lmax - LX)) - ((2 * cB[a] + 1) << (Lmax - LB)) -
+                      (static_cast<int64_t>(qa) << (Lmax + 1));
+    E.off[a] = ldexpf(static_cast<float>(v), -(Lmax + 1));
+  }
+  return E;
+}
+
+// true if source tile U can hold a pair closer than nu to the target tile
+__device__ __forceinline__ bool tile_near(const NearParams& P, int U, const Entry& E, float4 tlo, float4 thi) {
+  const float4 slo = P.tile_lo[U], shi = P.tile_hi[U];
+  const float gx = fmaxf(fmaxf(slo.x + E.off[0] - thi.x, tlo.x - (shi.x + E.off[0])), 0.f);
+  const float gy = fmaxf(fmaxf(slo.y + E.off[1] - thi.y, tlo.y - (shi.y + E.off[1])), 0.f);
+  const float gz = fmaxf(fmaxf(slo.z + E.off[2] - thi.z, tlo.z - (shi.z + E.off[2])), 0.f);
+  return gx * gx + gy * gy + gz * gz < E.nu2 * 1.0001f;
+}
+
+// Candidate bits of one staged tile for this lane's target: bit j is set when
+// |x_t|^2 + (|s_j|^2 - nu'^2) - 2 x_t.s_j < 0, with the slot holding
+// (-2 s, |s|^2 - nu'^2), nu'^2 = nu^2 (1 + 2^-12).  The margin is far above
+// the rounding error of this expanded form (~2e-6 nu^2 for coordinates within
+// ~3 nu of the leaf centre), so no pair with r < nu is missed; the exact
+// r < nu decision is taken again on the candidates.
+__device__ __forceinline__ uint32_t candidate_bits(const float4* __restrict__ slots, float4 xt, float tt) {
+  uint32_t bits = 0u;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const float4 a = slots[j];
+    const float r2m = fmaf(a.x, xt.x, fmaf(a.y, xt.y, fmaf(a.z, xt.z, tt + a.w)));
+    bits |= (r2m < 0.f) ? (1u << j) : 0u;
+  }
+  return bits;
+}
+
+// Walks the set bits of up to four 32-bit words in order; slot index in idx.
+struct BitWalker {
+  uint32_t m0, m1, m2, m3;
+  int base;
+  __device__ __forceinline__ bool next(int& idx) {
+    if ((m0 | m1 | m2 | m3) == 0u) return false;
+    while (m0 == 0u) {
+      m0 = m1;
+      m1 = m2;
+      m2 = m3;
+      m3 = 0u;
+      base += 32;
+    }
+    idx = base + __ffs(m0) - 1;
+    m0 &= m0 - 1u;
+    return true;
+  }
+};
+
 // ---------------------------------------------------------------- mixed
+// Each surviving source tile is staged in shared memory (moved into the
+// target leaf's frame); the warp walks its 32 sources, every lane tests its
+// own target and the lanes with a pair inside the cutoff evaluate it.  The
+// tile's partial sums are added to a two-sum (hi, lo) accumulator.
 template <int KM, bool GRAD, int NT>
 __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ NearParams P) {
-  constexpr int D = 3;
   __shared__ float4 s_pos[4][kTile];
   __shared__ float4 s_f[(KM & 1) ? 4 : 1][kTile];
   __shared__ float4 s_g[(KM & 2) ? 4 : 1][kTile];
@@ -99,10 +185,12 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
   const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
   const int LB = P.leaf_level[B];
   int64_t cB[3];
-  leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
+  leaf_coords<3>(P.leaf_anchor[B], LB, P.M, cB);
   const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
   const bool on = lane < nt;
   const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  // |x_t|^2; +inf for an empty lane makes every candidate test fail
+  const float tt = on ? fmaf(xt.x, xt.x, fmaf(xt.y, xt.y, xt.z * xt.z)) : __int_as_float(0x7f800000);
 
   float uh[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
   float Gh[GRAD ? 9 : 1], Gl[GRAD ? 9 : 1];
@@ -111,56 +199,44 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
 
   const int e1 = P.near_off[B + 1];
   for (int e = P.near_off[B]; e < e1; ++e) {
-    const int X = P.near_leaf[e];
-    const int32_t qp = P.near_q[e];
-    const int LX = P.leaf_level[X];
-    const int Lmin = min(LB, LX), Lmax = max(LB, LX);
-    const float nuinv = ldexpf(1.f, Lmin + 1);
-    const float nu = ldexpf(1.f, -(Lmin + 1));
-    const float nu2 = nu * nu;
-    const float tscale = 2.f * nuinv * nuinv;
-    int64_t cX[3];
-    leaf_coords<D>(P.leaf_anchor[X], LX, P.M, cX);
-    float off[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      int64_t v = ((2 * cX[a] + 1) << (Lmax - LX)) - ((2 * cB[a] + 1) << (Lmax - LB)) -
-                  (static_cast<int64_t>(unpack_q(qp, a)) << (Lmax + 1));
-      off[a] = ldexpf(static_cast<float>(v), -(Lmax + 1));
-    }
-    const float cull = nu2 * 1.0001f;
-    const int U0 = P.leaf_tile0[X], U1 = U0 + P.leaf_ntile[X];
+    const Entry E = make_entry(P, e, LB, cB);
+    const float nu2 = E.nu2, nuinv = E.nuinv;
+    const float nu2m = nu2 * (1.f + 0x1p-12f);
+    const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
     for (int U = U0; U < U1; ++U) {
-      const float4 slo = P.tile_lo[U], shi = P.tile_hi[U];
-      float gx = fmaxf(fmaxf(slo.x + off[0] - thi.x, tlo.x - (shi.x + off[0])), 0.f);
-      float gy = fmaxf(fmaxf(slo.y + off[1] - thi.y, tlo.y - (shi.y + off[1])), 0.f);
-      float gz = fmaxf(fmaxf(slo.z + off[2] - thi.z, tlo.z - (shi.z + off[2])), 0.f);
-      if (gx * gx + gy * gy + gz * gz >= cull) continue;
+      if (!tile_near(P, U, E, tlo, thi)) continue;
       const int s0 = P.tile_start[U], ns = P.tile_count[U];
       __syncwarp();
       if (lane < ns) {
         const float4 r = P.rel[s0 + lane];
-        s_pos[wid][lane] = make_float4(r.x + off[0], r.y + off[1], r.z + off[2], 0.f);
+        const float sx = r.x + E.off[0], sy = r.y + E.off[1], sz = r.z + E.off[2];
+        s_pos[wid][lane] = make_float4(-2.f * sx, -2.f * sy, -2.f * sz,
+                                       fmaf(sx, sx, fmaf(sy, sy, sz * sz)) - nu2m);
         if (KM & 1) s_f[(KM & 1) ? wid : 0][lane] = P.f32[s0 + lane];
         if (KM & 2) {
           s_g[(KM & 2) ? wid : 0][lane] = P.g32[s0 + lane];
           s_n[(KM & 2) ? wid : 0][lane] = P.n32[s0 + lane];
         }
+      } else {
+        s_pos[wid][lane] = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));   // never a candidate
       }
       __syncwarp();
-      if (!on) continue;
       float p[3] = {0.f, 0.f, 0.f};
       float pg[GRAD ? 9 : 1];
 #pragma unroll
       for (int k = 0; k < (GRAD ? 9 : 1); ++k) pg[k] = 0.f;
-      for (int j = 0; j < ns; ++j) {
-        const float4 sp = s_pos[wid][j];
-        const float dx = xt.x - sp.x, dy = xt.y - sp.y, dz = xt.z - sp.z;
+#pragma unroll 4
+      for (int j = 0; j < kTile; ++j) {
+        // candidate test |x_t|^2 + |s|^2 - nu'^2 - 2 x_t.s < 0 (cheap, margin
+        // 2^-12 nu^2 >> its rounding error), then the exact test r^2 < nu^2
+        const float4 a = s_pos[wid][j];
+        if (fmaf(a.x, xt.x, fmaf(a.y, xt.y, fmaf(a.z, xt.z, tt + a.w))) >= 0.f) continue;
+        const float dx = fmaf(0.5f, a.x, xt.x), dy = fmaf(0.5f, a.y, xt.y), dz = fmaf(0.5f, a.z, xt.z);
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (r2 < nu2 && r2 > 0.f) {
           float ri = rsqrtf(r2);
           ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);      // one Newton step
-          const float t = fmaf(r2, tscale, -1.f);
+          const float t = fmaf(2.f, r2 * (nuinv * nuinv), -1.f);
           const float ri2 = ri * ri;
           if (KM & 1) {
             const float g = horner<NT>(P.c32[P_GS], t);
@@ -186,10 +262,10 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
               for (int jj = 0; jj < 3; ++jj) {
                 const float a1 = fmaf(A1, fv[jj], C1 * xv[jj] * xf);
 #pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                  float v = fmaf(a1, xv[m], C * xv[jj] * fv[m]);
-                  if (jj == m) v = fmaf(C, xf, v);
-                  pg[jj * 3 + m] += v;
+                for (int mm = 0; mm < 3; ++mm) {
+                  float v = fmaf(a1, xv[mm], C * xv[jj] * fv[mm]);
+                  if (jj == mm) v = fmaf(C, xf, v);
+                  pg[jj * 3 + mm] += v;
                 }
               }
             }
@@ -237,11 +313,16 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
 }
 
 // ----------------------------------------------------------------- FP64
+// Same traversal and FP32 candidate test; every candidate is then decided
+// exactly in FP64 with the oracle's operation order.
 template <int KM, bool GRAD, int NT>
 __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ NearParams P) {
-  constexpr int D = 3;
+  constexpr int NB = (KM == 1) ? 4 : 2;
+  constexpr int NS = NB * kTile;
   constexpr int NF = 3 + ((KM & 1) ? 3 : 0) + ((KM & 2) ? 7 : 0);
-  __shared__ double s_src[4][NF][kTile];
+  __shared__ float4 sA[4][NS];
+  __shared__ double sD[4][NF][NS];
+  __shared__ double sQ[4][NB][4];                    // per staged tile: q, 1/nu
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x * 4 + wid;
   if (tile >= P.n_tile) return;
@@ -250,9 +331,11 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
   const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
   const int LB = P.leaf_level[B];
   int64_t cB[3];
-  leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
+  leaf_coords<3>(P.leaf_anchor[B], LB, P.M, cB);
   const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
   const bool on = lane < nt;
+  const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float tt = fmaf(xt.x, xt.x, fmaf(xt.y, xt.y, xt.z * xt.z));
   double wt[3] = {0.0, 0.0, 0.0};
   if (on)
 #pragma unroll
@@ -263,116 +346,122 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
 #pragma unroll
   for (int k = 0; k < (GRAD ? 9 : 1); ++k) G[k] = 0.0;
 
-  const int e1 = P.near_off[B + 1];
-  for (int e = P.near_off[B]; e < e1; ++e) {
-    const int X = P.near_leaf[e];
-    const int32_t qp = P.near_q[e];
-    const int LX = P.leaf_level[X];
-    const int Lmin = min(LB, LX), Lmax = max(LB, LX);
-    const double nuinv = ldexp(1.0, Lmin + 1);
-    const double nu = ldexp(1.0, -(Lmin + 1));
-    const double nu2 = nu * nu;
-    const double tscale = 2.0 * nuinv * nuinv;
-    const double q[3] = {static_cast<double>(unpack_q(qp, 0)), static_cast<double>(unpack_q(qp, 1)),
-                         static_cast<double>(unpack_q(qp, 2))};
-    int64_t cX[3];
-    leaf_coords<D>(P.leaf_anchor[X], LX, P.M, cX);
-    float off[3];
+  int nb = 0;
+  auto flush = [&]() {
+    __syncwarp();
+    uint32_t m[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      int64_t v = ((2 * cX[a] + 1) << (Lmax - LX)) - ((2 * cB[a] + 1) << (Lmax - LB)) -
-                  (static_cast<int64_t>(unpack_q(qp, a)) << (Lmax + 1));
-      off[a] = ldexpf(static_cast<float>(v), -(Lmax + 1));
-    }
-    const float cull = static_cast<float>(nu2) * 1.0001f;
-    const int U0 = P.leaf_tile0[X], U1 = U0 + P.leaf_ntile[X];
-    for (int U = U0; U < U1; ++U) {
-      const float4 slo = P.tile_lo[U], shi = P.tile_hi[U];
-      float gx = fmaxf(fmaxf(slo.x + off[0] - thi.x, tlo.x - (shi.x + off[0])), 0.f);
-      float gy = fmaxf(fmaxf(slo.y + off[1] - thi.y, tlo.y - (shi.y + off[1])), 0.f);
-      float gz = fmaxf(fmaxf(slo.z + off[2] - thi.z, tlo.z - (shi.z + off[2])), 0.f);
-      if (gx * gx + gy * gy + gz * gz >= cull) continue;
-      const int s0 = P.tile_start[U], ns = P.tile_count[U];
-      __syncwarp();
-      if (lane < ns) {
-        const int64_t sidx = s0 + lane;
-        int k = 0;
+    for (int w = 0; w < NB; ++w)
+      if (w < nb) m[w] = candidate_bits(&sA[wid][w * kTile], xt, tt);
+    BitWalker bw{on ? m[0] : 0u, on ? m[1] : 0u, on ? m[2] : 0u, on ? m[3] : 0u, 0};
+    int idx;
+    while (bw.next(idx)) {
+      const double* q = sQ[wid][idx >> 5];
+      const double dx = __dadd_rn(__dsub_rn(wt[0], sD[wid][0][idx]), q[0]);
+      const double dy = __dadd_rn(__dsub_rn(wt[1], sD[wid][1][idx]), q[1]);
+      const double dz = __dadd_rn(__dsub_rn(wt[2], sD[wid][2][idx]), q[2]);
+      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      const double nuinv = q[3];
+      const double rho2 = r2 * (nuinv * nuinv);          // exact: nuinv is a power of two
+      if (!(rho2 < 1.0 && r2 > 0.0)) continue;
+      const double ri = 1.0 / sqrt(r2);
+      const double t = fma(2.0, rho2, -1.0);
+      const double ri2 = ri * ri;
+      int k = 3;
+      if (KM & 1) {
+        const double g = horner<NT>(P.c64[P_GS], t);
+        const double h = horner<NT>(P.c64[P_HS], t);
+        const double A = fma(g, nuinv, ri);
+        const double C = ri2 * fma(h, nuinv, ri);
+        const double fx = sD[wid][k][idx], fy = sD[wid][k + 1][idx], fz = sD[wid][k + 2][idx];
+        k += 3;
+        const double xf = fma(dx, fx, fma(dy, fy, dz * fz));
+        const double Cx = C * xf;
+        acc[0] = fma(A, fx, fma(Cx, dx, acc[0]));
+        acc[1] = fma(A, fy, fma(Cx, dy, acc[1]));
+        acc[2] = fma(A, fz, fma(Cx, dz, acc[2]));
+        if (GRAD) {
+          const double dg = horner<NT>(P.c64[P_DGS], t);
+          const double dh = horner<NT>(P.c64[P_DHS], t);
+          const double nu3i = nuinv * nuinv * nuinv;
+          const double ri3 = ri2 * ri;
+          const double A1 = fma(2.0 * dg, nu3i, -ri3);
+          const double C1 = fma(-3.0 * ri3, ri2, ri2 * fma(2.0 * dh, nu3i, -2.0 * h * nuinv * ri2));
+          const double xv[3] = {dx, dy, dz};
+          const double fv[3] = {fx, fy, fz};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) s_src[wid][k++][lane] = P.w[a * N + sidx];
-        if (KM & 1)
+          for (int jj = 0; jj < 3; ++jj) {
+            const double a1 = fma(A1, fv[jj], C1 * xv[jj] * xf);
 #pragma unroll
-          for (int a = 0; a < 3; ++a) s_src[wid][k++][lane] = P.f64[a * N + sidx];
-        if (KM & 2) {
-#pragma unroll
-          for (int a = 0; a < 3; ++a) s_src[wid][k++][lane] = P.g64[a * N + sidx];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) s_src[wid][k++][lane] = P.n64[a * N + sidx];
-        }
-      }
-      __syncwarp();
-      if (!on) continue;
-      for (int j = 0; j < ns; ++j) {
-        const double dx = __dadd_rn(__dsub_rn(wt[0], s_src[wid][0][j]), q[0]);
-        const double dy = __dadd_rn(__dsub_rn(wt[1], s_src[wid][1][j]), q[1]);
-        const double dz = __dadd_rn(__dsub_rn(wt[2], s_src[wid][2][j]), q[2]);
-        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        if (r2 < nu2 && r2 > 0.0) {
-          const double ri = 1.0 / sqrt(r2);
-          const double t = fma(r2, tscale, -1.0);
-          const double ri2 = ri * ri;
-          int k = 3;
-          if (KM & 1) {
-            const double g = horner<NT>(P.c64[P_GS], t);
-            const double h = horner<NT>(P.c64[P_HS], t);
-            const double A = fma(g, nuinv, ri);
-            const double C = ri2 * fma(h, nuinv, ri);
-            const double fx = s_src[wid][k][j], fy = s_src[wid][k + 1][j], fz = s_src[wid][k + 2][j];
-            k += 3;
-            const double xf = fma(dx, fx, fma(dy, fy, dz * fz));
-            const double Cx = C * xf;
-            acc[0] = fma(A, fx, fma(Cx, dx, acc[0]));
-            acc[1] = fma(A, fy, fma(Cx, dy, acc[1]));
-            acc[2] = fma(A, fz, fma(Cx, dz, acc[2]));
-            if (GRAD) {
-              const double dg = horner<NT>(P.c64[P_DGS], t);
-              const double dh = horner<NT>(P.c64[P_DHS], t);
-              const double nu3i = nuinv * nuinv * nuinv;
-              const double ri3 = ri2 * ri;
-              const double A1 = fma(2.0 * dg, nu3i, -ri3);
-              const double C1 = fma(-3.0 * ri3, ri2, ri2 * fma(2.0 * dh, nu3i, -2.0 * h * nuinv * ri2));
-              const double xv[3] = {dx, dy, dz};
-              const double fv[3] = {fx, fy, fz};
-#pragma unroll
-              for (int jj = 0; jj < 3; ++jj) {
-                const double a1 = fma(A1, fv[jj], C1 * xv[jj] * xf);
-#pragma unroll
-                for (int m = 0; m < 3; ++m) {
-                  double v = fma(a1, xv[m], C * xv[jj] * fv[m]);
-                  if (jj == m) v = fma(C, xf, v);
-                  G[jj * 3 + m] += v;
-                }
-              }
+            for (int mm = 0; mm < 3; ++mm) {
+              double v = fma(a1, xv[mm], C * xv[jj] * fv[mm]);
+              if (jj == mm) v = fma(C, xf, v);
+              G[jj * 3 + mm] += v;
             }
           }
-          if (KM & 2) {
-            const double pt = horner<NT>(P.c64[P_PT], t);
-            const double qt = horner<NT>(P.c64[P_QT], t);
-            const double gx_ = s_src[wid][k][j], gy_ = s_src[wid][k + 1][j], gz_ = s_src[wid][k + 2][j];
-            const double nx = s_src[wid][k + 3][j], ny = s_src[wid][k + 4][j], nz = s_src[wid][k + 5][j];
-            const double gn = s_src[wid][k + 6][j];
-            const double xn = fma(dx, nx, fma(dy, ny, dz * nz));
-            const double xg = fma(dx, gx_, fma(dy, gy_, dz * gz_));
-            const double Dc = pt * nuinv * ri2;
-            const double Ec = -6.0 * ri2 * ri2 * fma(qt, nuinv, ri);
-            const double Ex = Ec * xg * xn + Dc * gn;
-            acc[0] += fma(Dc, fma(gx_, xn, nx * xg), Ex * dx);
-            acc[1] += fma(Dc, fma(gy_, xn, ny * xg), Ex * dy);
-            acc[2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
-          }
         }
       }
+      if (KM & 2) {
+        const double pt = horner<NT>(P.c64[P_PT], t);
+        const double qt = horner<NT>(P.c64[P_QT], t);
+        const double gx_ = sD[wid][k][idx], gy_ = sD[wid][k + 1][idx], gz_ = sD[wid][k + 2][idx];
+        const double nx = sD[wid][k + 3][idx], ny = sD[wid][k + 4][idx], nz = sD[wid][k + 5][idx];
+        const double gn = sD[wid][k + 6][idx];
+        const double xn = fma(dx, nx, fma(dy, ny, dz * nz));
+        const double xg = fma(dx, gx_, fma(dy, gy_, dz * gz_));
+        const double Dc = pt * nuinv * ri2;
+        const double Ec = -6.0 * ri2 * ri2 * fma(qt, nuinv, ri);
+        const double Ex = Ec * xg * xn + Dc * gn;
+        acc[0] += fma(Dc, fma(gx_, xn, nx * xg), Ex * dx);
+        acc[1] += fma(Dc, fma(gy_, xn, ny * xg), Ex * dy);
+        acc[2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
+      }
+    }
+    __syncwarp();
+    nb = 0;
+  };
+
+  const int e1 = P.near_off[B + 1];
+  for (int e = P.near_off[B]; e < e1; ++e) {
+    const Entry E = make_entry(P, e, LB, cB);
+    const float nu2m = E.nu2 * (1.f + 0x1p-12f);
+    const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
+    for (int U = U0; U < U1; ++U) {
+      if (!tile_near(P, U, E, tlo, thi)) continue;
+      if (nb == NB) flush();
+      const int s0 = P.tile_start[U], ns = P.tile_count[U];
+      const int slot = nb * kTile + lane;
+      if (lane == 0) {
+        sQ[wid][nb][0] = E.q[0];
+        sQ[wid][nb][1] = E.q[1];
+        sQ[wid][nb][2] = E.q[2];
+        sQ[wid][nb][3] = static_cast<double>(E.nuinv);
+      }
+      if (lane < ns) {
+        const int64_t sidx = s0 + lane;
+        const float4 r = P.rel[sidx];
+        const float sx = r.x + E.off[0], sy = r.y + E.off[1], sz = r.z + E.off[2];
+        sA[wid][slot] = make_float4(-2.f * sx, -2.f * sy, -2.f * sz, fmaf(sx, sx, fmaf(sy, sy, sz * sz)) - nu2m);
+        int k = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sD[wid][k++][slot] = P.w[a * N + sidx];
+        if (KM & 1)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) sD[wid][k++][slot] = P.f64[a * N + sidx];
+        if (KM & 2) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) sD[wid][k++][slot] = P.g64[a * N + sidx];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) sD[wid][k++][slot] = P.n64[a * N + sidx];
+        }
+      } else {
+        sA[wid][slot] = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
+      }
+      ++nb;
     }
   }
+  if (nb > 0) flush();
+
   if (!on) return;
   const int64_t o = P.perm[t0 + lane];
   const double nutinv = ldexp(1.0, LB + 1);
