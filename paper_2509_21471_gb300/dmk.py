@@ -225,33 +225,40 @@ def eval(x, f=None, g=None, n=None, **plan_kwargs):
 class DMKStokesFn(torch.autograd.Function):
     """u = near-field Stokeslet(x, f) with gradients for f and x.
 
-    Backward (the tree, hence every residual scale, is held fixed):
-      dL/df = S[w]                   (S_R is even and symmetric, so the transpose is itself)
-      dL/dx_k = (grad u_k)^T w_k + (grad v_k)^T f_k,  v = S[w]
-    computed with two eval_grad calls; no pair terms are stored.
+    The forward pass builds a plan from x (or uses the one given).  Backward
+    holds the tree, hence every residual scale nu_ts, fixed:
+      dL/df   = S[w]                  (S_R is even and symmetric: the operator is its own transpose)
+      dL/dx_k = (grad u_k)^T w_k + (grad v_k)^T f_k,   v = S[w]
+    computed with two dmk_stokes_eval_grad calls; no pair terms are stored.
     """
 
     @staticmethod
-    def forward(ctx, x, f, plan):
+    def forward(ctx, x, f, plan, plan_kwargs):
+        if plan is None:
+            plan = Plan(x.detach(), **plan_kwargs)   # released with the autograd graph
         ctx.plan = plan
-        ctx.save_for_backward(x, f)
+        ctx.save_for_backward(f)
         return plan.eval(f.detach())
 
     @staticmethod
     def backward(ctx, w):
-        x, f = ctx.saved_tensors
+        (f,) = ctx.saved_tensors
         plan = ctx.plan
         w = w.contiguous()
-        grad_f = grad_x = None
-        if ctx.needs_input_grad[1] or ctx.needs_input_grad[0]:
-            v, gv = plan.eval_grad(w, want_u=True)
+        grad_x = grad_f = None
+        v, gv = plan.eval_grad(w, want_u=True)
+        if ctx.needs_input_grad[1]:
             grad_f = v
         if ctx.needs_input_grad[0]:
             gu = plan.eval_grad(f.detach())
             grad_x = torch.einsum("tjm,tj->tm", gu, w) + torch.einsum("tjm,tj->tm", gv, f.detach())
-        return grad_x, (grad_f if ctx.needs_input_grad[1] else None), None
+        return grad_x, grad_f, None, None
 
 
-def near_stokeslet(x, f, plan):
-    """Differentiable near-field Stokeslet velocity (autograd through DMKStokesFn)."""
-    return DMKStokesFn.apply(x, f, plan)
+def near_stokeslet(x, f, plan=None, **plan_kwargs):
+    """Differentiable near-field Stokeslet velocity u(x, f) (float64 tensors on CUDA).
+
+    Without ``plan`` a plan (FP64 unless ``precision`` is given) is built from x
+    in the forward pass; gradients hold its tree fixed."""
+    plan_kwargs.setdefault("precision", FP64)
+    return DMKStokesFn.apply(x, f, plan, plan_kwargs)
