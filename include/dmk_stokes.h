@@ -65,7 +65,8 @@ enum { DMK_COMPONENTS_ALL = 0, DMK_COMPONENTS_NEAR = 1 };
 typedef struct {
   int32_t dim;           /* 2 or 3 */
   int32_t periodic;      /* 0 free space; 1 periodic unit cell (Sec. 6.2) */
-  int32_t kernels;       /* bitmask DMK_KERNEL_*; the stresslet needs n_rhs == 1 */
+  int32_t kernels;       /* bitmask DMK_KERNEL_*; the stresslet and the gradient
+                            need n_rhs == 1 */
   int32_t precision;     /* DMK_PRECISION_FP64: all arithmetic in float64.
                             DMK_PRECISION_MIXED: pair terms in float32 with
                             leaf-relative coordinates and compensated (two-sum)
@@ -123,10 +124,10 @@ dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const do
  * library reserves statically on every GPU that loads it, until exit.
  * The paper has no counterpart; this is a deployment variant.
  *   Arguments, layouts and results: as dmk_stokes_eval.
- *   Limit: plans needing more than 64 MiB of scratch (mixed precision:
- *   128 bytes per point, about 524k points; FP64: 80 bytes per point, about
- *   838k points; plus 32 bytes per system) return DMK_ERR_INVALID_ARG before
- *   any work is queued.  The plan's device must be current.
+ *   Limit: plans needing more than 64 MiB of scratch (with n_rhs = 1: mixed
+ *   precision 128 bytes per point, about 524k points; FP64 80 bytes per
+ *   point, about 838k points; more with several force columns; plus 32
+ *   bytes per system) return DMK_ERR_INVALID_ARG before any work is queued.  The plan's device must be current.
  *   Sharing: all calls on a device use the same array, which keeps the last
  *   call's contents (what must start at zero is cleared by every call); calls
  *   whose work overlaps on the GPU race on it, so queue them on one stream.

@@ -49,7 +49,10 @@ dmk_status_t validate_opts(const dmk_stokes_opts_t* o, std::string& msg) {
     return DMK_ERR_UNSUPPORTED;
   }
   if (o->dim == 2) { msg = "2D kernels are not provided by this library version"; return DMK_ERR_UNSUPPORTED; }
-  if (o->n_rhs != 1) { msg = "n_rhs > 1 is not provided by this library version"; return DMK_ERR_UNSUPPORTED; }
+  if (o->n_rhs != 1 && (o->kernels & DMK_KERNEL_STRESSLET)) {
+    msg = "the stresslet takes one density column (n_rhs = 1)";
+    return DMK_ERR_UNSUPPORTED;
+  }
   return DMK_OK;
 }
 
@@ -193,6 +196,8 @@ dmk_status_t dmk_stokes_eval_grad(dmk_stokes_plan_t plan, const double* d_f, con
   if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
   if (plan->p.opts.kernels != DMK_KERNEL_STOKESLET)
     return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient is provided for the Stokeslet only");
+  if (plan->p.opts.n_rhs != 1)
+    return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient is provided for n_rhs = 1");
   if (plan->p.tree.N > 0 && !d_gradu) return set_err(plan, DMK_ERR_INVALID_ARG, "d_gradu is NULL");
   (void)d_g;
   (void)d_n;

@@ -205,6 +205,9 @@ void dfree(T*& ptr, cudaStream_t s) {
   ptr = nullptr;
 }
 
+// force columns the kernels are compiled for: 1, 4 or 16 (n_rhs padded up)
+inline int padded_rhs(int n_rhs) { return n_rhs <= 1 ? 1 : (n_rhs <= 4 ? 4 : 16); }
+
 inline int grid_for(int64_t n, int block) {
   int64_t g = (n + block - 1) / block;
   if (g < 1) g = 1;

@@ -3,10 +3,10 @@
 
 namespace dmk {
 
-#define DMK_EXT_M(KM, GR, NT) extern template void run_near_mixed3<KM, GR, NT>(const NearParams&, cudaStream_t);
+#define DMK_EXT_M(KM, GR, NT, NR) extern template void run_near_mixed3<KM, GR, NT, NR>(const NearParams&, cudaStream_t);
 #define DMK_EXT_M_NT(NT) DMK_FOR_EACH_VARIANT(DMK_EXT_M, NT)
 DMK_NT_MIXED(DMK_EXT_M_NT)
-#define DMK_EXT_D(KM, GR, NT) extern template void run_near_fp64_3<KM, GR, NT>(const NearParams&, cudaStream_t);
+#define DMK_EXT_D(KM, GR, NT, NR) extern template void run_near_fp64_3<KM, GR, NT, NR>(const NearParams&, cudaStream_t);
 #define DMK_EXT_D_NT(NT) DMK_FOR_EACH_VARIANT(DMK_EXT_D, NT)
 DMK_NT_FP64(DMK_EXT_D_NT)
 
@@ -31,6 +31,31 @@ __global__ void k_perm_n32(int64_t N, const int32_t* __restrict__ perm, const do
   double gn = g[o * 3] * n[o * 3] + g[o * 3 + 1] * n[o * 3 + 1] + g[o * 3 + 2] * n[o * 3 + 2];
   out[i] = make_float4(static_cast<float>(n[o * 3]), static_cast<float>(n[o * 3 + 1]),
                        static_cast<float>(n[o * 3 + 2]), static_cast<float>(gn));
+}
+
+// sorted FP32 force columns: out[k*N + i] = f[perm[i]][:][k] (k < nr; zero up to NR)
+__global__ void k_perm_f32_cols(int64_t N, int nr, int NR, const int32_t* __restrict__ perm,
+                                const double* __restrict__ f, float4* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int64_t o = perm[i];
+  for (int k = 0; k < NR; ++k) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < nr)
+      v = make_float4(static_cast<float>(f[(o * 3 + 0) * nr + k]), static_cast<float>(f[(o * 3 + 1) * nr + k]),
+                      static_cast<float>(f[(o * 3 + 2) * nr + k]), 0.f);
+    out[k * N + i] = v;
+  }
+}
+
+// sorted FP64 force columns: out[(k*3 + a)*N + i] = f[perm[i]][a][k]
+__global__ void k_perm_f64_cols(int64_t N, int nr, int NR, const int32_t* __restrict__ perm,
+                                const double* __restrict__ f, double* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int64_t o = perm[i];
+  for (int k = 0; k < NR; ++k)
+    for (int a = 0; a < 3; ++a) out[(k * 3 + a) * N + i] = k < nr ? f[(o * 3 + a) * nr + k] : 0.0;
 }
 
 // sorted SoA FP64 copy: out[a*N + i] = in[perm[i]*D + a]
@@ -124,9 +149,9 @@ int pick_nt(const int* set, int n, int need) {
   return -1;
 }
 
-void dispatch_mixed3(int km, bool grad, int nt, const NearParams& P, cudaStream_t s) {
-#define DMK_CASE(KM, GR, NT) \
-  if (km == KM && grad == GR && nt == NT) { run_near_mixed3<KM, GR, NT>(P, s); return; }
+void dispatch_mixed3(int km, bool grad, int nt, int nr, const NearParams& P, cudaStream_t s) {
+#define DMK_CASE(KM, GR, NT, NR) \
+  if (km == KM && grad == GR && nt == NT && nr == NR) { run_near_mixed3<KM, GR, NT, NR>(P, s); return; }
 #define DMK_CASE_NT(NT) DMK_FOR_EACH_VARIANT(DMK_CASE, NT)
   DMK_NT_MIXED(DMK_CASE_NT)
 #undef DMK_CASE
@@ -134,9 +159,9 @@ void dispatch_mixed3(int km, bool grad, int nt, const NearParams& P, cudaStream_
   throw Error{DMK_ERR_UNSUPPORTED, "no mixed kernel for this table size"};
 }
 
-void dispatch_fp64_3(int km, bool grad, int nt, const NearParams& P, cudaStream_t s) {
-#define DMK_CASE(KM, GR, NT) \
-  if (km == KM && grad == GR && nt == NT) { run_near_fp64_3<KM, GR, NT>(P, s); return; }
+void dispatch_fp64_3(int km, bool grad, int nt, int nr, const NearParams& P, cudaStream_t s) {
+#define DMK_CASE(KM, GR, NT, NR) \
+  if (km == KM && grad == GR && nt == NT && nr == NR) { run_near_fp64_3<KM, GR, NT, NR>(P, s); return; }
 #define DMK_CASE_NT(NT) DMK_FOR_EACH_VARIANT(DMK_CASE, NT)
   DMK_NT_FP64(DMK_CASE_NT)
 #undef DMK_CASE
@@ -162,6 +187,8 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   const bool grad = d_gradu != nullptr;
   if (N == 0) return;
   const int B = 256;
+  const int nr = p.opts.n_rhs;
+  const int NR = padded_rhs(nr);
 
   NearParams P{};
   P.N = N;
@@ -186,6 +213,7 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   P.u = d_u;
   P.gradu = d_gradu;
   P.self_base = -p.tables.phi0 / (2.0 * M_PI);
+  P.n_rhs = nr;
 
   // sorted copies of the densities (plan-owned workspace)
   char* ws = static_cast<char*>(workspace);
@@ -194,7 +222,7 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     float4* g32 = f32 + N;
     float4* n32 = g32 + N;
     if (km & 1) {
-      k_perm_f32<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_f, f32);
+      k_perm_f32_cols<<<grid_for(N, B), B, 0, s>>>(N, nr, NR, T.perm, d_f, f32);
       ++p.launches;
     }
     if (km & 2) {
@@ -207,13 +235,13 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     P.g32 = g32;
     P.n32 = n32;
   }
-  double* f64 = reinterpret_cast<double*>(ws + (mixed ? 3 * N * sizeof(float4) : 0));
+  double* f64 = reinterpret_cast<double*>(ws + (mixed ? std::max(3, NR) * N * sizeof(float4) : 0));
   double* g64 = f64 + 3 * N;
   double* n64 = g64 + 3 * N;
   const bool need64 = !mixed || ((km & 2) && p.opts.periodic);
   if (need64) {
     if (km & 1) {
-      k_perm_soa<<<grid_for(N, B), B, 0, s>>>(N, 3, T.perm, d_f, f64);
+      k_perm_f64_cols<<<grid_for(N, B), B, 0, s>>>(N, nr, NR, T.perm, d_f, f64);
       ++p.launches;
     }
     if (km & 2) {
@@ -246,8 +274,8 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
       P.c64[id][k] = k < tb.n64[id] ? tb.p64[id][k] : 0.0;
     }
   if (T.n_tile > 0) {
-    if (mixed) dispatch_mixed3(km, grad, nt, P, s);
-    else dispatch_fp64_3(km, grad, nt, P, s);
+    if (mixed) dispatch_mixed3(km, grad, nt, NR, P, s);
+    else dispatch_fp64_3(km, grad, nt, NR, P, s);
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());
   }
@@ -298,9 +326,10 @@ int64_t count_useful_pairs(const Plan& p) {
 
 size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N) {
   const bool mixed = o.precision == DMK_PRECISION_MIXED;
+  const int NR = padded_rhs(o.n_rhs);
   size_t b = 0;
-  if (mixed) b += 3 * N * sizeof(float4);
-  b += (3 + 3 + 4) * N * sizeof(double);
+  if (mixed) b += std::max(3, NR) * N * sizeof(float4);
+  b += std::max(3 + 3 + 4, 3 * NR) * N * sizeof(double);
   return b;
 }
 

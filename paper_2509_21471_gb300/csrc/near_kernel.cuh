@@ -55,16 +55,17 @@ struct NearParams {
   const int32_t* perm;
   const float4* rel;     // mixed: leaf-relative FP32 coordinates (sorted)
   const double* w;       // FP64 in-cell coordinates, SoA [3][N] (sorted)
-  const float4* f32;     // mixed, sorted Stokeslet forces
+  const float4* f32;     // mixed, sorted Stokeslet forces, [NR][N] (column k at k*N)
   const float4* g32;     // mixed, sorted stresslet strengths
   const float4* n32;     // mixed, sorted orientations, .w = g.n
-  const double* f64;     // FP64 sorted forces SoA [3][N]
+  const double* f64;     // FP64 sorted forces SoA [NR][3][N]
   const double* g64;     // FP64 sorted strengths SoA [3][N]
   const double* n64;     // FP64 sorted orientations SoA [3][N] (+ [3] g.n)
-  const double* f_orig;  // caller's forces [N][3] (self term)
-  double* u;             // [N][3] caller order (may be null for grad-only)
+  const double* f_orig;  // caller's forces [N][3][n_rhs] (self term)
+  double* u;             // [N][3][n_rhs] caller order (may be null for grad-only)
   double* gradu;         // [N][3][3] caller order
   double self_base;      // -phi(0) / (2 pi)
+  int n_rhs;             // force columns of the caller's arrays
   float c32[P_COUNT][kPolyCap];
   double c64[P_COUNT][kPolyCap];
 };
@@ -172,15 +173,18 @@ struct BitWalker {
 // target leaf's frame); the warp walks its 32 sources, every lane tests its
 // own target and the lanes with a pair inside the cutoff evaluate it.  The
 // tile's partial sums are added to a two-sum (hi, lo) accumulator.
-template <int KM, bool GRAD, int NT>
+template <int KM, bool GRAD, int NT, int NR>
 __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ NearParams P) {
+  static_assert(NR == 1 || (KM == 1 && !GRAD), "several force columns: Stokeslet velocity only");
+  constexpr bool COMP = (NR == 1);                     // two-sum accumulation
   __shared__ float4 s_pos[4][kTile];
-  __shared__ float4 s_f[(KM & 1) ? 4 : 1][kTile];
+  __shared__ float4 s_f[(KM & 1) ? 4 : 1][(KM & 1) ? NR : 1][kTile];
   __shared__ float4 s_g[(KM & 2) ? 4 : 1][kTile];
   __shared__ float4 s_n[(KM & 2) ? 4 : 1][kTile];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x * 4 + wid;
   if (tile >= P.n_tile) return;
+  const int64_t N = P.N;
   const int B = P.tile_leaf[tile];
   const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
   const int LB = P.leaf_level[B];
@@ -192,7 +196,11 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
   // |x_t|^2; +inf for an empty lane makes every candidate test fail
   const float tt = on ? fmaf(xt.x, xt.x, fmaf(xt.y, xt.y, xt.z * xt.z)) : __int_as_float(0x7f800000);
 
-  float uh[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
+  float uh[NR][3], ul[COMP ? 3 : 1];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) uh[k][0] = uh[k][1] = uh[k][2] = 0.f;
+#pragma unroll
+  for (int a = 0; a < (COMP ? 3 : 1); ++a) ul[a] = 0.f;
   float Gh[GRAD ? 9 : 1], Gl[GRAD ? 9 : 1];
 #pragma unroll
   for (int k = 0; k < (GRAD ? 9 : 1); ++k) Gh[k] = Gl[k] = 0.f;
@@ -212,7 +220,9 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
         const float sx = r.x + E.off[0], sy = r.y + E.off[1], sz = r.z + E.off[2];
         s_pos[wid][lane] = make_float4(-2.f * sx, -2.f * sy, -2.f * sz,
                                        fmaf(sx, sx, fmaf(sy, sy, sz * sz)) - nu2m);
-        if (KM & 1) s_f[(KM & 1) ? wid : 0][lane] = P.f32[s0 + lane];
+        if (KM & 1)
+#pragma unroll
+          for (int k = 0; k < NR; ++k) s_f[(KM & 1) ? wid : 0][(KM & 1) ? k : 0][lane] = P.f32[k * N + s0 + lane];
         if (KM & 2) {
           s_g[(KM & 2) ? wid : 0][lane] = P.g32[s0 + lane];
           s_n[(KM & 2) ? wid : 0][lane] = P.n32[s0 + lane];
@@ -221,7 +231,9 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
         s_pos[wid][lane] = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));   // never a candidate
       }
       __syncwarp();
-      float p[3] = {0.f, 0.f, 0.f};
+      float p[NR][3];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) p[k][0] = p[k][1] = p[k][2] = 0.f;
       float pg[GRAD ? 9 : 1];
 #pragma unroll
       for (int k = 0; k < (GRAD ? 9 : 1); ++k) pg[k] = 0.f;
@@ -243,29 +255,32 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
             const float h = horner<NT>(P.c32[P_HS], t);
             const float A = fmaf(g, nuinv, ri);
             const float C = ri2 * fmaf(h, nuinv, ri);
-            const float4 fs = s_f[(KM & 1) ? wid : 0][j];
-            const float xf = fmaf(dx, fs.x, fmaf(dy, fs.y, dz * fs.z));
-            const float Cx = C * xf;
-            p[0] = fmaf(A, fs.x, fmaf(Cx, dx, p[0]));
-            p[1] = fmaf(A, fs.y, fmaf(Cx, dy, p[1]));
-            p[2] = fmaf(A, fs.z, fmaf(Cx, dz, p[2]));
-            if (GRAD) {
-              const float dg = horner<NT>(P.c32[P_DGS], t);
-              const float dh = horner<NT>(P.c32[P_DHS], t);
-              const float nu3i = nuinv * nuinv * nuinv;
-              const float ri3 = ri2 * ri;
-              const float A1 = fmaf(2.f * dg, nu3i, -ri3);
-              const float C1 = fmaf(-3.f * ri3, ri2, ri2 * fmaf(2.f * dh, nu3i, -2.f * h * nuinv * ri2));
-              const float xv[3] = {dx, dy, dz};
-              const float fv[3] = {fs.x, fs.y, fs.z};
 #pragma unroll
-              for (int jj = 0; jj < 3; ++jj) {
-                const float a1 = fmaf(A1, fv[jj], C1 * xv[jj] * xf);
+            for (int k = 0; k < NR; ++k) {
+              const float4 fs = s_f[(KM & 1) ? wid : 0][(KM & 1) ? k : 0][j];
+              const float xf = fmaf(dx, fs.x, fmaf(dy, fs.y, dz * fs.z));
+              const float Cx = C * xf;
+              p[k][0] = fmaf(A, fs.x, fmaf(Cx, dx, p[k][0]));
+              p[k][1] = fmaf(A, fs.y, fmaf(Cx, dy, p[k][1]));
+              p[k][2] = fmaf(A, fs.z, fmaf(Cx, dz, p[k][2]));
+              if (GRAD) {
+                const float dg = horner<NT>(P.c32[P_DGS], t);
+                const float dh = horner<NT>(P.c32[P_DHS], t);
+                const float nu3i = nuinv * nuinv * nuinv;
+                const float ri3 = ri2 * ri;
+                const float A1 = fmaf(2.f * dg, nu3i, -ri3);
+                const float C1 = fmaf(-3.f * ri3, ri2, ri2 * fmaf(2.f * dh, nu3i, -2.f * h * nuinv * ri2));
+                const float xv[3] = {dx, dy, dz};
+                const float fv[3] = {fs.x, fs.y, fs.z};
 #pragma unroll
-                for (int mm = 0; mm < 3; ++mm) {
-                  float v = fmaf(a1, xv[mm], C * xv[jj] * fv[mm]);
-                  if (jj == mm) v = fmaf(C, xf, v);
-                  pg[jj * 3 + mm] += v;
+                for (int jj = 0; jj < 3; ++jj) {
+                  const float a1 = fmaf(A1, fv[jj], C1 * xv[jj] * xf);
+#pragma unroll
+                  for (int mm = 0; mm < 3; ++mm) {
+                    float v = fmaf(a1, xv[mm], C * xv[jj] * fv[mm]);
+                    if (jj == mm) v = fmaf(C, xf, v);
+                    pg[jj * 3 + mm] += v;
+                  }
                 }
               }
             }
@@ -280,14 +295,21 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
             const float Dc = pt * nuinv * ri2;
             const float Ec = -6.f * ri2 * ri2 * fmaf(qt, nuinv, ri);
             const float Ex = Ec * xg * xn + Dc * nsv.w;      // coefficient of x
-            p[0] += fmaf(Dc, fmaf(gs.x, xn, nsv.x * xg), Ex * dx);
-            p[1] += fmaf(Dc, fmaf(gs.y, xn, nsv.y * xg), Ex * dy);
-            p[2] += fmaf(Dc, fmaf(gs.z, xn, nsv.z * xg), Ex * dz);
+            p[0][0] += fmaf(Dc, fmaf(gs.x, xn, nsv.x * xg), Ex * dx);
+            p[0][1] += fmaf(Dc, fmaf(gs.y, xn, nsv.y * xg), Ex * dy);
+            p[0][2] += fmaf(Dc, fmaf(gs.z, xn, nsv.z * xg), Ex * dz);
           }
         }
       }
+      if (COMP) {
 #pragma unroll
-      for (int a = 0; a < 3; ++a) two_sum_add(uh[a], ul[a], p[a]);
+        for (int a = 0; a < 3; ++a) two_sum_add(uh[0][a], ul[a], p[0][a]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) uh[k][a] += p[k][a];
+      }
       if (GRAD) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) two_sum_add(Gh[k], Gl[k], pg[k]);
@@ -297,12 +319,20 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
   if (!on) return;
   const int64_t o = P.perm[t0 + lane];
   const double nutinv = ldexp(1.0, LB + 1);
+  const int nr = P.n_rhs;
   if (P.u) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      double v = (static_cast<double>(uh[a]) + static_cast<double>(ul[a])) * kInv8Pi;
-      if (KM & 1) v += P.self_base * nutinv * P.f_orig[o * 3 + a];
-      P.u[o * 3 + a] = v;
+    for (int k = 0; k < NR; ++k) {
+      if (k >= nr) break;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double v = static_cast<double>(uh[k][a]);
+        if (COMP) v += static_cast<double>(ul[a]);
+        v *= kInv8Pi;
+        const int64_t q = (o * 3 + a) * nr + k;
+        if (KM & 1) v += P.self_base * nutinv * P.f_orig[q];
+        P.u[q] = v;
+      }
     }
   }
   if (GRAD) {
@@ -315,16 +345,24 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
 // ----------------------------------------------------------------- FP64
 // Same traversal and FP32 candidate test; every candidate is then decided
 // exactly in FP64 with the oracle's operation order.
-template <int KM, bool GRAD, int NT>
+template <int KM, bool GRAD, int NT, int NR>
+struct Fp64Shape {
+  static constexpr int NB = (NR == 1) ? ((KM == 1) ? 4 : 2) : 1;     // staged tiles per batch
+  static constexpr int WPB = (NR > 4) ? 2 : 4;                       // warps per block
+};
+
+template <int KM, bool GRAD, int NT, int NR>
 __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ NearParams P) {
-  constexpr int NB = (KM == 1) ? 4 : 2;
+  static_assert(NR == 1 || (KM == 1 && !GRAD), "several force columns: Stokeslet velocity only");
+  constexpr int NB = Fp64Shape<KM, GRAD, NT, NR>::NB;
+  constexpr int WPB = Fp64Shape<KM, GRAD, NT, NR>::WPB;
   constexpr int NS = NB * kTile;
-  constexpr int NF = 3 + ((KM & 1) ? 3 : 0) + ((KM & 2) ? 7 : 0);
-  __shared__ float4 sA[4][NS];
-  __shared__ double sD[4][NF][NS];
-  __shared__ double sQ[4][NB][4];                    // per staged tile: q, 1/nu
+  constexpr int NF = 3 + ((KM & 1) ? 3 * NR : 0) + ((KM & 2) ? 7 : 0);
+  __shared__ float4 sA[WPB][NS];
+  __shared__ double sD[WPB][NF][NS];
+  __shared__ double sQ[WPB][NB][4];                  // per staged tile: q, 1/nu
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * 4 + wid;
+  const int tile = blockIdx.x * WPB + wid;
   if (tile >= P.n_tile) return;
   const int64_t N = P.N;
   const int B = P.tile_leaf[tile];
@@ -341,7 +379,9 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
 #pragma unroll
     for (int a = 0; a < 3; ++a) wt[a] = P.w[a * N + t0 + lane];
 
-  double acc[3] = {0.0, 0.0, 0.0};
+  double acc[NR][3];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) acc[k][0] = acc[k][1] = acc[k][2] = 0.0;
   double G[GRAD ? 9 : 1];
 #pragma unroll
   for (int k = 0; k < (GRAD ? 9 : 1); ++k) G[k] = 0.0;
@@ -373,30 +413,33 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
         const double h = horner<NT>(P.c64[P_HS], t);
         const double A = fma(g, nuinv, ri);
         const double C = ri2 * fma(h, nuinv, ri);
-        const double fx = sD[wid][k][idx], fy = sD[wid][k + 1][idx], fz = sD[wid][k + 2][idx];
-        k += 3;
-        const double xf = fma(dx, fx, fma(dy, fy, dz * fz));
-        const double Cx = C * xf;
-        acc[0] = fma(A, fx, fma(Cx, dx, acc[0]));
-        acc[1] = fma(A, fy, fma(Cx, dy, acc[1]));
-        acc[2] = fma(A, fz, fma(Cx, dz, acc[2]));
-        if (GRAD) {
-          const double dg = horner<NT>(P.c64[P_DGS], t);
-          const double dh = horner<NT>(P.c64[P_DHS], t);
-          const double nu3i = nuinv * nuinv * nuinv;
-          const double ri3 = ri2 * ri;
-          const double A1 = fma(2.0 * dg, nu3i, -ri3);
-          const double C1 = fma(-3.0 * ri3, ri2, ri2 * fma(2.0 * dh, nu3i, -2.0 * h * nuinv * ri2));
-          const double xv[3] = {dx, dy, dz};
-          const double fv[3] = {fx, fy, fz};
 #pragma unroll
-          for (int jj = 0; jj < 3; ++jj) {
-            const double a1 = fma(A1, fv[jj], C1 * xv[jj] * xf);
+        for (int c = 0; c < NR; ++c) {
+          const double fx = sD[wid][k][idx], fy = sD[wid][k + 1][idx], fz = sD[wid][k + 2][idx];
+          k += 3;
+          const double xf = fma(dx, fx, fma(dy, fy, dz * fz));
+          const double Cx = C * xf;
+          acc[c][0] = fma(A, fx, fma(Cx, dx, acc[c][0]));
+          acc[c][1] = fma(A, fy, fma(Cx, dy, acc[c][1]));
+          acc[c][2] = fma(A, fz, fma(Cx, dz, acc[c][2]));
+          if (GRAD) {
+            const double dg = horner<NT>(P.c64[P_DGS], t);
+            const double dh = horner<NT>(P.c64[P_DHS], t);
+            const double nu3i = nuinv * nuinv * nuinv;
+            const double ri3 = ri2 * ri;
+            const double A1 = fma(2.0 * dg, nu3i, -ri3);
+            const double C1 = fma(-3.0 * ri3, ri2, ri2 * fma(2.0 * dh, nu3i, -2.0 * h * nuinv * ri2));
+            const double xv[3] = {dx, dy, dz};
+            const double fv[3] = {fx, fy, fz};
 #pragma unroll
-            for (int mm = 0; mm < 3; ++mm) {
-              double v = fma(a1, xv[mm], C * xv[jj] * fv[mm]);
-              if (jj == mm) v = fma(C, xf, v);
-              G[jj * 3 + mm] += v;
+            for (int jj = 0; jj < 3; ++jj) {
+              const double a1 = fma(A1, fv[jj], C1 * xv[jj] * xf);
+#pragma unroll
+              for (int mm = 0; mm < 3; ++mm) {
+                double v = fma(a1, xv[mm], C * xv[jj] * fv[mm]);
+                if (jj == mm) v = fma(C, xf, v);
+                G[jj * 3 + mm] += v;
+              }
             }
           }
         }
@@ -412,9 +455,9 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
         const double Dc = pt * nuinv * ri2;
         const double Ec = -6.0 * ri2 * ri2 * fma(qt, nuinv, ri);
         const double Ex = Ec * xg * xn + Dc * gn;
-        acc[0] += fma(Dc, fma(gx_, xn, nx * xg), Ex * dx);
-        acc[1] += fma(Dc, fma(gy_, xn, ny * xg), Ex * dy);
-        acc[2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
+        acc[0][0] += fma(Dc, fma(gx_, xn, nx * xg), Ex * dx);
+        acc[0][1] += fma(Dc, fma(gy_, xn, ny * xg), Ex * dy);
+        acc[0][2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
       }
     }
     __syncwarp();
@@ -447,7 +490,7 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
         for (int a = 0; a < 3; ++a) sD[wid][k++][slot] = P.w[a * N + sidx];
         if (KM & 1)
 #pragma unroll
-          for (int a = 0; a < 3; ++a) sD[wid][k++][slot] = P.f64[a * N + sidx];
+          for (int a = 0; a < 3 * NR; ++a) sD[wid][k++][slot] = P.f64[a * N + sidx];
         if (KM & 2) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) sD[wid][k++][slot] = P.g64[a * N + sidx];
@@ -465,12 +508,18 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
   if (!on) return;
   const int64_t o = P.perm[t0 + lane];
   const double nutinv = ldexp(1.0, LB + 1);
+  const int nr = P.n_rhs;
   if (P.u) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      double v = acc[a] * kInv8Pi;
-      if (KM & 1) v += P.self_base * nutinv * P.f_orig[o * 3 + a];
-      P.u[o * 3 + a] = v;
+    for (int c = 0; c < NR; ++c) {
+      if (c >= nr) break;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double v = acc[c][a] * kInv8Pi;
+        const int64_t q = (o * 3 + a) * nr + c;
+        if (KM & 1) v += P.self_base * nutinv * P.f_orig[q];
+        P.u[q] = v;
+      }
     }
   }
   if (GRAD) {
@@ -479,18 +528,19 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
   }
 }
 
-template <int KM, bool GRAD, int NT>
+template <int KM, bool GRAD, int NT, int NR>
 void run_near_mixed3(const NearParams& P, cudaStream_t s) {
-  k_near_mixed3<KM, GRAD, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P);
+  k_near_mixed3<KM, GRAD, NT, NR><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P);
 }
-template <int KM, bool GRAD, int NT>
+template <int KM, bool GRAD, int NT, int NR>
 void run_near_fp64_3(const NearParams& P, cudaStream_t s) {
-  k_near_fp64_3<KM, GRAD, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P);
+  constexpr int WPB = Fp64Shape<KM, GRAD, NT, NR>::WPB;
+  k_near_fp64_3<KM, GRAD, NT, NR><<<(P.n_tile + WPB - 1) / WPB, 32 * WPB, 0, s>>>(P);
 }
 
-// instantiation lists (near_mixed.cu, near_fp64.cu)
+// instantiation lists (near_mixed.cu, near_fp64.cu): (kernels, gradient, NT, NR)
 #define DMK_FOR_EACH_VARIANT(M, NT) \
-  M(1, false, NT) M(2, false, NT) M(3, false, NT) M(1, true, NT)
+  M(1, false, NT, 1) M(2, false, NT, 1) M(3, false, NT, 1) M(1, true, NT, 1) M(1, false, NT, 4) M(1, false, NT, 16)
 
 #define DMK_NT_MIXED(X) X(8) X(12) X(16) X(20) X(24)
 #define DMK_NT_FP64(X) X(16) X(20) X(24) X(28) X(32)

@@ -85,12 +85,15 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _as_dev(t, dim, name, device):
+def _as_dev(t, dim, name, device, n_rhs=1):
     if not isinstance(t, torch.Tensor):
         t = torch.as_tensor(np.asarray(t, dtype=np.float64))
     t = t.to(device=device, dtype=torch.float64).contiguous()
-    if t.dim() != 2 or t.shape[1] != dim:
-        raise ValueError(f"{name} must have shape [n, {dim}]")
+    if n_rhs == 1 and t.dim() == 3 and t.shape[2] == 1:
+        t = t[:, :, 0].contiguous()
+    ok = (t.dim() == 2 and t.shape[1] == dim) if n_rhs == 1 else (t.dim() == 3 and t.shape[1:] == (dim, n_rhs))
+    if not ok:
+        raise ValueError(f"{name} must have shape [n, {dim}]" + ("" if n_rhs == 1 else f"[{n_rhs}]"))
     return t
 
 
@@ -135,13 +138,16 @@ class Plan:
         _check(code, None)
 
     # ------------------------------------------------------------------
+    def _out_shape(self):
+        return (self.n, self.dim) if self.n_rhs == 1 else (self.n, self.dim, self.n_rhs)
+
     def eval(self, f=None, g=None, n=None, out=None, stream=None):
-        """dmk_stokes_eval: near component u [n, dim] (float64, caller order)."""
-        f = None if f is None else _as_dev(f, self.dim, "f", self.device)
+        """dmk_stokes_eval: near component u [n, dim] or [n, dim, n_rhs] (float64, caller order)."""
+        f = None if f is None else _as_dev(f, self.dim, "f", self.device, self.n_rhs)
         g = None if g is None else _as_dev(g, self.dim, "g", self.device)
         n = None if n is None else _as_dev(n, self.dim, "n", self.device)
         if out is None:
-            out = torch.empty((self.n, self.dim), dtype=torch.float64, device=self.device)
+            out = torch.empty(self._out_shape(), dtype=torch.float64, device=self.device)
         code = _lib.dmk_stokes_eval(self._h, _ptr(f), _ptr(g), _ptr(n), _ptr(out), _stream_ptr(stream))
         _check(code, self._h)
         return out
@@ -149,11 +155,11 @@ class Plan:
     def eval_noalloc(self, f=None, g=None, n=None, out=None, stream=None):
         """dmk_stokes_eval_noalloc: as eval, with the library's static scratch
         array instead of the plan's workspace (no device allocation)."""
-        f = None if f is None else _as_dev(f, self.dim, "f", self.device)
+        f = None if f is None else _as_dev(f, self.dim, "f", self.device, self.n_rhs)
         g = None if g is None else _as_dev(g, self.dim, "g", self.device)
         n = None if n is None else _as_dev(n, self.dim, "n", self.device)
         if out is None:
-            out = torch.empty((self.n, self.dim), dtype=torch.float64, device=self.device)
+            out = torch.empty(self._out_shape(), dtype=torch.float64, device=self.device)
         code = _lib.dmk_stokes_eval_noalloc(self._h, _ptr(f), _ptr(g), _ptr(n), _ptr(out), _stream_ptr(stream))
         _check(code, self._h)
         return out
