@@ -112,3 +112,30 @@ def prolate_split_3d(win, nu, kmax):
                                 else k3.stresslet_res(win, dd, nu)),
         rcut=nu, kmax=kmax, ghat=lambda k: win.gammahat(k * nu, n=600),
         self=k3.stokeslet_self_coeff(win, nu))
+
+
+def gaussian_split_2d(sigma, tol=1e-16):
+    """2D Hasimoto split: real-space residual by the App. B route with the
+    Gaussian mollifier (no compact support, cut at erfc-level tol)."""
+    from .window import GaussianWindow
+    from . import kernels2d as k2
+    win = GaussianWindow(sigma)
+    kern = k2.Kernel2D(win)
+    rcut = sigma * np.sqrt(-np.log(tol)) + 1e-12
+    kmax = 2.0 / sigma * np.sqrt(-np.log(tol))
+    return dict(
+        real=lambda dd, which: (k2.stokeslet_res(kern, dd, 1.0, cut=False) if which == "S"
+                                else k2.stresslet_res(kern, dd, 1.0, cut=False)),
+        rcut=rcut, kmax=kmax, ghat=win.gammahat_closed,
+        self=k2.stokeslet_self_coeff(kern, 1.0))
+
+
+def prolate_split_2d(kern, nu, kmax):
+    """2D prolate split at scale nu, kern a kernels2d.Kernel2D."""
+    from . import kernels2d as k2
+    win = kern.win
+    return dict(
+        real=lambda dd, which: (k2.stokeslet_res(kern, dd, nu) if which == "S"
+                                else k2.stresslet_res(kern, dd, nu)),
+        rcut=nu, kmax=kmax, ghat=lambda k: win.gammahat(k * nu, n=600),
+        self=k2.stokeslet_self_coeff(kern, nu))
