@@ -136,8 +136,8 @@ dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const do
 dmk_status_t dmk_stokes_eval_noalloc(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
                                      const double* d_n, double* d_u, void* stream);
 
-/* Velocity gradient of the Stokeslet near component (the stresslet gradient is
- * not provided: DMK_ERR_UNSUPPORTED):
+/* Velocity gradient of the 3D Stokeslet near component (the stresslet gradient
+ * and the 2D gradient are not provided: DMK_ERR_UNSUPPORTED):
  *   d_gradu [n][dim][dim][n_rhs], gradu[t][j][m] = d u_j / d x_m at x_t with the
  *   tree (and so every nu_ts) held fixed; the self term does not depend on x.
  *   d_u may be NULL; if not NULL it receives the velocity as dmk_stokes_eval does.
@@ -174,7 +174,13 @@ dmk_status_t dmk_stokes_plan_tree(dmk_stokes_plan_t plan, int32_t* perm, int32_t
  * phi(0) and the polynomial coefficients (monomials in t = 2 rho^2 - 1) of the
  * residual functions; no GPU needed.
  *   out_c, out_phi0   scalars (may be NULL)
- *   which             0 gS, 1 hS, 2 pT, 3 qT, 4 dgS/ds, 5 dhS/ds
+ *   which             3D: 0 gS, 1 hS, 2 pT, 3 qT, 4 dgS/ds, 5 dhS/ds, with
+ *                     gS = (Sdiag-1)/rho, hS = (Soffd-1)/rho, pT = Tdiag/rho,
+ *                     qT = (Toffd-1)/rho (Sec. 5.2 functions at rho = r/nu);
+ *                     2D: 0 m_d, 1 m_o, 2 m_td, 3 m_to, the mollified App. B
+ *                     functions Mdiag/r, Moffd/r^3, MTdiag/r^3, MToffd/r^5 at
+ *                     unit scale, and 6 their limit Mdiag(r)/r at r = 0
+ *                     (one value, Eq. (msdiag0))
  *   fp32              0 the float64 table, 1 the float32 table
  *   coef, max_terms   output buffer; returns the number of terms in *n_terms. */
 dmk_status_t dmk_stokes_kernel_table(int32_t dim, double eps, int32_t kernels, int32_t which,

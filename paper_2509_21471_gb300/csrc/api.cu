@@ -48,7 +48,6 @@ dmk_status_t validate_opts(const dmk_stokes_opts_t* o, std::string& msg) {
     msg = "the far field is not provided: use components = DMK_COMPONENTS_NEAR";
     return DMK_ERR_UNSUPPORTED;
   }
-  if (o->dim == 2) { msg = "2D kernels are not provided by this library version"; return DMK_ERR_UNSUPPORTED; }
   if (o->n_rhs != 1 && (o->kernels & DMK_KERNEL_STRESSLET)) {
     msg = "the stresslet takes one density column (n_rhs = 1)";
     return DMK_ERR_UNSUPPORTED;
@@ -194,6 +193,7 @@ dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const do
 dmk_status_t dmk_stokes_eval_grad(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
                                   const double* d_n, double* d_u, double* d_gradu, void* stream) {
   if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
+  if (plan->p.opts.dim != 3) return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient is provided in 3D");
   if (plan->p.opts.kernels != DMK_KERNEL_STOKESLET)
     return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient is provided for the Stokeslet only");
   if (plan->p.opts.n_rhs != 1)
@@ -305,8 +305,9 @@ dmk_status_t dmk_stokes_plan_tree(dmk_stokes_plan_t plan, int32_t* perm, int32_t
 dmk_status_t dmk_stokes_kernel_table(int32_t dim, double eps, int32_t kernels, int32_t which, int32_t fp32,
                                      double* out_c, double* out_phi0, double* coef, int32_t max_terms,
                                      int32_t* n_terms) {
-  if (dim != 3) return set_err(nullptr, DMK_ERR_UNSUPPORTED, "2D tables are not provided by this library version");
-  if (which < 0 || which >= dmk::P_COUNT) return set_err(nullptr, DMK_ERR_INVALID_ARG, "bad table id");
+  if (dim != 2 && dim != 3) return set_err(nullptr, DMK_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (which < 0 || which > 6 || (dim == 2 && which >= 4 && which != 6) || (dim == 3 && which == 6))
+    return set_err(nullptr, DMK_ERR_INVALID_ARG, "bad table id");
   double c = dmk::bandlimit_for_eps(eps, kernels);
   if (c <= 0) return set_err(nullptr, DMK_ERR_INVALID_ARG, "eps outside Table 2 range");
   static thread_local dmk::KernelTables tb;
@@ -314,6 +315,11 @@ dmk_status_t dmk_stokes_kernel_table(int32_t dim, double eps, int32_t kernels, i
     return set_err(nullptr, DMK_ERR_UNSUPPORTED, "table build failed");
   if (out_c) *out_c = tb.c;
   if (out_phi0) *out_phi0 = tb.phi0;
+  if (which == 6) {
+    if (n_terms) *n_terms = 1;
+    if (coef && max_terms > 0) coef[0] = tb.self2d_m0;
+    return DMK_OK;
+  }
   int n = fp32 ? tb.n32[which] : tb.n64[which];
   if (n_terms) *n_terms = n;
   if (coef)

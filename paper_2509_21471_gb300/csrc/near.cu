@@ -1,61 +1,72 @@
-// Near-field dispatch, force permutation and the periodic stresslet zero mode.
+// Near-field dispatch, density permutation, the periodic stresslet zero mode
+// and the useful-pair count (2D and 3D).
 #include "near_kernel.cuh"
 
 namespace dmk {
 
-#define DMK_EXT_M(KM, GR, NT, NR) extern template void run_near_mixed3<KM, GR, NT, NR>(const NearParams&, cudaStream_t);
-#define DMK_EXT_M_NT(NT) DMK_FOR_EACH_VARIANT(DMK_EXT_M, NT)
+#define DMK_EXT_M(D, KM, GR, NT, NR) \
+  extern template void run_near_mixed<D, KM, GR, NT, NR>(const NearParams&, cudaStream_t);
+#define DMK_EXT_D(D, KM, GR, NT, NR) \
+  extern template void run_near_fp64<D, KM, GR, NT, NR>(const NearParams&, cudaStream_t);
+#define DMK_EXT_M_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_EXT_M, NT) DMK_FOR_EACH_VARIANT_2D(DMK_EXT_M, NT)
+#define DMK_EXT_D_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_EXT_D, NT) DMK_FOR_EACH_VARIANT_2D(DMK_EXT_D, NT)
 DMK_NT_MIXED(DMK_EXT_M_NT)
-#define DMK_EXT_D(KM, GR, NT, NR) extern template void run_near_fp64_3<KM, GR, NT, NR>(const NearParams&, cudaStream_t);
-#define DMK_EXT_D_NT(NT) DMK_FOR_EACH_VARIANT(DMK_EXT_D, NT)
 DMK_NT_FP64(DMK_EXT_D_NT)
 
 namespace {
 
-// sorted FP32 copy of a [N][3] FP64 array: out[i] = in[perm[i]]
+// sorted FP32 copy of a [N][D] FP64 array: out[i] = in[perm[i]] (z = 0 in 2D)
+template <int D>
 __global__ void k_perm_f32(int64_t N, const int32_t* __restrict__ perm, const double* __restrict__ in,
                            float4* __restrict__ out) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   int64_t o = perm[i];
-  out[i] = make_float4(static_cast<float>(in[o * 3]), static_cast<float>(in[o * 3 + 1]),
-                       static_cast<float>(in[o * 3 + 2]), 0.f);
+  float v[3] = {0.f, 0.f, 0.f};
+  for (int a = 0; a < D; ++a) v[a] = static_cast<float>(in[o * D + a]);
+  out[i] = make_float4(v[0], v[1], v[2], 0.f);
 }
 
 // sorted orientation vectors with .w = g.n (g.n in FP64, then rounded)
+template <int D>
 __global__ void k_perm_n32(int64_t N, const int32_t* __restrict__ perm, const double* __restrict__ g,
                            const double* __restrict__ n, float4* __restrict__ out) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   int64_t o = perm[i];
-  double gn = g[o * 3] * n[o * 3] + g[o * 3 + 1] * n[o * 3 + 1] + g[o * 3 + 2] * n[o * 3 + 2];
-  out[i] = make_float4(static_cast<float>(n[o * 3]), static_cast<float>(n[o * 3 + 1]),
-                       static_cast<float>(n[o * 3 + 2]), static_cast<float>(gn));
+  double gn = 0.0;
+  float v[3] = {0.f, 0.f, 0.f};
+  for (int a = 0; a < D; ++a) {
+    gn += g[o * D + a] * n[o * D + a];
+    v[a] = static_cast<float>(n[o * D + a]);
+  }
+  out[i] = make_float4(v[0], v[1], v[2], static_cast<float>(gn));
 }
 
 // sorted FP32 force columns: out[k*N + i] = f[perm[i]][:][k] (k < nr; zero up to NR)
+template <int D>
 __global__ void k_perm_f32_cols(int64_t N, int nr, int NR, const int32_t* __restrict__ perm,
                                 const double* __restrict__ f, float4* __restrict__ out) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   int64_t o = perm[i];
   for (int k = 0; k < NR; ++k) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    float v[3] = {0.f, 0.f, 0.f};
     if (k < nr)
-      v = make_float4(static_cast<float>(f[(o * 3 + 0) * nr + k]), static_cast<float>(f[(o * 3 + 1) * nr + k]),
-                      static_cast<float>(f[(o * 3 + 2) * nr + k]), 0.f);
-    out[k * N + i] = v;
+      for (int a = 0; a < D; ++a) v[a] = static_cast<float>(f[(o * D + a) * nr + k]);
+    out[k * N + i] = make_float4(v[0], v[1], v[2], 0.f);
   }
 }
 
-// sorted FP64 force columns: out[(k*3 + a)*N + i] = f[perm[i]][a][k]
+// sorted FP64 force columns: out[(k*D + a)*N + i] = f[perm[i]][a][k]
+template <int D>
 __global__ void k_perm_f64_cols(int64_t N, int nr, int NR, const int32_t* __restrict__ perm,
                                 const double* __restrict__ f, double* __restrict__ out) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   int64_t o = perm[i];
   for (int k = 0; k < NR; ++k)
-    for (int a = 0; a < 3; ++a) out[(k * 3 + a) * N + i] = k < nr ? f[(o * 3 + a) * nr + k] : 0.0;
+    for (int a = 0; a < D; ++a) out[(k * D + a) * N + i] = k < nr ? f[(o * D + a) * nr + k] : 0.0;
 }
 
 // sorted SoA FP64 copy: out[a*N + i] = in[perm[i]*D + a]
@@ -101,6 +112,7 @@ __global__ void k_zero_apply(int64_t N, int D, const double* __restrict__ w, con
 // Number of pairs (t, s) with 0 < r2 < nu_ts^2, decided in float64 exactly as
 // the FP64 kernel does.  Source tiles are culled by bounding box and single
 // sources by an FP32 test with the kernels' margin before the FP64 decision.
+template <int D>
 __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned long long* out) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x * 4 + wid;
@@ -109,17 +121,17 @@ __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned lo
   const int B = P.tile_leaf[tile];
   const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
   const int LB = P.leaf_level[B];
-  int64_t cB[3];
-  leaf_coords<3>(P.leaf_anchor[B], LB, P.M, cB);
+  int64_t cB[3] = {0, 0, 0};
+  leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
   const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
   const bool on = lane < nt;
   const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
   double wt[3] = {0.0, 0.0, 0.0};
   if (on)
-    for (int a = 0; a < 3; ++a) wt[a] = P.w[a * N + t0 + lane];
+    for (int a = 0; a < D; ++a) wt[a] = P.w[a * N + t0 + lane];
   unsigned long long cnt = 0;
   for (int e = P.near_off[B]; e < P.near_off[B + 1]; ++e) {
-    const Entry E = make_entry(P, e, LB, cB);
+    const Entry E = make_entry<D>(P, e, LB, cB);
     const float nu2m = E.nu2 * (1.f + 0x1p-12f);
     const double nu2 = static_cast<double>(E.nu2);
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
@@ -130,8 +142,9 @@ __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned lo
         const float4 r = P.rel[s0 + j];
         const float dx = xt.x - (r.x + E.off[0]), dy = xt.y - (r.y + E.off[1]), dz = xt.z - (r.z + E.off[2]);
         if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= nu2m) continue;
+        // (dx*dx + dy*dy) [+ dz*dz], unfused, as in the FP64 kernel
         double r2 = 0.0;
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < D; ++a) {
           const double d = __dadd_rn(__dsub_rn(wt[a], P.w[a * N + s0 + j]), E.q[a]);
           r2 = __dadd_rn(r2, __dmul_rn(d, d));
         }
@@ -149,49 +162,28 @@ int pick_nt(const int* set, int n, int need) {
   return -1;
 }
 
-void dispatch_mixed3(int km, bool grad, int nt, int nr, const NearParams& P, cudaStream_t s) {
-#define DMK_CASE(KM, GR, NT, NR) \
-  if (km == KM && grad == GR && nt == NT && nr == NR) { run_near_mixed3<KM, GR, NT, NR>(P, s); return; }
-#define DMK_CASE_NT(NT) DMK_FOR_EACH_VARIANT(DMK_CASE, NT)
-  DMK_NT_MIXED(DMK_CASE_NT)
-#undef DMK_CASE
-#undef DMK_CASE_NT
-  throw Error{DMK_ERR_UNSUPPORTED, "no mixed kernel for this table size"};
+void dispatch(bool mixed, int dim, int km, bool grad, int nt, int nr, const NearParams& P, cudaStream_t s) {
+#define DMK_CASE_M(D, KM, GR, NT, NR)                                                  \
+  if (mixed && dim == D && km == KM && grad == GR && nt == NT && nr == NR) {           \
+    run_near_mixed<D, KM, GR, NT, NR>(P, s);                                           \
+    return;                                                                            \
+  }
+#define DMK_CASE_D(D, KM, GR, NT, NR)                                                  \
+  if (!mixed && dim == D && km == KM && grad == GR && nt == NT && nr == NR) {          \
+    run_near_fp64<D, KM, GR, NT, NR>(P, s);                                            \
+    return;                                                                            \
+  }
+#define DMK_CASE_M_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_CASE_M, NT) DMK_FOR_EACH_VARIANT_2D(DMK_CASE_M, NT)
+#define DMK_CASE_D_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_CASE_D, NT) DMK_FOR_EACH_VARIANT_2D(DMK_CASE_D, NT)
+  DMK_NT_MIXED(DMK_CASE_M_NT)
+  DMK_NT_FP64(DMK_CASE_D_NT)
+  throw Error{DMK_ERR_UNSUPPORTED, "no compiled near-field kernel for this configuration"};
 }
 
-void dispatch_fp64_3(int km, bool grad, int nt, int nr, const NearParams& P, cudaStream_t s) {
-#define DMK_CASE(KM, GR, NT, NR) \
-  if (km == KM && grad == GR && nt == NT && nr == NR) { run_near_fp64_3<KM, GR, NT, NR>(P, s); return; }
-#define DMK_CASE_NT(NT) DMK_FOR_EACH_VARIANT(DMK_CASE, NT)
-  DMK_NT_FP64(DMK_CASE_NT)
-#undef DMK_CASE
-#undef DMK_CASE_NT
-  throw Error{DMK_ERR_UNSUPPORTED, "no FP64 kernel for this table size"};
-}
-
-}  // namespace
-
-void launch_near(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u,
-                 double* d_gradu, cudaStream_t s) {
-  launch_near_ws(p, d_f, d_g, d_n, d_u, d_gradu, s, p.fsorted, p.reduce_buf);
-}
-
-void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u,
-                    double* d_gradu, cudaStream_t s, void* workspace, double* reduce_buf) {
+NearParams tree_params(const Plan& p) {
   const DeviceTree& T = p.tree;
-  const int64_t N = T.N;
-  const int D = p.opts.dim;
-  if (D != 3) throw Error{DMK_ERR_UNSUPPORTED, "2D near field is not built in this library version"};
-  const bool mixed = p.opts.precision == DMK_PRECISION_MIXED;
-  const int km = (d_f ? 1 : 0) | (d_g ? 2 : 0);
-  const bool grad = d_gradu != nullptr;
-  if (N == 0) return;
-  const int B = 256;
-  const int nr = p.opts.n_rhs;
-  const int NR = padded_rhs(nr);
-
   NearParams P{};
-  P.N = N;
+  P.N = T.N;
   P.n_tile = T.n_tile;
   P.M = T.M;
   P.tile_leaf = T.tile_leaf;
@@ -209,26 +201,28 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   P.perm = T.perm;
   P.rel = T.rel;
   P.w = T.w;
-  P.f_orig = d_f;
-  P.u = d_u;
-  P.gradu = d_gradu;
-  P.self_base = -p.tables.phi0 / (2.0 * M_PI);
-  P.n_rhs = nr;
+  return P;
+}
 
-  // sorted copies of the densities (plan-owned workspace)
-  char* ws = static_cast<char*>(workspace);
+// sorted copies of the densities in the workspace
+template <int D>
+void perm_densities(const Plan& p, bool mixed, int km, int nr, int NR, const double* d_f, const double* d_g,
+                    const double* d_n, char* ws, NearParams& P, cudaStream_t s) {
+  const DeviceTree& T = p.tree;
+  const int64_t N = T.N;
+  const int B = 256;
   if (mixed) {
     float4* f32 = reinterpret_cast<float4*>(ws);
     float4* g32 = f32 + N;
     float4* n32 = g32 + N;
     if (km & 1) {
-      k_perm_f32_cols<<<grid_for(N, B), B, 0, s>>>(N, nr, NR, T.perm, d_f, f32);
+      k_perm_f32_cols<D><<<grid_for(N, B), B, 0, s>>>(N, nr, NR, T.perm, d_f, f32);
       ++p.launches;
     }
     if (km & 2) {
-      k_perm_f32<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_g, g32);
+      k_perm_f32<D><<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_g, g32);
       ++p.launches;
-      k_perm_n32<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_g, d_n, n32);
+      k_perm_n32<D><<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_g, d_n, n32);
       ++p.launches;
     }
     P.f32 = f32;
@@ -240,22 +234,56 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   double* n64 = g64 + 3 * N;
   const bool need64 = !mixed || ((km & 2) && p.opts.periodic);
   if (need64) {
-    if (km & 1) {
-      k_perm_f64_cols<<<grid_for(N, B), B, 0, s>>>(N, nr, NR, T.perm, d_f, f64);
+    if ((km & 1) && !mixed) {
+      k_perm_f64_cols<D><<<grid_for(N, B), B, 0, s>>>(N, nr, NR, T.perm, d_f, f64);
       ++p.launches;
     }
     if (km & 2) {
-      k_perm_soa<<<grid_for(N, B), B, 0, s>>>(N, 3, T.perm, d_g, g64);
+      k_perm_soa<<<grid_for(N, B), B, 0, s>>>(N, D, T.perm, d_g, g64);
       ++p.launches;
-      k_perm_soa<<<grid_for(N, B), B, 0, s>>>(N, 3, T.perm, d_n, n64);
+      k_perm_soa<<<grid_for(N, B), B, 0, s>>>(N, D, T.perm, d_n, n64);
       ++p.launches;
-      k_gn64<<<grid_for(N, B), B, 0, s>>>(N, 3, g64, n64);
+      k_gn64<<<grid_for(N, B), B, 0, s>>>(N, D, g64, n64);
       ++p.launches;
     }
   }
   P.f64 = f64;
   P.g64 = g64;
   P.n64 = n64;
+}
+
+}  // namespace
+
+void launch_near(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u,
+                 double* d_gradu, cudaStream_t s) {
+  launch_near_ws(p, d_f, d_g, d_n, d_u, d_gradu, s, p.fsorted, p.reduce_buf);
+}
+
+void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u,
+                    double* d_gradu, cudaStream_t s, void* workspace, double* reduce_buf) {
+  const DeviceTree& T = p.tree;
+  const int64_t N = T.N;
+  const int D = p.opts.dim;
+  const bool mixed = p.opts.precision == DMK_PRECISION_MIXED;
+  const int km = (d_f ? 1 : 0) | (d_g ? 2 : 0);
+  const bool grad = d_gradu != nullptr;
+  if (grad && D != 3) throw Error{DMK_ERR_UNSUPPORTED, "the gradient is provided in 3D"};
+  if (N == 0) return;
+  const int B = 256;
+  const int nr = p.opts.n_rhs;
+  const int NR = padded_rhs(nr);
+
+  NearParams P = tree_params(p);
+  P.f_orig = d_f;
+  P.u = d_u;
+  P.gradu = d_gradu;
+  // 3D: -phi(0)/(2 pi) (times 1/nu_t in the kernel); 2D: -m_d(0)/(8 pi) (plus 2 log(nu_t)/(8 pi))
+  P.self_base = (D == 3) ? -p.tables.phi0 / (2.0 * M_PI) : -p.tables.self2d_m0 / (8.0 * M_PI);
+  P.n_rhs = nr;
+
+  char* ws = static_cast<char*>(workspace);
+  if (D == 3) perm_densities<3>(p, mixed, km, nr, NR, d_f, d_g, d_n, ws, P, s);
+  else perm_densities<2>(p, mixed, km, nr, NR, d_f, d_g, d_n, ws, P, s);
   DMK_CUDA_TRY(cudaGetLastError());
 
   const KernelTables& tb = p.tables;
@@ -274,17 +302,16 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
       P.c64[id][k] = k < tb.n64[id] ? tb.p64[id][k] : 0.0;
     }
   if (T.n_tile > 0) {
-    if (mixed) dispatch_mixed3(km, grad, nt, NR, P, s);
-    else dispatch_fp64_3(km, grad, nt, NR, P, s);
+    dispatch(mixed, D, km, grad, nt, NR, P, s);
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());
   }
 
   if ((km & 2) && p.opts.periodic && d_u) {
     DMK_CUDA_TRY(cudaMemsetAsync(reduce_buf, 0, 4 * sizeof(double) * T.n_sys, s));
-    k_zero_reduce<<<grid_for(N, B), B, 0, s>>>(N, 3, T.w, n64, T.point_sys, reduce_buf);
+    k_zero_reduce<<<grid_for(N, B), B, 0, s>>>(N, D, T.w, P.n64, T.point_sys, reduce_buf);
     ++p.launches;
-    k_zero_apply<<<grid_for(N, B), B, 0, s>>>(N, 3, T.w, T.perm, T.point_sys, reduce_buf, d_u);
+    k_zero_apply<<<grid_for(N, B), B, 0, s>>>(N, D, T.w, T.perm, T.point_sys, reduce_buf, d_u);
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());
   }
@@ -293,28 +320,11 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
 int64_t count_useful_pairs(const Plan& p) {
   const DeviceTree& T = p.tree;
   if (T.N == 0 || T.n_tile == 0) return 0;
-  NearParams P{};
-  P.N = T.N;
-  P.n_tile = T.n_tile;
-  P.tile_leaf = T.tile_leaf;
-  P.tile_start = T.tile_start;
-  P.tile_count = T.tile_count;
-  P.leaf_level = T.leaf_level;
-  P.leaf_tile0 = T.leaf_tile0;
-  P.leaf_ntile = T.leaf_ntile;
-  P.near_off = T.near_off;
-  P.near_leaf = T.near_leaf;
-  P.near_q = T.near_q;
-  P.w = T.w;
-  P.rel = T.rel;
-  P.M = T.M;
-  P.tile_lo = T.tile_lo;
-  P.tile_hi = T.tile_hi;
-  P.leaf_anchor = T.leaf_anchor;
+  const NearParams P = tree_params(p);
   unsigned long long* d = dalloc<unsigned long long>(1, p.stream);
   DMK_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), p.stream));
-  if (p.opts.dim != 3) throw Error{DMK_ERR_UNSUPPORTED, "pair count is provided in 3D"};
-  k_count_useful<<<(T.n_tile + 3) / 4, 128, 0, p.stream>>>(P, d);
+  if (p.opts.dim == 3) k_count_useful<3><<<(T.n_tile + 3) / 4, 128, 0, p.stream>>>(P, d);
+  else k_count_useful<2><<<(T.n_tile + 3) / 4, 128, 0, p.stream>>>(P, d);
   ++p.launches;
   DMK_CUDA_TRY(cudaGetLastError());
   unsigned long long h = 0;

@@ -1,14 +1,20 @@
-// Near-field (residual + self) kernels, 3D.
+// Near-field (residual + self) kernels, 2D and 3D.
 //
 // Sec. 5.2, Eqs. (res_stokeslet), (Soffdiag), (res_stresslet), (T-offd), with
 // the length-scale remark closing Sec. 5.2 (real-space functions at rho = r/nu).
-// With the even polynomials gS, hS, pT, qT of s = rho^2 (tables.h) and r < nu:
+// Every pair term has the form
+//   S_R f     = [A f + C (x.f) x] / (8 pi)
+//   T_R:(g n) = [D (g (x.n) + x (g.n) + n (x.g)) + E x (x.g)(x.n)] / (8 pi)
+// 3D, with the even polynomials gS, hS, pT, qT of s = rho^2 (tables.h):
+//   A = 1/r + gS/nu,  C = 1/r^3 + hS/(nu r^2),
+//   D = pT/(nu r^2),  E = -6 (1/r^5 + qT/(nu r^4)).
+// 2D (App. B functions m_d, m_o, m_td, m_to at unit scale, scaled by nu):
+//   A = -log rho^2 - m_d,  C = 2/r^2 - m_o/nu^2,
+//   D = -m_td/nu^2,        E = -8/r^4 + 6 m_to/nu^4.
+// Self terms (Eq. (S_self); App. B.1 in 2D): 3D -phi(0)/(2 pi nu_t) f_t,
+// 2D (-m_d(0) + 2 log nu_t) f_t / (8 pi).
 //
-//   S_R f  = [ (1/r + gS/nu) f + (1/r^3 + hS/(nu r^2)) (x.f) x ] / (8 pi)
-//   T_R:(g n) = [ pT/(nu r^2) (g (x.n) + x (g.n) + n (x.g))
-//                 - 6 (1/r^5 + qT/(nu r^4)) x (x.g)(x.n) ] / (8 pi)
-//
-// Gradient (Stokeslet; derivative of Eq. (res_stokeslet), tree held fixed):
+// Gradient (3D Stokeslet; derivative of Eq. (res_stokeslet), tree held fixed):
 //   d_m (S_R f)_j = A1 x_m f_j + C1 x_m x_j (x.f) + C (delta_jm (x.f) + x_j f_m)
 //   A1 = (-1/r^3 + 2 gS'/nu^3) / 8pi,
 //   C1 = (-3/r^5 + 2 hS'/(nu^3 r^2) - 2 hS/(nu r^4)) / 8pi,   ' = d/ds.
@@ -24,11 +30,11 @@
 //
 // MIXED: coordinates are FP32 offsets from the leaf centre; a source is moved
 // into the target leaf's frame by the exact dyadic offset (c_X - c_B - q),
-// computed in integers.  Pair terms are FP32 (rsqrt + one Newton step), each
-// source tile's partial sum is added to a two-sum (hi, lo) accumulator.
+// computed in integers.  Pair terms are FP32 (3D: rsqrt + one Newton step),
+// each source tile's partial sum is added to a two-sum (hi, lo) accumulator.
 // FP64: coordinates are the in-cell FP64 values; the pair displacement is
-// (w_t - w_s) + q and r^2 = (dx*dx + dy*dy) + dz*dz without fused operations,
-// so the r < nu decision is the same as in a plain FP64 evaluation.
+// (w_t - w_s) + q and r^2 = (dx*dx + dy*dy) [+ dz*dz] without fused
+// operations, so the r < nu decision is the same as in a plain FP64 evaluation.
 #pragma once
 #include "common.cuh"
 
@@ -53,18 +59,18 @@ struct NearParams {
   const int32_t* near_leaf;
   const int32_t* near_q;
   const int32_t* perm;
-  const float4* rel;     // mixed: leaf-relative FP32 coordinates (sorted)
-  const double* w;       // FP64 in-cell coordinates, SoA [3][N] (sorted)
+  const float4* rel;     // leaf-relative FP32 coordinates (sorted; z = 0 in 2D)
+  const double* w;       // FP64 in-cell coordinates, SoA [D][N] (sorted)
   const float4* f32;     // mixed, sorted Stokeslet forces, [NR][N] (column k at k*N)
   const float4* g32;     // mixed, sorted stresslet strengths
   const float4* n32;     // mixed, sorted orientations, .w = g.n
-  const double* f64;     // FP64 sorted forces SoA [NR][3][N]
-  const double* g64;     // FP64 sorted strengths SoA [3][N]
-  const double* n64;     // FP64 sorted orientations SoA [3][N] (+ [3] g.n)
-  const double* f_orig;  // caller's forces [N][3][n_rhs] (self term)
-  double* u;             // [N][3][n_rhs] caller order (may be null for grad-only)
+  const double* f64;     // FP64 sorted forces SoA [NR][D][N]
+  const double* g64;     // FP64 sorted strengths SoA [D][N]
+  const double* n64;     // FP64 sorted orientations SoA [D][N] (+ [D] g.n)
+  const double* f_orig;  // caller's forces [N][D][n_rhs] (self term)
+  double* u;             // [N][D][n_rhs] caller order (may be null for grad-only)
   double* gradu;         // [N][3][3] caller order
-  double self_base;      // -phi(0) / (2 pi)
+  double self_base;      // 3D: -phi(0)/(2 pi); 2D: -m_d(0)/(8 pi)
   int n_rhs;             // force columns of the caller's arrays
   float c32[P_COUNT][kPolyCap];
   double c64[P_COUNT][kPolyCap];
@@ -87,12 +93,20 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
 }
 
 constexpr double kInv8Pi = 0.039788735772973836;   // 1 / (8 pi)
+constexpr double kLn2 = 0.6931471805599453;
+
+// self-term coefficient of a target in a leaf at level LB (nu_t = 2^-(LB+1))
+template <int D>
+__device__ __forceinline__ double self_coeff(const NearParams& P, int LB) {
+  if (D == 3) return P.self_base * ldexp(1.0, LB + 1);
+  return P.self_base - 2.0 * (LB + 1) * kLn2 * kInv8Pi;        // + 2 log(nu_t) / (8 pi)
+}
 
 // ------------------------------------------------------ tile traversal
 // Per near-list entry of the target leaf B: the source leaf X, its image
 // offset q, the residual scale nu = 2^-(min(L_B, L_X) + 1) and the exact dyadic
 // offset (c_X - c_B - q) that moves X's leaf-relative FP32 coordinates into B's
-// frame (computed in integers, exact in FP32 for every level <= 21).
+// frame (computed in integers; exact in FP32 for neighbouring leaves).
 struct Entry {
   int X;
   float off[3];
@@ -101,6 +115,7 @@ struct Entry {
   double q[3];
 };
 
+template <int D>
 __device__ __forceinline__ Entry make_entry(const NearParams& P, int e, int LB, const int64_t* cB) {
   Entry E;
   E.X = P.near_leaf[e];
@@ -110,15 +125,19 @@ __device__ __forceinline__ Entry make_entry(const NearParams& P, int e, int LB, 
   E.nuinv = ldexpf(1.f, Lmin + 1);
   const float nu = ldexpf(1.f, -(Lmin + 1));
   E.nu2 = nu * nu;
-  int64_t cX[3];
-  leaf_coords<3>(P.leaf_anchor[E.X], LX, P.M, cX);
+  int64_t cX[3] = {0, 0, 0};
+  leaf_coords<D>(P.leaf_anchor[E.X], LX, P.M, cX);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    const int qa = unpack_q(qp, a);
-    E.q[a] = static_cast<double>(qa);
-    const int64_t v = ((2 * cX[a] + 1) << (Lmax - LX)) - ((2 * cB[a] + 1) << (Lmax - LB)) -
-                      (static_cast<int64_t>(qa) << (Lmax + 1));
-    E.off[a] = ldexpf(static_cast<float>(v), -(Lmax + 1));
+    E.q[a] = 0.0;
+    E.off[a] = 0.f;
+    if (a < D) {
+      const int qa = unpack_q(qp, a);
+      E.q[a] = static_cast<double>(qa);
+      const int64_t v = ((2 * cX[a] + 1) << (Lmax - LX)) - ((2 * cB[a] + 1) << (Lmax - LB)) -
+                        (static_cast<int64_t>(qa) << (Lmax + 1));
+      E.off[a] = ldexpf(static_cast<float>(v), -(Lmax + 1));
+    }
   }
   return E;
 }
@@ -173,9 +192,10 @@ struct BitWalker {
 // target leaf's frame); the warp walks its 32 sources, every lane tests its
 // own target and the lanes with a pair inside the cutoff evaluate it.  The
 // tile's partial sums are added to a two-sum (hi, lo) accumulator.
-template <int KM, bool GRAD, int NT, int NR>
-__global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ NearParams P) {
+template <int D, int KM, bool GRAD, int NT, int NR>
+__global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ NearParams P) {
   static_assert(NR == 1 || (KM == 1 && !GRAD), "several force columns: Stokeslet velocity only");
+  static_assert(D == 3 || !GRAD, "the gradient kernel is 3D");
   constexpr bool COMP = (NR == 1);                     // two-sum accumulation
   __shared__ float4 s_pos[4][kTile];
   __shared__ float4 s_f[(KM & 1) ? 4 : 1][(KM & 1) ? NR : 1][kTile];
@@ -188,8 +208,8 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
   const int B = P.tile_leaf[tile];
   const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
   const int LB = P.leaf_level[B];
-  int64_t cB[3];
-  leaf_coords<3>(P.leaf_anchor[B], LB, P.M, cB);
+  int64_t cB[3] = {0, 0, 0};
+  leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
   const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
   const bool on = lane < nt;
   const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -207,8 +227,9 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
 
   const int e1 = P.near_off[B + 1];
   for (int e = P.near_off[B]; e < e1; ++e) {
-    const Entry E = make_entry(P, e, LB, cB);
+    const Entry E = make_entry<D>(P, e, LB, cB);
     const float nu2 = E.nu2, nuinv = E.nuinv;
+    const float nu2inv = nuinv * nuinv;
     const float nu2m = nu2 * (1.f + 0x1p-12f);
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
     for (int U = U0; U < U1; ++U) {
@@ -245,70 +266,88 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
         if (fmaf(a.x, xt.x, fmaf(a.y, xt.y, fmaf(a.z, xt.z, tt + a.w))) >= 0.f) continue;
         const float dx = fmaf(0.5f, a.x, xt.x), dy = fmaf(0.5f, a.y, xt.y), dz = fmaf(0.5f, a.z, xt.z);
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (r2 < nu2 && r2 > 0.f) {
-          float ri = rsqrtf(r2);
+        if (!(r2 < nu2 && r2 > 0.f)) continue;
+        const float rho2 = r2 * nu2inv;
+        const float t = fmaf(2.f, rho2, -1.f);
+        float ri = 0.f, ri2, logr2 = 0.f;
+        if (D == 3) {
+          ri = rsqrtf(r2);
           ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);      // one Newton step
-          const float t = fmaf(2.f, r2 * (nuinv * nuinv), -1.f);
-          const float ri2 = ri * ri;
-          if (KM & 1) {
-            const float g = horner<NT>(P.c32[P_GS], t);
-            const float h = horner<NT>(P.c32[P_HS], t);
-            const float A = fmaf(g, nuinv, ri);
-            const float C = ri2 * fmaf(h, nuinv, ri);
+          ri2 = ri * ri;
+        } else {
+          ri2 = __frcp_rn(r2);
+          logr2 = __logf(rho2);
+        }
+        if (KM & 1) {
+          const float g = horner<NT>(P.c32[P_GS], t);
+          const float h = horner<NT>(P.c32[P_HS], t);
+          float A, C;
+          if (D == 3) {
+            A = fmaf(g, nuinv, ri);
+            C = ri2 * fmaf(h, nuinv, ri);
+          } else {
+            A = -logr2 - g;
+            C = fmaf(-h, nu2inv, 2.f * ri2);
+          }
 #pragma unroll
-            for (int k = 0; k < NR; ++k) {
-              const float4 fs = s_f[(KM & 1) ? wid : 0][(KM & 1) ? k : 0][j];
-              const float xf = fmaf(dx, fs.x, fmaf(dy, fs.y, dz * fs.z));
-              const float Cx = C * xf;
-              p[k][0] = fmaf(A, fs.x, fmaf(Cx, dx, p[k][0]));
-              p[k][1] = fmaf(A, fs.y, fmaf(Cx, dy, p[k][1]));
-              p[k][2] = fmaf(A, fs.z, fmaf(Cx, dz, p[k][2]));
-              if (GRAD) {
-                const float dg = horner<NT>(P.c32[P_DGS], t);
-                const float dh = horner<NT>(P.c32[P_DHS], t);
-                const float nu3i = nuinv * nuinv * nuinv;
-                const float ri3 = ri2 * ri;
-                const float A1 = fmaf(2.f * dg, nu3i, -ri3);
-                const float C1 = fmaf(-3.f * ri3, ri2, ri2 * fmaf(2.f * dh, nu3i, -2.f * h * nuinv * ri2));
-                const float xv[3] = {dx, dy, dz};
-                const float fv[3] = {fs.x, fs.y, fs.z};
+          for (int k = 0; k < NR; ++k) {
+            const float4 fs = s_f[(KM & 1) ? wid : 0][(KM & 1) ? k : 0][j];
+            const float xf = fmaf(dx, fs.x, fmaf(dy, fs.y, dz * fs.z));
+            const float Cx = C * xf;
+            p[k][0] = fmaf(A, fs.x, fmaf(Cx, dx, p[k][0]));
+            p[k][1] = fmaf(A, fs.y, fmaf(Cx, dy, p[k][1]));
+            if (D == 3) p[k][2] = fmaf(A, fs.z, fmaf(Cx, dz, p[k][2]));
+            if (GRAD) {
+              const float dg = horner<NT>(P.c32[P_DGS], t);
+              const float dh = horner<NT>(P.c32[P_DHS], t);
+              const float nu3i = nuinv * nuinv * nuinv;
+              const float ri3 = ri2 * ri;
+              const float A1 = fmaf(2.f * dg, nu3i, -ri3);
+              const float C1 = fmaf(-3.f * ri3, ri2, ri2 * fmaf(2.f * dh, nu3i, -2.f * h * nuinv * ri2));
+              const float xv[3] = {dx, dy, dz};
+              const float fv[3] = {fs.x, fs.y, fs.z};
 #pragma unroll
-                for (int jj = 0; jj < 3; ++jj) {
-                  const float a1 = fmaf(A1, fv[jj], C1 * xv[jj] * xf);
+              for (int jj = 0; jj < 3; ++jj) {
+                const float a1 = fmaf(A1, fv[jj], C1 * xv[jj] * xf);
 #pragma unroll
-                  for (int mm = 0; mm < 3; ++mm) {
-                    float v = fmaf(a1, xv[mm], C * xv[jj] * fv[mm]);
-                    if (jj == mm) v = fmaf(C, xf, v);
-                    pg[jj * 3 + mm] += v;
-                  }
+                for (int mm = 0; mm < 3; ++mm) {
+                  float v = fmaf(a1, xv[mm], C * xv[jj] * fv[mm]);
+                  if (jj == mm) v = fmaf(C, xf, v);
+                  pg[jj * 3 + mm] += v;
                 }
               }
             }
           }
-          if (KM & 2) {
-            const float pt = horner<NT>(P.c32[P_PT], t);
-            const float qt = horner<NT>(P.c32[P_QT], t);
-            const float4 gs = s_g[(KM & 2) ? wid : 0][j];
-            const float4 nsv = s_n[(KM & 2) ? wid : 0][j];
-            const float xn = fmaf(dx, nsv.x, fmaf(dy, nsv.y, dz * nsv.z));
-            const float xg = fmaf(dx, gs.x, fmaf(dy, gs.y, dz * gs.z));
-            const float Dc = pt * nuinv * ri2;
-            const float Ec = -6.f * ri2 * ri2 * fmaf(qt, nuinv, ri);
-            const float Ex = Ec * xg * xn + Dc * nsv.w;      // coefficient of x
-            p[0][0] += fmaf(Dc, fmaf(gs.x, xn, nsv.x * xg), Ex * dx);
-            p[0][1] += fmaf(Dc, fmaf(gs.y, xn, nsv.y * xg), Ex * dy);
-            p[0][2] += fmaf(Dc, fmaf(gs.z, xn, nsv.z * xg), Ex * dz);
+        }
+        if (KM & 2) {
+          const float pt = horner<NT>(P.c32[P_PT], t);
+          const float qt = horner<NT>(P.c32[P_QT], t);
+          const float4 gs = s_g[(KM & 2) ? wid : 0][j];
+          const float4 nsv = s_n[(KM & 2) ? wid : 0][j];
+          const float xn = fmaf(dx, nsv.x, fmaf(dy, nsv.y, dz * nsv.z));
+          const float xg = fmaf(dx, gs.x, fmaf(dy, gs.y, dz * gs.z));
+          float Dc, Ec;
+          if (D == 3) {
+            Dc = pt * nuinv * ri2;
+            Ec = -6.f * ri2 * ri2 * fmaf(qt, nuinv, ri);
+          } else {
+            Dc = -pt * nu2inv;
+            Ec = fmaf(6.f * qt, nu2inv * nu2inv, -8.f * ri2 * ri2);
           }
+          const float Ex = Ec * xg * xn + Dc * nsv.w;      // coefficient of x
+          p[0][0] += fmaf(Dc, fmaf(gs.x, xn, nsv.x * xg), Ex * dx);
+          p[0][1] += fmaf(Dc, fmaf(gs.y, xn, nsv.y * xg), Ex * dy);
+          if (D == 3) p[0][2] += fmaf(Dc, fmaf(gs.z, xn, nsv.z * xg), Ex * dz);
         }
       }
       if (COMP) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) two_sum_add(uh[0][a], ul[a], p[0][a]);
+        for (int a = 0; a < D; ++a) two_sum_add(uh[0][a], ul[a], p[0][a]);
       } else {
 #pragma unroll
         for (int k = 0; k < NR; ++k)
 #pragma unroll
-          for (int a = 0; a < 3; ++a) uh[k][a] += p[k][a];
+          for (int a = 0; a < D; ++a) uh[k][a] += p[k][a];
       }
       if (GRAD) {
 #pragma unroll
@@ -318,19 +357,19 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
   }
   if (!on) return;
   const int64_t o = P.perm[t0 + lane];
-  const double nutinv = ldexp(1.0, LB + 1);
+  const double sc = self_coeff<D>(P, LB);
   const int nr = P.n_rhs;
   if (P.u) {
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
       if (k >= nr) break;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
+      for (int a = 0; a < D; ++a) {
         double v = static_cast<double>(uh[k][a]);
         if (COMP) v += static_cast<double>(ul[a]);
         v *= kInv8Pi;
-        const int64_t q = (o * 3 + a) * nr + k;
-        if (KM & 1) v += P.self_base * nutinv * P.f_orig[q];
+        const int64_t q = (o * D + a) * nr + k;
+        if (KM & 1) v += sc * P.f_orig[q];
         P.u[q] = v;
       }
     }
@@ -345,19 +384,21 @@ __global__ void __launch_bounds__(128) k_near_mixed3(const __grid_constant__ Nea
 // ----------------------------------------------------------------- FP64
 // Same traversal and FP32 candidate test; every candidate is then decided
 // exactly in FP64 with the oracle's operation order.
-template <int KM, bool GRAD, int NT, int NR>
+template <int D, int KM, bool GRAD, int NT, int NR>
 struct Fp64Shape {
   static constexpr int NB = (NR == 1) ? ((KM == 1) ? 4 : 2) : 1;     // staged tiles per batch
   static constexpr int WPB = (NR > 4) ? 2 : 4;                       // warps per block
 };
 
-template <int KM, bool GRAD, int NT, int NR>
-__global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ NearParams P) {
+template <int D, int KM, bool GRAD, int NT, int NR>
+__global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearParams P) {
   static_assert(NR == 1 || (KM == 1 && !GRAD), "several force columns: Stokeslet velocity only");
-  constexpr int NB = Fp64Shape<KM, GRAD, NT, NR>::NB;
-  constexpr int WPB = Fp64Shape<KM, GRAD, NT, NR>::WPB;
+  static_assert(D == 3 || !GRAD, "the gradient kernel is 3D");
+  constexpr int NB = Fp64Shape<D, KM, GRAD, NT, NR>::NB;
+  constexpr int WPB = Fp64Shape<D, KM, GRAD, NT, NR>::WPB;
   constexpr int NS = NB * kTile;
-  constexpr int NF = 3 + ((KM & 1) ? 3 * NR : 0) + ((KM & 2) ? 7 : 0);
+  constexpr int NF = D + ((KM & 1) ? D * NR : 0) + ((KM & 2) ? 2 * D + 1 : 0);
+  constexpr int Z = (D == 3) ? 2 : 0;   // index of the z row where one exists
   __shared__ float4 sA[WPB][NS];
   __shared__ double sD[WPB][NF][NS];
   __shared__ double sQ[WPB][NB][4];                  // per staged tile: q, 1/nu
@@ -368,8 +409,8 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
   const int B = P.tile_leaf[tile];
   const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
   const int LB = P.leaf_level[B];
-  int64_t cB[3];
-  leaf_coords<3>(P.leaf_anchor[B], LB, P.M, cB);
+  int64_t cB[3] = {0, 0, 0};
+  leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
   const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
   const bool on = lane < nt;
   const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -377,7 +418,7 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
   double wt[3] = {0.0, 0.0, 0.0};
   if (on)
 #pragma unroll
-    for (int a = 0; a < 3; ++a) wt[a] = P.w[a * N + t0 + lane];
+    for (int a = 0; a < D; ++a) wt[a] = P.w[a * N + t0 + lane];
 
   double acc[NR][3];
 #pragma unroll
@@ -399,29 +440,48 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
       const double* q = sQ[wid][idx >> 5];
       const double dx = __dadd_rn(__dsub_rn(wt[0], sD[wid][0][idx]), q[0]);
       const double dy = __dadd_rn(__dsub_rn(wt[1], sD[wid][1][idx]), q[1]);
-      const double dz = __dadd_rn(__dsub_rn(wt[2], sD[wid][2][idx]), q[2]);
-      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      double dz = 0.0, r2;
+      if (D == 3) {
+        dz = __dadd_rn(__dsub_rn(wt[2], sD[wid][Z][idx]), q[2]);
+        r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+      } else {
+        r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+      }
       const double nuinv = q[3];
-      const double rho2 = r2 * (nuinv * nuinv);          // exact: nuinv is a power of two
+      const double nu2inv = nuinv * nuinv;
+      const double rho2 = r2 * nu2inv;                  // exact: nuinv is a power of two
       if (!(rho2 < 1.0 && r2 > 0.0)) continue;
-      const double ri = 1.0 / sqrt(r2);
       const double t = fma(2.0, rho2, -1.0);
-      const double ri2 = ri * ri;
-      int k = 3;
+      double ri = 0.0, ri2, logr2 = 0.0;
+      if (D == 3) {
+        ri = 1.0 / sqrt(r2);
+        ri2 = ri * ri;
+      } else {
+        ri2 = 1.0 / r2;
+        logr2 = log(rho2);
+      }
+      int k = D;
       if (KM & 1) {
         const double g = horner<NT>(P.c64[P_GS], t);
         const double h = horner<NT>(P.c64[P_HS], t);
-        const double A = fma(g, nuinv, ri);
-        const double C = ri2 * fma(h, nuinv, ri);
+        double A, C;
+        if (D == 3) {
+          A = fma(g, nuinv, ri);
+          C = ri2 * fma(h, nuinv, ri);
+        } else {
+          A = -logr2 - g;
+          C = fma(-h, nu2inv, 2.0 * ri2);
+        }
 #pragma unroll
         for (int c = 0; c < NR; ++c) {
-          const double fx = sD[wid][k][idx], fy = sD[wid][k + 1][idx], fz = sD[wid][k + 2][idx];
-          k += 3;
+          const double fx = sD[wid][k][idx], fy = sD[wid][k + 1][idx];
+          const double fz = (D == 3) ? sD[wid][k + Z][idx] : 0.0;
+          k += D;
           const double xf = fma(dx, fx, fma(dy, fy, dz * fz));
           const double Cx = C * xf;
           acc[c][0] = fma(A, fx, fma(Cx, dx, acc[c][0]));
           acc[c][1] = fma(A, fy, fma(Cx, dy, acc[c][1]));
-          acc[c][2] = fma(A, fz, fma(Cx, dz, acc[c][2]));
+          if (D == 3) acc[c][2] = fma(A, fz, fma(Cx, dz, acc[c][2]));
           if (GRAD) {
             const double dg = horner<NT>(P.c64[P_DGS], t);
             const double dh = horner<NT>(P.c64[P_DHS], t);
@@ -447,17 +507,25 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
       if (KM & 2) {
         const double pt = horner<NT>(P.c64[P_PT], t);
         const double qt = horner<NT>(P.c64[P_QT], t);
-        const double gx_ = sD[wid][k][idx], gy_ = sD[wid][k + 1][idx], gz_ = sD[wid][k + 2][idx];
-        const double nx = sD[wid][k + 3][idx], ny = sD[wid][k + 4][idx], nz = sD[wid][k + 5][idx];
-        const double gn = sD[wid][k + 6][idx];
+        const double gx_ = sD[wid][k][idx], gy_ = sD[wid][k + 1][idx];
+        const double gz_ = (D == 3) ? sD[wid][k + Z][idx] : 0.0;
+        const double nx = sD[wid][k + D][idx], ny = sD[wid][k + D + 1][idx];
+        const double nz = (D == 3) ? sD[wid][k + D + Z][idx] : 0.0;
+        const double gn = sD[wid][k + 2 * D][idx];
         const double xn = fma(dx, nx, fma(dy, ny, dz * nz));
         const double xg = fma(dx, gx_, fma(dy, gy_, dz * gz_));
-        const double Dc = pt * nuinv * ri2;
-        const double Ec = -6.0 * ri2 * ri2 * fma(qt, nuinv, ri);
+        double Dc, Ec;
+        if (D == 3) {
+          Dc = pt * nuinv * ri2;
+          Ec = -6.0 * ri2 * ri2 * fma(qt, nuinv, ri);
+        } else {
+          Dc = -pt * nu2inv;
+          Ec = fma(6.0 * qt, nu2inv * nu2inv, -8.0 * ri2 * ri2);
+        }
         const double Ex = Ec * xg * xn + Dc * gn;
         acc[0][0] += fma(Dc, fma(gx_, xn, nx * xg), Ex * dx);
         acc[0][1] += fma(Dc, fma(gy_, xn, ny * xg), Ex * dy);
-        acc[0][2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
+        if (D == 3) acc[0][2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
       }
     }
     __syncwarp();
@@ -466,7 +534,7 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
 
   const int e1 = P.near_off[B + 1];
   for (int e = P.near_off[B]; e < e1; ++e) {
-    const Entry E = make_entry(P, e, LB, cB);
+    const Entry E = make_entry<D>(P, e, LB, cB);
     const float nu2m = E.nu2 * (1.f + 0x1p-12f);
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
     for (int U = U0; U < U1; ++U) {
@@ -487,15 +555,15 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
         sA[wid][slot] = make_float4(-2.f * sx, -2.f * sy, -2.f * sz, fmaf(sx, sx, fmaf(sy, sy, sz * sz)) - nu2m);
         int k = 0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) sD[wid][k++][slot] = P.w[a * N + sidx];
+        for (int a = 0; a < D; ++a) sD[wid][k++][slot] = P.w[a * N + sidx];
         if (KM & 1)
 #pragma unroll
-          for (int a = 0; a < 3 * NR; ++a) sD[wid][k++][slot] = P.f64[a * N + sidx];
+          for (int a = 0; a < D * NR; ++a) sD[wid][k++][slot] = P.f64[a * N + sidx];
         if (KM & 2) {
 #pragma unroll
-          for (int a = 0; a < 3; ++a) sD[wid][k++][slot] = P.g64[a * N + sidx];
+          for (int a = 0; a < D; ++a) sD[wid][k++][slot] = P.g64[a * N + sidx];
 #pragma unroll
-          for (int a = 0; a < 4; ++a) sD[wid][k++][slot] = P.n64[a * N + sidx];
+          for (int a = 0; a < D + 1; ++a) sD[wid][k++][slot] = P.n64[a * N + sidx];
         }
       } else {
         sA[wid][slot] = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));
@@ -507,17 +575,17 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
 
   if (!on) return;
   const int64_t o = P.perm[t0 + lane];
-  const double nutinv = ldexp(1.0, LB + 1);
+  const double sc = self_coeff<D>(P, LB);
   const int nr = P.n_rhs;
   if (P.u) {
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
       if (c >= nr) break;
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
+      for (int a = 0; a < D; ++a) {
         double v = acc[c][a] * kInv8Pi;
-        const int64_t q = (o * 3 + a) * nr + c;
-        if (KM & 1) v += P.self_base * nutinv * P.f_orig[q];
+        const int64_t q = (o * D + a) * nr + c;
+        if (KM & 1) v += sc * P.f_orig[q];
         P.u[q] = v;
       }
     }
@@ -528,19 +596,22 @@ __global__ void __launch_bounds__(128) k_near_fp64_3(const __grid_constant__ Nea
   }
 }
 
-template <int KM, bool GRAD, int NT, int NR>
-void run_near_mixed3(const NearParams& P, cudaStream_t s) {
-  k_near_mixed3<KM, GRAD, NT, NR><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P);
+template <int D, int KM, bool GRAD, int NT, int NR>
+void run_near_mixed(const NearParams& P, cudaStream_t s) {
+  k_near_mixed<D, KM, GRAD, NT, NR><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P);
 }
-template <int KM, bool GRAD, int NT, int NR>
-void run_near_fp64_3(const NearParams& P, cudaStream_t s) {
-  constexpr int WPB = Fp64Shape<KM, GRAD, NT, NR>::WPB;
-  k_near_fp64_3<KM, GRAD, NT, NR><<<(P.n_tile + WPB - 1) / WPB, 32 * WPB, 0, s>>>(P);
+template <int D, int KM, bool GRAD, int NT, int NR>
+void run_near_fp64(const NearParams& P, cudaStream_t s) {
+  constexpr int WPB = Fp64Shape<D, KM, GRAD, NT, NR>::WPB;
+  k_near_fp64<D, KM, GRAD, NT, NR><<<(P.n_tile + WPB - 1) / WPB, 32 * WPB, 0, s>>>(P);
 }
 
-// instantiation lists (near_mixed.cu, near_fp64.cu): (kernels, gradient, NT, NR)
-#define DMK_FOR_EACH_VARIANT(M, NT) \
-  M(1, false, NT, 1) M(2, false, NT, 1) M(3, false, NT, 1) M(1, true, NT, 1) M(1, false, NT, 4) M(1, false, NT, 16)
+// instantiation lists (near_mixed*.cu, near_fp64*.cu): (dim, kernels, gradient, NT, NR)
+#define DMK_FOR_EACH_VARIANT_3D(M, NT) \
+  M(3, 1, false, NT, 1) M(3, 2, false, NT, 1) M(3, 3, false, NT, 1) M(3, 1, true, NT, 1) \
+  M(3, 1, false, NT, 4) M(3, 1, false, NT, 16)
+#define DMK_FOR_EACH_VARIANT_2D(M, NT) \
+  M(2, 1, false, NT, 1) M(2, 2, false, NT, 1) M(2, 3, false, NT, 1) M(2, 1, false, NT, 4) M(2, 1, false, NT, 16)
 
 #define DMK_NT_MIXED(X) X(8) X(12) X(16) X(20) X(24)
 #define DMK_NT_FP64(X) X(16) X(20) X(24) X(28) X(32)

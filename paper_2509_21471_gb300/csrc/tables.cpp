@@ -251,6 +251,149 @@ void deriv_s(const double* p, int n, double* dp, int* dn) {
 
 }  // namespace
 
+// ------------------------------------------------------------- 2D (App. B)
+namespace {
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n from the
+// three-term recurrence, initial guesses cos(pi (i + 3/4) / (n + 1/2)))
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+const double kR2 = 1.0 + std::sqrt(2.0);   // truncation radius R = 1 + sqrt(d), Sec. 2.3
+
+// Bessel-combination series below z = 2.  With j0_m the z^{2m} coefficient
+// of J0 and j1_m the z^{2m+1} coefficient of J1:
+//   d : J0 - J1/z                             = sum (j0_m - j1_m) z^{2m}
+//   o : (2 J1 - z J0)/z^3                     = sum (2 j1_m - j0_m) z^{2m-2}
+//   td: (4 J1 - 2 z J0 - z^2 J1)/z^3          = sum (4 j1_m - 2 j0_m - j1_{m-1}) z^{2m-2}
+//   to: ((8/3) J1 - (4/3) z J0 - z^2 J1/3)/z^5 = sum ((8/3) j1_m - (4/3) j0_m - j1_{m-1}/3) z^{2m-4}
+// (the terms with negative powers vanish identically).
+double combo_series(int kind, double z) {
+  double z2 = z * z;
+  double sum = 0.0, j0m = 1.0, j1m = 0.5, j1prev = 0.0, zp = 1.0;   // m = 0
+  for (int m = 0; m < 40; ++m) {
+    double coef = 0.0;
+    int pw = 0;
+    switch (kind) {
+      case 0: coef = j0m - j1m; pw = 2 * m; break;
+      case 1: coef = 2.0 * j1m - j0m; pw = 2 * m - 2; break;
+      case 2: coef = 4.0 * j1m - 2.0 * j0m - j1prev; pw = 2 * m - 2; break;
+      default: coef = (8.0 / 3.0) * j1m - (4.0 / 3.0) * j0m - j1prev / 3.0; pw = 2 * m - 4; break;
+    }
+    if (pw >= 0) {
+      sum += coef * zp;
+      zp *= z2;
+    }
+    j1prev = j1m;
+    j0m *= -1.0 / (4.0 * (m + 1.0) * (m + 1.0));
+    j1m *= -1.0 / (4.0 * (m + 1.0) * (m + 2.0));
+  }
+  return sum;
+}
+
+double combo(int kind, double z) {
+  if (z < 2.0) return combo_series(kind, z);
+  const double J0 = std::cyl_bessel_j(0.0, z), J1 = std::cyl_bessel_j(1.0, z);
+  switch (kind) {
+    case 0: return J0 - J1 / z;
+    case 1: return (2.0 * J1 - z * J0) / (z * z * z);
+    case 2: return (4.0 * J1 - 2.0 * z * J0 - z * z * J1) / (z * z * z);
+    default: return ((8.0 / 3.0) * J1 - (4.0 / 3.0) * z * J0 - z * z * J1 / 3.0) / (z * z * z * z * z);
+  }
+}
+
+// B-hat^R(k) = (1 - J0(Rk) - R k J1(Rk)/2) / k^4 (Eq. (Btrunc_hat), d = 2);
+// series sum_{m>=2} (-1)^m (m - 1) (z/2)^{2m} / (m!)^2 below z = 1/2.
+double bhat_trunc2(double k) {
+  const double z = kR2 * k;
+  double num;
+  if (z < 0.5) {
+    num = 0.0;
+    double t = 1.0;    // (z/2)^{2m} / (m!)^2
+    for (int m = 1; m < 30; ++m) {
+      t *= (z * z / 4.0) / (double(m) * m);
+      num += ((m % 2) ? -1.0 : 1.0) * (m - 1.0) * t;
+    }
+    if (k == 0.0) return std::pow(kR2, 4) / 64.0;
+  } else {
+    num = 1.0 - std::cyl_bessel_j(0.0, z) - 0.5 * z * std::cyl_bessel_j(1.0, z);
+  }
+  return num / (k * k * k * k);
+}
+
+}  // namespace
+
+static int build_tables_2d(const ProlateSeries& ser, double c, double fp32_tol, KernelTables* out) {
+  // gamma-hat(k) = phi-hat(k) - k phi-hat'(k)/2 on Gauss-Legendre nodes of [0, c]
+  // (Eq. (gammaB_in_phi); phi-hat(k) = 2 int_0^1 phi(t) cos(kt) dt)
+  std::vector<double> tx, tw, kx, kw;
+  gauss_legendre(200, tx, tw);
+  gauss_legendre(160, kx, kw);
+  const int nt = 200, nk = 160;
+  std::vector<double> tn(nt), phit(nt);
+  for (int i = 0; i < nt; ++i) {
+    tn[i] = 0.5 * (tx[i] + 1.0);
+    phit[i] = series_phi(ser, tn[i]);
+  }
+  std::vector<double> kn(nk), weight(nk);
+  for (int j = 0; j < nk; ++j) {
+    const double k = 0.5 * c * (kx[j] + 1.0);
+    double ph = 0.0, dph = 0.0;
+    for (int i = 0; i < nt; ++i) {
+      ph += tw[i] * phit[i] * std::cos(k * tn[i]);
+      dph -= tw[i] * tn[i] * phit[i] * std::sin(k * tn[i]);
+    }
+    // 2 int_0^1 = int_{-1}^{1} with the half-interval Jacobian 1/2 folded in
+    const double gam = ph - 0.5 * k * dph;
+    kn[j] = k;
+    weight[j] = 0.5 * c * kw[j] * bhat_trunc2(k) * gam;
+  }
+  // M-functions at unit scale: m = 4 int k^p G(k rho) B-hat^R gamma-hat dk (+ 2(1 - log R) for m_d)
+  const int pw[4] = {3, 5, 5, 7};
+  auto mfun = [&](int kind, double rho) {
+    double s = 0.0;
+    for (int j = 0; j < nk; ++j) s += std::pow(kn[j], pw[kind]) * combo(kind, kn[j] * rho) * weight[j];
+    s *= 4.0;
+    if (kind == 0) s += 2.0 * (1.0 - std::log(kR2));
+    return s;
+  };
+  double fv[4][kFitN];
+  for (int j = 0; j < kFitN; ++j) {
+    const double t = std::cos(M_PI * (j + 0.5) / kFitN);
+    const double rho = std::sqrt(0.5 * (t + 1.0));
+    for (int kind = 0; kind < 4; ++kind) fv[kind][j] = mfun(kind, rho);
+  }
+  const int ids[4] = {P_GS, P_HS, P_PT, P_QT};
+  for (int kind = 0; kind < 4; ++kind)
+    fit(fv[kind], fp32_tol, &out->n64[ids[kind]], out->p64[ids[kind]], &out->n32[ids[kind]], out->p32[ids[kind]]);
+  // lim_{r->0} Mdiag(r)/r = 2 int B-hat^R gamma-hat k^3 dk + 2(1 - log R) (Eqs. (msdiag0), (msdiag))
+  double s = 0.0;
+  for (int j = 0; j < nk; ++j) s += kn[j] * kn[j] * kn[j] * weight[j];
+  out->self2d_m0 = 2.0 * s + 2.0 * (1.0 - std::log(kR2));
+  return 0;
+}
+
 int build_tables(int dim, double c, double fp32_tol, KernelTables* out) {
   *out = KernelTables();
   out->dim = dim;
@@ -258,7 +401,8 @@ int build_tables(int dim, double c, double fp32_tol, KernelTables* out) {
   ProlateSeries ser;
   if (prolate_series(c, &ser)) return 1;
   out->phi0 = series_phi(ser, 0.0);
-  if (dim != 3) return 3;   // the 2D tables are built by build_tables_2d
+  if (dim == 2) return build_tables_2d(ser, c, fp32_tol, out);
+  if (dim != 3) return 3;
 
   double fg[kFitN], fh[kFitN], fp[kFitN], fq[kFitN];
   for (int j = 0; j < kFitN; ++j) {

@@ -75,3 +75,23 @@ def test_host_tables_match_oracle_residual_functions(dmk_lib, eps):
         f = lambda ss: ((k3.Sdiag if base == 0 else k3.Soffd)(w, np.sqrt(ss)) - 1) / np.sqrt(ss)
         fd = (f(s + h) - f(s - h)) / (2 * h)
         assert np.max(np.abs(np.polynomial.polynomial.polyval(t, pd) - fd)) < 1e-6 * np.abs(fd).max() + 1e-8
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-8, 1e-12])
+def test_host_tables_2d_match_oracle(dmk_lib, eps):
+    from oracle import kernels2d as k2
+    kern = k2.Kernel2D(ProlateWindow(bandlimit_c(eps, stokeslet=True, stresslet=True)))
+    rho = np.linspace(0.01, 0.999, 150)
+    t = 2 * rho ** 2 - 1
+    for which, fn in enumerate((kern.m_d, kern.m_o, kern.m_td, kern.m_to)):
+        ref = fn(rho)
+        _, _, p64 = dmk_lib.kernel_table(2, eps, which, kernels=3)
+        _, _, p32 = dmk_lib.kernel_table(2, eps, which, fp32=True, kernels=3)
+        scale = np.abs(ref).max()
+        # m_to weighs k^7: near k = c the two sides' gamma-hat quadratures differ
+        # by rounding, ~1e-12 of max|m_to| at small rho
+        assert np.max(np.abs(np.polynomial.polynomial.polyval(t, p64) - ref)) < 5e-12 * scale, which
+        assert np.max(np.abs(np.polynomial.polynomial.polyval(t, p32) - ref)) < max(eps / 50, 3e-7) * scale, which
+        assert len(p64) <= 32 and len(p32) <= 24
+    _, _, m0 = dmk_lib.kernel_table(2, eps, 6, kernels=3)
+    assert abs(m0[0] - kern.self_md0()) < 1e-12 * abs(kern.self_md0())
