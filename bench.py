@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--leaf-capacity", type=int, default=0, help="0 = paper's n_s for eps")
     ap.add_argument("--cpu-sample", type=int, default=4000, help="points in the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (eps = 1e-10, 2D periodic, batched, gradient)")
     return ap.parse_args()
 
 
@@ -152,6 +154,96 @@ def run_reference(args):
                                        f"(oracle tree + near pass, numpy, 1 thread)"},
             "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------- other workloads
+def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
+    """The remaining workloads of the hot path, each timed per step (plan +
+    eval, or forward + backward) and per near-field evaluation (plan reused),
+    in both precisions.  Reported beside the headline; not part of it."""
+    import numpy as np
+    import torch
+
+    def measure(make_plan, evaluate, n_targets, k):
+        out = {}
+        for name, prec in (("mixed", dmk.MIXED), ("fp64", dmk.FP64)):
+            kk = k if prec == dmk.MIXED else k_fp64
+            def step():
+                p = make_plan(prec)
+                evaluate(p)
+                p.close()
+            step()
+            torch.cuda.synchronize()
+            t_step = max_over_ranks(sum(timed(step, kk)) / kk / 1e3)
+            p = make_plan(prec)
+            evaluate(p)
+            torch.cuda.synchronize()
+            st = p.stats()
+            t_near = max_over_ranks(sum(timed(lambda: evaluate(p), kk)) / kk / 1e3)
+            p.close()
+            out[name] = {"ms_per_step": 1e3 * t_step, "targets_per_s": n_targets / t_step,
+                         "near_ms": 1e3 * t_near, "useful_pairs": st["useful_pairs"],
+                         "gpairs_useful": st["useful_pairs"] / t_near / 1e9, "leaves": st["leaves"],
+                         "leaf_capacity": st["leaf_capacity"]}
+        out["speedup_mixed_over_fp64"] = out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+        return out
+
+    res = {}
+    # 3D clustered, eps = 1e-10 (MIXED takes FP64 pair terms below eps = 2e-7)
+    x, f = wl.clustered_3d(n=args.n, sigma=0.02, seed_index=1 + 100 * rank)
+    xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
+    ud = torch.empty_like(fd)
+    r = measure(lambda prec: dmk.Plan(xd, eps=1e-10, precision=prec), lambda p: p.eval(fd, out=ud), len(x), k_mixed)
+    r.update(workload="3d-free-stokeslet-clustered-8gauss", n_points=len(x), eps=1e-10,
+             mixed_pair_arith="fp64 (eps < 2e-7)")
+    res["clustered_3d_eps1e-10"] = r
+    del xd, fd, ud
+
+    # 2D periodic unit square, Stokeslet + stresslet (k = 0 term included), eps = 1e-8
+    x, f, g, nrm = wl.periodic_2d(n=args.n, seed_index=2 + 100 * rank)
+    xd, fd, gd, nd = (torch.as_tensor(a, device="cuda") for a in (x, f, g, nrm))
+    ud = torch.empty_like(fd)
+    r = measure(lambda prec: dmk.Plan(xd, eps=1e-8, periodic=True, kernels=dmk.STOKESLET | dmk.STRESSLET,
+                                      precision=prec),
+                lambda p: p.eval(fd, gd, nd, out=ud), len(x), k_mixed)
+    r.update(workload="2d-periodic-stokeslet+stresslet-uniform", n_points=len(x), eps=1e-8,
+             mixed_pair_arith="fp64 (eps < 2e-7)")
+    res["periodic_2d_eps1e-8"] = r
+    del xd, fd, gd, nd, ud
+
+    # 256 independent 3D systems, 16 force columns, one plan and one launch
+    x, F, offs = wl.batched_3d(seed_index=3 + 100 * rank)
+    xd, Fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(F, device="cuda")
+    Ud = torch.empty_like(Fd)
+    r = measure(lambda prec: dmk.Plan(xd, eps=1e-6, precision=prec, n_rhs=16, offsets=offs),
+                lambda p: p.eval(Fd, out=Ud), len(x), 2)
+    r.update(workload="batched-256-systems-16-rhs", n_points=len(x), n_systems=len(offs) - 1, rhs=16, eps=1e-6,
+             mixed_pair_arith="fp32")
+    res["batched_256x16_eps1e-6"] = r
+    del xd, Fd, Ud
+
+    # differentiation: 3D periodic, N = 2e5, L = 1/2 |u - u_tgt|^2, gradients w.r.t. x and f
+    x, f = wl.periodic_3d(n=200_000, seed_index=4 + 100 * rank)
+    rng = wl.rng_for(4 + 100 * rank, extra=1)
+    xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
+    u_tgt = dmk.eval(xd, torch.as_tensor(f + 0.1 * rng.standard_normal(f.shape), device="cuda"),
+                     eps=1e-8, periodic=True, precision=dmk.FP64)
+    out = {}
+    for name, prec in (("mixed", dmk.MIXED), ("fp64", dmk.FP64)):
+        def fwd_bwd():
+            xt = xd.clone().requires_grad_(True)
+            ft = fd.clone().requires_grad_(True)
+            u = dmk.near_stokeslet(xt, ft, eps=1e-8, periodic=True, precision=prec)
+            (0.5 * ((u - u_tgt) ** 2).sum()).backward()
+        fwd_bwd()
+        torch.cuda.synchronize()
+        t = max_over_ranks(sum(timed(fwd_bwd, 2)) / 2 / 1e3)
+        out[name] = {"ms_per_step": 1e3 * t, "targets_per_s": len(x) / t}
+    out.update(workload="3d-periodic-uniform-loss-gradient", n_points=len(x), eps=1e-8,
+               step="plan + forward + backward (grad w.r.t. x and f)",
+               speedup_mixed_over_fp64=out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"])
+    res["gradient_periodic_3d_eps1e-8"] = out
+    return res
 
 
 # ------------------------------------------------------------------ our arm
@@ -277,10 +369,14 @@ def run_ours(args):
     achieved = near["mixed"]["useful_pairs"] * flops_per_pair / (near["mixed"]["ms"] / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": "k_near_mixed3 (near field, mixed precision)",
+                "kernel": "k_near_mixed<3,1,false,16,1> (near field, mixed precision)",
                 "flops_per_useful_pair": flops_per_pair,
                 "peak_basis": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
                               "(max SM clock of MEASURED_PEAKS.json)"}
+
+    extras = None
+    if not args.no_extras:
+        extras = run_extras(args, dmk, wl, timed, max_over_ranks, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -298,7 +394,7 @@ def run_ours(args):
                 "speedup_mixed_over_fp64": t_fp64 / (t_mixed / args.steps),
                 "near_field": near, "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_note": "our kernels per step (plan + eval); CUB sort/scan kernels not counted",
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks}
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "other_workloads": extras}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

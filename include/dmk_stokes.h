@@ -70,7 +70,11 @@ typedef struct {
   int32_t precision;     /* DMK_PRECISION_FP64: all arithmetic in float64.
                             DMK_PRECISION_MIXED: pair terms in float32 with
                             leaf-relative coordinates and compensated (two-sum)
-                            accumulation; self term and output in float64. */
+                            accumulation; self term and output in float64.
+                            FP32 pair terms carry a relative l2 error of about
+                            1e-7..2e-6, so for eps < 2e-7 MIXED takes the pair
+                            terms in float64 (an FP32 test still selects the
+                            candidate pairs) and meets eps like FP64. */
   int32_t components;    /* DMK_COMPONENTS_NEAR (the far field is not provided:
                             DMK_COMPONENTS_ALL returns DMK_ERR_UNSUPPORTED) */
   int32_t leaf_capacity; /* n_s, max points per leaf; 0 = the paper's value for

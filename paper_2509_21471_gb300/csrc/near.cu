@@ -156,6 +156,15 @@ __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned lo
   if (lane == 0 && cnt) atomicAdd(out, cnt);
 }
 
+// MIXED precision evaluates pair terms in FP32 only where that meets the
+// requested tolerance: its relative l2 error is set by FP32 rounding of the
+// pair terms (about 1e-7 to 2e-6 on clustered points), so below eps = 2e-7 the
+// pair terms are taken in FP64 (the FP32 candidate filter is kept).
+constexpr double kFp32PairMinEps = 2e-7;
+bool fp32_pairs(const dmk_stokes_opts_t& o) {
+  return o.precision == DMK_PRECISION_MIXED && o.eps >= kFp32PairMinEps;
+}
+
 int pick_nt(const int* set, int n, int need) {
   for (int i = 0; i < n; ++i)
     if (set[i] >= need) return set[i];
@@ -264,7 +273,7 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   const DeviceTree& T = p.tree;
   const int64_t N = T.N;
   const int D = p.opts.dim;
-  const bool mixed = p.opts.precision == DMK_PRECISION_MIXED;
+  const bool mixed = fp32_pairs(p.opts);
   const int km = (d_f ? 1 : 0) | (d_g ? 2 : 0);
   const bool grad = d_gradu != nullptr;
   if (grad && D != 3) throw Error{DMK_ERR_UNSUPPORTED, "the gradient is provided in 3D"};
@@ -297,10 +306,13 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   int nt = mixed ? pick_nt(kSetM, 5, need) : pick_nt(kSetD, 5, need);
   if (nt < 0) throw Error{DMK_ERR_UNSUPPORTED, "kernel table longer than the compiled kernels"};
   for (int id = 0; id < P_COUNT; ++id)
-    for (int k = 0; k < kPolyCap; ++k) {
-      P.c32[id][k] = k < tb.n32[id] ? tb.p32[id][k] : 0.f;
-      P.c64[id][k] = k < tb.n64[id] ? tb.p64[id][k] : 0.0;
-    }
+    for (int k = 0; k < kPolyCap; ++k) P.c64[id][k] = k < tb.n64[id] ? tb.p64[id][k] : 0.0;
+  auto c32 = [&](int id, int k) { return k < tb.n32[id] ? tb.p32[id][k] : 0.f; };
+  for (int k = 0; k < kPolyCap; ++k) {
+    P.c32p[0][k] = make_float2(c32(P_GS, k), c32(P_HS, k));
+    P.c32p[1][k] = make_float2(c32(P_PT, k), c32(P_QT, k));
+    P.c32p[2][k] = make_float2(c32(P_DGS, k), c32(P_DHS, k));
+  }
   if (T.n_tile > 0) {
     dispatch(mixed, D, km, grad, nt, NR, P, s);
     ++p.launches;
@@ -335,7 +347,7 @@ int64_t count_useful_pairs(const Plan& p) {
 }
 
 size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N) {
-  const bool mixed = o.precision == DMK_PRECISION_MIXED;
+  const bool mixed = fp32_pairs(o);
   const int NR = padded_rhs(o.n_rhs);
   size_t b = 0;
   if (mixed) b += std::max(3, NR) * N * sizeof(float4);

@@ -72,7 +72,7 @@ struct NearParams {
   double* gradu;         // [N][3][3] caller order
   double self_base;      // 3D: -phi(0)/(2 pi); 2D: -m_d(0)/(8 pi)
   int n_rhs;             // force columns of the caller's arrays
-  float c32[P_COUNT][kPolyCap];
+  float2 c32p[3][kPolyCap];   // FP32 pairs (gS, hS), (pT, qT), (gS', hS')
   double c64[P_COUNT][kPolyCap];
 };
 
@@ -189,15 +189,52 @@ struct BitWalker {
 
 // ---------------------------------------------------------------- mixed
 // Each surviving source tile is staged in shared memory (moved into the
-// target leaf's frame); the warp walks its 32 sources, every lane tests its
-// own target and the lanes with a pair inside the cutoff evaluate it.  The
-// tile's partial sums are added to a two-sum (hi, lo) accumulator.
+// target leaf's frame).  Every lane first tests its target against all 32
+// staged sources with the expanded form |x_t|^2 + (|s|^2 - nu'^2) - 2 x_t.s,
+// two sources per packed FP32x2 FMA, and collects the signs into a bit mask
+// (bit j: source j is a candidate).  The warp then walks the union of the
+// lanes' masks; for each source in it every lane takes the exact FP32 test
+// r^2 < nu^2 and the lanes inside the cutoff evaluate the pair.  The kernel
+// polynomials are evaluated in pairs ((gS, hS), (pT, qT), (gS', hS')) by packed
+// Horner.  The tile's partial sums are added to a two-sum (hi, lo) accumulator.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+template <int NT>
+__device__ __forceinline__ float2 horner2(const float2 (&c)[kPolyCap], float t) {
+  const float2 tt = f2(t, t);
+  float2 v = c[NT - 1];
+#pragma unroll
+  for (int k = NT - 2; k >= 0; --k) v = __ffma2_rn(v, tt, c[k]);
+  return v;
+}
+
+// bit j of the result is the sign of (|x_t|^2 + w_j + a_j . x_t), j = 0..31,
+// from the test rows of one staged tile (x, y, z, w as float[32] each)
+__device__ __forceinline__ uint32_t candidate_mask(const float4 (&rows)[4][8], float4 xt, float tt) {
+  const float2 X = f2(xt.x, xt.x), Y = f2(xt.y, xt.y), Z = f2(xt.z, xt.z), T = f2(tt, tt);
+  uint32_t bits = 0u;
+#pragma unroll
+  for (int q = 7; q >= 0; --q) {
+    const float4 ax = rows[0][q], ay = rows[1][q], az = rows[2][q], aw = rows[3][q];
+    const float2 hi = __ffma2_rn(f2(ax.z, ax.w), X,
+                                 __ffma2_rn(f2(ay.z, ay.w), Y, __ffma2_rn(f2(az.z, az.w), Z, __fadd2_rn(f2(aw.z, aw.w), T))));
+    const float2 lo = __ffma2_rn(f2(ax.x, ax.y), X,
+                                 __ffma2_rn(f2(ay.x, ay.y), Y, __ffma2_rn(f2(az.x, az.y), Z, __fadd2_rn(f2(aw.x, aw.y), T))));
+    bits = __funnelshift_l(__float_as_uint(hi.y), bits, 1);   // source 4q+3
+    bits = __funnelshift_l(__float_as_uint(hi.x), bits, 1);
+    bits = __funnelshift_l(__float_as_uint(lo.y), bits, 1);
+    bits = __funnelshift_l(__float_as_uint(lo.x), bits, 1);   // source 4q
+  }
+  return bits;
+}
+
 template <int D, int KM, bool GRAD, int NT, int NR>
 __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ NearParams P) {
   static_assert(NR == 1 || (KM == 1 && !GRAD), "several force columns: Stokeslet velocity only");
   static_assert(D == 3 || !GRAD, "the gradient kernel is 3D");
   constexpr bool COMP = (NR == 1);                     // two-sum accumulation
-  __shared__ float4 s_pos[4][kTile];
+  __shared__ float4 s_tst[4][4][8];                    // test rows: -2 s (x, y, z), |s|^2 - nu'^2
+  __shared__ float4 s_pos[4][kTile];                   // s (x, y, z) in the target leaf's frame
   __shared__ float4 s_f[(KM & 1) ? 4 : 1][(KM & 1) ? NR : 1][kTile];
   __shared__ float4 s_g[(KM & 2) ? 4 : 1][kTile];
   __shared__ float4 s_n[(KM & 2) ? 4 : 1][kTile];
@@ -215,6 +252,10 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
   const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
   // |x_t|^2; +inf for an empty lane makes every candidate test fail
   const float tt = on ? fmaf(xt.x, xt.x, fmaf(xt.y, xt.y, xt.z * xt.z)) : __int_as_float(0x7f800000);
+  float* const rowx = reinterpret_cast<float*>(s_tst[wid][0]);
+  float* const rowy = reinterpret_cast<float*>(s_tst[wid][1]);
+  float* const rowz = reinterpret_cast<float*>(s_tst[wid][2]);
+  float* const roww = reinterpret_cast<float*>(s_tst[wid][3]);
 
   float uh[NR][3], ul[COMP ? 3 : 1];
 #pragma unroll
@@ -239,8 +280,11 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
       if (lane < ns) {
         const float4 r = P.rel[s0 + lane];
         const float sx = r.x + E.off[0], sy = r.y + E.off[1], sz = r.z + E.off[2];
-        s_pos[wid][lane] = make_float4(-2.f * sx, -2.f * sy, -2.f * sz,
-                                       fmaf(sx, sx, fmaf(sy, sy, sz * sz)) - nu2m);
+        rowx[lane] = -2.f * sx;
+        rowy[lane] = -2.f * sy;
+        rowz[lane] = -2.f * sz;
+        roww[lane] = fmaf(sx, sx, fmaf(sy, sy, sz * sz)) - nu2m;
+        s_pos[wid][lane] = make_float4(sx, sy, sz, 0.f);
         if (KM & 1)
 #pragma unroll
           for (int k = 0; k < NR; ++k) s_f[(KM & 1) ? wid : 0][(KM & 1) ? k : 0][lane] = P.f32[k * N + s0 + lane];
@@ -249,22 +293,24 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
           s_n[(KM & 2) ? wid : 0][lane] = P.n32[s0 + lane];
         }
       } else {
-        s_pos[wid][lane] = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000));   // never a candidate
+        rowx[lane] = rowy[lane] = rowz[lane] = 0.f;
+        roww[lane] = __int_as_float(0x7f800000);      // never a candidate
       }
       __syncwarp();
+      // candidate test (margin 2^-12 nu^2, far above its rounding error), then
+      // the exact test r^2 < nu^2 for the sources some lane marked
+      uint32_t m = __reduce_or_sync(0xffffffffu, candidate_mask(s_tst[wid], xt, tt));
       float p[NR][3];
 #pragma unroll
       for (int k = 0; k < NR; ++k) p[k][0] = p[k][1] = p[k][2] = 0.f;
       float pg[GRAD ? 9 : 1];
 #pragma unroll
       for (int k = 0; k < (GRAD ? 9 : 1); ++k) pg[k] = 0.f;
-#pragma unroll 4
-      for (int j = 0; j < kTile; ++j) {
-        // candidate test |x_t|^2 + |s|^2 - nu'^2 - 2 x_t.s < 0 (cheap, margin
-        // 2^-12 nu^2 >> its rounding error), then the exact test r^2 < nu^2
-        const float4 a = s_pos[wid][j];
-        if (fmaf(a.x, xt.x, fmaf(a.y, xt.y, fmaf(a.z, xt.z, tt + a.w))) >= 0.f) continue;
-        const float dx = fmaf(0.5f, a.x, xt.x), dy = fmaf(0.5f, a.y, xt.y), dz = fmaf(0.5f, a.z, xt.z);
+      while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1u;
+        const float4 sp = s_pos[wid][j];
+        const float dx = xt.x - sp.x, dy = xt.y - sp.y, dz = xt.z - sp.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (!(r2 < nu2 && r2 > 0.f)) continue;
         const float rho2 = r2 * nu2inv;
@@ -279,16 +325,17 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
           logr2 = __logf(rho2);
         }
         if (KM & 1) {
-          const float g = horner<NT>(P.c32[P_GS], t);
-          const float h = horner<NT>(P.c32[P_HS], t);
+          const float2 gh = horner2<NT>(P.c32p[0], t);
           float A, C;
           if (D == 3) {
-            A = fmaf(g, nuinv, ri);
-            C = ri2 * fmaf(h, nuinv, ri);
+            A = fmaf(gh.x, nuinv, ri);
+            C = ri2 * fmaf(gh.y, nuinv, ri);
           } else {
-            A = -logr2 - g;
-            C = fmaf(-h, nu2inv, 2.f * ri2);
+            A = -logr2 - gh.x;
+            C = fmaf(-gh.y, nu2inv, 2.f * ri2);
           }
+          float2 dgh = f2(0.f, 0.f);
+          if (GRAD) dgh = horner2<NT>(P.c32p[2], t);
 #pragma unroll
           for (int k = 0; k < NR; ++k) {
             const float4 fs = s_f[(KM & 1) ? wid : 0][(KM & 1) ? k : 0][j];
@@ -298,12 +345,10 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
             p[k][1] = fmaf(A, fs.y, fmaf(Cx, dy, p[k][1]));
             if (D == 3) p[k][2] = fmaf(A, fs.z, fmaf(Cx, dz, p[k][2]));
             if (GRAD) {
-              const float dg = horner<NT>(P.c32[P_DGS], t);
-              const float dh = horner<NT>(P.c32[P_DHS], t);
               const float nu3i = nuinv * nuinv * nuinv;
               const float ri3 = ri2 * ri;
-              const float A1 = fmaf(2.f * dg, nu3i, -ri3);
-              const float C1 = fmaf(-3.f * ri3, ri2, ri2 * fmaf(2.f * dh, nu3i, -2.f * h * nuinv * ri2));
+              const float A1 = fmaf(2.f * dgh.x, nu3i, -ri3);
+              const float C1 = fmaf(-3.f * ri3, ri2, ri2 * fmaf(2.f * dgh.y, nu3i, -2.f * gh.y * nuinv * ri2));
               const float xv[3] = {dx, dy, dz};
               const float fv[3] = {fs.x, fs.y, fs.z};
 #pragma unroll
@@ -320,19 +365,18 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
           }
         }
         if (KM & 2) {
-          const float pt = horner<NT>(P.c32[P_PT], t);
-          const float qt = horner<NT>(P.c32[P_QT], t);
+          const float2 pq = horner2<NT>(P.c32p[1], t);
           const float4 gs = s_g[(KM & 2) ? wid : 0][j];
           const float4 nsv = s_n[(KM & 2) ? wid : 0][j];
           const float xn = fmaf(dx, nsv.x, fmaf(dy, nsv.y, dz * nsv.z));
           const float xg = fmaf(dx, gs.x, fmaf(dy, gs.y, dz * gs.z));
           float Dc, Ec;
           if (D == 3) {
-            Dc = pt * nuinv * ri2;
-            Ec = -6.f * ri2 * ri2 * fmaf(qt, nuinv, ri);
+            Dc = pq.x * nuinv * ri2;
+            Ec = -6.f * ri2 * ri2 * fmaf(pq.y, nuinv, ri);
           } else {
-            Dc = -pt * nu2inv;
-            Ec = fmaf(6.f * qt, nu2inv * nu2inv, -8.f * ri2 * ri2);
+            Dc = -pq.x * nu2inv;
+            Ec = fmaf(6.f * pq.y, nu2inv * nu2inv, -8.f * ri2 * ri2);
           }
           const float Ex = Ec * xg * xn + Dc * nsv.w;      // coefficient of x
           p[0][0] += fmaf(Dc, fmaf(gs.x, xn, nsv.x * xg), Ex * dx);

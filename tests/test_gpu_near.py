@@ -2,10 +2,10 @@
 
 Tolerances: the FP64 path evaluates the same formulas as the oracle, with
 polynomial kernel tables fitted to ~1e-15 relative and a different summation
-order, so relative l2 <= 1e-12.  The mixed path (FP32 pair terms, two-sum
-accumulation) must meet 10 * eps for eps >= 1e-7; below that its error is set
-by FP32 rounding of the pair terms (~1e-7 each, ~1e-6 in l2 for the
-stresslet's 1/r^2 kernel on clustered points) and is checked against 2e-6.
+order, so relative l2 <= 1e-12.  The mixed path must meet 10 * eps: FP32
+pair terms with two-sum accumulation for eps >= 2e-7 (their error, ~1e-7 to
+2e-6 in l2, is set by FP32 rounding of the pair terms), FP64 pair terms after
+an FP32 candidate test below that.
 """
 import zlib
 
@@ -26,7 +26,7 @@ FP64_TOL = 1e-12
 
 
 def mixed_tol(eps):
-    return 10 * eps if eps >= 1e-7 else 2e-6
+    return 10 * eps
 
 
 @pytest.fixture(scope="module")

@@ -3,8 +3,8 @@
 The FP64 path evaluates m_d, m_o, m_td, m_to from polynomial tables fitted to
 the same App. B quadratures the oracle sums directly (table error ~1e-14
 relative), so the bound is relative l2 <= 1e-12 as in 3D.  The mixed path
-(FP32 pair terms with FP32 log, two-sum accumulation) meets 10 * eps for
-eps >= 1e-7 and 2e-6 below that (FP32 floor of the pair terms).
+meets 10 * eps: FP32 pair terms (FP32 log, two-sum accumulation) for
+eps >= 2e-7, FP64 pair terms after an FP32 candidate test below that.
 """
 import zlib
 
@@ -25,7 +25,7 @@ FP64_TOL = 1e-12
 
 
 def mixed_tol(eps):
-    return 10 * eps if eps >= 1e-7 else 2e-6
+    return 10 * eps
 
 
 @pytest.fixture(scope="module")
