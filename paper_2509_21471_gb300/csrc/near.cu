@@ -1,6 +1,6 @@
 // Near-field dispatch, density permutation, the periodic stresslet zero mode
 // and the useful-pair count (2D and 3D).
-#include "near_kernel.cuh"
+#include "near_ff.cuh"
 
 namespace dmk {
 
@@ -12,6 +12,9 @@ namespace dmk {
 #define DMK_EXT_D_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_EXT_D, NT) DMK_FOR_EACH_VARIANT_2D(DMK_EXT_D, NT)
 DMK_NT_MIXED(DMK_EXT_M_NT)
 DMK_NT_FP64(DMK_EXT_D_NT)
+#define DMK_EXT_F(KM, NT) extern template void run_near_ff<KM, NT>(const NearParams&, const FFParams&, cudaStream_t);
+#define DMK_EXT_F_NT(NT) DMK_FOR_EACH_FF(DMK_EXT_F, NT)
+DMK_NT_FP64(DMK_EXT_F_NT)
 
 namespace {
 
@@ -109,6 +112,52 @@ __global__ void k_zero_apply(int64_t N, int D, const double* __restrict__ w, con
   for (int a = 0; a < D; ++a) u[o * D + a] -= w[a * N + i] * s[0] - s[1 + a];
 }
 
+// FP32 residual of the leaf-relative coordinates: rel_lo = (w - c) - rel, so
+// that rel + rel_lo carries the FP64 offset from the leaf centre c in FF.
+// One warp per tile, as the plan's rel is computed.
+template <int D>
+__global__ void k_rel_lo(const __grid_constant__ NearParams P, float4* __restrict__ out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= P.n_tile || lane >= P.tile_count[warp]) return;
+  const int leaf = P.tile_leaf[warp];
+  const int lev = P.leaf_level[leaf];
+  int64_t c[3] = {0, 0, 0};
+  leaf_coords<D>(P.leaf_anchor[leaf], lev, P.M, c);
+  const double h = ldexp(1.0, -lev);
+  const int64_t i = P.tile_start[warp] + lane;
+  const float4 r = P.rel[i];
+  const float rv[3] = {r.x, r.y, r.z};
+  float v[3] = {0.f, 0.f, 0.f};
+  for (int a = 0; a < D; ++a) {
+    const double centre = (static_cast<double>(c[a]) + 0.5) * h;
+    v[a] = __double2float_rn((P.w[a * P.N + i] - centre) - static_cast<double>(rv[a]));
+  }
+  out[i] = make_float4(v[0], v[1], v[2], 0.f);
+}
+
+// sorted FF split of a [N][3] FP64 array (hi = rounded value, lo = rounded
+// remainder); with n != nullptr, .w holds the split of g.n (g = in)
+__global__ void k_split_ff(int64_t N, const int32_t* __restrict__ perm, const double* __restrict__ in,
+                           const double* __restrict__ n, float4* __restrict__ hi, float4* __restrict__ lo) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t o = perm[i];
+  const double* src = n ? n : in;
+  float h[4], l[4];
+  double gn = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double v = src[o * 3 + a];
+    h[a] = __double2float_rn(v);
+    l[a] = __double2float_rn(v - static_cast<double>(h[a]));
+    if (n) gn += in[o * 3 + a] * n[o * 3 + a];
+  }
+  h[3] = __double2float_rn(gn);
+  l[3] = __double2float_rn(gn - static_cast<double>(h[3]));
+  hi[i] = make_float4(h[0], h[1], h[2], h[3]);
+  lo[i] = make_float4(l[0], l[1], l[2], l[3]);
+}
+
 // Number of pairs (t, s) with 0 < r2 < nu_ts^2, decided in float64 exactly as
 // the FP64 kernel does.  Source tiles are culled by bounding box and single
 // sources by an FP32 test with the kernels' margin before the FP64 decision.
@@ -160,9 +209,28 @@ __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned lo
 // requested tolerance: its relative l2 error is set by FP32 rounding of the
 // pair terms (about 1e-7 to 2e-6 on clustered points), so below eps = 2e-7 the
 // pair terms are taken in FP64 (the FP32 candidate filter is kept).
+// There (3D, one force column) the pair terms are evaluated in float-float
+// (k_near_ff), which GB300 runs far faster than FP64; the gradient, 2D and
+// several force columns take FP64 pair terms.
 constexpr double kFp32PairMinEps = 2e-7;
 bool fp32_pairs(const dmk_stokes_opts_t& o) {
   return o.precision == DMK_PRECISION_MIXED && o.eps >= kFp32PairMinEps;
+}
+bool ff_pairs(const dmk_stokes_opts_t& o) {
+  return o.precision == DMK_PRECISION_MIXED && o.eps < kFp32PairMinEps && o.dim == 3 && o.n_rhs == 1;
+}
+
+// workspace: [FP32 sorted densities (fp32 pairs)] [FP64 sorted densities] [FF split densities]
+struct WsLayout {
+  size_t f64_off, ff_off, bytes;
+};
+WsLayout ws_layout(const dmk_stokes_opts_t& o, int64_t N) {
+  const int NR = padded_rhs(o.n_rhs);
+  WsLayout L;
+  L.f64_off = fp32_pairs(o) ? std::max(3, NR) * N * sizeof(float4) : 0;
+  L.ff_off = L.f64_off + std::max(3 + 3 + 4, 3 * NR) * N * sizeof(double);
+  L.bytes = L.ff_off + (ff_pairs(o) ? 7 * N * sizeof(float4) : 0);
+  return L;
 }
 
 int pick_nt(const int* set, int n, int need) {
@@ -187,6 +255,17 @@ void dispatch(bool mixed, int dim, int km, bool grad, int nt, int nr, const Near
   DMK_NT_MIXED(DMK_CASE_M_NT)
   DMK_NT_FP64(DMK_CASE_D_NT)
   throw Error{DMK_ERR_UNSUPPORTED, "no compiled near-field kernel for this configuration"};
+}
+
+void dispatch_ff(int km, int nt, const NearParams& P, const FFParams& F, cudaStream_t s) {
+#define DMK_CASE_F(KM, NT)                  \
+  if (km == KM && nt == NT) {               \
+    run_near_ff<KM, NT>(P, F, s);           \
+    return;                                 \
+  }
+#define DMK_CASE_F_NT(NT) DMK_FOR_EACH_FF(DMK_CASE_F, NT)
+  DMK_NT_FP64(DMK_CASE_F_NT)
+  throw Error{DMK_ERR_UNSUPPORTED, "no compiled float-float kernel for this configuration"};
 }
 
 NearParams tree_params(const Plan& p) {
@@ -215,8 +294,8 @@ NearParams tree_params(const Plan& p) {
 
 // sorted copies of the densities in the workspace
 template <int D>
-void perm_densities(const Plan& p, bool mixed, int km, int nr, int NR, const double* d_f, const double* d_g,
-                    const double* d_n, char* ws, NearParams& P, cudaStream_t s) {
+void perm_densities(const Plan& p, bool mixed, bool ff, int km, int nr, int NR, const double* d_f,
+                    const double* d_g, const double* d_n, char* ws, NearParams& P, cudaStream_t s) {
   const DeviceTree& T = p.tree;
   const int64_t N = T.N;
   const int B = 256;
@@ -238,12 +317,12 @@ void perm_densities(const Plan& p, bool mixed, int km, int nr, int NR, const dou
     P.g32 = g32;
     P.n32 = n32;
   }
-  double* f64 = reinterpret_cast<double*>(ws + (mixed ? std::max(3, NR) * N * sizeof(float4) : 0));
+  double* f64 = reinterpret_cast<double*>(ws + ws_layout(p.opts, N).f64_off);
   double* g64 = f64 + 3 * N;
   double* n64 = g64 + 3 * N;
-  const bool need64 = !mixed || ((km & 2) && p.opts.periodic);
+  const bool need64 = (!mixed && !ff) || ((km & 2) && p.opts.periodic);
   if (need64) {
-    if ((km & 1) && !mixed) {
+    if ((km & 1) && !mixed && !ff) {
       k_perm_f64_cols<D><<<grid_for(N, B), B, 0, s>>>(N, nr, NR, T.perm, d_f, f64);
       ++p.launches;
     }
@@ -261,6 +340,48 @@ void perm_densities(const Plan& p, bool mixed, int km, int nr, int NR, const dou
   P.n64 = n64;
 }
 
+// FF inputs: rel_lo and the hi / lo split of the sorted densities
+FFParams ff_inputs(const Plan& p, int km, const double* d_f, const double* d_g, const double* d_n, char* ws,
+                   const NearParams& P, cudaStream_t s) {
+  const DeviceTree& T = p.tree;
+  const int64_t N = T.N;
+  const int B = 256;
+  float4* base = reinterpret_cast<float4*>(ws + ws_layout(p.opts, N).ff_off);
+  FFParams F{};
+  F.rel_lo = base;
+  F.f_hi = base + N;
+  F.f_lo = base + 2 * N;
+  F.g_hi = base + 3 * N;
+  F.g_lo = base + 4 * N;
+  F.n_hi = base + 5 * N;
+  F.n_lo = base + 6 * N;
+  if (T.n_tile > 0) {
+    k_rel_lo<3><<<grid_for(int64_t(T.n_tile) * 32, 256), 256, 0, s>>>(P, base);
+    ++p.launches;
+  }
+  if (km & 1) {
+    k_split_ff<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_f, nullptr, base + N, base + 2 * N);
+    ++p.launches;
+  }
+  if (km & 2) {
+    k_split_ff<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_g, nullptr, base + 3 * N, base + 4 * N);
+    ++p.launches;
+    k_split_ff<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_g, d_n, base + 5 * N, base + 6 * N);
+    ++p.launches;
+  }
+  const KernelTables& tb = p.tables;
+  auto c64 = [&](int id, int k) { return k < tb.n64[id] ? tb.p64[id][k] : 0.0; };
+  auto hi = [](double v) { return static_cast<float>(v); };
+  auto lo = [](double v) { return static_cast<float>(v - static_cast<double>(static_cast<float>(v))); };
+  for (int k = 0; k < kPolyCap; ++k) {
+    F.chi[0][k] = make_float2(hi(c64(P_GS, k)), hi(c64(P_HS, k)));
+    F.clo[0][k] = make_float2(lo(c64(P_GS, k)), lo(c64(P_HS, k)));
+    F.chi[1][k] = make_float2(hi(c64(P_PT, k)), hi(c64(P_QT, k)));
+    F.clo[1][k] = make_float2(lo(c64(P_PT, k)), lo(c64(P_QT, k)));
+  }
+  return F;
+}
+
 }  // namespace
 
 void launch_near(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u,
@@ -276,6 +397,7 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   const bool mixed = fp32_pairs(p.opts);
   const int km = (d_f ? 1 : 0) | (d_g ? 2 : 0);
   const bool grad = d_gradu != nullptr;
+  const bool ff = ff_pairs(p.opts) && !grad && d_u;
   if (grad && D != 3) throw Error{DMK_ERR_UNSUPPORTED, "the gradient is provided in 3D"};
   if (N == 0) return;
   const int B = 256;
@@ -291,8 +413,8 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   P.n_rhs = nr;
 
   char* ws = static_cast<char*>(workspace);
-  if (D == 3) perm_densities<3>(p, mixed, km, nr, NR, d_f, d_g, d_n, ws, P, s);
-  else perm_densities<2>(p, mixed, km, nr, NR, d_f, d_g, d_n, ws, P, s);
+  if (D == 3) perm_densities<3>(p, mixed, ff, km, nr, NR, d_f, d_g, d_n, ws, P, s);
+  else perm_densities<2>(p, mixed, ff, km, nr, NR, d_f, d_g, d_n, ws, P, s);
   DMK_CUDA_TRY(cudaGetLastError());
 
   const KernelTables& tb = p.tables;
@@ -314,7 +436,8 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     P.c32p[2][k] = make_float2(c32(P_DGS, k), c32(P_DHS, k));
   }
   if (T.n_tile > 0) {
-    dispatch(mixed, D, km, grad, nt, NR, P, s);
+    if (ff) dispatch_ff(km, nt, P, ff_inputs(p, km, d_f, d_g, d_n, ws, P, s), s);
+    else dispatch(mixed, D, km, grad, nt, NR, P, s);
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());
   }
@@ -346,13 +469,6 @@ int64_t count_useful_pairs(const Plan& p) {
   return static_cast<int64_t>(h);
 }
 
-size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N) {
-  const bool mixed = fp32_pairs(o);
-  const int NR = padded_rhs(o.n_rhs);
-  size_t b = 0;
-  if (mixed) b += std::max(3, NR) * N * sizeof(float4);
-  b += std::max(3 + 3 + 4, 3 * NR) * N * sizeof(double);
-  return b;
-}
+size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N) { return ws_layout(o, N).bytes; }
 
 }  // namespace dmk

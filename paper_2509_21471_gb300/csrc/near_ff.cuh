@@ -1,0 +1,323 @@
+// Float-float near-field kernel (3D): the MIXED path for eps below the FP32
+// floor of the pair terms.
+//
+// GB300 runs FP64 at about 1/74 of its FP32 FMA rate, so the tight-tolerance
+// pair terms are evaluated in float-float (FF) arithmetic: every quantity is an
+// unevaluated sum hi + lo of two floats (about 48 significant bits), built from
+// the error-free transformations two-sum (Knuth) and two-product by FMA
+// (exact product error fma(a, b, -ab)).  The formulas are those of the FP64
+// kernel (Sec. 5.2, Eqs. (res_stokeslet), (Soffdiag), (res_stresslet),
+// (T-offd) with the length-scale remark closing Sec. 5.2):
+//   S_R f     = [A f + C (x.f) x] / (8 pi),   A = 1/r + gS/nu,  C = (1/r + hS/nu)/r^2
+//   T_R:(g n) = [D (g (x.n) + x (g.n) + n (x.g)) + E x (x.g)(x.n)] / (8 pi),
+//               D = pT/(nu r^2),  E = -6 (1/r + qT/nu)/r^4
+// with gS, hS, pT, qT polynomials in t = 2 rho^2 - 1 whose FP64 coefficients
+// are split into FF pairs and evaluated two at a time by packed FP32x2 Horner.
+//
+// Inputs in FF: leaf-relative coordinates (rel + rel_lo, the FP32 residual of
+// the FP64 offset from the leaf centre), forces, strengths and orientations
+// (FP64 values split as hi + lo).  1/r is FP32 rsqrt refined by one Newton step
+// in FF.  Candidate pairs come from the FP32 test of the mixed kernel (on the hi
+// parts, margin 2^-12 nu^2); the cutoff r < nu is then decided on the FF r^2.
+//
+// Work decomposition: one warp per target tile.  Each surviving source tile is
+// staged in shared memory; each lane marks its candidate sources in a bit mask;
+// the candidate (target, source) pairs of the warp are written to a shared
+// queue (grouped by target) and evaluated 32 at a time by all lanes, so the
+// expensive FF pair evaluation runs on full warps whatever the geometry; each
+// lane then adds the results of its own target's pairs to its FF accumulator.
+#pragma once
+#include "near_kernel.cuh"
+
+namespace dmk {
+
+struct FFParams {
+  const float4* rel_lo;  // FP32 residual of the leaf-relative coordinates (sorted)
+  const float4* f_hi;    // sorted forces, hi / lo
+  const float4* f_lo;
+  const float4* g_hi;    // sorted stresslet strengths, hi / lo
+  const float4* g_lo;
+  const float4* n_hi;    // sorted orientations, hi / lo; .w = g.n hi / lo
+  const float4* n_lo;
+  float2 chi[2][kPolyCap];   // (gS, hS), (pT, qT): hi parts of the FP64 coefficients
+  float2 clo[2][kPolyCap];   // lo parts
+};
+
+// ------------------------------------------------------------ FF helpers
+// Round-to-nearest intrinsics throughout so that no operation is contracted.
+struct ff {
+  float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {   // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_scale(ff a, float s) {        // s a power of two: exact
+  return {__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)};
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ double ff_to_double(ff a) {
+  return static_cast<double>(a.hi) + static_cast<double>(a.lo);
+}
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// packed pair of FF numbers (two polynomials at once)
+struct ff2 {
+  float2 hi, lo;
+};
+
+// Horner for two polynomials in FF with packed FP32x2 operations; the running
+// value is kept unnormalised between steps (its lo part stays within a few
+// ulp of hi), normalised once at the end.
+template <int NT>
+__device__ __forceinline__ ff2 horner_ff2(const float2 (&chi)[kPolyCap], const float2 (&clo)[kPolyCap], ff t) {
+  const float2 th = make_float2(t.hi, t.hi), tl = make_float2(t.lo, t.lo);
+  float2 vh = chi[NT - 1], vl = clo[NT - 1];
+#pragma unroll
+  for (int k = NT - 2; k >= 0; --k) {
+    const float2 p = __fmul2_rn(vh, th);
+    float2 e = __ffma2_rn(vh, th, make_float2(-p.x, -p.y));
+    e = __ffma2_rn(vh, tl, e);
+    e = __ffma2_rn(vl, th, e);
+    const float2 c = chi[k];
+    const float2 s = __fadd2_rn(p, c);
+    const float2 bb = sub2(s, p);
+    const float2 err = __fadd2_rn(sub2(p, sub2(s, bb)), sub2(c, bb));
+    vh = s;
+    vl = __fadd2_rn(err, __fadd2_rn(e, clo[k]));
+  }
+  const ff a = fast_two_sum(vh.x, vl.x), b = fast_two_sum(vh.y, vl.y);
+  return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)};
+}
+
+// 1/sqrt(r2) in FF: FP32 rsqrt y, then y (1 + d/2) with d = 1 - r2 y^2 from an
+// FF product (relative error ~2^-44 from the one Newton step)
+__device__ __forceinline__ ff ff_rsqrt(ff r2) {
+  const float y = rsqrtf(r2.hi);
+  const float y2 = __fmul_rn(y, y);
+  const ff yy = {y2, fmaf(y, y, -y2)};
+  const ff q = ff_mul(r2, yy);
+  const float d = __fsub_rn(__fsub_rn(1.f, q.hi), q.lo);
+  return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), d));
+}
+
+// ------------------------------------------------------------------ kernel
+constexpr int kFFQueue = 128;   // candidate pairs evaluated per round (per warp)
+
+template <int KM, int NT>
+__global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearParams P,
+                                                 const __grid_constant__ FFParams F) {
+  constexpr int D = 3;
+  __shared__ float4 s_tst[4][4][8];                 // FP32 test rows (as in the mixed kernel)
+  __shared__ float4 s_ph[4][kTile], s_pl[4][kTile];  // source position in the target frame, FF
+  __shared__ float4 s_ah[4][kTile], s_al[4][kTile];  // Stokeslet force / stresslet strength, FF
+  __shared__ float4 s_nh[(KM & 2) ? 4 : 1][kTile], s_nl[(KM & 2) ? 4 : 1][kTile];   // orientation, .w = g.n
+  __shared__ float4 s_bh[(KM == 3) ? 4 : 1][kTile], s_bl[(KM == 3) ? 4 : 1][kTile];  // stresslet strength if both
+  __shared__ float4 s_th[4][kTile], s_tl[4][kTile];  // targets, FF
+  __shared__ uint16_t s_q[4][kFFQueue];              // queue: target lane << 5 | source slot
+  __shared__ float2 s_r[4][3][kFFQueue];             // per queued pair: contribution (hi, lo) x 3
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * 4 + wid;
+  if (tile >= P.n_tile) return;
+  const int B = P.tile_leaf[tile];
+  const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
+  const int LB = P.leaf_level[B];
+  int64_t cB[3] = {0, 0, 0};
+  leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
+  const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
+  const bool on = lane < nt;
+  const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float tt = on ? fmaf(xt.x, xt.x, fmaf(xt.y, xt.y, xt.z * xt.z)) : __int_as_float(0x7f800000);
+  s_th[wid][lane] = xt;
+  s_tl[wid][lane] = on ? F.rel_lo[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  float* const rowx = reinterpret_cast<float*>(s_tst[wid][0]);
+  float* const rowy = reinterpret_cast<float*>(s_tst[wid][1]);
+  float* const rowz = reinterpret_cast<float*>(s_tst[wid][2]);
+  float* const roww = reinterpret_cast<float*>(s_tst[wid][3]);
+  ff acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+
+  const int e1 = P.near_off[B + 1];
+  for (int e = P.near_off[B]; e < e1; ++e) {
+    const Entry E = make_entry<D>(P, e, LB, cB);
+    const float nu2 = E.nu2, nuinv = E.nuinv;
+    const float nu2inv = nuinv * nuinv;
+    const float nu2m = nu2 * (1.f + 0x1p-12f);
+    const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
+    for (int U = U0; U < U1; ++U) {
+      if (!tile_near(P, U, E, tlo, thi)) continue;
+      const int s0 = P.tile_start[U], ns = P.tile_count[U];
+      __syncwarp();
+      if (lane < ns) {
+        const int64_t si = s0 + lane;
+        const float4 r = P.rel[si], rl = F.rel_lo[si];
+        // source in the target leaf's frame: (rel + off) + rel_lo, off exact
+        const ff sx = two_sum(r.x, E.off[0]), sy = two_sum(r.y, E.off[1]), sz = two_sum(r.z, E.off[2]);
+        const ff px = fast_two_sum(sx.hi, __fadd_rn(sx.lo, rl.x));
+        const ff py = fast_two_sum(sy.hi, __fadd_rn(sy.lo, rl.y));
+        const ff pz = fast_two_sum(sz.hi, __fadd_rn(sz.lo, rl.z));
+        s_ph[wid][lane] = make_float4(px.hi, py.hi, pz.hi, 0.f);
+        s_pl[wid][lane] = make_float4(px.lo, py.lo, pz.lo, 0.f);
+        rowx[lane] = -2.f * px.hi;
+        rowy[lane] = -2.f * py.hi;
+        rowz[lane] = -2.f * pz.hi;
+        roww[lane] = fmaf(px.hi, px.hi, fmaf(py.hi, py.hi, pz.hi * pz.hi)) - nu2m;
+        if (KM & 1) {
+          s_ah[wid][lane] = F.f_hi[si];
+          s_al[wid][lane] = F.f_lo[si];
+        }
+        if (KM & 2) {
+          if (KM == 3) {
+            s_bh[(KM == 3) ? wid : 0][lane] = F.g_hi[si];
+            s_bl[(KM == 3) ? wid : 0][lane] = F.g_lo[si];
+          } else {
+            s_ah[wid][lane] = F.g_hi[si];
+            s_al[wid][lane] = F.g_lo[si];
+          }
+          s_nh[(KM & 2) ? wid : 0][lane] = F.n_hi[si];
+          s_nl[(KM & 2) ? wid : 0][lane] = F.n_lo[si];
+        }
+      } else {
+        rowx[lane] = rowy[lane] = rowz[lane] = 0.f;
+        roww[lane] = __int_as_float(0x7f800000);      // never a candidate
+      }
+      __syncwarp();
+      // candidates of this lane's target; the warp's list grouped by target
+      uint32_t bits = candidate_mask(s_tst[wid], xt, tt);
+      const int cnt = __popc(bits);
+      int off = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += v;
+      }
+      const int total = __shfl_sync(0xffffffffu, off, 31);
+      off -= cnt;                                       // exclusive prefix
+      for (int base = 0; base < total; base += kFFQueue) {
+        // queue the entries [base, base + kFFQueue) of the warp's list
+        {
+          uint32_t b = bits;
+          int i = off;
+          for (; b && i < base; ++i) b &= b - 1u;
+          for (; b && i < base + kFFQueue; ++i) {
+            const int j = __ffs(b) - 1;
+            b &= b - 1u;
+            s_q[wid][i - base] = static_cast<uint16_t>((lane << 5) | j);
+          }
+        }
+        __syncwarp();
+        const int n = min(kFFQueue, total - base);
+        for (int q0 = 0; q0 < n; q0 += 32) {
+          const int qi = q0 + lane;
+          if (qi >= n) continue;
+          const int ent = s_q[wid][qi];
+          const int tl = ent >> 5, j = ent & 31;
+          const float4 th = s_th[wid][tl], tlw = s_tl[wid][tl];
+          const float4 ph = s_ph[wid][j], pl = s_pl[wid][j];
+          ff dx = two_sum(th.x, -ph.x), dy = two_sum(th.y, -ph.y), dz = two_sum(th.z, -ph.z);
+          dx = fast_two_sum(dx.hi, __fadd_rn(dx.lo, __fsub_rn(tlw.x, pl.x)));
+          dy = fast_two_sum(dy.hi, __fadd_rn(dy.lo, __fsub_rn(tlw.y, pl.y)));
+          dz = fast_two_sum(dz.hi, __fadd_rn(dz.lo, __fsub_rn(tlw.z, pl.z)));
+          const ff r2 = ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+          float2 res[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+          const bool inside = (r2.hi < nu2 || (r2.hi == nu2 && r2.lo < 0.f)) && (r2.hi > 0.f);
+          if (inside) {
+            const ff rho2 = ff_scale(r2, nu2inv);
+            // t = 2 rho^2 - 1; the FP32 difference is not exact for rho^2 < 1/4
+            const ff t0 = two_sum(__fmul_rn(2.f, rho2.hi), -1.f);
+            const ff t = fast_two_sum(t0.hi, __fadd_rn(t0.lo, __fmul_rn(2.f, rho2.lo)));
+            const ff ri = ff_rsqrt(r2);
+            const ff ri2 = ff_mul(ri, ri);
+            const ff xv[3] = {dx, dy, dz};
+            ff out[3];
+            if (KM & 1) {
+              const ff2 gh = horner_ff2<NT>(F.chi[0], F.clo[0], t);
+              const ff A = ff_add(ri, ff_scale({gh.hi.x, gh.lo.x}, nuinv));
+              const ff C = ff_mul(ri2, ff_add(ri, ff_scale({gh.hi.y, gh.lo.y}, nuinv)));
+              const float4 fh = s_ah[wid][j], fl = s_al[wid][j];
+              const ff fv[3] = {{fh.x, fl.x}, {fh.y, fl.y}, {fh.z, fl.z}};
+              const ff xf = ff_add(ff_add(ff_mul(dx, fv[0]), ff_mul(dy, fv[1])), ff_mul(dz, fv[2]));
+              const ff Cx = ff_mul(C, xf);
+#pragma unroll
+              for (int a = 0; a < 3; ++a) out[a] = ff_add(ff_mul(A, fv[a]), ff_mul(Cx, xv[a]));
+            } else {
+              out[0] = out[1] = out[2] = {0.f, 0.f};
+            }
+            if (KM & 2) {
+              const ff2 pq = horner_ff2<NT>(F.chi[1], F.clo[1], t);
+              const float4 gh4 = (KM == 3) ? s_bh[(KM == 3) ? wid : 0][j] : s_ah[wid][j];
+              const float4 gl4 = (KM == 3) ? s_bl[(KM == 3) ? wid : 0][j] : s_al[wid][j];
+              const float4 nh4 = s_nh[(KM & 2) ? wid : 0][j], nl4 = s_nl[(KM & 2) ? wid : 0][j];
+              const ff gv[3] = {{gh4.x, gl4.x}, {gh4.y, gl4.y}, {gh4.z, gl4.z}};
+              const ff nv[3] = {{nh4.x, nl4.x}, {nh4.y, nl4.y}, {nh4.z, nl4.z}};
+              const ff gn = {nh4.w, nl4.w};
+              const ff xn = ff_add(ff_add(ff_mul(dx, nv[0]), ff_mul(dy, nv[1])), ff_mul(dz, nv[2]));
+              const ff xg = ff_add(ff_add(ff_mul(dx, gv[0]), ff_mul(dy, gv[1])), ff_mul(dz, gv[2]));
+              const ff Dc = ff_mul(ff_scale({pq.hi.x, pq.lo.x}, nuinv), ri2);
+              const ff Ec = ff_scale(ff_mul(ff_mul(ri2, ri2), ff_add(ri, ff_scale({pq.hi.y, pq.lo.y}, nuinv))), -6.f);
+              // E (x.g)(x.n) + D (g.n): coefficient of x
+              const ff Ex = ff_add(ff_mul(Ec, ff_mul(xg, xn)), ff_mul(Dc, gn));
+#pragma unroll
+              for (int a = 0; a < 3; ++a) {
+                const ff sym = ff_add(ff_mul(gv[a], xn), ff_mul(nv[a], xg));
+                out[a] = ff_add(out[a], ff_add(ff_mul(Dc, sym), ff_mul(Ex, xv[a])));
+              }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) res[a] = make_float2(out[a].hi, out[a].lo);
+          }
+#pragma unroll
+          for (int a = 0; a < 3; ++a) s_r[wid][a][qi] = res[a];
+        }
+        __syncwarp();
+        // this lane's own entries of the round
+        const int i0 = max(off, base), i1 = min(off + cnt, base + kFFQueue);
+        for (int i = i0; i < i1; ++i) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            const float2 v = s_r[wid][a][i - base];
+            acc[a] = ff_add(acc[a], {v.x, v.y});
+          }
+        }
+        __syncwarp();
+      }
+    }
+  }
+  if (!on) return;
+  const int64_t o = P.perm[t0 + lane];
+  const double sc = self_coeff<D>(P, LB);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    double v = ff_to_double(acc[a]) * kInv8Pi;
+    const int64_t q = o * D + a;
+    if (KM & 1) v += sc * P.f_orig[q];
+    P.u[q] = v;
+  }
+}
+
+template <int KM, int NT>
+void run_near_ff(const NearParams& P, const FFParams& F, cudaStream_t s) {
+  k_near_ff<KM, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, F);
+}
+
+#define DMK_FOR_EACH_FF(M, NT) M(1, NT) M(2, NT) M(3, NT)
+
+}  // namespace dmk

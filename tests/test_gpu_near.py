@@ -4,8 +4,8 @@ Tolerances: the FP64 path evaluates the same formulas as the oracle, with
 polynomial kernel tables fitted to ~1e-15 relative and a different summation
 order, so relative l2 <= 1e-12.  The mixed path must meet 10 * eps: FP32
 pair terms with two-sum accumulation for eps >= 2e-7 (their error, ~1e-7 to
-2e-6 in l2, is set by FP32 rounding of the pair terms), FP64 pair terms after
-an FP32 candidate test below that.
+2e-6 in l2, is set by FP32 rounding of the pair terms), float-float pair terms
+below that (one force column; the gradient takes FP64 pair terms).
 """
 import zlib
 
@@ -64,6 +64,9 @@ CASES = [
     ("clustered-periodic-stresslet", 1500, True, True, 2, 24, 1e-8),
     ("uniform-1000-eps1e-10", 1000, False, False, 1, 40, 1e-10),
     ("uniform-700-eps1e-3", 700, False, False, 3, 30, 1e-3),
+    ("clustered-2000-both-eps1e-9", 2000, True, False, 3, 32, 1e-9),
+    ("periodic-1500-both-eps1e-8", 1500, False, True, 3, 40, 1e-8),
+    ("uniform-800-eps1e-12", 800, False, False, 1, 30, 1e-12),
 ]
 
 
