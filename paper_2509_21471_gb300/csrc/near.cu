@@ -12,7 +12,8 @@ namespace dmk {
 #define DMK_EXT_D_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_EXT_D, NT) DMK_FOR_EACH_VARIANT_2D(DMK_EXT_D, NT)
 DMK_NT_MIXED(DMK_EXT_M_NT)
 DMK_NT_FP64(DMK_EXT_D_NT)
-#define DMK_EXT_F(KM, NT) extern template void run_near_ff<KM, NT>(const NearParams&, const FFParams&, cudaStream_t);
+#define DMK_EXT_F(KM, GR, NT) \
+  extern template void run_near_ff<KM, GR, NT>(const NearParams&, const FFParams&, cudaStream_t);
 #define DMK_EXT_F_NT(NT) DMK_FOR_EACH_FF(DMK_EXT_F, NT)
 DMK_NT_FP64(DMK_EXT_F_NT)
 
@@ -209,8 +210,8 @@ __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned lo
 // requested tolerance: its relative l2 error is set by FP32 rounding of the
 // pair terms (about 1e-7 to 2e-6 on clustered points), so below eps = 2e-7 the
 // pair terms are taken in FP64 (the FP32 candidate filter is kept).
-// There (3D, one force column) the pair terms are evaluated in float-float
-// (k_near_ff), which GB300 runs far faster than FP64; the gradient, 2D and
+// There (3D, one force column) the pair terms, and the gradient, are evaluated
+// in float-float (k_near_ff), which GB300 runs far faster than FP64; 2D and
 // several force columns take FP64 pair terms.
 constexpr double kFp32PairMinEps = 2e-7;
 bool fp32_pairs(const dmk_stokes_opts_t& o) {
@@ -257,11 +258,11 @@ void dispatch(bool mixed, int dim, int km, bool grad, int nt, int nr, const Near
   throw Error{DMK_ERR_UNSUPPORTED, "no compiled near-field kernel for this configuration"};
 }
 
-void dispatch_ff(int km, int nt, const NearParams& P, const FFParams& F, cudaStream_t s) {
-#define DMK_CASE_F(KM, NT)                  \
-  if (km == KM && nt == NT) {               \
-    run_near_ff<KM, NT>(P, F, s);           \
-    return;                                 \
+void dispatch_ff(int km, bool grad, int nt, const NearParams& P, const FFParams& F, cudaStream_t s) {
+#define DMK_CASE_F(KM, GR, NT)                          \
+  if (km == KM && grad == GR && nt == NT) {             \
+    run_near_ff<KM, GR, NT>(P, F, s);                   \
+    return;                                             \
   }
 #define DMK_CASE_F_NT(NT) DMK_FOR_EACH_FF(DMK_CASE_F, NT)
   DMK_NT_FP64(DMK_CASE_F_NT)
@@ -373,12 +374,12 @@ FFParams ff_inputs(const Plan& p, int km, const double* d_f, const double* d_g, 
   auto c64 = [&](int id, int k) { return k < tb.n64[id] ? tb.p64[id][k] : 0.0; };
   auto hi = [](double v) { return static_cast<float>(v); };
   auto lo = [](double v) { return static_cast<float>(v - static_cast<double>(static_cast<float>(v))); };
-  for (int k = 0; k < kPolyCap; ++k) {
-    F.chi[0][k] = make_float2(hi(c64(P_GS, k)), hi(c64(P_HS, k)));
-    F.clo[0][k] = make_float2(lo(c64(P_GS, k)), lo(c64(P_HS, k)));
-    F.chi[1][k] = make_float2(hi(c64(P_PT, k)), hi(c64(P_QT, k)));
-    F.clo[1][k] = make_float2(lo(c64(P_PT, k)), lo(c64(P_QT, k)));
-  }
+  const int pairs[3][2] = {{P_GS, P_HS}, {P_PT, P_QT}, {P_DGS, P_DHS}};
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < kPolyCap; ++k) {
+      F.chi[q][k] = make_float2(hi(c64(pairs[q][0], k)), hi(c64(pairs[q][1], k)));
+      F.clo[q][k] = make_float2(lo(c64(pairs[q][0], k)), lo(c64(pairs[q][1], k)));
+    }
   return F;
 }
 
@@ -397,7 +398,7 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   const bool mixed = fp32_pairs(p.opts);
   const int km = (d_f ? 1 : 0) | (d_g ? 2 : 0);
   const bool grad = d_gradu != nullptr;
-  const bool ff = ff_pairs(p.opts) && !grad && d_u;
+  const bool ff = ff_pairs(p.opts) && (d_u || grad);
   if (grad && D != 3) throw Error{DMK_ERR_UNSUPPORTED, "the gradient is provided in 3D"};
   if (N == 0) return;
   const int B = 256;
@@ -436,7 +437,7 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     P.c32p[2][k] = make_float2(c32(P_DGS, k), c32(P_DHS, k));
   }
   if (T.n_tile > 0) {
-    if (ff) dispatch_ff(km, nt, P, ff_inputs(p, km, d_f, d_g, d_n, ws, P, s), s);
+    if (ff) dispatch_ff(km, grad, nt, P, ff_inputs(p, km, d_f, d_g, d_n, ws, P, s), s);
     else dispatch(mixed, D, km, grad, nt, NR, P, s);
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());

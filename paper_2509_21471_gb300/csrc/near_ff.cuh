@@ -39,8 +39,8 @@ struct FFParams {
   const float4* g_lo;
   const float4* n_hi;    // sorted orientations, hi / lo; .w = g.n hi / lo
   const float4* n_lo;
-  float2 chi[2][kPolyCap];   // (gS, hS), (pT, qT): hi parts of the FP64 coefficients
-  float2 clo[2][kPolyCap];   // lo parts
+  float2 chi[3][kPolyCap];   // (gS, hS), (pT, qT), (gS', hS'): hi parts of the FP64 coefficients
+  float2 clo[3][kPolyCap];   // lo parts
 };
 
 // ------------------------------------------------------------ FF helpers
@@ -72,6 +72,12 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
 }
 __device__ __forceinline__ ff ff_scale(ff a, float s) {        // s a power of two: exact
   return {__fmul_rn(a.hi, s), __fmul_rn(a.lo, s)};
+}
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {         // b any float
+  const float p = __fmul_rn(a.hi, b);
+  float e = fmaf(a.hi, b, -p);
+  e = fmaf(a.lo, b, e);
+  return fast_two_sum(p, e);
 }
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ double ff_to_double(ff a) {
@@ -121,12 +127,17 @@ __device__ __forceinline__ ff ff_rsqrt(ff r2) {
 }
 
 // ------------------------------------------------------------------ kernel
-constexpr int kFFQueue = 128;   // candidate pairs evaluated per round (per warp)
-
-template <int KM, int NT>
+// GRAD (Stokeslet only) adds the velocity gradient, the derivative of
+// Eq. (res_stokeslet) with the tree held fixed:
+//   d_m (S_R f)_j = A1 x_m f_j + C1 x_m x_j (x.f) + C (delta_jm (x.f) + x_j f_m)
+//   A1 = -1/r^3 + 2 gS'/nu^3,  C1 = -3/r^5 + (2 hS'/nu^3 - 2 hS/(nu r^2))/r^2.
+template <int KM, bool GRAD, int NT>
 __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearParams P,
                                                  const __grid_constant__ FFParams F) {
+  static_assert(!GRAD || KM == 1, "the gradient kernel is the Stokeslet's");
   constexpr int D = 3;
+  constexpr int NO = GRAD ? 12 : 3;                  // outputs per pair: u (3) [+ grad u (9)]
+  constexpr int kFFQueue = GRAD ? 64 : 128;          // candidate pairs evaluated per round (per warp)
   __shared__ float4 s_tst[4][4][8];                 // FP32 test rows (as in the mixed kernel)
   __shared__ float4 s_ph[4][kTile], s_pl[4][kTile];  // source position in the target frame, FF
   __shared__ float4 s_ah[4][kTile], s_al[4][kTile];  // Stokeslet force / stresslet strength, FF
@@ -134,7 +145,7 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
   __shared__ float4 s_bh[(KM == 3) ? 4 : 1][kTile], s_bl[(KM == 3) ? 4 : 1][kTile];  // stresslet strength if both
   __shared__ float4 s_th[4][kTile], s_tl[4][kTile];  // targets, FF
   __shared__ uint16_t s_q[4][kFFQueue];              // queue: target lane << 5 | source slot
-  __shared__ float2 s_r[4][3][kFFQueue];             // per queued pair: contribution (hi, lo) x 3
+  __shared__ float2 s_r[4][NO][kFFQueue];            // per queued pair: contributions (hi, lo)
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x * 4 + wid;
   if (tile >= P.n_tile) return;
@@ -153,7 +164,9 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
   float* const rowy = reinterpret_cast<float*>(s_tst[wid][1]);
   float* const rowz = reinterpret_cast<float*>(s_tst[wid][2]);
   float* const roww = reinterpret_cast<float*>(s_tst[wid][3]);
-  ff acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  ff acc[NO];
+#pragma unroll
+  for (int a = 0; a < NO; ++a) acc[a] = {0.f, 0.f};
 
   const int e1 = P.near_off[B + 1];
   for (int e = P.near_off[B]; e < e1; ++e) {
@@ -237,7 +250,9 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
           dy = fast_two_sum(dy.hi, __fadd_rn(dy.lo, __fsub_rn(tlw.y, pl.y)));
           dz = fast_two_sum(dz.hi, __fadd_rn(dz.lo, __fsub_rn(tlw.z, pl.z)));
           const ff r2 = ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
-          float2 res[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+          float2 res[NO];
+#pragma unroll
+          for (int a = 0; a < NO; ++a) res[a] = make_float2(0.f, 0.f);
           const bool inside = (r2.hi < nu2 || (r2.hi == nu2 && r2.lo < 0.f)) && (r2.hi > 0.f);
           if (inside) {
             const ff rho2 = ff_scale(r2, nu2inv);
@@ -247,7 +262,7 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
             const ff ri = ff_rsqrt(r2);
             const ff ri2 = ff_mul(ri, ri);
             const ff xv[3] = {dx, dy, dz};
-            ff out[3];
+            ff out[NO];
             if (KM & 1) {
               const ff2 gh = horner_ff2<NT>(F.chi[0], F.clo[0], t);
               const ff A = ff_add(ri, ff_scale({gh.hi.x, gh.lo.x}, nuinv));
@@ -258,6 +273,27 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
               const ff Cx = ff_mul(C, xf);
 #pragma unroll
               for (int a = 0; a < 3; ++a) out[a] = ff_add(ff_mul(A, fv[a]), ff_mul(Cx, xv[a]));
+              if (GRAD) {
+                const ff2 dgh = horner_ff2<NT>(F.chi[2], F.clo[2], t);
+                const float nu3i = nuinv * nuinv * nuinv;
+                const ff ri3 = ff_mul(ri2, ri);
+                const ff A1 = ff_add(ff_scale({dgh.hi.x, dgh.lo.x}, 2.f * nu3i), ff_neg(ri3));
+                const ff hnr = ff_mul(ff_scale({gh.hi.y, gh.lo.y}, 2.f * nuinv), ri2);
+                const ff C1 = ff_add(ff_mul_f(ff_mul(ri3, ri2), -3.f),
+                                     ff_mul(ri2, ff_add(ff_scale({dgh.hi.y, dgh.lo.y}, 2.f * nu3i), ff_neg(hnr))));
+                const ff Cxf = ff_mul(C, xf);
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj) {
+                  const ff a1 = ff_add(ff_mul(A1, fv[jj]), ff_mul(ff_mul(C1, xv[jj]), xf));
+                  const ff cx = ff_mul(C, xv[jj]);
+#pragma unroll
+                  for (int mm = 0; mm < 3; ++mm) {
+                    ff v = ff_add(ff_mul(a1, xv[mm]), ff_mul(cx, fv[mm]));
+                    if (jj == mm) v = ff_add(v, Cxf);
+                    out[3 + jj * 3 + mm] = v;
+                  }
+                }
+              }
             } else {
               out[0] = out[1] = out[2] = {0.f, 0.f};
             }
@@ -272,7 +308,7 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
               const ff xn = ff_add(ff_add(ff_mul(dx, nv[0]), ff_mul(dy, nv[1])), ff_mul(dz, nv[2]));
               const ff xg = ff_add(ff_add(ff_mul(dx, gv[0]), ff_mul(dy, gv[1])), ff_mul(dz, gv[2]));
               const ff Dc = ff_mul(ff_scale({pq.hi.x, pq.lo.x}, nuinv), ri2);
-              const ff Ec = ff_scale(ff_mul(ff_mul(ri2, ri2), ff_add(ri, ff_scale({pq.hi.y, pq.lo.y}, nuinv))), -6.f);
+              const ff Ec = ff_mul_f(ff_mul(ff_mul(ri2, ri2), ff_add(ri, ff_scale({pq.hi.y, pq.lo.y}, nuinv))), -6.f);
               // E (x.g)(x.n) + D (g.n): coefficient of x
               const ff Ex = ff_add(ff_mul(Ec, ff_mul(xg, xn)), ff_mul(Dc, gn));
 #pragma unroll
@@ -282,17 +318,17 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
               }
             }
 #pragma unroll
-            for (int a = 0; a < 3; ++a) res[a] = make_float2(out[a].hi, out[a].lo);
+            for (int a = 0; a < NO; ++a) res[a] = make_float2(out[a].hi, out[a].lo);
           }
 #pragma unroll
-          for (int a = 0; a < 3; ++a) s_r[wid][a][qi] = res[a];
+          for (int a = 0; a < NO; ++a) s_r[wid][a][qi] = res[a];
         }
         __syncwarp();
         // this lane's own entries of the round
         const int i0 = max(off, base), i1 = min(off + cnt, base + kFFQueue);
         for (int i = i0; i < i1; ++i) {
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
+          for (int a = 0; a < NO; ++a) {
             const float2 v = s_r[wid][a][i - base];
             acc[a] = ff_add(acc[a], {v.x, v.y});
           }
@@ -304,20 +340,26 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
   if (!on) return;
   const int64_t o = P.perm[t0 + lane];
   const double sc = self_coeff<D>(P, LB);
+  if (P.u) {
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    double v = ff_to_double(acc[a]) * kInv8Pi;
-    const int64_t q = o * D + a;
-    if (KM & 1) v += sc * P.f_orig[q];
-    P.u[q] = v;
+    for (int a = 0; a < D; ++a) {
+      double v = ff_to_double(acc[a]) * kInv8Pi;
+      const int64_t q = o * D + a;
+      if (KM & 1) v += sc * P.f_orig[q];
+      P.u[q] = v;
+    }
+  }
+  if (GRAD) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) P.gradu[o * 9 + k] = ff_to_double(acc[3 + k]) * kInv8Pi;
   }
 }
 
-template <int KM, int NT>
+template <int KM, bool GRAD, int NT>
 void run_near_ff(const NearParams& P, const FFParams& F, cudaStream_t s) {
-  k_near_ff<KM, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, F);
+  k_near_ff<KM, GRAD, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, F);
 }
 
-#define DMK_FOR_EACH_FF(M, NT) M(1, NT) M(2, NT) M(3, NT)
+#define DMK_FOR_EACH_FF(M, NT) M(1, false, NT) M(2, false, NT) M(3, false, NT) M(1, true, NT)
 
 }  // namespace dmk

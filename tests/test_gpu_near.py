@@ -67,6 +67,8 @@ CASES = [
     ("clustered-2000-both-eps1e-9", 2000, True, False, 3, 32, 1e-9),
     ("periodic-1500-both-eps1e-8", 1500, False, True, 3, 40, 1e-8),
     ("uniform-800-eps1e-12", 800, False, False, 1, 30, 1e-12),
+    ("clustered-1200-both-eps1e-12", 1200, True, False, 3, 30, 1e-12),
+    ("periodic-1000-stresslet-eps1e-11", 1000, False, True, 2, 30, 1e-11),
 ]
 
 
@@ -93,9 +95,12 @@ def test_tree_and_near_parity(dmk, name, N, clustered, periodic, kernels, ns, ep
     p32.close()
 
 
-def test_gradient_parity(dmk):
+@pytest.mark.parametrize("eps", [1e-6, 1e-8, 1e-10])
+def test_gradient_parity(dmk, eps):
+    """FP64 and MIXED velocity gradients against the oracle's derivative of the
+    residual Stokeslet (MIXED: FP32 pair terms at 1e-6, float-float below)."""
     rng = np.random.default_rng(77)
-    N, ns, eps = 1200, 40, 1e-6
+    N, ns = 1200, 40
     x = wl.uniform_points(rng, N, 3)
     f = wl.forces(rng, N, 3)
     tr = Tree(x, ns)
