@@ -12,8 +12,8 @@ namespace dmk {
 #define DMK_EXT_D_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_EXT_D, NT) DMK_FOR_EACH_VARIANT_2D(DMK_EXT_D, NT)
 DMK_NT_MIXED(DMK_EXT_M_NT)
 DMK_NT_FP64(DMK_EXT_D_NT)
-#define DMK_EXT_F(KM, GR, NT) \
-  extern template void run_near_ff<KM, GR, NT>(const NearParams&, const FFParams&, cudaStream_t);
+#define DMK_EXT_F(D, KM, GR, NT) \
+  extern template void run_near_ff<D, KM, GR, NT>(const NearParams&, const FFParams&, cudaStream_t);
 #define DMK_EXT_F_NT(NT) DMK_FOR_EACH_FF(DMK_EXT_F, NT)
 DMK_NT_FP64(DMK_EXT_F_NT)
 
@@ -137,21 +137,22 @@ __global__ void k_rel_lo(const __grid_constant__ NearParams P, float4* __restric
   out[i] = make_float4(v[0], v[1], v[2], 0.f);
 }
 
-// sorted FF split of a [N][3] FP64 array (hi = rounded value, lo = rounded
-// remainder); with n != nullptr, .w holds the split of g.n (g = in)
+// sorted FF split of a [N][D] FP64 array (hi = rounded value, lo = rounded
+// remainder; z = 0 in 2D); with n != nullptr, .w holds the split of g.n (g = in)
+template <int D>
 __global__ void k_split_ff(int64_t N, const int32_t* __restrict__ perm, const double* __restrict__ in,
                            const double* __restrict__ n, float4* __restrict__ hi, float4* __restrict__ lo) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int64_t o = perm[i];
   const double* src = n ? n : in;
-  float h[4], l[4];
+  float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
   double gn = 0.0;
-  for (int a = 0; a < 3; ++a) {
-    const double v = src[o * 3 + a];
+  for (int a = 0; a < D; ++a) {
+    const double v = src[o * D + a];
     h[a] = __double2float_rn(v);
     l[a] = __double2float_rn(v - static_cast<double>(h[a]));
-    if (n) gn += in[o * 3 + a] * n[o * 3 + a];
+    if (n) gn += in[o * D + a] * n[o * D + a];
   }
   h[3] = __double2float_rn(gn);
   l[3] = __double2float_rn(gn - static_cast<double>(h[3]));
@@ -210,15 +211,15 @@ __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned lo
 // requested tolerance: its relative l2 error is set by FP32 rounding of the
 // pair terms (about 1e-7 to 2e-6 on clustered points), so below eps = 2e-7 the
 // pair terms are taken in FP64 (the FP32 candidate filter is kept).
-// There (3D, one force column) the pair terms, and the gradient, are evaluated
-// in float-float (k_near_ff), which GB300 runs far faster than FP64; 2D and
-// several force columns take FP64 pair terms.
+// There (one force column) the pair terms, and the gradient, are evaluated in
+// float-float (k_near_ff), which GB300 runs far faster than FP64; several
+// force columns take FP64 pair terms.
 constexpr double kFp32PairMinEps = 2e-7;
 bool fp32_pairs(const dmk_stokes_opts_t& o) {
   return o.precision == DMK_PRECISION_MIXED && o.eps >= kFp32PairMinEps;
 }
 bool ff_pairs(const dmk_stokes_opts_t& o) {
-  return o.precision == DMK_PRECISION_MIXED && o.eps < kFp32PairMinEps && o.dim == 3 && o.n_rhs == 1;
+  return o.precision == DMK_PRECISION_MIXED && o.eps < kFp32PairMinEps && o.n_rhs == 1;
 }
 
 // workspace: [FP32 sorted densities (fp32 pairs)] [FP64 sorted densities] [FF split densities]
@@ -258,11 +259,11 @@ void dispatch(bool mixed, int dim, int km, bool grad, int nt, int nr, const Near
   throw Error{DMK_ERR_UNSUPPORTED, "no compiled near-field kernel for this configuration"};
 }
 
-void dispatch_ff(int km, bool grad, int nt, const NearParams& P, const FFParams& F, cudaStream_t s) {
-#define DMK_CASE_F(KM, GR, NT)                          \
-  if (km == KM && grad == GR && nt == NT) {             \
-    run_near_ff<KM, GR, NT>(P, F, s);                   \
-    return;                                             \
+void dispatch_ff(int dim, int km, bool grad, int nt, const NearParams& P, const FFParams& F, cudaStream_t s) {
+#define DMK_CASE_F(D, KM, GR, NT)                                 \
+  if (dim == D && km == KM && grad == GR && nt == NT) {           \
+    run_near_ff<D, KM, GR, NT>(P, F, s);                          \
+    return;                                                       \
   }
 #define DMK_CASE_F_NT(NT) DMK_FOR_EACH_FF(DMK_CASE_F, NT)
   DMK_NT_FP64(DMK_CASE_F_NT)
@@ -356,19 +357,27 @@ FFParams ff_inputs(const Plan& p, int km, const double* d_f, const double* d_g, 
   F.g_lo = base + 4 * N;
   F.n_hi = base + 5 * N;
   F.n_lo = base + 6 * N;
+  const bool d3 = p.opts.dim == 3;
+  const unsigned gt = grid_for(int64_t(T.n_tile) * 32, 256), gp = grid_for(N, B);
   if (T.n_tile > 0) {
-    k_rel_lo<3><<<grid_for(int64_t(T.n_tile) * 32, 256), 256, 0, s>>>(P, base);
+    if (d3) k_rel_lo<3><<<gt, 256, 0, s>>>(P, base);
+    else k_rel_lo<2><<<gt, 256, 0, s>>>(P, base);
     ++p.launches;
   }
   if (km & 1) {
-    k_split_ff<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_f, nullptr, base + N, base + 2 * N);
+    if (d3) k_split_ff<3><<<gp, B, 0, s>>>(N, T.perm, d_f, nullptr, base + N, base + 2 * N);
+    else k_split_ff<2><<<gp, B, 0, s>>>(N, T.perm, d_f, nullptr, base + N, base + 2 * N);
     ++p.launches;
   }
   if (km & 2) {
-    k_split_ff<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_g, nullptr, base + 3 * N, base + 4 * N);
-    ++p.launches;
-    k_split_ff<<<grid_for(N, B), B, 0, s>>>(N, T.perm, d_g, d_n, base + 5 * N, base + 6 * N);
-    ++p.launches;
+    if (d3) {
+      k_split_ff<3><<<gp, B, 0, s>>>(N, T.perm, d_g, nullptr, base + 3 * N, base + 4 * N);
+      k_split_ff<3><<<gp, B, 0, s>>>(N, T.perm, d_g, d_n, base + 5 * N, base + 6 * N);
+    } else {
+      k_split_ff<2><<<gp, B, 0, s>>>(N, T.perm, d_g, nullptr, base + 3 * N, base + 4 * N);
+      k_split_ff<2><<<gp, B, 0, s>>>(N, T.perm, d_g, d_n, base + 5 * N, base + 6 * N);
+    }
+    p.launches += 2;
   }
   const KernelTables& tb = p.tables;
   auto c64 = [&](int id, int k) { return k < tb.n64[id] ? tb.p64[id][k] : 0.0; };
@@ -437,7 +446,7 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     P.c32p[2][k] = make_float2(c32(P_DGS, k), c32(P_DHS, k));
   }
   if (T.n_tile > 0) {
-    if (ff) dispatch_ff(km, grad, nt, P, ff_inputs(p, km, d_f, d_g, d_n, ws, P, s), s);
+    if (ff) dispatch_ff(D, km, grad, nt, P, ff_inputs(p, km, d_f, d_g, d_n, ws, P, s), s);
     else dispatch(mixed, D, km, grad, nt, NR, P, s);
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());

@@ -1,5 +1,5 @@
-// Float-float near-field kernel (3D): the MIXED path for eps below the FP32
-// floor of the pair terms.
+// Float-float near-field kernel (2D and 3D): the MIXED path for eps below the
+// FP32 floor of the pair terms.
 //
 // GB300 runs FP64 at about 1/74 of its FP32 FMA rate, so the tight-tolerance
 // pair terms are evaluated in float-float (FF) arithmetic: every quantity is an
@@ -13,6 +13,10 @@
 //               D = pT/(nu r^2),  E = -6 (1/r + qT/nu)/r^4
 // with gS, hS, pT, qT polynomials in t = 2 rho^2 - 1 whose FP64 coefficients
 // are split into FF pairs and evaluated two at a time by packed FP32x2 Horner.
+// In 2D (App. B functions m_d, m_o, m_td, m_to in the same tables):
+//   A = -log rho^2 - m_d,  C = 2/r^2 - m_o/nu^2,  D = -m_td/nu^2,
+//   E = -8/r^4 + 6 m_to/nu^4,
+// with log rho^2 in FF by argument reduction and the atanh series.
 //
 // Inputs in FF: leaf-relative coordinates (rel + rel_lo, the FP32 residual of
 // the FP64 offset from the leaf centre), forces, strengths and orientations
@@ -126,17 +130,60 @@ __device__ __forceinline__ ff ff_rsqrt(ff r2) {
   return fast_two_sum(y, __fmul_rn(__fmul_rn(0.5f, y), d));
 }
 
+// 1/r2 in FF: FP32 reciprocal y, then y (1 + d) with d = 1 - r2 y (one Newton step)
+__device__ __forceinline__ ff ff_rcp(ff r2) {
+  const float y = __frcp_rn(r2.hi);
+  const ff q = ff_mul_f(r2, y);
+  const float d = __fsub_rn(__fsub_rn(1.f, q.hi), q.lo);
+  return fast_two_sum(y, __fmul_rn(y, d));
+}
+
+// log(x) in FF for 0 < x (normalised FF): x = 2^e m with m in [sqrt(1/2),
+// sqrt(2)); log m = 2 atanh(s), s = (m - 1)/(m + 1), |s| < 0.172, summed as
+// 2 s sum_k s^(2k)/(2k+1) (terms k >= 4 in FP32: they are below 1e-7 of the
+// sum), plus e log 2 with log 2 in FF.
+__device__ __forceinline__ ff ff_log(ff x) {
+  int e;
+  float m0 = frexpf(x.hi, &e);                          // x.hi = m0 2^e, m0 in [1/2, 1)
+  if (m0 < 0.70710678f) --e;
+  const float sc = ldexpf(1.f, -e);                      // exact
+  const ff m = {__fmul_rn(x.hi, sc), __fmul_rn(x.lo, sc)};
+  const ff num = fast_two_sum(__fsub_rn(m.hi, 1.f), m.lo);    // m.hi - 1 exact (Sterbenz)
+  const ff den = ff_add(m, {1.f, 0.f});
+  const float q1 = __fdiv_rn(num.hi, den.hi);
+  const ff rr = ff_add(num, ff_neg(ff_mul_f(den, q1)));
+  const ff sv = fast_two_sum(q1, __fdiv_rn(rr.hi, den.hi));
+  const ff z = ff_mul(sv, sv);
+  // FP32 tail: sum_{k>=4} z^(k-4)/(2k+1), k = 4..10
+  float tail = 1.f / 21.f;
+  tail = fmaf(tail, z.hi, 1.f / 19.f);
+  tail = fmaf(tail, z.hi, 1.f / 17.f);
+  tail = fmaf(tail, z.hi, 1.f / 15.f);
+  tail = fmaf(tail, z.hi, 1.f / 13.f);
+  tail = fmaf(tail, z.hi, 1.f / 11.f);
+  tail = fmaf(tail, z.hi, 1.f / 9.f);
+  // FF steps k = 3, 2, 1, 0
+  constexpr double c7 = 1.0 / 7.0, c5 = 1.0 / 5.0, c3 = 1.0 / 3.0;
+  ff v = {tail, 0.f};
+  v = ff_add(ff_mul(v, z), {static_cast<float>(c7), static_cast<float>(c7 - static_cast<double>(static_cast<float>(c7)))});
+  v = ff_add(ff_mul(v, z), {static_cast<float>(c5), static_cast<float>(c5 - static_cast<double>(static_cast<float>(c5)))});
+  v = ff_add(ff_mul(v, z), {static_cast<float>(c3), static_cast<float>(c3 - static_cast<double>(static_cast<float>(c3)))});
+  v = ff_add(ff_mul(v, z), {1.f, 0.f});
+  constexpr double ln2 = 0.6931471805599453094;
+  const ff l2 = {static_cast<float>(ln2), static_cast<float>(ln2 - static_cast<double>(static_cast<float>(ln2)))};
+  return ff_add(ff_scale(ff_mul(sv, v), 2.f), ff_mul_f(l2, static_cast<float>(e)));
+}
+
 // ------------------------------------------------------------------ kernel
 // GRAD (Stokeslet only) adds the velocity gradient, the derivative of
 // Eq. (res_stokeslet) with the tree held fixed:
 //   d_m (S_R f)_j = A1 x_m f_j + C1 x_m x_j (x.f) + C (delta_jm (x.f) + x_j f_m)
 //   A1 = -1/r^3 + 2 gS'/nu^3,  C1 = -3/r^5 + (2 hS'/nu^3 - 2 hS/(nu r^2))/r^2.
-template <int KM, bool GRAD, int NT>
+template <int D, int KM, bool GRAD, int NT>
 __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearParams P,
                                                  const __grid_constant__ FFParams F) {
-  static_assert(!GRAD || KM == 1, "the gradient kernel is the Stokeslet's");
-  constexpr int D = 3;
-  constexpr int NO = GRAD ? 12 : 3;                  // outputs per pair: u (3) [+ grad u (9)]
+  static_assert(!GRAD || (KM == 1 && D == 3), "the gradient kernel is the 3D Stokeslet's");
+  constexpr int NO = GRAD ? 12 : D;                  // outputs per pair: u (D) [+ grad u (9)]
   constexpr int kFFQueue = GRAD ? 64 : 128;          // candidate pairs evaluated per round (per warp)
   __shared__ float4 s_tst[4][4][8];                 // FP32 test rows (as in the mixed kernel)
   __shared__ float4 s_ph[4][kTile], s_pl[4][kTile];  // source position in the target frame, FF
@@ -245,11 +292,15 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
           const int tl = ent >> 5, j = ent & 31;
           const float4 th = s_th[wid][tl], tlw = s_tl[wid][tl];
           const float4 ph = s_ph[wid][j], pl = s_pl[wid][j];
-          ff dx = two_sum(th.x, -ph.x), dy = two_sum(th.y, -ph.y), dz = two_sum(th.z, -ph.z);
+          ff dx = two_sum(th.x, -ph.x), dy = two_sum(th.y, -ph.y), dz = {0.f, 0.f};
           dx = fast_two_sum(dx.hi, __fadd_rn(dx.lo, __fsub_rn(tlw.x, pl.x)));
           dy = fast_two_sum(dy.hi, __fadd_rn(dy.lo, __fsub_rn(tlw.y, pl.y)));
-          dz = fast_two_sum(dz.hi, __fadd_rn(dz.lo, __fsub_rn(tlw.z, pl.z)));
-          const ff r2 = ff_add(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)), ff_mul(dz, dz));
+          ff r2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
+          if (D == 3) {
+            dz = two_sum(th.z, -ph.z);
+            dz = fast_two_sum(dz.hi, __fadd_rn(dz.lo, __fsub_rn(tlw.z, pl.z)));
+            r2 = ff_add(r2, ff_mul(dz, dz));
+          }
           float2 res[NO];
 #pragma unroll
           for (int a = 0; a < NO; ++a) res[a] = make_float2(0.f, 0.f);
@@ -259,20 +310,33 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
             // t = 2 rho^2 - 1; the FP32 difference is not exact for rho^2 < 1/4
             const ff t0 = two_sum(__fmul_rn(2.f, rho2.hi), -1.f);
             const ff t = fast_two_sum(t0.hi, __fadd_rn(t0.lo, __fmul_rn(2.f, rho2.lo)));
-            const ff ri = ff_rsqrt(r2);
-            const ff ri2 = ff_mul(ri, ri);
+            ff ri = {0.f, 0.f}, ri2, logr2 = {0.f, 0.f};
+            if (D == 3) {
+              ri = ff_rsqrt(r2);
+              ri2 = ff_mul(ri, ri);
+            } else {
+              ri2 = ff_rcp(r2);
+              logr2 = ff_log(rho2);
+            }
             const ff xv[3] = {dx, dy, dz};
             ff out[NO];
             if (KM & 1) {
               const ff2 gh = horner_ff2<NT>(F.chi[0], F.clo[0], t);
-              const ff A = ff_add(ri, ff_scale({gh.hi.x, gh.lo.x}, nuinv));
-              const ff C = ff_mul(ri2, ff_add(ri, ff_scale({gh.hi.y, gh.lo.y}, nuinv)));
+              ff A, C;
+              if (D == 3) {
+                A = ff_add(ri, ff_scale({gh.hi.x, gh.lo.x}, nuinv));
+                C = ff_mul(ri2, ff_add(ri, ff_scale({gh.hi.y, gh.lo.y}, nuinv)));
+              } else {
+                A = ff_neg(ff_add(logr2, {gh.hi.x, gh.lo.x}));
+                C = ff_add(ff_scale(ri2, 2.f), ff_neg(ff_scale({gh.hi.y, gh.lo.y}, nu2inv)));
+              }
               const float4 fh = s_ah[wid][j], fl = s_al[wid][j];
               const ff fv[3] = {{fh.x, fl.x}, {fh.y, fl.y}, {fh.z, fl.z}};
-              const ff xf = ff_add(ff_add(ff_mul(dx, fv[0]), ff_mul(dy, fv[1])), ff_mul(dz, fv[2]));
+              ff xf = ff_add(ff_mul(dx, fv[0]), ff_mul(dy, fv[1]));
+              if (D == 3) xf = ff_add(xf, ff_mul(dz, fv[2]));
               const ff Cx = ff_mul(C, xf);
 #pragma unroll
-              for (int a = 0; a < 3; ++a) out[a] = ff_add(ff_mul(A, fv[a]), ff_mul(Cx, xv[a]));
+              for (int a = 0; a < D; ++a) out[a] = ff_add(ff_mul(A, fv[a]), ff_mul(Cx, xv[a]));
               if (GRAD) {
                 const ff2 dgh = horner_ff2<NT>(F.chi[2], F.clo[2], t);
                 const float nu3i = nuinv * nuinv * nuinv;
@@ -295,7 +359,8 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
                 }
               }
             } else {
-              out[0] = out[1] = out[2] = {0.f, 0.f};
+#pragma unroll
+              for (int a = 0; a < D; ++a) out[a] = {0.f, 0.f};
             }
             if (KM & 2) {
               const ff2 pq = horner_ff2<NT>(F.chi[1], F.clo[1], t);
@@ -305,14 +370,25 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
               const ff gv[3] = {{gh4.x, gl4.x}, {gh4.y, gl4.y}, {gh4.z, gl4.z}};
               const ff nv[3] = {{nh4.x, nl4.x}, {nh4.y, nl4.y}, {nh4.z, nl4.z}};
               const ff gn = {nh4.w, nl4.w};
-              const ff xn = ff_add(ff_add(ff_mul(dx, nv[0]), ff_mul(dy, nv[1])), ff_mul(dz, nv[2]));
-              const ff xg = ff_add(ff_add(ff_mul(dx, gv[0]), ff_mul(dy, gv[1])), ff_mul(dz, gv[2]));
-              const ff Dc = ff_mul(ff_scale({pq.hi.x, pq.lo.x}, nuinv), ri2);
-              const ff Ec = ff_mul_f(ff_mul(ff_mul(ri2, ri2), ff_add(ri, ff_scale({pq.hi.y, pq.lo.y}, nuinv))), -6.f);
+              ff xn = ff_add(ff_mul(dx, nv[0]), ff_mul(dy, nv[1]));
+              ff xg = ff_add(ff_mul(dx, gv[0]), ff_mul(dy, gv[1]));
+              if (D == 3) {
+                xn = ff_add(xn, ff_mul(dz, nv[2]));
+                xg = ff_add(xg, ff_mul(dz, gv[2]));
+              }
+              ff Dc, Ec;
+              if (D == 3) {
+                Dc = ff_mul(ff_scale({pq.hi.x, pq.lo.x}, nuinv), ri2);
+                Ec = ff_mul_f(ff_mul(ff_mul(ri2, ri2), ff_add(ri, ff_scale({pq.hi.y, pq.lo.y}, nuinv))), -6.f);
+              } else {
+                Dc = ff_neg(ff_scale({pq.hi.x, pq.lo.x}, nu2inv));
+                Ec = ff_add(ff_scale(ff_mul(ri2, ri2), -8.f),
+                            ff_mul_f(ff_scale({pq.hi.y, pq.lo.y}, nu2inv * nu2inv), 6.f));
+              }
               // E (x.g)(x.n) + D (g.n): coefficient of x
               const ff Ex = ff_add(ff_mul(Ec, ff_mul(xg, xn)), ff_mul(Dc, gn));
 #pragma unroll
-              for (int a = 0; a < 3; ++a) {
+              for (int a = 0; a < D; ++a) {
                 const ff sym = ff_add(ff_mul(gv[a], xn), ff_mul(nv[a], xg));
                 out[a] = ff_add(out[a], ff_add(ff_mul(Dc, sym), ff_mul(Ex, xv[a])));
               }
@@ -355,11 +431,13 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
   }
 }
 
-template <int KM, bool GRAD, int NT>
+template <int D, int KM, bool GRAD, int NT>
 void run_near_ff(const NearParams& P, const FFParams& F, cudaStream_t s) {
-  k_near_ff<KM, GRAD, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, F);
+  k_near_ff<D, KM, GRAD, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, F);
 }
 
-#define DMK_FOR_EACH_FF(M, NT) M(1, false, NT) M(2, false, NT) M(3, false, NT) M(1, true, NT)
+#define DMK_FOR_EACH_FF(M, NT)                                                    \
+  M(3, 1, false, NT) M(3, 2, false, NT) M(3, 3, false, NT) M(3, 1, true, NT)     \
+  M(2, 1, false, NT) M(2, 2, false, NT) M(2, 3, false, NT)
 
 }  // namespace dmk
