@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <set>
@@ -55,6 +56,30 @@ dmk_status_t validate_opts(const dmk_stokes_opts_t* o, std::string& msg) {
   return DMK_OK;
 }
 
+// Kernel tables depend only on (dim, c, FP32 tolerance); the 2D ones take a
+// few tens of milliseconds of host quadrature (App. B), so every process keeps
+// the tables it has built and plans with the same parameters copy them.
+bool cached_tables(int dim, double c, double fp32_tol, dmk::KernelTables* out) {
+  struct Entry {
+    int dim;
+    double c, tol;
+    std::unique_ptr<dmk::KernelTables> tables;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  for (const Entry& e : cache)
+    if (e.dim == dim && e.c == c && e.tol == fp32_tol) {
+      *out = *e.tables;
+      return true;
+    }
+  auto t = std::make_unique<dmk::KernelTables>();
+  if (dmk::build_tables(dim, c, fp32_tol, t.get()) != 0) return false;
+  *out = *t;
+  if (cache.size() < 64) cache.push_back(Entry{dim, c, fp32_tol, std::move(t)});
+  return true;
+}
+
 void configure_pool(int dev) {
   static std::mutex mu;
   static std::set<int> done;
@@ -105,7 +130,7 @@ dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64
     double c = dmk::bandlimit_for_eps(opts->eps, opts->kernels);
     if (c <= 0) throw dmk::Error{DMK_ERR_INVALID_ARG, "eps outside Table 2 range"};
     double fp32_tol = std::max(opts->eps / 100.0, 1e-8);
-    if (dmk::build_tables(opts->dim, c, fp32_tol, &p.tables) != 0)
+    if (!cached_tables(opts->dim, c, fp32_tol, &p.tables))
       throw dmk::Error{DMK_ERR_UNSUPPORTED, "kernel tables could not be built for this dimension"};
     p.leaf_capacity = opts->leaf_capacity > 0 ? opts->leaf_capacity
                                               : dmk::leaf_capacity_for_eps(opts->eps, opts->dim);

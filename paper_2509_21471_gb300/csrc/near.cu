@@ -93,14 +93,30 @@ __global__ void k_gn64(int64_t N, int D, const double* __restrict__ g, double* _
 // Periodic stresslet k = 0 term (Sec. 5.3, after Eq. (ewald_far)):
 //   u0(x_t) = -sum_s (w_t - w_s)(g_s . n_s) = -( w_t G - W ),
 //   G = sum_s g_s.n_s,  W = sum_s w_s (g_s.n_s), per system.
+// Points are sorted by system, so a warp almost always holds one system: its
+// four partial sums are then reduced by shuffles and added by one lane.
 __global__ void k_zero_reduce(int64_t N, int D, const double* __restrict__ w, const double* __restrict__ n64,
                               const int32_t* __restrict__ psys, double* __restrict__ sums) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  double gn = n64[D * N + i];
-  double* s = sums + 4 * psys[i];
-  atomicAdd(s, gn);
-  for (int a = 0; a < D; ++a) atomicAdd(s + 1 + a, w[a * N + i] * gn);
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool on = i < N;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  int sys = -1;
+  if (on) {
+    sys = psys[i];
+    v[0] = n64[D * N + i];
+    for (int a = 0; a < D; ++a) v[1 + a] = w[a * N + i] * v[0];
+  }
+  const int sys0 = __shfl_sync(0xffffffffu, sys, 0);
+  const bool uniform = __all_sync(0xffffffffu, !on || sys == sys0);
+  if (uniform) {
+    for (int k = 0; k < 4; ++k)
+      for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    if (lane == 0 && sys0 >= 0)
+      for (int k = 0; k < 1 + D; ++k) atomicAdd(sums + 4 * sys0 + k, v[k]);
+  } else if (on) {
+    for (int k = 0; k < 1 + D; ++k) atomicAdd(sums + 4 * sys + k, v[k]);
+  }
 }
 
 __global__ void k_zero_apply(int64_t N, int D, const double* __restrict__ w, const int32_t* __restrict__ perm,
