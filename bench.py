@@ -369,7 +369,8 @@ def run_ours(args):
     achieved = near["mixed"]["useful_pairs"] * flops_per_pair / (near["mixed"]["ms"] / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "kernel": "k_near_mixed<3,1,false,16,1> (near field, mixed precision)",
+                "kernel": f"k_near_mixed<3,1,false,{min(v for v in (8, 10, 12, 13, 14, 16) if v >= max(c32))},1> "
+                          "(near field, mixed precision)",
                 "flops_per_useful_pair": flops_per_pair,
                 "peak_basis": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
                               "(max SM clock of MEASURED_PEAKS.json)"}

@@ -59,6 +59,10 @@ dmk_status_t validate_opts(const dmk_stokes_opts_t* o, std::string& msg) {
 // Kernel tables depend only on (dim, c, FP32 tolerance); the 2D ones take a
 // few tens of milliseconds of host quadrature (App. B), so every process keeps
 // the tables it has built and plans with the same parameters copy them.
+// Truncation of the FP32 tables (Chebyshev tail relative to max |f|): a tenth
+// of eps, no lower than FP32 rounding of the pair terms can use.
+double fp32_table_tol(double eps) { return std::max(eps / 10.0, 1e-8); }
+
 bool cached_tables(int dim, double c, double fp32_tol, dmk::KernelTables* out) {
   struct Entry {
     int dim;
@@ -129,8 +133,7 @@ dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64
     configure_pool(p.device);
     double c = dmk::bandlimit_for_eps(opts->eps, opts->kernels);
     if (c <= 0) throw dmk::Error{DMK_ERR_INVALID_ARG, "eps outside Table 2 range"};
-    double fp32_tol = std::max(opts->eps / 100.0, 1e-8);
-    if (!cached_tables(opts->dim, c, fp32_tol, &p.tables))
+    if (!cached_tables(opts->dim, c, fp32_table_tol(opts->eps), &p.tables))
       throw dmk::Error{DMK_ERR_UNSUPPORTED, "kernel tables could not be built for this dimension"};
     p.leaf_capacity = opts->leaf_capacity > 0 ? opts->leaf_capacity
                                               : dmk::leaf_capacity_for_eps(opts->eps, opts->dim);
@@ -336,7 +339,7 @@ dmk_status_t dmk_stokes_kernel_table(int32_t dim, double eps, int32_t kernels, i
   double c = dmk::bandlimit_for_eps(eps, kernels);
   if (c <= 0) return set_err(nullptr, DMK_ERR_INVALID_ARG, "eps outside Table 2 range");
   static thread_local dmk::KernelTables tb;
-  if (dmk::build_tables(dim, c, std::max(eps / 100.0, 1e-8), &tb) != 0)
+  if (dmk::build_tables(dim, c, fp32_table_tol(eps), &tb) != 0)
     return set_err(nullptr, DMK_ERR_UNSUPPORTED, "table build failed");
   if (out_c) *out_c = tb.c;
   if (out_phi0) *out_phi0 = tb.phi0;

@@ -449,9 +449,9 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   for (int id : ids)
     if (id >= 0) need = std::max(need, mixed ? tb.n32[id] : tb.n64[id]);
   if (grad) need = std::max(need, std::max(mixed ? tb.n32[P_DGS] : tb.n64[P_DGS], mixed ? tb.n32[P_DHS] : tb.n64[P_DHS]));
-  static const int kSetM[] = {8, 12, 16, 20, 24};
+  static const int kSetM[] = {8, 10, 12, 13, 14, 16};
   static const int kSetD[] = {16, 20, 24, 28, 32};
-  int nt = mixed ? pick_nt(kSetM, 5, need) : pick_nt(kSetD, 5, need);
+  int nt = mixed ? pick_nt(kSetM, 6, need) : pick_nt(kSetD, 5, need);
   if (nt < 0) throw Error{DMK_ERR_UNSUPPORTED, "kernel table longer than the compiled kernels"};
   for (int id = 0; id < P_COUNT; ++id)
     for (int k = 0; k < kPolyCap; ++k) P.c64[id][k] = k < tb.n64[id] ? tb.p64[id][k] : 0.0;

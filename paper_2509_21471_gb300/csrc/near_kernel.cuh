@@ -657,7 +657,7 @@ void run_near_fp64(const NearParams& P, cudaStream_t s) {
 #define DMK_FOR_EACH_VARIANT_2D(M, NT) \
   M(2, 1, false, NT, 1) M(2, 2, false, NT, 1) M(2, 3, false, NT, 1) M(2, 1, false, NT, 4) M(2, 1, false, NT, 16)
 
-#define DMK_NT_MIXED(X) X(8) X(12) X(16) X(20) X(24)
+#define DMK_NT_MIXED(X) X(8) X(10) X(12) X(13) X(14) X(16)   // FP32 pair terms: eps >= 2e-7
 #define DMK_NT_FP64(X) X(16) X(20) X(24) X(28) X(32)
 
 }  // namespace dmk

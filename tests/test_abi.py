@@ -66,7 +66,8 @@ def test_host_tables_match_oracle_residual_functions(dmk_lib, eps):
         scale = np.abs(r).max()
         assert np.max(np.abs(v64 - r)) < 2e-13 * scale, which
         assert len(p64) <= 32 and len(p32) <= 24          # compiled kernel sizes
-        assert np.max(np.abs(v32 - r)) < max(eps / 50, 3e-7) * scale, which
+        # FP32 tables drop the Chebyshev tail below eps/10 of max |f|
+        assert np.max(np.abs(v32 - r)) < max(eps / 5, 3e-7) * scale, which
     # derivative tables (d/ds, s = rho^2) against finite differences of the oracle
     for which, base in ((4, 0), (5, 1)):
         _, _, pd = dmk_lib.kernel_table(3, eps, which, kernels=3)
@@ -91,7 +92,7 @@ def test_host_tables_2d_match_oracle(dmk_lib, eps):
         # m_to weighs k^7: near k = c the two sides' gamma-hat quadratures differ
         # by rounding, ~1e-12 of max|m_to| at small rho
         assert np.max(np.abs(np.polynomial.polynomial.polyval(t, p64) - ref)) < 5e-12 * scale, which
-        assert np.max(np.abs(np.polynomial.polynomial.polyval(t, p32) - ref)) < max(eps / 50, 3e-7) * scale, which
+        assert np.max(np.abs(np.polynomial.polynomial.polyval(t, p32) - ref)) < max(eps / 5, 3e-7) * scale, which
         assert len(p64) <= 32 and len(p32) <= 24
     _, _, m0 = dmk_lib.kernel_table(2, eps, 6, kernels=3)
     assert abs(m0[0] - kern.self_md0()) < 1e-12 * abs(kern.self_md0())
