@@ -202,8 +202,10 @@ __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned lo
     const float nu2m = E.nu2 * (1.f + 0x1p-12f);
     const double nu2 = static_cast<double>(E.nu2);
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
-    for (int U = U0; U < U1; ++U) {
-      if (!on || !tile_near(P, U, E, tlo, thi)) continue;
+    for (int Ub = U0; Ub < U1; Ub += 32)
+    for (uint32_t tm = near_tile_mask(P, Ub, U1, E, tlo, thi, lane); tm; tm &= tm - 1u) {
+      const int U = Ub + __ffs(tm) - 1;
+      if (!on) continue;
       const int s0 = P.tile_start[U], ns = P.tile_count[U];
       for (int j = 0; j < ns; ++j) {
         const float4 r = P.rel[s0 + j];

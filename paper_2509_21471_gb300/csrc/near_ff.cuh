@@ -222,8 +222,9 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
     const float nu2inv = nuinv * nuinv;
     const float nu2m = nu2 * (1.f + 0x1p-12f);
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
-    for (int U = U0; U < U1; ++U) {
-      if (!tile_near(P, U, E, tlo, thi)) continue;
+    for (int Ub = U0; Ub < U1; Ub += 32)
+    for (uint32_t tm = near_tile_mask(P, Ub, U1, E, tlo, thi, lane); tm; tm &= tm - 1u) {
+      const int U = Ub + __ffs(tm) - 1;
       const int s0 = P.tile_start[U], ns = P.tile_count[U];
       __syncwarp();
       if (lane < ns) {

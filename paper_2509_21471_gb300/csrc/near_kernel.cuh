@@ -151,6 +151,15 @@ __device__ __forceinline__ bool tile_near(const NearParams& P, int U, const Entr
   return gx * gx + gy * gy + gz * gz < E.nu2 * 1.0001f;
 }
 
+// The source tiles Ub + lane (< Uend) of a near leaf that can hold a pair
+// closer than nu to the target tile, tested by the whole warp at once (one
+// tile per lane) and returned as a bit mask over [Ub, Ub + 32).
+__device__ __forceinline__ uint32_t near_tile_mask(const NearParams& P, int Ub, int Uend, const Entry& E,
+                                                   float4 tlo, float4 thi, int lane) {
+  const int U = Ub + lane;
+  return __ballot_sync(0xffffffffu, U < Uend && tile_near(P, U, E, tlo, thi));
+}
+
 // Candidate bits of one staged tile for this lane's target: bit j is set when
 // |x_t|^2 + (|s_j|^2 - nu'^2) - 2 x_t.s_j < 0, with the slot holding
 // (-2 s, |s|^2 - nu'^2), nu'^2 = nu^2 (1 + 2^-12).  The margin is far above
@@ -273,8 +282,9 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
     const float nu2inv = nuinv * nuinv;
     const float nu2m = nu2 * (1.f + 0x1p-12f);
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
-    for (int U = U0; U < U1; ++U) {
-      if (!tile_near(P, U, E, tlo, thi)) continue;
+    for (int Ub = U0; Ub < U1; Ub += 32)
+    for (uint32_t tm = near_tile_mask(P, Ub, U1, E, tlo, thi, lane); tm; tm &= tm - 1u) {
+      const int U = Ub + __ffs(tm) - 1;
       const int s0 = P.tile_start[U], ns = P.tile_count[U];
       __syncwarp();
       if (lane < ns) {
@@ -581,8 +591,9 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
     const Entry E = make_entry<D>(P, e, LB, cB);
     const float nu2m = E.nu2 * (1.f + 0x1p-12f);
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
-    for (int U = U0; U < U1; ++U) {
-      if (!tile_near(P, U, E, tlo, thi)) continue;
+    for (int Ub = U0; Ub < U1; Ub += 32)
+    for (uint32_t tm = near_tile_mask(P, Ub, U1, E, tlo, thi, lane); tm; tm &= tm - 1u) {
+      const int U = Ub + __ffs(tm) - 1;
       if (nb == NB) flush();
       const int s0 = P.tile_start[U], ns = P.tile_count[U];
       const int slot = nb * kTile + lane;
