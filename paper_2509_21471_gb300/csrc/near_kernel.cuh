@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
 // exactly in FP64 with the oracle's operation order.
 template <int D, int KM, bool GRAD, int NT, int NR>
 struct Fp64Shape {
-  static constexpr int NB = (NR == 1) ? ((KM == 1) ? 4 : 2) : 1;     // staged tiles per batch
+  static constexpr int NB = (NR == 1) ? ((KM == 1 && !GRAD) ? 4 : 2) : 1;   // staged tiles per batch
   static constexpr int WPB = (NR > 4) ? 2 : 4;                       // warps per block
 };
 
@@ -481,106 +481,185 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
 #pragma unroll
   for (int k = 0; k < (GRAD ? 9 : 1); ++k) G[k] = 0.0;
 
+  // One candidate pair (target coordinates w3, staged source slot idx):
+  // decided and evaluated in FP64 with the oracle's operation order; the
+  // contributions are added to a (velocity, [NR][3]) and gr (gradient).
+  auto pair = [&](const double (&w3)[3], int idx, double (&a)[NR][3], double (&gr)[GRAD ? 9 : 1]) {
+    const double* q = sQ[wid][idx >> 5];
+    const double dx = __dadd_rn(__dsub_rn(w3[0], sD[wid][0][idx]), q[0]);
+    const double dy = __dadd_rn(__dsub_rn(w3[1], sD[wid][1][idx]), q[1]);
+    double dz = 0.0, r2;
+    if (D == 3) {
+      dz = __dadd_rn(__dsub_rn(w3[2], sD[wid][Z][idx]), q[2]);
+      r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    } else {
+      r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+    }
+    const double nuinv = q[3];
+    const double nu2inv = nuinv * nuinv;
+    const double rho2 = r2 * nu2inv;                  // exact: nuinv is a power of two
+    if (!(rho2 < 1.0 && r2 > 0.0)) return;
+    const double t = fma(2.0, rho2, -1.0);
+    double ri = 0.0, ri2, logr2 = 0.0;
+    if (D == 3) {
+      ri = 1.0 / sqrt(r2);
+      ri2 = ri * ri;
+    } else {
+      ri2 = 1.0 / r2;
+      logr2 = log(rho2);
+    }
+    int k = D;
+    if (KM & 1) {
+      const double g = horner<NT>(P.c64[P_GS], t);
+      const double h = horner<NT>(P.c64[P_HS], t);
+      double A, C;
+      if (D == 3) {
+        A = fma(g, nuinv, ri);
+        C = ri2 * fma(h, nuinv, ri);
+      } else {
+        A = -logr2 - g;
+        C = fma(-h, nu2inv, 2.0 * ri2);
+      }
+#pragma unroll
+      for (int c = 0; c < NR; ++c) {
+        const double fx = sD[wid][k][idx], fy = sD[wid][k + 1][idx];
+        const double fz = (D == 3) ? sD[wid][k + Z][idx] : 0.0;
+        k += D;
+        const double xf = fma(dx, fx, fma(dy, fy, dz * fz));
+        const double Cx = C * xf;
+        a[c][0] = fma(A, fx, fma(Cx, dx, a[c][0]));
+        a[c][1] = fma(A, fy, fma(Cx, dy, a[c][1]));
+        if (D == 3) a[c][2] = fma(A, fz, fma(Cx, dz, a[c][2]));
+        if (GRAD) {
+          const double dg = horner<NT>(P.c64[P_DGS], t);
+          const double dh = horner<NT>(P.c64[P_DHS], t);
+          const double nu3i = nuinv * nuinv * nuinv;
+          const double ri3 = ri2 * ri;
+          const double A1 = fma(2.0 * dg, nu3i, -ri3);
+          const double C1 = fma(-3.0 * ri3, ri2, ri2 * fma(2.0 * dh, nu3i, -2.0 * h * nuinv * ri2));
+          const double xv[3] = {dx, dy, dz};
+          const double fv[3] = {fx, fy, fz};
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) {
+            const double a1 = fma(A1, fv[jj], C1 * xv[jj] * xf);
+#pragma unroll
+            for (int mm = 0; mm < 3; ++mm) {
+              double v = fma(a1, xv[mm], C * xv[jj] * fv[mm]);
+              if (jj == mm) v = fma(C, xf, v);
+              gr[jj * 3 + mm] += v;
+            }
+          }
+        }
+      }
+    }
+    if (KM & 2) {
+      const double pt = horner<NT>(P.c64[P_PT], t);
+      const double qt = horner<NT>(P.c64[P_QT], t);
+      const double gx_ = sD[wid][k][idx], gy_ = sD[wid][k + 1][idx];
+      const double gz_ = (D == 3) ? sD[wid][k + Z][idx] : 0.0;
+      const double nx = sD[wid][k + D][idx], ny = sD[wid][k + D + 1][idx];
+      const double nz = (D == 3) ? sD[wid][k + D + Z][idx] : 0.0;
+      const double gn = sD[wid][k + 2 * D][idx];
+      const double xn = fma(dx, nx, fma(dy, ny, dz * nz));
+      const double xg = fma(dx, gx_, fma(dy, gy_, dz * gz_));
+      double Dc, Ec;
+      if (D == 3) {
+        Dc = pt * nuinv * ri2;
+        Ec = -6.0 * ri2 * ri2 * fma(qt, nuinv, ri);
+      } else {
+        Dc = -pt * nu2inv;
+        Ec = fma(6.0 * qt, nu2inv * nu2inv, -8.0 * ri2 * ri2);
+      }
+      const double Ex = Ec * xg * xn + Dc * gn;
+      a[0][0] += fma(Dc, fma(gx_, xn, nx * xg), Ex * dx);
+      a[0][1] += fma(Dc, fma(gy_, xn, ny * xg), Ex * dy);
+      if (D == 3) a[0][2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
+    }
+  };
+
+  // NR == 1: the warp's candidate pairs are queued (grouped by target) and
+  // evaluated 32 at a time by all lanes, so the FP64 pair path runs on full
+  // warps; each lane then adds its own target's results.  NR > 1: every lane
+  // walks its own candidates.
+  constexpr int NO = GRAD ? 12 : D;
+  constexpr int Q = (NR == 1) ? 64 : 1;              // queued pairs per round
+  __shared__ double s_wt[(NR == 1) ? WPB : 1][3][kTile];
+  __shared__ uint16_t s_q[(NR == 1) ? WPB : 1][Q];
+  __shared__ double s_r[(NR == 1) ? WPB : 1][(NR == 1) ? NO : 1][Q];
+  if (NR == 1)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s_wt[(NR == 1) ? wid : 0][c][lane] = wt[c];
+
   int nb = 0;
   auto flush = [&]() {
     __syncwarp();
     uint32_t m[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
     for (int w = 0; w < NB; ++w)
-      if (w < nb) m[w] = candidate_bits(&sA[wid][w * kTile], xt, tt);
-    BitWalker bw{on ? m[0] : 0u, on ? m[1] : 0u, on ? m[2] : 0u, on ? m[3] : 0u, 0};
-    int idx;
-    while (bw.next(idx)) {
-      const double* q = sQ[wid][idx >> 5];
-      const double dx = __dadd_rn(__dsub_rn(wt[0], sD[wid][0][idx]), q[0]);
-      const double dy = __dadd_rn(__dsub_rn(wt[1], sD[wid][1][idx]), q[1]);
-      double dz = 0.0, r2;
-      if (D == 3) {
-        dz = __dadd_rn(__dsub_rn(wt[2], sD[wid][Z][idx]), q[2]);
-        r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-      } else {
-        r2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+      if (w < nb) m[w] = on ? candidate_bits(&sA[wid][w * kTile], xt, tt) : 0u;
+    if (NR == 1) {
+      const int qw = (NR == 1) ? wid : 0;
+      int cnt = 0;
+#pragma unroll
+      for (int w = 0; w < NB; ++w) cnt += __popc(m[w]);
+      int off = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += v;
       }
-      const double nuinv = q[3];
-      const double nu2inv = nuinv * nuinv;
-      const double rho2 = r2 * nu2inv;                  // exact: nuinv is a power of two
-      if (!(rho2 < 1.0 && r2 > 0.0)) continue;
-      const double t = fma(2.0, rho2, -1.0);
-      double ri = 0.0, ri2, logr2 = 0.0;
-      if (D == 3) {
-        ri = 1.0 / sqrt(r2);
-        ri2 = ri * ri;
-      } else {
-        ri2 = 1.0 / r2;
-        logr2 = log(rho2);
-      }
-      int k = D;
-      if (KM & 1) {
-        const double g = horner<NT>(P.c64[P_GS], t);
-        const double h = horner<NT>(P.c64[P_HS], t);
-        double A, C;
-        if (D == 3) {
-          A = fma(g, nuinv, ri);
-          C = ri2 * fma(h, nuinv, ri);
-        } else {
-          A = -logr2 - g;
-          C = fma(-h, nu2inv, 2.0 * ri2);
-        }
+      const int total = __shfl_sync(0xffffffffu, off, 31);
+      off -= cnt;
+      for (int base = 0; base < total; base += Q) {
+        {   // queue this lane's entries with index in [base, base + Q)
+          int i = off;
 #pragma unroll
-        for (int c = 0; c < NR; ++c) {
-          const double fx = sD[wid][k][idx], fy = sD[wid][k + 1][idx];
-          const double fz = (D == 3) ? sD[wid][k + Z][idx] : 0.0;
-          k += D;
-          const double xf = fma(dx, fx, fma(dy, fy, dz * fz));
-          const double Cx = C * xf;
-          acc[c][0] = fma(A, fx, fma(Cx, dx, acc[c][0]));
-          acc[c][1] = fma(A, fy, fma(Cx, dy, acc[c][1]));
-          if (D == 3) acc[c][2] = fma(A, fz, fma(Cx, dz, acc[c][2]));
-          if (GRAD) {
-            const double dg = horner<NT>(P.c64[P_DGS], t);
-            const double dh = horner<NT>(P.c64[P_DHS], t);
-            const double nu3i = nuinv * nuinv * nuinv;
-            const double ri3 = ri2 * ri;
-            const double A1 = fma(2.0 * dg, nu3i, -ri3);
-            const double C1 = fma(-3.0 * ri3, ri2, ri2 * fma(2.0 * dh, nu3i, -2.0 * h * nuinv * ri2));
-            const double xv[3] = {dx, dy, dz};
-            const double fv[3] = {fx, fy, fz};
-#pragma unroll
-            for (int jj = 0; jj < 3; ++jj) {
-              const double a1 = fma(A1, fv[jj], C1 * xv[jj] * xf);
-#pragma unroll
-              for (int mm = 0; mm < 3; ++mm) {
-                double v = fma(a1, xv[mm], C * xv[jj] * fv[mm]);
-                if (jj == mm) v = fma(C, xf, v);
-                G[jj * 3 + mm] += v;
-              }
+          for (int w = 0; w < NB; ++w) {
+            uint32_t bm = m[w];
+            if (i + __popc(bm) <= base) {
+              i += __popc(bm);
+              continue;
+            }
+            while (bm && i < base + Q) {
+              const int j = __ffs(bm) - 1;
+              bm &= bm - 1u;
+              if (i >= base) s_q[qw][i - base] = static_cast<uint16_t>((lane << 7) | (w * kTile + j));
+              ++i;
             }
           }
         }
-      }
-      if (KM & 2) {
-        const double pt = horner<NT>(P.c64[P_PT], t);
-        const double qt = horner<NT>(P.c64[P_QT], t);
-        const double gx_ = sD[wid][k][idx], gy_ = sD[wid][k + 1][idx];
-        const double gz_ = (D == 3) ? sD[wid][k + Z][idx] : 0.0;
-        const double nx = sD[wid][k + D][idx], ny = sD[wid][k + D + 1][idx];
-        const double nz = (D == 3) ? sD[wid][k + D + Z][idx] : 0.0;
-        const double gn = sD[wid][k + 2 * D][idx];
-        const double xn = fma(dx, nx, fma(dy, ny, dz * nz));
-        const double xg = fma(dx, gx_, fma(dy, gy_, dz * gz_));
-        double Dc, Ec;
-        if (D == 3) {
-          Dc = pt * nuinv * ri2;
-          Ec = -6.0 * ri2 * ri2 * fma(qt, nuinv, ri);
-        } else {
-          Dc = -pt * nu2inv;
-          Ec = fma(6.0 * qt, nu2inv * nu2inv, -8.0 * ri2 * ri2);
+        __syncwarp();
+        const int n = min(Q, total - base);
+        for (int q0 = 0; q0 < n; q0 += 32) {
+          const int qi = q0 + lane;
+          if (qi >= n) continue;
+          const int ent = s_q[qw][qi];
+          const int tl = ent >> 7;
+          const double w3[3] = {s_wt[qw][0][tl], s_wt[qw][1][tl], s_wt[qw][2][tl]};
+          double a[NR][3] = {};
+          double gr[GRAD ? 9 : 1] = {};
+          pair(w3, ent & 127, a, gr);
+#pragma unroll
+          for (int c = 0; c < D; ++c) s_r[qw][c % NO][qi] = a[0][c];
+          if (GRAD)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) s_r[qw][(D + c) % NO][qi] = gr[c];
         }
-        const double Ex = Ec * xg * xn + Dc * gn;
-        acc[0][0] += fma(Dc, fma(gx_, xn, nx * xg), Ex * dx);
-        acc[0][1] += fma(Dc, fma(gy_, xn, ny * xg), Ex * dy);
-        if (D == 3) acc[0][2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
+        __syncwarp();
+        const int i0 = max(off, base), i1 = min(off + cnt, base + Q);
+        for (int i = i0; i < i1; ++i) {
+#pragma unroll
+          for (int c = 0; c < D; ++c) acc[0][c] += s_r[qw][c % NO][i - base];
+          if (GRAD)
+#pragma unroll
+            for (int c = 0; c < 9; ++c) G[c] += s_r[qw][(D + c) % NO][i - base];
+        }
+        __syncwarp();
       }
+    } else {
+      BitWalker bw{m[0], m[1], m[2], m[3], 0};
+      int idx;
+      while (bw.next(idx)) pair(wt, idx, acc, G);
     }
     __syncwarp();
     nb = 0;

@@ -125,3 +125,37 @@ def test_eval_captured_in_cuda_graph(dmk):
         ref = p.eval(F)
         assert torch.equal(u_static, ref), trial
     p.close()
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_one_column_eval_captured_in_cuda_graph(dmk, eps):
+    """One force column, periodic Stokeslet + stresslet: FP32 pair terms at
+    1e-6, float-float pair terms at 1e-9; the replay equals an eager call
+    (up to the order of the zero-mode reductions)."""
+    rng = np.random.default_rng(421)
+    N = 8000
+    x = torch.as_tensor(wl.uniform_points(rng, N, 3), device="cuda")
+    ins = [torch.zeros((N, 3), dtype=torch.float64, device="cuda") for _ in range(3)]
+    u_static = torch.zeros((N, 3), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        p = dmk.Plan(x, eps=eps, periodic=True, kernels=dmk.STOKESLET | dmk.STRESSLET, precision=dmk.MIXED,
+                     stream=s)
+        p.eval(*ins, out=u_static, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        p.eval(*ins, out=u_static, stream=s)
+    for trial in range(2):
+        new = [torch.as_tensor(wl.forces(rng, N, 3, zero_mean=True), device="cuda"),
+               torch.as_tensor(wl.stresslet_strengths(rng, N, 3), device="cuda"),
+               torch.as_tensor(wl.unit_normals(rng, N, 3), device="cuda")]
+        for a, b in zip(ins, new):
+            a.copy_(b)
+        g.replay()
+        torch.cuda.synchronize()
+        ref = p.eval(*new)
+        # the zero-mode sums are reduced with atomics: equal up to their order
+        scale = float(ref.abs().max())
+        assert torch.allclose(u_static, ref, rtol=0.0, atol=1e-13 * scale), trial
+    p.close()

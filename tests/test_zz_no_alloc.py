@@ -26,19 +26,20 @@ def dmk(dmk_lib):
     return dmk_lib
 
 
-@pytest.mark.parametrize("precision,periodic,kernels,tol", [
-    (1, False, 1, 1e-5),      # mixed precision, tolerance 10 eps at eps = 1e-6
-    (0, True, 3, 1e-12),      # FP64, periodic Stokeslet + stresslet (zero-mode sums)
-    (1, True, 2, 1e-5),
+@pytest.mark.parametrize("precision,periodic,kernels,eps,tol", [
+    (1, False, 1, 1e-6, 1e-5),      # mixed precision (FP32 pair terms), tolerance 10 eps
+    (0, True, 3, 1e-6, 1e-12),      # FP64, periodic Stokeslet + stresslet (zero-mode sums)
+    (1, True, 2, 1e-6, 1e-5),
+    (1, True, 3, 1e-9, 1e-8),       # mixed below eps 2e-7: float-float pair terms
 ])
-def test_noalloc_matches_eval_on_two_calls(dmk, precision, periodic, kernels, tol):
+def test_noalloc_matches_eval_on_two_calls(dmk, precision, periodic, kernels, eps, tol):
     rng = np.random.default_rng(2024 + 10 * precision + kernels)
     N = 3000
     x = wl.gaussian_mixture_points(rng, N, 3, 8, 0.03)
     f = torch.as_tensor(wl.forces(rng, N, 3), device="cuda") if kernels & 1 else None
     g = torch.as_tensor(wl.stresslet_strengths(rng, N, 3), device="cuda") if kernels & 2 else None
     n = torch.as_tensor(wl.unit_normals(rng, N, 3), device="cuda") if kernels & 2 else None
-    p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=1e-6, periodic=periodic, kernels=kernels,
+    p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=eps, periodic=periodic, kernels=kernels,
                  precision=precision, leaf_capacity=48)
     u_ref = p.eval(f, g, n).cpu().numpy()
     for _ in range(2):
