@@ -367,8 +367,13 @@ def run_ours(args):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = near["mixed"]["useful_pairs"] * flops_per_pair / (near["mixed"]["ms"] / 1e3) / 1e12
+    # DRAM bytes per launch of this kernel from ncu (dram__bytes_read.sum +
+    # dram__bytes_write.sum) on the same recipe at N = 5e5, scaled by the point
+    # count: profiles/near_mixed_clustered5e5.md
+    traffic = 31.37e6 * args.n / 500_000 if args.eps == 1e-6 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None,
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "traffic_note": "bytes per launch, ncu capture at N=5e5 scaled by the point count",
                 "kernel": f"k_near_mixed<3,1,false,{min(v for v in (8, 10, 12, 13, 14, 16) if v >= max(c32))},1> "
                           "(near field, mixed precision)",
                 "flops_per_useful_pair": flops_per_pair,
