@@ -84,6 +84,44 @@ bool cached_tables(int dim, double c, double fp32_tol, dmk::KernelTables* out) {
   return true;
 }
 
+}  // namespace
+
+namespace dmk {
+namespace {
+// pinned slots: blocks of 256 slots of 16 int32, handed out from a free list
+struct PinnedPool {
+  std::mutex mu;
+  std::vector<int32_t*> free_list;
+};
+PinnedPool& pinned_pool() {
+  static PinnedPool pool;   // blocks stay allocated until the process exits
+  return pool;
+}
+}  // namespace
+
+int32_t* pinned_slot() {
+  PinnedPool& pool = pinned_pool();
+  std::lock_guard<std::mutex> lk(pool.mu);
+  if (pool.free_list.empty()) {
+    void* b = nullptr;
+    if (cudaMallocHost(&b, 256 * 16 * sizeof(int32_t)) != cudaSuccess)
+      throw Error{DMK_ERR_NOMEM, "pinned host allocation failed"};
+    for (int k = 255; k >= 0; --k) pool.free_list.push_back(static_cast<int32_t*>(b) + 16 * k);
+  }
+  int32_t* r = pool.free_list.back();
+  pool.free_list.pop_back();
+  return r;
+}
+
+void pinned_release(int32_t* slot) {
+  PinnedPool& pool = pinned_pool();
+  std::lock_guard<std::mutex> lk(pool.mu);
+  pool.free_list.push_back(slot);
+}
+}  // namespace dmk
+
+namespace {
+
 void configure_pool(int dev) {
   static std::mutex mu;
   static std::set<int> done;
@@ -98,12 +136,12 @@ void configure_pool(int dev) {
 }
 
 void release(dmk::Plan& p) {
-  cudaStream_t s = p.stream;
-  dmk::free_tree(p.tree, s);
-  dmk::dfree(p.fsorted, s);
-  dmk::dfree(p.reduce_buf, s);
-  dmk::dfree(p.status, s);
-  if (p.h_status) cudaFreeHost(p.h_status);
+  dmk::free_tree(p.tree, p.stream);
+  p.fsorted = nullptr;
+  p.reduce_buf = nullptr;
+  p.status = nullptr;
+  p.arena.release();
+  if (p.h_status) dmk::pinned_release(p.h_status);
   p.h_status = nullptr;
 }
 
@@ -139,13 +177,17 @@ dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64
                                               : dmk::leaf_capacity_for_eps(opts->eps, opts->dim);
     p.tree.N = N;
     p.tree.n_sys = n_sys;
-    p.status = dmk::dalloc<int>(1, p.stream);
-    DMK_CUDA_TRY(cudaMemsetAsync(p.status, 0, sizeof(int), p.stream));
-    DMK_CUDA_TRY(cudaMallocHost(&p.h_status, sizeof(int)));
-    dmk::build_tree(p, d_src, h_offsets);
+    // one arena block for the tree (~80 bytes per point) and the evaluation workspace
+    p.arena.s = p.stream;
     p.fsorted_bytes = dmk::eval_workspace_bytes(p.opts, N);
-    p.fsorted = dmk::dalloc<char>(p.fsorted_bytes, p.stream);
-    p.reduce_buf = dmk::dalloc<double>(4 * n_sys, p.stream);
+    p.arena.reserve(p.fsorted_bytes + static_cast<size_t>(N) * 96 + 32 * static_cast<size_t>(n_sys) +
+                    (size_t(8) << 20));
+    p.status = p.arena.alloc<int>(1);
+    DMK_CUDA_TRY(cudaMemsetAsync(p.status, 0, sizeof(int), p.stream));
+    p.h_status = dmk::pinned_slot();
+    dmk::build_tree(p, d_src, h_offsets);
+    p.fsorted = p.arena.alloc<char>(p.fsorted_bytes);
+    p.reduce_buf = p.arena.alloc<double>(4 * n_sys);
     DMK_CUDA_TRY(cudaGetLastError());
     // everything above is complete when the call returns: the plan may then be
     // used from any stream and the coordinate buffer reused

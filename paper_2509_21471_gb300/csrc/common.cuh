@@ -2,8 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/dmk_stokes.h"
 #include "tables.h"
@@ -154,6 +156,57 @@ struct DeviceTree {
   int32_t* leaf_ntile = nullptr;
 };
 
+// Bump allocator over a few large stream-ordered blocks.  A plan's device
+// arrays come from one arena (returned in one call per block when the plan is
+// destroyed) and the tree builder's scratch from another, released when the
+// build ends; a pointer from an arena is never freed on its own.
+struct Arena {
+  cudaStream_t s = nullptr;
+  std::vector<void*> blocks;
+  char* cur = nullptr;
+  size_t left = 0;
+  size_t next = size_t(16) << 20;       // size of the next block
+  Arena() = default;
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  void reserve(size_t bytes) {
+    if (bytes > next) next = bytes;
+  }
+  void* alloc_bytes(size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    if (bytes > left) {
+      const size_t sz = std::max(bytes, next);
+      void* ptr = nullptr;
+      DMK_CUDA_TRY(cudaMallocAsync(&ptr, sz, s));
+      blocks.push_back(ptr);
+      cur = static_cast<char*>(ptr);
+      left = sz;
+      next = std::max(next, sz) * 2;
+    }
+    void* r = cur;
+    cur += bytes;
+    left -= bytes;
+    return r;
+  }
+  template <typename T>
+  T* alloc(size_t n) {
+    return static_cast<T*>(alloc_bytes(n * sizeof(T)));
+  }
+  void release() {
+    for (void* b : blocks) cudaFreeAsync(b, s);
+    blocks.clear();
+    cur = nullptr;
+    left = 0;
+  }
+  ~Arena() { release(); }
+};
+
+// Small pinned host buffers (16 int32 each) shared by all plans of the process:
+// pinned allocation costs far more than the plan build otherwise needs.
+int32_t* pinned_slot();
+void pinned_release(int32_t* slot);
+
 struct Plan {
   dmk_stokes_opts_t opts{};
   int leaf_capacity = 0;
@@ -167,7 +220,8 @@ struct Plan {
   double* gn_sorted = nullptr; // stresslet: sorted g (SoA) , n (SoA), g.n
   double* reduce_buf = nullptr;
   int* status = nullptr;       // device status word
-  int* h_status = nullptr;     // pinned host mirror
+  int* h_status = nullptr;     // pinned host mirror (a pinned_slot)
+  Arena arena;                 // device arrays of the plan
   std::string last_error;
   int64_t useful_pairs = -1;   // cached by dmk_stokes_plan_stats
   mutable int64_t launches = 0;  // kernels launched by this library for this plan

@@ -33,19 +33,14 @@ struct LeafArrays {
   int32_t* sys = nullptr;
 };
 
-void alloc_leaves(LeafArrays& L, int64_t n, cudaStream_t s) {
-  L.anchor = dalloc<uint64_t>(n, s);
-  L.level = dalloc<int32_t>(n, s);
-  L.start = dalloc<int32_t>(n, s);
-  L.count = dalloc<int32_t>(n, s);
-  L.sys = dalloc<int32_t>(n, s);
-}
-void free_leaves(LeafArrays& L, cudaStream_t s) {
-  dfree(L.anchor, s);
-  dfree(L.level, s);
-  dfree(L.start, s);
-  dfree(L.count, s);
-  dfree(L.sys, s);
+// leaf arrays of one refinement step (from the plan's arena: the last step's
+// arrays become the tree's)
+void alloc_leaves(LeafArrays& L, int64_t n, Arena& A) {
+  L.anchor = A.alloc<uint64_t>(n);
+  L.level = A.alloc<int32_t>(n);
+  L.start = A.alloc<int32_t>(n);
+  L.count = A.alloc<int32_t>(n);
+  L.sys = A.alloc<int32_t>(n);
 }
 
 template <int D>
@@ -368,13 +363,12 @@ __global__ void k_point_sys(int n_sys, const int32_t* __restrict__ offs, int32_t
 }
 
 // exclusive scan of n int32 values; returns the total (host-synchronising)
-int64_t scan_total(const int32_t* in, int32_t* out, int n, cudaStream_t s, int32_t* h_pinned) {
+int64_t scan_total(const int32_t* in, int32_t* out, int n, cudaStream_t s, int32_t* h_pinned, Arena& scratch) {
   if (n == 0) return 0;
   size_t bytes = 0;
   DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, n, s));
-  void* tmp = dalloc<char>(bytes, s);
+  void* tmp = scratch.alloc_bytes(bytes);
   DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, bytes, in, out, n, s));
-  dfree(tmp, s);
   DMK_CUDA_TRY(cudaMemcpyAsync(h_pinned, out + (n - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   DMK_CUDA_TRY(cudaMemcpyAsync(h_pinned + 1, in + (n - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   DMK_CUDA_TRY(cudaStreamSynchronize(s));
@@ -394,22 +388,25 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   const int B = 256;
   const double lo0 = p.opts.box_lo[0], lo1 = p.opts.box_lo[1], lo2 = D == 3 ? p.opts.box_lo[2] : 0.0;
 
-  int32_t* h_pin = nullptr;
-  DMK_CUDA_TRY(cudaMallocHost(&h_pin, 4 * sizeof(int32_t)));
-  struct PinGuard { int32_t* q; ~PinGuard() { cudaFreeHost(q); } } pin_guard{h_pin};
+  int32_t* h_pin = pinned_slot();
+  struct PinGuard { int32_t* q; ~PinGuard() { pinned_release(q); } } pin_guard{h_pin};
+  Arena& A = p.arena;                  // the tree's arrays
+  Arena scratch;                       // released when the build returns
+  scratch.s = s;
+  scratch.reserve(static_cast<size_t>(N) * 48 + (size_t(4) << 20));
 
   // system offsets on the device
   std::vector<int32_t> offs32(n_sys + 1);
   for (int k = 0; k <= n_sys; ++k) offs32[k] = static_cast<int32_t>(h_offsets[k]);
-  int32_t* d_offs = dalloc<int32_t>(n_sys + 1, s);
+  int32_t* d_offs = scratch.alloc<int32_t>(n_sys + 1);
   DMK_CUDA_TRY(cudaMemcpyAsync(d_offs, offs32.data(), (n_sys + 1) * sizeof(int32_t),
                                cudaMemcpyHostToDevice, s));
 
   // ---- keys and sort -------------------------------------------------------
-  uint64_t* key_in = dalloc<uint64_t>(N, s);
-  uint64_t* skeys = dalloc<uint64_t>(N, s);
-  int32_t* idx_in = dalloc<int32_t>(N, s);
-  T.perm = dalloc<int32_t>(N, s);
+  uint64_t* key_in = scratch.alloc<uint64_t>(N);
+  uint64_t* skeys = scratch.alloc<uint64_t>(N);
+  int32_t* idx_in = scratch.alloc<int32_t>(N);
+  T.perm = A.alloc<int32_t>(N);
   if (N > 0) {
     k_keys<D><<<grid_for(N, B), B, 0, s>>>(N, d_src, lo0, lo1, lo2, T.periodic, M, key_in, idx_in, p.status);
     ++p.launches;
@@ -418,30 +415,26 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
     if (n_sys == 1) {
       DMK_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, bytes, key_in, skeys, idx_in, T.perm,
                                                    static_cast<int>(N), 0, D * M, s));
-      void* tmp = dalloc<char>(bytes, s);
+      void* tmp = scratch.alloc_bytes(bytes);
       DMK_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, bytes, key_in, skeys, idx_in, T.perm,
                                                    static_cast<int>(N), 0, D * M, s));
-      dfree(tmp, s);
     } else {
       DMK_CUDA_TRY(cub::DeviceSegmentedRadixSort::SortPairs(
           nullptr, bytes, key_in, skeys, idx_in, T.perm, static_cast<int>(N), n_sys, d_offs, d_offs + 1,
           0, D * M, s));
-      void* tmp = dalloc<char>(bytes, s);
+      void* tmp = scratch.alloc_bytes(bytes);
       DMK_CUDA_TRY(cub::DeviceSegmentedRadixSort::SortPairs(
           tmp, bytes, key_in, skeys, idx_in, T.perm, static_cast<int>(N), n_sys, d_offs, d_offs + 1,
           0, D * M, s));
-      dfree(tmp, s);
     }
   }
-  dfree(key_in, s);
-  dfree(idx_in, s);
-  T.w = dalloc<double>(N * D, s);
+  T.w = A.alloc<double>(N * D);
   if (N > 0) {
     k_gather_w<D><<<grid_for(N, B), B, 0, s>>>(N, d_src, T.perm, lo0, lo1, lo2, T.periodic, T.w);
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());
   }
-  T.point_sys = dalloc<int32_t>(N, s);
+  T.point_sys = A.alloc<int32_t>(N);
   if (N > 0) {
     int64_t maxn = 0;
     for (int k = 0; k < n_sys; ++k) maxn = std::max<int64_t>(maxn, h_offsets[k + 1] - h_offsets[k]);
@@ -454,34 +447,31 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   // ---- (a) adaptive refinement -------------------------------------------
   LeafArrays cur, nxt;
   int64_t n_leaf = n_sys;
-  alloc_leaves(cur, n_leaf, s);
+  alloc_leaves(cur, n_leaf, A);
   k_init_roots<<<grid_for(n_sys, B), B, 0, s>>>(n_sys, d_offs, cur);
   ++p.launches;
   DMK_CUDA_TRY(cudaGetLastError());
-  int32_t* begin = dalloc<int32_t>(n_sys + 1, s);
+  int32_t* begin = A.alloc<int32_t>(n_sys + 1);
 
   auto refine = [&](const int32_t* flag) -> bool {
-    int32_t* nch = dalloc<int32_t>(n_leaf, s);
-    int32_t* pos = dalloc<int32_t>(n_leaf, s);
+    int32_t* nch = scratch.alloc<int32_t>(n_leaf);
+    int32_t* pos = scratch.alloc<int32_t>(n_leaf);
     k_split_flags<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, p.leaf_capacity, M,
                                                        flag, nch);
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());
-    int64_t total = scan_total(nch, pos, static_cast<int>(n_leaf), s, h_pin);
+    int64_t total = scan_total(nch, pos, static_cast<int>(n_leaf), s, h_pin, scratch);
     bool changed = total != n_leaf;
     if (changed) {
       if (total >= (int64_t(1) << 31)) throw Error{DMK_ERR_NOMEM, "tree too large"};
-      alloc_leaves(nxt, total, s);
+      alloc_leaves(nxt, total, A);
       k_refine<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, nch, pos, nxt, skeys, M);
       ++p.launches;
       DMK_CUDA_TRY(cudaGetLastError());
-      free_leaves(cur, s);
       cur = nxt;
       nxt = LeafArrays();
       n_leaf = total;
     }
-    dfree(nch, s);
-    dfree(pos, s);
     return changed;
   };
 
@@ -489,11 +479,11 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
     if (!refine(nullptr)) break;
 
   // ---- (b) level restriction --------------------------------------------
-  int* d_any = dalloc<int>(1, s);
+  int* d_any = scratch.alloc<int>(1);
   for (int it = 0; it < 4 * M + 8; ++it) {
     k_sys_begin<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), n_sys, cur.sys, begin);
     ++p.launches;
-    int32_t* flag = dalloc<int32_t>(n_leaf, s);
+    int32_t* flag = scratch.alloc<int32_t>(n_leaf);
     DMK_CUDA_TRY(cudaMemsetAsync(flag, 0, n_leaf * sizeof(int32_t), s));
     DMK_CUDA_TRY(cudaMemsetAsync(d_any, 0, sizeof(int), s));
     k_balance<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
@@ -504,10 +494,8 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
     DMK_CUDA_TRY(cudaStreamSynchronize(s));
     bool any = h_pin[2] != 0;
     if (any) refine(flag);
-    dfree(flag, s);
     if (!any) break;
   }
-  dfree(d_any, s);
   k_sys_begin<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), n_sys, cur.sys, begin);
   ++p.launches;
   DMK_CUDA_TRY(cudaGetLastError());
@@ -521,37 +509,36 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   T.sys_leaf_begin = begin;
 
   // ---- near lists ------------------------------------------------------------
-  int32_t* ncount = dalloc<int32_t>(n_leaf, s);
-  T.near_off = dalloc<int32_t>(n_leaf + 1, s);
+  int32_t* ncount = scratch.alloc<int32_t>(n_leaf);
+  T.near_off = A.alloc<int32_t>(n_leaf + 1);
   k_near_count<D><<<grid_for(n_leaf, 128), 128, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
                                                         ncount, p.status);
   ++p.launches;
   DMK_CUDA_TRY(cudaGetLastError());
-  T.n_near = scan_total(ncount, T.near_off, static_cast<int>(n_leaf), s, h_pin);
+  T.n_near = scan_total(ncount, T.near_off, static_cast<int>(n_leaf), s, h_pin, scratch);
   k_set_value<<<1, 1, 0, s>>>(T.near_off + n_leaf, static_cast<int32_t>(T.n_near));
   ++p.launches;
   DMK_CUDA_TRY(cudaGetLastError());
-  T.near_leaf = dalloc<int32_t>(T.n_near, s);
-  T.near_q = dalloc<int32_t>(T.n_near, s);
+  T.near_leaf = A.alloc<int32_t>(T.n_near);
+  T.near_q = A.alloc<int32_t>(T.n_near);
   k_near_fill<D><<<grid_for(n_leaf, 128), 128, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
                                                        T.near_off, T.near_leaf, T.near_q, p.status);
   ++p.launches;
   DMK_CUDA_TRY(cudaGetLastError());
-  dfree(ncount, s);
 
   // ---- tiles, leaf-relative FP32 coordinates, bounding boxes ---------------------
-  T.leaf_ntile = dalloc<int32_t>(n_leaf, s);
-  T.leaf_tile0 = dalloc<int32_t>(n_leaf, s);
+  T.leaf_ntile = A.alloc<int32_t>(n_leaf);
+  T.leaf_tile0 = A.alloc<int32_t>(n_leaf);
   k_tile_count<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur.count, T.leaf_ntile);
   ++p.launches;
   DMK_CUDA_TRY(cudaGetLastError());
-  T.n_tile = static_cast<int32_t>(scan_total(T.leaf_ntile, T.leaf_tile0, static_cast<int>(n_leaf), s, h_pin));
-  T.tile_leaf = dalloc<int32_t>(T.n_tile, s);
-  T.tile_start = dalloc<int32_t>(T.n_tile, s);
-  T.tile_count = dalloc<int32_t>(T.n_tile, s);
-  T.tile_lo = dalloc<float4>(T.n_tile, s);
-  T.tile_hi = dalloc<float4>(T.n_tile, s);
-  T.rel = dalloc<float4>(N, s);
+  T.n_tile = static_cast<int32_t>(scan_total(T.leaf_ntile, T.leaf_tile0, static_cast<int>(n_leaf), s, h_pin, scratch));
+  T.tile_leaf = A.alloc<int32_t>(T.n_tile);
+  T.tile_start = A.alloc<int32_t>(T.n_tile);
+  T.tile_count = A.alloc<int32_t>(T.n_tile);
+  T.tile_lo = A.alloc<float4>(T.n_tile);
+  T.tile_hi = A.alloc<float4>(T.n_tile);
+  T.rel = A.alloc<float4>(N);
   k_tile_fill<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur.start, cur.count, T.leaf_tile0,
                                                 T.tile_leaf, T.tile_start, T.tile_count);
   ++p.launches;
@@ -563,8 +550,6 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());
   }
-  dfree(skeys, s);
-  dfree(d_offs, s);
 }
 
 }  // namespace
@@ -575,26 +560,9 @@ void build_tree(Plan& p, const double* d_src, const int64_t* h_offsets) {
 }
 
 void free_tree(DeviceTree& t, cudaStream_t s) {
-  dfree(t.perm, s);
-  dfree(t.w, s);
-  dfree(t.rel, s);
-  dfree(t.point_sys, s);
-  dfree(t.leaf_anchor, s);
-  dfree(t.leaf_level, s);
-  dfree(t.leaf_start, s);
-  dfree(t.leaf_count, s);
-  dfree(t.leaf_sys, s);
-  dfree(t.sys_leaf_begin, s);
-  dfree(t.near_off, s);
-  dfree(t.near_leaf, s);
-  dfree(t.near_q, s);
-  dfree(t.tile_leaf, s);
-  dfree(t.tile_start, s);
-  dfree(t.tile_count, s);
-  dfree(t.tile_lo, s);
-  dfree(t.tile_hi, s);
-  dfree(t.leaf_tile0, s);
-  dfree(t.leaf_ntile, s);
+  // the arrays live in the plan's arena, which the plan releases
+  (void)s;
+  t = DeviceTree();
 }
 
 }  // namespace dmk
