@@ -122,14 +122,16 @@ __device__ inline int32_t lower_bound_key(const uint64_t* __restrict__ keys, int
   return lo;
 }
 
+// child j of leaf i of `in` (j = 0 only if the leaf is not split) written at
+// position pos[i] + j of `out`; a child's point range is found by two
+// independent binary searches in the leaf's sorted keys
 template <int D>
-__global__ void k_refine(int n, LeafArrays in, const int32_t* __restrict__ nchild,
-                         const int32_t* __restrict__ pos, LeafArrays out,
-                         const uint64_t* __restrict__ skeys, int M) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int32_t p = pos[i];
+__device__ inline void refine_child(int i, int j, const LeafArrays& in, const int32_t* __restrict__ nchild,
+                                    const int32_t* __restrict__ pos, const LeafArrays& out,
+                                    const uint64_t* __restrict__ skeys, int M) {
+  const int32_t p = pos[i];
   if (nchild[i] == 1) {
+    if (j != 0) return;
     out.anchor[p] = in.anchor[i];
     out.level[p] = in.level[i];
     out.start[p] = in.start[i];
@@ -137,22 +139,71 @@ __global__ void k_refine(int n, LeafArrays in, const int32_t* __restrict__ nchil
     out.sys[p] = in.sys[i];
     return;
   }
-  int lev = in.level[i];
-  int sh = D * (M - lev - 1);
-  uint64_t span = uint64_t(1) << sh;
-  int32_t s0 = in.start[i], s1 = in.start[i] + in.count[i];
-  int32_t b = s0;
-  for (int j = 0; j < (1 << D); ++j) {
-    uint64_t ca = in.anchor[i] + (uint64_t(j) << sh);
-    int32_t e = (j == (1 << D) - 1) ? s1 : lower_bound_key(skeys, b, s1, ca + span);
-    out.anchor[p + j] = ca;
-    out.level[p + j] = lev + 1;
-    out.start[p + j] = b;
-    out.count[p + j] = e - b;
-    out.sys[p + j] = in.sys[i];
-    b = e;
-  }
+  const int lev = in.level[i];
+  const int sh = D * (M - lev - 1);
+  const uint64_t span = uint64_t(1) << sh;
+  const int32_t s0 = in.start[i], s1 = in.start[i] + in.count[i];
+  const uint64_t ca = in.anchor[i] + (uint64_t(j) << sh);
+  const int32_t b = (j == 0) ? s0 : lower_bound_key(skeys, s0, s1, ca);
+  const int32_t e = (j == (1 << D) - 1) ? s1 : lower_bound_key(skeys, s0, s1, ca + span);
+  out.anchor[p + j] = ca;
+  out.level[p + j] = lev + 1;
+  out.start[p + j] = b;
+  out.count[p + j] = e - b;
+  out.sys[p + j] = in.sys[i];
 }
+
+// one thread per (leaf, child)
+template <int D>
+__global__ void k_refine(int n, LeafArrays in, const int32_t* __restrict__ nchild,
+                         const int32_t* __restrict__ pos, LeafArrays out,
+                         const uint64_t* __restrict__ skeys, int M) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int i = static_cast<int>(t >> D), j = static_cast<int>(t & ((1 << D) - 1));
+  if (i >= n) return;
+  refine_child<D>(i, j, in, nchild, pos, out, skeys, M);
+}
+
+// The same two steps with the leaf count in device memory, so that levels are
+// chained without a host round trip: arrays have a capacity cap >= count,
+// slots beyond the count get no children, and the last leaf writes the next
+// level's count.
+template <int D>
+__global__ void k_split_flags_dev(int cap, const int32_t* __restrict__ d_n, LeafArrays L, int ns, int M,
+                                  int32_t* __restrict__ nchild) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cap) return;
+  const int n = min(*d_n, cap);
+  nchild[i] = (i < n) ? ((L.count[i] > ns && L.level[i] < M) ? (1 << D) : 1) : 0;
+}
+
+template <int D>
+__global__ void k_refine_dev(int cap, int cap_out, const int32_t* __restrict__ d_n, LeafArrays in,
+                             const int32_t* __restrict__ nchild, const int32_t* __restrict__ pos,
+                             LeafArrays out, const uint64_t* __restrict__ skeys, int M,
+                             int32_t* __restrict__ d_n_out, int* __restrict__ status) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int i = static_cast<int>(t >> D), j = static_cast<int>(t & ((1 << D) - 1));
+  if (i >= cap) return;
+  const int n = min(*d_n, cap);
+  if (i >= n) return;
+  if (pos[i] + nchild[i] > cap_out) {          // cannot happen by the capacity bound; guarded anyway
+    if (j == 0) atomicOr(status, ST_TREE_INCONSISTENT);
+    if (i == n - 1 && j == 0) *d_n_out = min(pos[i], cap_out);
+    return;
+  }
+  if (i == n - 1 && j == 0) *d_n_out = pos[i] + nchild[i];
+  refine_child<D>(i, j, in, nchild, pos, out, skeys, M);
+}
+
+// total of an exclusive scan: out[n] = out[n - 1] + in[n - 1] (and *copy if given)
+__global__ void k_scan_total(int n, const int32_t* __restrict__ in, int32_t* __restrict__ out,
+                             int32_t* __restrict__ copy) {
+  const int32_t v = out[n - 1] + in[n - 1];
+  out[n] = v;
+  if (copy) *copy = v;
+}
+
 
 __global__ void k_sys_begin(int n, int n_sys, const int32_t* __restrict__ sys, int32_t* __restrict__ begin) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -187,111 +238,140 @@ __device__ inline bool neighbour(const int64_t* c, const int* dl, int lev, int p
   return true;
 }
 
+// Level restriction check, one warp per leaf and one lane per neighbour
+// direction: a touching leaf more than one level coarser is flagged for a split.
 template <int D>
 __global__ void k_balance(int n, LeafArrays L, const int32_t* __restrict__ begin, int M, int periodic,
                           int32_t* __restrict__ flag, int* __restrict__ any) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int lev = L.level[i];
+  const int i = static_cast<int>((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int k = threadIdx.x & 31;
+  const int ndir = (D == 3) ? 27 : 9;
+  if (i >= n || k >= ndir) return;
+  const int lev = L.level[i];
   if (lev < 2) return;
+  int dl[3] = {k % 3 - 1, (k / 3) % 3 - 1, D == 3 ? (k / 9) % 3 - 1 : 0};
+  if (dl[0] == 0 && dl[1] == 0 && dl[2] == 0) return;
   int64_t c[3];
   leaf_coords<D>(L.anchor[i], lev, M, c);
-  int32_t b = begin[L.sys[i]], e = begin[L.sys[i] + 1];
-  const int ndir = (D == 3) ? 27 : 9;
-  for (int k = 0; k < ndir; ++k) {
-    int dl[3] = {k % 3 - 1, (k / 3) % 3 - 1, (k / 9) % 3 - 1};
-    if (dl[0] == 0 && dl[1] == 0 && (D == 2 || dl[2] == 0)) continue;
-    int64_t nb[3];
-    int q[3];
-    if (!neighbour<D>(c, dl, lev, periodic, nb, q)) continue;
-    int32_t X = find_leaf(L.anchor, b, e, box_anchor<D>(nb, lev, M));
-    if (L.level[X] < lev - 1) {
-      flag[X] = 1;
-      *any = 1;
-    }
+  int64_t nb[3];
+  int q[3];
+  if (!neighbour<D>(c, dl, lev, periodic, nb, q)) return;
+  const int32_t b = begin[L.sys[i]], e = begin[L.sys[i] + 1];
+  const int32_t X = find_leaf(L.anchor, b, e, box_anchor<D>(nb, lev, M));
+  if (L.level[X] < lev - 1) {
+    flag[X] = 1;
+    *any = 1;
   }
 }
 
-// Enumerates the near list of leaf i; calls emit(X, qpacked) for each entry.
-template <int D, typename F>
-__device__ inline int near_entries(int i, const LeafArrays& L, const int32_t* __restrict__ begin, int M,
-                                   int periodic, int* status, F emit) {
-  int lev = L.level[i];
+// Near lists, one warp per leaf and one lane per neighbour direction (the
+// centre direction is the leaf itself).  Each lane finds the leaves touching
+// its neighbour box (one at the same or a coarser level, or the up to 4 finer
+// children adjacent to the leaf); entries already found in an earlier
+// direction are dropped, so the list is that of a sequential walk over the
+// directions in order.  Entries go to a fixed-stride scratch (kMaxNear per
+// leaf) and are compacted after the scan of the counts.
+template <int D>
+__global__ void __launch_bounds__(256) k_near_warp(int n, LeafArrays L, const int32_t* __restrict__ begin,
+                                                   int M, int periodic, int32_t* __restrict__ sl,
+                                                   int32_t* __restrict__ sq, int32_t* __restrict__ cnt_out,
+                                                   int* status) {
+  __shared__ int32_t s_leaf[8][32][4];
+  __shared__ int32_t s_nc[8][32];
+  __shared__ int32_t s_q[8][32];
+  const int wid = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int i = static_cast<int>((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  if (i >= n) return;                                  // whole warps leave together
+  const int ndir = (D == 3) ? 27 : 9;
+  const int lev = L.level[i];
   int64_t c[3];
   leaf_coords<D>(L.anchor[i], lev, M, c);
-  int32_t b = begin[L.sys[i]], e = begin[L.sys[i] + 1];
-  int32_t got_leaf[kMaxNear];
-  int32_t got_q[kMaxNear];
-  int cnt = 0;
-  const int ndir = (D == 3) ? 27 : 9;
-  for (int k = 0; k < ndir; ++k) {
+  const int32_t b = begin[L.sys[i]], e = begin[L.sys[i] + 1];
+  int nc = 0;
+  int32_t qp = 0;
+  int32_t cand[4] = {-1, -1, -1, -1};
+  if (k < ndir) {
     int dl[3] = {k % 3 - 1, (k / 3) % 3 - 1, D == 3 ? (k / 9) % 3 - 1 : 0};
     int64_t nb[3];
     int q[3];
-    if (!neighbour<D>(c, dl, lev, periodic, nb, q)) continue;
-    int32_t qp = pack_q(q[0], q[1], D == 3 ? q[2] : 0);
-    int32_t X = find_leaf(L.anchor, b, e, box_anchor<D>(nb, lev, M));
-    int32_t cand[4];
-    int nc = 0;
-    if (L.level[X] <= lev) {
-      cand[nc++] = X;
-    } else {
-      for (int j = 0; j < (1 << D); ++j) {
-        int o[3] = {j & 1, (j >> 1) & 1, (j >> 2) & 1};
-        bool ok = true;
-        for (int a = 0; a < D; ++a) {
-          if (dl[a] == 1 && o[a] != 0) ok = false;
-          if (dl[a] == -1 && o[a] != 1) ok = false;
+    if (neighbour<D>(c, dl, lev, periodic, nb, q)) {
+      qp = pack_q(q[0], q[1], D == 3 ? q[2] : 0);
+      const int32_t X = find_leaf(L.anchor, b, e, box_anchor<D>(nb, lev, M));
+      if (L.level[X] <= lev) {
+        cand[nc++] = X;
+      } else {
+        for (int j = 0; j < (1 << D); ++j) {
+          const int o[3] = {j & 1, (j >> 1) & 1, (j >> 2) & 1};
+          bool ok = true;
+          for (int a = 0; a < D; ++a) {
+            if (dl[a] == 1 && o[a] != 0) ok = false;
+            if (dl[a] == -1 && o[a] != 1) ok = false;
+          }
+          if (!ok) continue;
+          int64_t ch[3];
+          for (int a = 0; a < D; ++a) ch[a] = 2 * nb[a] + o[a];
+          const uint64_t ca = box_anchor<D>(ch, lev + 1, M);
+          const int32_t Y = find_leaf(L.anchor, b, e, ca);
+          if (L.level[Y] != lev + 1 || L.anchor[Y] != ca) {
+            atomicOr(status, ST_TREE_INCONSISTENT);
+            continue;
+          }
+          if (nc < 4) cand[nc++] = Y;
         }
-        if (!ok) continue;
-        int64_t ch[3];
-        for (int a = 0; a < D; ++a) ch[a] = 2 * nb[a] + o[a];
-        uint64_t ca = box_anchor<D>(ch, lev + 1, M);
-        int32_t Y = find_leaf(L.anchor, b, e, ca);
-        if (L.level[Y] != lev + 1 || L.anchor[Y] != ca) {
-          atomicOr(status, ST_TREE_INCONSISTENT);
-          continue;
-        }
-        if (nc < 4) cand[nc++] = Y;
       }
-    }
-    for (int m = 0; m < nc; ++m) {
-      bool dup = false;
-      for (int r = 0; r < cnt; ++r)
-        if (got_leaf[r] == cand[m] && got_q[r] == qp) dup = true;
-      if (dup) continue;
-      if (cnt >= kMaxNear) {
-        atomicOr(status, ST_NEAR_OVERFLOW);
-        continue;
-      }
-      got_leaf[cnt] = cand[m];
-      got_q[cnt] = qp;
-      emit(cnt, cand[m], qp);
-      ++cnt;
     }
   }
-  return cnt;
+  s_nc[wid][k] = nc;
+  s_q[wid][k] = qp;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) s_leaf[wid][k][m] = cand[m];
+  __syncwarp();
+  // keep the candidates not found in an earlier direction
+  uint32_t keep = 0u;
+  for (int m = 0; m < nc; ++m) {
+    bool dup = false;
+    for (int d2 = 0; d2 < k && !dup; ++d2) {
+      if (s_q[wid][d2] != qp) continue;
+      for (int m2 = 0; m2 < s_nc[wid][d2]; ++m2)
+        if (s_leaf[wid][d2][m2] == cand[m]) dup = true;
+    }
+    if (!dup) keep |= 1u << m;
+  }
+  const int kept = __popc(keep);
+  int off = kept;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, off, o);
+    if (k >= o) off += v;
+  }
+  const int total = __shfl_sync(0xffffffffu, off, 31);
+  off -= kept;
+  for (int m = 0; m < nc; ++m) {
+    if (!(keep & (1u << m))) continue;
+    if (off < kMaxNear) {
+      sl[static_cast<int64_t>(i) * kMaxNear + off] = cand[m];
+      sq[static_cast<int64_t>(i) * kMaxNear + off] = qp;
+    }
+    ++off;
+  }
+  if (k == 0) {
+    if (total > kMaxNear) atomicOr(status, ST_NEAR_OVERFLOW);
+    cnt_out[i] = min(total, kMaxNear);
+  }
 }
 
-template <int D>
-__global__ void k_near_count(int n, LeafArrays L, const int32_t* __restrict__ begin, int M, int periodic,
-                             int32_t* __restrict__ cnt_out, int* status) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// scratch lists (kMaxNear stride) -> CSR, one warp per leaf
+__global__ void k_near_compact(int n, const int32_t* __restrict__ cnt, const int32_t* __restrict__ off,
+                               const int32_t* __restrict__ sl, const int32_t* __restrict__ sq,
+                               int32_t* __restrict__ nl, int32_t* __restrict__ nq) {
+  const int i = static_cast<int>((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int k = threadIdx.x & 31;
   if (i >= n) return;
-  cnt_out[i] = near_entries<D>(i, L, begin, M, periodic, status, [](int, int32_t, int32_t) {});
-}
-
-template <int D>
-__global__ void k_near_fill(int n, LeafArrays L, const int32_t* __restrict__ begin, int M, int periodic,
-                            const int32_t* __restrict__ off, int32_t* __restrict__ nl,
-                            int32_t* __restrict__ nq, int* status) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int32_t o = off[i];
-  near_entries<D>(i, L, begin, M, periodic, status, [&](int r, int32_t X, int32_t qp) {
-    nl[o + r] = X;
-    nq[o + r] = qp;
-  });
+  const int c = cnt[i], o = off[i];
+  for (int r = k; r < c; r += 32) {
+    nl[o + r] = sl[static_cast<int64_t>(i) * kMaxNear + r];
+    nq[o + r] = sq[static_cast<int64_t>(i) * kMaxNear + r];
+  }
 }
 
 __global__ void k_tile_count(int n, const int32_t* __restrict__ count, int32_t* __restrict__ ntile) {
@@ -314,16 +394,17 @@ __global__ void k_tile_fill(int n, const int32_t* __restrict__ start, const int3
   }
 }
 
-// one warp per tile: leaf-relative FP32 coordinates and the tile bounding box
+// one warp per tile (tiles below the device count *d_ntile, the grid covers a
+// capacity): leaf-relative FP32 coordinates and the tile bounding box
 template <int D>
-__global__ void k_rel_bbox(int n_tile, int64_t N, const int32_t* __restrict__ tleaf,
+__global__ void k_rel_bbox(const int32_t* __restrict__ d_ntile, int64_t N, const int32_t* __restrict__ tleaf,
                            const int32_t* __restrict__ tstart, const int32_t* __restrict__ tcount,
                            const uint64_t* __restrict__ anchor, const int32_t* __restrict__ level,
                            const double* __restrict__ w, int M, float4* __restrict__ rel,
                            float4* __restrict__ tlo, float4* __restrict__ thi) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
-  if (warp >= n_tile) return;
+  if (warp >= *d_ntile) return;
   int leaf = tleaf[warp];
   int lev = level[leaf];
   int64_t c[3] = {0, 0, 0};
@@ -360,19 +441,6 @@ __global__ void k_point_sys(int n_sys, const int32_t* __restrict__ offs, int32_t
   int k = blockIdx.y;
   int64_t i = offs[k] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k < n_sys && i < offs[k + 1]) ps[i] = k;
-}
-
-// exclusive scan of n int32 values; returns the total (host-synchronising)
-int64_t scan_total(const int32_t* in, int32_t* out, int n, cudaStream_t s, int32_t* h_pinned, Arena& scratch) {
-  if (n == 0) return 0;
-  size_t bytes = 0;
-  DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, n, s));
-  void* tmp = scratch.alloc_bytes(bytes);
-  DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, bytes, in, out, n, s));
-  DMK_CUDA_TRY(cudaMemcpyAsync(h_pinned, out + (n - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  DMK_CUDA_TRY(cudaMemcpyAsync(h_pinned + 1, in + (n - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-  DMK_CUDA_TRY(cudaStreamSynchronize(s));
-  return static_cast<int64_t>(h_pinned[0]) + h_pinned[1];
 }
 
 template <int D>
@@ -445,56 +513,87 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   }
 
   // ---- (a) adaptive refinement -------------------------------------------
+  // Levels are chained on the device (leaf counts in device memory, arrays
+  // sized by a capacity) and the host reads the count every kChain levels.
+  // Capacity: a split leaf holds more than n_s points, so at most
+  // N / (n_s + 1) leaves split per level, each adding 2^D - 1 leaves.
+  constexpr int kChain = 4;
   LeafArrays cur, nxt;
-  int64_t n_leaf = n_sys;
-  alloc_leaves(cur, n_leaf, A);
+  alloc_leaves(cur, n_sys, A);
   k_init_roots<<<grid_for(n_sys, B), B, 0, s>>>(n_sys, d_offs, cur);
   ++p.launches;
   DMK_CUDA_TRY(cudaGetLastError());
   int32_t* begin = A.alloc<int32_t>(n_sys + 1);
-
-  auto refine = [&](const int32_t* flag) -> bool {
-    int32_t* nch = scratch.alloc<int32_t>(n_leaf);
-    int32_t* pos = scratch.alloc<int32_t>(n_leaf);
-    k_split_flags<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, p.leaf_capacity, M,
-                                                       flag, nch);
-    ++p.launches;
-    DMK_CUDA_TRY(cudaGetLastError());
-    int64_t total = scan_total(nch, pos, static_cast<int>(n_leaf), s, h_pin, scratch);
-    bool changed = total != n_leaf;
-    if (changed) {
-      if (total >= (int64_t(1) << 31)) throw Error{DMK_ERR_NOMEM, "tree too large"};
-      alloc_leaves(nxt, total, A);
-      k_refine<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, nch, pos, nxt, skeys, M);
-      ++p.launches;
+  int32_t* d_cnt = scratch.alloc<int32_t>(M + 2);          // leaf count after each level
+  k_set_value<<<1, 1, 0, s>>>(d_cnt, n_sys);
+  ++p.launches;
+  const int64_t grow = ((int64_t(1) << D) - 1) * (N / (int64_t(p.leaf_capacity) + 1) + 1);
+  int64_t cap = n_sys;
+  int64_t n_leaf = n_sys;
+  for (int lev = 0; lev <= M;) {
+    for (int k = 0; k < kChain && lev <= M; ++k, ++lev) {
+      const int64_t cap_out = cap + grow;
+      if (cap_out >= (int64_t(1) << 31)) throw Error{DMK_ERR_NOMEM, "tree too large"};
+      int32_t* nch = scratch.alloc<int32_t>(cap);
+      int32_t* pos = scratch.alloc<int32_t>(cap);
+      k_split_flags_dev<D><<<grid_for(cap, B), B, 0, s>>>(static_cast<int>(cap), d_cnt + lev, cur,
+                                                           p.leaf_capacity, M, nch);
+      size_t bytes = 0;
+      DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, nch, pos, static_cast<int>(cap), s));
+      DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(scratch.alloc_bytes(bytes), bytes, nch, pos,
+                                                 static_cast<int>(cap), s));
+      alloc_leaves(nxt, cap_out, A);
+      k_refine_dev<D><<<grid_for(cap << D, B), B, 0, s>>>(static_cast<int>(cap), static_cast<int>(cap_out),
+                                                     d_cnt + lev, cur, nch, pos, nxt, skeys, M, d_cnt + lev + 1,
+                                                     p.status);
+      p.launches += 2;
       DMK_CUDA_TRY(cudaGetLastError());
       cur = nxt;
       nxt = LeafArrays();
-      n_leaf = total;
+      cap = cap_out;
     }
-    return changed;
-  };
-
-  for (int it = 0; it <= M; ++it)
-    if (!refine(nullptr)) break;
+    // converged when the last chained level split nothing
+    DMK_CUDA_TRY(cudaMemcpyAsync(h_pin, d_cnt + lev - 1, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    DMK_CUDA_TRY(cudaStreamSynchronize(s));
+    n_leaf = h_pin[1];
+    if (h_pin[0] == h_pin[1] || lev > M) break;
+  }
 
   // ---- (b) level restriction --------------------------------------------
+  // one host round trip per round: the flags, their scan and the flag of any
+  // violation are read together
   int* d_any = scratch.alloc<int>(1);
   for (int it = 0; it < 4 * M + 8; ++it) {
     k_sys_begin<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), n_sys, cur.sys, begin);
-    ++p.launches;
     int32_t* flag = scratch.alloc<int32_t>(n_leaf);
+    int32_t* nch = scratch.alloc<int32_t>(n_leaf);
+    int32_t* pos = scratch.alloc<int32_t>(n_leaf + 1);
     DMK_CUDA_TRY(cudaMemsetAsync(flag, 0, n_leaf * sizeof(int32_t), s));
     DMK_CUDA_TRY(cudaMemsetAsync(d_any, 0, sizeof(int), s));
-    k_balance<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
-                                                   flag, d_any);
-    ++p.launches;
+    k_balance<D><<<grid_for(n_leaf * 32, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
+                                                        flag, d_any);
+    k_split_flags<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, p.leaf_capacity, M,
+                                                       flag, nch);
+    size_t bytes = 0;
+    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, nch, pos, static_cast<int>(n_leaf), s));
+    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(scratch.alloc_bytes(bytes), bytes, nch, pos,
+                                               static_cast<int>(n_leaf), s));
+    k_scan_total<<<1, 1, 0, s>>>(static_cast<int>(n_leaf), nch, pos, nullptr);
+    p.launches += 4;
     DMK_CUDA_TRY(cudaGetLastError());
+    DMK_CUDA_TRY(cudaMemcpyAsync(h_pin, pos + n_leaf, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     DMK_CUDA_TRY(cudaMemcpyAsync(h_pin + 2, d_any, sizeof(int), cudaMemcpyDeviceToHost, s));
     DMK_CUDA_TRY(cudaStreamSynchronize(s));
-    bool any = h_pin[2] != 0;
-    if (any) refine(flag);
-    if (!any) break;
+    if (h_pin[2] == 0) break;
+    const int64_t total = h_pin[0];
+    if (total >= (int64_t(1) << 31)) throw Error{DMK_ERR_NOMEM, "tree too large"};
+    alloc_leaves(nxt, total, A);
+    k_refine<D><<<grid_for(n_leaf << D, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, nch, pos, nxt, skeys, M);
+    ++p.launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+    cur = nxt;
+    nxt = LeafArrays();
+    n_leaf = total;
   }
   k_sys_begin<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), n_sys, cur.sys, begin);
   ++p.launches;
@@ -508,48 +607,60 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   T.leaf_sys = cur.sys;
   T.sys_leaf_begin = begin;
 
-  // ---- near lists ------------------------------------------------------------
+  // ---- near lists (at most kMaxNear entries per leaf: no host round trip) ------
   int32_t* ncount = scratch.alloc<int32_t>(n_leaf);
+  int32_t* nsl = scratch.alloc<int32_t>(n_leaf * kMaxNear);
+  int32_t* nsq = scratch.alloc<int32_t>(n_leaf * kMaxNear);
   T.near_off = A.alloc<int32_t>(n_leaf + 1);
-  k_near_count<D><<<grid_for(n_leaf, 128), 128, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
-                                                        ncount, p.status);
-  ++p.launches;
+  k_near_warp<D><<<grid_for(n_leaf * 32, 256), 256, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
+                                                            nsl, nsq, ncount, p.status);
+  {
+    size_t bytes = 0;
+    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, ncount, T.near_off, static_cast<int>(n_leaf), s));
+    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(scratch.alloc_bytes(bytes), bytes, ncount, T.near_off,
+                                               static_cast<int>(n_leaf), s));
+  }
+  k_scan_total<<<1, 1, 0, s>>>(static_cast<int>(n_leaf), ncount, T.near_off, nullptr);
+  T.near_leaf = A.alloc<int32_t>(n_leaf * kMaxNear);
+  T.near_q = A.alloc<int32_t>(n_leaf * kMaxNear);
+  k_near_compact<<<grid_for(n_leaf * 32, 256), 256, 0, s>>>(static_cast<int>(n_leaf), ncount, T.near_off, nsl,
+                                                           nsq, T.near_leaf, T.near_q);
+  p.launches += 3;
   DMK_CUDA_TRY(cudaGetLastError());
-  T.n_near = scan_total(ncount, T.near_off, static_cast<int>(n_leaf), s, h_pin, scratch);
-  k_set_value<<<1, 1, 0, s>>>(T.near_off + n_leaf, static_cast<int32_t>(T.n_near));
-  ++p.launches;
-  DMK_CUDA_TRY(cudaGetLastError());
-  T.near_leaf = A.alloc<int32_t>(T.n_near);
-  T.near_q = A.alloc<int32_t>(T.n_near);
-  k_near_fill<D><<<grid_for(n_leaf, 128), 128, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
-                                                       T.near_off, T.near_leaf, T.near_q, p.status);
-  ++p.launches;
-  DMK_CUDA_TRY(cudaGetLastError());
+  DMK_CUDA_TRY(cudaMemcpyAsync(h_pin + 4, T.near_off + n_leaf, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
 
   // ---- tiles, leaf-relative FP32 coordinates, bounding boxes ---------------------
+  // at most N / kTile + n_leaf tiles: allocated by that bound, counted on the device
+  const int64_t tile_cap = N / kTile + n_leaf;
   T.leaf_ntile = A.alloc<int32_t>(n_leaf);
-  T.leaf_tile0 = A.alloc<int32_t>(n_leaf);
+  T.leaf_tile0 = A.alloc<int32_t>(n_leaf + 1);
+  int32_t* d_ntile = scratch.alloc<int32_t>(1);
   k_tile_count<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur.count, T.leaf_ntile);
-  ++p.launches;
-  DMK_CUDA_TRY(cudaGetLastError());
-  T.n_tile = static_cast<int32_t>(scan_total(T.leaf_ntile, T.leaf_tile0, static_cast<int>(n_leaf), s, h_pin, scratch));
-  T.tile_leaf = A.alloc<int32_t>(T.n_tile);
-  T.tile_start = A.alloc<int32_t>(T.n_tile);
-  T.tile_count = A.alloc<int32_t>(T.n_tile);
-  T.tile_lo = A.alloc<float4>(T.n_tile);
-  T.tile_hi = A.alloc<float4>(T.n_tile);
+  {
+    size_t bytes = 0;
+    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, T.leaf_ntile, T.leaf_tile0,
+                                               static_cast<int>(n_leaf), s));
+    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(scratch.alloc_bytes(bytes), bytes, T.leaf_ntile, T.leaf_tile0,
+                                               static_cast<int>(n_leaf), s));
+  }
+  k_scan_total<<<1, 1, 0, s>>>(static_cast<int>(n_leaf), T.leaf_ntile, T.leaf_tile0, d_ntile);
+  T.tile_leaf = A.alloc<int32_t>(tile_cap);
+  T.tile_start = A.alloc<int32_t>(tile_cap);
+  T.tile_count = A.alloc<int32_t>(tile_cap);
+  T.tile_lo = A.alloc<float4>(tile_cap);
+  T.tile_hi = A.alloc<float4>(tile_cap);
   T.rel = A.alloc<float4>(N);
   k_tile_fill<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur.start, cur.count, T.leaf_tile0,
                                                 T.tile_leaf, T.tile_start, T.tile_count);
-  ++p.launches;
+  k_rel_bbox<D><<<grid_for(tile_cap * 32, 256), 256, 0, s>>>(
+      d_ntile, N, T.tile_leaf, T.tile_start, T.tile_count, T.leaf_anchor, T.leaf_level, T.w, M, T.rel,
+      T.tile_lo, T.tile_hi);
+  p.launches += 4;
   DMK_CUDA_TRY(cudaGetLastError());
-  if (T.n_tile > 0) {
-    k_rel_bbox<D><<<grid_for(int64_t(T.n_tile) * 32, 256), 256, 0, s>>>(
-        T.n_tile, N, T.tile_leaf, T.tile_start, T.tile_count, T.leaf_anchor, T.leaf_level, T.w, M, T.rel,
-        T.tile_lo, T.tile_hi);
-    ++p.launches;
-    DMK_CUDA_TRY(cudaGetLastError());
-  }
+  DMK_CUDA_TRY(cudaMemcpyAsync(h_pin + 5, d_ntile, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DMK_CUDA_TRY(cudaStreamSynchronize(s));
+  T.n_near = h_pin[4];
+  T.n_tile = h_pin[5];
 }
 
 }  // namespace
