@@ -158,6 +158,7 @@ def run_reference(args):
 
 # ------------------------------------------------------- other workloads
 def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
+    from paper_2509_21471_gb300 import dist as pdist
     """The remaining workloads of the hot path, each timed per step (plan +
     eval, or forward + backward) and per near-field evaluation (plan reused),
     in both precisions.  Reported beside the headline; not part of it."""
@@ -190,7 +191,7 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
 
     res = {}
     # 3D clustered, eps = 1e-10 (MIXED takes FP64 pair terms below eps = 2e-7)
-    x, f = wl.clustered_3d(n=args.n, sigma=0.02, seed_index=1 + 100 * rank)
+    x, f = wl.clustered_3d(n=args.n, sigma=0.02, seed_index=pdist.seed_index(1, rank))
     xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
     ud = torch.empty_like(fd)
     r = measure(lambda prec: dmk.Plan(xd, eps=1e-10, precision=prec), lambda p: p.eval(fd, out=ud), len(x), k_mixed)
@@ -200,7 +201,7 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
     del xd, fd, ud
 
     # 2D periodic unit square, Stokeslet + stresslet (k = 0 term included), eps = 1e-8
-    x, f, g, nrm = wl.periodic_2d(n=args.n, seed_index=2 + 100 * rank)
+    x, f, g, nrm = wl.periodic_2d(n=args.n, seed_index=pdist.seed_index(2, rank))
     xd, fd, gd, nd = (torch.as_tensor(a, device="cuda") for a in (x, f, g, nrm))
     ud = torch.empty_like(fd)
     r = measure(lambda prec: dmk.Plan(xd, eps=1e-8, periodic=True, kernels=dmk.STOKESLET | dmk.STRESSLET,
@@ -212,7 +213,7 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
     del xd, fd, gd, nd, ud
 
     # 256 independent 3D systems, 16 force columns, one plan and one launch
-    x, F, offs = wl.batched_3d(seed_index=3 + 100 * rank)
+    x, F, offs = wl.batched_3d(seed_index=pdist.seed_index(3, rank))
     xd, Fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(F, device="cuda")
     Ud = torch.empty_like(Fd)
     r = measure(lambda prec: dmk.Plan(xd, eps=1e-6, precision=prec, n_rhs=16, offsets=offs),
@@ -223,8 +224,8 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
     del xd, Fd, Ud
 
     # differentiation: 3D periodic, N = 2e5, L = 1/2 |u - u_tgt|^2, gradients w.r.t. x and f
-    x, f = wl.periodic_3d(n=200_000, seed_index=4 + 100 * rank)
-    rng = wl.rng_for(4 + 100 * rank, extra=1)
+    x, f = wl.periodic_3d(n=200_000, seed_index=pdist.seed_index(4, rank))
+    rng = wl.rng_for(pdist.seed_index(4, rank), extra=1)
     xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
     u_tgt = dmk.eval(xd, torch.as_tensor(f + 0.1 * rng.standard_normal(f.shape), device="cuda"),
                      eps=1e-8, periodic=True, precision=dmk.FP64)
@@ -250,29 +251,20 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
 def run_ours(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    from paper_2509_21471_gb300 import dist as pdist
+    world = pdist.world_size()
+    rank = pdist.rank()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
+    pdist.init("nccl")
 
     from paper_2509_21471_gb300 import dmk, workloads as wl
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    barrier = pdist.barrier
+    max_over_ranks = pdist.max_over_ranks
 
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    x_np, f_np = wl.clustered_3d(n=args.n, sigma=0.02, seed_index=1 + 100 * rank)
+    x_np, f_np = wl.clustered_3d(n=args.n, sigma=0.02, seed_index=pdist.seed_index(1))
     N = x_np.shape[0]
     x_h = torch.from_numpy(x_np).pin_memory()
     f_h = torch.from_numpy(f_np).pin_memory()
@@ -319,7 +311,7 @@ def run_ours(args):
     ms_mixed = timed(lambda: step(dmk.MIXED), args.steps)
     clocks = sampler.stop()
     t_mixed = max_over_ranks(sum(ms_mixed) / 1e3)
-    value = world * N * args.steps / t_mixed
+    value = pdist.job_rate(N, args.steps, t_mixed)
 
     ms_fp64 = timed(lambda: step(dmk.FP64), max(1, args.steps // 2))
     t_fp64 = max_over_ranks(sum(ms_fp64) / 1e3) / len(ms_fp64)
@@ -353,7 +345,7 @@ def run_ours(args):
         u_h.copy_(u_d, non_blocking=True)
     ms_e2e = timed(e2e_step, args.steps)
     t_e2e = max_over_ranks(sum(ms_e2e) / 1e3)
-    e2e = {"value": world * N * args.steps / t_e2e, "unit": "targets/s",
+    e2e = {"value": pdist.job_rate(N, args.steps, t_e2e), "unit": "targets/s",
            "h2d_bytes_per_step": int(x_h.numel() * 8 + f_h.numel() * 8), "d2h_bytes_per_step": int(u_h.numel() * 8)}
 
     # ---- roofline of the dominant kernel (mixed near field): FP32 ALU bound
@@ -402,8 +394,7 @@ def run_ours(args):
                 "gpu_launches_note": "our kernels per step (plan + eval); CUB sort/scan kernels not counted",
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "other_workloads": extras}
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    pdist.finish()
 
 
 def main():
