@@ -70,6 +70,7 @@ struct NearParams {
   const double* f_orig;  // caller's forces [N][D][n_rhs] (self term)
   double* u;             // [N][D][n_rhs] caller order (may be null for grad-only)
   double* gradu;         // [N][3][3] caller order
+  double* acc;           // sorted FP64 accumulator [N][D] (symmetric Stokeslet pass), zeroed
   double self_base;      // 3D: -phi(0)/(2 pi); 2D: -m_d(0)/(8 pi)
   int n_rhs;             // force columns of the caller's arrays
   float2 c32p[3][kPolyCap];   // FP32 pairs (gS, hS), (pT, qT), (gS', hS')
@@ -435,6 +436,141 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
   }
 }
 
+// ------------------------------------------- mixed, Stokeslet, one column
+// The residual Stokeslet is even, S_R(-x) = S_R(x), and the pair rule and
+// scale nu_ts are symmetric, so one evaluation of a pair serves both points:
+// u_t += S_R(x) f_s and u_s += S_R(x) f_t with x = x_t - x_s.  The warp of
+// target tile T takes the source tiles U > T of its near list (the warp of U
+// skips T) and the tile itself (U = T, target side only, every ordered pair).
+// Same FP32 arithmetic and candidate test as k_near_mixed; the source side of
+// each union source is summed over the warp by shuffles into the lane that
+// owns the source slot, and both sides are added to an FP64 accumulator in
+// sorted order (atomically), finished by k_near_sym_finish.
+template <int D, int NT>
+__global__ void __launch_bounds__(128) k_near_sym(const __grid_constant__ NearParams P, double* __restrict__ acc) {
+  __shared__ float4 s_tst[4][4][8];
+  __shared__ float4 s_pos[4][kTile];
+  __shared__ float4 s_f[4][kTile];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile = blockIdx.x * 4 + wid;
+  if (tile >= P.n_tile) return;
+  const int64_t N = P.N;
+  const int B = P.tile_leaf[tile];
+  const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
+  const int LB = P.leaf_level[B];
+  int64_t cB[3] = {0, 0, 0};
+  leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
+  const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
+  const bool on = lane < nt;
+  const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 ft = on ? P.f32[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float tt = on ? fmaf(xt.x, xt.x, fmaf(xt.y, xt.y, xt.z * xt.z)) : __int_as_float(0x7f800000);
+  float* const rowx = reinterpret_cast<float*>(s_tst[wid][0]);
+  float* const rowy = reinterpret_cast<float*>(s_tst[wid][1]);
+  float* const rowz = reinterpret_cast<float*>(s_tst[wid][2]);
+  float* const roww = reinterpret_cast<float*>(s_tst[wid][3]);
+  float uh[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
+
+  const int e1 = P.near_off[B + 1];
+  for (int e = P.near_off[B]; e < e1; ++e) {
+    const Entry E = make_entry<D>(P, e, LB, cB);
+    const float nu2 = E.nu2, nuinv = E.nuinv;
+    const float nu2inv = nuinv * nuinv;
+    const float nu2m = nu2 * (1.f + 0x1p-12f);
+    const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
+    if (U1 <= tile) continue;                          // every tile of X precedes T
+    for (int Ub = U0; Ub < U1; Ub += 32)
+    for (uint32_t tm = near_tile_mask(P, Ub, U1, E, tlo, thi, lane) & __ballot_sync(0xffffffffu, Ub + lane >= tile);
+         tm; tm &= tm - 1u) {
+      const int U = Ub + __ffs(tm) - 1;
+      const bool sym = U != tile;
+      const int s0 = P.tile_start[U], ns = P.tile_count[U];
+      __syncwarp();
+      if (lane < ns) {
+        const float4 r = P.rel[s0 + lane];
+        const float sx = r.x + E.off[0], sy = r.y + E.off[1], sz = r.z + E.off[2];
+        rowx[lane] = -2.f * sx;
+        rowy[lane] = -2.f * sy;
+        rowz[lane] = -2.f * sz;
+        roww[lane] = fmaf(sx, sx, fmaf(sy, sy, sz * sz)) - nu2m;
+        s_pos[wid][lane] = make_float4(sx, sy, sz, 0.f);
+        s_f[wid][lane] = P.f32[s0 + lane];
+      } else {
+        rowx[lane] = rowy[lane] = rowz[lane] = 0.f;
+        roww[lane] = __int_as_float(0x7f800000);
+      }
+      __syncwarp();
+      uint32_t m = __reduce_or_sync(0xffffffffu, candidate_mask(s_tst[wid], xt, tt));
+      float p[3] = {0.f, 0.f, 0.f};                    // target side, this tile
+      float q[3] = {0.f, 0.f, 0.f};                    // source side of slot `lane`
+      while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1u;
+        const float4 sp = s_pos[wid][j];
+        const float dx = xt.x - sp.x, dy = xt.y - sp.y, dz = xt.z - sp.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool inside = r2 < nu2 && r2 > 0.f;
+        if (!__any_sync(0xffffffffu, inside)) continue;
+        const float rr = inside ? r2 : nu2;            // finite stand-in for the other lanes
+        const float rho2 = rr * nu2inv;
+        const float t = fmaf(2.f, rho2, -1.f);
+        const float2 gh = horner2<NT>(P.c32p[0], t);
+        float A, C;
+        if (D == 3) {
+          float ri = rsqrtf(rr);
+          ri = ri * fmaf(-0.5f * rr, ri * ri, 1.5f);      // one Newton step
+          A = fmaf(gh.x, nuinv, ri);
+          C = ri * ri * fmaf(gh.y, nuinv, ri);
+        } else {
+          A = -__logf(rho2) - gh.x;
+          C = fmaf(-gh.y, nu2inv, 2.f * __frcp_rn(rr));
+        }
+        A = inside ? A : 0.f;
+        C = inside ? C : 0.f;
+        const float4 fs = s_f[wid][j];
+        const float Cx = C * fmaf(dx, fs.x, fmaf(dy, fs.y, dz * fs.z));
+        p[0] = fmaf(A, fs.x, fmaf(Cx, dx, p[0]));
+        p[1] = fmaf(A, fs.y, fmaf(Cx, dy, p[1]));
+        if (D == 3) p[2] = fmaf(A, fs.z, fmaf(Cx, dz, p[2]));
+        if (sym) {
+          const float Ct = C * fmaf(dx, ft.x, fmaf(dy, ft.y, dz * ft.z));
+          float c[3] = {fmaf(A, ft.x, Ct * dx), fmaf(A, ft.y, Ct * dy), D == 3 ? fmaf(A, ft.z, Ct * dz) : 0.f};
+#pragma unroll
+          for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c[a] += __shfl_xor_sync(0xffffffffu, c[a], o);
+          if (lane == j)
+#pragma unroll
+            for (int a = 0; a < D; ++a) q[a] += c[a];
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) two_sum_add(uh[a], ul[a], p[a]);
+      if (sym && lane < ns && (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f))
+#pragma unroll
+        for (int a = 0; a < D; ++a) atomicAdd(acc + (s0 + lane) * D + a, static_cast<double>(q[a]));
+    }
+  }
+  if (on)
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+      atomicAdd(acc + (t0 + lane) * D + a, static_cast<double>(uh[a]) + static_cast<double>(ul[a]));
+  (void)N;
+}
+
+// u (caller order) = acc / (8 pi) + self term, one warp per tile
+template <int D>
+__global__ void k_near_sym_finish(const __grid_constant__ NearParams P, const double* __restrict__ acc) {
+  const int tile = static_cast<int>((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (tile >= P.n_tile || lane >= P.tile_count[tile]) return;
+  const int64_t i = P.tile_start[tile] + lane;
+  const int64_t o = P.perm[i];
+  const double sc = self_coeff<D>(P, P.leaf_level[P.tile_leaf[tile]]);
+#pragma unroll
+  for (int a = 0; a < D; ++a) P.u[o * D + a] = acc[i * D + a] * kInv8Pi + sc * P.f_orig[o * D + a];
+}
+
 // ----------------------------------------------------------------- FP64
 // Same traversal and FP32 candidate test; every candidate is then decided
 // exactly in FP64 with the oracle's operation order.
@@ -732,6 +868,13 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
 
 template <int D, int KM, bool GRAD, int NT, int NR>
 void run_near_mixed(const NearParams& P, cudaStream_t s) {
+  if constexpr (KM == 1 && !GRAD && NR == 1) {
+    if (P.acc && P.u) {
+      k_near_sym<D, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, P.acc);
+      k_near_sym_finish<D><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
+      return;
+    }
+  }
   k_near_mixed<D, KM, GRAD, NT, NR><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P);
 }
 template <int D, int KM, bool GRAD, int NT, int NR>
