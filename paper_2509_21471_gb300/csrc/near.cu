@@ -464,9 +464,11 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     P.c32p[2][k] = make_float2(c32(P_DGS, k), c32(P_DHS, k));
   }
   if (T.n_tile > 0) {
-    if (mixed && km == 1 && !grad && NR == 1 && d_u) {
-      // symmetric Stokeslet pass: both points of a pair from one evaluation,
-      // summed in a zeroed FP64 accumulator (the unused FP64 density region)
+    if ((mixed && km == 1 && !grad && NR == 1 && d_u) || (ff && !grad)) {
+      // symmetric passes (FP32 Stokeslet; float-float Stokeslet and stresslet):
+      // both points of a pair from one evaluation, summed in a zeroed FP64
+      // accumulator (the first 3N doubles of the FP64 density region, unused
+      // by these paths)
       P.acc = reinterpret_cast<double*>(ws + ws_layout(p.opts, N).f64_off);
       DMK_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(double) * D * N, s));
       ++p.launches;                                   // the finishing kernel

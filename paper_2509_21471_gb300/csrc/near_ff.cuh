@@ -193,6 +193,12 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
   __shared__ float4 s_th[4][kTile], s_tl[4][kTile];  // targets, FF
   __shared__ uint16_t s_q[4][kFFQueue];              // queue: target lane << 5 | source slot
   __shared__ float2 s_r[4][NO][kFFQueue];            // per queued pair: contributions (hi, lo)
+  // symmetric pass (all but the gradient): the targets' densities for the
+  // source side of each pair
+  constexpr bool SYM = !GRAD;
+  __shared__ float4 s_tfh[(SYM && (KM & 1)) ? 4 : 1][kTile], s_tfl[(SYM && (KM & 1)) ? 4 : 1][kTile];
+  __shared__ float4 s_tgh[(SYM && (KM & 2)) ? 4 : 1][kTile], s_tgl[(SYM && (KM & 2)) ? 4 : 1][kTile];
+  __shared__ float4 s_tnh[(SYM && (KM & 2)) ? 4 : 1][kTile], s_tnl[(SYM && (KM & 2)) ? 4 : 1][kTile];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x * 4 + wid;
   if (tile >= P.n_tile) return;
@@ -207,6 +213,20 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
   const float tt = on ? fmaf(xt.x, xt.x, fmaf(xt.y, xt.y, xt.z * xt.z)) : __int_as_float(0x7f800000);
   s_th[wid][lane] = xt;
   s_tl[wid][lane] = on ? F.rel_lo[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  if (SYM) {
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ws = SYM ? wid : 0;
+    if (KM & 1) {
+      s_tfh[(KM & 1) ? ws : 0][lane] = on ? F.f_hi[t0 + lane] : z4;
+      s_tfl[(KM & 1) ? ws : 0][lane] = on ? F.f_lo[t0 + lane] : z4;
+    }
+    if (KM & 2) {
+      s_tgh[(KM & 2) ? ws : 0][lane] = on ? F.g_hi[t0 + lane] : z4;
+      s_tgl[(KM & 2) ? ws : 0][lane] = on ? F.g_lo[t0 + lane] : z4;
+      s_tnh[(KM & 2) ? ws : 0][lane] = on ? F.n_hi[t0 + lane] : z4;
+      s_tnl[(KM & 2) ? ws : 0][lane] = on ? F.n_lo[t0 + lane] : z4;
+    }
+  }
   float* const rowx = reinterpret_cast<float*>(s_tst[wid][0]);
   float* const rowy = reinterpret_cast<float*>(s_tst[wid][1]);
   float* const rowz = reinterpret_cast<float*>(s_tst[wid][2]);
@@ -222,9 +242,14 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
     const float nu2inv = nuinv * nuinv;
     const float nu2m = nu2 * (1.f + 0x1p-12f);
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
+    // symmetric pass: the source tiles U >= T (T's own tile: target side only)
+    if (SYM && U1 <= tile) continue;
     for (int Ub = U0; Ub < U1; Ub += 32)
-    for (uint32_t tm = near_tile_mask(P, Ub, U1, E, tlo, thi, lane); tm; tm &= tm - 1u) {
+    for (uint32_t tm = near_tile_mask(P, Ub, U1, E, tlo, thi, lane) &
+                       (SYM ? __ballot_sync(0xffffffffu, Ub + lane >= tile) : 0xffffffffu);
+         tm; tm &= tm - 1u) {
       const int U = Ub + __ffs(tm) - 1;
+      const bool both = SYM && U != tile;              // source side too
       const int s0 = P.tile_start[U], ns = P.tile_count[U];
       __syncwarp();
       if (lane < ns) {
@@ -321,6 +346,7 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
             }
             const ff xv[3] = {dx, dy, dz};
             ff out[NO];
+            ff src[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // source side (symmetric pass)
             if (KM & 1) {
               const ff2 gh = horner_ff2<NT>(F.chi[0], F.clo[0], t);
               ff A, C;
@@ -338,6 +364,17 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
               const ff Cx = ff_mul(C, xf);
 #pragma unroll
               for (int a = 0; a < D; ++a) out[a] = ff_add(ff_mul(A, fv[a]), ff_mul(Cx, xv[a]));
+              if (SYM && both) {
+                // S_R is even: u_s += S_R(x) f_t
+                const float4 th4 = s_tfh[(SYM && (KM & 1)) ? wid : 0][tl];
+                const float4 tl4 = s_tfl[(SYM && (KM & 1)) ? wid : 0][tl];
+                const ff ftv[3] = {{th4.x, tl4.x}, {th4.y, tl4.y}, {th4.z, tl4.z}};
+                ff xft = ff_add(ff_mul(dx, ftv[0]), ff_mul(dy, ftv[1]));
+                if (D == 3) xft = ff_add(xft, ff_mul(dz, ftv[2]));
+                const ff Cxt = ff_mul(C, xft);
+#pragma unroll
+                for (int a = 0; a < D; ++a) src[a] = ff_add(ff_mul(A, ftv[a]), ff_mul(Cxt, xv[a]));
+              }
               if (GRAD) {
                 const ff2 dgh = horner_ff2<NT>(F.chi[2], F.clo[2], t);
                 const float nu3i = nuinv * nuinv * nuinv;
@@ -393,7 +430,30 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
                 const ff sym = ff_add(ff_mul(gv[a], xn), ff_mul(nv[a], xg));
                 out[a] = ff_add(out[a], ff_add(ff_mul(Dc, sym), ff_mul(Ex, xv[a])));
               }
+              if (SYM && both) {
+                // T_R is odd: u_s -= T_R(x) : (g_t n_t)
+                const int ws = (SYM && (KM & 2)) ? wid : 0;
+                const float4 gh5 = s_tgh[ws][tl], gl5 = s_tgl[ws][tl], nh5 = s_tnh[ws][tl], nl5 = s_tnl[ws][tl];
+                const ff gt[3] = {{gh5.x, gl5.x}, {gh5.y, gl5.y}, {gh5.z, gl5.z}};
+                const ff ntv[3] = {{nh5.x, nl5.x}, {nh5.y, nl5.y}, {nh5.z, nl5.z}};
+                const ff gnt = {nh5.w, nl5.w};
+                ff xnt = ff_add(ff_mul(dx, ntv[0]), ff_mul(dy, ntv[1]));
+                ff xgt = ff_add(ff_mul(dx, gt[0]), ff_mul(dy, gt[1]));
+                if (D == 3) {
+                  xnt = ff_add(xnt, ff_mul(dz, ntv[2]));
+                  xgt = ff_add(xgt, ff_mul(dz, gt[2]));
+                }
+                const ff Ext = ff_add(ff_mul(Ec, ff_mul(xgt, xnt)), ff_mul(Dc, gnt));
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                  const ff st = ff_add(ff_mul(gt[a], xnt), ff_mul(ntv[a], xgt));
+                  src[a] = ff_add(src[a], ff_neg(ff_add(ff_mul(Dc, st), ff_mul(Ext, xv[a]))));
+                }
+              }
             }
+            if (SYM && both)
+#pragma unroll
+              for (int a = 0; a < D; ++a) atomicAdd(P.acc + (s0 + j) * D + a, ff_to_double(src[a]));
 #pragma unroll
             for (int a = 0; a < NO; ++a) res[a] = make_float2(out[a].hi, out[a].lo);
           }
@@ -417,7 +477,11 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
   if (!on) return;
   const int64_t o = P.perm[t0 + lane];
   const double sc = self_coeff<D>(P, LB);
-  if (P.u) {
+  if (SYM) {
+    // both sides meet in the sorted FP64 accumulator, finished by k_near_sym_finish
+#pragma unroll
+    for (int a = 0; a < D; ++a) atomicAdd(P.acc + (t0 + lane) * D + a, ff_to_double(acc[a]));
+  } else if (P.u) {
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       double v = ff_to_double(acc[a]) * kInv8Pi;
@@ -435,6 +499,7 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
 template <int D, int KM, bool GRAD, int NT>
 void run_near_ff(const NearParams& P, const FFParams& F, cudaStream_t s) {
   k_near_ff<D, KM, GRAD, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, F);
+  if (!GRAD) k_near_sym_finish<D, KM><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
 }
 
 #define DMK_FOR_EACH_FF(M, NT)                                                    \

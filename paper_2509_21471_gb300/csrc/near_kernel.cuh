@@ -558,17 +558,21 @@ __global__ void __launch_bounds__(128) k_near_sym(const __grid_constant__ NearPa
   (void)N;
 }
 
-// u (caller order) = acc / (8 pi) + self term, one warp per tile
-template <int D>
+// u (caller order) = acc / (8 pi) [+ Stokeslet self term], one warp per tile
+template <int D, int KM>
 __global__ void k_near_sym_finish(const __grid_constant__ NearParams P, const double* __restrict__ acc) {
   const int tile = static_cast<int>((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (tile >= P.n_tile || lane >= P.tile_count[tile]) return;
   const int64_t i = P.tile_start[tile] + lane;
   const int64_t o = P.perm[i];
-  const double sc = self_coeff<D>(P, P.leaf_level[P.tile_leaf[tile]]);
+  const double sc = (KM & 1) ? self_coeff<D>(P, P.leaf_level[P.tile_leaf[tile]]) : 0.0;
 #pragma unroll
-  for (int a = 0; a < D; ++a) P.u[o * D + a] = acc[i * D + a] * kInv8Pi + sc * P.f_orig[o * D + a];
+  for (int a = 0; a < D; ++a) {
+    double v = acc[i * D + a] * kInv8Pi;
+    if (KM & 1) v += sc * P.f_orig[o * D + a];
+    P.u[o * D + a] = v;
+  }
 }
 
 // ----------------------------------------------------------------- FP64
@@ -871,7 +875,7 @@ void run_near_mixed(const NearParams& P, cudaStream_t s) {
   if constexpr (KM == 1 && !GRAD && NR == 1) {
     if (P.acc && P.u) {
       k_near_sym<D, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, P.acc);
-      k_near_sym_finish<D><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
+      k_near_sym_finish<D, 1><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
       return;
     }
   }
