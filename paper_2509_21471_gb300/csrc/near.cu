@@ -240,16 +240,19 @@ bool ff_pairs(const dmk_stokes_opts_t& o) {
   return o.precision == DMK_PRECISION_MIXED && o.eps < kFp32PairMinEps && o.n_rhs == 1;
 }
 
-// workspace: [FP32 sorted densities (fp32 pairs)] [FP64 sorted densities] [FF split densities]
+// workspace: [FP32 sorted densities (fp32 pairs)] [FP64 sorted densities]
+// [FF split densities] [FP64 accumulator of the symmetric FP64 pass]
 struct WsLayout {
-  size_t f64_off, ff_off, bytes;
+  size_t f64_off, ff_off, acc_off, bytes;
 };
 WsLayout ws_layout(const dmk_stokes_opts_t& o, int64_t N) {
   const int NR = padded_rhs(o.n_rhs);
   WsLayout L;
   L.f64_off = fp32_pairs(o) ? std::max(3, NR) * N * sizeof(float4) : 0;
   L.ff_off = L.f64_off + std::max(3 + 3 + 4, 3 * NR) * N * sizeof(double);
-  L.bytes = L.ff_off + (ff_pairs(o) ? 7 * N * sizeof(float4) : 0);
+  L.acc_off = L.ff_off + (ff_pairs(o) ? 7 * N * sizeof(float4) : 0);
+  const bool fp64_sym = o.precision == DMK_PRECISION_FP64 && o.n_rhs == 1;
+  L.bytes = L.acc_off + (fp64_sym ? 3 * N * sizeof(double) : 0);
   return L;
 }
 
@@ -464,12 +467,14 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     P.c32p[2][k] = make_float2(c32(P_DGS, k), c32(P_DHS, k));
   }
   if (T.n_tile > 0) {
-    if ((mixed && km == 1 && !grad && NR == 1 && d_u) || (ff && !grad)) {
-      // symmetric passes (FP32 Stokeslet; float-float Stokeslet and stresslet):
-      // both points of a pair from one evaluation, summed in a zeroed FP64
-      // accumulator (the first 3N doubles of the FP64 density region, unused
-      // by these paths)
-      P.acc = reinterpret_cast<double*>(ws + ws_layout(p.opts, N).f64_off);
+    const bool fp64_sym = !mixed && !ff && NR == 1 && !grad && d_u;
+    if ((mixed && km == 1 && !grad && NR == 1 && d_u) || (ff && !grad) || fp64_sym) {
+      // symmetric passes (FP32 Stokeslet; float-float and FP64 Stokeslet and
+      // stresslet): both points of a pair from one evaluation, summed in a
+      // zeroed FP64 accumulator (FP32 / FF: the first 3N doubles of the FP64
+      // density region, which these paths leave unused; FP64: its own region)
+      const WsLayout L = ws_layout(p.opts, N);
+      P.acc = reinterpret_cast<double*>(ws + (fp64_sym ? L.acc_off : L.f64_off));
       DMK_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(double) * D * N, s));
       ++p.launches;                                   // the finishing kernel
     }

@@ -621,10 +621,32 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
 #pragma unroll
   for (int k = 0; k < (GRAD ? 9 : 1); ++k) G[k] = 0.0;
 
+  // Symmetric pass (one column, no gradient): the warp of target tile T takes
+  // the source tiles U >= T; for U > T each pair also gives the source its
+  // contribution (S_R even, T_R odd), from the target's densities s_td.
+  constexpr bool SYM64 = (NR == 1 && !GRAD);
+  constexpr int NTD = ((KM & 1) ? D : 0) + ((KM & 2) ? 2 * D + 1 : 0);
+  __shared__ double s_td[SYM64 ? WPB : 1][SYM64 ? NTD : 1][kTile];
+  __shared__ int s_s0[SYM64 ? WPB : 1][NB];           // per staged tile: first point, -1 if U == T
+  const int tw = SYM64 ? wid : 0;
+  if (SYM64 && P.acc) {
+    int k = 0;
+    if (KM & 1)
+#pragma unroll
+      for (int a = 0; a < D; ++a) s_td[tw][k++][lane] = on ? P.f64[a * N + t0 + lane] : 0.0;
+    if (KM & 2) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) s_td[tw][k++][lane] = on ? P.g64[a * N + t0 + lane] : 0.0;
+#pragma unroll
+      for (int a = 0; a < D + 1; ++a) s_td[tw][k++][lane] = on ? P.n64[a * N + t0 + lane] : 0.0;
+    }
+  }
+
   // One candidate pair (target coordinates w3, staged source slot idx):
   // decided and evaluated in FP64 with the oracle's operation order; the
   // contributions are added to a (velocity, [NR][3]) and gr (gradient).
-  auto pair = [&](const double (&w3)[3], int idx, double (&a)[NR][3], double (&gr)[GRAD ? 9 : 1]) {
+  auto pair = [&](const double (&w3)[3], int idx, double (&a)[NR][3], double (&gr)[GRAD ? 9 : 1], int tl,
+                  double (&sr)[3]) {
     const double* q = sQ[wid][idx >> 5];
     const double dx = __dadd_rn(__dsub_rn(w3[0], sD[wid][0][idx]), q[0]);
     const double dy = __dadd_rn(__dsub_rn(w3[1], sD[wid][1][idx]), q[1]);
@@ -670,6 +692,14 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
         a[c][0] = fma(A, fx, fma(Cx, dx, a[c][0]));
         a[c][1] = fma(A, fy, fma(Cx, dy, a[c][1]));
         if (D == 3) a[c][2] = fma(A, fz, fma(Cx, dz, a[c][2]));
+        if (SYM64 && tl >= 0) {
+          // S_R is even: the source gets S_R(x) f_t
+          const double tfx = s_td[tw][0][tl], tfy = s_td[tw][1][tl], tfz = (D == 3) ? s_td[tw][Z][tl] : 0.0;
+          const double Ct = C * fma(dx, tfx, fma(dy, tfy, dz * tfz));
+          sr[0] += fma(A, tfx, Ct * dx);
+          sr[1] += fma(A, tfy, Ct * dy);
+          if (D == 3) sr[2] += fma(A, tfz, Ct * dz);
+        }
         if (GRAD) {
           const double dg = horner<NT>(P.c64[P_DGS], t);
           const double dh = horner<NT>(P.c64[P_DHS], t);
@@ -714,6 +744,21 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
       a[0][0] += fma(Dc, fma(gx_, xn, nx * xg), Ex * dx);
       a[0][1] += fma(Dc, fma(gy_, xn, ny * xg), Ex * dy);
       if (D == 3) a[0][2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
+      if (SYM64 && tl >= 0) {
+        // T_R is odd: the source gets -T_R(x) : (g_t n_t)
+        const int kg = (KM & 1) ? D : 0;
+        const double tgx = s_td[tw][kg][tl], tgy = s_td[tw][kg + 1][tl];
+        const double tgz = (D == 3) ? s_td[tw][kg + Z][tl] : 0.0;
+        const double tnx = s_td[tw][kg + D][tl], tny = s_td[tw][kg + D + 1][tl];
+        const double tnz = (D == 3) ? s_td[tw][kg + D + Z][tl] : 0.0;
+        const double tgn = s_td[tw][kg + 2 * D][tl];
+        const double xnt = fma(dx, tnx, fma(dy, tny, dz * tnz));
+        const double xgt = fma(dx, tgx, fma(dy, tgy, dz * tgz));
+        const double Ext = Ec * xgt * xnt + Dc * tgn;
+        sr[0] -= fma(Dc, fma(tgx, xnt, tnx * xgt), Ext * dx);
+        sr[1] -= fma(Dc, fma(tgy, xnt, tny * xgt), Ext * dy);
+        if (D == 3) sr[2] -= fma(Dc, fma(tgz, xnt, tnz * xgt), Ext * dz);
+      }
     }
   };
 
@@ -722,7 +767,7 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
   // warps; each lane then adds its own target's results.  NR > 1: every lane
   // walks its own candidates.
   constexpr int NO = GRAD ? 12 : D;
-  constexpr int Q = (NR == 1) ? 64 : 1;              // queued pairs per round
+  constexpr int Q = (NR == 1) ? ((KM == 3 && D == 3) ? 32 : 64) : 1;   // queued pairs per round (48 KB limit)
   __shared__ double s_wt[(NR == 1) ? WPB : 1][3][kTile];
   __shared__ uint16_t s_q[(NR == 1) ? WPB : 1][Q];
   __shared__ double s_r[(NR == 1) ? WPB : 1][(NR == 1) ? NO : 1][Q];
@@ -778,7 +823,13 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
           const double w3[3] = {s_wt[qw][0][tl], s_wt[qw][1][tl], s_wt[qw][2][tl]};
           double a[NR][3] = {};
           double gr[GRAD ? 9 : 1] = {};
-          pair(w3, ent & 127, a, gr);
+          double sr[3] = {0.0, 0.0, 0.0};
+          const int idx = ent & 127;
+          const int ss0 = (SYM64 && P.acc) ? s_s0[tw][idx >> 5] : -1;
+          pair(w3, idx, a, gr, ss0 >= 0 ? tl : -1, sr);
+          if (SYM64 && ss0 >= 0 && (sr[0] != 0.0 || sr[1] != 0.0 || sr[2] != 0.0))
+#pragma unroll
+            for (int c = 0; c < D; ++c) atomicAdd(P.acc + (ss0 + (idx & 31)) * D + c, sr[c]);
 #pragma unroll
           for (int c = 0; c < D; ++c) s_r[qw][c % NO][qi] = a[0][c];
           if (GRAD)
@@ -799,7 +850,8 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
     } else {
       BitWalker bw{m[0], m[1], m[2], m[3], 0};
       int idx;
-      while (bw.next(idx)) pair(wt, idx, acc, G);
+      double sr[3];
+      while (bw.next(idx)) pair(wt, idx, acc, G, -1, sr);
     }
     __syncwarp();
     nb = 0;
@@ -810,13 +862,18 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
     const Entry E = make_entry<D>(P, e, LB, cB);
     const float nu2m = E.nu2 * (1.f + 0x1p-12f);
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
+    const bool sym = SYM64 && P.acc;
+    if (sym && U1 <= tile) continue;
     for (int Ub = U0; Ub < U1; Ub += 32)
-    for (uint32_t tm = near_tile_mask(P, Ub, U1, E, tlo, thi, lane); tm; tm &= tm - 1u) {
+    for (uint32_t tm = near_tile_mask(P, Ub, U1, E, tlo, thi, lane) &
+                       (sym ? __ballot_sync(0xffffffffu, Ub + lane >= tile) : 0xffffffffu);
+         tm; tm &= tm - 1u) {
       const int U = Ub + __ffs(tm) - 1;
       if (nb == NB) flush();
       const int s0 = P.tile_start[U], ns = P.tile_count[U];
       const int slot = nb * kTile + lane;
       if (lane == 0) {
+        if (SYM64) s_s0[tw][nb] = (sym && U != tile) ? s0 : -1;
         sQ[wid][nb][0] = E.q[0];
         sQ[wid][nb][1] = E.q[1];
         sQ[wid][nb][2] = E.q[2];
@@ -848,6 +905,12 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
   if (nb > 0) flush();
 
   if (!on) return;
+  if (SYM64 && P.acc) {
+    // both sides meet in the sorted accumulator, finished by k_near_sym_finish
+#pragma unroll
+    for (int a = 0; a < D; ++a) atomicAdd(P.acc + (t0 + lane) * D + a, acc[0][a]);
+    return;
+  }
   const int64_t o = P.perm[t0 + lane];
   const double sc = self_coeff<D>(P, LB);
   const int nr = P.n_rhs;
@@ -885,6 +948,7 @@ template <int D, int KM, bool GRAD, int NT, int NR>
 void run_near_fp64(const NearParams& P, cudaStream_t s) {
   constexpr int WPB = Fp64Shape<D, KM, GRAD, NT, NR>::WPB;
   k_near_fp64<D, KM, GRAD, NT, NR><<<(P.n_tile + WPB - 1) / WPB, 32 * WPB, 0, s>>>(P);
+  if (NR == 1 && !GRAD && P.acc) k_near_sym_finish<D, KM><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
 }
 
 // instantiation lists (near_mixed*.cu, near_fp64*.cu): (dim, kernels, gradient, NT, NR)

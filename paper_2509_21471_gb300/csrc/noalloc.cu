@@ -15,7 +15,7 @@
 //     needs more is rejected with DMK_ERR_INVALID_ARG before anything runs
 //     (mixed precision at eps >= 2e-7: 128 bytes per point, about 524k
 //     points; mixed below 2e-7: 192 bytes per point, about 349k points; FP64:
-//     80 bytes per point, about 838k points; plus 32 bytes per system);
+//     104 bytes per point, about 645k points; plus 32 bytes per system);
 //   * every GPU that loads the library holds the array until the process exits;
 //   * all calls on a device share the array and it keeps the last call's
 //     contents; the zero-mode sums are cleared at the start of every call;
