@@ -349,13 +349,6 @@ def run_ours(args):
            "h2d_bytes_per_step": int(x_h.numel() * 8 + f_h.numel() * 8), "d2h_bytes_per_step": int(u_h.numel() * 8)}
 
     # ---- roofline of the dominant kernel (mixed near field): FP32 ALU bound
-    c32 = [len(dmk.kernel_table(3, args.eps, w, fp32=True)[2]) for w in (0, 1)]
-    # Algorithmic flops (FMA = 2) of the symmetric Stokeslet pass: per unordered
-    # pair the geometry, 1/r and both polynomials once (40 + 2(n_g - 1) + 2(n_h - 1),
-    # including one application to a force) plus the second application (18);
-    # useful_pairs counts ordered pairs, so per useful pair half of that.
-    flops_one_side = 40 + 2 * (c32[0] - 1) + 2 * (c32[1] - 1)
-    flops_per_pair = (flops_one_side + 18) / 2
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -363,22 +356,37 @@ def run_ours(args):
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = near["mixed"]["useful_pairs"] * flops_per_pair / (near["mixed"]["ms"] / 1e3) / 1e12
-    # DRAM bytes per launch of this kernel from ncu (dram__bytes_read.sum +
-    # dram__bytes_write.sum); None until the current kernel has been captured
-    traffic = None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": traffic,
-                "traffic_note": "bytes per launch, ncu capture at N=5e5 scaled by the point count",
-                "kernel": f"k_near_sym<3,{min(v for v in (8, 10, 12, 13, 14, 16) if v >= max(c32))}> "
-                          "(symmetric near field, mixed precision)",
-                "flops_per_useful_pair": flops_per_pair,
-                "flops_note": "symmetric pass: one evaluation per unordered pair serves both points; "
-                              "a one-sided kernel does flops_one_side per useful pair",
-                "flops_one_side": flops_one_side,
-                "frac_at_one_sided_flops": achieved * flops_one_side / flops_per_pair / peak_tflops,
-                "peak_basis": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
-                              "(max SM clock of MEASURED_PEAKS.json)"}
+    peak_basis = (f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                  "(max SM clock of MEASURED_PEAKS.json)")
+    if args.eps >= 2e-7:
+        c32 = [len(dmk.kernel_table(3, args.eps, w, fp32=True)[2]) for w in (0, 1)]
+        # Algorithmic flops (FMA = 2) of the symmetric Stokeslet pass: per unordered
+        # pair the geometry, 1/r and both polynomials once (40 + 2(n_g - 1) + 2(n_h - 1),
+        # including one application to a force) plus the second application (18);
+        # useful_pairs counts ordered pairs, so per useful pair half of that.
+        flops_one_side = 40 + 2 * (c32[0] - 1) + 2 * (c32[1] - 1)
+        flops_per_pair = (flops_one_side + 18) / 2
+        achieved = near["mixed"]["useful_pairs"] * flops_per_pair / (near["mixed"]["ms"] / 1e3) / 1e12
+        # DRAM bytes per launch of this kernel from ncu (dram__bytes_read.sum +
+        # dram__bytes_write.sum); None until the current kernel has been captured
+        traffic = None
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tflops, "traffic": traffic,
+                    "traffic_note": "bytes per launch, ncu capture at N=5e5 scaled by the point count",
+                    "kernel": f"k_near_sym<3,{min(v for v in (8, 10, 12, 13, 14, 16) if v >= max(c32))}> "
+                              "(symmetric near field, mixed precision)",
+                    "flops_per_useful_pair": flops_per_pair,
+                    "flops_note": "symmetric pass: one evaluation per unordered pair serves both points; "
+                                  "a one-sided kernel does flops_one_side per useful pair",
+                    "flops_one_side": flops_one_side,
+                    "frac_at_one_sided_flops": achieved * flops_one_side / flops_per_pair / peak_tflops,
+                    "peak_basis": peak_basis}
+    else:
+        # below eps 2e-7 MIXED runs float-float pair terms (k_near_ff): FP32-pipe
+        # bound, with no per-pair flop figure of the method to divide
+        roofline = {"bound": "alu", "achieved": None, "peak": peak_tflops, "unit": "TFLOP/s", "frac": None,
+                    "traffic": None, "kernel": "k_near_ff (float-float near field)", "peak_basis": peak_basis,
+                    "note": "float-float arithmetic: see the ncu FP32-pipe utilisation in profiles/"}
 
     extras = None
     if not args.no_extras:
