@@ -368,8 +368,9 @@ def run_ours(args):
         flops_per_pair = (flops_one_side + 18) / 2
         achieved = near["mixed"]["useful_pairs"] * flops_per_pair / (near["mixed"]["ms"] / 1e3) / 1e12
         # DRAM bytes per launch of this kernel from ncu (dram__bytes_read.sum +
-        # dram__bytes_write.sum); None until the current kernel has been captured
-        traffic = None
+        # dram__bytes_write.sum) on the same recipe at N = 5e5, scaled by the
+        # point count: profiles/near_sym_clustered5e5.md
+        traffic = 29.37e6 * args.n / 500_000 if args.eps == 1e-6 else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops, "traffic": traffic,
                     "traffic_note": "bytes per launch, ncu capture at N=5e5 scaled by the point count",
