@@ -116,11 +116,12 @@ dmk_status_t dmk_stokes_plan_batched(const dmk_stokes_opts_t* opts, int32_t n_sy
  *        (required if the stresslet bit is set; rho_s = g_s (x) n_s, Eq. (stokes_stress_sum))
  *   d_u  [n][dim][n_rhs] output, overwritten
  * Does not allocate; may be captured in a CUDA graph.  With one force column
- * (and for the stresslet) each pair is evaluated once for both of its points
- * (the residual Stokeslet is even, the stresslet odd) and the two sides meet
- * in an FP64 accumulator by atomic additions, so repeated calls agree to
- * within the order of those additions (~1e-16 relative), not bit for bit;
- * several force columns are bitwise reproducible. */
+ * the FP32 Stokeslet pass and the float-float and FP64 passes evaluate each
+ * pair once for both of its points (the residual Stokeslet is even, the
+ * stresslet odd); the two sides meet in an FP64 accumulator by atomic
+ * additions, so repeated calls agree to within the order of those additions
+ * (~1e-16 relative), not bit for bit.  The periodic stresslet zero mode is
+ * also summed atomically.  Other configurations are bitwise reproducible. */
 dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
                              const double* d_n, double* d_u, void* stream);
 
