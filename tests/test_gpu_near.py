@@ -153,3 +153,31 @@ def test_out_of_range_point_is_reported(dmk):
     with pytest.raises(dmk.DMKError) as ei:
         p.sync_status()
     assert ei.value.code == 2
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_refinement_to_the_maximum_level(dmk, dim):
+    """40 coincident points and a tight pair with n_s = 8: the tree refines to
+    the maximum level M (21 in 3D, 31 in 2D) at that spot, the leaf there keeps
+    all its points, and level restriction cascades out from it.  Tree parity
+    is exact; coincident pairs are skipped on both sides."""
+    rng = np.random.default_rng(1234 + dim)
+    x = wl.uniform_points(rng, 600, dim)
+    x[:40] = x[40]                                   # 41 coincident points
+    x[41] = x[40] + 1e-9                             # a near neighbour far below the finest cell
+    f = wl.forces(rng, 600, dim)
+    ns = 8
+    tr = Tree(x, ns)
+    assert int(tr.leaf_level.max()) == {3: 21, 2: 31}[dim]
+    if dim == 3:
+        win = ProlateWindow(bandlimit_c(1e-6))
+        u_ref = onear.near_lists(tr, dict(win=win, stokeslet=True), f=f)
+    else:
+        from oracle import kernels2d as k2
+        u_ref = onear.near_lists(tr, dict(k2d=k2.Kernel2D(ProlateWindow(bandlimit_c(1e-6))), stokeslet=True), f=f)
+    for prec in (0, 1):
+        p, u = _run(dmk, x, f=f, eps=1e-6, ns=ns, precision=prec)
+        if prec == 0:
+            assert_tree_equal(p.tree(), tr)
+        assert rel_l2(u, u_ref) < (FP64_TOL if prec == 0 else 1e-5)
+        p.close()
