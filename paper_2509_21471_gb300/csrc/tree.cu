@@ -205,11 +205,15 @@ __global__ void k_scan_total(int n, const int32_t* __restrict__ in, int32_t* __r
 }
 
 
-__global__ void k_sys_begin(int n, int n_sys, const int32_t* __restrict__ sys, int32_t* __restrict__ begin) {
+// first leaf of every system; also clears flag[0, n) and *any when given
+__global__ void k_sys_begin(int n, int n_sys, const int32_t* __restrict__ sys, int32_t* __restrict__ begin,
+                            int32_t* __restrict__ flag = nullptr, int* __restrict__ any = nullptr) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (i == 0 || sys[i] != sys[i - 1]) begin[sys[i]] = i;
   if (i == n - 1) begin[n_sys] = n;
+  if (flag) flag[i] = 0;
+  if (any && i == 0) *any = 0;
 }
 
 // last leaf in [b, e) with anchor <= key
@@ -443,6 +447,63 @@ __global__ void k_point_sys(int n_sys, const int32_t* __restrict__ offs, int32_t
   if (k < n_sys && i < offs[k + 1]) ps[i] = k;
 }
 
+// Exclusive scan of n counts by one block (n <= kSmallScan): out[i] for i < n,
+// the total in out[n] (and in *copy when given).  One launch where the library
+// scan takes three for the small arrays of the tree build.
+constexpr int kSmallScan = 1024 * 64;
+__global__ void __launch_bounds__(1024) k_scan_small(int n, const int32_t* __restrict__ in,
+                                                     int32_t* __restrict__ out, int32_t* __restrict__ copy) {
+  __shared__ int32_t wsum[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int per = (n + 1023) / 1024;
+  const int b = min(t * per, n), e = min(b + per, n);
+  int32_t sum = 0;
+  for (int i = b; i < e; ++i) sum += in[i];
+  int32_t v = sum;                                   // inclusive scan within the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) wsum[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int32_t x = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wsum[lane] = x;                                  // inclusive over warps
+  }
+  __syncthreads();
+  int32_t run = v - sum + (w > 0 ? wsum[w - 1] : 0);
+  for (int i = b; i < e; ++i) {
+    out[i] = run;
+    run += in[i];
+  }
+  if (t == 0) {
+    out[n] = wsum[31];
+    if (copy) *copy = wsum[31];
+  }
+}
+
+// exclusive scan of n counts into out[0, n] (out[n] = total, also to *copy)
+void scan_counts(const int32_t* in, int32_t* out, int n, cudaStream_t s, Arena& scratch, int32_t* copy,
+                 int64_t& launches) {
+  if (n <= kSmallScan) {
+    k_scan_small<<<1, 1024, 0, s>>>(n, in, out, copy);
+    ++launches;
+  } else {
+    size_t bytes = 0;
+    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, n, s));
+    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(scratch.alloc_bytes(bytes), bytes, in, out, n, s));
+    k_scan_total<<<1, 1, 0, s>>>(n, in, out, copy);
+    ++launches;
+  }
+  DMK_CUDA_TRY(cudaGetLastError());
+}
+
 template <int D>
 void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   DeviceTree& T = p.tree;
@@ -535,13 +596,10 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
       const int64_t cap_out = cap + grow;
       if (cap_out >= (int64_t(1) << 31)) throw Error{DMK_ERR_NOMEM, "tree too large"};
       int32_t* nch = scratch.alloc<int32_t>(cap);
-      int32_t* pos = scratch.alloc<int32_t>(cap);
+      int32_t* pos = scratch.alloc<int32_t>(cap + 1);
       k_split_flags_dev<D><<<grid_for(cap, B), B, 0, s>>>(static_cast<int>(cap), d_cnt + lev, cur,
                                                            p.leaf_capacity, M, nch);
-      size_t bytes = 0;
-      DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, nch, pos, static_cast<int>(cap), s));
-      DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(scratch.alloc_bytes(bytes), bytes, nch, pos,
-                                                 static_cast<int>(cap), s));
+      scan_counts(nch, pos, static_cast<int>(cap), s, scratch, nullptr, p.launches);
       alloc_leaves(nxt, cap_out, A);
       k_refine_dev<D><<<grid_for(cap << D, B), B, 0, s>>>(static_cast<int>(cap), static_cast<int>(cap_out),
                                                      d_cnt + lev, cur, nch, pos, nxt, skeys, M, d_cnt + lev + 1,
@@ -564,22 +622,16 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   // violation are read together
   int* d_any = scratch.alloc<int>(1);
   for (int it = 0; it < 4 * M + 8; ++it) {
-    k_sys_begin<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), n_sys, cur.sys, begin);
     int32_t* flag = scratch.alloc<int32_t>(n_leaf);
     int32_t* nch = scratch.alloc<int32_t>(n_leaf);
     int32_t* pos = scratch.alloc<int32_t>(n_leaf + 1);
-    DMK_CUDA_TRY(cudaMemsetAsync(flag, 0, n_leaf * sizeof(int32_t), s));
-    DMK_CUDA_TRY(cudaMemsetAsync(d_any, 0, sizeof(int), s));
+    k_sys_begin<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), n_sys, cur.sys, begin, flag, d_any);
     k_balance<D><<<grid_for(n_leaf * 32, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
                                                         flag, d_any);
     k_split_flags<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, p.leaf_capacity, M,
                                                        flag, nch);
-    size_t bytes = 0;
-    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, nch, pos, static_cast<int>(n_leaf), s));
-    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(scratch.alloc_bytes(bytes), bytes, nch, pos,
-                                               static_cast<int>(n_leaf), s));
-    k_scan_total<<<1, 1, 0, s>>>(static_cast<int>(n_leaf), nch, pos, nullptr);
-    p.launches += 4;
+    scan_counts(nch, pos, static_cast<int>(n_leaf), s, scratch, nullptr, p.launches);
+    p.launches += 3;
     DMK_CUDA_TRY(cudaGetLastError());
     DMK_CUDA_TRY(cudaMemcpyAsync(h_pin, pos + n_leaf, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     DMK_CUDA_TRY(cudaMemcpyAsync(h_pin + 2, d_any, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -614,18 +666,12 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   T.near_off = A.alloc<int32_t>(n_leaf + 1);
   k_near_warp<D><<<grid_for(n_leaf * 32, 256), 256, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
                                                             nsl, nsq, ncount, p.status);
-  {
-    size_t bytes = 0;
-    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, ncount, T.near_off, static_cast<int>(n_leaf), s));
-    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(scratch.alloc_bytes(bytes), bytes, ncount, T.near_off,
-                                               static_cast<int>(n_leaf), s));
-  }
-  k_scan_total<<<1, 1, 0, s>>>(static_cast<int>(n_leaf), ncount, T.near_off, nullptr);
+  scan_counts(ncount, T.near_off, static_cast<int>(n_leaf), s, scratch, nullptr, p.launches);
   T.near_leaf = A.alloc<int32_t>(n_leaf * kMaxNear);
   T.near_q = A.alloc<int32_t>(n_leaf * kMaxNear);
   k_near_compact<<<grid_for(n_leaf * 32, 256), 256, 0, s>>>(static_cast<int>(n_leaf), ncount, T.near_off, nsl,
                                                            nsq, T.near_leaf, T.near_q);
-  p.launches += 3;
+  p.launches += 2;
   DMK_CUDA_TRY(cudaGetLastError());
   DMK_CUDA_TRY(cudaMemcpyAsync(h_pin + 4, T.near_off + n_leaf, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
 
@@ -636,14 +682,7 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   T.leaf_tile0 = A.alloc<int32_t>(n_leaf + 1);
   int32_t* d_ntile = scratch.alloc<int32_t>(1);
   k_tile_count<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur.count, T.leaf_ntile);
-  {
-    size_t bytes = 0;
-    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, bytes, T.leaf_ntile, T.leaf_tile0,
-                                               static_cast<int>(n_leaf), s));
-    DMK_CUDA_TRY(cub::DeviceScan::ExclusiveSum(scratch.alloc_bytes(bytes), bytes, T.leaf_ntile, T.leaf_tile0,
-                                               static_cast<int>(n_leaf), s));
-  }
-  k_scan_total<<<1, 1, 0, s>>>(static_cast<int>(n_leaf), T.leaf_ntile, T.leaf_tile0, d_ntile);
+  scan_counts(T.leaf_ntile, T.leaf_tile0, static_cast<int>(n_leaf), s, scratch, d_ntile, p.launches);
   T.tile_leaf = A.alloc<int32_t>(tile_cap);
   T.tile_start = A.alloc<int32_t>(tile_cap);
   T.tile_count = A.alloc<int32_t>(tile_cap);
@@ -655,7 +694,7 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   k_rel_bbox<D><<<grid_for(tile_cap * 32, 256), 256, 0, s>>>(
       d_ntile, N, T.tile_leaf, T.tile_start, T.tile_count, T.leaf_anchor, T.leaf_level, T.w, M, T.rel,
       T.tile_lo, T.tile_hi);
-  p.launches += 4;
+  p.launches += 3;
   DMK_CUDA_TRY(cudaGetLastError());
   DMK_CUDA_TRY(cudaMemcpyAsync(h_pin + 5, d_ntile, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   DMK_CUDA_TRY(cudaStreamSynchronize(s));
