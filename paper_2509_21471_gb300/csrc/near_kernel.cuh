@@ -245,7 +245,10 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
   constexpr bool COMP = (NR == 1);                     // two-sum accumulation
   __shared__ float4 s_tst[4][4][8];                    // test rows: -2 s (x, y, z), |s|^2 - nu'^2
   __shared__ float4 s_pos[4][kTile];                   // s (x, y, z) in the target leaf's frame
-  __shared__ float4 s_f[(KM & 1) ? 4 : 1][(KM & 1) ? NR : 1][kTile];
+  constexpr int NP = (NR > 1) ? NR / 2 : 1;          // force columns in packed pairs (NR > 1)
+  __shared__ float4 s_f[(KM & 1) ? 4 : 1][1][kTile];
+  __shared__ float4 s_fxy[(NR > 1) ? 4 : 1][NP][kTile];  // (x_k, x_k+1, y_k, y_k+1)
+  __shared__ float2 s_fz[(NR > 1) ? 4 : 1][NP][kTile];   // (z_k, z_k+1)
   __shared__ float4 s_g[(KM & 2) ? 4 : 1][kTile];
   __shared__ float4 s_n[(KM & 2) ? 4 : 1][kTile];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -267,9 +270,11 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
   float* const rowz = reinterpret_cast<float*>(s_tst[wid][2]);
   float* const roww = reinterpret_cast<float*>(s_tst[wid][3]);
 
-  float uh[NR][3], ul[COMP ? 3 : 1];
+  float uh[1][3], ul[COMP ? 3 : 1];
+  uh[0][0] = uh[0][1] = uh[0][2] = 0.f;
+  float2 uh2[NP][3];
 #pragma unroll
-  for (int k = 0; k < NR; ++k) uh[k][0] = uh[k][1] = uh[k][2] = 0.f;
+  for (int k = 0; k < NP; ++k) uh2[k][0] = uh2[k][1] = uh2[k][2] = f2(0.f, 0.f);
 #pragma unroll
   for (int a = 0; a < (COMP ? 3 : 1); ++a) ul[a] = 0.f;
   float Gh[GRAD ? 9 : 1], Gl[GRAD ? 9 : 1];
@@ -296,9 +301,18 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
         rowz[lane] = -2.f * sz;
         roww[lane] = fmaf(sx, sx, fmaf(sy, sy, sz * sz)) - nu2m;
         s_pos[wid][lane] = make_float4(sx, sy, sz, 0.f);
-        if (KM & 1)
+        if (KM & 1) {
+          if (NR == 1) {
+            s_f[(KM & 1) ? wid : 0][0][lane] = P.f32[s0 + lane];
+          } else {
 #pragma unroll
-          for (int k = 0; k < NR; ++k) s_f[(KM & 1) ? wid : 0][(KM & 1) ? k : 0][lane] = P.f32[k * N + s0 + lane];
+            for (int kp = 0; kp < NP; ++kp) {
+              const float4 fa = P.f32[(2 * kp) * N + s0 + lane], fb = P.f32[(2 * kp + 1) * N + s0 + lane];
+              s_fxy[(NR > 1) ? wid : 0][kp][lane] = make_float4(fa.x, fb.x, fa.y, fb.y);
+              s_fz[(NR > 1) ? wid : 0][kp][lane] = f2(fa.z, fb.z);
+            }
+          }
+        }
         if (KM & 2) {
           s_g[(KM & 2) ? wid : 0][lane] = P.g32[s0 + lane];
           s_n[(KM & 2) ? wid : 0][lane] = P.n32[s0 + lane];
@@ -311,9 +325,10 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
       // candidate test (margin 2^-12 nu^2, far above its rounding error), then
       // the exact test r^2 < nu^2 for the sources some lane marked
       uint32_t m = __reduce_or_sync(0xffffffffu, candidate_mask(s_tst[wid], xt, tt));
-      float p[NR][3];
+      float p[1][3] = {{0.f, 0.f, 0.f}};
+      float2 p2[NP][3];
 #pragma unroll
-      for (int k = 0; k < NR; ++k) p[k][0] = p[k][1] = p[k][2] = 0.f;
+      for (int k = 0; k < NP; ++k) p2[k][0] = p2[k][1] = p2[k][2] = f2(0.f, 0.f);
       float pg[GRAD ? 9 : 1];
 #pragma unroll
       for (int k = 0; k < (GRAD ? 9 : 1); ++k) pg[k] = 0.f;
@@ -347,9 +362,23 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
           }
           float2 dgh = f2(0.f, 0.f);
           if (GRAD) dgh = horner2<NT>(P.c32p[2], t);
+          if (NR > 1) {
+            // several columns: the kernel terms once, applied to two columns per
+            // packed FP32x2 instruction
+            const float2 A2 = f2(A, A), C2 = f2(C, C), dx2 = f2(dx, dx), dy2 = f2(dy, dy), dz2 = f2(dz, dz);
 #pragma unroll
-          for (int k = 0; k < NR; ++k) {
-            const float4 fs = s_f[(KM & 1) ? wid : 0][(KM & 1) ? k : 0][j];
+            for (int kp = 0; kp < NP; ++kp) {
+              const float4 fxy = s_fxy[(NR > 1) ? wid : 0][kp][j];
+              const float2 fx2 = f2(fxy.x, fxy.y), fy2 = f2(fxy.z, fxy.w), fz2 = s_fz[(NR > 1) ? wid : 0][kp][j];
+              const float2 Cx2 = __fmul2_rn(C2, __ffma2_rn(dx2, fx2, __ffma2_rn(dy2, fy2, __fmul2_rn(dz2, fz2))));
+              p2[kp][0] = __ffma2_rn(A2, fx2, __ffma2_rn(Cx2, dx2, p2[kp][0]));
+              p2[kp][1] = __ffma2_rn(A2, fy2, __ffma2_rn(Cx2, dy2, p2[kp][1]));
+              if (D == 3) p2[kp][2] = __ffma2_rn(A2, fz2, __ffma2_rn(Cx2, dz2, p2[kp][2]));
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < (NR == 1 ? 1 : 0); ++k) {
+            const float4 fs = s_f[(KM & 1) ? wid : 0][0][j];
             const float xf = fmaf(dx, fs.x, fmaf(dy, fs.y, dz * fs.z));
             const float Cx = C * xf;
             p[k][0] = fmaf(A, fs.x, fmaf(Cx, dx, p[k][0]));
@@ -400,9 +429,9 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
         for (int a = 0; a < D; ++a) two_sum_add(uh[0][a], ul[a], p[0][a]);
       } else {
 #pragma unroll
-        for (int k = 0; k < NR; ++k)
+        for (int k = 0; k < NP; ++k)
 #pragma unroll
-          for (int a = 0; a < D; ++a) uh[k][a] += p[k][a];
+          for (int a = 0; a < D; ++a) uh2[k][a] = __fadd2_rn(uh2[k][a], p2[k][a]);
       }
       if (GRAD) {
 #pragma unroll
@@ -420,7 +449,8 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
       if (k >= nr) break;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
-        double v = static_cast<double>(uh[k][a]);
+        double v = (NR == 1) ? static_cast<double>(uh[0][a])
+                             : static_cast<double>((k & 1) ? uh2[k >> 1][a].y : uh2[k >> 1][a].x);
         if (COMP) v += static_cast<double>(ul[a]);
         v *= kInv8Pi;
         const int64_t q = (o * D + a) * nr + k;
