@@ -136,7 +136,7 @@ dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const do
  *   Arguments, layouts and results: as dmk_stokes_eval.
  *   Limit: plans needing more than 64 MiB of scratch (with n_rhs = 1: mixed
  *   precision at eps >= 2e-7 128 bytes per point, about 524k points; mixed
- *   below 2e-7 192 bytes per point, about 349k points; FP64 104 bytes per
+ *   below 2e-7 288 bytes per point in 3D (192 in 2D), about 233k points; FP64 104 bytes per
  *   point, about 645k points; more with several force columns; plus 32
  *   bytes per system) return DMK_ERR_INVALID_ARG before any work is queued.
  *   The plan's device must be current.

@@ -242,8 +242,9 @@ bool ff_pairs(const dmk_stokes_opts_t& o) {
 
 // workspace: [FP32 sorted densities (fp32 pairs)] [FP64 sorted densities]
 // [FF split densities] [FP64 accumulator of the symmetric FP64 pass]
+// [FP64 accumulator of the symmetric float-float gradient pass, 12 per point]
 struct WsLayout {
-  size_t f64_off, ff_off, acc_off, bytes;
+  size_t f64_off, ff_off, acc_off, accg_off, bytes;
 };
 WsLayout ws_layout(const dmk_stokes_opts_t& o, int64_t N) {
   const int NR = padded_rhs(o.n_rhs);
@@ -252,7 +253,8 @@ WsLayout ws_layout(const dmk_stokes_opts_t& o, int64_t N) {
   L.ff_off = L.f64_off + std::max(3 + 3 + 4, 3 * NR) * N * sizeof(double);
   L.acc_off = L.ff_off + (ff_pairs(o) ? 7 * N * sizeof(float4) : 0);
   const bool fp64_sym = o.precision == DMK_PRECISION_FP64 && o.n_rhs == 1;
-  L.bytes = L.acc_off + (fp64_sym ? 3 * N * sizeof(double) : 0);
+  L.accg_off = L.acc_off + (fp64_sym ? 3 * N * sizeof(double) : 0);
+  L.bytes = L.accg_off + ((ff_pairs(o) && o.dim == 3) ? 12 * N * sizeof(double) : 0);
   return L;
 }
 
@@ -468,7 +470,13 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   }
   if (T.n_tile > 0) {
     const bool fp64_sym = !mixed && !ff && NR == 1 && !grad && d_u;
-    if ((mixed && km == 1 && !grad && NR == 1 && d_u) || (ff && !grad) || fp64_sym) {
+    if (ff && grad) {
+      // symmetric float-float gradient pass: velocity and gradient accumulated
+      // both ways, 12 values per point
+      P.acc = reinterpret_cast<double*>(ws + ws_layout(p.opts, N).accg_off);
+      DMK_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(double) * 12 * N, s));
+      ++p.launches;                                   // the finishing kernel
+    } else if ((mixed && km == 1 && !grad && NR == 1 && d_u) || (ff && !grad) || fp64_sym) {
       // symmetric passes (FP32 Stokeslet; float-float and FP64 Stokeslet and
       // stresslet): both points of a pair from one evaluation, summed in a
       // zeroed FP64 accumulator (FP32 / FF: the first 3N doubles of the FP64

@@ -193,9 +193,9 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
   __shared__ float4 s_th[4][kTile], s_tl[4][kTile];  // targets, FF
   __shared__ uint16_t s_q[4][kFFQueue];              // queue: target lane << 5 | source slot
   __shared__ float2 s_r[4][NO][kFFQueue];            // per queued pair: contributions (hi, lo)
-  // symmetric pass (all but the gradient): the targets' densities for the
-  // source side of each pair
-  constexpr bool SYM = !GRAD;
+  // symmetric pass: the targets' densities for the source side of each pair
+  // (the gradient of the source is minus the derivative at x: grad S_R is odd)
+  constexpr bool SYM = true;
   __shared__ float4 s_tfh[(SYM && (KM & 1)) ? 4 : 1][kTile], s_tfl[(SYM && (KM & 1)) ? 4 : 1][kTile];
   __shared__ float4 s_tgh[(SYM && (KM & 2)) ? 4 : 1][kTile], s_tgl[(SYM && (KM & 2)) ? 4 : 1][kTile];
   __shared__ float4 s_tnh[(SYM && (KM & 2)) ? 4 : 1][kTile], s_tnl[(SYM && (KM & 2)) ? 4 : 1][kTile];
@@ -347,6 +347,9 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
             const ff xv[3] = {dx, dy, dz};
             ff out[NO];
             ff src[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};   // source side (symmetric pass)
+            ff srcg[GRAD ? 9 : 1];                             // source side of the gradient
+#pragma unroll
+            for (int a = 0; a < (GRAD ? 9 : 1); ++a) srcg[a] = {0.f, 0.f};
             if (KM & 1) {
               const ff2 gh = horner_ff2<NT>(F.chi[0], F.clo[0], t);
               ff A, C;
@@ -393,6 +396,25 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
                     ff v = ff_add(ff_mul(a1, xv[mm]), ff_mul(cx, fv[mm]));
                     if (jj == mm) v = ff_add(v, Cxf);
                     out[3 + jj * 3 + mm] = v;
+                  }
+                }
+                if (SYM && both) {
+                  // the source's gradient: minus the same expression with f_t
+                  const float4 th4 = s_tfh[(SYM && (KM & 1)) ? wid : 0][tl];
+                  const float4 tl4 = s_tfl[(SYM && (KM & 1)) ? wid : 0][tl];
+                  const ff ftv[3] = {{th4.x, tl4.x}, {th4.y, tl4.y}, {th4.z, tl4.z}};
+                  const ff xft = ff_add(ff_add(ff_mul(dx, ftv[0]), ff_mul(dy, ftv[1])), ff_mul(dz, ftv[2]));
+                  const ff Cxft = ff_mul(C, xft);
+#pragma unroll
+                  for (int jj = 0; jj < 3; ++jj) {
+                    const ff a1 = ff_add(ff_mul(A1, ftv[jj]), ff_mul(ff_mul(C1, xv[jj]), xft));
+                    const ff cx = ff_mul(C, xv[jj]);
+#pragma unroll
+                    for (int mm = 0; mm < 3; ++mm) {
+                      ff v = ff_add(ff_mul(a1, xv[mm]), ff_mul(cx, ftv[mm]));
+                      if (jj == mm) v = ff_add(v, Cxft);
+                      srcg[jj * 3 + mm] = ff_neg(v);
+                    }
                   }
                 }
               }
@@ -451,9 +473,13 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
                 }
               }
             }
-            if (SYM && both)
+            if (SYM && both) {
 #pragma unroll
-              for (int a = 0; a < D; ++a) atomicAdd(P.acc + (s0 + j) * D + a, ff_to_double(src[a]));
+              for (int a = 0; a < D; ++a) atomicAdd(P.acc + (s0 + j) * NO + a, ff_to_double(src[a]));
+              if (GRAD)
+#pragma unroll
+                for (int a = 0; a < 9; ++a) atomicAdd(P.acc + (s0 + j) * NO + 3 + a, ff_to_double(srcg[a]));
+            }
 #pragma unroll
             for (int a = 0; a < NO; ++a) res[a] = make_float2(out[a].hi, out[a].lo);
           }
@@ -475,31 +501,37 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
     }
   }
   if (!on) return;
-  const int64_t o = P.perm[t0 + lane];
-  const double sc = self_coeff<D>(P, LB);
-  if (SYM) {
-    // both sides meet in the sorted FP64 accumulator, finished by k_near_sym_finish
+  // both sides meet in the sorted FP64 accumulator (NO values per point),
+  // finished by k_near_sym_finish / k_near_sym_finish_grad
 #pragma unroll
-    for (int a = 0; a < D; ++a) atomicAdd(P.acc + (t0 + lane) * D + a, ff_to_double(acc[a]));
-  } else if (P.u) {
+  for (int a = 0; a < NO; ++a) atomicAdd(P.acc + (t0 + lane) * NO + a, ff_to_double(acc[a]));
+  (void)LB;
+}
+
+// velocity (if asked) and gradient from the accumulator of the symmetric
+// gradient pass: u at [0, 3), grad u at [3, 12) per sorted point
+template <int D>
+__global__ void k_near_sym_finish_grad(const __grid_constant__ NearParams P, const double* __restrict__ acc) {
+  static_assert(D == 3, "the gradient is 3D");
+  const int tile = static_cast<int>((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (tile >= P.n_tile || lane >= P.tile_count[tile]) return;
+  const int64_t i = P.tile_start[tile] + lane;
+  const int64_t o = P.perm[i];
+  if (P.u) {
+    const double sc = self_coeff<3>(P, P.leaf_level[P.tile_leaf[tile]]);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      double v = ff_to_double(acc[a]) * kInv8Pi;
-      const int64_t q = o * D + a;
-      if (KM & 1) v += sc * P.f_orig[q];
-      P.u[q] = v;
-    }
+    for (int a = 0; a < 3; ++a) P.u[o * 3 + a] = acc[i * 12 + a] * kInv8Pi + sc * P.f_orig[o * 3 + a];
   }
-  if (GRAD) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) P.gradu[o * 9 + k] = ff_to_double(acc[3 + k]) * kInv8Pi;
-  }
+  for (int k = 0; k < 9; ++k) P.gradu[o * 9 + k] = acc[i * 12 + 3 + k] * kInv8Pi;
 }
 
 template <int D, int KM, bool GRAD, int NT>
 void run_near_ff(const NearParams& P, const FFParams& F, cudaStream_t s) {
   k_near_ff<D, KM, GRAD, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, F);
-  if (!GRAD) k_near_sym_finish<D, KM><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
+  if (GRAD) k_near_sym_finish_grad<3><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
+  else k_near_sym_finish<D, KM><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
 }
 
 #define DMK_FOR_EACH_FF(M, NT)                                                    \

@@ -14,7 +14,8 @@
 //   * the array holds kNoAllocScratchBytes (64 MiB); a plan whose evaluation
 //     needs more is rejected with DMK_ERR_INVALID_ARG before anything runs
 //     (mixed precision at eps >= 2e-7: 128 bytes per point, about 524k
-//     points; mixed below 2e-7: 192 bytes per point, about 349k points; FP64:
+//     points; mixed below 2e-7: 288 bytes per point in 3D (192 in
+//     2D), about 233k points; FP64:
 //     104 bytes per point, about 645k points; plus 32 bytes per system);
 //   * every GPU that loads the library holds the array until the process exits;
 //   * all calls on a device share the array and it keeps the last call's
