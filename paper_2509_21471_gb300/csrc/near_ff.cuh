@@ -475,10 +475,10 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
             }
             if (SYM && both) {
 #pragma unroll
-              for (int a = 0; a < D; ++a) atomicAdd(P.acc + (s0 + j) * NO + a, ff_to_double(src[a]));
+              for (int a = 0; a < D; ++a) atomicAdd(P.acc + (static_cast<int64_t>(s0) + j) * NO + a, ff_to_double(src[a]));
               if (GRAD)
 #pragma unroll
-                for (int a = 0; a < 9; ++a) atomicAdd(P.acc + (s0 + j) * NO + 3 + a, ff_to_double(srcg[a]));
+                for (int a = 0; a < 9; ++a) atomicAdd(P.acc + (static_cast<int64_t>(s0) + j) * NO + 3 + a, ff_to_double(srcg[a]));
             }
 #pragma unroll
             for (int a = 0; a < NO; ++a) res[a] = make_float2(out[a].hi, out[a].lo);
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearPar
   // both sides meet in the sorted FP64 accumulator (NO values per point),
   // finished by k_near_sym_finish / k_near_sym_finish_grad
 #pragma unroll
-  for (int a = 0; a < NO; ++a) atomicAdd(P.acc + (t0 + lane) * NO + a, ff_to_double(acc[a]));
+  for (int a = 0; a < NO; ++a) atomicAdd(P.acc + (static_cast<int64_t>(t0) + lane) * NO + a, ff_to_double(acc[a]));
   (void)LB;
 }
 

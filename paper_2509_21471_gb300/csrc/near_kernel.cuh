@@ -578,13 +578,13 @@ __global__ void __launch_bounds__(128) k_near_sym(const __grid_constant__ NearPa
       for (int a = 0; a < D; ++a) two_sum_add(uh[a], ul[a], p[a]);
       if (sym && lane < ns && (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f))
 #pragma unroll
-        for (int a = 0; a < D; ++a) atomicAdd(acc + (s0 + lane) * D + a, static_cast<double>(q[a]));
+        for (int a = 0; a < D; ++a) atomicAdd(acc + (static_cast<int64_t>(s0) + lane) * D + a, static_cast<double>(q[a]));
     }
   }
   if (on)
 #pragma unroll
     for (int a = 0; a < D; ++a)
-      atomicAdd(acc + (t0 + lane) * D + a, static_cast<double>(uh[a]) + static_cast<double>(ul[a]));
+      atomicAdd(acc + (static_cast<int64_t>(t0) + lane) * D + a, static_cast<double>(uh[a]) + static_cast<double>(ul[a]));
   (void)N;
 }
 
@@ -859,7 +859,7 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
           pair(w3, idx, a, gr, ss0 >= 0 ? tl : -1, sr);
           if (SYM64 && ss0 >= 0 && (sr[0] != 0.0 || sr[1] != 0.0 || sr[2] != 0.0))
 #pragma unroll
-            for (int c = 0; c < D; ++c) atomicAdd(P.acc + (ss0 + (idx & 31)) * D + c, sr[c]);
+            for (int c = 0; c < D; ++c) atomicAdd(P.acc + (static_cast<int64_t>(ss0) + (idx & 31)) * D + c, sr[c]);
 #pragma unroll
           for (int c = 0; c < D; ++c) s_r[qw][c % NO][qi] = a[0][c];
           if (GRAD)
@@ -938,7 +938,7 @@ __global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearP
   if (SYM64 && P.acc) {
     // both sides meet in the sorted accumulator, finished by k_near_sym_finish
 #pragma unroll
-    for (int a = 0; a < D; ++a) atomicAdd(P.acc + (t0 + lane) * D + a, acc[0][a]);
+    for (int a = 0; a < D; ++a) atomicAdd(P.acc + (static_cast<int64_t>(t0) + lane) * D + a, acc[0][a]);
     return;
   }
   const int64_t o = P.perm[t0 + lane];
