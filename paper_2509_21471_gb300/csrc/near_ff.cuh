@@ -179,28 +179,31 @@ __device__ __forceinline__ ff ff_log(ff x) {
 // Eq. (res_stokeslet) with the tree held fixed:
 //   d_m (S_R f)_j = A1 x_m f_j + C1 x_m x_j (x.f) + C (delta_jm (x.f) + x_j f_m)
 //   A1 = -1/r^3 + 2 gS'/nu^3,  C1 = -3/r^5 + (2 hS'/nu^3 - 2 hS/(nu r^2))/r^2.
+// warps (target tiles) per block: measured best on GB300 (3D 4, 2D 1)
+template <int D> constexpr int kFFWarps = (D == 3) ? 4 : 1;
 template <int D, int KM, bool GRAD, int NT>
-__global__ void __launch_bounds__(128) k_near_ff(const __grid_constant__ NearParams P,
-                                                 const __grid_constant__ FFParams F) {
+__global__ void __launch_bounds__(32 * kFFWarps<D>) k_near_ff(const __grid_constant__ NearParams P,
+                                                           const __grid_constant__ FFParams F) {
   static_assert(!GRAD || (KM == 1 && D == 3), "the gradient kernel is the 3D Stokeslet's");
   constexpr int NO = GRAD ? 12 : D;                  // outputs per pair: u (D) [+ grad u (9)]
   constexpr int kFFQueue = GRAD ? 64 : 128;          // candidate pairs evaluated per round (per warp)
-  __shared__ float4 s_tst[4][4][8];                 // FP32 test rows (as in the mixed kernel)
-  __shared__ float4 s_ph[4][kTile], s_pl[4][kTile];  // source position in the target frame, FF
-  __shared__ float4 s_ah[4][kTile], s_al[4][kTile];  // Stokeslet force / stresslet strength, FF
-  __shared__ float4 s_nh[(KM & 2) ? 4 : 1][kTile], s_nl[(KM & 2) ? 4 : 1][kTile];   // orientation, .w = g.n
-  __shared__ float4 s_bh[(KM == 3) ? 4 : 1][kTile], s_bl[(KM == 3) ? 4 : 1][kTile];  // stresslet strength if both
-  __shared__ float4 s_th[4][kTile], s_tl[4][kTile];  // targets, FF
-  __shared__ uint16_t s_q[4][kFFQueue];              // queue: target lane << 5 | source slot
-  __shared__ float2 s_r[4][NO][kFFQueue];            // per queued pair: contributions (hi, lo)
+  constexpr int W = kFFWarps<D>;
+  __shared__ float4 s_tst[W][4][8];                  // FP32 test rows (as in the mixed kernel)
+  __shared__ float4 s_ph[W][kTile], s_pl[W][kTile];  // source position in the target frame, FF
+  __shared__ float4 s_ah[W][kTile], s_al[W][kTile];  // Stokeslet force / stresslet strength, FF
+  __shared__ float4 s_nh[(KM & 2) ? W : 1][kTile], s_nl[(KM & 2) ? W : 1][kTile];   // orientation, .w = g.n
+  __shared__ float4 s_bh[(KM == 3) ? W : 1][kTile], s_bl[(KM == 3) ? W : 1][kTile];  // stresslet strength if both
+  __shared__ float4 s_th[W][kTile], s_tl[W][kTile];  // targets, FF
+  __shared__ uint16_t s_q[W][kFFQueue];              // queue: target lane << 5 | source slot
+  __shared__ float2 s_r[W][NO][kFFQueue];            // per queued pair: contributions (hi, lo)
   // symmetric pass: the targets' densities for the source side of each pair
   // (the gradient of the source is minus the derivative at x: grad S_R is odd)
   constexpr bool SYM = true;
-  __shared__ float4 s_tfh[(SYM && (KM & 1)) ? 4 : 1][kTile], s_tfl[(SYM && (KM & 1)) ? 4 : 1][kTile];
-  __shared__ float4 s_tgh[(SYM && (KM & 2)) ? 4 : 1][kTile], s_tgl[(SYM && (KM & 2)) ? 4 : 1][kTile];
-  __shared__ float4 s_tnh[(SYM && (KM & 2)) ? 4 : 1][kTile], s_tnl[(SYM && (KM & 2)) ? 4 : 1][kTile];
+  __shared__ float4 s_tfh[(SYM && (KM & 1)) ? W : 1][kTile], s_tfl[(SYM && (KM & 1)) ? W : 1][kTile];
+  __shared__ float4 s_tgh[(SYM && (KM & 2)) ? W : 1][kTile], s_tgl[(SYM && (KM & 2)) ? W : 1][kTile];
+  __shared__ float4 s_tnh[(SYM && (KM & 2)) ? W : 1][kTile], s_tnl[(SYM && (KM & 2)) ? W : 1][kTile];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * 4 + wid;
+  const int tile = blockIdx.x * W + wid;
   if (tile >= P.n_tile) return;
   const int B = P.tile_leaf[tile];
   const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
@@ -529,7 +532,7 @@ __global__ void k_near_sym_finish_grad(const __grid_constant__ NearParams P, con
 
 template <int D, int KM, bool GRAD, int NT>
 void run_near_ff(const NearParams& P, const FFParams& F, cudaStream_t s) {
-  k_near_ff<D, KM, GRAD, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, F);
+  k_near_ff<D, KM, GRAD, NT><<<(P.n_tile + kFFWarps<D> - 1) / kFFWarps<D>, 32 * kFFWarps<D>, 0, s>>>(P, F);
   if (GRAD) k_near_sym_finish_grad<3><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
   else k_near_sym_finish<D, KM><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
 }

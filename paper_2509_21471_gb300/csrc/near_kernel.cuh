@@ -238,21 +238,23 @@ __device__ __forceinline__ uint32_t candidate_mask(const float4 (&rows)[4][8], f
   return bits;
 }
 
+constexpr int kMixWarps = 1;                           // warps (target tiles) per block
 template <int D, int KM, bool GRAD, int NT, int NR>
-__global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ NearParams P) {
+__global__ void __launch_bounds__(32 * kMixWarps) k_near_mixed(const __grid_constant__ NearParams P) {
   static_assert(NR == 1 || (KM == 1 && !GRAD), "several force columns: Stokeslet velocity only");
   static_assert(D == 3 || !GRAD, "the gradient kernel is 3D");
   constexpr bool COMP = (NR == 1);                     // two-sum accumulation
-  __shared__ float4 s_tst[4][4][8];                    // test rows: -2 s (x, y, z), |s|^2 - nu'^2
-  __shared__ float4 s_pos[4][kTile];                   // s (x, y, z) in the target leaf's frame
+  constexpr int W = kMixWarps;
+  __shared__ float4 s_tst[W][4][8];                    // test rows: -2 s (x, y, z), |s|^2 - nu'^2
+  __shared__ float4 s_pos[W][kTile];                   // s (x, y, z) in the target leaf's frame
   constexpr int NP = (NR > 1) ? NR / 2 : 1;          // force columns in packed pairs (NR > 1)
-  __shared__ float4 s_f[(KM & 1) ? 4 : 1][1][kTile];
-  __shared__ float4 s_fxy[(NR > 1) ? 4 : 1][NP][kTile];  // (x_k, x_k+1, y_k, y_k+1)
-  __shared__ float2 s_fz[(NR > 1) ? 4 : 1][NP][kTile];   // (z_k, z_k+1)
-  __shared__ float4 s_g[(KM & 2) ? 4 : 1][kTile];
-  __shared__ float4 s_n[(KM & 2) ? 4 : 1][kTile];
+  __shared__ float4 s_f[(KM & 1) ? W : 1][1][kTile];
+  __shared__ float4 s_fxy[(NR > 1) ? W : 1][NP][kTile];  // (x_k, x_k+1, y_k, y_k+1)
+  __shared__ float2 s_fz[(NR > 1) ? W : 1][NP][kTile];   // (z_k, z_k+1)
+  __shared__ float4 s_g[(KM & 2) ? W : 1][kTile];
+  __shared__ float4 s_n[(KM & 2) ? W : 1][kTile];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * 4 + wid;
+  const int tile = blockIdx.x * W + wid;
   if (tile >= P.n_tile) return;
   const int64_t N = P.N;
   const int B = P.tile_leaf[tile];
@@ -476,14 +478,18 @@ __global__ void __launch_bounds__(128) k_near_mixed(const __grid_constant__ Near
 // each union source is summed over the warp by shuffles into the lane that
 // owns the source slot, and both sides are added to an FP64 accumulator in
 // sorted order (atomically), finished by k_near_sym_finish.
+constexpr int kSymWarps = 1;                           // warps (target tiles) per block
 template <int D, int NT>
-__global__ void __launch_bounds__(128) k_near_sym(const __grid_constant__ NearParams P, double* __restrict__ acc) {
-  __shared__ float4 s_tst[4][4][8];
-  __shared__ float4 s_pos[4][kTile];
-  __shared__ float4 s_f[4][kTile];
+__global__ void __launch_bounds__(32 * kSymWarps, 28 / kSymWarps) k_near_sym(const __grid_constant__ NearParams P, double* __restrict__ acc) {
+  __shared__ float4 s_tst[kSymWarps][4][8];
+  __shared__ float4 s_pos[kSymWarps][kTile];
+  __shared__ float4 s_f[kSymWarps][kTile];
+  __shared__ float s_q[kSymWarps][kTile * 3];          // source side of the staged tile
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * 4 + wid;
+  const int tile = blockIdx.x * kSymWarps + wid;
   if (tile >= P.n_tile) return;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) s_q[wid][lane * 3 + a] = 0.f;
   const int64_t N = P.N;
   const int B = P.tile_leaf[tile];
   const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
@@ -532,15 +538,13 @@ __global__ void __launch_bounds__(128) k_near_sym(const __grid_constant__ NearPa
       __syncwarp();
       uint32_t m = __reduce_or_sync(0xffffffffu, candidate_mask(s_tst[wid], xt, tt));
       float p[3] = {0.f, 0.f, 0.f};                    // target side, this tile
-      float q[3] = {0.f, 0.f, 0.f};                    // source side of slot `lane`
-      while (m) {
-        const int j = __ffs(m) - 1;
-        m &= m - 1u;
+      // One pair (this lane's target, staged source j): adds the target side
+      // to p and returns the source side (A f_t + C (x.f_t) x) in c.
+      auto pair = [&](int j, float (&c)[3]) {
         const float4 sp = s_pos[wid][j];
         const float dx = xt.x - sp.x, dy = xt.y - sp.y, dz = xt.z - sp.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const bool inside = r2 < nu2 && r2 > 0.f;
-        if (!__any_sync(0xffffffffu, inside)) continue;
         const float rr = inside ? r2 : nu2;            // finite stand-in for the other lanes
         const float rho2 = rr * nu2inv;
         const float t = fmaf(2.f, rho2, -1.f);
@@ -562,23 +566,77 @@ __global__ void __launch_bounds__(128) k_near_sym(const __grid_constant__ NearPa
         p[0] = fmaf(A, fs.x, fmaf(Cx, dx, p[0]));
         p[1] = fmaf(A, fs.y, fmaf(Cx, dy, p[1]));
         if (D == 3) p[2] = fmaf(A, fs.z, fmaf(Cx, dz, p[2]));
-        if (sym) {
-          const float Ct = C * fmaf(dx, ft.x, fmaf(dy, ft.y, dz * ft.z));
-          float c[3] = {fmaf(A, ft.x, Ct * dx), fmaf(A, ft.y, Ct * dy), D == 3 ? fmaf(A, ft.z, Ct * dz) : 0.f};
+        const float Ct = C * fmaf(dx, ft.x, fmaf(dy, ft.y, dz * ft.z));
+        c[0] = fmaf(A, ft.x, Ct * dx);
+        c[1] = fmaf(A, ft.y, Ct * dy);
+        c[2] = D == 3 ? fmaf(A, ft.z, Ct * dz) : 0.f;
+      };
+      if (!sym) {
+        float c[3];
+        while (m) {
+          const int j = __ffs(m) - 1;
+          m &= m - 1u;
+          pair(j, c);
+        }
+      } else {
+        // The source sides of two consecutive sources (2 x 3 components,
+        // padded to 4) are summed over the warp together by a transposing
+        // butterfly: each exchange halves the values a lane keeps, so 7
+        // shuffles sum all six, leaving the total of (source s, component a)
+        // in lane 16 s + 4 a, which stores it in the source's slot.
+        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+        const int a_own = (b3 ? 2 : 0) + (b2 ? 1 : 0);
+        auto reduce2 = [&](const float (&c0)[3], const float (&c1)[3], int j0, int j1) {
+          float x[3];
 #pragma unroll
-          for (int a = 0; a < D; ++a)
+          for (int a = 0; a < 3; ++a) {                  // keep source b4
+            const float send = b4 ? c0[a] : c1[a];
+            x[a] = (b4 ? c1[a] : c0[a]) + __shfl_xor_sync(0xffffffffu, send, 16);
+          }
+          // keep components {0, 1} (b3 = 0) or {2, pad} (b3 = 1)
+          const float y0 = (b3 ? x[2] : x[0]) + __shfl_xor_sync(0xffffffffu, b3 ? x[0] : x[2], 8);
+          const float y1 = (b3 ? 0.f : x[1]) + __shfl_xor_sync(0xffffffffu, b3 ? x[1] : 0.f, 8);
+          float z = (b2 ? y1 : y0) + __shfl_xor_sync(0xffffffffu, b2 ? y0 : y1, 4);
+          z += __shfl_xor_sync(0xffffffffu, z, 2);
+          z += __shfl_xor_sync(0xffffffffu, z, 1);
+          const int js = b4 ? j1 : j0;
+          if ((lane & 3) == 0 && a_own < 3 && js >= 0) s_q[wid][js * 3 + a_own] = z;   // each slot once per tile
+        };
+        int jp = -1;                                     // source held back for the next round
+        float cp[3] = {0.f, 0.f, 0.f};
+        while (m) {
+          const int j = __ffs(m) - 1;
+          m &= m - 1u;
+          float c[3];
+          pair(j, c);
+          if (jp < 0) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c[a] += __shfl_xor_sync(0xffffffffu, c[a], o);
-          if (lane == j)
-#pragma unroll
-            for (int a = 0; a < D; ++a) q[a] += c[a];
+            for (int a = 0; a < 3; ++a) cp[a] = c[a];
+            jp = j;
+            continue;
+          }
+          reduce2(cp, c, jp, j);
+          jp = -1;
+        }
+        if (jp >= 0) {
+          const float z3[3] = {0.f, 0.f, 0.f};
+          reduce2(cp, z3, jp, -1);
         }
       }
 #pragma unroll
       for (int a = 0; a < D; ++a) two_sum_add(uh[a], ul[a], p[a]);
-      if (sym && lane < ns && (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f))
+      __syncwarp();
+      if (sym && lane < ns) {
+        float q[3];
 #pragma unroll
-        for (int a = 0; a < D; ++a) atomicAdd(acc + (static_cast<int64_t>(s0) + lane) * D + a, static_cast<double>(q[a]));
+        for (int a = 0; a < 3; ++a) {
+          q[a] = s_q[wid][lane * 3 + a];
+          s_q[wid][lane * 3 + a] = 0.f;
+        }
+        if (q[0] != 0.f || q[1] != 0.f || q[2] != 0.f)
+#pragma unroll
+          for (int a = 0; a < D; ++a) atomicAdd(acc + (static_cast<int64_t>(s0) + lane) * D + a, static_cast<double>(q[a]));
+      }
     }
   }
   if (on)
@@ -615,7 +673,7 @@ struct Fp64Shape {
 };
 
 template <int D, int KM, bool GRAD, int NT, int NR>
-__global__ void __launch_bounds__(128) k_near_fp64(const __grid_constant__ NearParams P) {
+__global__ void __launch_bounds__(32 * Fp64Shape<D, KM, GRAD, NT, NR>::WPB) k_near_fp64(const __grid_constant__ NearParams P) {
   static_assert(NR == 1 || (KM == 1 && !GRAD), "several force columns: Stokeslet velocity only");
   static_assert(D == 3 || !GRAD, "the gradient kernel is 3D");
   constexpr int NB = Fp64Shape<D, KM, GRAD, NT, NR>::NB;
@@ -967,12 +1025,12 @@ template <int D, int KM, bool GRAD, int NT, int NR>
 void run_near_mixed(const NearParams& P, cudaStream_t s) {
   if constexpr (KM == 1 && !GRAD && NR == 1) {
     if (P.acc && P.u) {
-      k_near_sym<D, NT><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P, P.acc);
+      k_near_sym<D, NT><<<(P.n_tile + kSymWarps - 1) / kSymWarps, 32 * kSymWarps, 0, s>>>(P, P.acc);
       k_near_sym_finish<D, 1><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
       return;
     }
   }
-  k_near_mixed<D, KM, GRAD, NT, NR><<<(P.n_tile + 3) / 4, 128, 0, s>>>(P);
+  k_near_mixed<D, KM, GRAD, NT, NR><<<(P.n_tile + kMixWarps - 1) / kMixWarps, 32 * kMixWarps, 0, s>>>(P);
 }
 template <int D, int KM, bool GRAD, int NT, int NR>
 void run_near_fp64(const NearParams& P, cudaStream_t s) {
