@@ -449,23 +449,44 @@ __global__ void k_point_sys(int n_sys, const int32_t* __restrict__ offs, int32_t
 
 // Exclusive scan of n counts by one block (n <= kSmallScan): out[i] for i < n,
 // the total in out[n] (and in *copy when given).  One launch where the library
-// scan takes three for the small arrays of the tree build.
+// scan takes three for the small arrays of the tree build.  Each warp scans a
+// contiguous segment 32 elements at a time (coalesced); a first pass forms the
+// counts (kept in out[] and, if side is given, in side[]) and the warp totals,
+// a second pass writes the prefix sums.  The counts come from a functor, so
+// that the split flags of a refinement level are formed in the same launch.
 constexpr int kSmallScan = 1024 * 64;
-__global__ void __launch_bounds__(1024) k_scan_small(int n, const int32_t* __restrict__ in,
+struct CountsIn {                                    // plain counts
+  const int32_t* in;
+  __device__ int32_t operator()(int i) const { return in[i]; }
+};
+template <int D>
+struct SplitCounts {                                 // children of leaf i: 2^D if split, else 1
+  LeafArrays L;
+  int ns, M;
+  const int32_t* flag;                               // level restriction flags, or null
+  const int32_t* d_n;                                // chained level: leaf count (slots beyond get 0)
+  __device__ int32_t operator()(int i) const {
+    if (d_n && i >= *d_n) return 0;
+    const bool split = flag ? (flag[i] != 0) : (L.count[i] > ns && L.level[i] < M);
+    return split ? (1 << D) : 1;
+  }
+};
+template <class F>
+__global__ void __launch_bounds__(1024) k_scan_small(int n, F f, int32_t* __restrict__ side,
                                                      int32_t* __restrict__ out, int32_t* __restrict__ copy) {
   __shared__ int32_t wsum[32];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int per = (n + 1023) / 1024;
-  const int b = min(t * per, n), e = min(b + per, n);
+  const int seg = (((n + 31) >> 5) + 31) & ~31;      // elements per warp, a multiple of 32
+  const int b = min(w * seg, n), e = min(b + seg, n);
   int32_t sum = 0;
-  for (int i = b; i < e; ++i) sum += in[i];
-  int32_t v = sum;                                   // inclusive scan within the warp
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t y = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += y;
+  for (int i = b + lane; i < e; i += 32) {
+    const int32_t v = f(i);
+    out[i] = v;
+    if (side) side[i] = v;
+    sum += v;
   }
-  if (lane == 31) wsum[w] = v;
+  sum = static_cast<int32_t>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(sum)));
+  if (lane == 0) wsum[w] = sum;
   __syncthreads();
   if (w == 0) {
     int32_t x = wsum[lane];
@@ -477,10 +498,18 @@ __global__ void __launch_bounds__(1024) k_scan_small(int n, const int32_t* __res
     wsum[lane] = x;                                  // inclusive over warps
   }
   __syncthreads();
-  int32_t run = v - sum + (w > 0 ? wsum[w - 1] : 0);
-  for (int i = b; i < e; ++i) {
-    out[i] = run;
-    run += in[i];
+  int32_t run = w > 0 ? wsum[w - 1] : 0;
+  for (int i0 = b; i0 < e; i0 += 32) {
+    const int i = i0 + lane;
+    const int32_t v = i < e ? out[i] : 0;            // this lane's own count from the first pass
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (i < e) out[i] = run + x - v;
+    run += __shfl_sync(0xffffffffu, x, 31);
   }
   if (t == 0) {
     out[n] = wsum[31];
@@ -492,7 +521,7 @@ __global__ void __launch_bounds__(1024) k_scan_small(int n, const int32_t* __res
 void scan_counts(const int32_t* in, int32_t* out, int n, cudaStream_t s, Arena& scratch, int32_t* copy,
                  int64_t& launches) {
   if (n <= kSmallScan) {
-    k_scan_small<<<1, 1024, 0, s>>>(n, in, out, copy);
+    k_scan_small<<<1, 1024, 0, s>>>(n, CountsIn{in}, nullptr, out, copy);
     ++launches;
   } else {
     size_t bytes = 0;
@@ -502,6 +531,25 @@ void scan_counts(const int32_t* in, int32_t* out, int n, cudaStream_t s, Arena& 
     ++launches;
   }
   DMK_CUDA_TRY(cudaGetLastError());
+}
+
+// children per leaf (nchild, n entries) and their exclusive scan (pos, n + 1
+// entries): one launch for the small arrays, the flags kernel and the library
+// scan otherwise
+template <int D>
+void split_and_scan(const SplitCounts<D>& f, int n, int32_t* nchild, int32_t* pos, cudaStream_t s,
+                    Arena& scratch, int64_t& launches) {
+  if (n <= kSmallScan) {
+    k_scan_small<<<1, 1024, 0, s>>>(n, f, nchild, pos, nullptr);
+    ++launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+    return;
+  }
+  if (f.d_n) k_split_flags_dev<D><<<grid_for(n, 256), 256, 0, s>>>(n, f.d_n, f.L, f.ns, f.M, nchild);
+  else k_split_flags<D><<<grid_for(n, 256), 256, 0, s>>>(n, f.L, f.ns, f.M, f.flag, nchild);
+  ++launches;
+  DMK_CUDA_TRY(cudaGetLastError());
+  scan_counts(nchild, pos, n, s, scratch, nullptr, launches);
 }
 
 template <int D>
@@ -597,14 +645,13 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
       if (cap_out >= (int64_t(1) << 31)) throw Error{DMK_ERR_NOMEM, "tree too large"};
       int32_t* nch = scratch.alloc<int32_t>(cap);
       int32_t* pos = scratch.alloc<int32_t>(cap + 1);
-      k_split_flags_dev<D><<<grid_for(cap, B), B, 0, s>>>(static_cast<int>(cap), d_cnt + lev, cur,
-                                                           p.leaf_capacity, M, nch);
-      scan_counts(nch, pos, static_cast<int>(cap), s, scratch, nullptr, p.launches);
+      split_and_scan<D>(SplitCounts<D>{cur, p.leaf_capacity, M, nullptr, d_cnt + lev}, static_cast<int>(cap), nch,
+                        pos, s, scratch, p.launches);
       alloc_leaves(nxt, cap_out, A);
       k_refine_dev<D><<<grid_for(cap << D, B), B, 0, s>>>(static_cast<int>(cap), static_cast<int>(cap_out),
                                                      d_cnt + lev, cur, nch, pos, nxt, skeys, M, d_cnt + lev + 1,
                                                      p.status);
-      p.launches += 2;
+      ++p.launches;
       DMK_CUDA_TRY(cudaGetLastError());
       cur = nxt;
       nxt = LeafArrays();
@@ -628,10 +675,9 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
     k_sys_begin<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), n_sys, cur.sys, begin, flag, d_any);
     k_balance<D><<<grid_for(n_leaf * 32, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
                                                         flag, d_any);
-    k_split_flags<D><<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, p.leaf_capacity, M,
-                                                       flag, nch);
-    scan_counts(nch, pos, static_cast<int>(n_leaf), s, scratch, nullptr, p.launches);
-    p.launches += 3;
+    split_and_scan<D>(SplitCounts<D>{cur, p.leaf_capacity, M, flag, nullptr}, static_cast<int>(n_leaf), nch, pos, s,
+                      scratch, p.launches);
+    p.launches += 2;
     DMK_CUDA_TRY(cudaGetLastError());
     DMK_CUDA_TRY(cudaMemcpyAsync(h_pin, pos + n_leaf, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     DMK_CUDA_TRY(cudaMemcpyAsync(h_pin + 2, d_any, sizeof(int), cudaMemcpyDeviceToHost, s));
