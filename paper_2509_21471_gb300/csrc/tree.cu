@@ -50,6 +50,24 @@ __device__ inline double in_cell(double x, double lo, int periodic) {
   return w;
 }
 
+// FP64 work runs at ~1/74 of the FP32 rate on this part, so the exact steps
+// below use integer operations on the bit pattern where they can.
+constexpr int64_t kOneBits = 0x3FF0000000000000LL;   // bit pattern of 1.0
+// w clamped to [0, 1] (w finite): negative values (sign bit) to 0, above 1 to 1
+__device__ inline double clamp01(double w) {
+  const int64_t b = __double_as_longlong(w);
+  return b < 0 ? 0.0 : (b > kOneBits ? 1.0 : w);
+}
+// floor(w 2^M) for 0 <= w <= 1, exact (w 2^M is exact in FP64)
+__device__ inline int64_t cell_index(double w, int M) {
+  const int64_t b = __double_as_longlong(w);
+  const int e = static_cast<int>((b >> 52) & 0x7ff);   // biased exponent
+  if (e == 0) return 0;                                // zero or subnormal
+  const int64_t m = (b & ((int64_t(1) << 52) - 1)) | (int64_t(1) << 52);
+  const int sh = 1075 - e - M;                         // 52 - (e - 1023) - M >= 52 - M for w <= 1
+  return sh >= 63 ? 0 : (m >> sh);
+}
+
 template <int D>
 __global__ void k_keys(int64_t N, const double* __restrict__ x, double lo0, double lo1, double lo2,
                        int periodic, int M, uint64_t* __restrict__ key, int32_t* __restrict__ idx,
@@ -57,7 +75,6 @@ __global__ void k_keys(int64_t N, const double* __restrict__ x, double lo0, doub
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const double lo[3] = {lo0, lo1, lo2};
-  const double scale = ldexp(1.0, M);
   const int64_t cmax = (int64_t(1) << M) - 1;
   int64_t c[3] = {0, 0, 0};
   for (int a = 0; a < D; ++a) {
@@ -67,12 +84,15 @@ __global__ void k_keys(int64_t N, const double* __restrict__ x, double lo0, doub
       xa = lo[a];
     }
     double w = in_cell<D>(xa, lo[a], periodic);
-    if (!periodic && (w < 0.0 || w > 1.0)) {
-      atomicOr(status, ST_OUT_OF_RANGE);
-      w = fmin(fmax(w, 0.0), 1.0);
+    if (!periodic) {
+      const int64_t b = __double_as_longlong(w);
+      if (b < 0 || b > kOneBits) {                     // w < 0 (or -0) or w > 1
+        if (b != static_cast<int64_t>(0x8000000000000000ULL)) atomicOr(status, ST_OUT_OF_RANGE);
+        w = clamp01(w);
+      }
     }
-    int64_t ci = static_cast<int64_t>(floor(w * scale));
-    c[a] = ci < 0 ? 0 : (ci > cmax ? cmax : ci);
+    const int64_t ci = cell_index(w, M);
+    c[a] = ci > cmax ? cmax : ci;
   }
   key[i] = morton<D>(c);
   idx[i] = static_cast<int32_t>(i);
@@ -89,7 +109,7 @@ __global__ void k_gather_w(int64_t N, const double* __restrict__ x, const int32_
     double xa = x[o * D + a];
     if (!isfinite(xa)) xa = lo[a];
     double v = in_cell<D>(xa, lo[a], periodic);
-    if (!periodic) v = fmin(fmax(v, 0.0), 1.0);
+    if (!periodic) v = clamp01(v);
     w[a * N + i] = v;
   }
 }
@@ -413,13 +433,14 @@ __global__ void k_rel_bbox(const int32_t* __restrict__ d_ntile, int64_t N, const
   int lev = level[leaf];
   int64_t c[3] = {0, 0, 0};
   leaf_coords<D>(anchor[leaf], lev, M, c);
-  const double h = ldexp(1.0, -lev);
   float v[3] = {0.f, 0.f, 0.f};
   bool on = lane < tcount[warp];
   if (on) {
     int64_t p = tstart[warp] + lane;
     for (int a = 0; a < D; ++a) {
-      double centre = (static_cast<double>(c[a]) + 0.5) * h;
+      // centre (c + 1/2) 2^-lev = (2c + 1) 2^-(lev+1): exact, scaled in the exponent bits
+      const double centre = __longlong_as_double(__double_as_longlong(static_cast<double>(2 * c[a] + 1)) -
+                                                  (static_cast<int64_t>(lev + 1) << 52));
       v[a] = __double2float_rn(w[a * N + p] - centre);
     }
     rel[p] = make_float4(v[0], v[1], v[2], 0.f);
