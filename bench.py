@@ -46,7 +46,39 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (eps = 1e-10, 2D periodic, batched, gradient)")
+    ap.add_argument("--batched-only", type=int, default=0, metavar="N_SYS",
+                    help="profiling aid: time only the mixed near field of the batched workload "
+                         "(N_SYS systems x 16 columns, plan reused) and print its own line")
     return ap.parse_args()
+
+
+def run_batched_only(args):
+    """The batched workload at N_SYS systems, mixed precision, near field only:
+    a small case of the several-column kernel for profiling."""
+    import torch
+    from paper_2509_21471_gb300 import dmk, workloads as wl
+    x, F, offs = wl.batched_3d(n_sys=args.batched_only, seed_index=3)
+    xd, Fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(F, device="cuda")
+    Ud = torch.empty_like(Fd)
+    p = dmk.Plan(xd, eps=1e-6, precision=dmk.MIXED, n_rhs=16, offsets=offs)
+    for _ in range(max(1, args.warmup)):
+        p.eval(Fd, out=Ud)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        p.eval(Fd, out=Ud)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    st = p.stats()
+    p.sync_status()
+    p.close()
+    t = sorted(ms)[len(ms) // 2] / 1e3
+    print(json.dumps({"workload": "batched-systems-16-rhs", "n_systems": args.batched_only, "n_points": len(x),
+                      "eps": 1e-6, "near_ms_median": 1e3 * t, "useful_pairs": st["useful_pairs"],
+                      "gpairs_useful": st["useful_pairs"] / t / 1e9}), flush=True)
 
 
 def workload_config(args, ns):
@@ -426,6 +458,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.batched_only > 0:
+        run_batched_only(args)
     else:
         run_ours(args)
 
