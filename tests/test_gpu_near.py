@@ -155,6 +155,39 @@ def test_out_of_range_point_is_reported(dmk):
     assert ei.value.code == 2
 
 
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_nonfinite_point_is_reported(dmk, bad, periodic):
+    x = np.zeros((10, 3))
+    x[4, 2] = bad
+    p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=1e-6, periodic=periodic)
+    with pytest.raises(dmk.DMKError) as ei:
+        p.sync_status()
+    assert ei.value.code == 1
+    p.close()
+
+
+def test_points_on_the_box_faces_are_in_range(dmk):
+    """w = 0 and w = 1 exactly (x = -1/2, +1/2) are inside the free-space box;
+    w = 1 + 2^-50 is not."""
+    rng = np.random.default_rng(77)
+    x = wl.uniform_points(rng, 300, 3)
+    x[:8] = [[-0.5, -0.5, -0.5], [0.5, 0.5, 0.5], [-0.5, 0.5, 0.0], [0.5, -0.5, 0.25],
+             [0.0, 0.5, -0.5], [-0.0, 0.0, 0.5], [0.5, 0.5, -0.5], [-0.5, -0.5, 0.5]]
+    p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=1e-6, leaf_capacity=8)
+    p.sync_status()
+    tr = Tree(x, 8)
+    assert_tree_equal(p.tree(), tr)
+    p.close()
+    y = x.copy()
+    y[5, 0] = 0.5 + 2.0 ** -50
+    q = dmk.Plan(torch.as_tensor(y, device="cuda"), eps=1e-6, leaf_capacity=8)
+    with pytest.raises(dmk.DMKError) as ei:
+        q.sync_status()
+    assert ei.value.code == 2
+    q.close()
+
+
 @pytest.mark.parametrize("dim", [3, 2])
 def test_refinement_to_the_maximum_level(dmk, dim):
     """40 coincident points and a tight pair with n_s = 8: the tree refines to
