@@ -173,7 +173,13 @@ dmk_status_t dmk_stokes_sync_status(dmk_stokes_plan_t plan);
 dmk_status_t dmk_stokes_plan_stats(dmk_stokes_plan_t plan, int64_t stats[10]);
 
 /* Copies the plan's tree to HOST arrays (any pointer may be NULL):
- *   perm[n]        sorted position -> original index
+ *   perm[n]        sorted position -> original index.  Points are sorted by
+ *                  the Morton key of their finest cell; a plan with FP32 pair
+ *                  terms (MIXED, eps >= 2e-7) then orders the points inside
+ *                  each leaf by the Hilbert curve over the leaf's sub-cells
+ *                  three levels down (four in 2D; Morton order inside a
+ *                  sub-cell, leaves within that many levels of the maximum
+ *                  level unchanged), which makes the 32-point tiles compact.
  *   leaf_level[L], leaf_start[L], leaf_count[L], leaf_coords[L][dim] (box
  *   coordinates at the leaf's level), near_off[L+1], near_leaf[E],
  *   near_q[E][dim] (periodic image offsets q, displacement (w_t - w_s) + q).

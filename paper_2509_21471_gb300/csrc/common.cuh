@@ -121,12 +121,20 @@ __host__ __device__ inline int unpack_q(int32_t p, int a) {
 }
 
 // ----------------------------------------------------------------- plan
+// MIXED precision evaluates the pair terms in FP32 from this eps up (their l2
+// error is about 1e-7 to 2e-6), in float-float or FP64 below
+constexpr double kFp32PairMinEps = 2e-7;
+inline bool fp32_pair_terms(const dmk_stokes_opts_t& o) {
+  return o.precision == DMK_PRECISION_MIXED && o.eps >= kFp32PairMinEps;
+}
+
 struct DeviceTree {
   int dim = 3;
   int M = 21;                 // key bits per axis
   int periodic = 0;
   int n_sys = 1;
   int64_t N = 0;              // points (sources == targets)
+  int leaf_hilbert = 0;       // 1: points inside each leaf in Hilbert order of its sub-cells
   // points, sorted order
   int32_t* perm = nullptr;    // sorted index -> original index
   double* w = nullptr;        // in-cell coordinates, SoA [dim][N]

@@ -232,10 +232,7 @@ __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned lo
 // There (one force column) the pair terms, and the gradient, are evaluated in
 // float-float (k_near_ff), which GB300 runs far faster than FP64; several
 // force columns take FP64 pair terms.
-constexpr double kFp32PairMinEps = 2e-7;
-bool fp32_pairs(const dmk_stokes_opts_t& o) {
-  return o.precision == DMK_PRECISION_MIXED && o.eps >= kFp32PairMinEps;
-}
+bool fp32_pairs(const dmk_stokes_opts_t& o) { return fp32_pair_terms(o); }
 bool ff_pairs(const dmk_stokes_opts_t& o) {
   return o.precision == DMK_PRECISION_MIXED && o.eps < kFp32PairMinEps && o.n_rhs == 1;
 }

@@ -13,7 +13,7 @@ from oracle.tree import Tree
 from oracle.window import ProlateWindow
 from oracle.params import bandlimit_c
 from paper_2509_21471_gb300 import workloads as wl
-from tests.helpers import rel_l2
+from tests.helpers import rel_l2, leaf_hilbert_perm, hilbert_order
 
 pytestmark = pytest.mark.gpu
 EPS = 1e-6
@@ -63,7 +63,7 @@ def test_batched_systems_match_per_system_oracle(dmk, precision):
     p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=EPS, precision=precision, leaf_capacity=ns, offsets=offs)
     u = p.eval(torch.as_tensor(f, device="cuda")).cpu().numpy()
     p.sync_status()
-    gt = p.tree() if precision == 0 else None
+    gt = p.tree()
     leaf_base = 0
     for k, m in enumerate(sizes):
         sl = slice(offs[k], offs[k + 1])
@@ -75,7 +75,8 @@ def test_batched_systems_match_per_system_oracle(dmk, precision):
             assert np.array_equal(lv, tr.leaf_level)
             assert np.array_equal(gt["leaf_coords"][leaf_base: leaf_base + L], tr.leaf_coords)
             assert np.array_equal(gt["leaf_count"][leaf_base: leaf_base + L], tr.leaf_count)
-            assert np.array_equal(gt["perm"][offs[k]: offs[k + 1]] - offs[k], tr.perm)
+            expect = leaf_hilbert_perm(tr) if hilbert_order(precision, EPS) else tr.perm
+            assert np.array_equal(gt["perm"][offs[k]: offs[k + 1]] - offs[k], expect)
             off = gt["near_off"]
             for i in range(L):
                 e0, e1 = off[leaf_base + i], off[leaf_base + i + 1]

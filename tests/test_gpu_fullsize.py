@@ -128,7 +128,7 @@ def test_batched_256_systems_16_columns(dmk):
         assert np.array_equal(gt["leaf_level"][a:b], tr.leaf_level)
         assert np.array_equal(gt["leaf_coords"][a:b], tr.leaf_coords)
         assert np.array_equal(gt["leaf_count"][a:b], tr.leaf_count)
-        assert np.array_equal(gt["perm"][sl] - offs[k], tr.perm)
+        assert np.array_equal(gt["perm"][sl] - offs[k], tr.perm)       # FP64 plan: Morton order
         for i in range(len(tr.leaves)):
             e0, e1 = gt["near_off"][a + i], gt["near_off"][a + i + 1]
             got = {(int(gt["near_leaf"][e]) - a, tuple(int(v) for v in gt["near_q"][e])) for e in range(e0, e1)}

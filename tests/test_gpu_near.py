@@ -18,7 +18,7 @@ from oracle.tree import Tree
 from oracle.window import ProlateWindow
 from oracle.params import bandlimit_c
 from paper_2509_21471_gb300 import workloads as wl
-from tests.helpers import rel_l2, assert_tree_equal
+from tests.helpers import rel_l2, assert_tree_equal, hilbert_order
 
 pytestmark = pytest.mark.gpu
 
@@ -141,8 +141,7 @@ def test_faces_coincident_and_single_leaf(dmk):
         tr, u_ref = _oracle(x, f, None, None, 1e-6, ns, False, 1)
         for prec in (0, 1):
             p, u = _run(dmk, x, f=f, eps=1e-6, ns=ns, precision=prec)
-            if prec == 0:
-                assert_tree_equal(p.tree(), tr)
+            assert_tree_equal(p.tree(), tr, hilbert_order(prec, 1e-6))
             assert rel_l2(u, u_ref) < (FP64_TOL if prec == 0 else 1e-5)
 
 
@@ -177,7 +176,7 @@ def test_points_on_the_box_faces_are_in_range(dmk):
     p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=1e-6, leaf_capacity=8)
     p.sync_status()
     tr = Tree(x, 8)
-    assert_tree_equal(p.tree(), tr)
+    assert_tree_equal(p.tree(), tr, hilbert_order(dmk.MIXED, 1e-6))
     p.close()
     y = x.copy()
     y[5, 0] = 0.5 + 2.0 ** -50
@@ -210,7 +209,6 @@ def test_refinement_to_the_maximum_level(dmk, dim):
         u_ref = onear.near_lists(tr, dict(k2d=k2.Kernel2D(ProlateWindow(bandlimit_c(1e-6))), stokeslet=True), f=f)
     for prec in (0, 1):
         p, u = _run(dmk, x, f=f, eps=1e-6, ns=ns, precision=prec)
-        if prec == 0:
-            assert_tree_equal(p.tree(), tr)
+        assert_tree_equal(p.tree(), tr, hilbert_order(prec, 1e-6))
         assert rel_l2(u, u_ref) < (FP64_TOL if prec == 0 else 1e-5)
         p.close()

@@ -17,7 +17,7 @@ from oracle.tree import Tree
 from oracle.window import ProlateWindow
 from oracle.params import bandlimit_c
 from paper_2509_21471_gb300 import workloads as wl
-from tests.helpers import rel_l2, assert_tree_equal
+from tests.helpers import rel_l2, assert_tree_equal, hilbert_order
 
 pytestmark = pytest.mark.gpu
 
@@ -123,8 +123,7 @@ def test_faces_and_coincident_2d(dmk):
             tr, u_ref = _oracle(x, f, None, None, 1e-6, ns, periodic, 1)
             for prec in (0, 1):
                 p, u = _run(dmk, x, f=f, eps=1e-6, ns=ns, periodic=periodic, precision=prec)
-                if prec == 0:
-                    assert_tree_equal(p.tree(), tr)
+                assert_tree_equal(p.tree(), tr, hilbert_order(prec, 1e-6))
                 assert rel_l2(u, u_ref) < (FP64_TOL if prec == 0 else 1e-5)
                 p.close()
 
