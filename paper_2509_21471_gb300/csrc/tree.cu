@@ -474,7 +474,7 @@ __global__ void k_point_sys(int n_sys, const int32_t* __restrict__ offs, int32_t
 // order jumps between distant sub-cells, so inside every leaf the sub-cells
 // kHilbertLevels levels below the leaf are put in Hilbert-curve order (points
 // keep their Morton order inside a sub-cell): consecutive sub-cells are then
-// face neighbours and the tiles more compact (on GB300: FP32 near field 3.5 %
+// face neighbours and the tiles more compact (on GB300: FP32 near field 5 %
 // and the 16-column kernel 6.5 % faster).  Leaves deeper than
 // M - kHilbertLevels keep the Morton order.  Only plans with FP32 pair terms
 // take this order: the float-float passes measured 3 % slower with it (more
