@@ -34,8 +34,9 @@ def _kvectors(d, kmax):
 
 
 def ewald_sum(x, f=None, g=None, n=None, split=None, lo=None,
-              parts=("real", "fourier", "self", "zero")):
-    """Periodic sum on the unit cell.
+              parts=("real", "fourier", "self", "zero"), targets=None):
+    """Periodic sum on the unit cell, at every point (or at the points whose
+    indices are in ``targets``).
 
     split: dict with
       'real'  : callable(d[P, dim], which) -> kernel tensors for the residual
@@ -51,11 +52,12 @@ def ewald_sum(x, f=None, g=None, n=None, split=None, lo=None,
     lo = np.full(d, -0.5) if lo is None else np.asarray(lo)[:d]
     w = x - lo
     w = w - np.floor(w)
+    tset = np.arange(N) if targets is None else np.asarray(targets)
     u = np.zeros((N, d))
     # ---- real space: all images within rcut ------------------------------
     R = int(np.ceil(split["rcut"])) + 1
     images = np.array(list(itertools.product(range(-R, R + 1), repeat=d)), dtype=np.float64)
-    for t in (range(N) if "real" in parts else ()):
+    for t in (tset if "real" in parts else ()):
         dd = (w[t][None, None, :] - w[None, :, :]) + images[:, None, :]   # [img, s, d]
         dd = dd.reshape(-1, d)
         src = np.tile(np.arange(N), len(images))
@@ -70,12 +72,12 @@ def ewald_sum(x, f=None, g=None, n=None, split=None, lo=None,
     kv, kk = _kvectors(d, split["kmax"]) if "fourier" in parts else (np.zeros((0, d)), np.zeros(0))
     Bh = split["ghat"](kk) / kk ** 4
     ph = np.exp(-1j * (w @ kv.T))                       # [s, k] e^{-i k.w_s}
-    pt = np.conj(ph)                                    # [t, k] e^{+i k.w_t}
+    pt = np.exp(1j * (w[tset] @ kv.T))                  # [t, k] e^{+i k.w_t}
     if f is not None:
         rhat = ph.T @ f                                 # [k, d] sum_s f_s e^{-ik.w_s}
         kdot = np.sum(kv * rhat, axis=1)
         Shat_rho = (kk[:, None] ** 2 * rhat - kv * kdot[:, None]) * Bh[:, None]
-        u += np.real(pt @ Shat_rho)
+        u[tset] += np.real(pt @ Shat_rho)
     if g is not None:
         Gh = np.einsum("sk,sl,sm->klm", ph, g, n)       # [k, l, m]
         Gk = np.einsum("klm,km->kl", Gh, kv)            # G_jm k_m   (j = l index)
@@ -84,12 +86,12 @@ def ewald_sum(x, f=None, g=None, n=None, split=None, lo=None,
         kGk = np.einsum("kl,klm,km->k", kv, Gh, kv)
         That_rho = 1j * Bh[:, None] * (kk[:, None] ** 2 * (Gk + kv * tr[:, None] + GTk)
                                         - 2.0 * kv * kGk[:, None])
-        u += np.real(pt @ That_rho)
+        u[tset] += np.real(pt @ That_rho)
         if "zero" in parts:
-            u += stresslet_zero_mode(w, g, n)
+            u[tset] += stresslet_zero_mode(w, g, n, targets=tset)
     if f is not None and "self" in parts:
-        u += split["self"] * f
-    return u
+        u[tset] += split["self"] * f[tset]
+    return u if targets is None else u[tset]
 
 
 def gaussian_split_3d(sigma, tol=1e-16):
