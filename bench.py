@@ -222,13 +222,13 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
         return out
 
     res = {}
-    # 3D clustered, eps = 1e-10 (MIXED takes FP64 pair terms below eps = 2e-7)
+    # 3D clustered, eps = 1e-10 (MIXED takes float-float pair terms below eps = 2e-7)
     x, f = wl.clustered_3d(n=args.n, sigma=0.02, seed_index=pdist.seed_index(1, rank))
     xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
     ud = torch.empty_like(fd)
     r = measure(lambda prec: dmk.Plan(xd, eps=1e-10, precision=prec), lambda p: p.eval(fd, out=ud), len(x), k_mixed)
     r.update(workload="3d-free-stokeslet-clustered-8gauss", n_points=len(x), eps=1e-10,
-             mixed_pair_arith="fp64 (eps < 2e-7)")
+             mixed_pair_arith="float-float (eps < 2e-7)")
     res["clustered_3d_eps1e-10"] = r
     del xd, fd, ud
 
@@ -240,7 +240,7 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
                                       precision=prec),
                 lambda p: p.eval(fd, gd, nd, out=ud), len(x), k_mixed)
     r.update(workload="2d-periodic-stokeslet+stresslet-uniform", n_points=len(x), eps=1e-8,
-             mixed_pair_arith="fp64 (eps < 2e-7)")
+             mixed_pair_arith="float-float (eps < 2e-7)")
     res["periodic_2d_eps1e-8"] = r
     del xd, fd, gd, nd, ud
 
@@ -271,7 +271,13 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
         fwd_bwd()
         torch.cuda.synchronize()
         t = max_over_ranks(sum(timed(fwd_bwd, 2)) / 2 / 1e3)
-        out[name] = {"ms_per_step": 1e3 * t, "targets_per_s": len(x) / t}
+        # the backward pass alone: one dmk_stokes_eval_adjoint call (plan reused)
+        p = dmk.Plan(xd, eps=1e-8, periodic=True, precision=prec)
+        p.eval_adjoint(fd, u_tgt)
+        torch.cuda.synchronize()
+        t_b = max_over_ranks(sum(timed(lambda: p.eval_adjoint(fd, u_tgt), 3)) / 3 / 1e3)
+        p.close()
+        out[name] = {"ms_per_step": 1e3 * t, "targets_per_s": len(x) / t, "backward_adjoint_ms": 1e3 * t_b}
     out.update(workload="3d-periodic-uniform-loss-gradient", n_points=len(x), eps=1e-8,
                step="plan + forward + backward (grad w.r.t. x and f)",
                speedup_mixed_over_fp64=out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"])
@@ -407,9 +413,9 @@ def run_ours(args):
         flops_one_side = 40 + 2 * (c32[0] - 1) + 2 * (c32[1] - 1)
         flops_per_pair = (flops_one_side + 18) / 2
         achieved = near["mixed"]["useful_pairs"] * flops_per_pair / (near["mixed"]["ms"] / 1e3) / 1e12
-        # DRAM bytes per launch of this kernel from ncu (dram__bytes_read.sum +
-        # dram__bytes_write.sum) on the same recipe at N = 5e5, scaled by the
-        # point count: profiles/near_sym_clustered5e5.md
+        # DRAM bytes per launch of this kernel from one ncu capture
+        # (dram__bytes_read.sum + dram__bytes_write.sum) of the same recipe at
+        # N = 5e5, scaled by the point count
         traffic = 29.37e6 * args.n / 500_000 if args.eps == 1e-6 else None
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                     "frac": achieved / peak_tflops, "traffic": traffic,
@@ -427,7 +433,7 @@ def run_ours(args):
         # bound, with no per-pair flop figure of the method to divide
         roofline = {"bound": "alu", "achieved": None, "peak": peak_tflops, "unit": "TFLOP/s", "frac": None,
                     "traffic": None, "kernel": "k_near_ff (float-float near field)", "peak_basis": peak_basis,
-                    "note": "float-float arithmetic: see the ncu FP32-pipe utilisation in profiles/"}
+                    "note": "float-float arithmetic: no per-pair flop count of the method to divide"}
 
     extras = None
     if not args.no_extras:

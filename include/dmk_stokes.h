@@ -72,9 +72,17 @@ typedef struct {
                             leaf-relative coordinates and compensated (two-sum)
                             accumulation; self term and output in float64.
                             FP32 pair terms carry a relative l2 error of about
-                            1e-7..2e-6, so for eps < 2e-7 MIXED takes the pair
-                            terms in float64 (an FP32 test still selects the
-                            candidate pairs) and meets eps like FP64. */
+                            1e-7..2e-6, so for eps < 2e-7 (one force column)
+                            MIXED takes float-float pair terms (hi + lo floats,
+                            about 48 bits; an FP32 test still selects the
+                            candidate pairs) and meets eps like FP64; several
+                            columns below 2e-7 take float64 pair terms.
+                            Nearly coincident pairs, r <= nu/32 (FP32 pair
+                            terms) or r <= nu/1024 (float-float), are taken in
+                            float64 from the float64 coordinates, since
+                            leaf-relative coordinates cannot resolve them.
+                            The gradient and the adjoint take float-float pair
+                            terms at every eps. */
   int32_t components;    /* DMK_COMPONENTS_NEAR (the far field is not provided:
                             DMK_COMPONENTS_ALL returns DMK_ERR_UNSUPPORTED) */
   int32_t leaf_capacity; /* n_s, max points per leaf; 0 = the paper's value for
@@ -135,10 +143,11 @@ dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const do
  * The paper has no counterpart; this is a deployment variant.
  *   Arguments, layouts and results: as dmk_stokes_eval.
  *   Limit: plans needing more than 64 MiB of scratch (with n_rhs = 1: mixed
- *   precision at eps >= 2e-7 128 bytes per point, about 524k points; mixed
- *   below 2e-7 288 bytes per point in 3D (192 in 2D), about 233k points; FP64 104 bytes per
- *   point, about 645k points; more with several force columns; plus 32
- *   bytes per system) return DMK_ERR_INVALID_ARG before any work is queued.
+ *   precision at eps >= 2e-7 136 bytes per point, about 493k points; mixed
+ *   below 2e-7 296 bytes per point in 3D (200 in 2D), about 226k points;
+ *   FP64 104 bytes per point, about 645k points; more with several force
+ *   columns; plus 32 bytes per system) return DMK_ERR_INVALID_ARG before any
+ *   work is queued.
  *   The plan's device must be current.
  *   Sharing: all calls on a device use the same array, which keeps the last
  *   call's contents (what must start at zero is cleared by every call); calls
@@ -153,9 +162,37 @@ dmk_status_t dmk_stokes_eval_noalloc(dmk_stokes_plan_t plan, const double* d_f, 
  *   d_gradu [n][dim][dim][n_rhs], gradu[t][j][m] = d u_j / d x_m at x_t with the
  *   tree (and so every nu_ts) held fixed; the self term does not depend on x.
  *   d_u may be NULL; if not NULL it receives the velocity as dmk_stokes_eval does.
- * The derivative of Eq. (res_stokeslet) is derived in the library docs. */
+ * The derivative of Eq. (res_stokeslet) (Sec. 5.2) with Phi' = -2 phi
+ * (Eq. (def_erfc_like_fcn)):  S_R = A(r) I + C(r) x x^T gives
+ *   d_m (S_R f)_j = A'(r) x_m/r f_j + C'(r) x_m/r x_j (x.f) + C (delta_jm (x.f) + x_j f_m).
+ * MIXED plans take float-float pair terms for the gradient at every eps (FP32
+ * gradient terms, ~1/r^3, would carry a relative l2 error near 2e-5); a plan
+ * with FP32 velocity pair terms (eps >= 2e-7) allocates the gradient
+ * workspace (208 bytes per point) on its first eval_grad or eval_adjoint call,
+ * and host-synchronises that call. */
 dmk_status_t dmk_stokes_eval_grad(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
                                   const double* d_n, double* d_u, double* d_gradu, void* stream);
+
+/* Adjoint (reverse mode) of the 3D Stokeslet near component u = S[f] (eval
+ * with one force column) with the tree, hence every nu_ts, held fixed:
+ * for a scalar L with cotangent w = dL/du,
+ *   d_v  [n][3]  dL/df = S[w]: S_R is even and symmetric, so the operator is
+ *                its own transpose; the self term is the forward one on w;
+ *   d_gx [n][3]  dL/dx_t = sum_s G(w_t, f_s; x) + G(f_t, w_s; x), x = x_t - x_s,
+ *                G(a, b; x)_m = sum_j a_j d_m (S_R b)_j
+ *                             = [A1 (a.b) + C1 (x.a)(x.b)] x_m + C [a_m (x.b) + b_m (x.a)]
+ *                with A1 = A'/r, C1 = C'/r of the gradient above (the self term
+ *                does not depend on x).
+ *   d_f [n][3] forces, d_w [n][3] cotangents (device, caller order).
+ * One symmetric pass evaluates each pair once for both points and recomputes
+ * the pair terms (nothing is stored per pair); MIXED plans take float-float
+ * pair terms (nearly coincident pairs in FP64), FP64 plans FP64.  The first
+ * call allocates the adjoint workspace (128 bytes per point MIXED, 96 FP64)
+ * and host-synchronises.  Both outputs come from FP64 atomic additions
+ * (reproducible to the order of those additions).  Stresslet, 2D and several
+ * force columns: DMK_ERR_UNSUPPORTED. */
+dmk_status_t dmk_stokes_eval_adjoint(dmk_stokes_plan_t plan, const double* d_f, const double* d_w, double* d_v,
+                                     double* d_gx, void* stream);
 
 /* Synchronises the plan's last stream and returns the latched device status
  * (DMK_OK, DMK_ERR_OUT_OF_RANGE, DMK_ERR_INVALID_ARG for a non-finite point). */

@@ -136,6 +136,9 @@ void configure_pool(int dev) {
 }
 
 void release(dmk::Plan& p) {
+  if (p.aux) cudaFreeAsync(p.aux, p.stream);
+  p.aux = nullptr;
+  p.aux_bytes = 0;
   dmk::free_tree(p.tree, p.stream);
   p.fsorted = nullptr;
   p.reduce_buf = nullptr;
@@ -231,6 +234,24 @@ dmk_status_t dmk_stokes_plan_batched(const dmk_stokes_opts_t* opts, int32_t n_sy
   return make_plan(opts, n_sys, h_offsets, d_src, stream, out);
 }
 
+// The gradient and adjoint workspace (aux) is allocated on the plan's stream
+// by the first call that needs it, and the stream synchronised so that any
+// stream may use it; later calls reuse it.
+static void ensure_aux(dmk_stokes_plan_t plan, size_t bytes) {
+  dmk::Plan& p = plan->p;
+  if (bytes == 0 || p.aux_bytes >= bytes) return;
+  if (p.aux) {
+    // a smaller workspace from an earlier call: let its work finish first
+    DMK_CUDA_TRY(cudaStreamSynchronize(plan->last_stream));
+    cudaFreeAsync(p.aux, p.stream);
+  }
+  p.aux = nullptr;
+  p.aux_bytes = 0;
+  DMK_CUDA_TRY(cudaMallocAsync(&p.aux, bytes, p.stream));
+  DMK_CUDA_TRY(cudaStreamSynchronize(p.stream));
+  p.aux_bytes = bytes;
+}
+
 static dmk_status_t run_eval(dmk_stokes_plan_t plan, const double* d_f, const double* d_g, const double* d_n,
                              double* d_u, double* d_gradu, void* stream) {
   if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
@@ -246,6 +267,7 @@ static dmk_status_t run_eval(dmk_stokes_plan_t plan, const double* d_f, const do
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   plan->last_stream = s;
   try {
+    if (d_gradu && N > 0) ensure_aux(plan, dmk::aux_bytes_grad(p.opts, N));
     dmk::launch_near(p, want_s ? d_f : nullptr, want_t ? d_g : nullptr, want_t ? d_n : nullptr, d_u, d_gradu, s);
   } catch (const dmk::Error& e) {
     return set_err(plan, e.code, e.msg);
@@ -272,6 +294,28 @@ dmk_status_t dmk_stokes_eval_grad(dmk_stokes_plan_t plan, const double* d_f, con
   (void)d_g;
   (void)d_n;
   return run_eval(plan, d_f, nullptr, nullptr, d_u, d_gradu, stream);
+}
+
+dmk_status_t dmk_stokes_eval_adjoint(dmk_stokes_plan_t plan, const double* d_f, const double* d_w, double* d_v,
+                                     double* d_gx, void* stream) {
+  if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
+  dmk::Plan& p = plan->p;
+  if (p.opts.dim != 3) return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint is provided in 3D");
+  if (p.opts.kernels != DMK_KERNEL_STOKESLET)
+    return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint is provided for the Stokeslet only");
+  if (p.opts.n_rhs != 1) return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint is provided for n_rhs = 1");
+  const int64_t N = p.tree.N;
+  if (N > 0 && (!d_f || !d_w || !d_v || !d_gx))
+    return set_err(plan, DMK_ERR_INVALID_ARG, "d_f, d_w, d_v and d_gx are required");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  plan->last_stream = s;
+  try {
+    if (N > 0) ensure_aux(plan, dmk::aux_bytes_adjoint(p.opts, N));
+    dmk::launch_adjoint(p, d_f, d_w, d_v, d_gx, s, p.aux);
+  } catch (const dmk::Error& e) {
+    return set_err(plan, e.code, e.msg);
+  }
+  return DMK_OK;
 }
 
 dmk_status_t dmk_stokes_sync_status(dmk_stokes_plan_t plan) {

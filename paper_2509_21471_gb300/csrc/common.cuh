@@ -227,6 +227,8 @@ struct Plan {
   size_t fsorted_bytes = 0;
   double* gn_sorted = nullptr; // stresslet: sorted g (SoA) , n (SoA), g.n
   double* reduce_buf = nullptr;
+  void* aux = nullptr;         // gradient / adjoint workspace, allocated on first use
+  size_t aux_bytes = 0;
   int* status = nullptr;       // device status word
   int* h_status = nullptr;     // pinned host mirror (a pinned_slot)
   Arena arena;                 // device arrays of the plan
@@ -246,10 +248,17 @@ void free_tree(DeviceTree& t, cudaStream_t s);
 void launch_near(const Plan& p, const double* d_f, const double* d_g, const double* d_n,
                  double* d_u, double* d_gradu, cudaStream_t s);
 // same, with the evaluation scratch given explicitly: workspace of
-// eval_workspace_bytes(opts, N) bytes and reduce_buf of 4 * n_sys doubles
+// eval_workspace_bytes(opts, N) bytes, reduce_buf of 4 * n_sys doubles and,
+// for a gradient, aux of aux_bytes_grad(opts, N) bytes (may be null when 0)
 void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const double* d_n,
-                    double* d_u, double* d_gradu, cudaStream_t s, void* workspace, double* reduce_buf);
+                    double* d_u, double* d_gradu, cudaStream_t s, void* workspace, double* reduce_buf,
+                    void* aux);
 size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N);
+size_t aux_bytes_grad(const dmk_stokes_opts_t& o, int64_t N);
+size_t aux_bytes_adjoint(const dmk_stokes_opts_t& o, int64_t N);
+// adjoint pass of the 3D Stokeslet (v = S[w], dL/dx); aux of aux_bytes_adjoint bytes
+void launch_adjoint(const Plan& p, const double* d_f, const double* d_w, double* d_v, double* d_gx,
+                    cudaStream_t s, void* aux);
 
 int64_t count_useful_pairs(const Plan& p);
 

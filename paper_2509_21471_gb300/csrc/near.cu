@@ -1,6 +1,7 @@
 // Near-field dispatch, density permutation, the periodic stresslet zero mode
 // and the useful-pair count (2D and 3D).
-#include "near_ff.cuh"
+#include "near_adj.cuh"
+#include "near_close.cuh"
 
 namespace dmk {
 
@@ -16,6 +17,12 @@ DMK_NT_FP64(DMK_EXT_D_NT)
   extern template void run_near_ff<D, KM, GR, NT>(const NearParams&, const FFParams&, cudaStream_t);
 #define DMK_EXT_F_NT(NT) DMK_FOR_EACH_FF(DMK_EXT_F, NT)
 DMK_NT_FP64(DMK_EXT_F_NT)
+#define DMK_EXT_A(NT) extern template void run_near_adj<true, NT>(const NearParams&, const AdjParams&, cudaStream_t);
+DMK_NT_FP64(DMK_EXT_A)
+extern template void run_near_adj<false, 16>(const NearParams&, const AdjParams&, cudaStream_t);
+#define DMK_EXT_C(D, KM, GR, FFC) \
+  extern template void run_near_close<D, KM, GR, FFC>(const NearParams&, const CloseParams&, cudaStream_t);
+DMK_FOR_EACH_CLOSE(DMK_EXT_C)
 
 namespace {
 
@@ -240,9 +247,13 @@ bool ff_pairs(const dmk_stokes_opts_t& o) {
 // workspace: [FP32 sorted densities (fp32 pairs)] [FP64 sorted densities]
 // [FF split densities] [FP64 accumulator of the symmetric FP64 pass]
 // [FP64 accumulator of the symmetric float-float gradient pass, 12 per point]
+// [MIXED: count of the skipped nearly coincident pairs, then one mark per tile
+// (at most one tile per point)] [MIXED: their queue, close_cap(N) entries]
 struct WsLayout {
-  size_t f64_off, ff_off, acc_off, accg_off, bytes;
+  size_t f64_off, ff_off, acc_off, accg_off, flag_off, queue_off, bytes;
 };
+// capacity of the queue of skipped nearly coincident pairs (16 bytes each)
+int64_t close_cap(int64_t N) { return std::max<int64_t>(1024, N / 4); }
 WsLayout ws_layout(const dmk_stokes_opts_t& o, int64_t N) {
   const int NR = padded_rhs(o.n_rhs);
   WsLayout L;
@@ -251,7 +262,9 @@ WsLayout ws_layout(const dmk_stokes_opts_t& o, int64_t N) {
   L.acc_off = L.ff_off + (ff_pairs(o) ? 7 * N * sizeof(float4) : 0);
   const bool fp64_sym = o.precision == DMK_PRECISION_FP64 && o.n_rhs == 1;
   L.accg_off = L.acc_off + (fp64_sym ? 3 * N * sizeof(double) : 0);
-  L.bytes = L.accg_off + ((ff_pairs(o) && o.dim == 3) ? 12 * N * sizeof(double) : 0);
+  L.flag_off = L.accg_off + ((ff_pairs(o) && o.dim == 3) ? 12 * N * sizeof(double) : 0);
+  L.queue_off = L.flag_off + (o.precision == DMK_PRECISION_MIXED ? ((N + 1) * sizeof(int) + 15) / 16 * 16 : 0);
+  L.bytes = L.queue_off + (o.precision == DMK_PRECISION_MIXED ? close_cap(N) * sizeof(int4) : 0);
   return L;
 }
 
@@ -288,6 +301,29 @@ void dispatch_ff(int dim, int km, bool grad, int nt, const NearParams& P, const 
 #define DMK_CASE_F_NT(NT) DMK_FOR_EACH_FF(DMK_CASE_F, NT)
   DMK_NT_FP64(DMK_CASE_F_NT)
   throw Error{DMK_ERR_UNSUPPORTED, "no compiled float-float kernel for this configuration"};
+}
+
+void dispatch_close(int dim, int km, bool grad, bool ffc, const NearParams& P, const CloseParams& C,
+                    cudaStream_t s) {
+#define DMK_CASE_C(D, KM, GR, FFC)                                        \
+  if (dim == D && km == KM && grad == GR && ffc == FFC) {                 \
+    run_near_close<D, KM, GR, FFC>(P, C, s);                              \
+    return;                                                               \
+  }
+  DMK_FOR_EACH_CLOSE(DMK_CASE_C)
+  throw Error{DMK_ERR_UNSUPPORTED, "no compiled close-pair kernel for this configuration"};
+}
+
+// u (caller order) from the sorted accumulator of a symmetric pass
+void finish_sym(int dim, int km, bool grad, const NearParams& P, cudaStream_t s) {
+  const unsigned g = (P.n_tile + 7) / 8;
+  if (grad) k_near_sym_finish_grad<3><<<g, 256, 0, s>>>(P, P.acc);
+  else if (dim == 3 && km == 1) k_near_sym_finish<3, 1><<<g, 256, 0, s>>>(P, P.acc);
+  else if (dim == 3 && km == 2) k_near_sym_finish<3, 2><<<g, 256, 0, s>>>(P, P.acc);
+  else if (dim == 3 && km == 3) k_near_sym_finish<3, 3><<<g, 256, 0, s>>>(P, P.acc);
+  else if (dim == 2 && km == 1) k_near_sym_finish<2, 1><<<g, 256, 0, s>>>(P, P.acc);
+  else if (dim == 2 && km == 2) k_near_sym_finish<2, 2><<<g, 256, 0, s>>>(P, P.acc);
+  else k_near_sym_finish<2, 3><<<g, 256, 0, s>>>(P, P.acc);
 }
 
 NearParams tree_params(const Plan& p) {
@@ -363,12 +399,11 @@ void perm_densities(const Plan& p, bool mixed, bool ff, int km, int nr, int NR, 
 }
 
 // FF inputs: rel_lo and the hi / lo split of the sorted densities
-FFParams ff_inputs(const Plan& p, int km, const double* d_f, const double* d_g, const double* d_n, char* ws,
+FFParams ff_inputs(const Plan& p, int km, const double* d_f, const double* d_g, const double* d_n, float4* base,
                    const NearParams& P, cudaStream_t s) {
   const DeviceTree& T = p.tree;
   const int64_t N = T.N;
   const int B = 256;
-  float4* base = reinterpret_cast<float4*>(ws + ws_layout(p.opts, N).ff_off);
   FFParams F{};
   F.rel_lo = base;
   F.f_hi = base + N;
@@ -416,19 +451,36 @@ FFParams ff_inputs(const Plan& p, int km, const double* d_f, const double* d_g, 
 
 void launch_near(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u,
                  double* d_gradu, cudaStream_t s) {
-  launch_near_ws(p, d_f, d_g, d_n, d_u, d_gradu, s, p.fsorted, p.reduce_buf);
+  launch_near_ws(p, d_f, d_g, d_n, d_u, d_gradu, s, p.fsorted, p.reduce_buf, p.aux);
+}
+
+// MIXED gradients take float-float pair terms at every eps: the FP32 gradient
+// terms (1/r^3) carry a relative l2 error of ~2e-5, above 10 eps at eps = 1e-6.
+// A plan with FP32 pair terms then keeps the float-float inputs and the
+// accumulator of the gradient pass in a workspace of its own (aux), allocated
+// on the first gradient or adjoint call.
+bool ff_grad_aux(const dmk_stokes_opts_t& o) { return fp32_pair_terms(o) && o.n_rhs == 1; }
+
+size_t aux_bytes_grad(const dmk_stokes_opts_t& o, int64_t N) {
+  return ff_grad_aux(o) ? static_cast<size_t>(N) * (7 * sizeof(float4) + 12 * sizeof(double)) + 512 : 0;
+}
+size_t aux_bytes_adjoint(const dmk_stokes_opts_t& o, int64_t N) {
+  const size_t in = o.precision == DMK_PRECISION_MIXED ? 5 * sizeof(float4) : 6 * sizeof(double);
+  return static_cast<size_t>(N) * (in + 6 * sizeof(double)) + 512;
 }
 
 void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u,
-                    double* d_gradu, cudaStream_t s, void* workspace, double* reduce_buf) {
+                    double* d_gradu, cudaStream_t s, void* workspace, double* reduce_buf, void* aux) {
   const DeviceTree& T = p.tree;
   const int64_t N = T.N;
   const int D = p.opts.dim;
-  const bool mixed = fp32_pairs(p.opts);
   const int km = (d_f ? 1 : 0) | (d_g ? 2 : 0);
   const bool grad = d_gradu != nullptr;
-  const bool ff = ff_pairs(p.opts) && (d_u || grad);
+  const bool grad_aux = grad && ff_grad_aux(p.opts);   // float-float gradient of an FP32 plan
+  const bool mixed = fp32_pairs(p.opts) && !grad_aux;
+  const bool ff = (ff_pairs(p.opts) && (d_u || grad)) || grad_aux;
   if (grad && D != 3) throw Error{DMK_ERR_UNSUPPORTED, "the gradient is provided in 3D"};
+  if (grad_aux && !aux) throw Error{DMK_ERR_INVALID_ARG, "gradient workspace missing"};
   if (N == 0) return;
   const int B = 256;
   const int nr = p.opts.n_rhs;
@@ -443,6 +495,12 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   P.n_rhs = nr;
 
   char* ws = static_cast<char*>(workspace);
+  // float-float inputs and the symmetric gradient accumulator: in the plan's
+  // workspace for float-float plans, in aux for the gradient of an FP32 plan
+  const WsLayout WL = ws_layout(p.opts, N);
+  float4* ffbase = grad_aux ? static_cast<float4*>(aux) : reinterpret_cast<float4*>(ws + WL.ff_off);
+  double* accg = grad_aux ? reinterpret_cast<double*>(static_cast<char*>(aux) + 7 * N * sizeof(float4))
+                          : reinterpret_cast<double*>(ws + WL.accg_off);
   if (D == 3) perm_densities<3>(p, mixed, ff, km, nr, NR, d_f, d_g, d_n, ws, P, s);
   else perm_densities<2>(p, mixed, ff, km, nr, NR, d_f, d_g, d_n, ws, P, s);
   DMK_CUDA_TRY(cudaGetLastError());
@@ -457,6 +515,8 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   static const int kSetD[] = {16, 20, 24, 28, 32};
   int nt = mixed ? pick_nt(kSetM, 6, need) : pick_nt(kSetD, 5, need);
   if (nt < 0) throw Error{DMK_ERR_UNSUPPORTED, "kernel table longer than the compiled kernels"};
+  for (int id = 0; id < P_COUNT; ++id)   // FP64 tables of every path (nearly coincident pairs included)
+    if (tb.n64[id] > kPolyCap) throw Error{DMK_ERR_UNSUPPORTED, "FP64 kernel table longer than the kernels hold"};
   for (int id = 0; id < P_COUNT; ++id)
     for (int k = 0; k < kPolyCap; ++k) P.c64[id][k] = k < tb.n64[id] ? tb.p64[id][k] : 0.0;
   auto c32 = [&](int id, int k) { return k < tb.n32[id] ? tb.p32[id][k] : 0.f; };
@@ -470,7 +530,7 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     if (ff && grad) {
       // symmetric float-float gradient pass: velocity and gradient accumulated
       // both ways, 12 values per point
-      P.acc = reinterpret_cast<double*>(ws + ws_layout(p.opts, N).accg_off);
+      P.acc = accg;
       DMK_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(double) * 12 * N, s));
       ++p.launches;                                   // the finishing kernel
     } else if ((mixed && km == 1 && !grad && NR == 1 && d_u) || (ff && !grad) || fp64_sym) {
@@ -483,9 +543,38 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
       DMK_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(double) * D * N, s));
       ++p.launches;                                   // the finishing kernel
     }
-    if (ff) dispatch_ff(D, km, grad, nt, P, ff_inputs(p, km, d_f, d_g, d_n, ws, P, s), s);
-    else dispatch(mixed, D, km, grad, nt, NR, P, s);
+    const bool sym32 = mixed && km == 1 && !grad && NR == 1 && d_u;   // k_near_sym (P.acc set above)
+    if (ff || mixed) {
+      P.close_count = reinterpret_cast<int*>(ws + WL.flag_off);
+      P.close_flag = P.close_count + 1;
+      P.close_q = reinterpret_cast<int4*>(ws + WL.queue_off);
+      P.close_cap = static_cast<int>(close_cap(N));
+      DMK_CUDA_TRY(cudaMemsetAsync(P.close_count, 0, sizeof(int) * (T.n_tile + 1), s));
+    }
+    CloseParams C{};
+    C.f = d_f;
+    C.g = d_g;
+    C.n = d_n;
+    if (ff) {
+      const FFParams F = ff_inputs(p, km, d_f, d_g, d_n, ffbase, P, s);
+      dispatch_ff(D, km, grad, nt, P, F, s);
+      C.rel_lo = F.rel_lo;
+      C.acc = P.acc;
+      C.stride = grad ? 12 : D;
+      C.scale = kCloseFF;
+    } else {
+      dispatch(mixed, D, km, grad, nt, NR, P, s);
+      C.acc = sym32 ? P.acc : nullptr;
+      C.stride = D;
+      C.scale = kClose32;
+    }
     ++p.launches;
+    if (ff || mixed) {
+      // nearly coincident pairs in FP64, then the symmetric passes' finish
+      dispatch_close(D, km, grad, ff, P, C, s);
+      p.launches += 2;
+      if (ff || sym32) finish_sym(D, km, grad, P, s);
+    }
     DMK_CUDA_TRY(cudaGetLastError());
   }
 
@@ -497,6 +586,89 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());
   }
+}
+
+// Adjoint pass (near_adj.cuh): v = S[w] (dL/df) and dL/dx for the 3D
+// Stokeslet, one force column.  MIXED plans: float-float pair terms; FP64
+// plans: FP64.  aux holds the sorted inputs and the [N][6] accumulator.
+void launch_adjoint(const Plan& p, const double* d_f, const double* d_w, double* d_v, double* d_gx, cudaStream_t s,
+                    void* aux) {
+  const DeviceTree& T = p.tree;
+  const int64_t N = T.N;
+  if (N == 0) return;
+  if (!aux) throw Error{DMK_ERR_INVALID_ARG, "adjoint workspace missing"};
+  const bool ffp = p.opts.precision == DMK_PRECISION_MIXED;
+  const int B = 256;
+  NearParams P = tree_params(p);
+  P.self_base = -p.tables.phi0 / (2.0 * M_PI);
+  P.n_rhs = 1;
+  const KernelTables& tb = p.tables;
+  for (int id = 0; id < P_COUNT; ++id) {
+    if (tb.n64[id] > kPolyCap) throw Error{DMK_ERR_UNSUPPORTED, "FP64 kernel table longer than the kernels hold"};
+    for (int k = 0; k < kPolyCap; ++k) P.c64[id][k] = k < tb.n64[id] ? tb.p64[id][k] : 0.0;
+  }
+  AdjParams J{};
+  char* base = static_cast<char*>(aux);
+  const size_t in_bytes = static_cast<size_t>(N) * (ffp ? 5 * sizeof(float4) : 6 * sizeof(double));
+  J.acc = reinterpret_cast<double*>(base + ((in_bytes + 255) & ~size_t(255)));
+  J.w_orig = d_w;
+  J.v = d_v;
+  J.gx = d_gx;
+  const unsigned gp = grid_for(N, B);
+  if (ffp) {
+    float4* b4 = reinterpret_cast<float4*>(base);
+    J.rel_lo = b4;
+    J.f_hi = b4 + N;
+    J.f_lo = b4 + 2 * N;
+    J.w_hi = b4 + 3 * N;
+    J.w_lo = b4 + 4 * N;
+    if (T.n_tile > 0) {
+      k_rel_lo<3><<<grid_for(int64_t(T.n_tile) * 32, 256), 256, 0, s>>>(P, b4);
+      ++p.launches;
+    }
+    k_split_ff<3><<<gp, B, 0, s>>>(N, T.perm, d_f, nullptr, b4 + N, b4 + 2 * N);
+    k_split_ff<3><<<gp, B, 0, s>>>(N, T.perm, d_w, nullptr, b4 + 3 * N, b4 + 4 * N);
+    p.launches += 2;
+    auto c64 = [&](int id, int k) { return k < tb.n64[id] ? tb.p64[id][k] : 0.0; };
+    auto hi = [](double v) { return static_cast<float>(v); };
+    auto lo = [](double v) { return static_cast<float>(v - static_cast<double>(static_cast<float>(v))); };
+    const int pairs[3][2] = {{P_GS, P_HS}, {P_PT, P_QT}, {P_DGS, P_DHS}};
+    for (int q = 0; q < 3; ++q)
+      for (int k = 0; k < kPolyCap; ++k) {
+        J.chi[q][k] = make_float2(hi(c64(pairs[q][0], k)), hi(c64(pairs[q][1], k)));
+        J.clo[q][k] = make_float2(lo(c64(pairs[q][0], k)), lo(c64(pairs[q][1], k)));
+      }
+  } else {
+    double* b8 = reinterpret_cast<double*>(base);
+    J.f64 = b8;
+    J.w64 = b8 + 3 * N;
+    k_perm_soa<<<gp, B, 0, s>>>(N, 3, T.perm, d_f, b8);
+    k_perm_soa<<<gp, B, 0, s>>>(N, 3, T.perm, d_w, b8 + 3 * N);
+    p.launches += 2;
+  }
+  DMK_CUDA_TRY(cudaMemsetAsync(J.acc, 0, sizeof(double) * 6 * N, s));
+  if (T.n_tile > 0) {
+    int need = 1;
+    for (int id : {P_GS, P_HS, P_DGS, P_DHS}) need = std::max(need, tb.n64[id]);
+    static const int kSetD[] = {16, 20, 24, 28, 32};
+    const int nt = pick_nt(kSetD, 5, need);
+    if (nt < 0) throw Error{DMK_ERR_UNSUPPORTED, "kernel table longer than the compiled kernels"};
+    if (!ffp) {
+      run_near_adj<false, 16>(P, J, s);
+    } else {
+      switch (nt) {
+#define DMK_CASE_A(NT) \
+  case NT:             \
+    run_near_adj<true, NT>(P, J, s); \
+    break;
+        DMK_NT_FP64(DMK_CASE_A)
+        default:
+          throw Error{DMK_ERR_UNSUPPORTED, "no compiled adjoint kernel for this table length"};
+      }
+    }
+    p.launches += 2;
+  }
+  DMK_CUDA_TRY(cudaGetLastError());
 }
 
 int64_t count_useful_pairs(const Plan& p) {

@@ -174,6 +174,36 @@ __device__ __forceinline__ ff ff_log(ff x) {
   return ff_add(ff_scale(ff_mul(sv, v), 2.f), ff_mul_f(l2, static_cast<float>(e)));
 }
 
+// Source position in the target leaf's frame in FF: (rel + off) + rel_lo,
+// with off the exact dyadic offset of the source leaf (hi parts in ph, lo in pl).
+__device__ __forceinline__ void ff_source_pos(float4 r, float4 rl, const float (&off)[3], float4& ph, float4& pl) {
+  const ff sx = two_sum(r.x, off[0]), sy = two_sum(r.y, off[1]), sz = two_sum(r.z, off[2]);
+  const ff px = fast_two_sum(sx.hi, __fadd_rn(sx.lo, rl.x));
+  const ff py = fast_two_sum(sy.hi, __fadd_rn(sy.lo, rl.y));
+  const ff pz = fast_two_sum(sz.hi, __fadd_rn(sz.lo, rl.z));
+  ph = make_float4(px.hi, py.hi, pz.hi, 0.f);
+  pl = make_float4(px.lo, py.lo, pz.lo, 0.f);
+}
+
+// FF displacement x = target - source (target th + tl, source ph + pl) and r^2;
+// the float-float kernel and k_near_close decide "nearly coincident" on the
+// same r^2.hi, so they split the pairs exactly.
+template <int D>
+__device__ __forceinline__ ff ff_disp_r2(float4 th, float4 tl, float4 ph, float4 pl, ff& dx, ff& dy, ff& dz) {
+  dx = two_sum(th.x, -ph.x);
+  dy = two_sum(th.y, -ph.y);
+  dz = {0.f, 0.f};
+  dx = fast_two_sum(dx.hi, __fadd_rn(dx.lo, __fsub_rn(tl.x, pl.x)));
+  dy = fast_two_sum(dy.hi, __fadd_rn(dy.lo, __fsub_rn(tl.y, pl.y)));
+  ff r2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
+  if (D == 3) {
+    dz = two_sum(th.z, -ph.z);
+    dz = fast_two_sum(dz.hi, __fadd_rn(dz.lo, __fsub_rn(tl.z, pl.z)));
+    r2 = ff_add(r2, ff_mul(dz, dz));
+  }
+  return r2;
+}
+
 // ------------------------------------------------------------------ kernel
 // GRAD (Stokeslet only) adds the velocity gradient, the derivative of
 // Eq. (res_stokeslet) with the tree held fixed:
@@ -257,18 +287,14 @@ __global__ void __launch_bounds__(32 * kFFWarps<D>) k_near_ff(const __grid_const
       __syncwarp();
       if (lane < ns) {
         const int64_t si = s0 + lane;
-        const float4 r = P.rel[si], rl = F.rel_lo[si];
-        // source in the target leaf's frame: (rel + off) + rel_lo, off exact
-        const ff sx = two_sum(r.x, E.off[0]), sy = two_sum(r.y, E.off[1]), sz = two_sum(r.z, E.off[2]);
-        const ff px = fast_two_sum(sx.hi, __fadd_rn(sx.lo, rl.x));
-        const ff py = fast_two_sum(sy.hi, __fadd_rn(sy.lo, rl.y));
-        const ff pz = fast_two_sum(sz.hi, __fadd_rn(sz.lo, rl.z));
-        s_ph[wid][lane] = make_float4(px.hi, py.hi, pz.hi, 0.f);
-        s_pl[wid][lane] = make_float4(px.lo, py.lo, pz.lo, 0.f);
-        rowx[lane] = -2.f * px.hi;
-        rowy[lane] = -2.f * py.hi;
-        rowz[lane] = -2.f * pz.hi;
-        roww[lane] = fmaf(px.hi, px.hi, fmaf(py.hi, py.hi, pz.hi * pz.hi)) - nu2m;
+        float4 ph, pl;
+        ff_source_pos(P.rel[si], F.rel_lo[si], E.off, ph, pl);
+        s_ph[wid][lane] = ph;
+        s_pl[wid][lane] = pl;
+        rowx[lane] = -2.f * ph.x;
+        rowy[lane] = -2.f * ph.y;
+        rowz[lane] = -2.f * ph.z;
+        roww[lane] = fmaf(ph.x, ph.x, fmaf(ph.y, ph.y, ph.z * ph.z)) - nu2m;
         if (KM & 1) {
           s_ah[wid][lane] = F.f_hi[si];
           s_al[wid][lane] = F.f_lo[si];
@@ -319,21 +345,19 @@ __global__ void __launch_bounds__(32 * kFFWarps<D>) k_near_ff(const __grid_const
           if (qi >= n) continue;
           const int ent = s_q[wid][qi];
           const int tl = ent >> 5, j = ent & 31;
-          const float4 th = s_th[wid][tl], tlw = s_tl[wid][tl];
-          const float4 ph = s_ph[wid][j], pl = s_pl[wid][j];
-          ff dx = two_sum(th.x, -ph.x), dy = two_sum(th.y, -ph.y), dz = {0.f, 0.f};
-          dx = fast_two_sum(dx.hi, __fadd_rn(dx.lo, __fsub_rn(tlw.x, pl.x)));
-          dy = fast_two_sum(dy.hi, __fadd_rn(dy.lo, __fsub_rn(tlw.y, pl.y)));
-          ff r2 = ff_add(ff_mul(dx, dx), ff_mul(dy, dy));
-          if (D == 3) {
-            dz = two_sum(th.z, -ph.z);
-            dz = fast_two_sum(dz.hi, __fadd_rn(dz.lo, __fsub_rn(tlw.z, pl.z)));
-            r2 = ff_add(r2, ff_mul(dz, dz));
-          }
+          ff dx, dy, dz;
+          const ff r2 = ff_disp_r2<D>(s_th[wid][tl], s_tl[wid][tl], s_ph[wid][j], s_pl[wid][j], dx, dy, dz);
           float2 res[NO];
 #pragma unroll
           for (int a = 0; a < NO; ++a) res[a] = make_float2(0.f, 0.f);
-          const bool inside = (r2.hi < nu2 || (r2.hi == nu2 && r2.lo < 0.f)) && (r2.hi > 0.f);
+          // nearly coincident pairs (r^2 <= kCloseFF nu^2) are left to
+          // k_near_close (FP64); they mark the tiles of both points
+          const bool inside = (r2.hi < nu2 || (r2.hi == nu2 && r2.lo < 0.f)) && (r2.hi > nu2 * kCloseFF);
+          if (r2.hi <= nu2 * kCloseFF && (both || tl != j)) {
+            P.close_flag[tile] = 1;
+            if (both) P.close_flag[U] = 1;
+            close_push(P, t0 + tl, s0 + j, e, LB, both);
+          }
           if (inside) {
             const ff rho2 = ff_scale(r2, nu2inv);
             // t = 2 rho^2 - 1; the FP32 difference is not exact for rho^2 < 1/4
@@ -530,11 +554,11 @@ __global__ void k_near_sym_finish_grad(const __grid_constant__ NearParams P, con
   for (int k = 0; k < 9; ++k) P.gradu[o * 9 + k] = acc[i * 12 + 3 + k] * kInv8Pi;
 }
 
+// Leaves its sums in P.acc: the caller adds the nearly coincident pairs
+// (k_near_close) and finishes with k_near_sym_finish(_grad).
 template <int D, int KM, bool GRAD, int NT>
 void run_near_ff(const NearParams& P, const FFParams& F, cudaStream_t s) {
   k_near_ff<D, KM, GRAD, NT><<<(P.n_tile + kFFWarps<D> - 1) / kFFWarps<D>, 32 * kFFWarps<D>, 0, s>>>(P, F);
-  if (GRAD) k_near_sym_finish_grad<3><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
-  else k_near_sym_finish<D, KM><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
 }
 
 #define DMK_FOR_EACH_FF(M, NT)                                                    \

@@ -71,6 +71,10 @@ struct NearParams {
   double* u;             // [N][D][n_rhs] caller order (may be null for grad-only)
   double* gradu;         // [N][3][3] caller order
   double* acc;           // sorted FP64 accumulator [N][D] (symmetric Stokeslet pass), zeroed
+  int* close_flag;       // per target tile, zeroed: set where a nearly coincident pair was skipped
+  int* close_count;      // skipped pairs queued (zeroed; may exceed close_cap)
+  int4* close_q;         // queued pairs: (target, source, near-list entry, L_B | both << 8), sorted indices
+  int close_cap;
   double self_base;      // 3D: -phi(0)/(2 pi); 2D: -m_d(0)/(8 pi)
   int n_rhs;             // force columns of the caller's arrays
   float2 c32p[3][kPolyCap];   // FP32 pairs (gS, hS), (pT, qT), (gS', hS')
@@ -101,6 +105,135 @@ template <int D>
 __device__ __forceinline__ double self_coeff(const NearParams& P, int LB) {
   if (D == 3) return P.self_base * ldexp(1.0, LB + 1);
   return P.self_base - 2.0 * (LB + 1) * kLn2 * kInv8Pi;        // + 2 log(nu_t) / (8 pi)
+}
+
+// ------------------------------------------------ nearly coincident pairs
+// FP32 and float-float pair terms start from leaf-relative coordinates whose
+// rounding error (about 2^-23 h in FP32 for a leaf of side h, 2^-48 h in
+// float-float) is a relative error 2^-23 h / r of the displacement x: for
+// nearly coincident points it would dominate the pair term, which is also the
+// largest one (S_R -> S as r -> 0, App. A.1).  The FP32 kernels skip the pairs
+// with r^2 <= kClose32 nu^2 (r <= nu/32: beyond it x carries at most ~8e-6
+// relative error) and the float-float kernel those with r^2 <= kCloseFF nu^2
+// (r <= nu/1024); k_near_close (near_close.cuh) then evaluates them with
+// close_pair_fp64: x = (w_t - w_s) + q from the FP64 in-cell coordinates and
+// the pair terms with the FP64 kernel's arithmetic.
+constexpr float kClose32 = 0x1p-10f;
+constexpr float kCloseFF = 0x1p-20f;
+
+// Densities of one point: [0, 3) Stokeslet force, [3, 6) stresslet strength
+// g, [6, 9) orientation n, [9] g.n.  out (zeroed by the caller): [0, 3) target
+// side of the velocity, [3, 12) of the gradient (grad[j*3+m] = d_m u_j);
+// [12, 15), [15, 24) the source side (only if both): S_R is even, T_R and
+// grad S_R odd.  Terms without the 1/(8 pi) factor, as in the kernels.
+constexpr int kClosePairOut = 24;
+template <int D, int KM, bool GRAD>
+__device__ __noinline__ void close_pair_fp64(const NearParams& P, int64_t it, int64_t is, const double* q,
+                                             double nuinv, const double* sd, const double* td, bool both,
+                                             double* out) {
+  const int64_t N = P.N;
+  double x[3] = {0.0, 0.0, 0.0};
+  double r2 = 0.0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    x[a] = __dadd_rn(__dsub_rn(P.w[a * N + it], P.w[a * N + is]), q[a]);
+    r2 = __dadd_rn(r2, __dmul_rn(x[a], x[a]));
+  }
+  const double nu2inv = nuinv * nuinv;
+  const double rho2 = r2 * nu2inv;
+  if (!(rho2 < 1.0 && r2 > 0.0)) return;
+  const double t = fma(2.0, rho2, -1.0);
+  double ri = 0.0, ri2, logr2 = 0.0;
+  if (D == 3) {
+    ri = 1.0 / sqrt(r2);
+    ri2 = ri * ri;
+  } else {
+    ri2 = 1.0 / r2;
+    logr2 = log(rho2);
+  }
+  const double dx = x[0], dy = x[1], dz = x[2];
+  if (KM & 1) {
+    const double g = horner<kPolyCap>(P.c64[P_GS], t);
+    const double h = horner<kPolyCap>(P.c64[P_HS], t);
+    double A, C;
+    if (D == 3) {
+      A = fma(g, nuinv, ri);
+      C = ri2 * fma(h, nuinv, ri);
+    } else {
+      A = -logr2 - g;
+      C = fma(-h, nu2inv, 2.0 * ri2);
+    }
+    double A1 = 0.0, C1 = 0.0;
+    if (GRAD) {
+      const double dg = horner<kPolyCap>(P.c64[P_DGS], t);
+      const double dh = horner<kPolyCap>(P.c64[P_DHS], t);
+      const double nu3i = nuinv * nuinv * nuinv;
+      const double ri3 = ri2 * ri;
+      A1 = fma(2.0 * dg, nu3i, -ri3);
+      C1 = fma(-3.0 * ri3, ri2, ri2 * fma(2.0 * dh, nu3i, -2.0 * h * nuinv * ri2));
+    }
+    for (int side = 0; side < (both ? 2 : 1); ++side) {
+      const double* fv = side ? td : sd;               // target side: the source's force
+      const double sgn = side ? -1.0 : 1.0;            // grad S_R is odd
+      double* o = out + 12 * side;
+      const double xf = fma(dx, fv[0], fma(dy, fv[1], dz * fv[2]));
+      const double Cx = C * xf;
+      o[0] += fma(A, fv[0], Cx * dx);
+      o[1] += fma(A, fv[1], Cx * dy);
+      if (D == 3) o[2] += fma(A, fv[2], Cx * dz);
+      if (GRAD) {
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const double a1 = fma(A1, fv[jj], C1 * x[jj] * xf);
+#pragma unroll
+          for (int mm = 0; mm < 3; ++mm) {
+            double v = fma(a1, x[mm], C * x[jj] * fv[mm]);
+            if (jj == mm) v = fma(C, xf, v);
+            o[3 + jj * 3 + mm] += sgn * v;
+          }
+        }
+      }
+    }
+  }
+  if (KM & 2) {
+    const double pt = horner<kPolyCap>(P.c64[P_PT], t);
+    const double qt = horner<kPolyCap>(P.c64[P_QT], t);
+    double Dc, Ec;
+    if (D == 3) {
+      Dc = pt * nuinv * ri2;
+      Ec = -6.0 * ri2 * ri2 * fma(qt, nuinv, ri);
+    } else {
+      Dc = -pt * nu2inv;
+      Ec = fma(6.0 * qt, nu2inv * nu2inv, -8.0 * ri2 * ri2);
+    }
+    for (int side = 0; side < (both ? 2 : 1); ++side) {
+      const double* dv = side ? td : sd;
+      const double sgn = side ? -1.0 : 1.0;            // T_R is odd
+      double* o = out + 12 * side;
+      const double xn = fma(dx, dv[6], fma(dy, dv[7], dz * dv[8]));
+      const double xg = fma(dx, dv[3], fma(dy, dv[4], dz * dv[5]));
+      const double Ex = Ec * xg * xn + Dc * dv[9];
+#pragma unroll
+      for (int a = 0; a < D; ++a) o[a] += sgn * fma(Dc, fma(dv[3 + a], xn, dv[6 + a] * xg), Ex * x[a]);
+    }
+  }
+}
+
+// Queues a skipped nearly coincident pair (target t, source s, sorted
+// indices) of near-list entry e of the target leaf (level LB); both: the pair
+// gives the source its side too (symmetric passes).  Beyond the capacity only
+// the count grows, and the tiles' marks take over (k_near_close).
+__device__ __forceinline__ void close_push(const NearParams& P, int64_t t, int64_t s, int e, int LB, bool both) {
+  const int k = atomicAdd(P.close_count, 1);
+  if (k < P.close_cap)
+    P.close_q[k] = make_int4(static_cast<int>(t), static_cast<int>(s), e, LB | (both ? 256 : 0));
+}
+
+// two-sum accumulator (hi, lo) += v for an FP64 value v
+__device__ __forceinline__ void two_sum_add_d(float& hi, float& lo, double v) {
+  const float vh = __double2float_rn(v);
+  two_sum_add(hi, lo, vh);
+  lo += __double2float_rn(v - static_cast<double>(vh));
 }
 
 // ------------------------------------------------------ tile traversal
@@ -293,6 +426,7 @@ __global__ void __launch_bounds__(32 * kMixWarps, 24 / kMixWarps) k_near_mixed(c
     const float nu2 = E.nu2, nuinv = E.nuinv;
     const float nu2inv = nuinv * nuinv;
     const float nu2m = nu2 * (1.f + 0x1p-12f);
+    const float thr = nu2 * kClose32;                  // nearly coincident: k_near_close
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
     for (int Ub = U0; Ub < U1; Ub += 32)
     for (uint32_t tm = near_tile_mask(P, Ub, U1, E, tlo, thi, lane); tm; tm &= tm - 1u) {
@@ -335,13 +469,15 @@ __global__ void __launch_bounds__(32 * kMixWarps, 24 / kMixWarps) k_near_mixed(c
       float pg[GRAD ? 9 : 1];
 #pragma unroll
       for (int k = 0; k < (GRAD ? 9 : 1); ++k) pg[k] = 0.f;
+      float rmin = __int_as_float(0x7f800000);         // smallest r^2 of the staged tile
       while (m) {
         const int j = __ffs(m) - 1;
         m &= m - 1u;
         const float4 sp = s_pos[wid][j];
         const float dx = xt.x - sp.x, dy = xt.y - sp.y, dz = xt.z - sp.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (!(r2 < nu2 && r2 > 0.f)) continue;
+        rmin = fminf(rmin, r2);
+        if (!(r2 < nu2 && r2 > thr)) continue;         // r^2 <= thr: queued below
         const float rho2 = r2 * nu2inv;
         const float t = fmaf(2.f, rho2, -1.f);
         float ri = 0.f, ri2, logr2 = 0.f;
@@ -435,6 +571,19 @@ __global__ void __launch_bounds__(32 * kMixWarps, 24 / kMixWarps) k_near_mixed(c
 #pragma unroll
         for (int k = 0; k < 9; ++k) two_sum_add(Gh[k], Gl[k], pg[k]);
       }
+      // skipped nearly coincident pairs mark T for k_near_close (on T's own
+      // tile the self pair, r = 0, always triggers the scan and is left out);
+      // this one-sided pass stays bitwise reproducible, so they are not queued
+      if (__any_sync(0xffffffffu, on && rmin <= thr)) {
+        bool any = false;
+        if (on)
+          for (int j = 0; j < ns; ++j) {
+            const float4 sp = s_pos[wid][j];
+            const float dx = xt.x - sp.x, dy = xt.y - sp.y, dz = xt.z - sp.z;
+            any |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= thr && !(U == tile && j == lane);
+          }
+        if (__any_sync(0xffffffffu, any) && lane == 0) P.close_flag[tile] = 1;
+      }
     }
   }
   if (!on) return;
@@ -509,6 +658,7 @@ __global__ void __launch_bounds__(32 * kSymWarps, 28 / kSymWarps) k_near_sym(con
     const float nu2 = E.nu2, nuinv = E.nuinv;
     const float nu2inv = nuinv * nuinv;
     const float nu2m = nu2 * (1.f + 0x1p-12f);
+    const float thr = nu2 * kClose32;                  // nearly coincident: k_near_close
     const int U0 = P.leaf_tile0[E.X], U1 = U0 + P.leaf_ntile[E.X];
     if (U1 <= tile) continue;                          // every tile of X precedes T
     for (int Ub = U0; Ub < U1; Ub += 32)
@@ -535,12 +685,13 @@ __global__ void __launch_bounds__(32 * kSymWarps, 28 / kSymWarps) k_near_sym(con
       uint32_t m = __reduce_or_sync(0xffffffffu, candidate_mask(s_tst[wid], xt, tt));
       float p[3] = {0.f, 0.f, 0.f};                    // target side, this tile
       // One pair (this lane's target, staged source j): adds the target side
-      // to p and returns the source side (A f_t + C (x.f_t) x) in c.
-      auto pair = [&](int j, float (&c)[3]) {
+      // to p and returns the source side (A f_t + C (x.f_t) x) in c.  Pairs
+      // with r^2 <= thr are left to k_near_close.
+      auto pair = [&](int j, float (&c)[3]) -> float {
         const float4 sp = s_pos[wid][j];
         const float dx = xt.x - sp.x, dy = xt.y - sp.y, dz = xt.z - sp.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        const bool inside = r2 < nu2 && r2 > 0.f;
+        const bool inside = r2 < nu2 && r2 > thr;
         const float rr = inside ? r2 : nu2;            // finite stand-in for the other lanes
         const float rho2 = rr * nu2inv;
         const float t = fmaf(2.f, rho2, -1.f);
@@ -566,15 +717,23 @@ __global__ void __launch_bounds__(32 * kSymWarps, 28 / kSymWarps) k_near_sym(con
         c[0] = fmaf(A, ft.x, Ct * dx);
         c[1] = fmaf(A, ft.y, Ct * dy);
         c[2] = D == 3 ? fmaf(A, ft.z, Ct * dz) : 0.f;
+        return r2;
       };
+      // skipped nearly coincident pairs (r^2 <= thr) mark the tiles of both
+      // points for k_near_close: the smallest r^2 of the staged tile, or on
+      // T's own tile the count of pairs at r^2 <= thr (the self pair is one)
+      bool skipped;
       if (!sym) {
         float c[3];
+        int ncl = 0;
         while (m) {
           const int j = __ffs(m) - 1;
           m &= m - 1u;
-          pair(j, c);
+          ncl += (pair(j, c) <= thr) ? 1 : 0;
         }
+        skipped = on && ncl > 1;
       } else {
+        float rmin = __int_as_float(0x7f800000);
         // The source sides of two consecutive sources (2 x 3 components,
         // padded to 4) are summed over the warp together by a transposing
         // butterfly: each exchange halves the values a lane keeps, so 7
@@ -604,7 +763,7 @@ __global__ void __launch_bounds__(32 * kSymWarps, 28 / kSymWarps) k_near_sym(con
           const int j = __ffs(m) - 1;
           m &= m - 1u;
           float c[3];
-          pair(j, c);
+          rmin = fminf(rmin, pair(j, c));
           if (jp < 0) {
 #pragma unroll
             for (int a = 0; a < 3; ++a) cp[a] = c[a];
@@ -618,6 +777,21 @@ __global__ void __launch_bounds__(32 * kSymWarps, 28 / kSymWarps) k_near_sym(con
           const float z3[3] = {0.f, 0.f, 0.f};
           reduce2(cp, z3, jp, -1);
         }
+        skipped = rmin <= thr;
+      }
+      if (__any_sync(0xffffffffu, skipped)) {
+        if (lane == 0) {
+          P.close_flag[tile] = 1;
+          P.close_flag[U] = 1;
+        }
+        // queue them (same FP32 arithmetic as the pair path)
+        if (on)
+          for (int j = 0; j < ns; ++j) {
+            const float4 sp = s_pos[wid][j];
+            const float dx = xt.x - sp.x, dy = xt.y - sp.y, dz = xt.z - sp.z;
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= thr && (sym || j != lane))
+              close_push(P, t0 + lane, s0 + j, e, LB, sym);
+          }
       }
 #pragma unroll
       for (int a = 0; a < D; ++a) two_sum_add(uh[a], ul[a], p[a]);
@@ -1017,12 +1191,14 @@ __global__ void __launch_bounds__(32 * Fp64Shape<D, KM, GRAD, NT, NR>::WPB) k_ne
   }
 }
 
+// The symmetric FP32 pass (P.acc set) leaves its sums in P.acc: the caller
+// adds the nearly coincident pairs (k_near_close) and finishes with
+// k_near_sym_finish.
 template <int D, int KM, bool GRAD, int NT, int NR>
 void run_near_mixed(const NearParams& P, cudaStream_t s) {
   if constexpr (KM == 1 && !GRAD && NR == 1) {
     if (P.acc && P.u) {
       k_near_sym<D, NT><<<(P.n_tile + kSymWarps - 1) / kSymWarps, 32 * kSymWarps, 0, s>>>(P, P.acc);
-      k_near_sym_finish<D, 1><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
       return;
     }
   }

@@ -13,10 +13,10 @@
 // Limits and sharing (also documented in include/dmk_stokes.h):
 //   * the array holds kNoAllocScratchBytes (64 MiB); a plan whose evaluation
 //     needs more is rejected with DMK_ERR_INVALID_ARG before anything runs
-//     (mixed precision at eps >= 2e-7: 128 bytes per point, about 524k
-//     points; mixed below 2e-7: 288 bytes per point in 3D (192 in
-//     2D), about 233k points; FP64:
-//     104 bytes per point, about 645k points; plus 32 bytes per system);
+//     (mixed precision at eps >= 2e-7: 136 bytes per point, about 493k
+//     points; mixed below 2e-7: 296 bytes per point in 3D (200 in 2D),
+//     about 226k points; FP64: 104 bytes per point, about 645k points; plus
+//     32 bytes per system);
 //   * every GPU that loads the library holds the array until the process exits;
 //   * all calls on a device share the array and it keeps the last call's
 //     contents; the zero-mode sums are cleared at the start of every call;
@@ -101,7 +101,7 @@ extern "C" dmk_status_t dmk_stokes_eval_noalloc(dmk_stokes_plan_t plan, const do
   plan->last_stream = s;
   try {
     dmk::launch_near_ws(p, want_s ? d_f : nullptr, want_t ? d_g : nullptr, want_t ? d_n : nullptr, d_u, nullptr,
-                        s, scratch, reinterpret_cast<double*>(static_cast<char*>(scratch) + ws));
+                        s, scratch, reinterpret_cast<double*>(static_cast<char*>(scratch) + ws), nullptr);
   } catch (const dmk::Error& e) {
     return dmk::record_error(plan, e.code, e.msg);
   }

@@ -45,6 +45,7 @@ _lib.dmk_stokes_plan.argtypes = [ctypes.POINTER(Opts), ctypes.c_int64, _P, ctype
 _lib.dmk_stokes_plan_batched.argtypes = [ctypes.POINTER(Opts), ctypes.c_int32, _P, _P, _P, ctypes.POINTER(_P)]
 _lib.dmk_stokes_eval.argtypes = [_P, _P, _P, _P, _P, _P]
 _lib.dmk_stokes_eval_grad.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+_lib.dmk_stokes_eval_adjoint.argtypes = [_P, _P, _P, _P, _P, _P]
 _lib.dmk_stokes_eval_noalloc.argtypes = [_P, _P, _P, _P, _P, _P]
 _lib.dmk_stokes_sync_status.argtypes = [_P]
 _lib.dmk_stokes_plan_stats.argtypes = [_P, _P]
@@ -56,13 +57,13 @@ _lib.dmk_stokes_destroy.restype = None
 _lib.dmk_stokes_last_error.argtypes = [_P]
 _lib.dmk_stokes_last_error.restype = ctypes.c_char_p
 for _name in ("dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
-              "dmk_stokes_eval_grad",
+              "dmk_stokes_eval_grad", "dmk_stokes_eval_adjoint",
               "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree",
               "dmk_stokes_kernel_table"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 EXPORTED = ["dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
-            "dmk_stokes_eval_grad",
+            "dmk_stokes_eval_grad", "dmk_stokes_eval_adjoint",
             "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree", "dmk_stokes_kernel_table",
             "dmk_stokes_destroy", "dmk_stokes_last_error"]
 
@@ -173,6 +174,16 @@ class Plan:
         _check(code, self._h)
         return (u, gu) if want_u else gu
 
+    def eval_adjoint(self, f, w, stream=None):
+        """dmk_stokes_eval_adjoint: (dL/df, dL/dx), both [n, 3], for cotangent w = dL/du."""
+        f = _as_dev(f, self.dim, "f", self.device)
+        w = _as_dev(w, self.dim, "w", self.device)
+        v = torch.empty((self.n, self.dim), dtype=torch.float64, device=self.device)
+        gx = torch.empty((self.n, self.dim), dtype=torch.float64, device=self.device)
+        code = _lib.dmk_stokes_eval_adjoint(self._h, _ptr(f), _ptr(w), _ptr(v), _ptr(gx), _stream_ptr(stream))
+        _check(code, self._h)
+        return v, gx
+
     def sync_status(self):
         _check(_lib.dmk_stokes_sync_status(self._h), self._h)
 
@@ -235,7 +246,8 @@ class DMKStokesFn(torch.autograd.Function):
     holds the tree, hence every residual scale nu_ts, fixed:
       dL/df   = S[w]                  (S_R is even and symmetric: the operator is its own transpose)
       dL/dx_k = (grad u_k)^T w_k + (grad v_k)^T f_k,   v = S[w]
-    computed with two dmk_stokes_eval_grad calls; no pair terms are stored.
+    both from one dmk_stokes_eval_adjoint call (a symmetric pass that
+    recomputes the pair terms; nothing is stored per pair).
     """
 
     @staticmethod
@@ -249,16 +261,8 @@ class DMKStokesFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, w):
         (f,) = ctx.saved_tensors
-        plan = ctx.plan
-        w = w.contiguous()
-        grad_x = grad_f = None
-        v, gv = plan.eval_grad(w, want_u=True)
-        if ctx.needs_input_grad[1]:
-            grad_f = v
-        if ctx.needs_input_grad[0]:
-            gu = plan.eval_grad(f.detach())
-            grad_x = torch.einsum("tjm,tj->tm", gu, w) + torch.einsum("tjm,tj->tm", gv, f.detach())
-        return grad_x, grad_f, None, None
+        v, gx = ctx.plan.eval_adjoint(f.detach(), w)
+        return (gx if ctx.needs_input_grad[0] else None), (v if ctx.needs_input_grad[1] else None), None, None
 
 
 def near_stokeslet(x, f, plan=None, **plan_kwargs):

@@ -2,8 +2,9 @@
 
 * eval_grad against central finite differences of eval (FP64, plan rebuilt at
   x +- h with the tree checked unchanged), and against the oracle gradient;
-* the autograd function's dL/df and dL/dx for L = 1/2 |u - u_tgt|^2 against the
-  oracle adjoint (dL/df = S[w], dL/dx = (grad u)^T w + (grad v)^T f, v = S[w]);
+* the autograd function's dL/df and dL/dx for L = 1/2 |u - u_tgt|^2 (backward =
+  one dmk_stokes_eval_adjoint call) against the oracle adjoint (dL/df = S[w],
+  dL/dx = (grad u)^T w + (grad v)^T f, v = S[w]), and eval_adjoint directly;
 * torch.autograd.gradcheck on a tiny system;
 * the differentiation workload (3D periodic, N = 2e5 uniform, zero-mean forces,
   eps = 1e-8): directional finite differences of L on a 500-point subset.
@@ -76,11 +77,12 @@ def _oracle_adjoint(x, f, u_tgt, eps, ns, periodic):
 
 
 @pytest.mark.parametrize("periodic", [False, True])
-@pytest.mark.parametrize("precision", [0, 1])
-def test_autograd_matches_oracle_adjoint(dmk, periodic, precision):
-    """FP64: round-off bounds; MIXED at eps = 1e-8 (float-float pair terms): 10 eps."""
+@pytest.mark.parametrize("precision,eps", [(0, 1e-8), (1, 1e-8), (1, 1e-6)])
+def test_autograd_matches_oracle_adjoint(dmk, periodic, precision, eps):
+    """Backward = one dmk_stokes_eval_adjoint call.  FP64: round-off bounds;
+    MIXED (float-float pair terms at both eps): 10 eps."""
     rng = np.random.default_rng(302 + periodic)
-    N, ns, eps = 1500, 40, 1e-8
+    N, ns = 1500, 40
     x = wl.uniform_points(rng, N, 3)
     f = wl.forces(rng, N, 3, zero_mean=True)
     u_tgt = 0.1 * rng.standard_normal((N, 3))
@@ -94,6 +96,32 @@ def test_autograd_matches_oracle_adjoint(dmk, periodic, precision):
     assert rel_l2(u.detach().cpu().numpy(), u_o) < tol[0]
     assert rel_l2(ft.grad.cpu().numpy(), gf_o) < tol[1]
     assert rel_l2(xt.grad.cpu().numpy(), gx_o) < tol[2]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_eval_adjoint_clustered_matches_oracle(dmk, precision):
+    """dmk_stokes_eval_adjoint on clustered points (leaves on several levels,
+    coarse-neighbour pairs) against the oracle adjoint, and twice in a row
+    (the adjoint workspace is reused)."""
+    rng = np.random.default_rng(311)
+    N, ns, eps = 2500, 24, 1e-10
+    x = wl.gaussian_mixture_points(rng, N, 3, 8, 0.03)
+    f = wl.forces(rng, N, 3)
+    w = wl.forces(rng, N, 3)
+    tr = Tree(x, ns)
+    kern = dict(win=ProlateWindow(bandlimit_c(eps)), stokeslet=True)
+    _, gu = onear.near_lists(tr, kern, f=f, want_grad=True)
+    v_o, gv = onear.near_lists(tr, kern, f=w, want_grad=True)
+    gx_o = np.einsum("tjm,tj->tm", gu, w) + np.einsum("tjm,tj->tm", gv, f)
+    p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=eps, precision=precision, leaf_capacity=ns)
+    fd, wd = torch.as_tensor(f, device="cuda"), torch.as_tensor(w, device="cuda")
+    tol = 1e-11 if precision == 0 else 10 * eps
+    for _ in range(2):
+        v, gx = p.eval_adjoint(fd, wd)
+        p.sync_status()
+        assert rel_l2(v.cpu().numpy(), v_o) < tol
+        assert rel_l2(gx.cpu().numpy(), gx_o) < tol
+    p.close()
 
 
 def test_gradcheck_tiny(dmk):
