@@ -3,8 +3,9 @@
  * Stokes potentials (Jiang, Tornberg et al., arXiv 2509.21471).
  *
  * What it computes (the "near" component of the DMK sum, Sec. 5.3 Eq.
- * (three_part_sum) and Step 4 of Sec. 6.1): for every point t of a point set in
- * the unit box [lo, lo+1]^d (Sec. 1), d = 2 or 3, with sources == targets,
+ * (three_part_sum) and Step 4 of Sec. 6.1): for every target t of the unit box
+ * [lo, lo+1]^d (Sec. 1), d = 2 or 3, where the targets are the source points
+ * themselves or a separate point set,
  *
  *   u_t = sum_{s near t, 0 < r < nu_ts}  S_R,nu_ts(x_t - x_s) f_s      (Stokeslet)
  *       + sum_{s near t, 0 < r < nu_ts}  T_R,nu_ts(x_t - x_s) g_s n_s  (stresslet)
@@ -14,7 +15,8 @@
  * (res_stokeslet), (Soffdiag), (res_stresslet), (T-offd)) at the residual scale
  *   nu_ts = 2^-(min(L_t, L_s) + 1),   L = level of the point's leaf,
  * and the Stokeslet self term u_self = -phi(0)/(2 pi nu_t) f_t (Eq. (S_self),
- * nu_t = 2^-(L_t+1); the stresslet's is zero).  "near" = the sources of the
+ * nu_t = 2^-(L_t+1); the stresslet's is zero; separate targets, which carry
+ * no force, have none).  "near" = the sources of the
  * leaves touching t's leaf in the adaptive, level-restricted tree of Step 1
  * (periodic images included in the periodic case, Sec. 6.2).  In the periodic
  * stresslet case the k = 0 term u0(x_t) = -sum_s (x_t - x_s)(g_s . n_s)
@@ -100,8 +102,16 @@ typedef struct {
  * polynomial kernel tables for the bandlimit c of eps (remark closing Sec. 5.2).
  *   n_src   number of points (>= 0, < 2^31)
  *   d_src   [n_src][dim] coordinates
- *   n_trg, d_trg: separate targets are not provided; pass n_trg == n_src and
- *           d_trg == NULL (targets are the sources) else DMK_ERR_UNSUPPORTED.
+ *   n_trg, d_trg: d_trg == NULL with n_trg == n_src: the targets are the
+ *           sources; d_trg == NULL with n_trg == 0 < n_src: an empty set of
+ *           separate targets.  Otherwise d_trg [n_trg][dim] are separate targets
+ *           (0 <= n_trg < 2^31; the sums of Sec. 1 at points that need not be
+ *           sources): the tree is the sources' (leaf capacity counts sources,
+ *           Step 1(a)), each target takes the leaf containing it (empty leaves
+ *           included), its level L_t in nu_ts and that leaf's near list, and no
+ *           self term.  Every output then has n_trg rows in the caller's target
+ *           order.  The passes are one-sided (MIXED below eps 2e-7 takes FP64
+ *           pair terms); dmk_stokes_eval_adjoint returns DMK_ERR_UNSUPPORTED.
  *   stream  cudaStream_t or NULL
  *   out     receives the plan handle (set to NULL on failure)
  * Host-synchronises the stream a few times (tree sizes are read back). */
@@ -122,7 +132,7 @@ dmk_status_t dmk_stokes_plan_batched(const dmk_stokes_opts_t* opts, int32_t n_sy
  *   d_f  [n][dim][n_rhs] Stokeslet forces (required if the Stokeslet bit is set)
  *   d_g  [n][dim] stresslet strengths, d_n [n][dim] orientation vectors
  *        (required if the stresslet bit is set; rho_s = g_s (x) n_s, Eq. (stokes_stress_sum))
- *   d_u  [n][dim][n_rhs] output, overwritten
+ *   d_u  [n_trg][dim][n_rhs] output, overwritten (n_trg = n without separate targets)
  * Does not allocate; may be captured in a CUDA graph.  With one force column
  * the FP32 Stokeslet pass and the float-float and FP64 passes evaluate each
  * pair once for both of its points (the residual Stokeslet is even, the
@@ -157,14 +167,21 @@ dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const do
 dmk_status_t dmk_stokes_eval_noalloc(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
                                      const double* d_n, double* d_u, void* stream);
 
-/* Velocity gradient of the 3D Stokeslet near component (the stresslet gradient
- * and the 2D gradient are not provided: DMK_ERR_UNSUPPORTED):
- *   d_gradu [n][dim][dim][n_rhs], gradu[t][j][m] = d u_j / d x_m at x_t with the
- *   tree (and so every nu_ts) held fixed; the self term does not depend on x.
+/* Velocity gradient of the 3D near component, Stokeslet and / or stresslet
+ * (d_f, d_g, d_n as for dmk_stokes_eval; one density column; the 2D gradient
+ * is not provided: DMK_ERR_UNSUPPORTED):
+ *   d_gradu [n_trg][3][3], gradu[t][j][m] = d u_j / d x_m at x_t with the
+ *   tree (and so every nu_ts) held fixed; the self term does not depend on x,
+ *   the periodic stresslet k = 0 term adds -delta_jm sum_s g_s.n_s.
  *   d_u may be NULL; if not NULL it receives the velocity as dmk_stokes_eval does.
- * The derivative of Eq. (res_stokeslet) (Sec. 5.2) with Phi' = -2 phi
+ * Stokeslet: the derivative of Eq. (res_stokeslet) (Sec. 5.2) with Phi' = -2 phi
  * (Eq. (def_erfc_like_fcn)):  S_R = A(r) I + C(r) x x^T gives
  *   d_m (S_R f)_j = A'(r) x_m/r f_j + C'(r) x_m/r x_j (x.f) + C (delta_jm (x.f) + x_j f_m).
+ * Stresslet: the derivative of Eq. (res_stresslet) written as
+ * u_j = D(r) [g_j (x.n) + x_j (g.n) + n_j (x.g)] + E(r) x_j (x.g)(x.n):
+ *   d_m u_j = D'(r) x_m/r V_j + D (g_j n_m + delta_jm (g.n) + n_j g_m)
+ *           + E'(r) x_m/r x_j (x.g)(x.n) + E (delta_jm (x.g)(x.n) + x_j (g_m (x.n) + (x.g) n_m)),
+ * V_j the bracket of D; every precision takes FP64 pair terms for it.
  * MIXED plans take float-float pair terms for the gradient at every eps (FP32
  * gradient terms, ~1/r^3, would carry a relative l2 error near 2e-5); a plan
  * with FP32 velocity pair terms (eps >= 2e-7) allocates the gradient

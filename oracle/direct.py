@@ -52,13 +52,18 @@ def direct_sum(x, f=None, g=None, n=None, targets=None):
     return u
 
 
-def stresslet_zero_mode(w, g, n, targets=None):
-    """u0(x_t) = -sum_s (w_t - w_s)(g_s . n_s), as a plain double loop."""
+def stresslet_zero_mode(w, g, n, targets=None, wt=None):
+    """u0(x_t) = -sum_s (w_t - w_s)(g_s . n_s), as a plain double loop; the
+    targets are the points (all, or the indices in targets) or, with wt, the
+    separate in-cell target coordinates wt."""
     w = np.asarray(w, dtype=np.float64)
     N, d = w.shape
-    tset = np.arange(N) if targets is None else np.asarray(targets)
+    if wt is None:
+        tset = np.arange(N) if targets is None else np.asarray(targets)
+        wt = w[tset]
+    wt = np.asarray(wt, dtype=np.float64)
     gn = np.sum(g * n, axis=1)
-    u = np.zeros((len(tset), d))
-    for row, t in enumerate(tset):
-        u[row] = -np.sum((w[t][None, :] - w) * gn[:, None], axis=0)
+    u = np.zeros((len(wt), d))
+    for row in range(len(wt)):
+        u[row] = -np.sum((wt[row][None, :] - w) * gn[:, None], axis=0)
     return u

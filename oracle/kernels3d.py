@@ -87,6 +87,18 @@ def dSoffd(win, rho):
     return 2.0 * rho * win.dphi(rho)
 
 
+def dTdiag(win, rho):
+    """d/drho of Tdiag = -2 rho^2 phi'."""
+    rho = np.asarray(rho, dtype=np.float64)
+    return -4.0 * rho * win.dphi(rho) - 2.0 * rho ** 2 * win.d2phi(rho)
+
+
+def dToffd(win, rho):
+    """d/drho of Toffd = Phi + 2 rho phi - (2/3) rho^2 phi', with Phi' = -2 phi."""
+    rho = np.asarray(rho, dtype=np.float64)
+    return (2.0 / 3.0) * rho * win.dphi(rho) - (2.0 / 3.0) * rho ** 2 * win.d2phi(rho)
+
+
 # ------------------------------------------------------------------ tensors
 def stokeslet(x):
     """Full 3D Stokeslet S_jl(x) for displacement(s) x[..., 3]."""
@@ -155,3 +167,35 @@ def stokeslet_res_grad(win, x, nu):
          + C[..., None, None, None] * (eye[:, None, :] * x[..., None, :, None]
                                        + eye[None, :, :] * x[..., :, None, None]))
     return g
+
+
+def stresslet_res_grad(win, x, nu):
+    """d_k T_R,jlm(x) as array [..., j, l, m, k] (derivative of Eq. (res_stresslet)):
+    T_R = D(r) (delta_jl x_m + delta_lm x_j + delta_mj x_l) + O(r) x_j x_l x_m with
+    D = Tdiag/(8 pi r^3), O = -(3/4pi) Toffd/r^5, so
+    d_k T_R = D' x_k/r sym + D (delta_jl delta_mk + delta_lm delta_jk + delta_mj delta_lk)
+              + O' x_k/r x_j x_l x_m + O (delta_jk x_l x_m + x_j delta_lk x_m + x_j x_l delta_mk),
+    D' = (rho Tdiag' - 3 Tdiag)/(8 pi r^4),  O' = -(3/4pi)(rho Toffd' - 5 Toffd)/r^6."""
+    x = np.asarray(x, dtype=np.float64)
+    r = np.sqrt(np.sum(x * x, axis=-1))
+    rho = r / nu
+    inside = rho < 1.0
+    td, to = Tdiag(win, rho, False), Toffd(win, rho, False)
+    D = np.where(inside, td / (EIGHT_PI * r ** 3), 0.0)
+    O = np.where(inside, -3.0 / (4.0 * np.pi) * to / r ** 5, 0.0)
+    dD = np.where(inside, (rho * dTdiag(win, rho) - 3.0 * td) / (EIGHT_PI * r ** 4), 0.0)
+    dO = np.where(inside, -3.0 / (4.0 * np.pi) * (rho * dToffd(win, rho) - 5.0 * to) / r ** 6, 0.0)
+    e = np.eye(3)
+    xh = x / r[..., None]
+    sym = (e[:, :, None] * x[..., None, None, :] + e[None, :, :] * x[..., :, None, None]
+           + np.transpose(e)[:, None, :] * x[..., None, :, None])                       # [.., j, l, m]
+    xxx = x[..., :, None, None] * x[..., None, :, None] * x[..., None, None, :]
+    dsym = (e[:, :, None, None] * e[None, None, :, :] + e[None, :, :, None] * e[:, None, None, :]
+            + np.transpose(e)[:, None, :, None] * e[None, :, None, :])                   # [j, l, m, k]
+    dxxx = (e[:, None, None, :] * x[..., None, :, None, None] * x[..., None, None, :, None]
+            + x[..., :, None, None, None] * e[None, :, None, :] * x[..., None, None, :, None]
+            + x[..., :, None, None, None] * x[..., None, :, None, None] * e[None, None, :, :])
+    return (dD[..., None, None, None, None] * sym[..., None] * xh[..., None, None, None, :]
+            + D[..., None, None, None, None] * dsym
+            + dO[..., None, None, None, None] * xxx[..., None] * xh[..., None, None, None, :]
+            + O[..., None, None, None, None] * dxxx)

@@ -64,6 +64,10 @@ def _pair_values(kern, d, nu, fs, gs, ns, want_grad):
             grad += np.einsum("pjlm,pl->pjm", km.stokeslet_res_grad(tab, d, nu), fs)
     if kern.get("stresslet") and gs is not None:
         out += np.einsum("pjlm,pl,pm->pj", km.stresslet_res(tab, d, nu), gs, ns)
+        if want_grad:
+            if dim != 3:
+                raise NotImplementedError("the stresslet gradient is 3D")
+            grad += np.einsum("pjlmk,pl,pm->pjk", km.stresslet_res_grad(tab, d, nu), gs, ns)
     return out, grad
 
 
@@ -135,6 +139,70 @@ def near_lists(tree, kern, f=None, g=None, n=None, targets=None, want_grad=False
         if f is not None:
             u[row_of[T]] += _self_coeff(kern, d, float(np.ldexp(1.0, -(Lt + 1)))) * f[T]
     return (u, G) if want_grad else u
+
+
+def near_targets(tree, kern, xt, f=None, g=None, n=None, want_grad=False):
+    """Near component at separate target points xt (Sec. 1 states the sums
+    for target points x_t that need not be sources).  The tree is the
+    sources'; a target takes the level L_t of the leaf containing it, the pair
+    rule nu_ts = r_{min(L_t, L_s)+1} and the near list of that leaf, and has
+    no self term (it is not a source).  Pairs at r = 0 are skipped.
+    want_grad: also the velocity gradient at the targets (Stokeslet)."""
+    d = tree.dim
+    wt, tleaf = tree.locate(xt)
+    u = np.zeros((len(wt), d))
+    G = np.zeros((len(wt), d, d)) if want_grad else None
+    for B in np.unique(tleaf):
+        T = np.nonzero(tleaf == B)[0]
+        Lt = tree.leaf_level[B]
+        tt, ds, nus, srcs = [], [], [], []
+        for (X, q) in tree.near[B]:
+            S = tree.leaf_points(X)
+            if len(S) == 0:
+                continue
+            dd = (wt[T][:, None, :] - tree.w[S][None, :, :]) + np.array(q, dtype=np.float64)[None, None, :]
+            nu = float(nu_of_levels(Lt, tree.leaf_level[X]))
+            r2 = _r2(dd)
+            it, js = np.nonzero((r2 < nu * nu) & (r2 > 0.0))
+            tt.append(T[it])
+            srcs.append(S[js])
+            ds.append(dd[it, js])
+            nus.append(np.full(len(it), nu))
+        if not tt:
+            continue
+        tl, dd, nu, ss = (np.concatenate(a) for a in (tt, ds, nus, srcs))
+        vals, grads = _pair_values(kern, dd, nu, None if f is None else f[ss], None if g is None else g[ss],
+                                   None if n is None else n[ss], want_grad)
+        for j in range(d):
+            u[:, j] += np.bincount(tl, weights=vals[:, j], minlength=len(wt))
+            if want_grad:
+                for m in range(d):
+                    G[:, j, m] += np.bincount(tl, weights=grads[:, j, m], minlength=len(wt))
+    return (u, G) if want_grad else u
+
+
+def near_targets_brute(tree, kern, xt, f=None, g=None, n=None):
+    """The same by brute force over every source and periodic image, from the
+    target's leaf level and each source's leaf level only."""
+    import itertools
+    d = tree.dim
+    wt, tleaf = tree.locate(xt)
+    images = list(itertools.product((-1, 0, 1), repeat=d)) if tree.periodic else [(0,) * d]
+    u = np.zeros((len(wt), d))
+    for row in range(len(wt)):
+        nu_all = nu_of_levels(tree.leaf_level[tleaf[row]], tree.point_level)
+        ds, nus, srcs = [], [], []
+        for q in images:
+            dd = (wt[row][None, :] - tree.w) + np.array(q, dtype=np.float64)[None, :]
+            r2 = _r2(dd)
+            m = (r2 < nu_all * nu_all) & (r2 > 0.0)
+            ds.append(dd[m])
+            nus.append(nu_all[m])
+            srcs.append(np.nonzero(m)[0])
+        dd, nu, ss = np.concatenate(ds), np.concatenate(nus), np.concatenate(srcs)
+        u[row], _ = _pair_terms(kern, dd, nu, None if f is None else f[ss], None if g is None else g[ss],
+                                None if n is None else n[ss], False)
+    return u
 
 
 def near_brute(tree, kern, f=None, g=None, n=None, targets=None, want_grad=False):

@@ -187,6 +187,16 @@ class Tree:
                     out.append(item)
         return out
 
+    def locate(self, xt):
+        """Separate target points (Sec. 1: sources and targets may differ):
+        their in-cell coordinates and the index of the leaf containing each
+        (the tree is built from the sources; leaves partition the unit box,
+        empty leaves included, so every target has exactly one)."""
+        wt = in_cell_coords(xt, self.lo, self.periodic)
+        key = morton_key(cell_coords(wt, self.M), self.M)
+        leaf = np.searchsorted(self.leaf_anchor_key, key, side="right").astype(np.int64) - 1
+        return wt, leaf
+
     def leaf_points(self, i):
         """Original indices of the points in leaf i (in sorted order)."""
         s = self.leaf_start[i]

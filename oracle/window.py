@@ -135,6 +135,7 @@ class ProlateWindow(_WindowBase):
         self.lam = self.psi_int / npleg.legval(0.0, coef)    # lambda_0^c (Sec. 2.4, the eigen-relation above Eq. (PSWFhat))
         self.phi_coef = coef / self.psi_int
         self.dphi_coef = npleg.legder(self.phi_coef)
+        self.d2phi_coef = npleg.legder(self.dphi_coef)
         self.I0_coef = npleg.legint(self.phi_coef, lbnd=0.0)            # int_0^x phi
         self.I1_coef = npleg.legint(npleg.legmulx(self.phi_coef), lbnd=0.0)  # int_0^x s phi
 
@@ -151,6 +152,9 @@ class ProlateWindow(_WindowBase):
 
     def dphi(self, r):
         return self._masked(self.dphi_coef, r, 0.0)
+
+    def d2phi(self, r):
+        return self._masked(self.d2phi_coef, r, 0.0)
 
     def I0(self, r):
         """int_0^r phi(s) ds for r >= 0 (constant 1/2 beyond the support)."""
@@ -193,6 +197,10 @@ class GaussianWindow(_WindowBase):
     def dphi(self, r):
         r = np.asarray(r, dtype=np.float64)
         return -2.0 * r / self.sigma ** 2 * self.phi(r)
+
+    def d2phi(self, r):
+        r = np.asarray(r, dtype=np.float64)
+        return (4.0 * r * r / self.sigma ** 4 - 2.0 / self.sigma ** 2) * self.phi(r)
 
     def Phi(self, r):
         """Closed form: Phi_G = erfc(r/sigma) (Gaussian case of Eq. (harmonic_split))."""

@@ -10,9 +10,6 @@
 
 #include "common.cuh"
 
-namespace dmk {
-size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N);
-}
 
 namespace {
 
@@ -149,7 +146,8 @@ void release(dmk::Plan& p) {
 }
 
 dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64_t* h_offsets,
-                       const double* d_src, void* stream, dmk_stokes_plan_t* out) {
+                       const double* d_src, const double* d_trg, int64_t n_trg, void* stream,
+                       dmk_stokes_plan_t* out) {
   if (!out) return set_err(nullptr, DMK_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   std::string msg;
@@ -162,6 +160,9 @@ dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64
   const int64_t N = h_offsets[n_sys];
   if (N >= (int64_t(1) << 31)) return set_err(nullptr, DMK_ERR_INVALID_ARG, "too many points (>= 2^31)");
   if (N > 0 && !d_src) return set_err(nullptr, DMK_ERR_INVALID_ARG, "d_src is NULL");
+  if (d_trg && n_sys != 1) return set_err(nullptr, DMK_ERR_UNSUPPORTED, "separate targets need a single system");
+  if (d_trg && (n_trg < 0 || n_trg >= (int64_t(1) << 31)))
+    return set_err(nullptr, DMK_ERR_INVALID_ARG, "n_trg out of range");
 
   dmk_stokes_plan_t plan = new (std::nothrow) dmk_stokes_plan_s();
   if (!plan) return set_err(nullptr, DMK_ERR_NOMEM, "host allocation failed");
@@ -182,13 +183,14 @@ dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64
     p.tree.n_sys = n_sys;
     // one arena block for the tree (~80 bytes per point) and the evaluation workspace
     p.arena.s = p.stream;
-    p.fsorted_bytes = dmk::eval_workspace_bytes(p.opts, N);
+    p.fsorted_bytes = dmk::eval_workspace_bytes(p.opts, N, d_trg ? n_trg : N);
     p.arena.reserve(p.fsorted_bytes + static_cast<size_t>(N) * 96 + 32 * static_cast<size_t>(n_sys) +
                     (size_t(8) << 20));
     p.status = p.arena.alloc<int>(1);
     DMK_CUDA_TRY(cudaMemsetAsync(p.status, 0, sizeof(int), p.stream));
     p.h_status = dmk::pinned_slot();
     dmk::build_tree(p, d_src, h_offsets);
+    if (d_trg) dmk::build_targets(p, d_trg, n_trg);
     p.fsorted = p.arena.alloc<char>(p.fsorted_bytes);
     p.reduce_buf = p.arena.alloc<double>(4 * n_sys);
     DMK_CUDA_TRY(cudaGetLastError());
@@ -221,17 +223,22 @@ dmk_status_t dmk_stokes_plan(const dmk_stokes_opts_t* opts, int64_t n_src, const
                              int64_t n_trg, const double* d_trg, void* stream, dmk_stokes_plan_t* out) {
   if (out) *out = nullptr;
   if (n_src < 0) return set_err(nullptr, DMK_ERR_INVALID_ARG, "n_src < 0");
-  if (d_trg != nullptr || n_trg != n_src)
-    return set_err(nullptr, DMK_ERR_UNSUPPORTED, "separate targets are not provided (pass d_trg = NULL, n_trg = n_src)");
+  if (!d_trg && n_trg != n_src && n_trg != 0)
+    return set_err(nullptr, DMK_ERR_INVALID_ARG, "d_trg is NULL (targets are the sources) but n_trg != n_src");
   int64_t offs[2] = {0, n_src};
-  return make_plan(opts, 1, offs, d_src, stream, out);
+  if (!d_trg && n_trg == 0 && n_src > 0) {
+    // an empty set of separate targets (no valid pointer exists for it)
+    static const double kNoTarget[3] = {0.0, 0.0, 0.0};
+    return make_plan(opts, 1, offs, d_src, kNoTarget, 0, stream, out);
+  }
+  return make_plan(opts, 1, offs, d_src, d_trg, n_trg, stream, out);
 }
 
 dmk_status_t dmk_stokes_plan_batched(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64_t* h_offsets,
                                      const double* d_src, void* stream, dmk_stokes_plan_t* out) {
   if (out) *out = nullptr;
   if (n_sys > 65535) return set_err(nullptr, DMK_ERR_INVALID_ARG, "n_sys > 65535");
-  return make_plan(opts, n_sys, h_offsets, d_src, stream, out);
+  return make_plan(opts, n_sys, h_offsets, d_src, nullptr, 0, stream, out);
 }
 
 // The gradient and adjoint workspace (aux) is allocated on the plan's stream
@@ -257,13 +264,14 @@ static dmk_status_t run_eval(dmk_stokes_plan_t plan, const double* d_f, const do
   if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
   dmk::Plan& p = plan->p;
   const int64_t N = p.tree.N;
+  const int64_t NT = p.tree.sep ? p.tree.NT : N;
   const bool want_s = p.opts.kernels & DMK_KERNEL_STOKESLET;
   const bool want_t = p.opts.kernels & DMK_KERNEL_STRESSLET;
   if (N > 0) {
     if (want_s && !d_f) return set_err(plan, DMK_ERR_INVALID_ARG, "d_f is NULL but the Stokeslet is requested");
     if (want_t && (!d_g || !d_n)) return set_err(plan, DMK_ERR_INVALID_ARG, "d_g / d_n NULL but the stresslet is requested");
-    if (!d_u && !d_gradu) return set_err(plan, DMK_ERR_INVALID_ARG, "d_u is NULL");
   }
+  if (NT > 0 && !d_u && !d_gradu) return set_err(plan, DMK_ERR_INVALID_ARG, "d_u is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   plan->last_stream = s;
   try {
@@ -277,7 +285,7 @@ static dmk_status_t run_eval(dmk_stokes_plan_t plan, const double* d_f, const do
 
 dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const double* d_g, const double* d_n,
                              double* d_u, void* stream) {
-  if (valid_plan(plan) && plan->p.tree.N > 0 && !d_u)
+  if (valid_plan(plan) && (plan->p.tree.sep ? plan->p.tree.NT : plan->p.tree.N) > 0 && !d_u)
     return set_err(plan, DMK_ERR_INVALID_ARG, "d_u is NULL");
   return run_eval(plan, d_f, d_g, d_n, d_u, nullptr, stream);
 }
@@ -286,14 +294,11 @@ dmk_status_t dmk_stokes_eval_grad(dmk_stokes_plan_t plan, const double* d_f, con
                                   const double* d_n, double* d_u, double* d_gradu, void* stream) {
   if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
   if (plan->p.opts.dim != 3) return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient is provided in 3D");
-  if (plan->p.opts.kernels != DMK_KERNEL_STOKESLET)
-    return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient is provided for the Stokeslet only");
   if (plan->p.opts.n_rhs != 1)
     return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient is provided for n_rhs = 1");
-  if (plan->p.tree.N > 0 && !d_gradu) return set_err(plan, DMK_ERR_INVALID_ARG, "d_gradu is NULL");
-  (void)d_g;
-  (void)d_n;
-  return run_eval(plan, d_f, nullptr, nullptr, d_u, d_gradu, stream);
+  if ((plan->p.tree.sep ? plan->p.tree.NT : plan->p.tree.N) > 0 && !d_gradu)
+    return set_err(plan, DMK_ERR_INVALID_ARG, "d_gradu is NULL");
+  return run_eval(plan, d_f, d_g, d_n, d_u, d_gradu, stream);
 }
 
 dmk_status_t dmk_stokes_eval_adjoint(dmk_stokes_plan_t plan, const double* d_f, const double* d_w, double* d_v,
@@ -304,6 +309,7 @@ dmk_status_t dmk_stokes_eval_adjoint(dmk_stokes_plan_t plan, const double* d_f, 
   if (p.opts.kernels != DMK_KERNEL_STOKESLET)
     return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint is provided for the Stokeslet only");
   if (p.opts.n_rhs != 1) return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint is provided for n_rhs = 1");
+  if (p.tree.sep) return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint is provided for targets = sources");
   const int64_t N = p.tree.N;
   if (N > 0 && (!d_f || !d_w || !d_v || !d_gx))
     return set_err(plan, DMK_ERR_INVALID_ARG, "d_f, d_w, d_v and d_gx are required");
@@ -348,13 +354,17 @@ dmk_status_t dmk_stokes_plan_stats(dmk_stokes_plan_t plan, int64_t stats[10]) {
     cudaMemcpy(off.data(), T.near_off, (T.n_leaf + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost);
   }
   if (T.n_near > 0) cudaMemcpy(nl.data(), T.near_leaf, T.n_near * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  std::vector<int32_t> tst(T.sep ? T.n_leaf + 1 : 0);
+  if (T.sep && T.n_leaf > 0)
+    cudaMemcpy(tst.data(), T.leaf_tstart, (T.n_leaf + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost);
   int64_t issued = 0;
   int maxl = 0;
   for (int i = 0; i < T.n_leaf; ++i) {
     maxl = std::max(maxl, lvl[i]);
     int64_t src = 0;
     for (int e = off[i]; e < off[i + 1]; ++e) src += cnt[nl[e]];
-    issued += int64_t(cnt[i]) * src - cnt[i];
+    // targets of leaf i times the sources of its near leaves (the target itself excluded)
+    issued += T.sep ? int64_t(tst[i + 1] - tst[i]) * src : int64_t(cnt[i]) * src - cnt[i];
   }
   stats[0] = T.n_leaf;
   stats[1] = maxl;

@@ -162,6 +162,19 @@ struct DeviceTree {
   float4* tile_hi = nullptr;
   int32_t* leaf_tile0 = nullptr;       // first tile of each leaf
   int32_t* leaf_ntile = nullptr;
+  // separate targets (single-system plans; sep == 0: the targets are the points)
+  int sep = 0;
+  int64_t NT = 0;
+  int32_t* tperm = nullptr;            // sorted target -> caller's target index
+  double* tw = nullptr;                // in-cell target coordinates, SoA [dim][NT]
+  float4* trel = nullptr;              // leaf-relative FP32 target coordinates
+  int32_t* leaf_tstart = nullptr;      // [n_leaf + 1] targets of each leaf (sorted)
+  int32_t n_ttile = 0;
+  int32_t* ttile_leaf = nullptr;
+  int32_t* ttile_start = nullptr;
+  int32_t* ttile_count = nullptr;
+  float4* ttile_lo = nullptr;
+  float4* ttile_hi = nullptr;
 };
 
 // Bump allocator over a few large stream-ordered blocks.  A plan's device
@@ -242,6 +255,8 @@ constexpr uint32_t kPlanMagic = 0xD3C5A17Bu;
 
 // tree.cu
 void build_tree(Plan& p, const double* d_src, const int64_t* h_offsets);
+// separate targets of a single-system plan, located in the built tree
+void build_targets(Plan& p, const double* d_trg, int64_t n_trg);
 void free_tree(DeviceTree& t, cudaStream_t s);
 
 // near.cu
@@ -253,7 +268,8 @@ void launch_near(const Plan& p, const double* d_f, const double* d_g, const doub
 void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const double* d_n,
                     double* d_u, double* d_gradu, cudaStream_t s, void* workspace, double* reduce_buf,
                     void* aux);
-size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N);
+// N points (sources), NT targets (N when the targets are the points)
+size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N, int64_t NT);
 size_t aux_bytes_grad(const dmk_stokes_opts_t& o, int64_t N);
 size_t aux_bytes_adjoint(const dmk_stokes_opts_t& o, int64_t N);
 // adjoint pass of the 3D Stokeslet (v = S[w], dL/dx); aux of aux_bytes_adjoint bytes

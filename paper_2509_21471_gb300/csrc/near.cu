@@ -10,7 +10,7 @@ namespace dmk {
 #define DMK_EXT_D(D, KM, GR, NT, NR) \
   extern template void run_near_fp64<D, KM, GR, NT, NR>(const NearParams&, cudaStream_t);
 #define DMK_EXT_M_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_EXT_M, NT) DMK_FOR_EACH_VARIANT_2D(DMK_EXT_M, NT)
-#define DMK_EXT_D_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_EXT_D, NT) DMK_FOR_EACH_VARIANT_2D(DMK_EXT_D, NT)
+#define DMK_EXT_D_NT(NT) DMK_FOR_EACH_VARIANT_3D_FP64(DMK_EXT_D, NT) DMK_FOR_EACH_VARIANT_2D(DMK_EXT_D, NT)
 DMK_NT_MIXED(DMK_EXT_M_NT)
 DMK_NT_FP64(DMK_EXT_D_NT)
 #define DMK_EXT_F(D, KM, GR, NT) \
@@ -126,14 +126,19 @@ __global__ void k_zero_reduce(int64_t N, int D, const double* __restrict__ w, co
   }
 }
 
+// at the targets: N, w, perm are the targets' (the sums are the sources')
+// (and its gradient d_m u0_j = -delta_jm G, if gradu is given)
 __global__ void k_zero_apply(int64_t N, int D, const double* __restrict__ w, const int32_t* __restrict__ perm,
                              const int32_t* __restrict__ psys, const double* __restrict__ sums,
-                             double* __restrict__ u) {
+                             double* __restrict__ u, double* __restrict__ gradu) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const double* s = sums + 4 * psys[i];
+  const double* s = sums + 4 * (psys ? psys[i] : 0);   // psys null: one system (separate targets)
   int64_t o = perm[i];
-  for (int a = 0; a < D; ++a) u[o * D + a] -= w[a * N + i] * s[0] - s[1 + a];
+  if (u)
+    for (int a = 0; a < D; ++a) u[o * D + a] -= w[a * N + i] * s[0] - s[1 + a];
+  if (gradu)
+    for (int a = 0; a < D; ++a) gradu[o * D * D + a * (D + 1)] -= s[0];
 }
 
 // FP32 residual of the leaf-relative coordinates: rel_lo = (w - c) - rel, so
@@ -189,20 +194,20 @@ __global__ void k_split_ff(int64_t N, const int32_t* __restrict__ perm, const do
 template <int D>
 __global__ void k_count_useful(const __grid_constant__ NearParams P, unsigned long long* out) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * 4 + wid;
-  if (tile >= P.n_tile) return;
+  const int tile = blockIdx.x * 4 + wid;                // target tile
+  if (tile >= P.n_ttile) return;
   const int64_t N = P.N;
-  const int B = P.tile_leaf[tile];
-  const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
+  const int B = P.ttile_leaf[tile];
+  const int t0 = P.ttile_start[tile], nt = P.ttile_count[tile];
   const int LB = P.leaf_level[B];
   int64_t cB[3] = {0, 0, 0};
   leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
-  const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
+  const float4 tlo = P.ttile_lo[tile], thi = P.ttile_hi[tile];
   const bool on = lane < nt;
-  const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 xt = on ? P.trel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
   double wt[3] = {0.0, 0.0, 0.0};
   if (on)
-    for (int a = 0; a < D; ++a) wt[a] = P.w[a * N + t0 + lane];
+    for (int a = 0; a < D; ++a) wt[a] = P.tw[a * P.NT + t0 + lane];
   unsigned long long cnt = 0;
   for (int e = P.near_off[B]; e < P.near_off[B + 1]; ++e) {
     const Entry E = make_entry<D>(P, e, LB, cB);
@@ -254,7 +259,7 @@ struct WsLayout {
 };
 // capacity of the queue of skipped nearly coincident pairs (16 bytes each)
 int64_t close_cap(int64_t N) { return std::max<int64_t>(1024, N / 4); }
-WsLayout ws_layout(const dmk_stokes_opts_t& o, int64_t N) {
+WsLayout ws_layout(const dmk_stokes_opts_t& o, int64_t N, int64_t NT) {
   const int NR = padded_rhs(o.n_rhs);
   WsLayout L;
   L.f64_off = fp32_pairs(o) ? std::max(3, NR) * N * sizeof(float4) : 0;
@@ -263,7 +268,8 @@ WsLayout ws_layout(const dmk_stokes_opts_t& o, int64_t N) {
   const bool fp64_sym = o.precision == DMK_PRECISION_FP64 && o.n_rhs == 1;
   L.accg_off = L.acc_off + (fp64_sym ? 3 * N * sizeof(double) : 0);
   L.flag_off = L.accg_off + ((ff_pairs(o) && o.dim == 3) ? 12 * N * sizeof(double) : 0);
-  L.queue_off = L.flag_off + (o.precision == DMK_PRECISION_MIXED ? ((N + 1) * sizeof(int) + 15) / 16 * 16 : 0);
+  const int64_t NP = std::max(N, NT);                 // tiles: at most one per point or target
+  L.queue_off = L.flag_off + (o.precision == DMK_PRECISION_MIXED ? ((NP + 1) * sizeof(int) + 15) / 16 * 16 : 0);
   L.bytes = L.queue_off + (o.precision == DMK_PRECISION_MIXED ? close_cap(N) * sizeof(int4) : 0);
   return L;
 }
@@ -286,7 +292,7 @@ void dispatch(bool mixed, int dim, int km, bool grad, int nt, int nr, const Near
     return;                                                                            \
   }
 #define DMK_CASE_M_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_CASE_M, NT) DMK_FOR_EACH_VARIANT_2D(DMK_CASE_M, NT)
-#define DMK_CASE_D_NT(NT) DMK_FOR_EACH_VARIANT_3D(DMK_CASE_D, NT) DMK_FOR_EACH_VARIANT_2D(DMK_CASE_D, NT)
+#define DMK_CASE_D_NT(NT) DMK_FOR_EACH_VARIANT_3D_FP64(DMK_CASE_D, NT) DMK_FOR_EACH_VARIANT_2D(DMK_CASE_D, NT)
   DMK_NT_MIXED(DMK_CASE_M_NT)
   DMK_NT_FP64(DMK_CASE_D_NT)
   throw Error{DMK_ERR_UNSUPPORTED, "no compiled near-field kernel for this configuration"};
@@ -347,6 +353,18 @@ NearParams tree_params(const Plan& p) {
   P.perm = T.perm;
   P.rel = T.rel;
   P.w = T.w;
+  // targets of the one-sided passes
+  P.same_set = T.sep ? 0 : 1;
+  P.n_ttile = T.sep ? T.n_ttile : T.n_tile;
+  P.NT = T.sep ? T.NT : T.N;
+  P.ttile_leaf = T.sep ? T.ttile_leaf : T.tile_leaf;
+  P.ttile_start = T.sep ? T.ttile_start : T.tile_start;
+  P.ttile_count = T.sep ? T.ttile_count : T.tile_count;
+  P.ttile_lo = T.sep ? T.ttile_lo : T.tile_lo;
+  P.ttile_hi = T.sep ? T.ttile_hi : T.tile_hi;
+  P.trel = T.sep ? T.trel : T.rel;
+  P.tw = T.sep ? T.tw : T.w;
+  P.tperm = T.sep ? T.tperm : T.perm;
   return P;
 }
 
@@ -375,7 +393,7 @@ void perm_densities(const Plan& p, bool mixed, bool ff, int km, int nr, int NR, 
     P.g32 = g32;
     P.n32 = n32;
   }
-  double* f64 = reinterpret_cast<double*>(ws + ws_layout(p.opts, N).f64_off);
+  double* f64 = reinterpret_cast<double*>(ws + ws_layout(p.opts, N, T.sep ? T.NT : N).f64_off);
   double* g64 = f64 + 3 * N;
   double* n64 = g64 + 3 * N;
   const bool need64 = (!mixed && !ff) || ((km & 2) && p.opts.periodic);
@@ -476,12 +494,24 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   const int D = p.opts.dim;
   const int km = (d_f ? 1 : 0) | (d_g ? 2 : 0);
   const bool grad = d_gradu != nullptr;
-  const bool grad_aux = grad && ff_grad_aux(p.opts);   // float-float gradient of an FP32 plan
-  const bool mixed = fp32_pairs(p.opts) && !grad_aux;
-  const bool ff = (ff_pairs(p.opts) && (d_u || grad)) || grad_aux;
+  const bool sep = T.sep != 0;                          // separate targets: one-sided passes only
+  // the stresslet gradient takes FP64 pair terms in every precision
+  const bool grad64 = grad && (km & 2);
+  const bool grad_aux = grad && ff_grad_aux(p.opts) && !sep && !grad64;   // float-float gradient of an FP32 plan
+  const bool mixed = fp32_pairs(p.opts) && !grad_aux && !(sep && grad) && !grad64;
+  // the float-float kernels are symmetric passes; with separate targets MIXED
+  // below eps 2e-7 (and its gradient) takes FP64 pair terms
+  const bool ff = ((ff_pairs(p.opts) && (d_u || grad)) || grad_aux) && !sep && !grad64;
   if (grad && D != 3) throw Error{DMK_ERR_UNSUPPORTED, "the gradient is provided in 3D"};
   if (grad_aux && !aux) throw Error{DMK_ERR_INVALID_ARG, "gradient workspace missing"};
-  if (N == 0) return;
+  if (N == 0) {
+    // no sources: separate targets see nothing
+    if (sep && T.NT > 0) {
+      if (d_u) DMK_CUDA_TRY(cudaMemsetAsync(d_u, 0, sizeof(double) * T.NT * D * p.opts.n_rhs, s));
+      if (grad) DMK_CUDA_TRY(cudaMemsetAsync(d_gradu, 0, sizeof(double) * T.NT * 9, s));
+    }
+    return;
+  }
   const int B = 256;
   const int nr = p.opts.n_rhs;
   const int NR = padded_rhs(nr);
@@ -497,7 +527,7 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   char* ws = static_cast<char*>(workspace);
   // float-float inputs and the symmetric gradient accumulator: in the plan's
   // workspace for float-float plans, in aux for the gradient of an FP32 plan
-  const WsLayout WL = ws_layout(p.opts, N);
+  const WsLayout WL = ws_layout(p.opts, N, T.sep ? T.NT : N);
   float4* ffbase = grad_aux ? static_cast<float4*>(aux) : reinterpret_cast<float4*>(ws + WL.ff_off);
   double* accg = grad_aux ? reinterpret_cast<double*>(static_cast<char*>(aux) + 7 * N * sizeof(float4))
                           : reinterpret_cast<double*>(ws + WL.accg_off);
@@ -510,7 +540,9 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
   const int ids[4] = {(km & 1) ? P_GS : -1, (km & 1) ? P_HS : -1, (km & 2) ? P_PT : -1, (km & 2) ? P_QT : -1};
   for (int id : ids)
     if (id >= 0) need = std::max(need, mixed ? tb.n32[id] : tb.n64[id]);
-  if (grad) need = std::max(need, std::max(mixed ? tb.n32[P_DGS] : tb.n64[P_DGS], mixed ? tb.n32[P_DHS] : tb.n64[P_DHS]));
+  if (grad && (km & 1))
+    need = std::max(need, std::max(mixed ? tb.n32[P_DGS] : tb.n64[P_DGS], mixed ? tb.n32[P_DHS] : tb.n64[P_DHS]));
+  if (grad && (km & 2)) need = std::max(need, std::max(tb.n64[P_DPT], tb.n64[P_DQT]));
   static const int kSetM[] = {8, 10, 12, 13, 14, 16};
   static const int kSetD[] = {16, 20, 24, 28, 32};
   int nt = mixed ? pick_nt(kSetM, 6, need) : pick_nt(kSetD, 5, need);
@@ -525,31 +557,31 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     P.c32p[1][k] = make_float2(c32(P_PT, k), c32(P_QT, k));
     P.c32p[2][k] = make_float2(c32(P_DGS, k), c32(P_DHS, k));
   }
-  if (T.n_tile > 0) {
-    const bool fp64_sym = !mixed && !ff && NR == 1 && !grad && d_u;
+  if (P.n_ttile > 0 && T.n_tile > 0) {
+    const bool fp64_sym = !mixed && !ff && NR == 1 && !grad && d_u && !sep;
     if (ff && grad) {
       // symmetric float-float gradient pass: velocity and gradient accumulated
       // both ways, 12 values per point
       P.acc = accg;
       DMK_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(double) * 12 * N, s));
       ++p.launches;                                   // the finishing kernel
-    } else if ((mixed && km == 1 && !grad && NR == 1 && d_u) || (ff && !grad) || fp64_sym) {
+    } else if ((mixed && km == 1 && !grad && NR == 1 && d_u && !sep) || (ff && !grad) || fp64_sym) {
       // symmetric passes (FP32 Stokeslet; float-float and FP64 Stokeslet and
       // stresslet): both points of a pair from one evaluation, summed in a
       // zeroed FP64 accumulator (FP32 / FF: the first 3N doubles of the FP64
       // density region, which these paths leave unused; FP64: its own region)
-      const WsLayout L = ws_layout(p.opts, N);
+      const WsLayout L = ws_layout(p.opts, N, T.sep ? T.NT : N);
       P.acc = reinterpret_cast<double*>(ws + (fp64_sym ? L.acc_off : L.f64_off));
       DMK_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(double) * D * N, s));
       ++p.launches;                                   // the finishing kernel
     }
-    const bool sym32 = mixed && km == 1 && !grad && NR == 1 && d_u;   // k_near_sym (P.acc set above)
+    const bool sym32 = mixed && km == 1 && !grad && NR == 1 && d_u && !sep;   // k_near_sym (P.acc set above)
     if (ff || mixed) {
       P.close_count = reinterpret_cast<int*>(ws + WL.flag_off);
       P.close_flag = P.close_count + 1;
       P.close_q = reinterpret_cast<int4*>(ws + WL.queue_off);
       P.close_cap = static_cast<int>(close_cap(N));
-      DMK_CUDA_TRY(cudaMemsetAsync(P.close_count, 0, sizeof(int) * (T.n_tile + 1), s));
+      DMK_CUDA_TRY(cudaMemsetAsync(P.close_count, 0, sizeof(int) * (P.n_ttile + 1), s));
     }
     CloseParams C{};
     C.f = d_f;
@@ -578,11 +610,12 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     DMK_CUDA_TRY(cudaGetLastError());
   }
 
-  if ((km & 2) && p.opts.periodic && d_u) {
+  if ((km & 2) && p.opts.periodic && (d_u || grad)) {
     DMK_CUDA_TRY(cudaMemsetAsync(reduce_buf, 0, 4 * sizeof(double) * T.n_sys, s));
     k_zero_reduce<<<grid_for(N, B), B, 0, s>>>(N, D, T.w, P.n64, T.point_sys, reduce_buf);
     ++p.launches;
-    k_zero_apply<<<grid_for(N, B), B, 0, s>>>(N, D, T.w, T.perm, T.point_sys, reduce_buf, d_u);
+    if (sep) k_zero_apply<<<grid_for(T.NT, B), B, 0, s>>>(T.NT, D, T.tw, T.tperm, nullptr, reduce_buf, d_u, d_gradu);
+    else k_zero_apply<<<grid_for(N, B), B, 0, s>>>(N, D, T.w, T.perm, T.point_sys, reduce_buf, d_u, d_gradu);
     ++p.launches;
     DMK_CUDA_TRY(cudaGetLastError());
   }
@@ -673,12 +706,12 @@ void launch_adjoint(const Plan& p, const double* d_f, const double* d_w, double*
 
 int64_t count_useful_pairs(const Plan& p) {
   const DeviceTree& T = p.tree;
-  if (T.N == 0 || T.n_tile == 0) return 0;
   const NearParams P = tree_params(p);
+  if (T.N == 0 || P.n_ttile == 0) return 0;
   unsigned long long* d = dalloc<unsigned long long>(1, p.stream);
   DMK_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(unsigned long long), p.stream));
-  if (p.opts.dim == 3) k_count_useful<3><<<(T.n_tile + 3) / 4, 128, 0, p.stream>>>(P, d);
-  else k_count_useful<2><<<(T.n_tile + 3) / 4, 128, 0, p.stream>>>(P, d);
+  if (p.opts.dim == 3) k_count_useful<3><<<(P.n_ttile + 3) / 4, 128, 0, p.stream>>>(P, d);
+  else k_count_useful<2><<<(P.n_ttile + 3) / 4, 128, 0, p.stream>>>(P, d);
   ++p.launches;
   DMK_CUDA_TRY(cudaGetLastError());
   unsigned long long h = 0;
@@ -688,6 +721,6 @@ int64_t count_useful_pairs(const Plan& p) {
   return static_cast<int64_t>(h);
 }
 
-size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N) { return ws_layout(o, N).bytes; }
+size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N, int64_t NT) { return ws_layout(o, N, NT).bytes; }
 
 }  // namespace dmk

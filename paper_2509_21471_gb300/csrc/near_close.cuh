@@ -58,19 +58,19 @@ __global__ void __launch_bounds__(32 * kCloseWarps) k_near_close(const __grid_co
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x * kCloseWarps + wid;
   if (C.acc && *P.close_count <= P.close_cap) return;   // symmetric pass, queue complete: k_close_queue
-  if (tile >= P.n_tile || !P.close_flag[tile]) return;   // no skipped pair has a point in this tile
-  const int B = P.tile_leaf[tile];
-  const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
+  if (tile >= P.n_ttile || !P.close_flag[tile]) return;  // no skipped pair has a point in this tile
+  const int B = P.ttile_leaf[tile];
+  const int t0 = P.ttile_start[tile], nt = P.ttile_count[tile];
   const int LB = P.leaf_level[B];
   int64_t cB[3] = {0, 0, 0};
   leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
-  const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
+  const float4 tlo = P.ttile_lo[tile], thi = P.ttile_hi[tile];
   const bool on = lane < nt;
   const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  const float4 xt = on ? P.rel[t0 + lane] : z4;
-  const float4 xl = (FFC && on) ? C.rel_lo[t0 + lane] : z4;
+  const float4 xt = on ? P.trel[t0 + lane] : z4;
+  const float4 xl = (FFC && on) ? C.rel_lo[t0 + lane] : z4;   // float-float plans have no separate targets
   const int64_t it = t0 + lane;
-  const int64_t o = on ? P.perm[it] : 0;
+  const int64_t o = on ? P.tperm[it] : 0;
   const int nr = P.n_rhs;
 
   const int e1 = P.near_off[B + 1];
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(32 * kCloseWarps) k_near_close(const __grid_co
       if (on) {
         for (int j = 0; j < ns; ++j) {
           const int64_t is = s0 + j;
-          if (is == it) continue;                      // the target itself (its images are never close)
+          if (P.same_set && is == it) continue;        // the target itself (its images are never close)
           float r2;
           if (FFC) {
             ff dx, dy, dz;
@@ -207,7 +207,7 @@ void run_near_close(const NearParams& P, const CloseParams& C, cudaStream_t s) {
     const int cap_blocks = (P.close_cap + 127) / 128;
     k_close_queue<D, KM, GRAD><<<cap_blocks > 0 ? cap_blocks : 1, 128, 0, s>>>(P, C);
   }
-  k_near_close<D, KM, GRAD, FFC><<<(P.n_tile + kCloseWarps - 1) / kCloseWarps, 32 * kCloseWarps, 0, s>>>(P, C);
+  k_near_close<D, KM, GRAD, FFC><<<(P.n_ttile + kCloseWarps - 1) / kCloseWarps, 32 * kCloseWarps, 0, s>>>(P, C);
 }
 
 // (dim, kernels, gradient, float-float coordinates)

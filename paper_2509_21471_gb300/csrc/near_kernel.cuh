@@ -71,6 +71,19 @@ struct NearParams {
   double* u;             // [N][D][n_rhs] caller order (may be null for grad-only)
   double* gradu;         // [N][3][3] caller order
   double* acc;           // sorted FP64 accumulator [N][D] (symmetric Stokeslet pass), zeroed
+  // targets of the one-sided passes: the points themselves (same_set = 1,
+  // every ttile_* / t* array equals its source counterpart) or separate targets
+  int same_set;
+  int n_ttile;
+  int64_t NT;
+  const int32_t* ttile_leaf;
+  const int32_t* ttile_start;
+  const int32_t* ttile_count;
+  const float4* ttile_lo;
+  const float4* ttile_hi;
+  const float4* trel;    // FP32 leaf-relative target coordinates
+  const double* tw;      // FP64 in-cell target coordinates, SoA [D][NT]
+  const int32_t* tperm;  // sorted target -> caller's target index
   int* close_flag;       // per target tile, zeroed: set where a nearly coincident pair was skipped
   int* close_count;      // skipped pairs queued (zeroed; may exceed close_cap)
   int4* close_q;         // queued pairs: (target, source, near-list entry, L_B | both << 8), sorted indices
@@ -121,6 +134,7 @@ __device__ __forceinline__ double self_coeff(const NearParams& P, int LB) {
 constexpr float kClose32 = 0x1p-10f;
 constexpr float kCloseFF = 0x1p-20f;
 
+// it: sorted target index (coordinates P.tw), is: sorted source index (P.w).
 // Densities of one point: [0, 3) Stokeslet force, [3, 6) stresslet strength
 // g, [6, 9) orientation n, [9] g.n.  out (zeroed by the caller): [0, 3) target
 // side of the velocity, [3, 12) of the gradient (grad[j*3+m] = d_m u_j);
@@ -136,7 +150,7 @@ __device__ __noinline__ void close_pair_fp64(const NearParams& P, int64_t it, in
   double r2 = 0.0;
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    x[a] = __dadd_rn(__dsub_rn(P.w[a * N + it], P.w[a * N + is]), q[a]);
+    x[a] = __dadd_rn(__dsub_rn(P.tw[a * P.NT + it], P.w[a * N + is]), q[a]);
     r2 = __dadd_rn(r2, __dmul_rn(x[a], x[a]));
   }
   const double nu2inv = nuinv * nuinv;
@@ -391,17 +405,17 @@ __global__ void __launch_bounds__(32 * kMixWarps, 24 / kMixWarps) k_near_mixed(c
   __shared__ float4 s_g[(KM & 2) ? W : 1][kTile];
   __shared__ float4 s_n[(KM & 2) ? W : 1][kTile];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * W + wid;
-  if (tile >= P.n_tile) return;
+  const int tile = blockIdx.x * W + wid;               // target tile
+  if (tile >= P.n_ttile) return;
   const int64_t N = P.N;
-  const int B = P.tile_leaf[tile];
-  const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
+  const int B = P.ttile_leaf[tile];
+  const int t0 = P.ttile_start[tile], nt = P.ttile_count[tile];
   const int LB = P.leaf_level[B];
   int64_t cB[3] = {0, 0, 0};
   leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
-  const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
+  const float4 tlo = P.ttile_lo[tile], thi = P.ttile_hi[tile];
   const bool on = lane < nt;
-  const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 xt = on ? P.trel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
   // |x_t|^2; +inf for an empty lane makes every candidate test fail
   const float tt = on ? fmaf(xt.x, xt.x, fmaf(xt.y, xt.y, xt.z * xt.z)) : __int_as_float(0x7f800000);
   float* const rowx = reinterpret_cast<float*>(s_tst[wid][0]);
@@ -580,15 +594,15 @@ __global__ void __launch_bounds__(32 * kMixWarps, 24 / kMixWarps) k_near_mixed(c
           for (int j = 0; j < ns; ++j) {
             const float4 sp = s_pos[wid][j];
             const float dx = xt.x - sp.x, dy = xt.y - sp.y, dz = xt.z - sp.z;
-            any |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= thr && !(U == tile && j == lane);
+            any |= fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= thr && !(P.same_set && U == tile && j == lane);
           }
         if (__any_sync(0xffffffffu, any) && lane == 0) P.close_flag[tile] = 1;
       }
     }
   }
   if (!on) return;
-  const int64_t o = P.perm[t0 + lane];
-  const double sc = self_coeff<D>(P, LB);
+  const int64_t o = P.tperm[t0 + lane];
+  const double sc = P.same_set ? self_coeff<D>(P, LB) : 0.0;   // separate targets: no self term
   const int nr = P.n_rhs;
   if (P.u) {
 #pragma unroll
@@ -601,7 +615,7 @@ __global__ void __launch_bounds__(32 * kMixWarps, 24 / kMixWarps) k_near_mixed(c
         if (COMP) v += static_cast<double>(ul[a]);
         v *= kInv8Pi;
         const int64_t q = (o * D + a) * nr + k;
-        if (KM & 1) v += sc * P.f_orig[q];
+        if ((KM & 1) && P.same_set) v += sc * P.f_orig[q];
         P.u[q] = v;
       }
     }
@@ -844,7 +858,7 @@ struct Fp64Shape {
 
 template <int D, int KM, bool GRAD, int NT, int NR>
 __global__ void __launch_bounds__(32 * Fp64Shape<D, KM, GRAD, NT, NR>::WPB) k_near_fp64(const __grid_constant__ NearParams P) {
-  static_assert(NR == 1 || (KM == 1 && !GRAD), "several force columns: Stokeslet velocity only");
+  static_assert(NR == 1 || (KM == 1 && !GRAD), "several force columns: velocity only");
   static_assert(D == 3 || !GRAD, "the gradient kernel is 3D");
   constexpr int NB = Fp64Shape<D, KM, GRAD, NT, NR>::NB;
   constexpr int WPB = Fp64Shape<D, KM, GRAD, NT, NR>::WPB;
@@ -855,22 +869,22 @@ __global__ void __launch_bounds__(32 * Fp64Shape<D, KM, GRAD, NT, NR>::WPB) k_ne
   __shared__ double sD[WPB][NF][NS];
   __shared__ double sQ[WPB][NB][4];                  // per staged tile: q, 1/nu
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x * WPB + wid;
-  if (tile >= P.n_tile) return;
+  const int tile = blockIdx.x * WPB + wid;             // target tile
+  if (tile >= P.n_ttile) return;
   const int64_t N = P.N;
-  const int B = P.tile_leaf[tile];
-  const int t0 = P.tile_start[tile], nt = P.tile_count[tile];
+  const int B = P.ttile_leaf[tile];
+  const int t0 = P.ttile_start[tile], nt = P.ttile_count[tile];
   const int LB = P.leaf_level[B];
   int64_t cB[3] = {0, 0, 0};
   leaf_coords<D>(P.leaf_anchor[B], LB, P.M, cB);
-  const float4 tlo = P.tile_lo[tile], thi = P.tile_hi[tile];
+  const float4 tlo = P.ttile_lo[tile], thi = P.ttile_hi[tile];
   const bool on = lane < nt;
-  const float4 xt = on ? P.rel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 xt = on ? P.trel[t0 + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
   const float tt = fmaf(xt.x, xt.x, fmaf(xt.y, xt.y, xt.z * xt.z));
   double wt[3] = {0.0, 0.0, 0.0};
   if (on)
 #pragma unroll
-    for (int a = 0; a < D; ++a) wt[a] = P.w[a * N + t0 + lane];
+    for (int a = 0; a < D; ++a) wt[a] = P.tw[a * P.NT + t0 + lane];
 
   double acc[NR][3];
 #pragma unroll
@@ -1002,6 +1016,35 @@ __global__ void __launch_bounds__(32 * Fp64Shape<D, KM, GRAD, NT, NR>::WPB) k_ne
       a[0][0] += fma(Dc, fma(gx_, xn, nx * xg), Ex * dx);
       a[0][1] += fma(Dc, fma(gy_, xn, ny * xg), Ex * dy);
       if (D == 3) a[0][2] += fma(Dc, fma(gz_, xn, nz * xg), Ex * dz);
+      if (GRAD) {
+        // derivative of u_j = Dc V_j + Ec x_j (x.g)(x.n), V = g (x.n) + x (g.n) + n (x.g):
+        //   d_m u_j = D1 x_m V_j + Dc (g_j n_m + delta_jm (g.n) + n_j g_m)
+        //           + E1 x_m x_j (x.g)(x.n) + Ec (delta_jm (x.g)(x.n) + x_j (g_m (x.n) + (x.g) n_m)),
+        // D1 = Dc'/r = 2 pT'/(nu^3 r^2) - 2 pT/(nu r^4),
+        // E1 = Ec'/r = -6 (-5/r^7 + 2 qT'/(nu^3 r^4) - 4 qT/(nu r^6))   (' = d/ds, s = rho^2)
+        const double dpt = horner<NT>(P.c64[P_DPT], t);
+        const double dqt = horner<NT>(P.c64[P_DQT], t);
+        const double nu3i = nuinv * nuinv * nuinv;
+        const double ri4 = ri2 * ri2;
+        const double D1 = fma(2.0 * dpt, nu3i * ri2, -2.0 * pt * nuinv * ri4);
+        const double E1 = -6.0 * fma(-5.0 * ri4 * ri2, ri, fma(2.0 * dqt, nu3i * ri4, -4.0 * qt * nuinv * ri4 * ri2));
+        const double xv[3] = {dx, dy, dz};
+        const double gv[3] = {gx_, gy_, gz_};
+        const double nv[3] = {nx, ny, nz};
+        const double xgn = xg * xn;
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          const double Vj = fma(gv[jj], xn, fma(xv[jj], gn, nv[jj] * xg));
+          const double c1 = fma(D1, Vj, E1 * xv[jj] * xgn);
+#pragma unroll
+          for (int mm = 0; mm < 3; ++mm) {
+            double v = fma(c1, xv[mm], Dc * fma(gv[jj], nv[mm], nv[jj] * gv[mm]));
+            v = fma(Ec * xv[jj], fma(gv[mm], xn, xg * nv[mm]), v);
+            if (jj == mm) v += fma(Dc, gn, Ec * xgn);
+            gr[jj * 3 + mm] += v;
+          }
+        }
+      }
       if (SYM64 && tl >= 0) {
         // T_R is odd: the source gets -T_R(x) : (g_t n_t)
         const int kg = (KM & 1) ? D : 0;
@@ -1169,8 +1212,8 @@ __global__ void __launch_bounds__(32 * Fp64Shape<D, KM, GRAD, NT, NR>::WPB) k_ne
     for (int a = 0; a < D; ++a) atomicAdd(P.acc + (static_cast<int64_t>(t0) + lane) * D + a, acc[0][a]);
     return;
   }
-  const int64_t o = P.perm[t0 + lane];
-  const double sc = self_coeff<D>(P, LB);
+  const int64_t o = P.tperm[t0 + lane];
+  const double sc = P.same_set ? self_coeff<D>(P, LB) : 0.0;   // separate targets: no self term
   const int nr = P.n_rhs;
   if (P.u) {
 #pragma unroll
@@ -1180,7 +1223,7 @@ __global__ void __launch_bounds__(32 * Fp64Shape<D, KM, GRAD, NT, NR>::WPB) k_ne
       for (int a = 0; a < D; ++a) {
         double v = acc[c][a] * kInv8Pi;
         const int64_t q = (o * D + a) * nr + c;
-        if (KM & 1) v += sc * P.f_orig[q];
+        if ((KM & 1) && P.same_set) v += sc * P.f_orig[q];
         P.u[q] = v;
       }
     }
@@ -1202,12 +1245,12 @@ void run_near_mixed(const NearParams& P, cudaStream_t s) {
       return;
     }
   }
-  k_near_mixed<D, KM, GRAD, NT, NR><<<(P.n_tile + kMixWarps - 1) / kMixWarps, 32 * kMixWarps, 0, s>>>(P);
+  k_near_mixed<D, KM, GRAD, NT, NR><<<(P.n_ttile + kMixWarps - 1) / kMixWarps, 32 * kMixWarps, 0, s>>>(P);
 }
 template <int D, int KM, bool GRAD, int NT, int NR>
 void run_near_fp64(const NearParams& P, cudaStream_t s) {
   constexpr int WPB = Fp64Shape<D, KM, GRAD, NT, NR>::WPB;
-  k_near_fp64<D, KM, GRAD, NT, NR><<<(P.n_tile + WPB - 1) / WPB, 32 * WPB, 0, s>>>(P);
+  k_near_fp64<D, KM, GRAD, NT, NR><<<(P.n_ttile + WPB - 1) / WPB, 32 * WPB, 0, s>>>(P);
   if (NR == 1 && !GRAD && P.acc) k_near_sym_finish<D, KM><<<(P.n_tile + 7) / 8, 256, 0, s>>>(P, P.acc);
 }
 
@@ -1215,6 +1258,9 @@ void run_near_fp64(const NearParams& P, cudaStream_t s) {
 #define DMK_FOR_EACH_VARIANT_3D(M, NT) \
   M(3, 1, false, NT, 1) M(3, 2, false, NT, 1) M(3, 3, false, NT, 1) M(3, 1, true, NT, 1) \
   M(3, 1, false, NT, 4) M(3, 1, false, NT, 16)
+// FP64 only: the stresslet gradient (every precision takes FP64 pair terms for it)
+#define DMK_FOR_EACH_VARIANT_3D_FP64(M, NT) \
+  DMK_FOR_EACH_VARIANT_3D(M, NT) M(3, 2, true, NT, 1) M(3, 3, true, NT, 1)
 #define DMK_FOR_EACH_VARIANT_2D(M, NT) \
   M(2, 1, false, NT, 1) M(2, 2, false, NT, 1) M(2, 3, false, NT, 1) M(2, 1, false, NT, 4) M(2, 1, false, NT, 16)
 

@@ -83,7 +83,7 @@ extern "C" dmk_status_t dmk_stokes_eval_noalloc(dmk_stokes_plan_t plan, const do
       return dmk::record_error(plan, DMK_ERR_INVALID_ARG, "d_g / d_n NULL but the stresslet is requested");
     if (!d_u) return dmk::record_error(plan, DMK_ERR_INVALID_ARG, "d_u is NULL");
   }
-  const size_t ws = (dmk::eval_workspace_bytes(p.opts, N) + 255) & ~size_t(255);
+  const size_t ws = (p.fsorted_bytes + 255) & ~size_t(255);
   const size_t red = 4 * sizeof(double) * static_cast<size_t>(p.tree.n_sys);
   if (ws + red > dmk::kNoAllocScratchBytes)
     return dmk::record_error(plan, DMK_ERR_INVALID_ARG,

@@ -421,11 +421,11 @@ int build_tables(int dim, double c, double fp32_tol, KernelTables* out) {
   fit(fh, fp32_tol, &out->n64[P_HS], out->p64[P_HS], &out->n32[P_HS], out->p32[P_HS]);
   fit(fp, fp32_tol, &out->n64[P_PT], out->p64[P_PT], &out->n32[P_PT], out->p32[P_PT]);
   fit(fq, fp32_tol, &out->n64[P_QT], out->p64[P_QT], &out->n32[P_QT], out->p32[P_QT]);
-  for (int id : {P_GS, P_HS}) {
+  for (int id : {P_GS, P_HS, P_PT, P_QT}) {
     int dn;
     double dp[kMaxTerms];
     deriv_s(out->p64[id], out->n64[id], dp, &dn);
-    int did = (id == P_GS) ? P_DGS : P_DHS;
+    int did = (id == P_GS) ? P_DGS : (id == P_HS) ? P_DHS : (id == P_PT) ? P_DPT : P_DQT;
     out->n64[did] = dn;
     for (int j = 0; j < dn; ++j) out->p64[did][j] = dp[j];
     deriv_s(out->p64[id], out->n32[id] < out->n64[id] ? std::min(out->n64[id], out->n32[id] + 1)

@@ -10,7 +10,7 @@
 //
 //   3D  gS(s) = (Sdiag(rho) - 1)/rho,  hS(s) = (Soffd(rho) - 1)/rho
 //       pT(s) =  Tdiag(rho)/rho,       qT(s) = (Toffd(rho) - 1)/rho
-//       dgS, dhS = d/ds of gS, hS                      (gradient kernel)
+//       dgS, dhS, dpT, dqT = d/ds of gS, hS, pT, qT      (gradient kernels)
 //   so that, with nu the residual scale, r < nu:
 //       S_R = (1/r + gS/nu) delta/(8 pi) + (1/r^3 + hS/(nu r^2)) x x/(8 pi)
 //       T_R = pT/(8 pi nu r^2) (delta x + ...) - (3/4pi)(1/r^5 + qT/(nu r^4)) x x x
@@ -23,7 +23,7 @@ namespace dmk {
 
 constexpr int kMaxTerms = 48;
 
-enum PolyId { P_GS = 0, P_HS = 1, P_PT = 2, P_QT = 3, P_DGS = 4, P_DHS = 5, P_COUNT = 6 };
+enum PolyId { P_GS = 0, P_HS = 1, P_PT = 2, P_QT = 3, P_DGS = 4, P_DHS = 5, P_DPT = 6, P_DQT = 7, P_COUNT = 8 };
 
 struct KernelTables {
   int dim = 3;

@@ -900,7 +900,104 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   T.n_tile = h_pin[5];
 }
 
+// ------------------------------------------------------ separate targets
+// The sums of Sec. 1 are stated for target points that need not be sources.
+// The tree is built from the sources (Step 1(a) counts sources); the targets
+// are sorted by the Morton key of their finest cell and each goes to the leaf
+// containing it: the leaves partition the box (empty leaves included) and are
+// sorted by anchor, so leaf i holds the targets with keys in
+// [anchor_i, anchor_{i+1}).  Per leaf they form tiles of <= 32 as the sources do.
+__global__ void k_leaf_trange(int n_leaf, const uint64_t* __restrict__ anchor, int64_t NT,
+                              const uint64_t* __restrict__ tkeys, int32_t* __restrict__ tstart) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n_leaf) return;
+  if (i == n_leaf) {
+    tstart[n_leaf] = static_cast<int32_t>(NT);
+    return;
+  }
+  int64_t lo = 0, hi = NT;                            // first target key >= anchor_i
+  const uint64_t a = anchor[i];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (tkeys[mid] < a) lo = mid + 1;
+    else hi = mid;
+  }
+  tstart[i] = static_cast<int32_t>(lo);
+}
+
+__global__ void k_range_count(int n, const int32_t* __restrict__ start, int32_t* __restrict__ count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) count[i] = start[i + 1] - start[i];
+}
+
+template <int D>
+void build_targets_t(Plan& p, const double* d_trg, int64_t NT) {
+  DeviceTree& T = p.tree;
+  cudaStream_t s = p.stream;
+  const int M = T.M;
+  const int B = 256;
+  const int n_leaf = T.n_leaf;
+  const double lo0 = p.opts.box_lo[0], lo1 = p.opts.box_lo[1], lo2 = D == 3 ? p.opts.box_lo[2] : 0.0;
+  Arena& A = p.arena;
+  Arena scratch;
+  scratch.s = s;
+  T.sep = 1;
+  T.NT = NT;
+  T.tperm = A.alloc<int32_t>(NT);
+  T.tw = A.alloc<double>(NT * D);
+  T.trel = A.alloc<float4>(NT);
+  T.leaf_tstart = A.alloc<int32_t>(n_leaf + 1);
+  uint64_t* key_in = scratch.alloc<uint64_t>(NT);
+  uint64_t* tkeys = scratch.alloc<uint64_t>(NT);
+  int32_t* idx_in = scratch.alloc<int32_t>(NT);
+  if (NT > 0) {
+    k_keys<D><<<grid_for(NT, B), B, 0, s>>>(NT, d_trg, lo0, lo1, lo2, T.periodic, M, key_in, idx_in, p.status);
+    ++p.launches;
+    DMK_CUDA_TRY(cudaGetLastError());
+    size_t bytes = 0;
+    DMK_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, bytes, key_in, tkeys, idx_in, T.tperm,
+                                                 static_cast<int>(NT), 0, D * M, s));
+    DMK_CUDA_TRY(cub::DeviceRadixSort::SortPairs(scratch.alloc_bytes(bytes), bytes, key_in, tkeys, idx_in,
+                                                 T.tperm, static_cast<int>(NT), 0, D * M, s));
+    k_gather_w<D><<<grid_for(NT, B), B, 0, s>>>(NT, d_trg, T.tperm, lo0, lo1, lo2, T.periodic, T.tw);
+    ++p.launches;
+  }
+  int32_t* tcount = scratch.alloc<int32_t>(n_leaf);
+  k_leaf_trange<<<grid_for(n_leaf + 1, B), B, 0, s>>>(n_leaf, T.leaf_anchor, NT, tkeys, T.leaf_tstart);
+  k_range_count<<<grid_for(n_leaf, B), B, 0, s>>>(n_leaf, T.leaf_tstart, tcount);
+  p.launches += 2;
+  int32_t* nttile = scratch.alloc<int32_t>(n_leaf);
+  int32_t* ttile0 = scratch.alloc<int32_t>(n_leaf + 1);
+  int32_t* d_ntt = scratch.alloc<int32_t>(1);
+  k_tile_count<<<grid_for(n_leaf, B), B, 0, s>>>(n_leaf, tcount, nttile);
+  ++p.launches;
+  scan_counts(nttile, ttile0, n_leaf, s, scratch, d_ntt, p.launches);
+  const int64_t cap = NT / kTile + n_leaf;
+  T.ttile_leaf = A.alloc<int32_t>(cap);
+  T.ttile_start = A.alloc<int32_t>(cap);
+  T.ttile_count = A.alloc<int32_t>(cap);
+  T.ttile_lo = A.alloc<float4>(cap);
+  T.ttile_hi = A.alloc<float4>(cap);
+  k_tile_fill<<<grid_for(n_leaf, B), B, 0, s>>>(n_leaf, T.leaf_tstart, tcount, ttile0, T.ttile_leaf, T.ttile_start,
+                                                T.ttile_count);
+  k_rel_bbox<D><<<grid_for(cap * 32, 256), 256, 0, s>>>(d_ntt, NT, T.ttile_leaf, T.ttile_start, T.ttile_count,
+                                                        T.leaf_anchor, T.leaf_level, T.tw, M, T.trel, T.ttile_lo,
+                                                        T.ttile_hi);
+  p.launches += 2;
+  DMK_CUDA_TRY(cudaGetLastError());
+  int32_t* h_pin = pinned_slot();
+  struct PinGuard { int32_t* q; ~PinGuard() { pinned_release(q); } } pin_guard{h_pin};
+  DMK_CUDA_TRY(cudaMemcpyAsync(h_pin, d_ntt, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  DMK_CUDA_TRY(cudaStreamSynchronize(s));
+  T.n_ttile = h_pin[0];
+}
+
 }  // namespace
+
+void build_targets(Plan& p, const double* d_trg, int64_t n_trg) {
+  if (p.opts.dim == 3) build_targets_t<3>(p, d_trg, n_trg);
+  else build_targets_t<2>(p, d_trg, n_trg);
+}
 
 void build_tree(Plan& p, const double* d_src, const int64_t* h_offsets) {
   if (p.opts.dim == 3) build_tree_t<3>(p, d_src, h_offsets);

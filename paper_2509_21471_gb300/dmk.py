@@ -114,7 +114,7 @@ class Plan:
     """dmk_stokes_plan / dmk_stokes_plan_batched on CUDA tensors."""
 
     def __init__(self, x, eps=1e-6, dim=None, periodic=False, kernels=STOKESLET, precision=MIXED,
-                 leaf_capacity=0, n_rhs=1, box_lo=None, offsets=None, stream=None, device=None):
+                 leaf_capacity=0, n_rhs=1, box_lo=None, offsets=None, stream=None, device=None, targets=None):
         device = device or (x.device if isinstance(x, torch.Tensor) and x.is_cuda else torch.device("cuda"))
         dim = dim or (x.shape[1])
         self.dim = dim
@@ -123,13 +123,15 @@ class Plan:
         self.device = device
         self._x = _as_dev(x, dim, "x", device)
         self.n = self._x.shape[0]
+        self._t = None if targets is None else _as_dev(targets, dim, "targets", device)
+        self.nt = self.n if targets is None else self._t.shape[0]     # rows of every output
         self.opts = make_opts(dim, periodic, kernels, precision, NEAR, leaf_capacity, n_rhs, eps, box_lo)
         self._h = ctypes.c_void_p()
         with torch.cuda.device(device):
             sp = _stream_ptr(stream)
             if offsets is None:
-                code = _lib.dmk_stokes_plan(ctypes.byref(self.opts), self.n, _ptr(self._x), self.n, None, sp,
-                                            ctypes.byref(self._h))
+                code = _lib.dmk_stokes_plan(ctypes.byref(self.opts), self.n, _ptr(self._x), self.nt, _ptr(self._t),
+                                            sp, ctypes.byref(self._h))
             else:
                 offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
                 self._offs = offs
@@ -140,7 +142,7 @@ class Plan:
 
     # ------------------------------------------------------------------
     def _out_shape(self):
-        return (self.n, self.dim) if self.n_rhs == 1 else (self.n, self.dim, self.n_rhs)
+        return (self.nt, self.dim) if self.n_rhs == 1 else (self.nt, self.dim, self.n_rhs)
 
     def eval(self, f=None, g=None, n=None, out=None, stream=None):
         """dmk_stokes_eval: near component u [n, dim] or [n, dim, n_rhs] (float64, caller order)."""
@@ -165,12 +167,15 @@ class Plan:
         _check(code, self._h)
         return out
 
-    def eval_grad(self, f, want_u=False, stream=None):
-        """dmk_stokes_eval_grad: gradu [n, dim, dim] (and u if want_u)."""
-        f = _as_dev(f, self.dim, "f", self.device)
-        gu = torch.empty((self.n, self.dim, self.dim), dtype=torch.float64, device=self.device)
-        u = torch.empty((self.n, self.dim), dtype=torch.float64, device=self.device) if want_u else None
-        code = _lib.dmk_stokes_eval_grad(self._h, _ptr(f), None, None, _ptr(u), _ptr(gu), _stream_ptr(stream))
+    def eval_grad(self, f=None, g=None, n=None, want_u=False, stream=None):
+        """dmk_stokes_eval_grad: gradu [n, dim, dim] (and u if want_u); forces f
+        (Stokeslet) and / or stresslet strengths g with orientations n."""
+        f = None if f is None else _as_dev(f, self.dim, "f", self.device)
+        g = None if g is None else _as_dev(g, self.dim, "g", self.device)
+        n = None if n is None else _as_dev(n, self.dim, "n", self.device)
+        gu = torch.empty((self.nt, self.dim, self.dim), dtype=torch.float64, device=self.device)
+        u = torch.empty((self.nt, self.dim), dtype=torch.float64, device=self.device) if want_u else None
+        code = _lib.dmk_stokes_eval_grad(self._h, _ptr(f), _ptr(g), _ptr(n), _ptr(u), _ptr(gu), _stream_ptr(stream))
         _check(code, self._h)
         return (u, gu) if want_u else gu
 

@@ -42,7 +42,10 @@ def test_invalid_arguments_rejected_without_gpu(dmk_lib):
     assert lib.dmk_stokes_plan(ctypes.byref(o), 0, None, 0, None, None, ctypes.byref(h)) == 3
     o = dmk_lib.make_opts()
     assert lib.dmk_stokes_plan(ctypes.byref(o), 10, None, 10, None, None, ctypes.byref(h)) == 1
-    assert lib.dmk_stokes_plan(ctypes.byref(o), 10, None, 5, None, None, ctypes.byref(h)) == 3
+    # targets are the sources (d_trg NULL) but n_trg != n_src
+    assert lib.dmk_stokes_plan(ctypes.byref(o), 10, None, 5, None, None, ctypes.byref(h)) == 1
+    # separate targets need a single system; a negative target count is rejected
+    assert lib.dmk_stokes_plan(ctypes.byref(o), 0, None, -1, ctypes.c_void_p(8), None, ctypes.byref(h)) == 1
     assert lib.dmk_stokes_eval(None, None, None, None, None, None) == 7
     assert lib.dmk_stokes_sync_status(None) == 7
     lib.dmk_stokes_destroy(None)

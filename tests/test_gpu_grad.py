@@ -182,3 +182,34 @@ def test_differentiation_workload_fd(dmk):
     assert len(an) >= 450
     an, fdv = np.array(an), np.array(fdv)
     assert np.linalg.norm(an - fdv) / np.linalg.norm(an) < 1e-5
+
+
+@pytest.mark.parametrize("kernels,periodic", [(3, False), (2, True), (2, False)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_stresslet_gradient_matches_oracle(dmk, kernels, periodic, precision):
+    """Gradient of the stresslet (and Stokeslet) near component against the
+    oracle's derivative of Eq. (res_stresslet) (itself pinned by finite
+    differences); periodic: plus the k = 0 term's -delta_jm sum g.n.  FP64
+    pair terms in both precisions."""
+    rng = np.random.default_rng(701 + kernels + 10 * periodic)
+    N, ns, eps = 2000, 40, 1e-8
+    x = wl.gaussian_mixture_points(rng, N, 3, 6, 0.05)
+    f = wl.forces(rng, N, 3)
+    g = wl.stresslet_strengths(rng, N, 3)
+    n = wl.unit_normals(rng, N, 3)
+    tr = Tree(x, ns, periodic=periodic)
+    st, sl = bool(kernels & 1), bool(kernels & 2)
+    kern = dict(win=ProlateWindow(bandlimit_c(eps, stokeslet=st, stresslet=sl)), stokeslet=st, stresslet=sl)
+    u_ref, G_ref = onear.near_lists(tr, kern, f=f if st else None, g=g, n=n, want_grad=True)
+    if periodic:
+        from oracle import direct as odirect
+        u_ref = u_ref + odirect.stresslet_zero_mode(tr.w, g, n)
+        G_ref = G_ref - np.sum(g * n) * np.eye(3)[None, :, :]
+    p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=eps, periodic=periodic, kernels=kernels,
+                 precision=precision, leaf_capacity=ns)
+    dev = lambda a: torch.as_tensor(a, device="cuda")
+    u, G = p.eval_grad(dev(f) if st else None, dev(g), dev(n), want_u=True)
+    p.sync_status()
+    p.close()
+    assert rel_l2(u.cpu().numpy(), u_ref) < 1e-12
+    assert rel_l2(G.cpu().numpy(), G_ref) < 1e-12

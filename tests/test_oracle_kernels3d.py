@@ -142,3 +142,30 @@ def test_gradient_matches_finite_differences(w):
             e[m] = h
             fd[:, :, m] = (k3.stokeslet_res(w, x + e, nu) - k3.stokeslet_res(w, x - e, nu)) / (2 * h)
         assert np.max(np.abs(G - fd)) < 1e-6 * np.max(np.abs(G))
+
+
+@pytest.mark.parametrize("w", WINS[:2] + [GaussianWindow(0.2)])
+def test_stresslet_gradient_matches_finite_differences(w):
+    """d_k T_R,jlm against central differences of T_R (pins the second
+    derivative of the window, phi'', and every term of the product rule)."""
+    nu = 0.25
+    rng = np.random.default_rng(6)
+    h = 1e-6
+    for _ in range(6):
+        x = rng.standard_normal(3)
+        x *= rng.uniform(0.05, 0.95) * nu / np.linalg.norm(x)
+        G = k3.stresslet_res_grad(w, x, nu)
+        fd = np.zeros((3, 3, 3, 3))
+        for k in range(3):
+            e = np.zeros(3)
+            e[k] = h
+            fd[..., k] = (k3.stresslet_res(w, x + e, nu, cut=False) - k3.stresslet_res(w, x - e, nu, cut=False)) / (2 * h)
+        assert np.max(np.abs(G - fd)) < 1e-6 * np.max(np.abs(G))
+
+
+@pytest.mark.parametrize("w", WINS[:2])
+def test_window_second_derivative_matches_finite_differences(w):
+    r = np.linspace(0.02, 0.98, 25)
+    h = 1e-5
+    fd = (w.dphi(r + h) - w.dphi(r - h)) / (2 * h)
+    assert np.max(np.abs(w.d2phi(r) - fd)) < 1e-7 * np.max(np.abs(fd))

@@ -101,3 +101,39 @@ def test_pair_counts_consistent():
     d = tr.w[:, None, :] - tr.w[None, :, :]
     r2 = near._r2(d)
     assert useful == int(np.count_nonzero((r2 < nu * nu) & (r2 > 0)))
+
+
+@pytest.mark.parametrize("per", [False, True])
+def test_separate_targets_lists_equal_brute_force(per):
+    """Targets that are not sources (Sec. 1): the leaf-list traversal from
+    each target's containing leaf equals brute force over all sources and
+    images; targets in empty leaves and on other leaf levels included."""
+    rng = np.random.default_rng(31 + per)
+    xs = wl.gaussian_mixture_points(rng, 350, 3, 3, 0.04)
+    xt = np.concatenate([wl.uniform_points(rng, 120, 3), wl.gaussian_mixture_points(rng, 80, 3, 3, 0.04)])
+    f = wl.forces(rng, 350, 3)
+    g = wl.stresslet_strengths(rng, 350, 3)
+    n = wl.unit_normals(rng, 350, 3)
+    tr = Tree(xs, 10, periodic=per)
+    kern = dict(win=WIN6, stokeslet=True, stresslet=True)
+    a = near.near_targets(tr, kern, xt, f=f, g=g, n=n)
+    b = near.near_targets_brute(tr, kern, xt, f=f, g=g, n=n)
+    assert rel(a, b) < 1e-14
+    _, leaf = tr.locate(xt)
+    assert np.any(tr.leaf_count[leaf] == 0)          # some targets sit in empty leaves
+
+
+def test_separate_targets_at_the_sources_drop_only_the_self_term():
+    """Targets placed exactly at the sources see every pair but the r = 0 one,
+    so the result is the near component minus the self term -phi(0)/(2 pi nu_t) f_t."""
+    rng = np.random.default_rng(33)
+    xs = wl.uniform_points(rng, 300, 3)
+    f = wl.forces(rng, 300, 3)
+    tr = Tree(xs, 16)
+    kern = dict(win=WIN6, stokeslet=True)
+    u = near.near_lists(tr, kern, f=f)
+    ut = near.near_targets(tr, kern, xs, f=f)
+    nu_t = np.ldexp(1.0, -(tr.point_level + 1))
+    self_term = (-float(WIN6.phi(0.0)) / (2 * np.pi * nu_t))[:, None] * f
+    assert rel(ut, u - self_term) < 1e-14
+    assert rel(ut, u) > 1e-3
