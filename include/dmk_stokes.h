@@ -259,6 +259,29 @@ dmk_status_t dmk_stokes_kernel_table(int32_t dim, double eps, int32_t kernels, i
                                      int32_t fp32, double* out_c, double* out_phi0,
                                      double* coef, int32_t max_terms, int32_t* n_terms);
 
+/* Sharding one system over n_ranks GPUs (host-only, no GPU needed; no paper
+ * counterpart: the paper's code is single-threaded, Sec. 8).  The near pass
+ * needs, for a target leaf, only the sources of its near list (FMM list 1,
+ * remark after Step 4 of Sec. 6.1).  Leaves are in Morton order, so contiguous
+ * leaf ranges are compact; dmk_stokes_partition_leaves splits [0, n_leaf) into
+ * n_ranks contiguous ranges [leaf_begin[r], leaf_begin[r+1]) of about equal
+ * issued pairs, cost(leaf) = targets(leaf) x sum_{X in near(leaf)} sources(X).
+ *   leaf_count[n_leaf]   sources per leaf; leaf_tcount[n_leaf] targets per
+ *                        leaf (NULL: the sources are the targets)
+ *   near_off[n_leaf+1], near_leaf[E]   the near lists (dmk_stokes_plan_tree)
+ *   leaf_begin[n_ranks+1] (out), rank_cost[n_ranks] (out, may be NULL)
+ * dmk_stokes_halo_leaves lists, sorted and unique, the leaves outside
+ * [begin, end) that appear in the near lists of the leaves inside: the
+ * sources whose densities a rank owning [begin, end) receives before its pass.
+ *   halo[max_halo] (out, may be NULL to query *n_halo), *n_halo (out).
+ * Both return DMK_ERR_INVALID_ARG for bad sizes or NULL required pointers. */
+dmk_status_t dmk_stokes_partition_leaves(int32_t n_leaf, const int32_t* leaf_count, const int32_t* leaf_tcount,
+                                         const int32_t* near_off, const int32_t* near_leaf, int32_t n_ranks,
+                                         int32_t* leaf_begin, int64_t* rank_cost);
+dmk_status_t dmk_stokes_halo_leaves(int32_t n_leaf, const int32_t* near_off, const int32_t* near_leaf,
+                                    int32_t begin, int32_t end, int32_t* halo, int32_t max_halo,
+                                    int32_t* n_halo);
+
 /* Releases the plan (device memory is freed on the plan's stream). NULL is ignored. */
 void dmk_stokes_destroy(dmk_stokes_plan_t plan);
 

@@ -52,6 +52,9 @@ _lib.dmk_stokes_plan_stats.argtypes = [_P, _P]
 _lib.dmk_stokes_plan_tree.argtypes = [_P] + [_P] * 8
 _lib.dmk_stokes_kernel_table.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, _P, _P, _P, ctypes.c_int32, _P]
+_lib.dmk_stokes_partition_leaves.argtypes = [ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, _P]
+_lib.dmk_stokes_halo_leaves.argtypes = [ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
+                                        _P]
 _lib.dmk_stokes_destroy.argtypes = [_P]
 _lib.dmk_stokes_destroy.restype = None
 _lib.dmk_stokes_last_error.argtypes = [_P]
@@ -59,13 +62,13 @@ _lib.dmk_stokes_last_error.restype = ctypes.c_char_p
 for _name in ("dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
               "dmk_stokes_eval_grad", "dmk_stokes_eval_adjoint",
               "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree",
-              "dmk_stokes_kernel_table"):
+              "dmk_stokes_kernel_table", "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 EXPORTED = ["dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
             "dmk_stokes_eval_grad", "dmk_stokes_eval_adjoint",
             "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree", "dmk_stokes_kernel_table",
-            "dmk_stokes_destroy", "dmk_stokes_last_error"]
+            "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves", "dmk_stokes_destroy", "dmk_stokes_last_error"]
 
 
 def _check(code, handle=None):
@@ -233,6 +236,32 @@ def kernel_table(dim, eps, which, fp32=False, kernels=STOKESLET):
     _check(_lib.dmk_stokes_kernel_table(dim, eps, kernels, which, int(fp32), ctypes.byref(c), ctypes.byref(phi0),
                                         buf.ctypes.data_as(ctypes.c_void_p), 64, ctypes.byref(nt)))
     return c.value, phi0.value, buf[: nt.value].copy()
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def partition_leaves(leaf_count, near_off, near_leaf, n_ranks, leaf_tcount=None):
+    """dmk_stokes_partition_leaves (host only): (leaf_begin [n_ranks + 1], cost per rank)."""
+    lc, no, nl = _i32(leaf_count), _i32(near_off), _i32(near_leaf)
+    tc = None if leaf_tcount is None else _i32(leaf_tcount)
+    begin = np.zeros(n_ranks + 1, np.int32)
+    cost = np.zeros(n_ranks, np.int64)
+    p = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    _check(_lib.dmk_stokes_partition_leaves(len(lc), p(lc), p(tc), p(no), p(nl), n_ranks, p(begin), p(cost)))
+    return begin, cost
+
+
+def halo_leaves(near_off, near_leaf, begin, end):
+    """dmk_stokes_halo_leaves (host only): the near-list leaves outside [begin, end)."""
+    no, nl = _i32(near_off), _i32(near_leaf)
+    n = ctypes.c_int32()
+    args = (len(no) - 1, no.ctypes.data_as(ctypes.c_void_p), nl.ctypes.data_as(ctypes.c_void_p), int(begin), int(end))
+    _check(_lib.dmk_stokes_halo_leaves(*args, None, 0, ctypes.byref(n)))
+    halo = np.zeros(max(n.value, 1), np.int32)
+    _check(_lib.dmk_stokes_halo_leaves(*args, halo.ctypes.data_as(ctypes.c_void_p), len(halo), ctypes.byref(n)))
+    return halo[: n.value]
 
 
 def eval(x, f=None, g=None, n=None, **plan_kwargs):
