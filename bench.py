@@ -167,6 +167,43 @@ def oracle_sample(n_sample, eps, ns, seed_extra=0):
     return time.perf_counter() - t0
 
 
+def _oracle_chunk(n_sample, eps, ns, seed_extra, part, parts):
+    """One worker's share of the oracle sample: the tree (every worker builds
+    it) and the near pass over its slice of the targets."""
+    import numpy as np
+    from paper_2509_21471_gb300 import workloads as wl
+    from oracle import near as onear
+    from oracle.tree import Tree
+    from oracle.window import ProlateWindow
+    from oracle.params import bandlimit_c
+    rng = wl.rng_for(1, extra=10 + seed_extra)
+    x = wl.gaussian_mixture_points(rng, n_sample, 3, 8, 0.02)
+    f = wl.forces(rng, n_sample, 3)
+    t0 = time.perf_counter()
+    tr = Tree(x, ns)
+    onear.near_lists(tr, dict(win=ProlateWindow(bandlimit_c(eps)), stokeslet=True), f=f,
+                     targets=np.array_split(np.arange(n_sample), parts)[part])
+    return time.perf_counter() - t0
+
+
+def oracle_timings(n_sample, eps, ns, repeats=3):
+    """The oracle on the host cores: one thread (median of `repeats` runs of the
+    whole sample) and all cores (a spawned process per core, each building the
+    tree and summing its share of the targets; wall time, median of `repeats`)."""
+    import multiprocessing as mp
+    import statistics
+    procs = os.cpu_count() or 1
+    one = statistics.median(oracle_sample(n_sample, eps, ns, k) for k in range(repeats))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.starmap(_oracle_chunk, [(200, eps, ns, 0, i, procs) for i in range(procs)])   # warm the workers
+        walls = []
+        for k in range(repeats):
+            t0 = time.perf_counter()
+            pool.starmap(_oracle_chunk, [(n_sample, eps, ns, k, i, procs) for i in range(procs)])
+            walls.append(time.perf_counter() - t0)
+    return one, statistics.median(walls), procs
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -282,6 +319,42 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
                step="plan + forward + backward (grad w.r.t. x and f)",
                speedup_mixed_over_fp64=out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"])
     res["gradient_periodic_3d_eps1e-8"] = out
+
+    # linear scaling (Sec. 8): sources and as many separate targets on a
+    # perturbed sphere (3D) or circle (2D), N_S = N_T, eps = 1e-6, the paper's
+    # leaf capacity; a step = plan (sources and targets) + eval + destroy, MIXED
+    sweep = []
+    for dim, kern, sizes in ((3, dmk.STOKESLET, (100_000, 250_000, 500_000, 1_000_000, 2_000_000, 4_000_000)),
+                             (3, dmk.STRESSLET, (1_000_000,)), (2, dmk.STOKESLET, (1_000_000, 4_000_000))):
+        for n in sizes:
+            xs, xt, f, g, nrm = wl.linear_scaling(n, dim=dim, seed_index=pdist.seed_index(5, rank))
+            xsd, xtd = torch.as_tensor(xs, device="cuda"), torch.as_tensor(xt, device="cuda")
+            fd = torch.as_tensor(f, device="cuda") if kern == dmk.STOKESLET else None
+            gd = torch.as_tensor(g, device="cuda") if kern == dmk.STRESSLET else None
+            nd = torch.as_tensor(nrm, device="cuda") if kern == dmk.STRESSLET else None
+            ud = torch.empty((n, dim), dtype=torch.float64, device="cuda")
+            levels = [0]
+
+            def step():
+                p = dmk.Plan(xsd, targets=xtd, eps=1e-6, kernels=kern, precision=dmk.MIXED)
+                p.eval(fd, gd, nd, out=ud)
+                p.close()
+            step()
+            torch.cuda.synchronize()
+            t = max_over_ranks(sum(timed(step, 2)) / 2 / 1e3)
+            p = dmk.Plan(xsd, targets=xtd, eps=1e-6, kernels=kern, precision=dmk.MIXED)
+            p.eval(fd, gd, nd, out=ud)
+            st = p.stats()
+            t_near = max_over_ranks(sum(timed(lambda: p.eval(fd, gd, nd, out=ud), 2)) / 2 / 1e3)
+            p.close()
+            sweep.append({"dim": dim, "kernel": "stokeslet" if kern == dmk.STOKESLET else "stresslet",
+                          "n_sources": n, "n_targets": n, "ms_per_step": 1e3 * t, "near_ms": 1e3 * t_near,
+                          "targets_per_s": n / t, "max_level": st["max_level"], "leaves": st["leaves"],
+                          "useful_pairs": st["useful_pairs"]})
+            del xsd, xtd, fd, gd, nd, ud
+    res["linear_scaling_perturbed_surface_eps1e-6"] = {
+        "workload": "perturbed sphere (3D) / circle (2D), separate targets, N_S = N_T", "precision": "mixed",
+        "points": sweep}
     return res
 
 
@@ -441,10 +514,13 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t = oracle_sample(args.cpu_sample, args.eps, ns_used)
-        cpu = {"value": args.cpu_sample / t, "unit": "targets/s", "cores": 1, "kind": "oracle",
-               "sample": f"same 8-Gaussian recipe at N={args.cpu_sample} points (oracle tree + near pass, "
-                         f"numpy, 1 thread), {t:.1f} s"}
+        t1, tn, procs = oracle_timings(args.cpu_sample, args.eps, ns_used)
+        cpu = {"value": args.cpu_sample / tn, "unit": "targets/s", "cores": procs, "kind": "oracle",
+               "sample": f"same 8-Gaussian recipe at N={args.cpu_sample} points (oracle tree + near pass, numpy), "
+                         f"one spawned process per core each building the tree and summing its share of the "
+                         f"targets, wall time median of 3: {tn:.2f} s",
+               "one_thread": {"value": args.cpu_sample / t1, "unit": "targets/s", "cores": 1,
+                              "seconds_median_of_3": t1}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,

@@ -98,3 +98,38 @@ def periodic_3d(n=200_000, seed_index=4):
     x = uniform_points(rng, n, 3)
     f = forces(rng, n, 3, zero_mean=True)
     return x, f
+
+
+def perturbed_sphere_points(rng, n, radius=0.35, amp=0.15):
+    """n points on the surface rho(theta, phi) = radius (1 + amp sin(3 theta) cos(4 phi))
+    centred in the box, (cos theta, phi) uniform: the "perturbed sphere" point
+    sets of the linear-scaling experiments (Sec. 8; the perturbation is not
+    specified there, this one stays inside [-0.4025, 0.4025]^3)."""
+    ct = rng.uniform(-1.0, 1.0, n)
+    ph = rng.uniform(0.0, 2.0 * np.pi, n)
+    th = np.arccos(ct)
+    rr = radius * (1.0 + amp * np.sin(3.0 * th) * np.cos(4.0 * ph))
+    st = np.sqrt(1.0 - ct * ct)
+    return np.stack([rr * st * np.cos(ph), rr * st * np.sin(ph), rr * ct], axis=1)
+
+
+def perturbed_circle_points(rng, n, radius=0.35, amp=0.15):
+    """n points on the curve rho(theta) = radius (1 + amp cos(5 theta)), theta
+    uniform: the "perturbed circle" of the 2D linear-scaling experiments (Sec. 8)."""
+    th = rng.uniform(0.0, 2.0 * np.pi, n)
+    rr = radius * (1.0 + amp * np.cos(5.0 * th))
+    return np.stack([rr * np.cos(th), rr * np.sin(th)], axis=1)
+
+
+def linear_scaling(n, dim=3, seed_index=5):
+    """Sources and as many separate targets on the perturbed sphere (3D) or
+    circle (2D), forces N(0,1), stresslet strengths N(0,1) and unit normals
+    (N_S = N_T = n, Sec. 8)."""
+    rng = rng_for(seed_index, extra=int(n % 997))
+    pts = perturbed_sphere_points if dim == 3 else perturbed_circle_points
+    xs = pts(rng, n)
+    xt = pts(rng, n)
+    f = forces(rng, n, dim)
+    g = stresslet_strengths(rng, n, dim)
+    nrm = unit_normals(rng, n, dim)
+    return xs, xt, f, g, nrm

@@ -147,3 +147,24 @@ def test_separate_targets_empty_sets(dmk, n_src, n_trg):
         assert u.shape == (n_trg, 3)
         assert torch.all(u == 0).item()
         p.close()
+
+
+@pytest.mark.parametrize("dim,kernels,eps", [(3, 1, 1e-6), (3, 2, 1e-6), (2, 3, 1e-6), (3, 1, 1e-9)])
+def test_linear_scaling_workload_parity(dmk, dim, kernels, eps):
+    """The perturbed sphere / circle workload (N_S = N_T, Sec. 8) at a size the
+    oracle finishes in seconds, with the paper's leaf capacity for eps."""
+    xs, xt, f, g, nrm = wl.linear_scaling(4000, dim=dim)
+    ns = 1200 if dim == 3 else 240
+    tr = Tree(xs, ns if dim == 3 else 60)
+    kern = _kern(dim, kernels, eps)
+    u_ref = onear.near_targets(tr, kern, xt, f=f if kernels & 1 else None, g=g if kernels & 2 else None,
+                               n=nrm if kernels & 2 else None)
+    dev = lambda a: torch.as_tensor(a, device="cuda")
+    for prec in (dmk.FP64, dmk.MIXED):
+        p = dmk.Plan(dev(xs), targets=dev(xt), eps=eps, kernels=kernels, precision=prec,
+                     leaf_capacity=ns if dim == 3 else 60)
+        u = p.eval(dev(f) if kernels & 1 else None, dev(g) if kernels & 2 else None,
+                   dev(nrm) if kernels & 2 else None).cpu().numpy()
+        p.sync_status()
+        p.close()
+        assert rel_l2(u, u_ref) < (1e-12 if prec == dmk.FP64 else 10 * eps)
