@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdmk_stokes.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["tables.cpp", "partition.cpp", "tree.cu", "near.cu", "near_mixed.cu", "near_mixed2d.cu", "near_fp64.cu",
-           "near_fp64_2d.cu", "near_ff.cu", "near_adj.cu", "near_close.cu", "api.cu", "noalloc.cu"]
+           "near_fp64_2d.cu", "near_ff.cu", "near_adj.cu", "near_close.cu", "ewald.cu", "api.cu", "noalloc.cu"]
 
 
 def _nvcc():
@@ -55,7 +55,10 @@ def build(verbose=False, extra_flags=()):
             if err.strip():
                 print(err)
     tmp = LIB + ".tmp"
-    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
+    # cuFFT (the Ewald far field's plain transforms), found at run time in the toolkit
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(_nvcc())), "lib64")
+    cmd = [_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static", "-L" + cuda_lib, "-lcufft",
+                                                               "-Xlinker", "-rpath=" + cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -228,9 +228,13 @@ struct Arena {
 int32_t* pinned_slot();
 void pinned_release(int32_t* slot);
 
+struct EwaldState;
+
 struct Plan {
   dmk_stokes_opts_t opts{};
   int leaf_capacity = 0;
+  int uniform_level = 0;       // > 0: every leaf at this level (single-level Ewald split)
+  EwaldState* ewald = nullptr; // far field of components = ALL (periodic 3D Stokeslet)
   cudaStream_t stream = nullptr;
   int device = 0;
   KernelTables tables;
@@ -272,6 +276,13 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
 size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N, int64_t NT);
 size_t aux_bytes_grad(const dmk_stokes_opts_t& o, int64_t N);
 size_t aux_bytes_adjoint(const dmk_stokes_opts_t& o, int64_t N);
+// ewald.cu: the single-level PSWF Ewald far field (components = ALL, periodic 3D Stokeslet)
+int ewald_level(int64_t N, int ns);
+void ewald_setup(Plan& p, int L);
+void ewald_free(Plan& p);
+void ewald_far(const Plan& p, const double* d_f, double* d_u, cudaStream_t s);
+void ewald_info(const Plan& p, int32_t info[4]);
+
 // adjoint pass of the 3D Stokeslet (v = S[w], dL/dx); aux of aux_bytes_adjoint bytes
 void launch_adjoint(const Plan& p, const double* d_f, const double* d_w, double* d_v, double* d_gx,
                     cudaStream_t s, void* aux);

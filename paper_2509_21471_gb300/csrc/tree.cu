@@ -777,7 +777,12 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
   int32_t* d_cnt = scratch.alloc<int32_t>(M + 2);          // leaf count after each level
   k_set_value<<<1, 1, 0, s>>>(d_cnt, n_sys);
   ++p.launches;
-  const int64_t grow = ((int64_t(1) << D) - 1) * (N / (int64_t(p.leaf_capacity) + 1) + 1);
+  // a uniform tree (single-level Ewald split) splits every box down to its level
+  const bool uniform = p.uniform_level > 0;
+  const int ns_split = uniform ? -1 : p.leaf_capacity;
+  const int lmax_split = uniform ? p.uniform_level : M;
+  const int64_t grow = uniform ? ((int64_t(1) << D) - 1) * (int64_t(1) << (D * p.uniform_level))
+                               : ((int64_t(1) << D) - 1) * (N / (int64_t(p.leaf_capacity) + 1) + 1);
   int64_t cap = n_sys;
   int64_t n_leaf = n_sys;
   for (int lev = 0; lev <= M;) {
@@ -786,7 +791,7 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
       if (cap_out >= (int64_t(1) << 31)) throw Error{DMK_ERR_NOMEM, "tree too large"};
       int32_t* nch = scratch.alloc<int32_t>(cap);
       int32_t* pos = scratch.alloc<int32_t>(cap + 1);
-      split_and_scan<D>(SplitCounts<D>{cur, p.leaf_capacity, M, nullptr, d_cnt + lev}, static_cast<int>(cap), nch,
+      split_and_scan<D>(SplitCounts<D>{cur, ns_split, lmax_split, nullptr, d_cnt + lev}, static_cast<int>(cap), nch,
                         pos, s, scratch, p.launches);
       alloc_leaves(nxt, cap_out, A);
       k_refine_dev<D><<<grid_for(cap << D, B), B, 0, s>>>(static_cast<int>(cap), static_cast<int>(cap_out),
@@ -816,7 +821,7 @@ void build_tree_t(Plan& p, const double* d_src, const int64_t* h_offsets) {
     k_sys_begin<<<grid_for(n_leaf, B), B, 0, s>>>(static_cast<int>(n_leaf), n_sys, cur.sys, begin, flag, d_any);
     k_balance<D><<<grid_for(n_leaf * 32, B), B, 0, s>>>(static_cast<int>(n_leaf), cur, begin, M, T.periodic,
                                                         flag, d_any);
-    split_and_scan<D>(SplitCounts<D>{cur, p.leaf_capacity, M, flag, nullptr}, static_cast<int>(n_leaf), nch, pos, s,
+    split_and_scan<D>(SplitCounts<D>{cur, ns_split, lmax_split, flag, nullptr}, static_cast<int>(n_leaf), nch, pos, s,
                       scratch, p.launches);
     p.launches += 2;
     DMK_CUDA_TRY(cudaGetLastError());

@@ -117,7 +117,8 @@ class Plan:
     """dmk_stokes_plan / dmk_stokes_plan_batched on CUDA tensors."""
 
     def __init__(self, x, eps=1e-6, dim=None, periodic=False, kernels=STOKESLET, precision=MIXED,
-                 leaf_capacity=0, n_rhs=1, box_lo=None, offsets=None, stream=None, device=None, targets=None):
+                 leaf_capacity=0, n_rhs=1, box_lo=None, offsets=None, stream=None, device=None, targets=None,
+                 components=NEAR):
         device = device or (x.device if isinstance(x, torch.Tensor) and x.is_cuda else torch.device("cuda"))
         dim = dim or (x.shape[1])
         self.dim = dim
@@ -128,7 +129,7 @@ class Plan:
         self.n = self._x.shape[0]
         self._t = None if targets is None else _as_dev(targets, dim, "targets", device)
         self.nt = self.n if targets is None else self._t.shape[0]     # rows of every output
-        self.opts = make_opts(dim, periodic, kernels, precision, NEAR, leaf_capacity, n_rhs, eps, box_lo)
+        self.opts = make_opts(dim, periodic, kernels, precision, components, leaf_capacity, n_rhs, eps, box_lo)
         self._h = ctypes.c_void_p()
         with torch.cuda.device(device):
             sp = _stream_ptr(stream)
