@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (eps = 1e-10, 2D periodic, batched, gradient)")
+    ap.add_argument("--ewald-only", type=int, default=0, metavar="N",
+                    help="profiling aid: time only the full periodic sum (components = ALL) of N uniform "
+                         "points at --eps, plan reused, and print its own line")
     ap.add_argument("--batched-only", type=int, default=0, metavar="N_SYS",
                     help="profiling aid: time only the mixed near field of the batched workload "
                          "(N_SYS systems x 16 columns, plan reused) and print its own line")
@@ -79,6 +82,33 @@ def run_batched_only(args):
     print(json.dumps({"workload": "batched-systems-16-rhs", "n_systems": args.batched_only, "n_points": len(x),
                       "eps": 1e-6, "near_ms_median": 1e3 * t, "useful_pairs": st["useful_pairs"],
                       "gpairs_useful": st["useful_pairs"] / t / 1e9}), flush=True)
+
+
+def run_ewald_only(args):
+    """The periodic full sum at N uniform points, mixed precision: a small case
+    of the Ewald far-field kernels (spreading, per-mode product, interpolation)."""
+    import torch
+    from paper_2509_21471_gb300 import dmk, workloads as wl
+    x, f = wl.periodic_3d(n=args.ewald_only, seed_index=4)
+    xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
+    ud = torch.empty_like(fd)
+    p = dmk.Plan(xd, eps=args.eps, periodic=True, precision=dmk.MIXED, components=dmk.ALL)
+    for _ in range(max(1, args.warmup)):
+        p.eval(fd, out=ud)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        p.eval(fd, out=ud)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    st = p.stats()
+    p.sync_status()
+    p.close()
+    print(json.dumps({"workload": "3d-periodic-uniform-full-sum", "n_points": args.ewald_only, "eps": args.eps,
+                      "uniform_level": st["max_level"], "eval_ms_median": sorted(ms)[len(ms) // 2]}), flush=True)
 
 
 def workload_config(args, ns):
@@ -320,6 +350,35 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
                speedup_mixed_over_fp64=out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"])
     res["gradient_periodic_3d_eps1e-8"] = out
 
+    # periodic 3D Stokeslet, full sum (components = ALL): the single-level PSWF
+    # Ewald split (near pass on a uniform tree + non-uniform FFT Fourier part)
+    ew = {}
+    for n, eps in ((200_000, 1e-8), (1_000_000, 1e-6)):
+        x, f = wl.periodic_3d(n=n, seed_index=pdist.seed_index(4, rank))
+        xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
+        ud = torch.empty_like(fd)
+        row = {}
+        for name, prec in (("mixed", dmk.MIXED), ("fp64", dmk.FP64)):
+            def step():
+                p = dmk.Plan(xd, eps=eps, periodic=True, precision=prec, components=dmk.ALL)
+                p.eval(fd, out=ud)
+                p.close()
+            step()
+            torch.cuda.synchronize()
+            t = max_over_ranks(sum(timed(step, 2)) / 2 / 1e3)
+            p = dmk.Plan(xd, eps=eps, periodic=True, precision=prec, components=dmk.ALL)
+            p.eval(fd, out=ud)
+            st = p.stats()
+            t_eval = max_over_ranks(sum(timed(lambda: p.eval(fd, out=ud), 2)) / 2 / 1e3)
+            p.close()
+            row[name] = {"ms_per_step": 1e3 * t, "eval_ms": 1e3 * t_eval, "targets_per_s": n / t,
+                         "uniform_level": st["max_level"]}
+        ew[f"n{n}_eps{eps:g}"] = dict(row, n_points=n, eps=eps)
+        del xd, fd, ud
+    res["ewald_periodic_3d_full_sum"] = {
+        "workload": "3d-periodic-uniform, full periodic Stokeslet sum (near + Fourier part)",
+        "step": "plan + eval (components = ALL)", "runs": ew}
+
     # linear scaling (Sec. 8): sources and as many separate targets on a
     # perturbed sphere (3D) or circle (2D), N_S = N_T, eps = 1e-6, the paper's
     # leaf capacity; a step = plan (sources and targets) + eval + destroy, MIXED
@@ -542,6 +601,8 @@ def main():
         run_reference(args)
     elif args.batched_only > 0:
         run_batched_only(args)
+    elif args.ewald_only > 0:
+        run_ewald_only(args)
     else:
         run_ours(args)
 

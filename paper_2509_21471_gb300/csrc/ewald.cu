@@ -237,10 +237,12 @@ struct EwaldState {
 };
 
 // Uniform tree level for the Ewald split: the smallest L >= 1 with at most
-// ns points per box (ns = the plan's leaf capacity, default 1000: near and far
-// work about even on uniform points), at most 4.
+// ns points per box (ns = the plan's leaf capacity, default 4000), at most 4.
+// Each level down costs 8x the grid of the Fourier part and saves 8x the
+// near pairs; on GB300 the grid (FFTs, spreading traffic) costs more than the
+// near pairs down to a few thousand points per box.
 int ewald_level(int64_t N, int ns) {
-  if (ns <= 0) ns = 1000;
+  if (ns <= 0) ns = 4000;
   int L = 1;
   while (L < 4 && static_cast<double>(N) / std::ldexp(1.0, 3 * L) > ns) ++L;
   return L;
