@@ -163,7 +163,8 @@ dmk_status_t dmk_stokes_eval(dmk_stokes_plan_t plan, const double* d_f, const do
  *   call's contents (what must start at zero is cleared by every call); calls
  *   whose work overlaps on the GPU race on it, so queue them on one stream.
  *   The first call on a device looks the array's address up (with that device
- *   current); make it before any stream capture. */
+ *   current); make it before any stream capture.  The address is kept for the
+ *   life of the process: resetting the device after that call is not supported. */
 dmk_status_t dmk_stokes_eval_noalloc(dmk_stokes_plan_t plan, const double* d_f, const double* d_g,
                                      const double* d_n, double* d_u, void* stream);
 

@@ -23,7 +23,9 @@
 //     calls whose work overlaps on the GPU race on the array;
 //   * the device address of the array is looked up once per device, with that
 //     device current, by the first call on the device; make that first call
-//     before any stream capture.
+//     before any stream capture.  The address is kept for the life of the
+//     process: a device reset (cudaDeviceReset) after the first call is not
+//     supported.
 #include <mutex>
 
 #include "common.cuh"
