@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--ewald-only", type=int, default=0, metavar="N",
                     help="profiling aid: time only the full periodic sum (components = ALL) of N uniform "
                          "points at --eps, plan reused, and print its own line")
+    ap.add_argument("--sweep", action="store_true",
+                    help="parameter sweep (Sec. 7): error of the periodic full sum (FP64) on 5000 uniform points "
+                         "against the bandlimit c (3c/pi = 2..34) and the grid width w (eps = 1e-3..1e-12), "
+                         "relative to 3c/pi = 36 at eps = 1e-12; prints its own line")
     ap.add_argument("--batched-only", type=int, default=0, metavar="N_SYS",
                     help="profiling aid: time only the mixed near field of the batched workload "
                          "(N_SYS systems x 16 columns, plan reused) and print its own line")
@@ -109,6 +113,43 @@ def run_ewald_only(args):
     p.close()
     print(json.dumps({"workload": "3d-periodic-uniform-full-sum", "n_points": args.ewald_only, "eps": args.eps,
                       "uniform_level": st["max_level"], "eval_ms_median": sorted(ms)[len(ms) // 2]}), flush=True)
+
+
+def run_sweep(args):
+    """E(c, w): relative l2 error of the periodic Stokeslet full sum (single-level
+    prolate Ewald split, FP64) on 5000 uniform points against the converged sum
+    (3c/pi = 36, eps = 1e-12), for 3c/pi = 2..34 and the grid widths of eps =
+    1e-3..1e-12; per row the fitted slope of log10 E in 3c/pi and the smallest
+    3c/pi reaching E <= eps, beside Table 2's value."""
+    import numpy as np
+    import torch
+    from paper_2509_21471_gb300 import dmk, workloads as wl
+    x, f = wl.periodic_3d(n=5000, seed_index=6)
+    xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
+
+    def total(c3, eps):
+        p = dmk.Plan(xd, eps=eps, periodic=True, precision=dmk.FP64, components=dmk.ALL, bandlimit=c3)
+        u = p.eval(fd).cpu().numpy()
+        p.sync_status()
+        p.close()
+        return u
+
+    ref = total(36, 1e-12)
+    table2 = {1e-3: 10, 1e-6: 17, 1e-9: 25, 1e-12: 31}
+    rows = []
+    for eps in (1e-3, 1e-6, 1e-9, 1e-12):
+        c3s = list(range(2, 35, 2))
+        errs = [float(np.linalg.norm(total(c3, eps) - ref) / np.linalg.norm(ref)) for c3 in c3s]
+        ok = [c3 for c3, e in zip(c3s, errs) if e <= eps]
+        # fitted where c limits the error: above 20x the row's floor (the grid width's accuracy)
+        floor = min(errs)
+        fit = [(c3, np.log10(e)) for c3, e in zip(c3s, errs) if e > 20 * floor and c3 >= 4]
+        slope = float(np.polyfit([a for a, _ in fit], [b for _, b in fit], 1)[0]) if len(fit) > 2 else None
+        rows.append({"eps": eps, "w": int(np.ceil(-np.log10(eps))) + 1, "three_c_over_pi": c3s, "rel_l2": errs,
+                     "first_c3_meeting_eps": ok[0] if ok else None, "table2_c3": table2[eps],
+                     "fit_slope_log10E_per_c3": slope})
+    print(json.dumps({"sweep": "E(c, w) of the periodic Stokeslet full sum, 5000 uniform points, FP64",
+                      "reference": "3c/pi = 36, eps = 1e-12", "rows": rows}), flush=True)
 
 
 def workload_config(args, ns):
@@ -603,6 +644,8 @@ def main():
         run_batched_only(args)
     elif args.ewald_only > 0:
         run_ewald_only(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

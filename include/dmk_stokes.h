@@ -90,10 +90,13 @@ typedef struct {
   int32_t leaf_capacity; /* n_s, max points per leaf; 0 = the paper's value for
                             eps (Sec. 8: 3D 600..3000, 2D 120..480) */
   int32_t n_rhs;         /* force columns, 1..16 */
-  int32_t reserved;      /* must be 0 */
+  int32_t bandlimit;     /* 0: the prolate bandlimit c from eps (below);
+                            2..36: c = bandlimit * pi / 3 (3c/pi given), for
+                            parameter studies such as E(c) of Sec. 7 */
   double eps;            /* tolerance in [1e-12, 1e-3]; selects the prolate
                             bandlimit c from Table 2 (3c/pi interpolated in
-                            log10 eps and rounded up) */
+                            log10 eps and rounded up) unless bandlimit is set,
+                            the FP32 table length and the Ewald grid width */
   double box_lo[3];      /* lower corner lo of the unit box (side 1) */
 } dmk_stokes_opts_t;
 

@@ -35,7 +35,10 @@ dmk_status_t validate_opts(const dmk_stokes_opts_t* o, std::string& msg) {
   }
   if (o->leaf_capacity < 0 || o->leaf_capacity > (1 << 20)) { msg = "leaf_capacity out of range"; return DMK_ERR_INVALID_ARG; }
   if (o->n_rhs < 1 || o->n_rhs > 16) { msg = "n_rhs must be in 1..16"; return DMK_ERR_INVALID_ARG; }
-  if (o->reserved != 0) { msg = "reserved must be 0"; return DMK_ERR_INVALID_ARG; }
+  if (o->bandlimit != 0 && (o->bandlimit < 2 || o->bandlimit > 36)) {
+    msg = "bandlimit (3c/pi) must be 0 or in 2..36";
+    return DMK_ERR_INVALID_ARG;
+  }
   if (!(o->eps >= 1e-12 * (1 - 1e-9) && o->eps <= 1e-3 * (1 + 1e-9))) {
     msg = "eps must lie in [1e-12, 1e-3] (Table 2 range)";
     return DMK_ERR_INVALID_ARG;
@@ -178,7 +181,7 @@ dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64
   try {
     DMK_CUDA_TRY(cudaGetDevice(&p.device));
     configure_pool(p.device);
-    double c = dmk::bandlimit_for_eps(opts->eps, opts->kernels);
+    double c = opts->bandlimit > 0 ? opts->bandlimit * M_PI / 3.0 : dmk::bandlimit_for_eps(opts->eps, opts->kernels);
     if (c <= 0) throw dmk::Error{DMK_ERR_INVALID_ARG, "eps outside Table 2 range"};
     if (!cached_tables(opts->dim, c, fp32_table_tol(opts->eps), &p.tables))
       throw dmk::Error{DMK_ERR_UNSUPPORTED, "kernel tables could not be built for this dimension"};

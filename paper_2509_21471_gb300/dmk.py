@@ -35,7 +35,7 @@ class DMKError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("periodic", ctypes.c_int32), ("kernels", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("components", ctypes.c_int32),
-                ("leaf_capacity", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("leaf_capacity", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("bandlimit", ctypes.c_int32),
                 ("eps", ctypes.c_double), ("box_lo", ctypes.c_double * 3)]
 
 
@@ -102,10 +102,10 @@ def _as_dev(t, dim, name, device, n_rhs=1):
 
 
 def make_opts(dim=3, periodic=False, kernels=STOKESLET, precision=MIXED, components=NEAR,
-              leaf_capacity=0, n_rhs=1, eps=1e-6, box_lo=None):
+              leaf_capacity=0, n_rhs=1, eps=1e-6, box_lo=None, bandlimit=0):
     o = Opts()
     o.dim, o.periodic, o.kernels, o.precision = dim, int(bool(periodic)), kernels, precision
-    o.components, o.leaf_capacity, o.n_rhs, o.reserved = components, leaf_capacity, n_rhs, 0
+    o.components, o.leaf_capacity, o.n_rhs, o.bandlimit = components, leaf_capacity, n_rhs, bandlimit
     o.eps = eps
     lo = [-0.5] * 3 if box_lo is None else list(box_lo) + [-0.5] * (3 - len(box_lo))
     for a in range(3):
@@ -118,7 +118,7 @@ class Plan:
 
     def __init__(self, x, eps=1e-6, dim=None, periodic=False, kernels=STOKESLET, precision=MIXED,
                  leaf_capacity=0, n_rhs=1, box_lo=None, offsets=None, stream=None, device=None, targets=None,
-                 components=NEAR):
+                 components=NEAR, bandlimit=0):
         device = device or (x.device if isinstance(x, torch.Tensor) and x.is_cuda else torch.device("cuda"))
         dim = dim or (x.shape[1])
         self.dim = dim
@@ -129,7 +129,8 @@ class Plan:
         self.n = self._x.shape[0]
         self._t = None if targets is None else _as_dev(targets, dim, "targets", device)
         self.nt = self.n if targets is None else self._t.shape[0]     # rows of every output
-        self.opts = make_opts(dim, periodic, kernels, precision, components, leaf_capacity, n_rhs, eps, box_lo)
+        self.opts = make_opts(dim, periodic, kernels, precision, components, leaf_capacity, n_rhs, eps, box_lo,
+                              bandlimit)
         self._h = ctypes.c_void_p()
         with torch.cuda.device(device):
             sp = _stream_ptr(stream)

@@ -86,3 +86,22 @@ def test_components_all_limits(dmk):
         p.eval_noalloc(f)
     assert ei.value.code == 3
     p.close()
+
+
+def test_bandlimit_override_table2_rows(dmk):
+    """With the bandlimit given explicitly (3c/pi), the full sum's error against
+    the Gaussian Ewald total falls with c, and Table 2's values of 3c/pi for
+    eps = 1e-3, 1e-6, 1e-9 meet their eps (grid width of eps = 1e-12)."""
+    rng = np.random.default_rng(930)
+    N = 150
+    x = wl.uniform_points(rng, N, 3)
+    f = wl.forces(rng, N, 3, zero_mean=True)
+    u_ref = ewald.ewald_sum(x, f=f, split=ewald.gaussian_split_3d(0.12))
+    errs = {}
+    for c3 in (6, 10, 17, 25):
+        p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=1e-12, periodic=True, precision=0, leaf_capacity=20,
+                     components=dmk.ALL, bandlimit=c3)
+        errs[c3] = rel_l2(p.eval(torch.as_tensor(f, device="cuda")).cpu().numpy(), u_ref)
+        p.close()
+    assert errs[6] > errs[10] > errs[17] > errs[25]
+    assert errs[10] < 1e-3 and errs[17] < 1e-6 and errs[25] < 1e-9
