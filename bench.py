@@ -398,16 +398,19 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
         x, f = wl.periodic_3d(n=n, seed_index=pdist.seed_index(4, rank))
         xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
         ud = torch.empty_like(fd)
-        row = {}
+        # the autotuner picks the uniform level (points per box) of the split
+        ns, tune = dmk.autotune(xd, fd, candidates=(n // 512 + 1, n // 64 + 1, n // 8 + 1), repeats=2, eps=eps,
+                                periodic=True, precision=dmk.MIXED, components=dmk.ALL)
+        row = {"autotune_ms_by_points_per_box": tune, "points_per_box": ns}
         for name, prec in (("mixed", dmk.MIXED), ("fp64", dmk.FP64)):
             def step():
-                p = dmk.Plan(xd, eps=eps, periodic=True, precision=prec, components=dmk.ALL)
+                p = dmk.Plan(xd, eps=eps, periodic=True, precision=prec, components=dmk.ALL, leaf_capacity=ns)
                 p.eval(fd, out=ud)
                 p.close()
             step()
             torch.cuda.synchronize()
             t = max_over_ranks(sum(timed(step, 2)) / 2 / 1e3)
-            p = dmk.Plan(xd, eps=eps, periodic=True, precision=prec, components=dmk.ALL)
+            p = dmk.Plan(xd, eps=eps, periodic=True, precision=prec, components=dmk.ALL, leaf_capacity=ns)
             p.eval(fd, out=ud)
             st = p.stats()
             t_eval = max_over_ranks(sum(timed(lambda: p.eval(fd, out=ud), 2)) / 2 / 1e3)

@@ -215,6 +215,23 @@ dmk_status_t dmk_stokes_eval_grad(dmk_stokes_plan_t plan, const double* d_f, con
 dmk_status_t dmk_stokes_eval_adjoint(dmk_stokes_plan_t plan, const double* d_f, const double* d_w, double* d_v,
                                      double* d_gx, void* stream);
 
+/* Autotuner (no paper counterpart; the paper fixes n_s per eps, Sec. 8):
+ * builds and evaluates a plan (dmk_stokes_plan + dmk_stokes_eval + destroy,
+ * targets = sources) for every candidate leaf capacity h_leaf_capacity[k],
+ * times each `repeats` times on `stream` with CUDA events after one untimed
+ * run, and returns the median times in h_ms[n_cand] (may be NULL) and the
+ * index of the fastest in *h_best.  The leaf capacity sets the tree: for
+ * components = DMK_COMPONENTS_ALL it sets the uniform level of the Ewald split
+ * (the smallest level with at most that many points per box), i.e. the
+ * balance between the near pass and the Fourier part; for the near component
+ * alone the smallest leaves always win (the far field that balances them in
+ * the DMK method is not part of that component).  d_u receives the velocity of
+ * the last run.  Host-synchronises. */
+dmk_status_t dmk_stokes_autotune(const dmk_stokes_opts_t* opts, int64_t n_src, const double* d_src,
+                                 const double* d_f, const double* d_g, const double* d_n, double* d_u,
+                                 int32_t n_cand, const int32_t* h_leaf_capacity, int32_t repeats, void* stream,
+                                 double* h_ms, int32_t* h_best);
+
 /* Synchronises the plan's last stream and returns the latched device status
  * (DMK_OK, DMK_ERR_OUT_OF_RANGE, DMK_ERR_INVALID_ARG for a non-finite point). */
 dmk_status_t dmk_stokes_sync_status(dmk_stokes_plan_t plan);

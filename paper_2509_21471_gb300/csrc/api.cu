@@ -337,6 +337,48 @@ dmk_status_t dmk_stokes_eval_adjoint(dmk_stokes_plan_t plan, const double* d_f, 
   return DMK_OK;
 }
 
+dmk_status_t dmk_stokes_autotune(const dmk_stokes_opts_t* opts, int64_t n_src, const double* d_src,
+                                 const double* d_f, const double* d_g, const double* d_n, double* d_u,
+                                 int32_t n_cand, const int32_t* h_leaf_capacity, int32_t repeats, void* stream,
+                                 double* h_ms, int32_t* h_best) {
+  if (!opts || n_cand < 1 || !h_leaf_capacity || repeats < 1 || !h_best)
+    return set_err(nullptr, DMK_ERR_INVALID_ARG, "bad autotune arguments");
+  for (int k = 0; k < n_cand; ++k)
+    if (h_leaf_capacity[k] < 1) return set_err(nullptr, DMK_ERR_INVALID_ARG, "candidate leaf capacity < 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_err(nullptr, DMK_ERR_CUDA, "cudaEventCreate failed");
+  std::vector<double> med(n_cand);
+  dmk_status_t st = DMK_OK;
+  for (int k = 0; k < n_cand && st == DMK_OK; ++k) {
+    dmk_stokes_opts_t o = *opts;
+    o.leaf_capacity = h_leaf_capacity[k];
+    std::vector<float> ms;
+    for (int r = 0; r <= repeats && st == DMK_OK; ++r) {   // the first run warms the pools up, untimed
+      cudaEventRecord(e0, s);
+      dmk_stokes_plan_t plan = nullptr;
+      st = dmk_stokes_plan(&o, n_src, d_src, n_src, nullptr, stream, &plan);
+      if (st == DMK_OK) st = dmk_stokes_eval(plan, d_f, d_g, d_n, d_u, stream);
+      if (plan) dmk_stokes_destroy(plan);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = set_err(nullptr, DMK_ERR_CUDA, "autotune timing failed");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0) ms.push_back(t);
+    }
+    if (st != DMK_OK) break;
+    std::sort(ms.begin(), ms.end());
+    med[k] = ms[ms.size() / 2];
+    if (h_ms) h_ms[k] = med[k];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DMK_OK) return st;
+  *h_best = static_cast<int32_t>(std::min_element(med.begin(), med.end()) - med.begin());
+  return DMK_OK;
+}
+
 dmk_status_t dmk_stokes_sync_status(dmk_stokes_plan_t plan) {
   if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
   dmk::Plan& p = plan->p;

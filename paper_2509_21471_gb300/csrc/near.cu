@@ -269,7 +269,7 @@ WsLayout ws_layout(const dmk_stokes_opts_t& o, int64_t N, int64_t NT) {
   L.accg_off = L.acc_off + (fp64_sym ? 3 * N * sizeof(double) : 0);
   L.flag_off = L.accg_off + ((ff_pairs(o) && o.dim == 3) ? 12 * N * sizeof(double) : 0);
   const int64_t NP = std::max(N, NT);                 // tiles: at most one per point or target
-  L.queue_off = L.flag_off + (o.precision == DMK_PRECISION_MIXED ? ((NP + 1) * sizeof(int) + 15) / 16 * 16 : 0);
+  L.queue_off = L.flag_off + (o.precision == DMK_PRECISION_MIXED ? ((NP + 2) * sizeof(int) + 15) / 16 * 16 : 0);
   L.bytes = L.queue_off + (o.precision == DMK_PRECISION_MIXED ? close_cap(N) * sizeof(int4) : 0);
   return L;
 }
@@ -578,10 +578,18 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     const bool sym32 = mixed && km == 1 && !grad && NR == 1 && d_u && !sep;   // k_near_sym (P.acc set above)
     if (ff || mixed) {
       P.close_count = reinterpret_cast<int*>(ws + WL.flag_off);
-      P.close_flag = P.close_count + 1;
+      P.close_flag = P.close_count + 2;
       P.close_q = reinterpret_cast<int4*>(ws + WL.queue_off);
       P.close_cap = static_cast<int>(close_cap(N));
-      DMK_CUDA_TRY(cudaMemsetAsync(P.close_count, 0, sizeof(int) * (P.n_ttile + 1), s));
+      DMK_CUDA_TRY(cudaMemsetAsync(P.close_count, 0, sizeof(int) * (P.n_ttile + 2), s));
+      // batched plans with several force columns: k_near_mixed takes its tiles
+      // from a work queue (a grid of 24 one-warp blocks per SM)
+      if (mixed && T.n_sys > 1 && NR > 1) {
+        P.work_count = P.close_count + 1;
+        int sms = 0;
+        DMK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device));
+        P.work_grid = std::min(sms * 24, std::max(1, P.n_ttile));
+      }
     }
     CloseParams C{};
     C.f = d_f;

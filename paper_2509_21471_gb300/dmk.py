@@ -55,6 +55,8 @@ _lib.dmk_stokes_kernel_table.argtypes = [ctypes.c_int32, ctypes.c_double, ctypes
 _lib.dmk_stokes_partition_leaves.argtypes = [ctypes.c_int32, _P, _P, _P, _P, ctypes.c_int32, _P, _P]
 _lib.dmk_stokes_halo_leaves.argtypes = [ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
                                         _P]
+_lib.dmk_stokes_autotune.argtypes = [ctypes.POINTER(Opts), ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_int32, _P,
+                                     ctypes.c_int32, _P, _P, _P]
 _lib.dmk_stokes_destroy.argtypes = [_P]
 _lib.dmk_stokes_destroy.restype = None
 _lib.dmk_stokes_last_error.argtypes = [_P]
@@ -62,13 +64,15 @@ _lib.dmk_stokes_last_error.restype = ctypes.c_char_p
 for _name in ("dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
               "dmk_stokes_eval_grad", "dmk_stokes_eval_adjoint",
               "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree",
-              "dmk_stokes_kernel_table", "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves"):
+              "dmk_stokes_kernel_table", "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves",
+              "dmk_stokes_autotune"):
     getattr(_lib, _name).restype = ctypes.c_int
 
 EXPORTED = ["dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
             "dmk_stokes_eval_grad", "dmk_stokes_eval_adjoint",
             "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree", "dmk_stokes_kernel_table",
-            "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves", "dmk_stokes_destroy", "dmk_stokes_last_error"]
+            "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves", "dmk_stokes_autotune", "dmk_stokes_destroy",
+            "dmk_stokes_last_error"]
 
 
 def _check(code, handle=None):
@@ -238,6 +242,27 @@ def kernel_table(dim, eps, which, fp32=False, kernels=STOKESLET):
     _check(_lib.dmk_stokes_kernel_table(dim, eps, kernels, which, int(fp32), ctypes.byref(c), ctypes.byref(phi0),
                                         buf.ctypes.data_as(ctypes.c_void_p), 64, ctypes.byref(nt)))
     return c.value, phi0.value, buf[: nt.value].copy()
+
+
+def autotune(x, f=None, g=None, n=None, candidates=(600, 1200, 2400), repeats=3, stream=None, **plan_kwargs):
+    """dmk_stokes_autotune: (best leaf capacity, {candidate: median ms of plan + eval})."""
+    x = _as_dev(x, x.shape[1], "x", x.device)
+    dim = x.shape[1]
+    o = make_opts(dim=dim, **{k: v for k, v in plan_kwargs.items() if k != "leaf_capacity"})
+    nr = o.n_rhs
+    f = None if f is None else _as_dev(f, dim, "f", x.device, nr)
+    g = None if g is None else _as_dev(g, dim, "g", x.device)
+    n = None if n is None else _as_dev(n, dim, "n", x.device)
+    u = torch.empty((x.shape[0], dim) if nr == 1 else (x.shape[0], dim, nr), dtype=torch.float64, device=x.device)
+    cand = _i32(candidates)
+    ms = np.zeros(len(cand), np.float64)
+    best = ctypes.c_int32()
+    with torch.cuda.device(x.device):
+        _check(_lib.dmk_stokes_autotune(ctypes.byref(o), x.shape[0], _ptr(x), _ptr(f), _ptr(g), _ptr(n), _ptr(u),
+                                        len(cand), cand.ctypes.data_as(ctypes.c_void_p), repeats,
+                                        _stream_ptr(stream), ms.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.byref(best)))
+    return int(cand[best.value]), {int(c): float(t) for c, t in zip(cand, ms)}
 
 
 def _i32(a):

@@ -105,3 +105,23 @@ def test_bandlimit_override_table2_rows(dmk):
         p.close()
     assert errs[6] > errs[10] > errs[17] > errs[25]
     assert errs[10] < 1e-3 and errs[17] < 1e-6 and errs[25] < 1e-9
+
+
+def test_autotune_picks_the_fastest_candidate(dmk):
+    """The autotuner times plan + eval per candidate leaf capacity (for the full
+    periodic sum: the uniform level of the Ewald split) and returns the fastest;
+    its result equals a plan built with that capacity."""
+    rng = np.random.default_rng(940)
+    N = 60000
+    x = torch.as_tensor(wl.uniform_points(rng, N, 3), device="cuda")
+    f = torch.as_tensor(wl.forces(rng, N, 3, zero_mean=True), device="cuda")
+    best, times = dmk.autotune(x, f, candidates=(300, 3000, 30000), repeats=2, eps=1e-6, periodic=True,
+                               precision=dmk.MIXED, components=dmk.ALL)
+    assert set(times) == {300, 3000, 30000} and all(t > 0 for t in times.values())
+    assert times[best] == min(times.values())
+    levels = set()
+    for ns in times:
+        p = dmk.Plan(x, eps=1e-6, periodic=True, precision=dmk.MIXED, components=dmk.ALL, leaf_capacity=ns)
+        levels.add(p.stats()["max_level"])
+        p.close()
+    assert levels == {1, 2, 3}                                   # three different splits
