@@ -578,18 +578,10 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
     const bool sym32 = mixed && km == 1 && !grad && NR == 1 && d_u && !sep;   // k_near_sym (P.acc set above)
     if (ff || mixed) {
       P.close_count = reinterpret_cast<int*>(ws + WL.flag_off);
-      P.close_flag = P.close_count + 2;
+      P.close_flag = P.close_count + 2;             // [1] unused
       P.close_q = reinterpret_cast<int4*>(ws + WL.queue_off);
       P.close_cap = static_cast<int>(close_cap(N));
       DMK_CUDA_TRY(cudaMemsetAsync(P.close_count, 0, sizeof(int) * (P.n_ttile + 2), s));
-      // batched plans with several force columns: k_near_mixed takes its tiles
-      // from a work queue (a grid of 24 one-warp blocks per SM)
-      if (mixed && T.n_sys > 1 && NR > 1) {
-        P.work_count = P.close_count + 1;
-        int sms = 0;
-        DMK_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device));
-        P.work_grid = std::min(sms * 24, std::max(1, P.n_ttile));
-      }
     }
     CloseParams C{};
     C.f = d_f;

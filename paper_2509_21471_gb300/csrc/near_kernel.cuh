@@ -84,8 +84,6 @@ struct NearParams {
   const float4* trel;    // FP32 leaf-relative target coordinates
   const double* tw;      // FP64 in-cell target coordinates, SoA [D][NT]
   const int32_t* tperm;  // sorted target -> caller's target index
-  int* work_count;       // k_near_mixed work queue: next target tile (zeroed), or null: one tile per warp
-  int work_grid;         // blocks of the work-queue launch
   int* close_flag;       // per target tile, zeroed: set where a nearly coincident pair was skipped
   int* close_count;      // skipped pairs queued (zeroed; may exceed close_cap)
   int4* close_q;         // queued pairs: (target, source, near-list entry, L_B | both << 8), sorted indices
@@ -407,16 +405,8 @@ __global__ void __launch_bounds__(32 * kMixWarps, 24 / kMixWarps) k_near_mixed(c
   __shared__ float4 s_g[(KM & 2) ? W : 1][kTile];
   __shared__ float4 s_n[(KM & 2) ? W : 1][kTile];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // target tile: one per warp of the grid, or (work queue, P.work_count set)
-  // taken in turn from a counter by a grid of a few warps per SM
-  auto next_tile = [&]() {
-    int t = 0;
-    if (lane == 0) t = atomicAdd(P.work_count, 1);
-    return __shfl_sync(0xffffffffu, t, 0);
-  };
-  for (int tile = P.work_count ? next_tile() : blockIdx.x * W + wid; tile < P.n_ttile;
-       tile = P.work_count ? next_tile() : P.n_ttile) {
-  __syncwarp();
+  const int tile = blockIdx.x * W + wid;               // target tile
+  if (tile >= P.n_ttile) return;
   const int64_t N = P.N;
   const int B = P.ttile_leaf[tile];
   const int t0 = P.ttile_start[tile], nt = P.ttile_count[tile];
@@ -610,7 +600,7 @@ __global__ void __launch_bounds__(32 * kMixWarps, 24 / kMixWarps) k_near_mixed(c
       }
     }
   }
-  if (!on) continue;
+  if (!on) return;
   const int64_t o = P.tperm[t0 + lane];
   const double sc = P.same_set ? self_coeff<D>(P, LB) : 0.0;   // separate targets: no self term
   const int nr = P.n_rhs;
@@ -634,7 +624,6 @@ __global__ void __launch_bounds__(32 * kMixWarps, 24 / kMixWarps) k_near_mixed(c
 #pragma unroll
     for (int k = 0; k < 9; ++k)
       P.gradu[o * 9 + k] = (static_cast<double>(Gh[k]) + static_cast<double>(Gl[k])) * kInv8Pi;
-  }
   }
 }
 
@@ -1256,8 +1245,7 @@ void run_near_mixed(const NearParams& P, cudaStream_t s) {
       return;
     }
   }
-  const int grid = P.work_count ? P.work_grid : (P.n_ttile + kMixWarps - 1) / kMixWarps;
-  k_near_mixed<D, KM, GRAD, NT, NR><<<grid, 32 * kMixWarps, 0, s>>>(P);
+  k_near_mixed<D, KM, GRAD, NT, NR><<<(P.n_ttile + kMixWarps - 1) / kMixWarps, 32 * kMixWarps, 0, s>>>(P);
 }
 template <int D, int KM, bool GRAD, int NT, int NR>
 void run_near_fp64(const NearParams& P, cudaStream_t s) {
