@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (eps = 1e-10, 2D periodic, batched, gradient)")
     ap.add_argument("--ewald-only", type=int, default=0, metavar="N",
-                    help="profiling aid: time only the full periodic sum (components = ALL) of N uniform "
+                    help="profiling aid: time only the full periodic sum (components = EWALD) of N uniform "
                          "points at --eps, plan reused, and print its own line")
     ap.add_argument("--sweep", action="store_true",
                     help="parameter sweep (Sec. 7): error of the periodic full sum (FP64) on 5000 uniform points "
@@ -96,7 +96,7 @@ def run_ewald_only(args):
     x, f = wl.periodic_3d(n=args.ewald_only, seed_index=4)
     xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
     ud = torch.empty_like(fd)
-    p = dmk.Plan(xd, eps=args.eps, periodic=True, precision=dmk.MIXED, components=dmk.ALL)
+    p = dmk.Plan(xd, eps=args.eps, periodic=True, precision=dmk.MIXED, components=dmk.EWALD)
     for _ in range(max(1, args.warmup)):
         p.eval(fd, out=ud)
     torch.cuda.synchronize()
@@ -128,7 +128,7 @@ def run_sweep(args):
     xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
 
     def total(c3, eps):
-        p = dmk.Plan(xd, eps=eps, periodic=True, precision=dmk.FP64, components=dmk.ALL, bandlimit=c3)
+        p = dmk.Plan(xd, eps=eps, periodic=True, precision=dmk.FP64, components=dmk.EWALD, bandlimit=c3)
         u = p.eval(fd).cpu().numpy()
         p.sync_status()
         p.close()
@@ -391,7 +391,7 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
                speedup_mixed_over_fp64=out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"])
     res["gradient_periodic_3d_eps1e-8"] = out
 
-    # periodic 3D Stokeslet, full sum (components = ALL): the single-level PSWF
+    # periodic 3D Stokeslet, full sum (components = EWALD): the single-level PSWF
     # Ewald split (near pass on a uniform tree + non-uniform FFT Fourier part)
     ew = {}
     for n, eps in ((200_000, 1e-8), (1_000_000, 1e-6)):
@@ -400,17 +400,17 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
         ud = torch.empty_like(fd)
         # the autotuner picks the uniform level (points per box) of the split
         ns, tune = dmk.autotune(xd, fd, candidates=(n // 512 + 1, n // 64 + 1, n // 8 + 1), repeats=2, eps=eps,
-                                periodic=True, precision=dmk.MIXED, components=dmk.ALL)
+                                periodic=True, precision=dmk.MIXED, components=dmk.EWALD)
         row = {"autotune_ms_by_points_per_box": tune, "points_per_box": ns}
         for name, prec in (("mixed", dmk.MIXED), ("fp64", dmk.FP64)):
             def step():
-                p = dmk.Plan(xd, eps=eps, periodic=True, precision=prec, components=dmk.ALL, leaf_capacity=ns)
+                p = dmk.Plan(xd, eps=eps, periodic=True, precision=prec, components=dmk.EWALD, leaf_capacity=ns)
                 p.eval(fd, out=ud)
                 p.close()
             step()
             torch.cuda.synchronize()
             t = max_over_ranks(sum(timed(step, 2)) / 2 / 1e3)
-            p = dmk.Plan(xd, eps=eps, periodic=True, precision=prec, components=dmk.ALL, leaf_capacity=ns)
+            p = dmk.Plan(xd, eps=eps, periodic=True, precision=prec, components=dmk.EWALD, leaf_capacity=ns)
             p.eval(fd, out=ud)
             st = p.stats()
             t_eval = max_over_ranks(sum(timed(lambda: p.eval(fd, out=ud), 2)) / 2 / 1e3)
@@ -421,7 +421,7 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
         del xd, fd, ud
     res["ewald_periodic_3d_full_sum"] = {
         "workload": "3d-periodic-uniform, full periodic Stokeslet sum (near + Fourier part)",
-        "step": "plan + eval (components = ALL)", "runs": ew}
+        "step": "plan + eval (components = EWALD)", "runs": ew}
 
     # linear scaling (Sec. 8): sources and as many separate targets on a
     # perturbed sphere (3D) or circle (2D), N_S = N_T, eps = 1e-6, the paper's

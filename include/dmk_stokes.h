@@ -62,7 +62,7 @@ typedef enum {
 
 enum { DMK_KERNEL_STOKESLET = 1, DMK_KERNEL_STRESSLET = 2 };
 enum { DMK_PRECISION_FP64 = 0, DMK_PRECISION_MIXED = 1 };
-enum { DMK_COMPONENTS_ALL = 0, DMK_COMPONENTS_NEAR = 1 };
+enum { DMK_COMPONENTS_ALL = 0, DMK_COMPONENTS_NEAR = 1, DMK_COMPONENTS_EWALD = 2 };
 
 typedef struct {
   int32_t dim;           /* 2 or 3 */
@@ -85,8 +85,29 @@ typedef struct {
                             leaf-relative coordinates cannot resolve them.
                             The gradient and the adjoint take float-float pair
                             terms at every eps. */
-  int32_t components;    /* DMK_COMPONENTS_NEAR (the far field is not provided:
-                            DMK_COMPONENTS_ALL returns DMK_ERR_UNSUPPORTED) */
+  int32_t components;    /* DMK_COMPONENTS_NEAR: the near component (residual
+                            pass + self term, + the periodic stresslet zero
+                            mode).
+                            DMK_COMPONENTS_ALL: the whole DMK sum, 3D, one
+                            force column, free space or periodic, Stokeslet
+                            and/or stresslet, sources or separate targets:
+                            the near component plus the far field of Sec. 6
+                            (leaf proxy charges on p^3 Chebyshev grids, child
+                            merges, level-l plane waves with N1 modes a side
+                            for the colleague difference kernels, the root
+                            kernel K_M,0: periodic Fourier series with N_per
+                            modes a side, or the truncated kernel of Eq.
+                            (Bmollhat_trunc) in free space, interpolation to
+                            the leaves).  p, N1, N_per from Table 2 (p
+                            interpolated in log10 eps, N1 = 2 (3c/pi) - 1,
+                            N_per = 2 floor(c / 2pi) + 1).  The far field runs
+                            in float32 where the pair terms do (MIXED, eps >=
+                            2e-7) and in float64 otherwise.  Single system;
+                            eval_grad / adjoint / noalloc: UNSUPPORTED.
+                            DMK_COMPONENTS_EWALD: the periodic 3D Stokeslet
+                            summed by a single-level prolate Ewald split on a
+                            uniform tree (near pass at the leaf scale + an FFT
+                            far field, Sec. 5.3), one column, targets = sources. */
   int32_t leaf_capacity; /* n_s, max points per leaf; 0 = the paper's value for
                             eps (Sec. 8: 3D 600..3000, 2D 120..480) */
   int32_t n_rhs;         /* force columns, 1..16 */
@@ -221,16 +242,25 @@ dmk_status_t dmk_stokes_eval_adjoint(dmk_stokes_plan_t plan, const double* d_f, 
  * times each `repeats` times on `stream` with CUDA events after one untimed
  * run, and returns the median times in h_ms[n_cand] (may be NULL) and the
  * index of the fastest in *h_best.  The leaf capacity sets the tree: for
- * components = DMK_COMPONENTS_ALL it sets the uniform level of the Ewald split
- * (the smallest level with at most that many points per box), i.e. the
- * balance between the near pass and the Fourier part; for the near component
- * alone the smallest leaves always win (the far field that balances them in
- * the DMK method is not part of that component).  d_u receives the velocity of
- * the last run.  Host-synchronises. */
+ * components = DMK_COMPONENTS_ALL it sets the balance between the near pass
+ * (work per target grows with n_s) and the far field (work per box); for
+ * DMK_COMPONENTS_EWALD it sets the uniform level of the Ewald split (the
+ * smallest level with at most that many points per box), i.e. the balance
+ * between the near pass and the Fourier part; for the near component alone
+ * the smallest leaves always win (the far field that balances them is not part
+ * of that component).  d_u receives the velocity of the last run.
+ * Host-synchronises. */
 dmk_status_t dmk_stokes_autotune(const dmk_stokes_opts_t* opts, int64_t n_src, const double* d_src,
                                  const double* d_f, const double* d_g, const double* d_n, double* d_u,
                                  int32_t n_cand, const int32_t* h_leaf_capacity, int32_t repeats, void* stream,
                                  double* h_ms, int32_t* h_best);
+
+/* Far-field sizes of a components = DMK_COMPONENTS_ALL plan (host values):
+ *   info[0] proxy order p, [1] plane-wave modes a side N1, [2] root modes a
+ *   side, [3] boxes of the tree (all levels), [4] boxes holding sources,
+ *   [5] boxes holding targets, [6] finest level, [7] 1 if the far field runs
+ *   in float32, 0 in float64.  All zero for other plans. */
+dmk_status_t dmk_stokes_far_info(dmk_stokes_plan_t plan, int32_t info[8]);
 
 /* Synchronises the plan's last stream and returns the latched device status
  * (DMK_OK, DMK_ERR_OUT_OF_RANGE, DMK_ERR_INVALID_ARG for a non-finite point). */

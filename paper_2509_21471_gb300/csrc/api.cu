@@ -29,8 +29,9 @@ dmk_status_t validate_opts(const dmk_stokes_opts_t* o, std::string& msg) {
   if (o->periodic != 0 && o->periodic != 1) { msg = "periodic must be 0 or 1"; return DMK_ERR_INVALID_ARG; }
   if (o->kernels < 1 || o->kernels > 3) { msg = "kernels must be a nonzero mask of 1|2"; return DMK_ERR_INVALID_ARG; }
   if (o->precision != 0 && o->precision != 1) { msg = "precision must be 0 or 1"; return DMK_ERR_INVALID_ARG; }
-  if (o->components != DMK_COMPONENTS_ALL && o->components != DMK_COMPONENTS_NEAR) {
-    msg = "components must be 0 or 1";
+  if (o->components != DMK_COMPONENTS_ALL && o->components != DMK_COMPONENTS_NEAR &&
+      o->components != DMK_COMPONENTS_EWALD) {
+    msg = "components must be 0, 1 or 2";
     return DMK_ERR_INVALID_ARG;
   }
   if (o->leaf_capacity < 0 || o->leaf_capacity > (1 << 20)) { msg = "leaf_capacity out of range"; return DMK_ERR_INVALID_ARG; }
@@ -45,10 +46,13 @@ dmk_status_t validate_opts(const dmk_stokes_opts_t* o, std::string& msg) {
   }
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(o->box_lo[a])) { msg = "box_lo not finite"; return DMK_ERR_INVALID_ARG; }
-  if (o->components == DMK_COMPONENTS_ALL &&
+  if (o->components == DMK_COMPONENTS_EWALD &&
       !(o->periodic == 1 && o->dim == 3 && o->kernels == DMK_KERNEL_STOKESLET && o->n_rhs == 1)) {
-    msg = "components = DMK_COMPONENTS_ALL is provided for the periodic 3D Stokeslet (single-level Ewald split) "
-          "with one force column";
+    msg = "components = DMK_COMPONENTS_EWALD is provided for the periodic 3D Stokeslet with one force column";
+    return DMK_ERR_UNSUPPORTED;
+  }
+  if (o->components == DMK_COMPONENTS_ALL && !(o->dim == 3 && o->n_rhs == 1)) {
+    msg = "components = DMK_COMPONENTS_ALL (the DMK far field) is provided in 3D with one force column";
     return DMK_ERR_UNSUPPORTED;
   }
   if (o->n_rhs != 1 && (o->kernels & DMK_KERNEL_STRESSLET)) {
@@ -139,6 +143,7 @@ void configure_pool(int dev) {
 
 void release(dmk::Plan& p) {
   dmk::ewald_free(p);
+  dmk::far_free(p);
   if (p.aux) cudaFreeAsync(p.aux, p.stream);
   p.aux = nullptr;
   p.aux_bytes = 0;
@@ -167,8 +172,10 @@ dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64
   if (N >= (int64_t(1) << 31)) return set_err(nullptr, DMK_ERR_INVALID_ARG, "too many points (>= 2^31)");
   if (N > 0 && !d_src) return set_err(nullptr, DMK_ERR_INVALID_ARG, "d_src is NULL");
   if (d_trg && n_sys != 1) return set_err(nullptr, DMK_ERR_UNSUPPORTED, "separate targets need a single system");
-  if (opts && opts->components == DMK_COMPONENTS_ALL && (n_sys != 1 || d_trg))
-    return set_err(nullptr, DMK_ERR_UNSUPPORTED, "components = ALL needs a single system, targets = sources");
+  if (opts && opts->components == DMK_COMPONENTS_EWALD && (n_sys != 1 || d_trg))
+    return set_err(nullptr, DMK_ERR_UNSUPPORTED, "components = EWALD needs a single system, targets = sources");
+  if (opts && opts->components == DMK_COMPONENTS_ALL && n_sys != 1)
+    return set_err(nullptr, DMK_ERR_UNSUPPORTED, "components = ALL needs a single system");
   if (d_trg && (n_trg < 0 || n_trg >= (int64_t(1) << 31)))
     return set_err(nullptr, DMK_ERR_INVALID_ARG, "n_trg out of range");
 
@@ -187,7 +194,7 @@ dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64
       throw dmk::Error{DMK_ERR_UNSUPPORTED, "kernel tables could not be built for this dimension"};
     p.leaf_capacity = opts->leaf_capacity > 0 ? opts->leaf_capacity
                                               : dmk::leaf_capacity_for_eps(opts->eps, opts->dim);
-    if (opts->components == DMK_COMPONENTS_ALL) p.uniform_level = dmk::ewald_level(N, opts->leaf_capacity);
+    if (opts->components == DMK_COMPONENTS_EWALD) p.uniform_level = dmk::ewald_level(N, opts->leaf_capacity);
     p.tree.N = N;
     p.tree.n_sys = n_sys;
     // one arena block for the tree (~80 bytes per point) and the evaluation workspace
@@ -201,6 +208,7 @@ dmk_status_t make_plan(const dmk_stokes_opts_t* opts, int32_t n_sys, const int64
     dmk::build_tree(p, d_src, h_offsets);
     if (d_trg) dmk::build_targets(p, d_trg, n_trg);
     if (p.uniform_level > 0) dmk::ewald_setup(p, p.uniform_level);
+    if (opts->components == DMK_COMPONENTS_ALL) dmk::far_setup(p);
     p.fsorted = p.arena.alloc<char>(p.fsorted_bytes);
     p.reduce_buf = p.arena.alloc<double>(4 * n_sys);
     DMK_CUDA_TRY(cudaGetLastError());
@@ -284,11 +292,13 @@ static dmk_status_t run_eval(dmk_stokes_plan_t plan, const double* d_f, const do
   if (NT > 0 && !d_u && !d_gradu) return set_err(plan, DMK_ERR_INVALID_ARG, "d_u is NULL");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   plan->last_stream = s;
-  if (p.ewald && d_gradu) return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient of components = ALL is not provided");
+  if ((p.ewald || p.far) && d_gradu)
+    return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient of components = ALL / EWALD is not provided");
   try {
     if (d_gradu && N > 0) ensure_aux(plan, dmk::aux_bytes_grad(p.opts, N));
     dmk::launch_near(p, want_s ? d_f : nullptr, want_t ? d_g : nullptr, want_t ? d_n : nullptr, d_u, d_gradu, s);
     if (p.ewald && d_u) dmk::ewald_far(p, d_f, d_u, s);   // + the Fourier part (Ewald far field)
+    if (p.far && d_u) dmk::far_run(p, want_s ? d_f : nullptr, want_t ? d_g : nullptr, want_t ? d_n : nullptr, d_u, s);
   } catch (const dmk::Error& e) {
     return set_err(plan, e.code, e.msg);
   }
@@ -322,7 +332,7 @@ dmk_status_t dmk_stokes_eval_adjoint(dmk_stokes_plan_t plan, const double* d_f, 
     return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint is provided for the Stokeslet only");
   if (p.opts.n_rhs != 1) return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint is provided for n_rhs = 1");
   if (p.tree.sep) return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint is provided for targets = sources");
-  if (p.ewald) return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint of components = ALL is not provided");
+  if (p.ewald || p.far) return set_err(plan, DMK_ERR_UNSUPPORTED, "the adjoint of components = ALL / EWALD is not provided");
   const int64_t N = p.tree.N;
   if (N > 0 && (!d_f || !d_w || !d_v || !d_gx))
     return set_err(plan, DMK_ERR_INVALID_ARG, "d_f, d_w, d_v and d_gx are required");
@@ -376,6 +386,13 @@ dmk_status_t dmk_stokes_autotune(const dmk_stokes_opts_t* opts, int64_t n_src, c
   cudaEventDestroy(e1);
   if (st != DMK_OK) return st;
   *h_best = static_cast<int32_t>(std::min_element(med.begin(), med.end()) - med.begin());
+  return DMK_OK;
+}
+
+dmk_status_t dmk_stokes_far_info(dmk_stokes_plan_t plan, int32_t info[8]) {
+  if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
+  if (!info) return set_err(plan, DMK_ERR_INVALID_ARG, "info is NULL");
+  dmk::far_info(plan->p, info);
   return DMK_OK;
 }
 

@@ -229,12 +229,14 @@ int32_t* pinned_slot();
 void pinned_release(int32_t* slot);
 
 struct EwaldState;
+struct FarState;
 
 struct Plan {
   dmk_stokes_opts_t opts{};
   int leaf_capacity = 0;
   int uniform_level = 0;       // > 0: every leaf at this level (single-level Ewald split)
-  EwaldState* ewald = nullptr; // far field of components = ALL (periodic 3D Stokeslet)
+  EwaldState* ewald = nullptr; // far field of components = EWALD (periodic 3D Stokeslet)
+  FarState* far = nullptr;     // DMK far field of components = ALL (3D)
   cudaStream_t stream = nullptr;
   int device = 0;
   KernelTables tables;
@@ -276,7 +278,15 @@ void launch_near_ws(const Plan& p, const double* d_f, const double* d_g, const d
 size_t eval_workspace_bytes(const dmk_stokes_opts_t& o, int64_t N, int64_t NT);
 size_t aux_bytes_grad(const dmk_stokes_opts_t& o, int64_t N);
 size_t aux_bytes_adjoint(const dmk_stokes_opts_t& o, int64_t N);
-// ewald.cu: the single-level PSWF Ewald far field (components = ALL, periodic 3D Stokeslet)
+// Gauss-Legendre nodes and weights on [-1, 1]
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+// far.cu: the DMK far field (components = ALL, 3D): proxy charges, plane waves, root, interpolation
+void far_setup(Plan& p);
+void far_free(Plan& p);
+void far_run(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u, cudaStream_t s);
+void far_info(const Plan& p, int32_t info[8]);
+size_t far_bytes(const Plan& p);
+// ewald.cu: the single-level PSWF Ewald far field (components = EWALD, periodic 3D Stokeslet)
 int ewald_level(int64_t N, int ns);
 void ewald_setup(Plan& p, int L);
 void ewald_free(Plan& p);

@@ -69,6 +69,8 @@ int fft_size(int lo) {
   }
 }
 
+}  // namespace
+
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton on P_n)
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
@@ -98,6 +100,8 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
     w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
   }
 }
+
+namespace {
 
 // ---------------------------------------------------------------- kernels
 // ES kernel weights of one coordinate: the w grid points g0 .. g0 + w - 1

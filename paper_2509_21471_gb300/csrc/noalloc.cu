@@ -92,7 +92,7 @@ extern "C" dmk_status_t dmk_stokes_eval_noalloc(dmk_stokes_plan_t plan, const do
                              "dmk_stokes_eval_noalloc: this plan needs " + std::to_string(ws + red) +
                                  " bytes of scratch; the static scratch holds " +
                                  std::to_string(dmk::kNoAllocScratchBytes) + " bytes (use dmk_stokes_eval)");
-  if (p.ewald)
+  if (p.ewald || p.far)
     return dmk::record_error(plan, DMK_ERR_UNSUPPORTED,
                              "dmk_stokes_eval_noalloc evaluates the near component only (components = NEAR)");
   int dev = -1;

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "DMK_OK", 1: "DMK_ERR_INVALID_ARG", 2: "DMK_ERR_OUT_OF_RANGE"
                 4: "DMK_ERR_NOMEM", 5: "DMK_ERR_CUDA", 6: "DMK_ERR_TIMEOUT", 7: "DMK_ERR_BAD_PLAN"}
 STOKESLET, STRESSLET = 1, 2
 FP64, MIXED = 0, 1
-ALL, NEAR = 0, 1
+ALL, NEAR, EWALD = 0, 1, 2
 
 
 class DMKError(RuntimeError):
@@ -57,6 +57,7 @@ _lib.dmk_stokes_halo_leaves.argtypes = [ctypes.c_int32, _P, _P, ctypes.c_int32, 
                                         _P]
 _lib.dmk_stokes_autotune.argtypes = [ctypes.POINTER(Opts), ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_int32, _P,
                                      ctypes.c_int32, _P, _P, _P]
+_lib.dmk_stokes_far_info.argtypes = [_P, _P]
 _lib.dmk_stokes_destroy.argtypes = [_P]
 _lib.dmk_stokes_destroy.restype = None
 _lib.dmk_stokes_last_error.argtypes = [_P]
@@ -71,8 +72,8 @@ for _name in ("dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "
 EXPORTED = ["dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
             "dmk_stokes_eval_grad", "dmk_stokes_eval_adjoint",
             "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree", "dmk_stokes_kernel_table",
-            "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves", "dmk_stokes_autotune", "dmk_stokes_destroy",
-            "dmk_stokes_last_error"]
+            "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves", "dmk_stokes_autotune", "dmk_stokes_far_info",
+            "dmk_stokes_destroy", "dmk_stokes_last_error"]
 
 
 def _check(code, handle=None):
@@ -206,6 +207,13 @@ class Plan:
         _check(_lib.dmk_stokes_plan_stats(self._h, ctypes.cast(s, ctypes.c_void_p)), self._h)
         keys = ["leaves", "max_level", "near_entries", "tiles", "issued_pairs", "three_c_over_pi",
                 "leaf_capacity", "points", "useful_pairs", "launches"]
+        return dict(zip(keys, [int(v) for v in s]))
+
+    def far_info(self):
+        """Far-field sizes of a components=ALL plan (zeros otherwise)."""
+        s = (ctypes.c_int32 * 8)()
+        _check(_lib.dmk_stokes_far_info(self._h, ctypes.cast(s, ctypes.c_void_p)), self._h)
+        keys = ["p", "n1", "root_modes", "boxes", "source_boxes", "target_boxes", "max_level", "fp32"]
         return dict(zip(keys, [int(v) for v in s]))
 
     def tree(self):

@@ -1,4 +1,4 @@
-"""components = ALL of a periodic 3D Stokeslet plan: the single-level PSWF
+"""components = EWALD of a periodic 3D Stokeslet plan: the single-level PSWF
 Ewald sum (Sec. 5.3, Eqs. (ewald_local), (ewald_far); the fast Ewald version
 of Sec. 8): near pass on a uniform tree at scale nu plus the Fourier part by a
 non-uniform FFT, against the oracle.
@@ -33,7 +33,7 @@ def dmk(dmk_lib):
 
 def _gpu_total(dmk, x, f, eps, prec, ns):
     p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=eps, periodic=True, precision=prec, leaf_capacity=ns,
-                 components=dmk.ALL)
+                 components=dmk.EWALD)
     u = p.eval(torch.as_tensor(f, device="cuda")).cpu().numpy()
     p.sync_status()
     st = p.stats()
@@ -74,10 +74,10 @@ def test_ewald_total_matches_gaussian_ewald(dmk, eps):
 
 def test_components_all_limits(dmk):
     x = torch.as_tensor(wl.uniform_points(np.random.default_rng(3), 500, 3), device="cuda")
-    with pytest.raises(dmk.DMKError) as ei:                # free space: the DMK far field is not provided
-        dmk.Plan(x, eps=1e-6, periodic=False, components=dmk.ALL)
+    with pytest.raises(dmk.DMKError) as ei:                # the Ewald split is periodic only
+        dmk.Plan(x, eps=1e-6, periodic=False, components=dmk.EWALD)
     assert ei.value.code == 3
-    p = dmk.Plan(x, eps=1e-6, periodic=True, components=dmk.ALL)
+    p = dmk.Plan(x, eps=1e-6, periodic=True, components=dmk.EWALD)
     f = torch.zeros((500, 3), dtype=torch.float64, device="cuda")
     with pytest.raises(dmk.DMKError) as ei:
         p.eval_grad(f)
@@ -100,7 +100,7 @@ def test_bandlimit_override_table2_rows(dmk):
     errs = {}
     for c3 in (6, 10, 17, 25):
         p = dmk.Plan(torch.as_tensor(x, device="cuda"), eps=1e-12, periodic=True, precision=0, leaf_capacity=20,
-                     components=dmk.ALL, bandlimit=c3)
+                     components=dmk.EWALD, bandlimit=c3)
         errs[c3] = rel_l2(p.eval(torch.as_tensor(f, device="cuda")).cpu().numpy(), u_ref)
         p.close()
     assert errs[6] > errs[10] > errs[17] > errs[25]
@@ -116,12 +116,12 @@ def test_autotune_picks_the_fastest_candidate(dmk):
     x = torch.as_tensor(wl.uniform_points(rng, N, 3), device="cuda")
     f = torch.as_tensor(wl.forces(rng, N, 3, zero_mean=True), device="cuda")
     best, times = dmk.autotune(x, f, candidates=(300, 3000, 30000), repeats=2, eps=1e-6, periodic=True,
-                               precision=dmk.MIXED, components=dmk.ALL)
+                               precision=dmk.MIXED, components=dmk.EWALD)
     assert set(times) == {300, 3000, 30000} and all(t > 0 for t in times.values())
     assert times[best] == min(times.values())
     levels = set()
     for ns in times:
-        p = dmk.Plan(x, eps=1e-6, periodic=True, precision=dmk.MIXED, components=dmk.ALL, leaf_capacity=ns)
+        p = dmk.Plan(x, eps=1e-6, periodic=True, precision=dmk.MIXED, components=dmk.EWALD, leaf_capacity=ns)
         levels.add(p.stats()["max_level"])
         p.close()
     assert levels == {1, 2, 3}                                   # three different splits
