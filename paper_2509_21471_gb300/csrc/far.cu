@@ -46,7 +46,7 @@ namespace dmk {
 namespace {
 
 constexpr int kMaxP = 64;          // proxy order and mode counts a side (Table 2 needs <= 63)
-constexpr int kRotTile = 32;       // rest columns per k_rot block
+constexpr int kRotTile = 64;       // rest columns per k_rot block
 constexpr int kRotThreads = 256;
 constexpr double kRTrunc = 2.7320508075688772;   // R = 1 + sqrt(3), Eq. (Btrunc_hat)
 
@@ -58,22 +58,46 @@ template <typename R> struct Cplx;
 template <> struct Cplx<float> { using T = float2; };
 template <> struct Cplx<double> { using T = double2; };
 
-// one stage of a separable transform: Y[r][m] (=, +=, = Re, += Re) sum_j A[m][j] X[j][r]
-// over the job's one or two inputs (the second with the second matrix), r < rest
+// one stage of a separable transform: Y[r][m] (=, +=) sum_j A[m][j] X[j][r] over the
+// job's one or two inputs (the second with the second matrix), r < rest; complex
+// arithmetic when X or A is complex, and the real part kept when Y is real
 struct RotJob {
   int64_t x0, x1;   // element offsets into the launch's X base (x1 < 0: none; x0 < 0: zero input)
   int64_t y;        // element offset into the Y base
   int32_t a0, a1;   // matrix of each input (0 or 1)
 };
 
-// shared-memory sub-arrays of k_rot start on 16-byte boundaries
+// shared memory of k_rot: A transposed [nmat][n_in][n4] (n4 = n_out rounded up to 4,
+// zero padded), X [nmat][n_in][kRotTile], Y [kRotTile][n_out]; each part 16-byte aligned
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 __host__ __device__ inline void rot_smem_layout(size_t bytesA, size_t bytesX, size_t* offX, size_t* offY) {
   *offX = align16(bytesA);
   *offY = *offX + align16(bytesX);
 }
 
-// MODE 0: write, 1: accumulate (for YC == false with complex arithmetic: the real part)
+// four consecutive entries from 16-byte aligned shared memory
+__device__ __forceinline__ void ld4(const float* p, float* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* v) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void ld4(const float2* p, float2* v) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  const float4 b = *reinterpret_cast<const float4*>(p + 2);
+  v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void ld4(const double2* p, double2* v) {
+  v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
+}
+
+// MODE 0: write, 1: accumulate.  Each thread owns a 4 x 4 register tile: four
+// consecutive columns r and four consecutive rows m; blockDim = 16 * (n4 / 4)
+// rounded up to a warp multiple.
 template <typename R, bool XC, bool AC, bool YC, int MODE>
 __global__ void __launch_bounds__(kRotThreads) k_rot(const RotJob* __restrict__ jobs, const void* __restrict__ Xb,
                                                      void* __restrict__ Yb, int64_t xoff, int64_t yoff,
@@ -87,16 +111,20 @@ __global__ void __launch_bounds__(kRotThreads) k_rot(const RotJob* __restrict__ 
   const RotJob J = jobs[blockIdx.x];
   const int r0 = blockIdx.y * kRotTile;
   if (r0 >= rest) return;
-  const int ninp = J.x1 >= 0 ? 2 : 1;
   const int nmat = two_mats ? 2 : 1;
+  const int ninp = (J.x1 >= 0 && two_mats) ? 2 : 1;
+  const int n4 = (n_out + 3) & ~3;
   size_t offX, offY;
-  rot_smem_layout(nmat * n_out * n_in * sizeof(TA), 2 * n_in * kRotTile * sizeof(TX), &offX, &offY);
-  TA* sA = reinterpret_cast<TA*>(smem);                                        // [nmat][n_out][n_in]
-  TX* sX = reinterpret_cast<TX*>(smem + offX);                                 // [2][n_in][kRotTile]
+  rot_smem_layout(nmat * n_in * n4 * sizeof(TA), nmat * n_in * kRotTile * sizeof(TX), &offX, &offY);
+  TA* sA = reinterpret_cast<TA*>(smem);                                        // [nmat][n_in][n4]
+  TX* sX = reinterpret_cast<TX*>(smem + offX);                                 // [nmat][n_in][kRotTile]
   TY* sY = reinterpret_cast<TY*>(smem + offY);                                 // [kRotTile][n_out]
-  for (int i = threadIdx.x; i < nmat * n_out * n_in; i += blockDim.x) {
-    const int which = i / (n_out * n_in), e = i - which * n_out * n_in;
-    sA[i] = (which == 0 ? static_cast<const TA*>(A0) : static_cast<const TA*>(A1))[e];
+  for (int i = threadIdx.x; i < nmat * n_in * n4; i += blockDim.x) {
+    const int which = i / (n_in * n4), e = i - which * n_in * n4;
+    const int j = e / n4, m = e - j * n4;
+    TA v{};
+    if (m < n_out) v = (which == 0 ? static_cast<const TA*>(A0) : static_cast<const TA*>(A1))[m * n_in + j];
+    sA[i] = v;
   }
   const int ncol = min(kRotTile, rest - r0);
   for (int k = 0; k < ninp; ++k) {
@@ -104,52 +132,65 @@ __global__ void __launch_bounds__(kRotThreads) k_rot(const RotJob* __restrict__ 
     const TX* X = static_cast<const TX*>(Xb) + xoff + xo;
     for (int i = threadIdx.x; i < n_in * kRotTile; i += blockDim.x) {
       const int j = i / kRotTile, c = i - j * kRotTile;
-      TX v;
-      if constexpr (XC) {
-        v.x = R(0);
-        v.y = R(0);
-      } else {
-        v = R(0);
-      }
+      TX v{};
       if (xo >= 0 && c < ncol) v = X[static_cast<int64_t>(j) * rest + r0 + c];
       sX[k * n_in * kRotTile + i] = v;
     }
   }
   __syncthreads();
-  const int c = threadIdx.x & (kRotTile - 1);
-  for (int m = threadIdx.x / kRotTile; m < n_out; m += blockDim.x / kRotTile) {
-    R ar = R(0), ai = R(0);
+  const int cq = threadIdx.x & 15, mc = threadIdx.x >> 4;
+  if (mc < n4 / 4) {
+    R ar[4][4], ai[4][4];        // [column][row]
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) ar[u][i] = ai[u][i] = R(0);
     for (int k = 0; k < ninp; ++k) {
       const int am = (k == 0 ? J.a0 : J.a1);
-      const TA* Am = sA + (am * n_out + m) * n_in;
-      const TX* Xk = sX + k * n_in * kRotTile + c;
+      const TA* Ak = sA + am * n_in * n4 + 4 * mc;
+      const TX* Xk = sX + k * n_in * kRotTile + 4 * cq;
       for (int j = 0; j < n_in; ++j) {
-        const TA a = Am[j];
-        const TX x = Xk[j * kRotTile];
-        if constexpr (AC && XC) {
-          ar = fma(a.x, x.x, ar);
-          ar = fma(-a.y, x.y, ar);
-          ai = fma(a.x, x.y, ai);
-          ai = fma(a.y, x.x, ai);
-        } else if constexpr (AC) {
-          ar = fma(a.x, x, ar);
-          ai = fma(a.y, x, ai);
-        } else if constexpr (XC) {
-          ar = fma(a, x.x, ar);
-          ai = fma(a, x.y, ai);
-        } else {
-          ar = fma(a, x, ar);
-        }
+        TA a[4];
+        TX x[4];
+        ld4(Ak + j * n4, a);
+        ld4(Xk + j * kRotTile, x);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            if constexpr (AC && XC) {
+              ar[u][i] = fma(a[i].x, x[u].x, ar[u][i]);
+              ar[u][i] = fma(-a[i].y, x[u].y, ar[u][i]);
+              ai[u][i] = fma(a[i].x, x[u].y, ai[u][i]);
+              ai[u][i] = fma(a[i].y, x[u].x, ai[u][i]);
+            } else if constexpr (AC) {
+              ar[u][i] = fma(a[i].x, x[u], ar[u][i]);
+              ai[u][i] = fma(a[i].y, x[u], ai[u][i]);
+            } else if constexpr (XC) {
+              ar[u][i] = fma(a[i], x[u].x, ar[u][i]);
+              ai[u][i] = fma(a[i], x[u].y, ai[u][i]);
+            } else {
+              ar[u][i] = fma(a[i], x[u], ar[u][i]);
+            }
+          }
       }
     }
-    TY out;
-    if constexpr (YC) {
-      out.x = ar;
-      out.y = ai;
-    } else {
-      out = ar;
-    }
-    sY[c * n_out + m] = out;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int m = 4 * mc + i, c = 4 * cq + u;
+        if (m < n_out) {
+          TY out;
+          if constexpr (YC) {
+            out.x = ar[u][i];
+            out.y = ai[u][i];
+          } else {
+            out = ar[u][i];
+          }
+          sY[c * n_out + m] = out;
+        }
+      }
   }
   __syncthreads();
   TY* Y = static_cast<TY*>(Yb) + yoff + J.y + static_cast<int64_t>(r0) * n_out;
@@ -170,126 +211,148 @@ __global__ void __launch_bounds__(kRotThreads) k_rot(const RotJob* __restrict__ 
 }
 
 // Lagrange basis at the Chebyshev points of the first kind in barycentric form
-// (weights (-1)^j sin((2j+1) pi / 2p)); exact at a node
+// (weights (-1)^j sin((2j+1) pi / 2p)), in the far field's precision; exact at a
+// node; out[j * stride] for j < pad (zero past p)
 template <typename R>
-__device__ inline void lagrange_row(double t, int p, const double* nodes, const double* bw, R* out, int stride = 1) {
-  double s = 0.0;
+__device__ inline void lagrange_row(R t, int p, const R* nodes, const R* bw, R* out, int stride, int pad) {
+  R s = R(0);
   int hit = -1;
   for (int j = 0; j < p; ++j) {
-    const double d = t - nodes[j];
-    if (d == 0.0) hit = j;
+    const R d = t - nodes[j];
+    if (d == R(0)) hit = j;
     else s += bw[j] / d;
   }
-  for (int j = 0; j < p; ++j) {
-    double v;
-    if (hit >= 0) v = (j == hit) ? 1.0 : 0.0;
-    else v = (bw[j] / (t - nodes[j])) / s;
-    out[j * stride] = static_cast<R>(v);
+  const R inv = hit >= 0 ? R(0) : R(1) / s;
+  for (int j = 0; j < pad; ++j) {
+    R v = R(0);
+    if (j < p) v = hit >= 0 ? (j == hit ? R(1) : R(0)) : (bw[j] / (t - nodes[j])) * inv;
+    out[j * stride] = v;
+  }
+}
+
+// padded proxy order: the Lagrange rows and grid rows of the leaf kernels are PB
+// long (zeros past p), PB a multiple of the c-chunk of the anterpolation (24 in
+// float32, 12 in float64)
+template <typename R> constexpr int ant_chunk() { return sizeof(R) == 4 ? 24 : 12; }
+constexpr int kAntChunk = 32;
+constexpr int kAntThreads = 544;
+
+// Lagrange weights of every point of the listed leaves, once per evaluation:
+// W[s][axis][PB] in sorted point order
+template <typename R>
+__global__ void k_far_weights(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
+                              const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ leaf_count,
+                              const double* __restrict__ w, int64_t N, const BoxGeo* __restrict__ box_geo, int p, int PB,
+                              const R* __restrict__ nodes, const R* __restrict__ bw, R* __restrict__ W) {
+  __shared__ R s_nodes[kMaxP], s_bw[kMaxP];
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    s_nodes[j] = nodes[j];
+    s_bw[j] = bw[j];
+  }
+  __syncthreads();
+  const int li = leaf_list[blockIdx.x];
+  const BoxGeo geo = box_geo[leaf_box[blockIdx.x]];
+  const int s0 = leaf_start[li], ns = leaf_count[li];
+  const double inv_half = 1.0 / geo.w;             // a power of two
+  for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) {
+    const int sl = i / 3, ax = i - 3 * sl;
+    const int64_t si = s0 + sl;
+    const double ctr = ax == 0 ? geo.x : (ax == 1 ? geo.y : geo.z);
+    const R t = static_cast<R>((w[ax * N + si] - ctr) * inv_half);
+    lagrange_row<R>(t, p, s_nodes, s_bw, W + (si * 3 + ax) * PB, 1, PB);
   }
 }
 
 // leaf proxy charges: q[box][slot+k][a][b][c] = sum_s L_a(x_s) L_b(y_s) L_c(z_s) v_s,k
 // for the three components of group grp0 + blockIdx.y (0: f; 1: rho_00, rho_11,
-// rho_22; 2: rho_01, rho_02, rho_12 of the symmetric part of g (x) n)
-constexpr int kAntChunk = 32;
-constexpr int kAntC = 8;
+// rho_22; 2: rho_01, rho_02, rho_12 of the symmetric part of g (x) n).  A thread owns
+// one (a, b) and a chunk of consecutive c; the leaf's weights stream through shared
+// memory 32 sources at a time.
 template <typename R>
-__global__ void __launch_bounds__(256) k_far_anterp(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
-                                                    const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ leaf_count,
-                                                    const double* __restrict__ w, int64_t N, const int32_t* __restrict__ perm,
-                                                    const BoxGeo* __restrict__ box_geo, const double* __restrict__ f,
-                                                    const double* __restrict__ g, const double* __restrict__ nrm, int grp0,
-                                                    int slot_f, int slot_t, int ncomp, R* __restrict__ q, int p,
-                                                    const double* __restrict__ nodes, const double* __restrict__ bw) {
+__global__ void __launch_bounds__(kAntThreads) k_far_anterp(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
+                                                            const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ leaf_count,
+                                                            const R* __restrict__ W, const int32_t* __restrict__ perm,
+                                                            const double* __restrict__ f, const double* __restrict__ g,
+                                                            const double* __restrict__ nrm, int grp0, int slot_f, int slot_t,
+                                                            int ncomp, R* __restrict__ q, int p, int PB) {
+  constexpr int CB = ant_chunk<R>();
   extern __shared__ __align__(16) unsigned char smem[];
-  R* sW = reinterpret_cast<R*>(smem);                          // [3][kAntChunk][p]
-  R* sV = sW + 3 * kAntChunk * p;                              // [kAntChunk][3]
-  __shared__ double s_nodes[kMaxP], s_bw[kMaxP];
+  R* sW = reinterpret_cast<R*>(smem);                          // [kAntChunk][3][PB]
+  R* sV = sW + kAntChunk * 3 * PB;                             // [kAntChunk][4]
   const int li = leaf_list[blockIdx.x];
   const int box = leaf_box[blockIdx.x];
   const int grp = grp0 + blockIdx.y;
   const int slot = grp == 0 ? slot_f : slot_t + 3 * (grp - 1);
-  for (int j = threadIdx.x; j < p; j += blockDim.x) {
-    s_nodes[j] = nodes[j];
-    s_bw[j] = bw[j];
-  }
-  const BoxGeo geo = box_geo[box];                            // centre x, y, z, half side
   const int s0 = leaf_start[li], ns = leaf_count[li];
-  const int nchunk = (p + kAntC - 1) / kAntC;
+  const int nchunk = PB / CB;
   const int ntask = p * p * nchunk;
   const int64_t p3 = static_cast<int64_t>(p) * p * p;
   R* qb = q + (static_cast<int64_t>(box) * ncomp + slot) * p3;
-  __syncthreads();
   for (int t0 = 0; t0 < ntask; t0 += blockDim.x) {
     const int task = t0 + threadIdx.x;
     const bool on = task < ntask;
     const int a = on ? task / (p * nchunk) : 0;
     const int rem = on ? task - a * p * nchunk : 0;
     const int b = rem / nchunk;
-    const int c0 = (rem - b * nchunk) * kAntC;
-    R acc[kAntC][3];
+    const int c0 = (rem - b * nchunk) * CB;
+    R acc[CB][3];
 #pragma unroll
-    for (int cc = 0; cc < kAntC; ++cc) acc[cc][0] = acc[cc][1] = acc[cc][2] = R(0);
+    for (int cc = 0; cc < CB; ++cc) acc[cc][0] = acc[cc][1] = acc[cc][2] = R(0);
     for (int sc = 0; sc < ns; sc += kAntChunk) {
       const int nc = min(kAntChunk, ns - sc);
       __syncthreads();
-      for (int i = threadIdx.x; i < 3 * kAntChunk; i += blockDim.x) {
-        const int ax = i / kAntChunk, sl = i - ax * kAntChunk;
-        R* dst = sW + (ax * kAntChunk + sl) * p;
-        if (sl < nc) {
-          const int64_t si = s0 + sc + sl;
-          const double ctr = ax == 0 ? geo.x : (ax == 1 ? geo.y : geo.z);
-          lagrange_row<R>((w[ax * N + si] - ctr) / geo.w, p, s_nodes, s_bw, dst);
+      const R* src = W + (static_cast<int64_t>(s0) + sc) * 3 * PB;
+      for (int i = threadIdx.x; i < nc * 3 * PB; i += blockDim.x) sW[i] = src[i];
+      for (int sl = threadIdx.x; sl < nc; sl += blockDim.x) {
+        double v0, v1, v2;
+        const int64_t o = perm[s0 + sc + sl];
+        if (grp == 0) {
+          v0 = f[o * 3];
+          v1 = f[o * 3 + 1];
+          v2 = f[o * 3 + 2];
         } else {
-          for (int j = 0; j < p; ++j) dst[j] = R(0);
-        }
-      }
-      for (int sl = threadIdx.x; sl < kAntChunk; sl += blockDim.x) {
-        double v0 = 0, v1 = 0, v2 = 0;
-        if (sl < nc) {
-          const int64_t o = perm[s0 + sc + sl];
-          if (grp == 0) {
-            v0 = f[o * 3];
-            v1 = f[o * 3 + 1];
-            v2 = f[o * 3 + 2];
+          const double g0 = g[o * 3], g1 = g[o * 3 + 1], g2 = g[o * 3 + 2];
+          const double n0 = nrm[o * 3], n1 = nrm[o * 3 + 1], n2 = nrm[o * 3 + 2];
+          if (grp == 1) {
+            v0 = g0 * n0;
+            v1 = g1 * n1;
+            v2 = g2 * n2;
           } else {
-            const double g0 = g[o * 3], g1 = g[o * 3 + 1], g2 = g[o * 3 + 2];
-            const double n0 = nrm[o * 3], n1 = nrm[o * 3 + 1], n2 = nrm[o * 3 + 2];
-            if (grp == 1) {
-              v0 = g0 * n0;
-              v1 = g1 * n1;
-              v2 = g2 * n2;
-            } else {
-              v0 = 0.5 * (g0 * n1 + g1 * n0);
-              v1 = 0.5 * (g0 * n2 + g2 * n0);
-              v2 = 0.5 * (g1 * n2 + g2 * n1);
-            }
+            v0 = 0.5 * (g0 * n1 + g1 * n0);
+            v1 = 0.5 * (g0 * n2 + g2 * n0);
+            v2 = 0.5 * (g1 * n2 + g2 * n1);
           }
         }
-        sV[sl * 3] = static_cast<R>(v0);
-        sV[sl * 3 + 1] = static_cast<R>(v1);
-        sV[sl * 3 + 2] = static_cast<R>(v2);
+        sV[sl * 4] = static_cast<R>(v0);
+        sV[sl * 4 + 1] = static_cast<R>(v1);
+        sV[sl * 4 + 2] = static_cast<R>(v2);
+        sV[sl * 4 + 3] = R(0);
       }
       __syncthreads();
       if (on) {
         for (int sl = 0; sl < nc; ++sl) {
-          const R wab = sW[sl * p + a] * sW[(kAntChunk + sl) * p + b];
-          const R* wc = sW + (2 * kAntChunk + sl) * p;
-          const R f0 = sV[sl * 3], f1 = sV[sl * 3 + 1], f2 = sV[sl * 3 + 2];
+          const R* ws = sW + sl * 3 * PB;
+          const R wab = ws[a] * ws[PB + b];
+          R fv[4];
+          ld4(sV + sl * 4, fv);
 #pragma unroll
-          for (int cc = 0; cc < kAntC; ++cc) {
-            const int ci = c0 + cc;
-            const R wv = ci < p ? wab * wc[ci] : R(0);
-            acc[cc][0] = fma(wv, f0, acc[cc][0]);
-            acc[cc][1] = fma(wv, f1, acc[cc][1]);
-            acc[cc][2] = fma(wv, f2, acc[cc][2]);
+          for (int c4 = 0; c4 < CB / 4; ++c4) {
+            R wc[4];
+            ld4(ws + 2 * PB + c0 + 4 * c4, wc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const R wv = wab * wc[i];
+              acc[4 * c4 + i][0] = fma(wv, fv[0], acc[4 * c4 + i][0]);
+              acc[4 * c4 + i][1] = fma(wv, fv[1], acc[4 * c4 + i][1]);
+              acc[4 * c4 + i][2] = fma(wv, fv[2], acc[4 * c4 + i][2]);
+            }
           }
         }
       }
     }
     if (on) {
 #pragma unroll
-      for (int cc = 0; cc < kAntC; ++cc) {
+      for (int cc = 0; cc < CB; ++cc) {
         const int ci = c0 + cc;
         if (ci < p)
           for (int k = 0; k < 3; ++k) qb[k * p3 + (static_cast<int64_t>(a) * p + b) * p + ci] = acc[cc][k];
@@ -365,23 +428,39 @@ __global__ void k_far_contract(int njob, const int32_t* __restrict__ job_box, co
   }
 }
 
-// incoming expansions: I[tb][k][m] = sum over the 27 colleague slots of
-// e^{-2 pi i m.delta / 3} O[colleague][k][m]  (slot s: delta_a = ((s / 3^a) % 3) - 1)
+// incoming expansions, phase e^{-2 pi i m.delta / 3} for a colleague at offset delta
+// (e = m.delta mod 3: 1, e^{-2 pi i/3}, e^{-4 pi i/3})
 template <typename R>
-__global__ void k_far_colleague(int ntb, const int32_t* __restrict__ coll, const typename Cplx<R>::T* __restrict__ O,
-                                typename Cplx<R>::T* __restrict__ I, int Mh, int nh, int nm) {
+__device__ __forceinline__ void add_phased(int e, R ox, R oy, R& sr, R& si) {
+  const R c120 = R(-0.5), s120 = R(0.86602540378443864676);
+  if (e == 0) {
+    sr += ox;
+    si += oy;
+  } else {
+    const R sn = e == 1 ? -s120 : s120;
+    sr += c120 * ox - sn * oy;
+    si += c120 * oy + sn * ox;
+  }
+}
+
+// listed target boxes from their 27 colleague slots (slot s: delta_a = ((s / 3^a) % 3) - 1):
+// I[tlist[i]][k][m] = sum_slots phase O[colleague][k][m]   (used for the root)
+template <typename R>
+__global__ void k_far_colleague(int nlist, const int32_t* __restrict__ tlist, const int32_t* __restrict__ coll,
+                                const typename Cplx<R>::T* __restrict__ O, typename Cplx<R>::T* __restrict__ I, int Mh,
+                                int nh, int nm) {
   using C = typename Cplx<R>::T;
   const int64_t modes = static_cast<int64_t>(nh) * nm * nm;
   const int64_t idx = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (idx >= static_cast<int64_t>(ntb) * 3 * modes) return;
-  const int tb = static_cast<int>(idx / (3 * modes));
-  const int64_t rem = idx - static_cast<int64_t>(tb) * 3 * modes;
+  if (idx >= static_cast<int64_t>(nlist) * 3 * modes) return;
+  const int li = static_cast<int>(idx / (3 * modes));
+  const int64_t rem = idx - static_cast<int64_t>(li) * 3 * modes;
   const int k = static_cast<int>(rem / modes);
   const int64_t mi = rem - k * modes;
+  const int tb = tlist[li];
   const int m0 = static_cast<int>(mi / (nm * nm));
   const int m1 = static_cast<int>((mi / nm) % nm) - Mh;
   const int m2 = static_cast<int>(mi % nm) - Mh;
-  const R c120 = R(-0.5), s120 = R(0.86602540378443864676);
   R sr = 0, si = 0;
   for (int s = 0; s < 27; ++s) {
     const int cb = coll[tb * 27 + s];
@@ -390,20 +469,412 @@ __global__ void k_far_colleague(int ntb, const int32_t* __restrict__ coll, const
     int e = (m0 * d0 + m1 * d1 + m2 * d2) % 3;
     if (e < 0) e += 3;
     const C o = O[(static_cast<int64_t>(cb) * 3 + k) * modes + mi];
-    if (e == 0) {
-      sr += o.x;
-      si += o.y;
-    } else {
-      // e^{-2 pi i e / 3}: e = 1 -> (-1/2, -sqrt3/2), e = 2 -> (-1/2, +sqrt3/2)
-      const R sn = e == 1 ? -s120 : s120;
-      sr += c120 * o.x - sn * o.y;
-      si += c120 * o.y + sn * o.x;
-    }
+    add_phased<R>(e, o.x, o.y, sr, si);
   }
   C r;
   r.x = sr;
   r.y = si;
-  I[idx] = r;
+  I[(static_cast<int64_t>(tb) * 3 + k) * modes + mi] = r;
+}
+
+// the eight children of one parent at once: their colleagues lie in the 4 x 4 x 4
+// window of boxes at the children's level around them (window slot w = w0 + 4 w1 + 16 w2
+// at position 2 c_parent - 1 + (w0, w1, w2)), so each window box is read once for all
+// eight.  The phase of a colleague at offset delta factors over the axes,
+// e^{-2 pi i m.delta/3} = prod_a f_a(delta_a), so the 27-term sums of the eight
+// children are three passes of 3-term sums (axis 0, then 1, then 2).
+// win[g][64]: box id or -1; chl[g][8]: target index of child o (o_a = bit a) or -1.
+constexpr int kGrpThreads = 128;
+template <typename R>
+__device__ __forceinline__ void axis_phase(int m, R& c, R& s) {     // f(+1) = e^{-2 pi i m / 3}; f(-1) = conj
+  int e = m % 3;
+  if (e < 0) e += 3;
+  c = e == 0 ? R(1) : R(-0.5);
+  s = e == 0 ? R(0) : (e == 1 ? R(-0.86602540378443864676) : R(0.86602540378443864676));
+}
+template <typename R>
+__device__ __forceinline__ void sum3(R c, R s, R xr_m, R xi_m, R xr_0, R xi_0, R xr_p, R xi_p, R& yr, R& yi) {
+  // y = f(-1) x_{-1} + x_0 + f(+1) x_{+1},  f(+1) = c + i s, f(-1) = c - i s
+  yr = xr_0 + c * (xr_m + xr_p) + s * (xi_m - xi_p);
+  yi = xi_0 + c * (xi_m + xi_p) + s * (xr_p - xr_m);
+}
+template <typename R>
+__global__ void __launch_bounds__(kGrpThreads) k_far_colleague_grp(const int32_t* __restrict__ win, const int32_t* __restrict__ chl,
+                                                                   const typename Cplx<R>::T* __restrict__ O,
+                                                                   typename Cplx<R>::T* __restrict__ I, int Mh, int nh, int nm) {
+  using C = typename Cplx<R>::T;
+  __shared__ int s_win[64], s_ch[8];
+  const int g = blockIdx.x, k = blockIdx.y;
+  if (threadIdx.x < 64) s_win[threadIdx.x] = win[g * 64 + threadIdx.x];
+  if (threadIdx.x < 8) s_ch[threadIdx.x] = chl[g * 8 + threadIdx.x];
+  __syncthreads();
+  const int64_t modes = static_cast<int64_t>(nh) * nm * nm;
+  const int64_t mi = blockIdx.z * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (mi >= modes) return;
+  const int m0 = static_cast<int>(mi / (nm * nm));
+  const int m1 = static_cast<int>((mi / nm) % nm) - Mh;
+  const int m2 = static_cast<int>(mi % nm) - Mh;
+  R c0, s0, c1, s1, c2, s2;
+  axis_phase<R>(m0, c0, s0);
+  axis_phase<R>(m1, c1, s1);
+  axis_phase<R>(m2, c2, s2);
+  const C* Ok = O + static_cast<int64_t>(k) * modes + mi;
+  // pass 0 (axis 0): t0[o0][w1][w2]
+  R t0r[2][4][4], t0i[2][4][4];
+#pragma unroll
+  for (int w2 = 0; w2 < 4; ++w2)
+#pragma unroll
+    for (int w1 = 0; w1 < 4; ++w1) {
+      R xr[4], xi[4];
+#pragma unroll
+      for (int w0 = 0; w0 < 4; ++w0) {
+        const int cb = s_win[w0 + 4 * w1 + 16 * w2];
+        xr[w0] = xi[w0] = R(0);
+        if (cb >= 0) {
+          const C v = Ok[static_cast<int64_t>(cb) * 3 * modes];
+          xr[w0] = v.x;
+          xi[w0] = v.y;
+        }
+      }
+#pragma unroll
+      for (int o0 = 0; o0 < 2; ++o0)
+        sum3<R>(c0, s0, xr[o0], xi[o0], xr[o0 + 1], xi[o0 + 1], xr[o0 + 2], xi[o0 + 2], t0r[o0][w1][w2], t0i[o0][w1][w2]);
+    }
+  // pass 1 (axis 1): t1[o0][o1][w2]
+  R t1r[2][2][4], t1i[2][2][4];
+#pragma unroll
+  for (int o0 = 0; o0 < 2; ++o0)
+#pragma unroll
+    for (int o1 = 0; o1 < 2; ++o1)
+#pragma unroll
+      for (int w2 = 0; w2 < 4; ++w2)
+        sum3<R>(c1, s1, t0r[o0][o1][w2], t0i[o0][o1][w2], t0r[o0][o1 + 1][w2], t0i[o0][o1 + 1][w2],
+                t0r[o0][o1 + 2][w2], t0i[o0][o1 + 2][w2], t1r[o0][o1][w2], t1i[o0][o1][w2]);
+  // pass 2 (axis 2) and the writes
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    const int o0 = o & 1, o1 = (o >> 1) & 1, o2 = o >> 2;
+    R yr, yi;
+    sum3<R>(c2, s2, t1r[o0][o1][o2], t1i[o0][o1][o2], t1r[o0][o1][o2 + 1], t1i[o0][o1][o2 + 1],
+            t1r[o0][o1][o2 + 2], t1i[o0][o1][o2 + 2], yr, yi);
+    const int tb = s_ch[o];
+    if (tb < 0) continue;
+    C r;
+    r.x = yr;
+    r.y = yi;
+    I[(static_cast<int64_t>(tb) * 3 + k) * modes + mi] = r;
+  }
+}
+
+// ------------------------------------------------------------------ fused transforms
+// One warp computes out(m, r) = sum_j A[j][m] X[xaddr(r) + j * sxj] for four
+// consecutive m and RU rows r = base + 32 u + lane (so that a warp reads 32
+// consecutive r), A transposed [n_j][n4] in shared memory (zero past n_m).  The
+// warps of the block share the (m-quad, r-block) units of one contraction.
+template <typename R, bool XC, bool AC, int RU, class XAddr, class Store>
+__device__ __forceinline__ void warp_contract(const typename std::conditional<XC, typename Cplx<R>::T, R>::type* X,
+                                              XAddr xaddr, int sxj, int n_j, int n_r,
+                                              const typename std::conditional<AC, typename Cplx<R>::T, R>::type* AT,
+                                              int n_m, Store store) {
+  using C = typename Cplx<R>::T;
+  using TX = typename std::conditional<XC, C, R>::type;
+  using TA = typename std::conditional<AC, C, R>::type;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int n4 = (n_m + 3) & ~3, nmq = n4 / 4, nrb = (n_r + 32 * RU - 1) / (32 * RU);
+  for (int unit = warp; unit < nmq * nrb; unit += nwarp) {
+    const int mq = unit % nmq, rb = unit / nmq;
+    int64_t xo[RU];
+    bool ok[RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int r = rb * 32 * RU + 32 * u + lane;
+      ok[u] = r < n_r;
+      xo[u] = ok[u] ? xaddr(r) : 0;
+    }
+    R ar[RU][4], ai[RU][4];
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) ar[u][i] = ai[u][i] = R(0);
+    for (int j = 0; j < n_j; ++j) {
+      TA a[4];
+      ld4(AT + j * n4 + 4 * mq, a);
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        const TX x = X[xo[u] + static_cast<int64_t>(j) * sxj];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          if constexpr (AC && XC) {
+            ar[u][i] = fma(a[i].x, x.x, ar[u][i]);
+            ar[u][i] = fma(-a[i].y, x.y, ar[u][i]);
+            ai[u][i] = fma(a[i].x, x.y, ai[u][i]);
+            ai[u][i] = fma(a[i].y, x.x, ai[u][i]);
+          } else if constexpr (AC) {
+            ar[u][i] = fma(a[i].x, x, ar[u][i]);
+            ai[u][i] = fma(a[i].y, x, ai[u][i]);
+          } else if constexpr (XC) {
+            ar[u][i] = fma(a[i], x.x, ar[u][i]);
+            ai[u][i] = fma(a[i], x.y, ai[u][i]);
+          } else {
+            ar[u][i] = fma(a[i], x, ar[u][i]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int m = 4 * mq + i;
+        if (ok[u] && m < n_m) store(m, rb * 32 * RU + 32 * u + lane, ar[u][i], ai[u][i]);
+      }
+  }
+}
+
+// transposed copy of a row-major [n_m][n_j] matrix into shared memory [n_j][n4]
+template <typename T>
+__device__ inline void load_AT(T* dst, const T* src, int n_m, int n_j) {
+  const int n4 = (n_m + 3) & ~3;
+  for (int i = threadIdx.x; i < n_j * n4; i += blockDim.x) {
+    const int j = i / n4, m = i - j * n4;
+    T v{};
+    if (m < n_m) v = src[m * n_j + j];
+    dst[i] = v;
+  }
+}
+
+// shared-memory sizes of the fused transforms (bytes), one box per block
+inline size_t fused_out_smem(int p, int nh, int nm, size_t er) {
+  const size_t ec = 2 * er;
+  const size_t mats = (static_cast<size_t>(p) * ((nh + 3) & ~3) + static_cast<size_t>(p) * ((nm + 3) & ~3)) * ec;
+  const size_t y1 = static_cast<size_t>(p) * p * nh * ec;
+  const size_t big = std::max(static_cast<size_t>(p) * p * p * er, static_cast<size_t>(p) * nh * nm * ec);
+  return align16(mats) + align16(y1) + align16(big);
+}
+inline size_t fused_ev_smem(int p, int nh, int nm, size_t er) {
+  const size_t ec = 2 * er;
+  const size_t p4 = (p + 3) & ~3;
+  const size_t mats = (static_cast<size_t>(nm) * p4 + static_cast<size_t>(nh) * p4) * ec;
+  return align16(mats) + align16(static_cast<size_t>(nh) * nm * p * ec) + align16(static_cast<size_t>(nh) * p * p * ec);
+}
+
+// outgoing plane waves of one box, all components, in shared memory:
+//   X = q[box][k] [a][b][c] -> Y1 [(b,c)][m0] -> Y2 [(c,m0)][m1] -> [(m0,m1)][m2],
+// the last stage contracted with the level kernel into O[box][3][modes] (first
+// component written, the others added)
+template <typename R>
+__global__ void __launch_bounds__(1024) k_far_out_fused(const int32_t* __restrict__ src_boxes, const int32_t* __restrict__ box_level,
+                                                        const R* __restrict__ q, int ncomp, int slot_f, int slot_t,
+                                                        const typename Cplx<R>::T* __restrict__ Eh,
+                                                        const typename Cplx<R>::T* __restrict__ E, const R* __restrict__ tab,
+                                                        typename Cplx<R>::T* __restrict__ O, int p, int Mh, int nh, int nm) {
+  using C = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int nh4 = (nh + 3) & ~3, nm4 = (nm + 3) & ~3;
+  C* sEh = reinterpret_cast<C*>(smem);                                  // [p][nh4]
+  C* sE = sEh + p * nh4;                                                // [p][nm4]
+  const size_t mats = align16((static_cast<size_t>(p) * nh4 + static_cast<size_t>(p) * nm4) * sizeof(C));
+  C* sY1 = reinterpret_cast<C*>(smem + mats);                           // [p*p][nh]
+  unsigned char* big = smem + mats + align16(static_cast<size_t>(p) * p * nh * sizeof(C));
+  R* sX = reinterpret_cast<R*>(big);                                    // [p^3] (stage 1 input)
+  C* sY2 = reinterpret_cast<C*>(big);                                   // [(c, m0)][nm] (stage 2 output)
+  const int box = src_boxes[blockIdx.x];
+  load_AT(sEh, Eh, nh, p);
+  load_AT(sE, E, nm, p);
+  const R h = static_cast<R>(2.0 * M_PI / 3.0 * static_cast<double>(1 << box_level[box]));
+  const int p2 = p * p;
+  const int64_t p3 = static_cast<int64_t>(p2) * p, modes = static_cast<int64_t>(nh) * nm * nm;
+  C* Ob = O + static_cast<int64_t>(box) * 3 * modes;
+  for (int k = 0; k < ncomp; ++k) {
+    const int comp = (slot_f >= 0 && k < 3) ? k : 3 + (k - slot_t);
+    const R* qk = q + (static_cast<int64_t>(box) * ncomp + k) * p3;
+    __syncthreads();
+    for (int i = threadIdx.x; i < p3; i += blockDim.x) sX[i] = qk[i];
+    __syncthreads();
+    warp_contract<R, false, true, 2>(sX, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, sEh, nh,
+                                     [&](int m, int r, R re, R im) { sY1[r * nh + m] = C{re, im}; });
+    __syncthreads();
+    warp_contract<R, true, true, 2>(sY1, [](int r) { return static_cast<int64_t>(r); }, p * nh, p, p * nh, sE, nm,
+                                    [&](int m, int r, R re, R im) { sY2[r * nm + m] = C{re, im}; });
+    __syncthreads();
+    // stage 3 in chunks of rows (m0, m1), staged in the free Y1 buffer so that the
+    // kernel contraction and the update of O run over consecutive modes
+    const int rows = nh * nm;
+    const int chunk = static_cast<int>((static_cast<size_t>(p) * p * nh) / nm);    // rows of nm modes that fit in Y1
+    for (int r0 = 0; r0 < rows; r0 += chunk) {
+      const int nr = min(chunk, rows - r0);
+      warp_contract<R, true, true, 2>(sY2, [r0](int r) { return static_cast<int64_t>(r0 + r); }, nh * nm, p, nr, sE, nm,
+                                      [&](int m, int r, R re, R im) { sY1[r * nm + m] = C{re, im}; });
+      __syncthreads();
+      for (int i = threadIdx.x; i < nr * nm; i += blockDim.x) {
+        const int r = r0 + i / nm, m = i - (i / nm) * nm;
+        const C v = sY1[i];
+        const int m0 = r / nm, m1 = r - m0 * nm - Mh, m2 = m - Mh;
+        const R mv[3] = {R(m0), R(m1), R(m2)};
+        const int qi = m0 * m0 + m1 * m1 + m2 * m2;
+        const R t = tab[qi], qq = R(qi);
+        const int64_t mi = static_cast<int64_t>(r) * nm + m;
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+          R cr = R(0), ci = R(0);
+          if (comp < 3) {
+            cr = h * t * ((jj == comp ? qq : R(0)) - mv[jj] * mv[comp]);
+          } else {
+            const int cc = comp - 3;
+            R w;
+            if (cc < 3) {
+              w = qq * (R(2) * (jj == cc ? mv[cc] : R(0)) + mv[jj]) - R(2) * mv[jj] * mv[cc] * mv[cc];
+            } else {
+              const int l = cc == 5 ? 1 : 0, n = cc == 3 ? 1 : 2;
+              w = R(2) * qq * ((jj == l ? mv[n] : R(0)) + (jj == n ? mv[l] : R(0))) - R(4) * mv[jj] * mv[l] * mv[n];
+            }
+            ci = h * h * t * w;
+          }
+          C add;
+          add.x = cr * v.x - ci * v.y;
+          add.y = cr * v.y + ci * v.x;
+          if (k == 0) {
+            Ob[jj * modes + mi] = add;
+          } else {
+            C o = Ob[jj * modes + mi];
+            o.x += add.x;
+            o.y += add.y;
+            Ob[jj * modes + mi] = o;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// child merge of one parent, one component per block (float32):
+//   q[parent] = sum over children o of (T_o0 (x) T_o1 (x) T_o2) q[child o]
+// each child through three contractions in shared memory; chl[g][8]: box id of
+// child o (o_a = bit a) or -1 (no sources)
+template <typename R>
+__global__ void __launch_bounds__(1024) k_far_merge_fused(const int32_t* __restrict__ parents, const int32_t* __restrict__ chl,
+                                                          R* __restrict__ q, int ncomp, const R* __restrict__ T0,
+                                                          const R* __restrict__ T1, int p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int p4 = (p + 3) & ~3, p2 = p * p;
+  const int64_t p3 = static_cast<int64_t>(p2) * p;
+  R* sT = reinterpret_cast<R*>(smem);                                   // [2][p][p4] transposed T_0, T_1
+  R* sX = sT + 2 * p * p4;
+  R* sY1 = sX + p3;
+  R* sY2 = sY1 + p3;
+  R* sAcc = sY2 + p3;
+  const int g = blockIdx.x, k = blockIdx.y;
+  load_AT(sT, T0, p, p);
+  load_AT(sT + p * p4, T1, p, p);
+  for (int i = threadIdx.x; i < p3; i += blockDim.x) sAcc[i] = R(0);
+  for (int o = 0; o < 8; ++o) {
+    const int cb = chl[g * 8 + o];
+    if (cb < 0) continue;
+    const R* X = q + (static_cast<int64_t>(cb) * ncomp + k) * p3;
+    __syncthreads();
+    for (int i = threadIdx.x; i < p3; i += blockDim.x) sX[i] = X[i];
+    __syncthreads();
+    const R* A0 = sT + (o & 1) * p * p4;
+    const R* A1 = sT + ((o >> 1) & 1) * p * p4;
+    const R* A2 = sT + (o >> 2) * p * p4;
+    warp_contract<R, false, false, 2>(sX, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A0, p,
+                                      [&](int m, int r, R re, R) { sY1[r * p + m] = re; });
+    __syncthreads();
+    warp_contract<R, false, false, 2>(sY1, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A1, p,
+                                      [&](int m, int r, R re, R) { sY2[r * p + m] = re; });
+    __syncthreads();
+    warp_contract<R, false, false, 2>(sY2, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A2, p,
+                                      [&](int m, int r, R re, R) { sAcc[r * p + m] += re; });
+  }
+  __syncthreads();
+  R* Y = q + (static_cast<int64_t>(parents[g]) * ncomp + k) * p3;
+  for (int i = threadIdx.x; i < p3; i += blockDim.x) Y[i] = sAcc[i];
+}
+
+// interpolation of one parent's potential grid to its children, one component per
+// block (float32): pot[child o] += (T_o0^T (x) T_o1^T (x) T_o2^T) pot[parent];
+// chl[g][8]: box id of child o or -1 (no targets)
+template <typename R>
+__global__ void __launch_bounds__(1024) k_far_interp_fused(const int32_t* __restrict__ parents, const int32_t* __restrict__ chl,
+                                                           R* __restrict__ pot, const R* __restrict__ T0t,
+                                                           const R* __restrict__ T1t, int p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int p4 = (p + 3) & ~3, p2 = p * p;
+  const int64_t p3 = static_cast<int64_t>(p2) * p;
+  R* sT = reinterpret_cast<R*>(smem);
+  R* sX = sT + 2 * p * p4;
+  R* sY1 = sX + p3;
+  R* sY2 = sY1 + p3;
+  R* sY3 = sY2 + p3;
+  const int g = blockIdx.x, k = blockIdx.y;
+  load_AT(sT, T0t, p, p);
+  load_AT(sT + p * p4, T1t, p, p);
+  const R* Xg = pot + (static_cast<int64_t>(parents[g]) * 3 + k) * p3;
+  for (int i = threadIdx.x; i < p3; i += blockDim.x) sX[i] = Xg[i];
+  for (int o = 0; o < 8; ++o) {
+    const int cb = chl[g * 8 + o];
+    if (cb < 0) continue;
+    __syncthreads();
+    const R* A0 = sT + (o & 1) * p * p4;
+    const R* A1 = sT + ((o >> 1) & 1) * p * p4;
+    const R* A2 = sT + (o >> 2) * p * p4;
+    warp_contract<R, false, false, 2>(sX, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A0, p,
+                                      [&](int m, int r, R re, R) { sY1[r * p + m] = re; });
+    __syncthreads();
+    warp_contract<R, false, false, 2>(sY1, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A1, p,
+                                      [&](int m, int r, R re, R) { sY2[r * p + m] = re; });
+    __syncthreads();
+    warp_contract<R, false, false, 2>(sY2, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A2, p,
+                                      [&](int m, int r, R re, R) { sY3[r * p + m] = re; });
+    __syncthreads();
+    R* Y = pot + (static_cast<int64_t>(cb) * 3 + k) * p3;
+    for (int i = threadIdx.x; i < p3; i += blockDim.x) Y[i] += sY3[i];
+  }
+}
+
+inline size_t fused_tree_smem(int p, size_t er) {
+  const size_t p4 = (p + 3) & ~3;
+  return (2 * static_cast<size_t>(p) * p4 + 4 * static_cast<size_t>(p) * p * p) * er;
+}
+
+// potential grid of one target box from its incoming expansion, in shared memory:
+//   I[tb][k] [(m0,m1)][m2] -> Y1 [(m0,m1)][c] -> Y2 [m0][b][c] -> Re [a][b][c] = pot[box][k]
+// (the m0 >= 0 half carries the weights 1, 2, 2, ... in Fh)
+template <typename R>
+__global__ void __launch_bounds__(1024) k_far_ev_fused(const int32_t* __restrict__ trg_boxes,
+                                                       const typename Cplx<R>::T* __restrict__ I,
+                                                       const typename Cplx<R>::T* __restrict__ Fh,
+                                                       const typename Cplx<R>::T* __restrict__ F, R* __restrict__ pot,
+                                                       int p, int nh, int nm) {
+  using C = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int p4 = (p + 3) & ~3;
+  C* sF = reinterpret_cast<C*>(smem);                                   // [nm][p4]: F^T
+  C* sFh = sF + nm * p4;                                                // [nh][p4]: Fh^T
+  const size_t mats = align16((static_cast<size_t>(nm) * p4 + static_cast<size_t>(nh) * p4) * sizeof(C));
+  C* sY1 = reinterpret_cast<C*>(smem + mats);                           // [(m0,m1)][p]
+  C* sY2 = reinterpret_cast<C*>(smem + mats + align16(static_cast<size_t>(nh) * nm * p * sizeof(C)));   // [m0][b][c]
+  const int tb = blockIdx.x;
+  const int box = trg_boxes[tb];
+  load_AT(sF, F, p, nm);
+  load_AT(sFh, Fh, p, nh);
+  const int p2 = p * p;
+  const int64_t p3 = static_cast<int64_t>(p2) * p, modes = static_cast<int64_t>(nh) * nm * nm;
+  for (int k = 0; k < 3; ++k) {
+    const C* Ik = I + (static_cast<int64_t>(tb) * 3 + k) * modes;
+    R* Pk = pot + (static_cast<int64_t>(box) * 3 + k) * p3;
+    __syncthreads();
+    warp_contract<R, true, true, 2>(Ik, [nm](int r) { return static_cast<int64_t>(r) * nm; }, 1, nm, nh * nm, sF, p,
+                                    [&](int m, int r, R re, R im) { sY1[r * p + m] = C{re, im}; });
+    __syncthreads();
+    warp_contract<R, true, true, 2>(sY1, [p, nm](int r) { return static_cast<int64_t>(r / p) * nm * p + (r % p); }, p, nm,
+                                    nh * p, sF, p,
+                                    [&](int m, int r, R re, R im) { sY2[(r / p) * p2 + m * p + (r % p)] = C{re, im}; });
+    __syncthreads();
+    warp_contract<R, true, true, 2>(sY2, [](int r) { return static_cast<int64_t>(r); }, p2, nh, p2, sFh, p,
+                                    [&](int m, int r, R re, R im) { Pk[static_cast<int64_t>(m) * p2 + r] = re; });
+  }
 }
 
 // free-space Stokeslet constant K_corr sum_s f_s = (1 / 4 pi R) sum_j q_root,j
@@ -424,21 +895,21 @@ __global__ void k_far_corr(const R* __restrict__ q_root, int slot_f, R* __restri
   for (int64_t i = threadIdx.x; i < p3; i += blockDim.x) pot_root[k * p3 + i] += add;
 }
 
-// leaf evaluation: u[caller][k] += sum_abc L_a(x) L_b(y) L_c(z) pot[box][k][a][b][c]
-// (one thread per target; the leaf's grid is read slab by slab through shared memory)
+// leaf evaluation: u[caller][k] += sum_abc L_a(x) L_b(y) L_c(z) pot[box][k][a][b][c].
+// One thread per target; its c-weights stay in registers (PB of them, zero past p),
+// the leaf's grid passes through shared memory one a-slab (3 x p x PB) at a time.
 constexpr int kEvThreads = 128;
-template <typename R>
+template <typename R, int PB>
 __global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
                                                          const int32_t* __restrict__ t_start, const int32_t* __restrict__ t_count,
-                                                         const double* __restrict__ tw,
-                                                         int64_t NT, const int32_t* __restrict__ tperm,
+                                                         const double* __restrict__ tw, int64_t NT, const int32_t* __restrict__ tperm,
                                                          const BoxGeo* __restrict__ box_geo, const R* __restrict__ pot, int p,
-                                                         const double* __restrict__ nodes, const double* __restrict__ bw,
+                                                         const R* __restrict__ nodes, const R* __restrict__ bw,
                                                          double* __restrict__ u) {
   extern __shared__ __align__(16) unsigned char smem[];
-  R* sL = reinterpret_cast<R*>(smem);                    // [3][p][kEvThreads]
-  R* sP = sL + 3 * p * kEvThreads;                       // [3][p][p] slab of the grid
-  __shared__ double s_nodes[kMaxP], s_bw[kMaxP];
+  R* sL = reinterpret_cast<R*>(smem);                    // [2][p][kEvThreads]
+  R* sP = sL + 2 * p * kEvThreads;                       // [3][p][PB]
+  __shared__ R s_nodes[kMaxP], s_bw[kMaxP];
   const int li = leaf_list[blockIdx.x];
   const int box = leaf_box[blockIdx.x];
   for (int j = threadIdx.x; j < p; j += blockDim.x) {
@@ -446,6 +917,7 @@ __global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restri
     s_bw[j] = bw[j];
   }
   const BoxGeo geo = box_geo[box];
+  const double inv_half = 1.0 / geo.w;
   const int t0 = t_start[li], nt = t_count ? t_count[li] : t_start[li + 1] - t0;
   const int64_t p2 = static_cast<int64_t>(p) * p, p3 = p2 * p;
   const R* P = pot + static_cast<int64_t>(box) * 3 * p3;
@@ -453,33 +925,57 @@ __global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restri
   for (int base = 0; base < nt; base += blockDim.x) {
     const int t = base + threadIdx.x;
     const bool on = t < nt;
+    R cw[PB];
+#pragma unroll
+    for (int j = 0; j < PB; ++j) cw[j] = R(0);
     if (on) {
-      for (int ax = 0; ax < 3; ++ax) {
-        const double ctr = ax == 0 ? geo.x : (ax == 1 ? geo.y : geo.z);
-        lagrange_row<R>((tw[ax * NT + t0 + t] - ctr) / geo.w, p, s_nodes, s_bw, sL + ax * p * kEvThreads + threadIdx.x,
-                        kEvThreads);
+      for (int ax = 0; ax < 2; ++ax) {
+        const double ctr = ax == 0 ? geo.x : geo.y;
+        const R x = static_cast<R>((tw[ax * NT + t0 + t] - ctr) * inv_half);
+        lagrange_row<R>(x, p, s_nodes, s_bw, sL + ax * p * kEvThreads + threadIdx.x, kEvThreads, p);
       }
+      // the c-weights into registers (unrolled over PB)
+      const R z = static_cast<R>((tw[2 * NT + t0 + t] - geo.z) * inv_half);
+      R ssum = R(0);
+      int hit = -1;
+      for (int j = 0; j < p; ++j) {
+        const R d = z - s_nodes[j];
+        if (d == R(0)) hit = j;
+        else ssum += s_bw[j] / d;
+      }
+      const R inv = hit >= 0 ? R(0) : R(1) / ssum;
+#pragma unroll
+      for (int j = 0; j < PB; ++j)
+        if (j < p) cw[j] = hit >= 0 ? (j == hit ? R(1) : R(0)) : (s_bw[j] / (z - s_nodes[j])) * inv;
     }
     R acc0 = 0, acc1 = 0, acc2 = 0;
     for (int a = 0; a < p; ++a) {
       __syncthreads();
-      for (int i = threadIdx.x; i < 3 * p2; i += blockDim.x) {
-        const int k = static_cast<int>(i / p2);
-        const int64_t e = i - k * p2;
-        sP[i] = P[k * p3 + a * p2 + e];
+      for (int i = threadIdx.x; i < 3 * p * PB; i += blockDim.x) {
+        const int k = i / (p * PB);
+        const int e = i - k * p * PB;
+        const int b = e / PB, c = e - b * PB;
+        sP[i] = c < p ? P[k * p3 + a * p2 + b * p + c] : R(0);
       }
       __syncthreads();
       if (on) {
-        const R la = sL[(0 * p + a) * kEvThreads + threadIdx.x];
+        const R la = sL[a * kEvThreads + threadIdx.x];
         for (int b = 0; b < p; ++b) {
-          const R lab = la * sL[(1 * p + b) * kEvThreads + threadIdx.x];
-          const R* row = sP + b * p;
+          const R lab = la * sL[(p + b) * kEvThreads + threadIdx.x];
+          const R* row = sP + b * PB;
           R r0 = 0, r1 = 0, r2 = 0;
-          for (int c = 0; c < p; ++c) {
-            const R lc = sL[(2 * p + c) * kEvThreads + threadIdx.x];
-            r0 = fma(lc, row[c], r0);
-            r1 = fma(lc, row[p2 + c], r1);
-            r2 = fma(lc, row[2 * p2 + c], r2);
+#pragma unroll
+          for (int c4 = 0; c4 < PB / 4; ++c4) {
+            R v0[4], v1[4], v2[4];
+            ld4(row + 4 * c4, v0);
+            ld4(row + p * PB + 4 * c4, v1);
+            ld4(row + 2 * p * PB + 4 * c4, v2);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              r0 = fma(cw[4 * c4 + i], v0[i], r0);
+              r1 = fma(cw[4 * c4 + i], v1[i], r1);
+              r2 = fma(cw[4 * c4 + i], v2[i], r2);
+            }
           }
           acc0 = fma(lab, r0, acc0);
           acc1 = fma(lab, r1, acc1);
@@ -574,12 +1070,20 @@ struct FarState {
   // device arrays
   BoxGeo* box_geo = nullptr;
   int32_t* box_level = nullptr;
-  double* nodes = nullptr;
-  double* bw = nullptr;
+  int PB = 0;                        // padded proxy order of the leaf kernels
+  size_t m_nodes = 0, m_bw = 0;      // Chebyshev points and barycentric weights in the bank
+  void* W = nullptr;                 // [N][3][PB] Lagrange weights of the sources
   int32_t* src_leaf = nullptr;       // [nsrc_leaf] leaf index, then box id at + nsrc_leaf
   int32_t* trg_leaf = nullptr;
   int32_t* src_box_list = nullptr;   // boxes with sources (outgoing jobs order)
-  int32_t* coll = nullptr;           // [ntrg_box][27]
+  int32_t* trg_box_list = nullptr;   // boxes with targets (incoming order)
+  int fused = 0;                     // 1: float32 transforms of a box in one kernel (shared memory fits)
+  size_t fused_out_bytes = 0, fused_ev_bytes = 0;
+  int32_t* coll = nullptr;           // [ntrg_box][27] (the root's row is used)
+  int32_t* root_tlist = nullptr;     // {target index of the root}
+  int ngrp = 0;                      // parents whose children hold targets
+  int32_t* grp_win = nullptr;        // [ngrp][64]
+  int32_t* grp_ch = nullptr;         // [ngrp][8]
   int32_t* root_box = nullptr;       // {0}
   void* mats = nullptr;              // matrix bank
   size_t m_T0 = 0, m_T1 = 0, m_T0t = 0, m_T1t = 0, m_Eh = 0, m_E = 0, m_Fh = 0, m_F = 0;
@@ -597,6 +1101,11 @@ struct FarState {
   std::vector<int> merge_level;
   std::vector<RotLaunch> interp[3];
   std::vector<int> interp_level;
+  // the same per level for the fused float32 kernels: parents and their 8 children
+  int fused_tree = 0;
+  size_t fused_tree_bytes = 0;
+  std::vector<int32_t*> mf_par, mf_ch, if_par, if_ch;
+  std::vector<int> mf_n, if_n;
   RotLaunch out1, out2, out3, ev1, ev2, ev3, r1, r2, r3, rv1, rv2, rv3;
   size_t bytes = 0;
 };
@@ -613,9 +1122,11 @@ void launch_rot_t(const FarState& F, const RotLaunch& L, const void* X, void* Y,
   using C = typename Cplx<R>::T;
   const size_t sa = ac ? sizeof(C) : sizeof(R), sx = xc ? sizeof(C) : sizeof(R), sy = yc ? sizeof(C) : sizeof(R);
   size_t offX, offY;
-  rot_smem_layout((two_mats ? 2 : 1) * n_out * n_in * sa, 2 * n_in * kRotTile * sx, &offX, &offY);
+  const int n4 = (n_out + 3) & ~3;
+  rot_smem_layout((two_mats ? 2 : 1) * n_in * n4 * sa, (two_mats ? 2 : 1) * n_in * kRotTile * sx, &offX, &offY);
   const size_t shm = offY + kRotTile * n_out * sy;
   const dim3 grid(L.n, (rest + kRotTile - 1) / kRotTile);
+  const int nthr = ((16 * (n4 / 4) + 31) / 32) * 32;
   const char* base = static_cast<const char*>(F.mats);
   const void* A0 = base + matA0;
   const void* A1 = base + matA1;
@@ -624,7 +1135,7 @@ void launch_rot_t(const FarState& F, const RotLaunch& L, const void* X, void* Y,
   do {                                                                                                        \
     auto kern = k_rot<R, XC_, AC_, YC_, MODE_>;                                                               \
     DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm))); \
-    kern<<<grid, kRotThreads, shm, s>>>(L.jobs, X, Y, xoff, yoff, A0, A1, tm, n_in, n_out, rest);            \
+    kern<<<grid, nthr, shm, s>>>(L.jobs, X, Y, xoff, yoff, A0, A1, tm, n_in, n_out, rest);                   \
   } while (0)
   if (!xc && !ac && !yc && mode == 0) DMK_ROT(false, false, false, 0);
   else if (!xc && !ac && !yc && mode == 1) DMK_ROT(false, false, false, 1);
@@ -669,7 +1180,12 @@ void far_setup(Plan& p) {
   F.M = tcp - 1;                                   // N1 = 2 (3c/pi) - 1 modes a side
   F.nh = F.M + 1;
   F.nm = 2 * F.M + 1;
-  if (F.p > kMaxP || F.nm > kMaxP) throw Error{DMK_ERR_UNSUPPORTED, "far-field order beyond the compiled maximum"};
+  if (F.p > 60 || F.nm > kMaxP) throw Error{DMK_ERR_UNSUPPORTED, "far-field order beyond the compiled maximum"};
+  {
+    const int cb = F.fp32 ? ant_chunk<float>() : ant_chunk<double>();
+    F.PB = ((F.p + cb - 1) / cb) * cb;
+    if (F.fp32 && F.PB > 48) throw Error{DMK_ERR_UNSUPPORTED, "far-field order beyond the compiled maximum"};
+  }
   F.p3 = static_cast<int64_t>(F.p) * F.p * F.p;
   F.modes = static_cast<int64_t>(F.nh) * F.nm * F.nm;
   const bool wS = o.kernels & DMK_KERNEL_STOKESLET, wT = o.kernels & DMK_KERNEL_STRESSLET;
@@ -815,6 +1331,35 @@ void far_setup(Plan& p) {
       coll[static_cast<size_t>(t) * 27 + sl] = it->second;
     }
   }
+  // parent groups for the colleague sums of every non-root target box
+  std::vector<int32_t> gwin, gch;
+  for (int i = 0; i < nb; ++i) {
+    const Box& b = boxes[i];
+    if (b.leaf >= 0 || b.trg == 0) continue;
+    const int l = b.lev + 1;
+    const int64_t n = int64_t(1) << l;
+    for (int w = 0; w < 64; ++w) {
+      const int64_t wd[3] = {w & 3, (w >> 2) & 3, w >> 4};
+      int64_t cc[3];
+      bool ok = true;
+      for (int a = 0; a < 3; ++a) {
+        cc[a] = 2 * b.c[a] - 1 + wd[a];
+        if (o.periodic) cc[a] = ((cc[a] % n) + n) % n;
+        else if (cc[a] < 0 || cc[a] >= n) ok = false;
+      }
+      int id = -1;
+      if (ok) {
+        auto it = at[l].find(morton<3>(cc));
+        if (it != at[l].end() && boxes[it->second].src > 0) id = it->second;
+      }
+      gwin.push_back(id);
+    }
+    for (int ch = 0; ch < 8; ++ch) gch.push_back(trg_index[b.child[ch]]);
+  }
+  F.ngrp = static_cast<int>(gch.size() / 8);
+  F.grp_win = upload(p, gwin);
+  F.grp_ch = upload(p, gch);
+  F.root_tlist = upload(p, std::vector<int32_t>{trg_index[0]});
   std::vector<BoxGeo> geo(nb);
   std::vector<int32_t> blev(nb);
   for (int i = 0; i < nb; ++i) {
@@ -862,6 +1407,8 @@ void far_setup(Plan& p) {
     }
     return off;
   };
+  F.m_nodes = put_real(nodes);
+  F.m_bw = put_real(bwt);
   // child -> parent anterpolation T_o[a][i] = L_a(((2o - 1) + xi_i) / 2), and the transposes
   for (int oo = 0; oo < 2; ++oo) {
     std::vector<double> Tm(P * P), Tt(P * P);
@@ -926,8 +1473,6 @@ void far_setup(Plan& p) {
   }
   F.mats = p.arena.alloc<char>(bank.size());
   DMK_CUDA_TRY(cudaMemcpyAsync(F.mats, bank.data(), bank.size(), cudaMemcpyHostToDevice, s));
-  F.nodes = upload(p, nodes);
-  F.bw = upload(p, bwt);
   F.box_geo = upload(p, geo);
   F.box_level = upload(p, blev);
   {
@@ -939,6 +1484,16 @@ void far_setup(Plan& p) {
     F.trg_leaf = upload(p, tl);
   }
   F.src_box_list = upload(p, src_boxes);
+  F.trg_box_list = upload(p, trg_boxes);
+  if (F.fp32) {
+    F.fused_out_bytes = fused_out_smem(F.p, F.nh, F.nm, sizeof(float));
+    F.fused_ev_bytes = fused_ev_smem(F.p, F.nh, F.nm, sizeof(float));
+    int dev_smem = 0;
+    DMK_CUDA_TRY(cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p.device));
+    F.fused = (std::max(F.fused_out_bytes, F.fused_ev_bytes) <= static_cast<size_t>(dev_smem)) ? 1 : 0;
+    F.fused_tree_bytes = fused_tree_smem(F.p, sizeof(float));
+    F.fused_tree = F.fused_tree_bytes <= static_cast<size_t>(dev_smem) ? 1 : 0;
+  }
   F.coll = upload(p, coll);
   F.root_box = upload(p, std::vector<int32_t>{0});
 
@@ -957,10 +1512,13 @@ void far_setup(Plan& p) {
   // merges: parent at level l (non-leaf, with sources), per component
   for (int l = maxlev - 1; l >= 0; --l) {
     std::vector<RotJob> j1, j2, j3;
+    std::vector<int32_t> fpar, fch;
     int np = 0;
     for (int i = 0; i < nb; ++i) {
       const Box& b = boxes[i];
       if (b.lev != l || b.leaf >= 0 || b.src == 0) continue;
+      fpar.push_back(i);
+      for (int ch = 0; ch < 8; ++ch) fch.push_back(boxes[b.child[ch]].src ? b.child[ch] : -1);
       for (int k = 0; k < nc; ++k) {
         const int64_t slotbase = (static_cast<int64_t>(np) * nc + k);      // per (parent, comp)
         for (int o12 = 0; o12 < 4; ++o12) {                                 // (o1, o2), stage 1 over o0
@@ -1001,6 +1559,9 @@ void far_setup(Plan& p) {
       ++np;
     }
     if (np == 0) continue;
+    F.mf_par.push_back(upload(p, fpar));
+    F.mf_ch.push_back(upload(p, fch));
+    F.mf_n.push_back(np);
     F.merge_level.push_back(l);
     F.merge[0].push_back(make_launch(p, j1));
     F.merge[1].push_back(make_launch(p, j2));
@@ -1010,10 +1571,13 @@ void far_setup(Plan& p) {
   // interpolation: parent at level l (non-leaf, with targets) to its children with targets
   for (int l = 0; l < maxlev; ++l) {
     std::vector<RotJob> j1, j2, j3;
+    std::vector<int32_t> fpar, fch;
     int np = 0;
     for (int i = 0; i < nb; ++i) {
       const Box& b = boxes[i];
       if (b.lev != l || b.leaf >= 0 || b.trg == 0) continue;
+      fpar.push_back(i);
+      for (int ch = 0; ch < 8; ++ch) fch.push_back(boxes[b.child[ch]].trg ? b.child[ch] : -1);
       for (int k = 0; k < 3; ++k) {
         const int64_t slotbase = static_cast<int64_t>(np) * 3 + k;
         for (int o0 = 0; o0 < 2; ++o0) {
@@ -1049,6 +1613,9 @@ void far_setup(Plan& p) {
       ++np;
     }
     if (np == 0) continue;
+    F.if_par.push_back(upload(p, fpar));
+    F.if_ch.push_back(upload(p, fch));
+    F.if_n.push_back(np);
     F.interp_level.push_back(l);
     F.interp[0].push_back(make_launch(p, j1));
     F.interp[1].push_back(make_launch(p, j2));
@@ -1119,6 +1686,7 @@ void far_setup(Plan& p) {
   F.s1 = big(static_cast<size_t>(max_jobs) * st * ec);
   F.s2 = big(static_cast<size_t>(max_jobs) * st * ec);
   F.rO = big(static_cast<size_t>(3) * F.rmodes * ec);
+  F.W = big(static_cast<size_t>(std::max<int64_t>(T.N, 1)) * 3 * F.PB * er);
   DMK_CUDA_TRY(cudaStreamSynchronize(s));
   p.far = Fp.release();
 }
@@ -1126,7 +1694,7 @@ void far_setup(Plan& p) {
 void far_free(Plan& p) {
   FarState* F = p.far;
   if (!F) return;
-  for (void** b : {&F->q, &F->pot, &F->O, &F->I, &F->s1, &F->s2, &F->rO})
+  for (void** b : {&F->q, &F->pot, &F->O, &F->I, &F->s1, &F->s2, &F->rO, &F->W})
     if (*b) cudaFreeAsync(*b, p.stream);
   delete F;                                   // small arrays live in the plan's arena
   p.far = nullptr;
@@ -1150,28 +1718,64 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
   C* O = static_cast<C*>(F.O);
   C* I = static_cast<C*>(F.I);
   const char* mats = static_cast<const char*>(F.mats);
-  // 1. leaf proxy charges
+  const R* nodes = reinterpret_cast<const R*>(mats + F.m_nodes);
+  const R* bw = reinterpret_cast<const R*>(mats + F.m_bw);
+  const int PB = F.PB;
+  // 1. Lagrange weights of the sources, leaf proxy charges
   if (F.nsrc_leaf > 0) {
-    const size_t shm = (3 * kAntChunk * P + 3 * kAntChunk) * sizeof(R);
+    R* W = static_cast<R*>(F.W);
+    k_far_weights<R><<<F.nsrc_leaf, 256, 0, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, T.w,
+                                                 T.N, F.box_geo, P, PB, nodes, bw, W);
+    DMK_CUDA_TRY(cudaGetLastError());
+    const size_t shm = (static_cast<size_t>(kAntChunk) * 3 * PB + 4 * kAntChunk) * sizeof(R);
     auto kern = k_far_anterp<R>;
     DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
+    const int ntask = P * P * (PB / ant_chunk<R>());
+    const int nthr = std::min(kAntThreads, ((ntask + 31) / 32) * 32);
     const int g0 = F.slot_f >= 0 ? 0 : 1;
     const int ng = (F.slot_f >= 0 ? 1 : 0) + (F.slot_t >= 0 ? 2 : 0);
-    kern<<<dim3(F.nsrc_leaf, ng), 256, shm, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, T.w,
-                                                 T.N, T.perm, F.box_geo, d_f, d_g, d_n, g0, F.slot_f, F.slot_t, nc, q, P,
-                                                 F.nodes, F.bw);
+    kern<<<dim3(F.nsrc_leaf, ng), nthr, shm, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, W,
+                                                  T.perm, d_f, d_g, d_n, g0, F.slot_f, F.slot_t, nc, q, P, PB);
     DMK_CUDA_TRY(cudaGetLastError());
-    ++p.launches;
+    p.launches += 2;
   }
   // 2. upward merges, finest parents first
-  for (size_t i = 0; i < F.merge_level.size(); ++i) {
+  const bool ftree = F.fused_tree && sizeof(R) == 4;
+  if constexpr (sizeof(R) == 4) {
+    if (ftree) {
+      auto kern = k_far_merge_fused<R>;
+      DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(F.fused_tree_bytes)));
+      for (size_t i = 0; i < F.merge_level.size(); ++i) {
+        kern<<<dim3(F.mf_n[i], nc), 1024, F.fused_tree_bytes, s>>>(F.mf_par[i], F.mf_ch[i], q, nc,
+                                                                   reinterpret_cast<const R*>(mats + F.m_T0),
+                                                                   reinterpret_cast<const R*>(mats + F.m_T1), P);
+        DMK_CUDA_TRY(cudaGetLastError());
+        ++p.launches;
+      }
+    }
+  }
+  for (size_t i = 0; i < (ftree ? 0 : F.merge_level.size()); ++i) {
     launch_rot(p, F.merge[0][i], q, F.s1, 0, 0, F.m_T0, F.m_T1, true, P, P, static_cast<int>(p2), 0, 0, 0, 0, s);
     launch_rot(p, F.merge[1][i], F.s1, F.s2, 0, 0, F.m_T0, F.m_T1, true, P, P, static_cast<int>(p2), 0, 0, 0, 0, s);
     launch_rot(p, F.merge[2][i], F.s2, q, 0, 0, F.m_T0, F.m_T1, true, P, P, static_cast<int>(p2), 0, 0, 0, 0, s);
   }
   // 3. outgoing plane waves of every box with sources, contracted with the level kernel
   const R* tab = reinterpret_cast<const R*>(mats + F.m_tab);
-  for (int k = 0; k < nc; ++k) {
+  const bool fused = F.fused && sizeof(R) == 4;
+  if constexpr (sizeof(R) == 4) {
+    if (fused && F.nsrc_box > 0) {
+      auto kern = k_far_out_fused<R>;
+      DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(F.fused_out_bytes)));
+      kern<<<F.nsrc_box, 1024, F.fused_out_bytes, s>>>(F.src_box_list, F.box_level, q, nc, F.slot_f, F.slot_t,
+                                                       reinterpret_cast<const C*>(mats + F.m_Eh),
+                                                       reinterpret_cast<const C*>(mats + F.m_E), tab, O, P, F.M, nh, nm);
+      DMK_CUDA_TRY(cudaGetLastError());
+      ++p.launches;
+    }
+  }
+  for (int k = 0; k < (fused ? 0 : nc); ++k) {
     launch_rot(p, F.out1, q, F.s1, k * P3, 0, F.m_Eh, F.m_Eh, false, P, nh, static_cast<int>(p2), 0, 1, 1, 0, s);
     launch_rot(p, F.out2, F.s1, F.s2, 0, 0, F.m_E, F.m_E, false, P, nm, P * nh, 1, 1, 1, 0, s);
     launch_rot(p, F.out3, F.s2, F.s1, 0, 0, F.m_E, F.m_E, false, P, nm, nh * nm, 1, 1, 1, 0, s);
@@ -1185,13 +1789,29 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
   }
   // 4. incoming expansions (colleague sums) and their potential grids (written)
   {
-    const int64_t tot = static_cast<int64_t>(F.ntrg_box) * 3 * F.modes;
-    if (tot > 0) {
-      k_far_colleague<R><<<grid_for(tot, 256), 256, 0, s>>>(F.ntrg_box, F.coll, O, I, F.M, nh, nm);
+    if (F.ntrg_box > 0) {
+      k_far_colleague<R><<<grid_for(3 * F.modes, 256), 256, 0, s>>>(1, F.root_tlist, F.coll, O, I, F.M, nh, nm);
       DMK_CUDA_TRY(cudaGetLastError());
       ++p.launches;
     }
-    for (int k = 0; k < 3; ++k) {
+    if (F.ngrp > 0) {
+      const dim3 grid(F.ngrp, 3, static_cast<unsigned>((F.modes + kGrpThreads - 1) / kGrpThreads));
+      k_far_colleague_grp<R><<<grid, kGrpThreads, 0, s>>>(F.grp_win, F.grp_ch, O, I, F.M, nh, nm);
+      DMK_CUDA_TRY(cudaGetLastError());
+      ++p.launches;
+    }
+    if constexpr (sizeof(R) == 4) {
+      if (fused && F.ntrg_box > 0) {
+        auto kern = k_far_ev_fused<R>;
+        DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(F.fused_ev_bytes)));
+        kern<<<F.ntrg_box, 1024, F.fused_ev_bytes, s>>>(F.trg_box_list, I, reinterpret_cast<const C*>(mats + F.m_Fh),
+                                                        reinterpret_cast<const C*>(mats + F.m_F), pot, P, nh, nm);
+        DMK_CUDA_TRY(cudaGetLastError());
+        ++p.launches;
+      }
+    }
+    for (int k = 0; k < (fused ? 0 : 3); ++k) {
       launch_rot(p, F.ev1, I, F.s1, k * F.modes, 0, F.m_Fh, F.m_Fh, false, nh, P, nm * nm, 1, 1, 1, 0, s);
       launch_rot(p, F.ev2, F.s1, F.s2, 0, 0, F.m_F, F.m_F, false, nm, P, nm * P, 1, 1, 1, 0, s);
       launch_rot(p, F.ev3, F.s2, pot, 0, k * P3, F.m_F, F.m_F, false, nm, P, static_cast<int>(p2), 1, 1, 0, 0, s);
@@ -1225,22 +1845,44 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
     }
   }
   // 6. interpolation down the tree
-  for (size_t i = 0; i < F.interp_level.size(); ++i) {
+  if constexpr (sizeof(R) == 4) {
+    if (ftree) {
+      auto kern = k_far_interp_fused<R>;
+      DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(F.fused_tree_bytes)));
+      for (size_t i = 0; i < F.interp_level.size(); ++i) {
+        kern<<<dim3(F.if_n[i], 3), 1024, F.fused_tree_bytes, s>>>(F.if_par[i], F.if_ch[i], pot,
+                                                                  reinterpret_cast<const R*>(mats + F.m_T0t),
+                                                                  reinterpret_cast<const R*>(mats + F.m_T1t), P);
+        DMK_CUDA_TRY(cudaGetLastError());
+        ++p.launches;
+      }
+    }
+  }
+  for (size_t i = 0; i < (ftree ? 0 : F.interp_level.size()); ++i) {
     launch_rot(p, F.interp[0][i], pot, F.s1, 0, 0, F.m_T0t, F.m_T1t, true, P, P, static_cast<int>(p2), 0, 0, 0, 0, s);
     launch_rot(p, F.interp[1][i], F.s1, F.s2, 0, 0, F.m_T0t, F.m_T1t, true, P, P, static_cast<int>(p2), 0, 0, 0, 0, s);
     launch_rot(p, F.interp[2][i], F.s2, pot, 0, 0, F.m_T0t, F.m_T1t, true, P, P, static_cast<int>(p2), 0, 0, 0, 1, s);
   }
   // 7. leaf grids at the targets
   if (F.ntrg_leaf > 0) {
-    const size_t shm = (3 * static_cast<size_t>(P) * kEvThreads + 3 * p2) * sizeof(R);
-    auto kern = k_far_eval<R>;
-    DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
-    if (T.sep)
-      kern<<<F.ntrg_leaf, kEvThreads, shm, s>>>(F.trg_leaf, F.trg_leaf + F.ntrg_leaf, T.leaf_tstart, nullptr, T.tw, T.NT,
-                                                T.tperm, F.box_geo, pot, P, F.nodes, F.bw, d_u);
-    else
-      kern<<<F.ntrg_leaf, kEvThreads, shm, s>>>(F.trg_leaf, F.trg_leaf + F.ntrg_leaf, T.leaf_start, T.leaf_count, T.w, T.N,
-                                                T.perm, F.box_geo, pot, P, F.nodes, F.bw, d_u);
+    const size_t shm = (2 * static_cast<size_t>(P) * kEvThreads + 3 * static_cast<size_t>(P) * PB) * sizeof(R);
+    auto go = [&](auto kern) {
+      DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
+      if (T.sep)
+        kern<<<F.ntrg_leaf, kEvThreads, shm, s>>>(F.trg_leaf, F.trg_leaf + F.ntrg_leaf, T.leaf_tstart, nullptr, T.tw,
+                                                  T.NT, T.tperm, F.box_geo, pot, P, nodes, bw, d_u);
+      else
+        kern<<<F.ntrg_leaf, kEvThreads, shm, s>>>(F.trg_leaf, F.trg_leaf + F.ntrg_leaf, T.leaf_start, T.leaf_count,
+                                                  T.w, T.N, T.perm, F.box_geo, pot, P, nodes, bw, d_u);
+    };
+    switch (PB) {
+      case 12: go(k_far_eval<R, 12>); break;
+      case 24: go(k_far_eval<R, 24>); break;
+      case 36: go(k_far_eval<R, 36>); break;
+      case 48: go(k_far_eval<R, 48>); break;
+      default: go(k_far_eval<R, 60>); break;
+    }
     DMK_CUDA_TRY(cudaGetLastError());
     ++p.launches;
   }
