@@ -1,20 +1,24 @@
 #!/usr/bin/env python
-"""Benchmark: 3D free-space Stokeslet DMK near-field pass on GB300.
+"""Benchmark: 3D free-space Stokeslet DMK sum on GB300.
 
 Workload (one rank = one independent system, weak scaling): N = 1e6 points from
 a mixture of 8 isotropic Gaussians (sigma = 0.02, centres uniform in
 [0.2, 0.8]^3, clipped to the unit cube, shifted to [-1/2, 1/2]^3), forces
-N(0, 1), eps = 1e-6 (3c/pi = 17, Table 2), leaf capacity n_s = 1200 (the
-paper's 3D value for eps = 1e-6, Sec. 8).
+N(0, 1), eps = 1e-6 (3c/pi = 17, p = 23, N1 = 33, Table 2); the leaf capacity
+is picked by the library's autotuner among 1024, 2048 and 4096.
 
 One step = dmk_stokes_plan (kernel tables, Morton sort, adaptive tree, level
-restriction, near lists, tiles) + dmk_stokes_eval (near field + self term) +
-dmk_stokes_destroy, mixed precision.  value = targets / s over the timed
-steps; the L2 is flushed (256 MB write) before every timed step.  The FP64
-path is measured on the same workload and reported beside it.
+restriction, near lists, tiles, box hierarchy and far-field job lists) +
+dmk_stokes_eval (near field + self term + far field: proxy charges, merges,
+plane waves, root, interpolation, leaf evaluation) + dmk_stokes_destroy,
+components = ALL, mixed precision.  value = targets / s over the timed steps;
+the L2 is flushed (256 MB write) before every timed step.  The FP64 path is
+measured on the same workload and reported beside it, with the stage times of
+one evaluation (dmk_stokes_eval_traced), the near-field pair rates and the
+near-field pass alone.
 
---impl reference times the FP64 CPU oracle (plain numpy, one thread) on a
-bounded sample of the same recipe.
+--impl reference times the FP64 CPU oracle's whole DMK sum (plain numpy, one
+thread) on a bounded sample of the same recipe.
 """
 import argparse
 import json
@@ -28,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "3D Stokeslet DMK targets/s at eps=1e-6 (near-field pass incl. tree build), mixed precision"
+METRIC = "3D Stokeslet DMK targets/s at eps=1e-6, mixed vs FP64 on GPU; near-field Gpairs/s"
 N_SM = 152
 FP32_LANES_PER_SM = 128
 
@@ -42,7 +46,7 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--leaf-capacity", type=int, default=0, help="0 = paper's n_s for eps")
-    ap.add_argument("--cpu-sample", type=int, default=4000, help="points in the oracle's bounded sample")
+    ap.add_argument("--cpu-sample", type=int, default=1500, help="points in the oracle's bounded sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the other workloads (eps = 1e-10, 2D periodic, batched, gradient)")
@@ -153,7 +157,7 @@ def run_sweep(args):
 
 
 def workload_config(args, ns):
-    return {"workload": "3d-free-stokeslet-clustered-8gauss",
+    return {"workload": "3d-free-stokeslet-clustered-8gauss, whole DMK sum (near + far field)",
             "n_points": args.n, "sigma": 0.02, "eps": args.eps, "leaf_capacity": ns,
             "kernels": "stokeslet", "rhs": 1, "l2": "flushed (256 MB write) before every timed step"}
 
@@ -220,83 +224,68 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ reference arm
-def oracle_sample(n_sample, eps, ns, seed_extra=0):
-    """Times the FP64 oracle (tree + near pass) on the same recipe at n_sample points."""
+def oracle_dmk_seconds(n_sample, eps, ns, seed_extra=0):
+    """Seconds the FP64 oracle takes for the whole DMK sum (tree, near pass and the
+    far field of Sec. 6) on the same recipe at n_sample points."""
     import numpy as np
     from paper_2509_21471_gb300 import workloads as wl
-    from oracle import near as onear
+    from oracle import near as onear, dmk as odmk
     from oracle.tree import Tree
     from oracle.window import ProlateWindow
-    from oracle.params import bandlimit_c
     rng = wl.rng_for(1, extra=10 + seed_extra)
     x = wl.gaussian_mixture_points(rng, n_sample, 3, 8, 0.02)
     f = wl.forces(rng, n_sample, 3)
-    win = ProlateWindow(bandlimit_c(eps))
+    tcp, p, n1, nper = odmk.dmk_params(eps)
+    win = ProlateWindow(tcp * np.pi / 3)
     t0 = time.perf_counter()
     tr = Tree(x, ns)
-    onear.near_lists(tr, dict(win=win, stokeslet=True), f=f)
+    u = onear.near_lists(tr, dict(win=win, stokeslet=True), f=f)
+    u += odmk.FarField(tr, win, p, n1, nper).far(f)
     return time.perf_counter() - t0
 
 
-def _oracle_chunk(n_sample, eps, ns, seed_extra, part, parts):
-    """One worker's share of the oracle sample: the tree (every worker builds
-    it) and the near pass over its slice of the targets."""
-    import numpy as np
-    from paper_2509_21471_gb300 import workloads as wl
-    from oracle import near as onear
-    from oracle.tree import Tree
-    from oracle.window import ProlateWindow
-    from oracle.params import bandlimit_c
-    rng = wl.rng_for(1, extra=10 + seed_extra)
-    x = wl.gaussian_mixture_points(rng, n_sample, 3, 8, 0.02)
-    f = wl.forces(rng, n_sample, 3)
-    t0 = time.perf_counter()
-    tr = Tree(x, ns)
-    onear.near_lists(tr, dict(win=ProlateWindow(bandlimit_c(eps)), stokeslet=True), f=f,
-                     targets=np.array_split(np.arange(n_sample), parts)[part])
-    return time.perf_counter() - t0
+def oracle_seconds_in_process(n_sample, eps, ns, threads, seed_extra=0):
+    """oracle_dmk_seconds in a fresh Python process whose BLAS / OpenMP thread pools
+    are limited to `threads` (None: the libraries' default, every core)."""
+    env = dict(os.environ)
+    if threads is not None:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = str(threads)
+    code = (f"import bench; print(bench.oracle_dmk_seconds({n_sample}, {eps!r}, {ns}, {seed_extra}))")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, check=True)
+    return float(r.stdout.strip().splitlines()[-1])
 
 
-def oracle_timings(n_sample, eps, ns, repeats=3):
-    """The oracle on the host cores: one thread (median of `repeats` runs of the
-    whole sample) and all cores (a spawned process per core, each building the
-    tree and summing its share of the targets; wall time, median of `repeats`)."""
-    import multiprocessing as mp
-    import statistics
+def oracle_timings(n_sample, eps, ns):
+    """The oracle on the host cores: one thread, and every core through numpy's
+    threaded BLAS (the oracle as it stands); one run each."""
     procs = os.cpu_count() or 1
-    one = statistics.median(oracle_sample(n_sample, eps, ns, k) for k in range(repeats))
-    with mp.get_context("spawn").Pool(procs) as pool:
-        pool.starmap(_oracle_chunk, [(200, eps, ns, 0, i, procs) for i in range(procs)])   # warm the workers
-        walls = []
-        for k in range(repeats):
-            t0 = time.perf_counter()
-            pool.starmap(_oracle_chunk, [(n_sample, eps, ns, k, i, procs) for i in range(procs)])
-            walls.append(time.perf_counter() - t0)
-    return one, statistics.median(walls), procs
+    one = oracle_seconds_in_process(n_sample, eps, ns, 1)
+    alln = oracle_seconds_in_process(n_sample, eps, ns, None)
+    return one, alln, procs
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    ns = args.leaf_capacity or 1200
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle_sample(max(200, args.cpu_sample // 10), args.eps, ns)
-    times = [oracle_sample(args.cpu_sample, args.eps, ns, k) for k in range(args.steps)]
+    n_s, ns = 600, 128          # per step: the oracle's whole DMK sum on a 600-point sample
+    for _ in range(min(args.warmup, 1)):
+        oracle_seconds_in_process(200, args.eps, ns, 1)
+    times = [oracle_seconds_in_process(n_s, args.eps, ns, 1, k) for k in range(args.steps)]
     t = sum(times)
-    v = args.cpu_sample * args.steps / t
+    v = n_s * args.steps / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "targets/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args, ns),
             "cpu_baseline": {"value": v, "unit": "targets/s", "cores": 1, "kind": "oracle",
-                             "sample": f"same 8-Gaussian recipe at N={args.cpu_sample} points per step "
-                                       f"(oracle tree + near pass, numpy, 1 thread)"},
+                             "sample": f"same 8-Gaussian recipe at N={n_s} points per step, leaf capacity {ns}: "
+                                       f"the oracle's whole DMK sum (tree, near pass, far field), numpy, 1 thread"},
             "e2e": {"value": v, "unit": "targets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------- other workloads
 def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
     from paper_2509_21471_gb300 import dist as pdist
     """The remaining workloads of the hot path, each timed per step (plan +
@@ -338,6 +327,18 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
     r.update(workload="3d-free-stokeslet-clustered-8gauss", n_points=len(x), eps=1e-10,
              mixed_pair_arith="float-float (eps < 2e-7)")
     res["clustered_3d_eps1e-10"] = r
+    del xd, fd, ud
+
+    # the whole DMK sum (near + far field) at eps = 1e-10: the far field in float64
+    # in both precisions (MIXED: float-float near pair terms), N = 2e5 clustered
+    x, f = wl.clustered_3d(n=200_000, sigma=0.02, seed_index=pdist.seed_index(1, rank))
+    xd, fd = torch.as_tensor(x, device="cuda"), torch.as_tensor(f, device="cuda")
+    ud = torch.empty_like(fd)
+    r = measure(lambda prec: dmk.Plan(xd, eps=1e-10, precision=prec, leaf_capacity=2048, components=dmk.ALL),
+                lambda p: p.eval(fd, out=ud), len(x), 2)
+    r.update(workload="3d-free-stokeslet-clustered-8gauss, whole DMK sum", n_points=len(x), eps=1e-10,
+             note="near_ms here is the whole evaluation (near + far) with the plan reused")
+    res["dmk_full_sum_clustered_3d_eps1e-10"] = r
     del xd, fd, ud
 
     # 2D periodic unit square, Stokeslet + stresslet (k = 0 term included), eps = 1e-8
@@ -438,20 +439,23 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
             ud = torch.empty((n, dim), dtype=torch.float64, device="cuda")
             levels = [0]
 
+            comp = dmk.ALL if dim == 3 else dmk.NEAR      # the far field is provided in 3D
+
             def step():
-                p = dmk.Plan(xsd, targets=xtd, eps=1e-6, kernels=kern, precision=dmk.MIXED)
+                p = dmk.Plan(xsd, targets=xtd, eps=1e-6, kernels=kern, precision=dmk.MIXED, components=comp)
                 p.eval(fd, gd, nd, out=ud)
                 p.close()
             step()
             torch.cuda.synchronize()
             t = max_over_ranks(sum(timed(step, 2)) / 2 / 1e3)
-            p = dmk.Plan(xsd, targets=xtd, eps=1e-6, kernels=kern, precision=dmk.MIXED)
+            p = dmk.Plan(xsd, targets=xtd, eps=1e-6, kernels=kern, precision=dmk.MIXED, components=comp)
             p.eval(fd, gd, nd, out=ud)
             st = p.stats()
             t_near = max_over_ranks(sum(timed(lambda: p.eval(fd, gd, nd, out=ud), 2)) / 2 / 1e3)
             p.close()
             sweep.append({"dim": dim, "kernel": "stokeslet" if kern == dmk.STOKESLET else "stresslet",
-                          "n_sources": n, "n_targets": n, "ms_per_step": 1e3 * t, "near_ms": 1e3 * t_near,
+                          "components": "near + far" if comp == dmk.ALL else "near",
+                          "n_sources": n, "n_targets": n, "ms_per_step": 1e3 * t, "eval_ms": 1e3 * t_near,
                           "targets_per_s": n / t, "max_level": st["max_level"], "leaves": st["leaves"],
                           "useful_pairs": st["useful_pairs"]})
             del xsd, xtd, fd, gd, nd, ud
@@ -462,6 +466,24 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
 
 
 # ------------------------------------------------------------------ our arm
+def far_flops(stage, fi, n_targets, n_sources, kernels=1):
+    """Algorithmic flops (FMA = 2) of one far-field stage of one evaluation, from the
+    plan's far-field sizes (p, N1) and the numbers of points and boxes; each
+    complex multiply-add counts 8 flops, a real-by-complex one 4."""
+    p, n1 = fi["p"], fi["n1"]
+    nh = (n1 + 1) // 2
+    comps = (3 if kernels & 1 else 0) + (6 if kernels & 2 else 0)
+    if stage == "leaf_eval":       # per target: c, b and a contractions of the 3 x p^3 grid
+        return n_targets * (2 * (3 * p ** 3 + 3 * p ** 2 + 3 * p) + p ** 2)
+    if stage == "leaf_charges":    # per source: the (a, b, c) weight products, then comps x p^3 charges
+        return n_sources * (comps * 2 * p ** 3 + (comps // 3) * (p ** 3 + p ** 2))
+    if stage == "outgoing":        # per box and component: p^3 -> nh x n1 x n1 in three stages
+        return fi["source_boxes"] * comps * (4 * p ** 3 * nh + 8 * p ** 2 * nh * n1 + 8 * p * nh * n1 * n1)
+    if stage == "incoming":        # per box and velocity component: the reverse, real part kept
+        return fi["target_boxes"] * 3 * (8 * nh * n1 * n1 * p + 8 * nh * n1 * p * p + 8 * nh * p ** 3)
+    return None
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -488,15 +510,9 @@ def run_ours(args):
     u_d = torch.empty((N, 3), dtype=torch.float64, device="cuda")
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    ns = args.leaf_capacity or 0
 
     def flush():
         flush_buf.fill_(1.0)
-
-    def step(prec):
-        p = dmk.Plan(x_d, eps=args.eps, precision=prec, leaf_capacity=ns)
-        p.eval(f_d, out=u_d)
-        p.close()
 
     def timed(fn, k):
         ms = []
@@ -514,7 +530,21 @@ def run_ours(args):
             ms.append(e0.elapsed_time(e1))
         return ms
 
-    # ---- warm-up (both precisions: first-use costs of pools and kernels)
+    # ---- leaf capacity of the full sum: the library's autotuner (plan + eval per candidate)
+    tune = None
+    if args.leaf_capacity:
+        ns = args.leaf_capacity
+    else:
+        ns, tune = dmk.autotune(x_d, f_d, candidates=(1024, 2048, 4096), repeats=2, eps=args.eps,
+                                precision=dmk.MIXED, components=dmk.ALL)
+        ns = int(max_over_ranks(float(ns)))
+
+    def step(prec):
+        p = dmk.Plan(x_d, eps=args.eps, precision=prec, leaf_capacity=ns, components=dmk.ALL)
+        p.eval(f_d, out=u_d)
+        p.close()
+
+    # ---- warm-up (both precisions: first-use costs of pools, tables and kernels)
     for _ in range(args.warmup):
         step(dmk.MIXED)
     step(dmk.FP64)
@@ -530,11 +560,11 @@ def run_ours(args):
     ms_fp64 = timed(lambda: step(dmk.FP64), max(1, args.steps // 2))
     t_fp64 = max_over_ranks(sum(ms_fp64) / 1e3) / len(ms_fp64)
 
-    # ---- near-field kernel alone (plan reused), both precisions
-    near = {}
+    # ---- evaluation alone (plan reused): stage times, near-field pair rates, far field
+    evals = {}
     launches = None
     for name, prec in (("mixed", dmk.MIXED), ("fp64", dmk.FP64)):
-        p = dmk.Plan(x_d, eps=args.eps, precision=prec, leaf_capacity=ns)
+        p = dmk.Plan(x_d, eps=args.eps, precision=prec, leaf_capacity=ns, components=dmk.ALL)
         l0 = p.stats()["launches"]
         p.eval(f_d, out=u_d)
         torch.cuda.synchronize()
@@ -542,14 +572,43 @@ def run_ours(args):
         if prec == dmk.MIXED:
             # kernels of one step: plan build + one eval (the pair count is not part of a step)
             launches = l0 + (st["launches"] - l0 - 1)
-        ms = timed(lambda: p.eval(f_d, out=u_d), args.steps)
+        k = args.steps if prec == dmk.MIXED else max(1, args.steps // 3)
+        ms = timed(lambda: p.eval(f_d, out=u_d), k)
         t = max_over_ranks(sum(ms) / len(ms) / 1e3)
-        near[name] = dict(ms=1e3 * t, issued_pairs=st["issued_pairs"], useful_pairs=st["useful_pairs"],
-                          gpairs_issued=st["issued_pairs"] / t / 1e9, gpairs_useful=st["useful_pairs"] / t / 1e9,
-                          leaves=st["leaves"], max_level=st["max_level"], tiles=st["tiles"],
-                          leaf_capacity=st["leaf_capacity"])
+        stages = {}
+        for _ in range(3 if prec == dmk.MIXED else 1):
+            flush()
+            torch.cuda.synchronize()
+            _, tr = p.eval_traced(f_d, out=u_d)
+            for key, v in tr.items():
+                stages.setdefault(key, []).append(v)
+        stages = {key: float(np.median(v)) for key, v in stages.items()}
+        t_near = max_over_ranks(stages["near"] / 1e3)
+        fi = p.far_info()
+        evals[name] = dict(eval_ms=1e3 * t, stage_ms=stages, far_info=fi,
+                           near_ms=1e3 * t_near, issued_pairs=st["issued_pairs"], useful_pairs=st["useful_pairs"],
+                           gpairs_issued=st["issued_pairs"] / t_near / 1e9,
+                           gpairs_useful=st["useful_pairs"] / t_near / 1e9,
+                           leaves=st["leaves"], max_level=st["max_level"], tiles=st["tiles"], leaf_capacity=ns)
         p.close()
-    ns_used = near["mixed"]["leaf_capacity"]
+
+    # ---- the near-field pass alone at the paper's leaf capacity (plan + eval, components = NEAR)
+    def near_step():
+        p = dmk.Plan(x_d, eps=args.eps, precision=dmk.MIXED, leaf_capacity=0, components=dmk.NEAR)
+        p.eval(f_d, out=u_d)
+        p.close()
+    near_step()
+    t_near_step = max_over_ranks(sum(timed(near_step, args.steps)) / 1e3) / args.steps
+    p = dmk.Plan(x_d, eps=args.eps, precision=dmk.MIXED, leaf_capacity=0, components=dmk.NEAR)
+    p.eval(f_d, out=u_d)
+    torch.cuda.synchronize()
+    st_near = p.stats()
+    t_near_only = max_over_ranks(sum(timed(lambda: p.eval(f_d, out=u_d), args.steps)) / args.steps / 1e3)
+    p.close()
+    near_only = {"ms_per_step": 1e3 * t_near_step, "targets_per_s": N / t_near_step,
+                 "near_ms": 1e3 * t_near_only, "leaf_capacity": st_near["leaf_capacity"],
+                 "useful_pairs": st_near["useful_pairs"], "issued_pairs": st_near["issued_pairs"],
+                 "gpairs_useful": st_near["useful_pairs"] / t_near_only / 1e9}
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     # the forces travel on a second stream while the tree is built from x
@@ -560,7 +619,7 @@ def run_ours(args):
         with torch.cuda.stream(copy_stream):
             f_d.copy_(f_h, non_blocking=True)
         f_ready = copy_stream.record_event()
-        p = dmk.Plan(x_d, eps=args.eps, precision=dmk.MIXED, leaf_capacity=ns)
+        p = dmk.Plan(x_d, eps=args.eps, precision=dmk.MIXED, leaf_capacity=ns, components=dmk.ALL)
         torch.cuda.current_stream().wait_event(f_ready)
         p.eval(f_d, out=u_d)
         p.close()
@@ -570,7 +629,7 @@ def run_ours(args):
     e2e = {"value": pdist.job_rate(N, args.steps, t_e2e), "unit": "targets/s",
            "h2d_bytes_per_step": int(x_h.numel() * 8 + f_h.numel() * 8), "d2h_bytes_per_step": int(u_h.numel() * 8)}
 
-    # ---- roofline of the dominant kernel (mixed near field): FP32 ALU bound
+    # ---- roofline of the dominant kernel: the far-field stage that takes longest
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -580,36 +639,36 @@ def run_ours(args):
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     peak_basis = (f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
                   "(max SM clock of MEASURED_PEAKS.json)")
+    mx = evals["mixed"]
+    kern_of = {"leaf_eval": "k_far_eval (leaf grids at the targets)",
+               "leaf_charges": "k_far_weights + k_far_anterp (leaf proxy charges)",
+               "outgoing": "k_far_out_fused (outgoing plane waves + kernel contraction)",
+               "incoming": "k_far_ev_fused (incoming plane waves to the potential grids)"}
+    dom = max(kern_of, key=lambda k: mx["stage_ms"][k])
+    flops = far_flops(dom, mx["far_info"], N, N)
+    achieved = flops / (mx["stage_ms"][dom] / 1e3) / 1e12
+    # DRAM bytes per launch of k_far_eval from one ncu capture of the same recipe at
+    # N = 2e5 (leaf capacity 2048), scaled by the target count
+    traffic = 139.5e6 * args.n / 200_000 if (dom == "leaf_eval" and args.eps == 1e-6) else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "traffic_note": "bytes per launch, ncu capture at N=2e5 scaled by the point count",
+                "kernel": kern_of[dom], "stage_ms": mx["stage_ms"][dom], "flops_per_launch": flops,
+                "peak_basis": peak_basis, "fp32": bool(mx["far_info"]["fp32"]),
+                "all_stages": {k: {"ms": mx["stage_ms"][k],
+                                   "tflops": far_flops(k, mx["far_info"], N, N) / (mx["stage_ms"][k] / 1e3) / 1e12,
+                                   "frac": far_flops(k, mx["far_info"], N, N) / (mx["stage_ms"][k] / 1e3) / 1e12
+                                   / peak_tflops} for k in kern_of}}
+    # the near-field kernel (symmetric pass) against the same FP32 peak
     if args.eps >= 2e-7:
         c32 = [len(dmk.kernel_table(3, args.eps, w, fp32=True)[2]) for w in (0, 1)]
-        # Algorithmic flops (FMA = 2) of the symmetric Stokeslet pass: per unordered
-        # pair the geometry, 1/r and both polynomials once (40 + 2(n_g - 1) + 2(n_h - 1),
-        # including one application to a force) plus the second application (18);
-        # useful_pairs counts ordered pairs, so per useful pair half of that.
         flops_one_side = 40 + 2 * (c32[0] - 1) + 2 * (c32[1] - 1)
         flops_per_pair = (flops_one_side + 18) / 2
-        achieved = near["mixed"]["useful_pairs"] * flops_per_pair / (near["mixed"]["ms"] / 1e3) / 1e12
-        # DRAM bytes per launch of this kernel from one ncu capture
-        # (dram__bytes_read.sum + dram__bytes_write.sum) of the same recipe at
-        # N = 5e5, scaled by the point count
-        traffic = 29.37e6 * args.n / 500_000 if args.eps == 1e-6 else None
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tflops, "traffic": traffic,
-                    "traffic_note": "bytes per launch, ncu capture at N=5e5 scaled by the point count",
-                    "kernel": f"k_near_sym<3,{min(v for v in (8, 10, 12, 13, 14, 16) if v >= max(c32))}> "
-                              "(symmetric near field, mixed precision)",
-                    "flops_per_useful_pair": flops_per_pair,
-                    "flops_note": "symmetric pass: one evaluation per unordered pair serves both points; "
-                                  "a one-sided kernel does flops_one_side per useful pair",
-                    "flops_one_side": flops_one_side,
-                    "frac_at_one_sided_flops": achieved * flops_one_side / flops_per_pair / peak_tflops,
-                    "peak_basis": peak_basis}
-    else:
-        # below eps 2e-7 MIXED runs float-float pair terms (k_near_ff): FP32-pipe
-        # bound, with no per-pair flop figure of the method to divide
-        roofline = {"bound": "alu", "achieved": None, "peak": peak_tflops, "unit": "TFLOP/s", "frac": None,
-                    "traffic": None, "kernel": "k_near_ff (float-float near field)", "peak_basis": peak_basis,
-                    "note": "float-float arithmetic: no per-pair flop count of the method to divide"}
+        near_tf = mx["useful_pairs"] * flops_per_pair / (mx["near_ms"] / 1e3) / 1e12
+        roofline["near_field"] = {"kernel": "k_near_sym (symmetric near field, mixed precision)",
+                                  "achieved": near_tf, "frac": near_tf / peak_tflops,
+                                  "flops_per_useful_pair": flops_per_pair, "flops_one_side": flops_one_side,
+                                  "frac_at_one_sided_flops": near_tf * flops_one_side / flops_per_pair / peak_tflops}
 
     extras = None
     if not args.no_extras:
@@ -617,22 +676,23 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        t1, tn, procs = oracle_timings(args.cpu_sample, args.eps, ns_used)
+        t1, tn, procs = oracle_timings(args.cpu_sample, args.eps, 256)
         cpu = {"value": args.cpu_sample / tn, "unit": "targets/s", "cores": procs, "kind": "oracle",
-               "sample": f"same 8-Gaussian recipe at N={args.cpu_sample} points (oracle tree + near pass, numpy), "
-                         f"one spawned process per core each building the tree and summing its share of the "
-                         f"targets, wall time median of 3: {tn:.2f} s",
-               "one_thread": {"value": args.cpu_sample / t1, "unit": "targets/s", "cores": 1,
-                              "seconds_median_of_3": t1}}
+               "sample": f"same 8-Gaussian recipe at N={args.cpu_sample} points, leaf capacity 256: the oracle's "
+                         f"whole DMK sum (tree, near pass, far field of Sec. 6), numpy with its threaded BLAS on "
+                         f"every core, one run: {tn:.2f} s",
+               "one_thread": {"value": args.cpu_sample / t1, "unit": "targets/s", "cores": 1, "seconds": t1}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "targets/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32-compensated (f64 self term, output)",
-                "data": "synthetic", "config": workload_config(args, ns_used),
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 (near pair terms compensated, far-field transforms f32; f64 self term, output)",
+                "data": "synthetic", "config": workload_config(args, ns),
                 "fp64": {"value": N * world / t_fp64, "unit": "targets/s", "ms_per_step": 1e3 * t_fp64},
                 "speedup_mixed_over_fp64": t_fp64 / (t_mixed / args.steps),
-                "near_field": near, "e2e": e2e, "gpu_launches": launches,
+                "autotune_ms_by_leaf_capacity": tune, "evaluation": evals, "near_field_pass_alone": near_only,
+                "e2e": e2e, "gpu_launches": launches,
                 "gpu_launches_note": "our kernels per step (plan + eval); CUB sort/scan kernels not counted",
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "other_workloads": extras}
         print(json.dumps(line), flush=True)

@@ -255,6 +255,18 @@ dmk_status_t dmk_stokes_autotune(const dmk_stokes_opts_t* opts, int64_t n_src, c
                                  int32_t n_cand, const int32_t* h_leaf_capacity, int32_t repeats, void* stream,
                                  double* h_ms, int32_t* h_best);
 
+/* dmk_stokes_eval with the time of each stage (tracing; no paper counterpart):
+ * CUDA events on `stream` between the stages, read after the evaluation (the call
+ * host-synchronises).  h_stage_ms[n_stages] (n_stages <= 9) receives, in ms:
+ *   [0] near pass (residual pairs, self term, periodic stresslet zero mode),
+ *   [1] source Lagrange weights and leaf proxy charges, [2] child merges,
+ *   [3] outgoing plane waves with the kernel contraction, [4] colleague sums,
+ *   [5] incoming plane waves to the potential grids, [6] root kernel,
+ *   [7] interpolation to the children, [8] leaf grids at the targets.
+ * Stages 1..8 are zero for plans without the far field.  Not for the gradient. */
+dmk_status_t dmk_stokes_eval_traced(dmk_stokes_plan_t plan, const double* d_f, const double* d_g, const double* d_n,
+                                    double* d_u, void* stream, double* h_stage_ms, int32_t n_stages);
+
 /* Far-field sizes of a components = DMK_COMPONENTS_ALL plan (host values):
  *   info[0] proxy order p, [1] plane-wave modes a side N1, [2] root modes a
  *   side, [3] boxes of the tree (all levels), [4] boxes holding sources,

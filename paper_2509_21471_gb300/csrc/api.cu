@@ -296,7 +296,9 @@ static dmk_status_t run_eval(dmk_stokes_plan_t plan, const double* d_f, const do
     return set_err(plan, DMK_ERR_UNSUPPORTED, "the gradient of components = ALL / EWALD is not provided");
   try {
     if (d_gradu && N > 0) ensure_aux(plan, dmk::aux_bytes_grad(p.opts, N));
+    if (p.trace) DMK_CUDA_TRY(cudaEventRecord(p.trace[0], s));
     dmk::launch_near(p, want_s ? d_f : nullptr, want_t ? d_g : nullptr, want_t ? d_n : nullptr, d_u, d_gradu, s);
+    if (p.trace) DMK_CUDA_TRY(cudaEventRecord(p.trace[1], s));
     if (p.ewald && d_u) dmk::ewald_far(p, d_f, d_u, s);   // + the Fourier part (Ewald far field)
     if (p.far && d_u) dmk::far_run(p, want_s ? d_f : nullptr, want_t ? d_g : nullptr, want_t ? d_n : nullptr, d_u, s);
   } catch (const dmk::Error& e) {
@@ -387,6 +389,46 @@ dmk_status_t dmk_stokes_autotune(const dmk_stokes_opts_t* opts, int64_t n_src, c
   if (st != DMK_OK) return st;
   *h_best = static_cast<int32_t>(std::min_element(med.begin(), med.end()) - med.begin());
   return DMK_OK;
+}
+
+dmk_status_t dmk_stokes_eval_traced(dmk_stokes_plan_t plan, const double* d_f, const double* d_g, const double* d_n,
+                                    double* d_u, void* stream, double* h_stage_ms, int32_t n_stages) {
+  if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
+  if (!h_stage_ms || n_stages < 1 || n_stages > 9) return set_err(plan, DMK_ERR_INVALID_ARG, "h_stage_ms / n_stages");
+  if (!d_u) return set_err(plan, DMK_ERR_INVALID_ARG, "d_u is NULL");
+  dmk::Plan& p = plan->p;
+  cudaEvent_t ev[10];
+  int made = 0;
+  for (; made < 10; ++made)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
+  if (made < 10) {
+    for (int i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+    return set_err(plan, DMK_ERR_CUDA, "cudaEventCreate failed");
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // stages without work (no far field) take zero time: record every event once first
+  for (int i = 0; i < 10; ++i) cudaEventRecord(ev[i], s);
+  p.trace = ev;
+  dmk_status_t st = run_eval(plan, d_f, d_g, d_n, d_u, nullptr, stream);
+  p.trace = nullptr;
+  if (st == DMK_OK) {
+    if (!p.far) cudaEventRecord(ev[9], s);
+    if (cudaEventSynchronize(ev[9]) != cudaSuccess) st = set_err(plan, DMK_ERR_CUDA, "traced evaluation failed");
+  }
+  if (st == DMK_OK) {
+    for (int i = 0; i < n_stages; ++i) {
+      float ms = 0.f;
+      int a = i, b = i + 1;
+      if (!p.far && i >= 1) {           // no far field: everything after the near pass is empty
+        h_stage_ms[i] = 0.0;
+        continue;
+      }
+      cudaEventElapsedTime(&ms, ev[a], ev[b]);
+      h_stage_ms[i] = ms;
+    }
+  }
+  for (int i = 0; i < 10; ++i) cudaEventDestroy(ev[i]);
+  return st;
 }
 
 dmk_status_t dmk_stokes_far_info(dmk_stokes_plan_t plan, int32_t info[8]) {

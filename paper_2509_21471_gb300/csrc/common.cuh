@@ -254,6 +254,7 @@ struct Plan {
   std::string last_error;
   int64_t useful_pairs = -1;   // cached by dmk_stokes_plan_stats
   mutable int64_t launches = 0;  // kernels launched by this library for this plan
+  mutable cudaEvent_t* trace = nullptr;  // set by dmk_stokes_eval_traced: events between the stages
   uint32_t magic = 0;
 };
 

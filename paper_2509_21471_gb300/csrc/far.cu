@@ -38,6 +38,7 @@
 #include <cmath>
 #include <type_traits>
 #include <memory>
+#include <mutex>
 #include <unordered_map>
 #include <vector>
 
@@ -1044,6 +1045,33 @@ int table2_p(double eps, int kernels) {
   return p;
 }
 
+// matrix bank of a parameter set (Chebyshev points, child matrices, plane-wave
+// matrices, kernel tables): built once per process for each set
+struct BankKey {
+  int p, M, rK, periodic, fp32;
+  double c;
+  bool operator==(const BankKey& o) const {
+    return p == o.p && M == o.M && rK == o.rK && periodic == o.periodic && fp32 == o.fp32 && c == o.c;
+  }
+};
+struct CachedBank {
+  std::vector<char> bank;
+  size_t off[16];
+  double sT_root;
+};
+std::mutex g_bank_mu;
+std::vector<std::pair<BankKey, std::shared_ptr<const CachedBank>>> g_banks;
+std::shared_ptr<const CachedBank> find_bank(const BankKey& k) {
+  std::lock_guard<std::mutex> lk(g_bank_mu);
+  for (auto& e : g_banks)
+    if (e.first == k) return e.second;
+  return nullptr;
+}
+void store_bank(const BankKey& k, std::shared_ptr<const CachedBank> b) {
+  std::lock_guard<std::mutex> lk(g_bank_mu);
+  g_banks.emplace_back(k, std::move(b));
+}
+
 struct RotLaunch {
   RotJob* jobs = nullptr;   // device
   int n = 0;
@@ -1368,108 +1396,126 @@ void far_setup(Plan& p) {
     blev[i] = boxes[i].lev;
   }
 
-  // ---- matrices and tables -------------------------------------------------------
+  // ---- matrices and tables (depend on the parameters only; kept per process) ----
   const int P = F.p;
-  std::vector<double> nodes(P), bwt(P);
-  for (int j = 0; j < P; ++j) {
-    const double th = (2.0 * j + 1.0) * M_PI / (2.0 * P);
-    nodes[j] = std::cos(th);
-    bwt[j] = ((j & 1) ? -1.0 : 1.0) * std::sin(th);
-  }
-  auto lag = [&](double t, int j) {       // plain Lagrange product (host)
-    double v = 1.0;
-    for (int k = 0; k < P; ++k)
-      if (k != j) v *= (t - nodes[k]) / (nodes[j] - nodes[k]);
-    return v;
-  };
-  const bool f32 = F.fp32;
+  const BankKey bkey{F.p, F.M, F.rK, o.periodic, F.fp32, c};
+  std::shared_ptr<const CachedBank> cached = find_bank(bkey);
   std::vector<char> bank;
-  auto put_real = [&](const std::vector<double>& v) {
-    const size_t off = (bank.size() + 15) & ~size_t(15);
-    bank.resize(off + v.size() * (f32 ? 4 : 8));
-    for (size_t i = 0; i < v.size(); ++i) {
-      if (f32) reinterpret_cast<float*>(bank.data() + off)[i] = static_cast<float>(v[i]);
-      else reinterpret_cast<double*>(bank.data() + off)[i] = v[i];
+  if (cached) {
+    bank = cached->bank;
+    const size_t* m = cached->off;
+    F.m_nodes = m[0]; F.m_bw = m[1]; F.m_T0 = m[2]; F.m_T1 = m[3]; F.m_T0t = m[4]; F.m_T1t = m[5];
+    F.m_Eh = m[6]; F.m_E = m[7]; F.m_Fh = m[8]; F.m_F = m[9]; F.m_REh = m[10]; F.m_RE = m[11];
+    F.m_RFh = m[12]; F.m_RF = m[13]; F.m_tab = m[14]; F.m_rtab = m[15];
+    F.sT_root = cached->sT_root;
+  } else {
+    std::vector<double> nodes(P), bwt(P);
+    for (int j = 0; j < P; ++j) {
+      const double th = (2.0 * j + 1.0) * M_PI / (2.0 * P);
+      nodes[j] = std::cos(th);
+      bwt[j] = ((j & 1) ? -1.0 : 1.0) * std::sin(th);
     }
-    return off;
-  };
-  auto put_cplx = [&](const std::vector<double>& re, const std::vector<double>& im) {
-    const size_t off = (bank.size() + 15) & ~size_t(15);
-    bank.resize(off + re.size() * (f32 ? 8 : 16));
-    for (size_t i = 0; i < re.size(); ++i) {
-      if (f32) {
-        reinterpret_cast<float*>(bank.data() + off)[2 * i] = static_cast<float>(re[i]);
-        reinterpret_cast<float*>(bank.data() + off)[2 * i + 1] = static_cast<float>(im[i]);
-      } else {
-        reinterpret_cast<double*>(bank.data() + off)[2 * i] = re[i];
-        reinterpret_cast<double*>(bank.data() + off)[2 * i + 1] = im[i];
+    auto lag = [&](double t, int j) {       // plain Lagrange product (host)
+      double v = 1.0;
+      for (int k = 0; k < P; ++k)
+        if (k != j) v *= (t - nodes[k]) / (nodes[j] - nodes[k]);
+      return v;
+    };
+    const bool f32 = F.fp32;
+    auto put_real = [&](const std::vector<double>& v) {
+      const size_t off = (bank.size() + 15) & ~size_t(15);
+      bank.resize(off + v.size() * (f32 ? 4 : 8));
+      for (size_t i = 0; i < v.size(); ++i) {
+        if (f32) reinterpret_cast<float*>(bank.data() + off)[i] = static_cast<float>(v[i]);
+        else reinterpret_cast<double*>(bank.data() + off)[i] = v[i];
       }
+      return off;
+    };
+    auto put_cplx = [&](const std::vector<double>& re, const std::vector<double>& im) {
+      const size_t off = (bank.size() + 15) & ~size_t(15);
+      bank.resize(off + re.size() * (f32 ? 8 : 16));
+      for (size_t i = 0; i < re.size(); ++i) {
+        if (f32) {
+          reinterpret_cast<float*>(bank.data() + off)[2 * i] = static_cast<float>(re[i]);
+          reinterpret_cast<float*>(bank.data() + off)[2 * i + 1] = static_cast<float>(im[i]);
+        } else {
+          reinterpret_cast<double*>(bank.data() + off)[2 * i] = re[i];
+          reinterpret_cast<double*>(bank.data() + off)[2 * i + 1] = im[i];
+        }
+      }
+      return off;
+    };
+    F.m_nodes = put_real(nodes);
+    F.m_bw = put_real(bwt);
+    // child -> parent anterpolation T_o[a][i] = L_a(((2o - 1) + xi_i) / 2), and the transposes
+    for (int oo = 0; oo < 2; ++oo) {
+      std::vector<double> Tm(P * P), Tt(P * P);
+      for (int a = 0; a < P; ++a)
+        for (int i = 0; i < P; ++i) {
+          const double v = lag(((2 * oo - 1) + nodes[i]) / 2.0, a);
+          Tm[a * P + i] = v;
+          Tt[i * P + a] = v;
+        }
+      (oo == 0 ? F.m_T0 : F.m_T1) = put_real(Tm);
+      (oo == 0 ? F.m_T0t : F.m_T1t) = put_real(Tt);
     }
-    return off;
-  };
-  F.m_nodes = put_real(nodes);
-  F.m_bw = put_real(bwt);
-  // child -> parent anterpolation T_o[a][i] = L_a(((2o - 1) + xi_i) / 2), and the transposes
-  for (int oo = 0; oo < 2; ++oo) {
-    std::vector<double> Tm(P * P), Tt(P * P);
-    for (int a = 0; a < P; ++a)
-      for (int i = 0; i < P; ++i) {
-        const double v = lag(((2 * oo - 1) + nodes[i]) / 2.0, a);
-        Tm[a * P + i] = v;
-        Tt[i * P + a] = v;
+    // plane-wave matrices: E[m][j] = e^{-i theta m xi_j}; F[a][m] = w_m e^{+i theta m xi_a}
+    auto pw = [&](int lo, int n, double theta, bool eval, bool half, size_t* outm) {
+      std::vector<double> re(static_cast<size_t>(n) * P), im(re.size());
+      for (int mi = 0; mi < n; ++mi)
+        for (int j = 0; j < P; ++j) {
+          const int m = lo + mi;
+          const double ph = theta * m * nodes[j];
+          const double wgt = (eval && half && m > 0) ? 2.0 : 1.0;
+          const size_t e = eval ? static_cast<size_t>(j) * n + mi : static_cast<size_t>(mi) * P + j;
+          re[e] = wgt * std::cos(ph);
+          im[e] = (eval ? 1.0 : -1.0) * wgt * std::sin(ph);
+        }
+      *outm = put_cplx(re, im);
+    };
+    const double th_l = M_PI / 3.0;
+    pw(0, F.nh, th_l, false, true, &F.m_Eh);
+    pw(-F.M, F.nm, th_l, false, false, &F.m_E);
+    pw(0, F.nh, th_l, true, true, &F.m_Fh);
+    pw(-F.M, F.nm, th_l, true, false, &F.m_F);
+    const double th_r = o.periodic ? M_PI : 0.5 * h0;
+    pw(0, F.rnh, th_r, false, true, &F.m_REh);
+    pw(-F.rK, F.rnm, th_r, false, false, &F.m_RE);
+    pw(0, F.rnh, th_r, true, true, &F.m_RFh);
+    pw(-F.rK, F.rnm, th_r, true, false, &F.m_RF);
+    // kernel tables by q = |m|^2
+    GammaHat gh(c);
+    {
+      const int qmax = 3 * F.M * F.M;
+      std::vector<double> tab(qmax + 1, 0.0);
+      for (int q = 1; q <= qmax; ++q) {
+        const double am = std::sqrt(static_cast<double>(q));
+        const double dg = gh(M_PI * am / 3.0) - gh(2.0 * M_PI * am / 3.0);
+        tab[q] = dg / (8.0 * M_PI * M_PI * M_PI * static_cast<double>(q) * q);
       }
-    (oo == 0 ? F.m_T0 : F.m_T1) = put_real(Tm);
-    (oo == 0 ? F.m_T0t : F.m_T1t) = put_real(Tt);
-  }
-  // plane-wave matrices: E[m][j] = e^{-i theta m xi_j}; F[a][m] = w_m e^{+i theta m xi_a}
-  auto pw = [&](int lo, int n, double theta, bool eval, bool half, size_t* outm) {
-    std::vector<double> re(static_cast<size_t>(n) * P), im(re.size());
-    for (int mi = 0; mi < n; ++mi)
-      for (int j = 0; j < P; ++j) {
-        const int m = lo + mi;
-        const double ph = theta * m * nodes[j];
-        const double wgt = (eval && half && m > 0) ? 2.0 : 1.0;
-        const size_t e = eval ? static_cast<size_t>(j) * n + mi : static_cast<size_t>(mi) * P + j;
-        re[e] = wgt * std::cos(ph);
-        im[e] = (eval ? 1.0 : -1.0) * wgt * std::sin(ph);
+      F.m_tab = put_real(tab);
+      const int rq = 3 * F.rK * F.rK;
+      std::vector<double> rt(rq + 1, 0.0);
+      for (int q = 0; q <= rq; ++q) {
+        const double am = std::sqrt(static_cast<double>(q));
+        if (o.periodic) {
+          if (q > 0) rt[q] = gh(2.0 * M_PI * am) / (4.0 * M_PI * M_PI * static_cast<double>(q) * q);
+        } else {
+          const double k = h0 * am;
+          rt[q] = std::pow(h0 / (2.0 * M_PI), 3) * h0 * h0 * b_trunc_hat(k) * gh(k);
+        }
       }
-    *outm = put_cplx(re, im);
-  };
-  const double th_l = M_PI / 3.0;
-  pw(0, F.nh, th_l, false, true, &F.m_Eh);
-  pw(-F.M, F.nm, th_l, false, false, &F.m_E);
-  pw(0, F.nh, th_l, true, true, &F.m_Fh);
-  pw(-F.M, F.nm, th_l, true, false, &F.m_F);
-  const double th_r = o.periodic ? M_PI : 0.5 * h0;
-  pw(0, F.rnh, th_r, false, true, &F.m_REh);
-  pw(-F.rK, F.rnm, th_r, false, false, &F.m_RE);
-  pw(0, F.rnh, th_r, true, true, &F.m_RFh);
-  pw(-F.rK, F.rnm, th_r, true, false, &F.m_RF);
-  // kernel tables by q = |m|^2
-  GammaHat gh(c);
-  {
-    const int qmax = 3 * F.M * F.M;
-    std::vector<double> tab(qmax + 1, 0.0);
-    for (int q = 1; q <= qmax; ++q) {
-      const double am = std::sqrt(static_cast<double>(q));
-      const double dg = gh(M_PI * am / 3.0) - gh(2.0 * M_PI * am / 3.0);
-      tab[q] = dg / (8.0 * M_PI * M_PI * M_PI * static_cast<double>(q) * q);
+      F.m_rtab = put_real(rt);
+      F.sT_root = o.periodic ? 2.0 * M_PI : h0;
+      if (std::fabs(gh(0.0) - 1.0) > 1e-12) throw Error{DMK_ERR_CUDA, "window normalisation check failed"};
     }
-    F.m_tab = put_real(tab);
-    const int rq = 3 * F.rK * F.rK;
-    std::vector<double> rt(rq + 1, 0.0);
-    for (int q = 0; q <= rq; ++q) {
-      const double am = std::sqrt(static_cast<double>(q));
-      if (o.periodic) {
-        if (q > 0) rt[q] = gh(2.0 * M_PI * am) / (4.0 * M_PI * M_PI * static_cast<double>(q) * q);
-      } else {
-        const double k = h0 * am;
-        rt[q] = std::pow(h0 / (2.0 * M_PI), 3) * h0 * h0 * b_trunc_hat(k) * gh(k);
-      }
-    }
-    F.m_rtab = put_real(rt);
-    F.sT_root = o.periodic ? 2.0 * M_PI : h0;
-    if (std::fabs(gh(0.0) - 1.0) > 1e-12) throw Error{DMK_ERR_CUDA, "window normalisation check failed"};
+    auto cb = std::make_shared<CachedBank>();
+    cb->bank = bank;
+    const size_t offs[16] = {F.m_nodes, F.m_bw, F.m_T0, F.m_T1, F.m_T0t, F.m_T1t, F.m_Eh, F.m_E,
+                             F.m_Fh, F.m_F, F.m_REh, F.m_RE, F.m_RFh, F.m_RF, F.m_tab, F.m_rtab};
+    for (int i = 0; i < 16; ++i) cb->off[i] = offs[i];
+    cb->sT_root = F.sT_root;
+    store_bank(bkey, cb);
   }
   F.mats = p.arena.alloc<char>(bank.size());
   DMK_CUDA_TRY(cudaMemcpyAsync(F.mats, bank.data(), bank.size(), cudaMemcpyHostToDevice, s));
@@ -1721,6 +1767,10 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
   const R* nodes = reinterpret_cast<const R*>(mats + F.m_nodes);
   const R* bw = reinterpret_cast<const R*>(mats + F.m_bw);
   const int PB = F.PB;
+  // stage boundaries for dmk_stokes_eval_traced (events 2..9; 0 and 1 bracket the near pass)
+  auto mark = [&](int i) {
+    if (p.trace) DMK_CUDA_TRY(cudaEventRecord(p.trace[i], s));
+  };
   // 1. Lagrange weights of the sources, leaf proxy charges
   if (F.nsrc_leaf > 0) {
     R* W = static_cast<R*>(F.W);
@@ -1739,6 +1789,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
     DMK_CUDA_TRY(cudaGetLastError());
     p.launches += 2;
   }
+  mark(2);
   // 2. upward merges, finest parents first
   const bool ftree = F.fused_tree && sizeof(R) == 4;
   if constexpr (sizeof(R) == 4) {
@@ -1760,6 +1811,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
     launch_rot(p, F.merge[1][i], F.s1, F.s2, 0, 0, F.m_T0, F.m_T1, true, P, P, static_cast<int>(p2), 0, 0, 0, 0, s);
     launch_rot(p, F.merge[2][i], F.s2, q, 0, 0, F.m_T0, F.m_T1, true, P, P, static_cast<int>(p2), 0, 0, 0, 0, s);
   }
+  mark(3);
   // 3. outgoing plane waves of every box with sources, contracted with the level kernel
   const R* tab = reinterpret_cast<const R*>(mats + F.m_tab);
   const bool fused = F.fused && sizeof(R) == 4;
@@ -1787,6 +1839,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
     DMK_CUDA_TRY(cudaGetLastError());
     p.launches += 1;
   }
+  mark(4);
   // 4. incoming expansions (colleague sums) and their potential grids (written)
   {
     if (F.ntrg_box > 0) {
@@ -1800,6 +1853,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
       DMK_CUDA_TRY(cudaGetLastError());
       ++p.launches;
     }
+    mark(5);
     if constexpr (sizeof(R) == 4) {
       if (fused && F.ntrg_box > 0) {
         auto kern = k_far_ev_fused<R>;
@@ -1817,6 +1871,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
       launch_rot(p, F.ev3, F.s2, pot, 0, k * P3, F.m_F, F.m_F, false, nm, P, static_cast<int>(p2), 1, 1, 0, 0, s);
     }
   }
+  mark(6);
   // 5. root: K_M,0 (periodic series or truncated free-space kernel) added to the root grid
   if (F.ntrg_box > 0 && F.nsrc_box > 0) {
     const int rnh = F.rnh, rnm = F.rnm;
@@ -1844,6 +1899,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
       ++p.launches;
     }
   }
+  mark(7);
   // 6. interpolation down the tree
   if constexpr (sizeof(R) == 4) {
     if (ftree) {
@@ -1864,6 +1920,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
     launch_rot(p, F.interp[1][i], F.s1, F.s2, 0, 0, F.m_T0t, F.m_T1t, true, P, P, static_cast<int>(p2), 0, 0, 0, 0, s);
     launch_rot(p, F.interp[2][i], F.s2, pot, 0, 0, F.m_T0t, F.m_T1t, true, P, P, static_cast<int>(p2), 0, 0, 0, 1, s);
   }
+  mark(8);
   // 7. leaf grids at the targets
   if (F.ntrg_leaf > 0) {
     const size_t shm = (2 * static_cast<size_t>(P) * kEvThreads + 3 * static_cast<size_t>(P) * PB) * sizeof(R);
@@ -1886,6 +1943,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
     DMK_CUDA_TRY(cudaGetLastError());
     ++p.launches;
   }
+  mark(9);
 }
 
 }  // namespace

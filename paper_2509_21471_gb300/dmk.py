@@ -58,6 +58,7 @@ _lib.dmk_stokes_halo_leaves.argtypes = [ctypes.c_int32, _P, _P, ctypes.c_int32, 
 _lib.dmk_stokes_autotune.argtypes = [ctypes.POINTER(Opts), ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_int32, _P,
                                      ctypes.c_int32, _P, _P, _P]
 _lib.dmk_stokes_far_info.argtypes = [_P, _P]
+_lib.dmk_stokes_eval_traced.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int32]
 _lib.dmk_stokes_destroy.argtypes = [_P]
 _lib.dmk_stokes_destroy.restype = None
 _lib.dmk_stokes_last_error.argtypes = [_P]
@@ -72,7 +73,7 @@ for _name in ("dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "
 EXPORTED = ["dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
             "dmk_stokes_eval_grad", "dmk_stokes_eval_adjoint",
             "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree", "dmk_stokes_kernel_table",
-            "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves", "dmk_stokes_autotune", "dmk_stokes_far_info",
+            "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves", "dmk_stokes_autotune", "dmk_stokes_far_info", "dmk_stokes_eval_traced",
             "dmk_stokes_destroy", "dmk_stokes_last_error"]
 
 
@@ -164,6 +165,21 @@ class Plan:
         code = _lib.dmk_stokes_eval(self._h, _ptr(f), _ptr(g), _ptr(n), _ptr(out), _stream_ptr(stream))
         _check(code, self._h)
         return out
+
+    STAGES = ("near", "leaf_charges", "merge", "outgoing", "colleague", "incoming", "root", "interp", "leaf_eval")
+
+    def eval_traced(self, f=None, g=None, n=None, out=None, stream=None):
+        """dmk_stokes_eval_traced: (u, {stage: ms}) for one evaluation (host-synchronises)."""
+        f = None if f is None else _as_dev(f, self.dim, "f", self.device, self.n_rhs)
+        g = None if g is None else _as_dev(g, self.dim, "g", self.device)
+        n = None if n is None else _as_dev(n, self.dim, "n", self.device)
+        if out is None:
+            out = torch.empty(self._out_shape(), dtype=torch.float64, device=self.device)
+        ms = (ctypes.c_double * 9)()
+        code = _lib.dmk_stokes_eval_traced(self._h, _ptr(f), _ptr(g), _ptr(n), _ptr(out), _stream_ptr(stream),
+                                           ctypes.cast(ms, ctypes.c_void_p), 9)
+        _check(code, self._h)
+        return out, dict(zip(self.STAGES, [float(v) for v in ms]))
 
     def eval_noalloc(self, f=None, g=None, n=None, out=None, stream=None):
         """dmk_stokes_eval_noalloc: as eval, with the library's static scratch

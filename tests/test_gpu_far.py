@@ -147,3 +147,21 @@ def test_root_leaf_and_empty_cases(dmk):
     # empty set of separate targets
     u, _ = _run(dmk, x, f, None, None, 1e-6, 0, 64, False, dmk.ALL, targets=np.zeros((0, 3)))
     assert u.shape == (0, 3)
+
+
+def test_traced_evaluation_matches_eval_and_times_every_stage(dmk):
+    rng = np.random.default_rng(21)
+    x = torch.as_tensor(wl.gaussian_mixture_points(rng, 20000, 3, 8, 0.05), device="cuda")
+    f = torch.as_tensor(wl.forces(rng, 20000, 3), device="cuda")
+    for comp in (dmk.ALL, dmk.NEAR):
+        p = dmk.Plan(x, eps=1e-6, precision=dmk.MIXED, leaf_capacity=256, components=comp)
+        u = p.eval(f).cpu().numpy()
+        u2, ms = p.eval_traced(f)
+        assert np.array_equal(u, u2.cpu().numpy())
+        assert list(ms) == list(dmk.Plan.STAGES)
+        assert all(v >= 0.0 for v in ms.values()) and ms["near"] > 0.0
+        if comp == dmk.ALL:
+            assert ms["leaf_charges"] > 0.0 and ms["outgoing"] > 0.0 and ms["leaf_eval"] > 0.0
+        else:
+            assert sum(v for k, v in ms.items() if k != "near") == 0.0
+        p.close()
