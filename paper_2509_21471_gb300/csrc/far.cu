@@ -235,8 +235,8 @@ __device__ inline void lagrange_row(R t, int p, const R* nodes, const R* bw, R* 
 // long (zeros past p), PB a multiple of the c-chunk of the anterpolation (24 in
 // float32, 12 in float64)
 template <typename R> constexpr int ant_chunk() { return sizeof(R) == 4 ? 24 : 12; }
-constexpr int kAntChunk = 32;
-constexpr int kAntThreads = 544;
+constexpr int kAntChunk = 64;
+constexpr int kAntThreads = 320;
 
 // Lagrange weights of every point of the listed leaves, once per evaluation:
 // W[s][axis][PB] in sorted point order
@@ -270,7 +270,7 @@ __global__ void k_far_weights(const int32_t* __restrict__ leaf_list, const int32
 // one (a, b) and a chunk of consecutive c; the leaf's weights stream through shared
 // memory 32 sources at a time.
 template <typename R>
-__global__ void __launch_bounds__(kAntThreads) k_far_anterp(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
+__global__ void __launch_bounds__(kAntThreads, 2) k_far_anterp(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
                                                             const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ leaf_count,
                                                             const R* __restrict__ W, const int32_t* __restrict__ perm,
                                                             const double* __restrict__ f, const double* __restrict__ g,
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kAntThreads) k_far_anterp(const int32_t* __res
   const int ntask = p * p * nchunk;
   const int64_t p3 = static_cast<int64_t>(p) * p * p;
   R* qb = q + (static_cast<int64_t>(box) * ncomp + slot) * p3;
-  for (int t0 = 0; t0 < ntask; t0 += blockDim.x) {
+  for (int t0 = blockIdx.z * blockDim.x; t0 < ntask; t0 += gridDim.z * blockDim.x) {
     const int task = t0 + threadIdx.x;
     const bool on = task < ntask;
     const int a = on ? task / (p * nchunk) : 0;
@@ -897,99 +897,128 @@ __global__ void k_far_corr(const R* __restrict__ q_root, int slot_f, R* __restri
 }
 
 // leaf evaluation: u[caller][k] += sum_abc L_a(x) L_b(y) L_c(z) pot[box][k][a][b][c].
-// One thread per target; its c-weights stay in registers (PB of them, zero past p),
-// the leaf's grid passes through shared memory one a-slab (3 x p x PB) at a time.
+// A block takes one chunk of at most kEvThreads targets of one leaf (item it:
+// leaf list entry it_leaf[it], first target it_off[it]), one thread per target;
+// its c-weights stay in registers (PB of them, zero past p).  The leaf's grid
+// passes through shared memory one a-slab (3 x p x PB) at a time, double
+// buffered: slab a + 1 is read into registers while slab a is used.
 constexpr int kEvThreads = 128;
 template <typename R, int PB>
-__global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
+__global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restrict__ it_leaf, const int32_t* __restrict__ it_off,
+                                                         const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
                                                          const int32_t* __restrict__ t_start, const int32_t* __restrict__ t_count,
                                                          const double* __restrict__ tw, int64_t NT, const int32_t* __restrict__ tperm,
                                                          const BoxGeo* __restrict__ box_geo, const R* __restrict__ pot, int p,
                                                          const R* __restrict__ nodes, const R* __restrict__ bw,
                                                          double* __restrict__ u) {
+  // slab entries per thread (p <= PB); prefetched into registers when that is few
+  constexpr int kSlabPer = (3 * PB * PB + kEvThreads - 1) / kEvThreads;
+  constexpr bool kPre = kSlabPer <= 16;
   extern __shared__ __align__(16) unsigned char smem[];
   R* sL = reinterpret_cast<R*>(smem);                    // [2][p][kEvThreads]
-  R* sP = sL + 2 * p * kEvThreads;                       // [3][p][PB]
+  R* sP = sL + 2 * p * kEvThreads;                       // [2 buffers][3][p][PB]
   __shared__ R s_nodes[kMaxP], s_bw[kMaxP];
-  const int li = leaf_list[blockIdx.x];
-  const int box = leaf_box[blockIdx.x];
+  const int e = it_leaf[blockIdx.x];
+  const int li = leaf_list[e];
+  const int box = leaf_box[e];
   for (int j = threadIdx.x; j < p; j += blockDim.x) {
     s_nodes[j] = nodes[j];
     s_bw[j] = bw[j];
   }
   const BoxGeo geo = box_geo[box];
   const double inv_half = 1.0 / geo.w;
-  const int t0 = t_start[li], nt = t_count ? t_count[li] : t_start[li + 1] - t0;
+  const int lt0 = t_start[li], lnt = t_count ? t_count[li] : t_start[li + 1] - lt0;
+  const int t0 = lt0 + it_off[blockIdx.x];
+  const int nt = min(kEvThreads, lnt - it_off[blockIdx.x]);
   const int64_t p2 = static_cast<int64_t>(p) * p, p3 = p2 * p;
+  const int slab = 3 * p * PB;
   const R* P = pot + static_cast<int64_t>(box) * 3 * p3;
   __syncthreads();
-  for (int base = 0; base < nt; base += blockDim.x) {
-    const int t = base + threadIdx.x;
-    const bool on = t < nt;
-    R cw[PB];
+  const int t = threadIdx.x;
+  const bool on = t < nt;
+  R cw[PB];
 #pragma unroll
-    for (int j = 0; j < PB; ++j) cw[j] = R(0);
-    if (on) {
-      for (int ax = 0; ax < 2; ++ax) {
-        const double ctr = ax == 0 ? geo.x : geo.y;
-        const R x = static_cast<R>((tw[ax * NT + t0 + t] - ctr) * inv_half);
-        lagrange_row<R>(x, p, s_nodes, s_bw, sL + ax * p * kEvThreads + threadIdx.x, kEvThreads, p);
-      }
-      // the c-weights into registers (unrolled over PB)
-      const R z = static_cast<R>((tw[2 * NT + t0 + t] - geo.z) * inv_half);
-      R ssum = R(0);
-      int hit = -1;
-      for (int j = 0; j < p; ++j) {
-        const R d = z - s_nodes[j];
-        if (d == R(0)) hit = j;
-        else ssum += s_bw[j] / d;
-      }
-      const R inv = hit >= 0 ? R(0) : R(1) / ssum;
-#pragma unroll
-      for (int j = 0; j < PB; ++j)
-        if (j < p) cw[j] = hit >= 0 ? (j == hit ? R(1) : R(0)) : (s_bw[j] / (z - s_nodes[j])) * inv;
+  for (int j = 0; j < PB; ++j) cw[j] = R(0);
+  if (on) {
+    for (int ax = 0; ax < 2; ++ax) {
+      const double ctr = ax == 0 ? geo.x : geo.y;
+      const R x = static_cast<R>((tw[ax * NT + t0 + t] - ctr) * inv_half);
+      lagrange_row<R>(x, p, s_nodes, s_bw, sL + ax * p * kEvThreads + threadIdx.x, kEvThreads, p);
     }
-    R acc0 = 0, acc1 = 0, acc2 = 0;
-    for (int a = 0; a < p; ++a) {
-      __syncthreads();
-      for (int i = threadIdx.x; i < 3 * p * PB; i += blockDim.x) {
-        const int k = i / (p * PB);
-        const int e = i - k * p * PB;
-        const int b = e / PB, c = e - b * PB;
-        sP[i] = c < p ? P[k * p3 + a * p2 + b * p + c] : R(0);
+    const R z = static_cast<R>((tw[2 * NT + t0 + t] - geo.z) * inv_half);
+    R ssum = R(0);
+    int hit = -1;
+    for (int j = 0; j < p; ++j) {
+      const R d = z - s_nodes[j];
+      if (d == R(0)) hit = j;
+      else ssum += s_bw[j] / d;
+    }
+    const R inv = hit >= 0 ? R(0) : R(1) / ssum;
+#pragma unroll
+    for (int j = 0; j < PB; ++j)
+      if (j < p) cw[j] = hit >= 0 ? (j == hit ? R(1) : R(0)) : (s_bw[j] / (z - s_nodes[j])) * inv;
+  }
+  // entry i of slab a: grid value (k, a, b, c) with i = (k p + b) PB + c (zero past p)
+  auto slab_val = [&](int a, int i) {
+    const int k = i / (p * PB);
+    const int r = i - k * p * PB;
+    const int b = r / PB, c = r - b * PB;
+    return c < p ? P[k * p3 + a * p2 + b * p + c] : R(0);
+  };
+  R pre[kPre ? kSlabPer : 1];
+  auto fetch = [&](int a) {
+#pragma unroll
+    for (int n = 0; n < (kPre ? kSlabPer : 1); ++n) {
+      const int i = threadIdx.x + n * kEvThreads;
+      pre[n] = i < slab ? slab_val(a, i) : R(0);
+    }
+  };
+  if constexpr (kPre) fetch(0);
+  R acc0 = 0, acc1 = 0, acc2 = 0;
+  for (int a = 0; a < p; ++a) {
+    R* buf = sP + (a & 1) * slab;
+    if constexpr (kPre) {
+#pragma unroll
+      for (int n = 0; n < kSlabPer; ++n) {
+        const int i = threadIdx.x + n * kEvThreads;
+        if (i < slab) buf[i] = pre[n];
       }
       __syncthreads();
-      if (on) {
-        const R la = sL[a * kEvThreads + threadIdx.x];
-        for (int b = 0; b < p; ++b) {
-          const R lab = la * sL[(p + b) * kEvThreads + threadIdx.x];
-          const R* row = sP + b * PB;
-          R r0 = 0, r1 = 0, r2 = 0;
+      if (a + 1 < p) fetch(a + 1);
+    } else {
+      for (int i = threadIdx.x; i < slab; i += kEvThreads) buf[i] = slab_val(a, i);
+      __syncthreads();
+    }
+    if (on) {
+      const R la = sL[a * kEvThreads + threadIdx.x];
+      for (int b = 0; b < p; ++b) {
+        const R lab = la * sL[(p + b) * kEvThreads + threadIdx.x];
+        const R* row = buf + b * PB;
+        R r0 = 0, r1 = 0, r2 = 0;
 #pragma unroll
-          for (int c4 = 0; c4 < PB / 4; ++c4) {
-            R v0[4], v1[4], v2[4];
-            ld4(row + 4 * c4, v0);
-            ld4(row + p * PB + 4 * c4, v1);
-            ld4(row + 2 * p * PB + 4 * c4, v2);
+        for (int c4 = 0; c4 < PB / 4; ++c4) {
+          R v0[4], v1[4], v2[4];
+          ld4(row + 4 * c4, v0);
+          ld4(row + p * PB + 4 * c4, v1);
+          ld4(row + 2 * p * PB + 4 * c4, v2);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              r0 = fma(cw[4 * c4 + i], v0[i], r0);
-              r1 = fma(cw[4 * c4 + i], v1[i], r1);
-              r2 = fma(cw[4 * c4 + i], v2[i], r2);
-            }
+          for (int i = 0; i < 4; ++i) {
+            r0 = fma(cw[4 * c4 + i], v0[i], r0);
+            r1 = fma(cw[4 * c4 + i], v1[i], r1);
+            r2 = fma(cw[4 * c4 + i], v2[i], r2);
           }
-          acc0 = fma(lab, r0, acc0);
-          acc1 = fma(lab, r1, acc1);
-          acc2 = fma(lab, r2, acc2);
         }
+        acc0 = fma(lab, r0, acc0);
+        acc1 = fma(lab, r1, acc1);
+        acc2 = fma(lab, r2, acc2);
       }
     }
-    if (on) {
-      const int64_t o = tperm[t0 + t];
-      u[o * 3] += static_cast<double>(acc0);
-      u[o * 3 + 1] += static_cast<double>(acc1);
-      u[o * 3 + 2] += static_cast<double>(acc2);
-    }
+  }
+  if (on) {
+    const int64_t o = tperm[t0 + t];
+    u[o * 3] += static_cast<double>(acc0);
+    u[o * 3 + 1] += static_cast<double>(acc1);
+    u[o * 3 + 2] += static_cast<double>(acc2);
   }
 }
 
@@ -1105,6 +1134,9 @@ struct FarState {
   int32_t* trg_leaf = nullptr;
   int32_t* src_box_list = nullptr;   // boxes with sources (outgoing jobs order)
   int32_t* trg_box_list = nullptr;   // boxes with targets (incoming order)
+  int n_ev_items = 0;                // leaf-evaluation work items: chunks of at most kEvThreads targets
+  int32_t* ev_item_leaf = nullptr;   // index into the target-leaf list
+  int32_t* ev_item_off = nullptr;    // first target of the chunk within its leaf
   int fused = 0;                     // 1: float32 transforms of a box in one kernel (shared memory fits)
   size_t fused_out_bytes = 0, fused_ev_bytes = 0;
   int32_t* coll = nullptr;           // [ntrg_box][27] (the root's row is used)
@@ -1531,6 +1563,19 @@ void far_setup(Plan& p) {
   }
   F.src_box_list = upload(p, src_boxes);
   F.trg_box_list = upload(p, trg_boxes);
+  {
+    std::vector<int32_t> il, io;
+    for (size_t e = 0; e < trg_leaf.size(); ++e) {
+      const int nt = tcnt[trg_leaf[e]];
+      for (int off = 0; off < nt; off += kEvThreads) {
+        il.push_back(static_cast<int32_t>(e));
+        io.push_back(off);
+      }
+    }
+    F.n_ev_items = static_cast<int>(il.size());
+    F.ev_item_leaf = upload(p, il);
+    F.ev_item_off = upload(p, io);
+  }
   if (F.fp32) {
     F.fused_out_bytes = fused_out_smem(F.p, F.nh, F.nm, sizeof(float));
     F.fused_ev_bytes = fused_ev_smem(F.p, F.nh, F.nm, sizeof(float));
@@ -1781,10 +1826,12 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
     auto kern = k_far_anterp<R>;
     DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
     const int ntask = P * P * (PB / ant_chunk<R>());
-    const int nthr = std::min(kAntThreads, ((ntask + 31) / 32) * 32);
+    // the (a, b, c-chunk) tasks of a leaf spread over nz blocks of nthr threads
+    const int nz = (ntask + kAntThreads - 1) / kAntThreads;
+    const int nthr = (((ntask + nz - 1) / nz + 31) / 32) * 32;
     const int g0 = F.slot_f >= 0 ? 0 : 1;
     const int ng = (F.slot_f >= 0 ? 1 : 0) + (F.slot_t >= 0 ? 2 : 0);
-    kern<<<dim3(F.nsrc_leaf, ng), nthr, shm, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, W,
+    kern<<<dim3(F.nsrc_leaf, ng, nz), nthr, shm, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, W,
                                                   T.perm, d_f, d_g, d_n, g0, F.slot_f, F.slot_t, nc, q, P, PB);
     DMK_CUDA_TRY(cudaGetLastError());
     p.launches += 2;
@@ -1922,16 +1969,18 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
   }
   mark(8);
   // 7. leaf grids at the targets
-  if (F.ntrg_leaf > 0) {
-    const size_t shm = (2 * static_cast<size_t>(P) * kEvThreads + 3 * static_cast<size_t>(P) * PB) * sizeof(R);
+  if (F.n_ev_items > 0) {
+    const size_t shm = (2 * static_cast<size_t>(P) * kEvThreads + 2 * 3 * static_cast<size_t>(P) * PB) * sizeof(R);
     auto go = [&](auto kern) {
       DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
       if (T.sep)
-        kern<<<F.ntrg_leaf, kEvThreads, shm, s>>>(F.trg_leaf, F.trg_leaf + F.ntrg_leaf, T.leaf_tstart, nullptr, T.tw,
-                                                  T.NT, T.tperm, F.box_geo, pot, P, nodes, bw, d_u);
+        kern<<<F.n_ev_items, kEvThreads, shm, s>>>(F.ev_item_leaf, F.ev_item_off, F.trg_leaf, F.trg_leaf + F.ntrg_leaf,
+                                                   T.leaf_tstart, nullptr, T.tw, T.NT, T.tperm, F.box_geo, pot, P,
+                                                   nodes, bw, d_u);
       else
-        kern<<<F.ntrg_leaf, kEvThreads, shm, s>>>(F.trg_leaf, F.trg_leaf + F.ntrg_leaf, T.leaf_start, T.leaf_count,
-                                                  T.w, T.N, T.perm, F.box_geo, pot, P, nodes, bw, d_u);
+        kern<<<F.n_ev_items, kEvThreads, shm, s>>>(F.ev_item_leaf, F.ev_item_off, F.trg_leaf, F.trg_leaf + F.ntrg_leaf,
+                                                   T.leaf_start, T.leaf_count, T.w, T.N, T.perm, F.box_geo, pot, P,
+                                                   nodes, bw, d_u);
     };
     switch (PB) {
       case 12: go(k_far_eval<R, 12>); break;
