@@ -647,9 +647,10 @@ def run_ours(args):
     dom = max(kern_of, key=lambda k: mx["stage_ms"][k])
     flops = far_flops(dom, mx["far_info"], N, N)
     achieved = flops / (mx["stage_ms"][dom] / 1e3) / 1e12
-    # DRAM bytes per launch of k_far_eval from one ncu capture of the same recipe at
-    # N = 2e5 (leaf capacity 2048), scaled by the target count
-    traffic = 139.5e6 * args.n / 200_000 if (dom == "leaf_eval" and args.eps == 1e-6) else None
+    # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
+    # dram__bytes_write.sum) of the same recipe at N = 2e5, scaled by the point count; none is
+    # recorded for the kernels as they now are
+    traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "traffic_note": "bytes per launch, ncu capture at N=2e5 scaled by the point count",
