@@ -686,6 +686,7 @@ __global__ void __launch_bounds__(1024) k_far_out_fused(const int32_t* __restric
   const int p2 = p * p;
   const int64_t p3 = static_cast<int64_t>(p2) * p, modes = static_cast<int64_t>(nh) * nm * nm;
   C* Ob = O + static_cast<int64_t>(box) * 3 * modes;
+  const bool raw3 = ncomp == 3 && slot_f == 0;   // Stokeslet alone: contract once after the three spectra
   for (int k = 0; k < ncomp; ++k) {
     const int comp = (slot_f >= 0 && k < 3) ? k : 3 + (k - slot_t);
     const R* qk = q + (static_cast<int64_t>(box) * ncomp + k) * p3;
@@ -707,6 +708,12 @@ __global__ void __launch_bounds__(1024) k_far_out_fused(const int32_t* __restric
       warp_contract<R, true, true, 2>(sY2, [r0](int r) { return static_cast<int64_t>(r0 + r); }, nh * nm, p, nr, sE, nm,
                                       [&](int m, int r, R re, R im) { sY1[r * nm + m] = C{re, im}; });
       __syncthreads();
+      if (raw3) {                    // Stokeslet alone: the raw spectrum of component k into O[box][k]
+        for (int i = threadIdx.x; i < nr * nm; i += blockDim.x)
+          Ob[k * modes + static_cast<int64_t>(r0) * nm + i] = sY1[i];
+        __syncthreads();
+        continue;
+      }
       for (int i = threadIdx.x; i < nr * nm; i += blockDim.x) {
         const int r = r0 + i / nm, m = i - (i / nm) * nm;
         const C v = sY1[i];
@@ -747,12 +754,30 @@ __global__ void __launch_bounds__(1024) k_far_out_fused(const int32_t* __restric
       __syncthreads();
     }
   }
+  if (raw3) {
+    // O_j = h t(q) (q rho_j - m_j (m . rho)) in place over the box's modes
+    __syncthreads();
+    for (int64_t mi = threadIdx.x; mi < modes; mi += blockDim.x) {
+      const int r = static_cast<int>(mi / nm), m = static_cast<int>(mi - static_cast<int64_t>(r) * nm);
+      const int m0 = r / nm, m1 = r - m0 * nm - Mh, m2 = m - Mh;
+      const int qi = m0 * m0 + m1 * m1 + m2 * m2;
+      const R sc = h * tab[qi], qq = R(qi);
+      const C x0 = Ob[mi], x1 = Ob[modes + mi], x2 = Ob[2 * modes + mi];
+      const R dr = R(m0) * x0.x + R(m1) * x1.x + R(m2) * x2.x;
+      const R di = R(m0) * x0.y + R(m1) * x1.y + R(m2) * x2.y;
+      Ob[mi] = C{sc * (qq * x0.x - R(m0) * dr), sc * (qq * x0.y - R(m0) * di)};
+      Ob[modes + mi] = C{sc * (qq * x1.x - R(m1) * dr), sc * (qq * x1.y - R(m1) * di)};
+      Ob[2 * modes + mi] = C{sc * (qq * x2.x - R(m2) * dr), sc * (qq * x2.y - R(m2) * di)};
+    }
+  }
 }
 
 // child merge of one parent, one component per block (float32):
-//   q[parent] = sum over children o of (T_o0 (x) T_o1 (x) T_o2) q[child o]
-// each child through three contractions in shared memory; chl[g][8]: box id of
-// child o (o_a = bit a) or -1 (no sources)
+//   q[parent] = sum over children o of (T_o0 (x) T_o1 (x) T_o2) q[child o],
+// with the sums over o0 and o1 taken after the first and second contractions
+// (Y1 = sum_o0 T_o0 q[o], Z_o2 = sum_o1 T_o1 Y1, q = sum_o2 T_o2 Z_o2: 14 instead
+// of 24 p^4 multiply-adds) in four p^3 buffers of shared memory; chl[g][8]: box
+// id of child o (o_a = bit a) or -1 (no sources)
 template <typename R>
 __global__ void __launch_bounds__(1024) k_far_merge_fused(const int32_t* __restrict__ parents, const int32_t* __restrict__ chl,
                                                           R* __restrict__ q, int ncomp, const R* __restrict__ T0,
@@ -761,40 +786,60 @@ __global__ void __launch_bounds__(1024) k_far_merge_fused(const int32_t* __restr
   const int p4 = (p + 3) & ~3, p2 = p * p;
   const int64_t p3 = static_cast<int64_t>(p2) * p;
   R* sT = reinterpret_cast<R*>(smem);                                   // [2][p][p4] transposed T_0, T_1
-  R* sX = sT + 2 * p * p4;
-  R* sY1 = sX + p3;
-  R* sY2 = sY1 + p3;
-  R* sAcc = sY2 + p3;
+  R* sX = sT + 2 * p * p4;                                              // child charges; later the result
+  R* sY = sX + p3;
+  R* sZ = sY + p3;                                                      // [2][p^3]: Z_0, Z_1
   const int g = blockIdx.x, k = blockIdx.y;
   load_AT(sT, T0, p, p);
   load_AT(sT + p * p4, T1, p, p);
-  for (int i = threadIdx.x; i < p3; i += blockDim.x) sAcc[i] = R(0);
-  for (int o = 0; o < 8; ++o) {
-    const int cb = chl[g * 8 + o];
-    if (cb < 0) continue;
-    const R* X = q + (static_cast<int64_t>(cb) * ncomp + k) * p3;
-    __syncthreads();
-    for (int i = threadIdx.x; i < p3; i += blockDim.x) sX[i] = X[i];
-    __syncthreads();
-    const R* A0 = sT + (o & 1) * p * p4;
-    const R* A1 = sT + ((o >> 1) & 1) * p * p4;
-    const R* A2 = sT + (o >> 2) * p * p4;
-    warp_contract<R, false, false, 2>(sX, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A0, p,
-                                      [&](int m, int r, R re, R) { sY1[r * p + m] = re; });
-    __syncthreads();
-    warp_contract<R, false, false, 2>(sY1, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A1, p,
-                                      [&](int m, int r, R re, R) { sY2[r * p + m] = re; });
-    __syncthreads();
-    warp_contract<R, false, false, 2>(sY2, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A2, p,
-                                      [&](int m, int r, R re, R) { sAcc[r * p + m] += re; });
-  }
+  int cz[2] = {0, 0};                                                   // contributions held in Z_o2
+  auto id = [](int r) { return static_cast<int64_t>(r); };
+  for (int o2 = 0; o2 < 2; ++o2)
+    for (int o1 = 0; o1 < 2; ++o1) {
+      int ny = 0;
+      for (int o0 = 0; o0 < 2; ++o0) {
+        const int cb = chl[g * 8 + (o0 | (o1 << 1) | (o2 << 2))];
+        if (cb < 0) continue;
+        const R* X = q + (static_cast<int64_t>(cb) * ncomp + k) * p3;
+        __syncthreads();
+        for (int i = threadIdx.x; i < p3; i += blockDim.x) sX[i] = X[i];
+        __syncthreads();
+        const bool first = ny == 0;
+        warp_contract<R, false, false, 2>(sX, id, p2, p, p2, sT + o0 * p * p4, p, [&](int m, int r, R re, R) {
+          if (first) sY[r * p + m] = re;
+          else sY[r * p + m] += re;
+        });
+        ++ny;
+      }
+      if (ny == 0) continue;
+      __syncthreads();
+      R* Z = sZ + o2 * p3;
+      const bool first = cz[o2] == 0;
+      warp_contract<R, false, false, 2>(sY, id, p2, p, p2, sT + o1 * p * p4, p, [&](int m, int r, R re, R) {
+        if (first) Z[r * p + m] = re;
+        else Z[r * p + m] += re;
+      });
+      ++cz[o2];
+    }
   __syncthreads();
+  int nw = 0;
+  for (int o2 = 0; o2 < 2; ++o2) {
+    if (cz[o2] == 0) continue;
+    const bool first = nw == 0;
+    warp_contract<R, false, false, 2>(sZ + o2 * p3, id, p2, p, p2, sT + o2 * p * p4, p, [&](int m, int r, R re, R) {
+      if (first) sX[r * p + m] = re;
+      else sX[r * p + m] += re;
+    });
+    ++nw;
+    __syncthreads();
+  }
   R* Y = q + (static_cast<int64_t>(parents[g]) * ncomp + k) * p3;
-  for (int i = threadIdx.x; i < p3; i += blockDim.x) Y[i] = sAcc[i];
+  for (int i = threadIdx.x; i < p3; i += blockDim.x) Y[i] = nw ? sX[i] : R(0);
 }
 
 // interpolation of one parent's potential grid to its children, one component per
-// block (float32): pot[child o] += (T_o0^T (x) T_o1^T (x) T_o2^T) pot[parent];
+// block (float32): pot[child o] += (T_o0^T (x) T_o1^T (x) T_o2^T) pot[parent], the
+// partial products shared (Z_o0 = T_o0^T pot, Y = T_o1^T Z_o0, child = T_o2^T Y);
 // chl[g][8]: box id of child o or -1 (no targets)
 template <typename R>
 __global__ void __launch_bounds__(1024) k_far_interp_fused(const int32_t* __restrict__ parents, const int32_t* __restrict__ chl,
@@ -804,34 +849,43 @@ __global__ void __launch_bounds__(1024) k_far_interp_fused(const int32_t* __rest
   const int p4 = (p + 3) & ~3, p2 = p * p;
   const int64_t p3 = static_cast<int64_t>(p2) * p;
   R* sT = reinterpret_cast<R*>(smem);
-  R* sX = sT + 2 * p * p4;
-  R* sY1 = sX + p3;
-  R* sY2 = sY1 + p3;
-  R* sY3 = sY2 + p3;
+  R* sX = sT + 2 * p * p4;                                              // parent grid; later a child's result
+  R* sY = sX + p3;
+  R* sZ = sY + p3;                                                      // [2][p^3]: Z_0, Z_1
   const int g = blockIdx.x, k = blockIdx.y;
   load_AT(sT, T0t, p, p);
   load_AT(sT + p * p4, T1t, p, p);
+  int need[2] = {0, 0};
+  for (int o = 0; o < 8; ++o)
+    if (chl[g * 8 + o] >= 0) need[o & 1] = 1;
   const R* Xg = pot + (static_cast<int64_t>(parents[g]) * 3 + k) * p3;
   for (int i = threadIdx.x; i < p3; i += blockDim.x) sX[i] = Xg[i];
-  for (int o = 0; o < 8; ++o) {
-    const int cb = chl[g * 8 + o];
-    if (cb < 0) continue;
-    __syncthreads();
-    const R* A0 = sT + (o & 1) * p * p4;
-    const R* A1 = sT + ((o >> 1) & 1) * p * p4;
-    const R* A2 = sT + (o >> 2) * p * p4;
-    warp_contract<R, false, false, 2>(sX, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A0, p,
-                                      [&](int m, int r, R re, R) { sY1[r * p + m] = re; });
-    __syncthreads();
-    warp_contract<R, false, false, 2>(sY1, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A1, p,
-                                      [&](int m, int r, R re, R) { sY2[r * p + m] = re; });
-    __syncthreads();
-    warp_contract<R, false, false, 2>(sY2, [](int r) { return static_cast<int64_t>(r); }, p2, p, p2, A2, p,
-                                      [&](int m, int r, R re, R) { sY3[r * p + m] = re; });
-    __syncthreads();
-    R* Y = pot + (static_cast<int64_t>(cb) * 3 + k) * p3;
-    for (int i = threadIdx.x; i < p3; i += blockDim.x) Y[i] += sY3[i];
+  __syncthreads();
+  auto id = [](int r) { return static_cast<int64_t>(r); };
+  for (int o0 = 0; o0 < 2; ++o0) {
+    if (!need[o0]) continue;
+    R* Z = sZ + o0 * p3;
+    warp_contract<R, false, false, 2>(sX, id, p2, p, p2, sT + o0 * p * p4, p,
+                                      [&](int m, int r, R re, R) { Z[r * p + m] = re; });
   }
+  for (int o0 = 0; o0 < 2; ++o0)
+    for (int o1 = 0; o1 < 2; ++o1) {
+      const int c0 = chl[g * 8 + (o0 | (o1 << 1))], c1 = chl[g * 8 + (o0 | (o1 << 1) | 4)];
+      if (c0 < 0 && c1 < 0) continue;
+      __syncthreads();
+      warp_contract<R, false, false, 2>(sZ + o0 * p3, id, p2, p, p2, sT + o1 * p * p4, p,
+                                        [&](int m, int r, R re, R) { sY[r * p + m] = re; });
+      for (int o2 = 0; o2 < 2; ++o2) {
+        const int cb = o2 ? c1 : c0;
+        if (cb < 0) continue;
+        __syncthreads();
+        warp_contract<R, false, false, 2>(sY, id, p2, p, p2, sT + o2 * p * p4, p,
+                                          [&](int m, int r, R re, R) { sX[r * p + m] = re; });
+        __syncthreads();
+        R* Yc = pot + (static_cast<int64_t>(cb) * 3 + k) * p3;
+        for (int i = threadIdx.x; i < p3; i += blockDim.x) Yc[i] += sX[i];
+      }
+    }
 }
 
 inline size_t fused_tree_smem(int p, size_t er) {
