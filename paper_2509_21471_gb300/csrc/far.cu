@@ -952,12 +952,13 @@ __global__ void k_far_corr(const R* __restrict__ q_root, int slot_f, R* __restri
 
 // leaf evaluation: u[caller][k] += sum_abc L_a(x) L_b(y) L_c(z) pot[box][k][a][b][c].
 // A block takes one chunk of at most kEvThreads targets of one leaf (item it:
-// leaf list entry it_leaf[it], first target it_off[it]), one thread per target;
-// its c-weights stay in registers (PB of them, zero past p).  The leaf's grid
-// passes through shared memory one a-slab (3 x p x PB) at a time, double
-// buffered: slab a + 1 is read into registers while slab a is used.
+// leaf list entry it_leaf[it], first target it_off[it]); a thread takes TT of
+// them (slots tid + u * blockDim), their c-weights in registers (PB each, zero
+// past p), so that every grid row read from shared memory serves TT targets.  The
+// leaf's grid passes through shared memory one a-slab (3 x p x PB) at a time,
+// double buffered: slab a + 1 is read into registers while slab a is used.
 constexpr int kEvThreads = 128;
-template <typename R, int PB>
+template <typename R, int PB, int TT>
 __global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restrict__ it_leaf, const int32_t* __restrict__ it_off,
                                                          const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
                                                          const int32_t* __restrict__ t_start, const int32_t* __restrict__ t_count,
@@ -965,17 +966,18 @@ __global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restri
                                                          const BoxGeo* __restrict__ box_geo, const R* __restrict__ pot, int p,
                                                          const R* __restrict__ nodes, const R* __restrict__ bw,
                                                          double* __restrict__ u) {
+  constexpr int NTH = kEvThreads / TT;                   // threads of the block
   // slab entries per thread (p <= PB); prefetched into registers when that is few
-  constexpr int kSlabPer = (3 * PB * PB + kEvThreads - 1) / kEvThreads;
-  constexpr bool kPre = kSlabPer <= 16;
+  constexpr int kSlabPer = (3 * PB * PB + NTH - 1) / NTH;
+  constexpr bool kPre = kSlabPer <= 32;
   extern __shared__ __align__(16) unsigned char smem[];
-  R* sL = reinterpret_cast<R*>(smem);                    // [2][p][kEvThreads]
+  R* sL = reinterpret_cast<R*>(smem);                    // [2][p][kEvThreads] a- and b-weights per target slot
   R* sP = sL + 2 * p * kEvThreads;                       // [2 buffers][3][p][PB]
   __shared__ R s_nodes[kMaxP], s_bw[kMaxP];
   const int e = it_leaf[blockIdx.x];
   const int li = leaf_list[e];
   const int box = leaf_box[e];
-  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+  for (int j = threadIdx.x; j < p; j += NTH) {
     s_nodes[j] = nodes[j];
     s_bw[j] = bw[j];
   }
@@ -988,29 +990,35 @@ __global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restri
   const int slab = 3 * p * PB;
   const R* P = pot + static_cast<int64_t>(box) * 3 * p3;
   __syncthreads();
-  const int t = threadIdx.x;
-  const bool on = t < nt;
-  R cw[PB];
+  R cw[TT][PB];
+  bool on[TT];
 #pragma unroll
-  for (int j = 0; j < PB; ++j) cw[j] = R(0);
-  if (on) {
-    for (int ax = 0; ax < 2; ++ax) {
-      const double ctr = ax == 0 ? geo.x : geo.y;
-      const R x = static_cast<R>((tw[ax * NT + t0 + t] - ctr) * inv_half);
-      lagrange_row<R>(x, p, s_nodes, s_bw, sL + ax * p * kEvThreads + threadIdx.x, kEvThreads, p);
-    }
-    const R z = static_cast<R>((tw[2 * NT + t0 + t] - geo.z) * inv_half);
-    R ssum = R(0);
-    int hit = -1;
-    for (int j = 0; j < p; ++j) {
-      const R d = z - s_nodes[j];
-      if (d == R(0)) hit = j;
-      else ssum += s_bw[j] / d;
-    }
-    const R inv = hit >= 0 ? R(0) : R(1) / ssum;
+  for (int uu = 0; uu < TT; ++uu) {
+    const int t = threadIdx.x + uu * NTH;
+    on[uu] = t < nt;
 #pragma unroll
-    for (int j = 0; j < PB; ++j)
-      if (j < p) cw[j] = hit >= 0 ? (j == hit ? R(1) : R(0)) : (s_bw[j] / (z - s_nodes[j])) * inv;
+    for (int j = 0; j < PB; ++j) cw[uu][j] = R(0);
+    if (on[uu]) {
+      for (int ax = 0; ax < 2; ++ax) {
+        const double ctr = ax == 0 ? geo.x : geo.y;
+        const R x = static_cast<R>((tw[ax * NT + t0 + t] - ctr) * inv_half);
+        lagrange_row<R>(x, p, s_nodes, s_bw, sL + ax * p * kEvThreads + t, kEvThreads, p);
+      }
+      const R z = static_cast<R>((tw[2 * NT + t0 + t] - geo.z) * inv_half);
+      R ssum = R(0);
+      int hit = -1;
+      for (int j = 0; j < p; ++j) {
+        const R d = z - s_nodes[j];
+        if (d == R(0)) hit = j;
+        else ssum += s_bw[j] / d;
+      }
+      const R inv = hit >= 0 ? R(0) : R(1) / ssum;
+#pragma unroll
+      for (int j = 0; j < PB; ++j)
+        if (j < p) cw[uu][j] = hit >= 0 ? (j == hit ? R(1) : R(0)) : (s_bw[j] / (z - s_nodes[j])) * inv;
+    } else {
+      for (int j = 0; j < p; ++j) sL[j * kEvThreads + t] = sL[(p + j) * kEvThreads + t] = R(0);
+    }
   }
   // entry i of slab a: grid value (k, a, b, c) with i = (k p + b) PB + c (zero past p)
   auto slab_val = [&](int a, int i) {
@@ -1023,57 +1031,68 @@ __global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restri
   auto fetch = [&](int a) {
 #pragma unroll
     for (int n = 0; n < (kPre ? kSlabPer : 1); ++n) {
-      const int i = threadIdx.x + n * kEvThreads;
+      const int i = threadIdx.x + n * NTH;
       pre[n] = i < slab ? slab_val(a, i) : R(0);
     }
   };
   if constexpr (kPre) fetch(0);
-  R acc0 = 0, acc1 = 0, acc2 = 0;
+  R acc[TT][3];
+#pragma unroll
+  for (int uu = 0; uu < TT; ++uu) acc[uu][0] = acc[uu][1] = acc[uu][2] = R(0);
   for (int a = 0; a < p; ++a) {
     R* buf = sP + (a & 1) * slab;
     if constexpr (kPre) {
 #pragma unroll
       for (int n = 0; n < kSlabPer; ++n) {
-        const int i = threadIdx.x + n * kEvThreads;
+        const int i = threadIdx.x + n * NTH;
         if (i < slab) buf[i] = pre[n];
       }
       __syncthreads();
       if (a + 1 < p) fetch(a + 1);
     } else {
-      for (int i = threadIdx.x; i < slab; i += kEvThreads) buf[i] = slab_val(a, i);
+      for (int i = threadIdx.x; i < slab; i += NTH) buf[i] = slab_val(a, i);
       __syncthreads();
     }
-    if (on) {
-      const R la = sL[a * kEvThreads + threadIdx.x];
-      for (int b = 0; b < p; ++b) {
-        const R lab = la * sL[(p + b) * kEvThreads + threadIdx.x];
-        const R* row = buf + b * PB;
-        R r0 = 0, r1 = 0, r2 = 0;
+    R la[TT];
 #pragma unroll
-        for (int c4 = 0; c4 < PB / 4; ++c4) {
-          R v0[4], v1[4], v2[4];
-          ld4(row + 4 * c4, v0);
-          ld4(row + p * PB + 4 * c4, v1);
-          ld4(row + 2 * p * PB + 4 * c4, v2);
+    for (int uu = 0; uu < TT; ++uu) la[uu] = sL[a * kEvThreads + threadIdx.x + uu * NTH];
+    for (int b = 0; b < p; ++b) {
+      const R* row = buf + b * PB;
+      R r[TT][3];
+#pragma unroll
+      for (int uu = 0; uu < TT; ++uu) r[uu][0] = r[uu][1] = r[uu][2] = R(0);
+#pragma unroll
+      for (int c4 = 0; c4 < PB / 4; ++c4) {
+        R v0[4], v1[4], v2[4];
+        ld4(row + 4 * c4, v0);
+        ld4(row + p * PB + 4 * c4, v1);
+        ld4(row + 2 * p * PB + 4 * c4, v2);
+#pragma unroll
+        for (int uu = 0; uu < TT; ++uu)
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            r0 = fma(cw[4 * c4 + i], v0[i], r0);
-            r1 = fma(cw[4 * c4 + i], v1[i], r1);
-            r2 = fma(cw[4 * c4 + i], v2[i], r2);
+            r[uu][0] = fma(cw[uu][4 * c4 + i], v0[i], r[uu][0]);
+            r[uu][1] = fma(cw[uu][4 * c4 + i], v1[i], r[uu][1]);
+            r[uu][2] = fma(cw[uu][4 * c4 + i], v2[i], r[uu][2]);
           }
-        }
-        acc0 = fma(lab, r0, acc0);
-        acc1 = fma(lab, r1, acc1);
-        acc2 = fma(lab, r2, acc2);
+      }
+#pragma unroll
+      for (int uu = 0; uu < TT; ++uu) {
+        const R lab = la[uu] * sL[(p + b) * kEvThreads + threadIdx.x + uu * NTH];
+        acc[uu][0] = fma(lab, r[uu][0], acc[uu][0]);
+        acc[uu][1] = fma(lab, r[uu][1], acc[uu][1]);
+        acc[uu][2] = fma(lab, r[uu][2], acc[uu][2]);
       }
     }
   }
-  if (on) {
-    const int64_t o = tperm[t0 + t];
-    u[o * 3] += static_cast<double>(acc0);
-    u[o * 3 + 1] += static_cast<double>(acc1);
-    u[o * 3 + 2] += static_cast<double>(acc2);
-  }
+#pragma unroll
+  for (int uu = 0; uu < TT; ++uu)
+    if (on[uu]) {
+      const int64_t o = tperm[t0 + threadIdx.x + uu * NTH];
+      u[o * 3] += static_cast<double>(acc[uu][0]);
+      u[o * 3 + 1] += static_cast<double>(acc[uu][1]);
+      u[o * 3 + 2] += static_cast<double>(acc[uu][2]);
+    }
 }
 
 // ------------------------------------------------------------------ host side
@@ -2025,23 +2044,29 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
   // 7. leaf grids at the targets
   if (F.n_ev_items > 0) {
     const size_t shm = (2 * static_cast<size_t>(P) * kEvThreads + 2 * 3 * static_cast<size_t>(P) * PB) * sizeof(R);
-    auto go = [&](auto kern) {
+    auto go = [&](auto kern, int tt) {
+      const int nth = kEvThreads / tt;
       DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
       if (T.sep)
-        kern<<<F.n_ev_items, kEvThreads, shm, s>>>(F.ev_item_leaf, F.ev_item_off, F.trg_leaf, F.trg_leaf + F.ntrg_leaf,
+        kern<<<F.n_ev_items, nth, shm, s>>>(F.ev_item_leaf, F.ev_item_off, F.trg_leaf, F.trg_leaf + F.ntrg_leaf,
                                                    T.leaf_tstart, nullptr, T.tw, T.NT, T.tperm, F.box_geo, pot, P,
                                                    nodes, bw, d_u);
       else
-        kern<<<F.n_ev_items, kEvThreads, shm, s>>>(F.ev_item_leaf, F.ev_item_off, F.trg_leaf, F.trg_leaf + F.ntrg_leaf,
+        kern<<<F.n_ev_items, nth, shm, s>>>(F.ev_item_leaf, F.ev_item_off, F.trg_leaf, F.trg_leaf + F.ntrg_leaf,
                                                    T.leaf_start, T.leaf_count, T.w, T.N, T.perm, F.box_geo, pot, P,
                                                    nodes, bw, d_u);
     };
-    switch (PB) {
-      case 12: go(k_far_eval<R, 12>); break;
-      case 24: go(k_far_eval<R, 24>); break;
-      case 36: go(k_far_eval<R, 36>); break;
-      case 48: go(k_far_eval<R, 48>); break;
-      default: go(k_far_eval<R, 60>); break;
+    if constexpr (sizeof(R) == 4) {
+      if (PB == 24) go(k_far_eval<R, 24, 2>, 2);
+      else go(k_far_eval<R, 48, 1>, 1);
+    } else {
+      switch (PB) {
+        case 12: go(k_far_eval<R, 12, 1>, 1); break;
+        case 24: go(k_far_eval<R, 24, 1>, 1); break;
+        case 36: go(k_far_eval<R, 36, 1>, 1); break;
+        case 48: go(k_far_eval<R, 48, 1>, 1); break;
+        default: go(k_far_eval<R, 60, 1>, 1); break;
+      }
     }
     DMK_CUDA_TRY(cudaGetLastError());
     ++p.launches;
