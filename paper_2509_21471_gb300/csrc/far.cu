@@ -1672,7 +1672,9 @@ void far_setup(Plan& p) {
   F.scr_stride = st;
   const int64_t P3 = F.p3;
   const int nc = F.ncomp;
-  int64_t max_jobs = std::max<int64_t>(std::max(F.nsrc_box, F.ntrg_box), 1);
+  // the generic stage kernels (and their job lists and scratch) serve what the fused
+  // float32 kernels do not: the root always, the boxes when the fused kernels are off
+  int64_t max_jobs = F.fused ? 1 : std::max<int64_t>(std::max(F.nsrc_box, F.ntrg_box), 1);
   // merges: parent at level l (non-leaf, with sources), per component
   for (int l = maxlev - 1; l >= 0; --l) {
     std::vector<RotJob> j1, j2, j3;
@@ -1727,10 +1729,11 @@ void far_setup(Plan& p) {
     F.mf_ch.push_back(upload(p, fch));
     F.mf_n.push_back(np);
     F.merge_level.push_back(l);
-    F.merge[0].push_back(make_launch(p, j1));
-    F.merge[1].push_back(make_launch(p, j2));
-    F.merge[2].push_back(make_launch(p, j3));
-    max_jobs = std::max<int64_t>(max_jobs, (static_cast<int64_t>(np) * nc * 4 * P3 + 2 * st - 1) / (2 * st) + 1);
+    F.merge[0].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j1));
+    F.merge[1].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j2));
+    F.merge[2].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j3));
+    if (!F.fused_tree)
+      max_jobs = std::max<int64_t>(max_jobs, (static_cast<int64_t>(np) * nc * 4 * P3 + 2 * st - 1) / (2 * st) + 1);
   }
   // interpolation: parent at level l (non-leaf, with targets) to its children with targets
   for (int l = 0; l < maxlev; ++l) {
@@ -1781,10 +1784,11 @@ void far_setup(Plan& p) {
     F.if_ch.push_back(upload(p, fch));
     F.if_n.push_back(np);
     F.interp_level.push_back(l);
-    F.interp[0].push_back(make_launch(p, j1));
-    F.interp[1].push_back(make_launch(p, j2));
-    F.interp[2].push_back(make_launch(p, j3));
-    max_jobs = std::max<int64_t>(max_jobs, (static_cast<int64_t>(np) * 3 * 4 * P3 + 2 * st - 1) / (2 * st) + 1);
+    F.interp[0].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j1));
+    F.interp[1].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j2));
+    F.interp[2].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j3));
+    if (!F.fused_tree)
+      max_jobs = std::max<int64_t>(max_jobs, (static_cast<int64_t>(np) * 3 * 4 * P3 + 2 * st - 1) / (2 * st) + 1);
   }
   // outgoing: one job per source box (the component is the launch offset); eval: per target box
   {
@@ -1816,24 +1820,22 @@ void far_setup(Plan& p) {
       J.y = static_cast<int64_t>(b) * 3 * P3;
       e3.push_back(J);
     }
-    F.out1 = make_launch(p, a1);
-    F.out2 = make_launch(p, a2);
-    F.out3 = make_launch(p, a3);
-    F.ev1 = make_launch(p, e1);
-    F.ev2 = make_launch(p, e2);
-    F.ev3 = make_launch(p, e3);
+    if (!F.fused) {
+      F.out1 = make_launch(p, a1);
+      F.out2 = make_launch(p, a2);
+      F.out3 = make_launch(p, a3);
+      F.ev1 = make_launch(p, e1);
+      F.ev2 = make_launch(p, e2);
+      F.ev3 = make_launch(p, e3);
+    }
     RotJob J;
     J.x1 = -1;
     J.a0 = J.a1 = 0;
     J.x0 = 0;
     J.y = 0;
-    std::vector<RotJob> one{J};
-    F.r1 = make_launch(p, one);                 // x: q[root] (+ component offset)
-    F.r2 = make_launch(p, one);
-    F.r3 = make_launch(p, one);
-    F.rv1 = make_launch(p, one);
-    F.rv2 = make_launch(p, one);
-    F.rv3 = make_launch(p, one);                // y: pot[root] (+ component offset), accumulate
+    // one job at offset 0 for every root stage: q[root], the scratch, pot[root] (+ component offsets)
+    const RotLaunch one = make_launch(p, std::vector<RotJob>{J});
+    F.r1 = F.r2 = F.r3 = F.rv1 = F.rv2 = F.rv3 = one;
   }
   // ---- big buffers -------------------------------------------------------------------
   const size_t er = elem_r(F), ec = 2 * er;
