@@ -35,6 +35,13 @@ if ROOT not in sys.path:
 METRIC = "3D Stokeslet DMK targets/s at eps=1e-6, mixed vs FP64 on GPU; near-field Gpairs/s"
 N_SM = 152
 FP32_LANES_PER_SM = 128
+# DRAM bytes per launch of the candidate dominant kernels at N = 5e5 (8-Gaussian recipe,
+# eps 1e-6, MIXED), keyed by (stage, leaf capacity); filled from ncu captures
+TRAFFIC_5E5 = {("near", 2048): 29.1e6, ("near", 4096): 29.0e6,
+               ("leaf_eval", 2048): 242.0e6, ("leaf_eval", 4096): 185.5e6,
+               ("leaf_charges", 2048): 643.0e6, ("leaf_charges", 4096): 577.2e6,
+               ("outgoing", 2048): 1301.6e6, ("outgoing", 4096): 957.7e6,
+               ("incoming", 2048): 1001.7e6, ("incoming", 4096): 744.3e6}
 
 
 def parse():
@@ -644,30 +651,37 @@ def run_ours(args):
                "leaf_charges": "k_far_weights + k_far_anterp (leaf proxy charges)",
                "outgoing": "k_far_out_fused (outgoing plane waves + kernel contraction)",
                "incoming": "k_far_ev_fused (incoming plane waves to the potential grids)"}
-    dom = max(kern_of, key=lambda k: mx["stage_ms"][k])
-    flops = far_flops(dom, mx["far_info"], N, N)
-    achieved = flops / (mx["stage_ms"][dom] / 1e3) / 1e12
-    # DRAM bytes per launch of the dominant kernel from one ncu capture (dram__bytes_read.sum +
-    # dram__bytes_write.sum) of the same recipe at N = 2e5, scaled by the point count; none is
-    # recorded for the kernels as they now are
-    traffic = None
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": traffic,
-                "traffic_note": "bytes per launch, ncu capture at N=2e5 scaled by the point count",
-                "kernel": kern_of[dom], "stage_ms": mx["stage_ms"][dom], "flops_per_launch": flops,
-                "peak_basis": peak_basis, "fp32": bool(mx["far_info"]["fp32"]),
-                "all_stages": {k: {"ms": mx["stage_ms"][k],
-                                   "tflops": far_flops(k, mx["far_info"], N, N) / (mx["stage_ms"][k] / 1e3) / 1e12,
-                                   "frac": far_flops(k, mx["far_info"], N, N) / (mx["stage_ms"][k] / 1e3) / 1e12
-                                   / peak_tflops} for k in kern_of}}
-    # the near-field kernel (symmetric pass) against the same FP32 peak
+    stage_flops = {k: far_flops(k, mx["far_info"], N, N) for k in kern_of}
+    near_tf = None
     if args.eps >= 2e-7:
         c32 = [len(dmk.kernel_table(3, args.eps, w, fp32=True)[2]) for w in (0, 1)]
+        # Algorithmic flops (FMA = 2) of the symmetric Stokeslet pass: per unordered
+        # pair the geometry, 1/r and both polynomials once (40 + 2(n_g - 1) + 2(n_h - 1),
+        # including one application to a force) plus the second application (18);
+        # useful_pairs counts ordered pairs, so per useful pair half of that.
         flops_one_side = 40 + 2 * (c32[0] - 1) + 2 * (c32[1] - 1)
         flops_per_pair = (flops_one_side + 18) / 2
-        near_tf = mx["useful_pairs"] * flops_per_pair / (mx["near_ms"] / 1e3) / 1e12
-        roofline["near_field"] = {"kernel": "k_near_sym (symmetric near field, mixed precision)",
-                                  "achieved": near_tf, "frac": near_tf / peak_tflops,
+        kern_of["near"] = "k_near_sym (symmetric near field, mixed precision)"
+        stage_flops["near"] = mx["useful_pairs"] * flops_per_pair
+        near_tf = stage_flops["near"] / (mx["stage_ms"]["near"] / 1e3) / 1e12
+    dom = max(kern_of, key=lambda k: mx["stage_ms"][k])
+    achieved = stage_flops[dom] / (mx["stage_ms"][dom] / 1e3) / 1e12
+    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+    # capture of the same recipe at N = 5e5 and the same leaf capacity, scaled by the
+    # point count (profiles/dram_traffic_clustered5e5.md)
+    traffic_5e5 = TRAFFIC_5E5.get((dom, ns)) if args.eps == 1e-6 else None
+    traffic = traffic_5e5 * args.n / 500_000 if traffic_5e5 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "traffic_note": "bytes per launch, ncu capture at N=5e5 (same leaf capacity) scaled by the point count",
+                "kernel": kern_of[dom], "stage_ms": mx["stage_ms"][dom], "flops_per_launch": stage_flops[dom],
+                "peak_basis": peak_basis, "fp32": bool(mx["far_info"]["fp32"]),
+                "all_stages": {k: {"ms": mx["stage_ms"][k],
+                                   "tflops": stage_flops[k] / (mx["stage_ms"][k] / 1e3) / 1e12,
+                                   "frac": stage_flops[k] / (mx["stage_ms"][k] / 1e3) / 1e12 / peak_tflops}
+                               for k in kern_of}}
+    if near_tf is not None:
+        roofline["near_field"] = {"kernel": kern_of["near"], "achieved": near_tf, "frac": near_tf / peak_tflops,
                                   "flops_per_useful_pair": flops_per_pair, "flops_one_side": flops_one_side,
                                   "frac_at_one_sided_flops": near_tf * flops_one_side / flops_per_pair / peak_tflops}
 
