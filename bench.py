@@ -5,7 +5,7 @@ Workload (one rank = one independent system, weak scaling): N = 1e6 points from
 a mixture of 8 isotropic Gaussians (sigma = 0.02, centres uniform in
 [0.2, 0.8]^3, clipped to the unit cube, shifted to [-1/2, 1/2]^3), forces
 N(0, 1), eps = 1e-6 (3c/pi = 17, p = 23, N1 = 33, Table 2); the leaf capacity
-is picked by the library's autotuner among 1024, 2048 and 4096.
+is picked by the library's autotuner among 1024, 2048, 3072, 4096 and 6144.
 
 One step = dmk_stokes_plan (kernel tables, Morton sort, adaptive tree, level
 restriction, near lists, tiles, box hierarchy and far-field job lists) +
@@ -542,7 +542,7 @@ def run_ours(args):
     if args.leaf_capacity:
         ns = args.leaf_capacity
     else:
-        ns, tune = dmk.autotune(x_d, f_d, candidates=(1024, 2048, 4096), repeats=2, eps=args.eps,
+        ns, tune = dmk.autotune(x_d, f_d, candidates=(1024, 2048, 3072, 4096, 6144), repeats=2, eps=args.eps,
                                 precision=dmk.MIXED, components=dmk.ALL)
         ns = int(max_over_ranks(float(ns)))
 

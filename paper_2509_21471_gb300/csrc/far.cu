@@ -1212,7 +1212,7 @@ struct FarState {
   int32_t* ev_item_off = nullptr;    // first target of the chunk within its leaf
   int fused = 0;                     // 1: float32 transforms of a box in one kernel (shared memory fits)
   size_t fused_out_bytes = 0, fused_ev_bytes = 0;
-  int32_t* coll = nullptr;           // [ntrg_box][27] (the root's row is used)
+  int32_t* coll = nullptr;           // [27] colleague slots of the root
   int32_t* root_tlist = nullptr;     // {target index of the root}
   int ngrp = 0;                      // parents whose children hold targets
   int32_t* grp_win = nullptr;        // [ngrp][64]
@@ -1445,8 +1445,10 @@ void far_setup(Plan& p) {
   F.ntrg_box = static_cast<int>(trg_boxes.size());
   F.nsrc_leaf = static_cast<int>(src_leaf.size());
   F.ntrg_leaf = static_cast<int>(trg_leaf.size());
-  std::vector<int32_t> coll(static_cast<size_t>(F.ntrg_box) * 27, -1);
-  for (int t = 0; t < F.ntrg_box; ++t) {
+  // 27 colleague slots of the root (target index 0: boxes are sorted by level); the
+  // other boxes take their colleagues from their parent's window below
+  std::vector<int32_t> coll(27, -1);
+  for (int t = 0; t < std::min(F.ntrg_box, 1); ++t) {
     const Box& b = boxes[trg_boxes[t]];
     const int64_t n = int64_t(1) << b.lev;
     for (int sl = 0; sl < 27; ++sl) {
@@ -1685,6 +1687,10 @@ void far_setup(Plan& p) {
       if (b.lev != l || b.leaf >= 0 || b.src == 0) continue;
       fpar.push_back(i);
       for (int ch = 0; ch < 8; ++ch) fch.push_back(boxes[b.child[ch]].src ? b.child[ch] : -1);
+      if (F.fused_tree) {
+        ++np;
+        continue;
+      }
       for (int k = 0; k < nc; ++k) {
         const int64_t slotbase = (static_cast<int64_t>(np) * nc + k);      // per (parent, comp)
         for (int o12 = 0; o12 < 4; ++o12) {                                 // (o1, o2), stage 1 over o0
@@ -1745,6 +1751,10 @@ void far_setup(Plan& p) {
       if (b.lev != l || b.leaf >= 0 || b.trg == 0) continue;
       fpar.push_back(i);
       for (int ch = 0; ch < 8; ++ch) fch.push_back(boxes[b.child[ch]].trg ? b.child[ch] : -1);
+      if (F.fused_tree) {
+        ++np;
+        continue;
+      }
       for (int k = 0; k < 3; ++k) {
         const int64_t slotbase = static_cast<int64_t>(np) * 3 + k;
         for (int o0 = 0; o0 < 2; ++o0) {
