@@ -50,7 +50,11 @@ The method (Sec. 6.1 Steps 1(c), 2, 3; Sec. 6.2; Sec. 7), as this file takes it:
     between the table rows and rounded up; N1 = 2 (3c/pi) - 1 and
     N_per = 2 floor(c / 2pi) + 1, which reproduce every row of the table.
 
-Only the 3D kernels are covered here.
+In 2D (App. B) the same steps run on p x p grids with N1 x N1 modes, 9
+colleagues, (h/2pi)^2, R = 1 + sqrt(2) and K_corr = (1 - log R)/(4 pi) (Sec. 5.3).
+The difference kernels K_D,l = K_R(r_l) - K_R(r_l+1) are compactly supported,
+so their Fourier transforms carry no constant and take the same
+(gamma-hat(k r_{l+1}) - gamma-hat(k r_l)) / k^4 form as in 3D.
 """
 import itertools
 import math
@@ -136,28 +140,51 @@ def stresslet_hat(kv, Bh, G):
                                  - 2.0 * kv * kGk[..., None])
 
 
-def B_trunc_hat(k):
-    """B-hat^R(k) in 3D, Eq. (Btrunc_hat); the k -> 0 limit is R^4 / 120."""
+def B_trunc_hat(k, d=3):
+    """B-hat^R(k), Eq. (Btrunc_hat), R = 1 + sqrt(d); the k -> 0 limits are R^4/120 (3D)
+    and R^4/64 (2D), reached through the Taylor series of the same brackets."""
+    from scipy.special import j0, j1
     k = np.asarray(k, dtype=np.float64)
-    R = R_TRUNC
+    R = 1.0 + math.sqrt(d)
     kr = k * R
-    out = np.full(k.shape, R ** 4 / 120.0)
+    out = np.empty(k.shape)
     m = kr > 1e-2
     x = kr[m]
-    out[m] = (1.0 + 0.5 * np.cos(x) - 1.5 * np.sin(x) / x) / k[m] ** 4
+    if d == 3:
+        out[m] = (1.0 + 0.5 * np.cos(x) - 1.5 * np.sin(x) / x) / k[m] ** 4
+    else:
+        out[m] = (1.0 - j0(x) - 0.5 * x * j1(x)) / k[m] ** 4
     s = ~m
     x = kr[s]
-    # Taylor series of the same bracket: x^4/120 - x^6/2520 + x^8/120960 (divided by k^4)
-    out[s] = R ** 4 * (1.0 / 120.0 - x ** 2 / 2520.0 + x ** 4 / 120960.0)
+    if d == 3:
+        # x^4/120 - x^6/2520 + x^8/120960 (divided by k^4)
+        out[s] = R ** 4 * (1.0 / 120.0 - x ** 2 / 2520.0 + x ** 4 / 120960.0)
+    else:
+        # 1 - J0(x) - x J1(x)/2 = x^4/64 - x^6/1152 + x^8/49152 (divided by k^4)
+        out[s] = R ** 4 * (1.0 / 64.0 - x ** 2 / 1152.0 + x ** 4 / 49152.0)
     return out
 
 
+def K_corr(d):
+    """The constant of the truncated free-space Stokeslet (Sec. 5.3 after Eq. (Bmollhat_trunc))."""
+    R = 1.0 + math.sqrt(d)
+    return 1.0 / (4.0 * np.pi * R) if d == 3 else (1.0 - math.log(R)) / (4.0 * np.pi)
+
+
+def _applyd(As, X, d):
+    """Y[a1..ad, ...] = sum_i prod_k As[k][a_k, i_k] X[i1..id, ...] (one matrix per axis)."""
+    Y = X
+    for ax in range(d):
+        Y = np.moveaxis(np.tensordot(As[ax], Y, axes=([1], [ax])), 0, ax)
+    return Y
+
+
 class FarField:
-    """The far component of the DMK sum on an oracle.tree.Tree (3D)."""
+    """The far component of the DMK sum on an oracle.tree.Tree (2D or 3D)."""
 
     def __init__(self, tree, win, p, n1, nper):
-        assert tree.dim == 3, "the oracle far field covers 3D"
         self.tree, self.win = tree, win
+        self.d = d = tree.dim
         self.p, self.n1, self.nper = int(p), int(n1), int(nper)
         self.xi = cheb_nodes(self.p)
         # child proxy points in the parent's coordinates: ((2o - 1) + xi) / 2
@@ -181,7 +208,8 @@ class FarField:
 
     def _children(self, B):
         lev, c = B
-        return [((lev + 1, tuple(2 * c[a] + o[a] for a in range(3))), o)
+        d = self.d
+        return [((lev + 1, tuple(2 * c[a] + o[a] for a in range(d))), o)
                 for o in self.tree.child_offsets]
 
     def _colleagues(self, B):
@@ -189,10 +217,11 @@ class FarField:
         the periodic case; delta is the offset of the colleague's image in units
         of the box side)."""
         lev, c = B
+        d = self.d
         n = 2 ** lev
         out = []
-        for dl in itertools.product((-1, 0, 1), repeat=3):
-            raw = tuple(c[a] + dl[a] for a in range(3))
+        for dl in itertools.product((-1, 0, 1), repeat=d):
+            raw = tuple(c[a] + dl[a] for a in range(d))
             if self.tree.periodic:
                 pos = tuple(v % n for v in raw)
             else:
@@ -213,104 +242,112 @@ class FarField:
         return (w - cB[None, :]) / (0.5 * r)
 
     def _level_Bhat(self, lev, k):
-        """B-hat of K_D,lev times (h/2pi)^3."""
+        """B-hat of K_D,lev times (h/2pi)^d."""
         r = 2.0 ** -lev
         h = 2.0 * np.pi / (3.0 * r)
         g = self.win.gammahat(k.ravel() * (0.5 * r), n=600) - self.win.gammahat(k.ravel() * r, n=600)
         g = g.reshape(k.shape)
         out = np.zeros(k.shape)
         nz = k > 0.0
-        out[nz] = g[nz] / k[nz] ** 4 * (h / (2.0 * np.pi)) ** 3
+        out[nz] = g[nz] / k[nz] ** 4 * (h / (2.0 * np.pi)) ** self.d
         return out
+
+    def _grid(self, axis_values):
+        return np.stack(np.meshgrid(*([axis_values] * self.d), indexing="ij"), axis=-1)
 
     # ------------------------------------------------------------- passes
     def charges(self, f=None, g=None, n=None):
-        """Upward pass: proxy charges of every box, {box: (qS[p,p,p,3], qT[p,p,p,3,3])}."""
-        tree, p = self.tree, self.p
+        """Upward pass: proxy charges of every box, {box: (qS[p]*d + [d], qT[p]*d + [d, d])}."""
+        tree, p, d = self.tree, self.p, self.d
+        shp = (p,) * d
         q = {}
         for i, L in enumerate(tree.leaves):
             S = tree.leaf_points(i)
-            qS = np.zeros((p, p, p, 3))
-            qT = np.zeros((p, p, p, 3, 3))
+            qS = np.zeros(shp + (d,))
+            qT = np.zeros(shp + (d, d))
             if len(S):
                 xi = self._local(L, tree.w[S])
-                A = [lagrange(self.xi, xi[:, a]) for a in range(3)]          # [j, s]
+                A = [lagrange(self.xi, xi[:, a]) for a in range(d)]          # [j, s]
+                idx = "abc"[:d]
+                spec = ",".join(f"{x}s" for x in idx)
                 if f is not None:
-                    qS = np.einsum("as,bs,cs,sk->abck", A[0], A[1], A[2], f[S])
+                    qS = np.einsum(f"{spec},sk->{idx}k", *A, f[S])
                 if g is not None:
                     rho = g[S][:, :, None] * n[S][:, None, :]
-                    qT = np.einsum("as,bs,cs,slm->abclm", A[0], A[1], A[2], rho)
+                    qT = np.einsum(f"{spec},slm->{idx}lm", *A, rho)
             q[L] = (qS, qT)
         for lev in range(self.maxlev - 1, -1, -1):
             for B in self.by_level[lev]:
                 if self._is_leaf(B):
                     continue
-                qS = np.zeros((p, p, p, 3))
-                qT = np.zeros((p, p, p, 3, 3))
+                qS = np.zeros(shp + (d,))
+                qT = np.zeros(shp + (d, d))
                 for (C, o) in self._children(B):
                     cS, cT = q[C]
-                    qS += _apply3_each(self.T[o[0]], self.T[o[1]], self.T[o[2]], cS)
-                    qT += _apply3_each(self.T[o[0]], self.T[o[1]], self.T[o[2]], cT)
+                    As = [self.T[o[a]] for a in range(d)]
+                    qS += _applyd(As, cS, d)
+                    qT += _applyd(As, cT, d)
                 q[B] = (qS, qT)
         return q
 
     def _level_modes(self, lev):
-        """k vectors [N1, N1, N1, 3] and (h/2pi)^3 B-hat of K_D,lev (computed once per level)."""
+        """k vectors [N1]*d + [d] and (h/2pi)^d B-hat of K_D,lev (computed once per level)."""
         if lev not in self._modes:
             r = 2.0 ** -lev
             h = 2.0 * np.pi / (3.0 * r)
-            mm = np.stack(np.meshgrid(self.m1, self.m1, self.m1, indexing="ij"), axis=-1)
-            kv = h * mm
+            kv = h * self._grid(self.m1)
             kk = np.sqrt(np.sum(kv * kv, axis=-1))
             self._modes[lev] = (kv, self._level_Bhat(lev, kk))
         return self._modes[lev]
 
     def outgoing(self, lev, qS, qT, want_S, want_T):
-        """Kernel-contracted outgoing plane waves O(m)[N1, N1, N1, 3] at level lev."""
+        """Kernel-contracted outgoing plane waves O(m)[N1]*d + [d] at level lev."""
         kv, Bh = self._level_modes(lev)
-        O = np.zeros(Bh.shape + (3,), dtype=np.complex128)
+        d = self.d
+        O = np.zeros(Bh.shape + (d,), dtype=np.complex128)
         if want_S:
-            O += stokeslet_hat(kv, Bh, _apply3(self.E, qS))
+            O += stokeslet_hat(kv, Bh, _applyd([self.E] * d, qS, d))
         if want_T:
-            O += stresslet_hat(kv, Bh, _apply3(self.E, qT))
+            O += stresslet_hat(kv, Bh, _applyd([self.E] * d, qT, d))
         return O
 
     def root(self, qS, qT, want_S, want_T):
-        """Root potential on the root proxy grid [p, p, p, 3]."""
+        """Root potential on the root proxy grid [p]*d + [d]."""
+        d = self.d
         if self.tree.periodic:
             K = (self.nper - 1) // 2
             kap = np.arange(-K, K + 1, dtype=np.float64)
             # z - c_0 = xi / 2 on the unit cell
             E0 = np.exp(-1j * np.pi * np.outer(kap, self.xi))
-            kv = 2.0 * np.pi * np.stack(np.meshgrid(kap, kap, kap, indexing="ij"), axis=-1)
+            kv = 2.0 * np.pi * self._grid(kap)
             kk = np.sqrt(np.sum(kv * kv, axis=-1))
             Bh = np.zeros(kk.shape)
             nz = kk > 0.0
             Bh[nz] = self.win.gammahat(kk[nz], n=600) / kk[nz] ** 4
         else:
-            h0 = 2.0 * np.pi / (2.0 + 2.0 * math.sqrt(3.0))
+            h0 = 2.0 * np.pi / (2.0 + 2.0 * math.sqrt(d))
             M0 = int(math.ceil(self.win.c / h0)) + 1
             mv = np.arange(-M0, M0 + 1, dtype=np.float64)
             E0 = np.exp(-1j * 0.5 * h0 * np.outer(mv, self.xi))
-            kv = h0 * np.stack(np.meshgrid(mv, mv, mv, indexing="ij"), axis=-1)
+            kv = h0 * self._grid(mv)
             kk = np.sqrt(np.sum(kv * kv, axis=-1))
-            Bh = (B_trunc_hat(kk.ravel()) * self.win.gammahat(kk.ravel(), n=600)).reshape(kk.shape)
-            Bh *= (h0 / (2.0 * np.pi)) ** 3
-        O = np.zeros(kk.shape + (3,), dtype=np.complex128)
+            Bh = (B_trunc_hat(kk.ravel(), d) * self.win.gammahat(kk.ravel(), n=600)).reshape(kk.shape)
+            Bh *= (h0 / (2.0 * np.pi)) ** d
+        O = np.zeros(kk.shape + (d,), dtype=np.complex128)
         if want_S:
-            O += stokeslet_hat(kv, Bh, _apply3(E0, qS))
+            O += stokeslet_hat(kv, Bh, _applyd([E0] * d, qS, d))
         if want_T:
-            O += stresslet_hat(kv, Bh, _apply3(E0, qT))
-        return np.real(_apply3(np.conj(E0).T, O))
+            O += stresslet_hat(kv, Bh, _applyd([E0] * d, qT, d))
+        return np.real(_applyd([np.conj(E0).T] * d, O, d))
 
     def far(self, f=None, g=None, n=None, levels=None, want_root=True):
         """u_far at every point (caller order).  levels: which difference levels
         to include (default all); want_root: include K_M,0 (and K_corr)."""
-        tree, p = self.tree, self.p
+        tree, p, d = self.tree, self.p, self.d
         want_S, want_T = f is not None, g is not None
         q = self.charges(f, g, n)
-        pot = {B: np.zeros((p, p, p, 3)) for B in self.boxes}
-        root = (0, (0, 0, 0))
+        pot = {B: np.zeros((p,) * d + (d,)) for B in self.boxes}
+        root = (0, (0,) * d)
         if want_root:
             pot[root] += self.root(q[root][0], q[root][1], want_S, want_T)
         EtH = np.conj(self.E).T                                            # [j, m] incoming
@@ -322,44 +359,65 @@ class FarField:
                 for B in self.by_level[lev]:
                     I = np.zeros_like(outs[B])
                     for (C, dl) in self._colleagues(B):
-                        ph = (w3 ** dl[0])[:, None, None] * (w3 ** dl[1])[None, :, None] \
-                            * (w3 ** dl[2])[None, None, :]
+                        ph = np.ones((1,) * d)
+                        for a in range(d):
+                            shape = [1] * d
+                            shape[a] = len(self.m1)
+                            ph = ph * (w3 ** dl[a]).reshape(shape)
                         I += ph[..., None] * outs[C]
-                    pot[B] += np.real(_apply3(EtH, I))
+                    pot[B] += np.real(_applyd([EtH] * d, I, d))
             if lev < self.maxlev:
                 for B in self.by_level[lev]:
                     if self._is_leaf(B):
                         continue
                     for (C, o) in self._children(B):
-                        pot[C] += _apply3_each(self.T[o[0]].T, self.T[o[1]].T, self.T[o[2]].T, pot[B])
-        u = np.zeros((tree.N, 3))
+                        pot[C] += _applyd([self.T[o[a]].T for a in range(d)], pot[B], d)
+        u = np.zeros((tree.N, d))
+        idx = "abc"[:d]
+        spec = ",".join(f"{x}s" for x in idx)
         for i, L in enumerate(tree.leaves):
             S = tree.leaf_points(i)
             if len(S) == 0:
                 continue
             xi = self._local(L, tree.w[S])
-            A = [lagrange(self.xi, xi[:, a]) for a in range(3)]
-            u[S] = np.einsum("as,bs,cs,abck->sk", A[0], A[1], A[2], pot[L])
+            A = [lagrange(self.xi, xi[:, a]) for a in range(d)]
+            u[S] = np.einsum(f"{spec},{idx}k->sk", *A, pot[L])
         if want_root and want_S and not tree.periodic:
-            u += np.sum(f, axis=0)[None, :] / (4.0 * np.pi * R_TRUNC)
+            u += np.sum(f, axis=0)[None, :] * K_corr(d)
         return u
 
 
 # ------------------------------------------------------------------ exact parts
-def level_exact(tree, win, lev, f=None, g=None, n=None):
+def _kernels(d, kern):
+    """(residual Stokeslet, residual stresslet, self coefficient, full Stokeslet,
+    full stresslet) for the dimension; kern is the window (3D) or a
+    kernels2d.Kernel2D (2D)."""
+    if d == 3:
+        return (lambda x, nu: k3.stokeslet_res(kern, x, nu), lambda x, nu: k3.stresslet_res(kern, x, nu),
+                lambda nu: k3.stokeslet_self_coeff(kern, nu), k3.stokeslet, k3.stresslet)
+    from . import kernels2d as k2
+    from .direct import stokeslet_2d, stresslet_2d
+    return (lambda x, nu: k2.stokeslet_res(kern, x, nu), lambda x, nu: k2.stresslet_res(kern, x, nu),
+            lambda nu: k2.stokeslet_self_coeff(kern, nu), stokeslet_2d, stresslet_2d)
+
+
+def level_exact(tree, kern, lev, f=None, g=None, n=None):
     """The level-lev difference component summed in real space:
     sum over (s, image) whose level-lev box is a colleague of t's level-lev
     box of K_D,lev(x_t - x_s - image) rho_s, with
-    K_D,lev = K_R(r_lev) - K_R(r_lev+1) (the residual kernels of Sec. 5.2) and
-    K_D,lev(0) from the self terms.  Points whose leaves are coarser than lev
-    have no level-lev box and take no part."""
+    K_D,lev = K_R(r_lev) - K_R(r_lev+1) (the residual kernels of Sec. 5.2 / App. B)
+    and K_D,lev(0) from the self terms.  Points whose leaves are coarser than lev
+    have no level-lev box and take no part.  kern: the window (3D) or a
+    kernels2d.Kernel2D (2D)."""
+    d = tree.dim
     N = tree.N
     r0, r1 = 2.0 ** -lev, 2.0 ** -(lev + 1)
-    u = np.zeros((N, 3))
-    box = tree.cell >> (tree.M - lev)                                     # [N, 3]
+    u = np.zeros((N, d))
+    box = tree.cell >> (tree.M - lev)                                     # [N, d]
     n_side = 2 ** lev
     idx = np.nonzero(tree.point_level >= lev)[0]
-    images = list(itertools.product((-1, 0, 1), repeat=3)) if tree.periodic else [(0, 0, 0)]
+    images = list(itertools.product((-1, 0, 1), repeat=d)) if tree.periodic else [(0,) * d]
+    KS = _kernels(d, kern)
     for t in idx:
         for img in images:
             im = np.array(img, dtype=np.int64)
@@ -369,43 +427,45 @@ def level_exact(tree, win, lev, f=None, g=None, n=None):
                 continue
             dd = (tree.w[t][None, :] - tree.w[S]) - im[None, :].astype(np.float64)
             same = (S == t) & (not any(img))
-            u[t] += _diff_pairs(win, dd, r0, r1, same, f, g, n, S)
+            u[t] += _diff_pairs(KS, d, dd, r0, r1, same, f, g, n, S)
     return u
 
 
-def _diff_pairs(win, dd, r0, r1, same, f, g, n, S):
-    out = np.zeros(3)
+def _diff_pairs(KS, d, dd, r0, r1, same, f, g, n, S):
+    Sres, Tres, self_c = KS[0], KS[1], KS[2]
+    out = np.zeros(d)
     m = ~same
     if np.any(m):
-        d = dd[m]
+        x = dd[m]
         if f is not None:
-            K = k3.stokeslet_res(win, d, r0) - k3.stokeslet_res(win, d, r1)
+            K = Sres(x, r0) - Sres(x, r1)
             out += np.einsum("pjl,pl->j", K, f[S[m]])
         if g is not None:
-            K = k3.stresslet_res(win, d, r0) - k3.stresslet_res(win, d, r1)
+            K = Tres(x, r0) - Tres(x, r1)
             out += np.einsum("pjlm,pl,pm->j", K, g[S[m]], n[S[m]])
     if np.any(same) and f is not None:
         # K_D(0) = K_M(r1)(0) - K_M(r0)(0), K_M,nu(0) = -self coefficient
-        coeff = -k3.stokeslet_self_coeff(win, r1) + k3.stokeslet_self_coeff(win, r0)
+        coeff = -self_c(r1) + self_c(r0)
         out += coeff * f[S[same]].sum(axis=0)
     return out
 
 
-def root_exact_free(tree, win, f=None, g=None, n=None):
+def root_exact_free(tree, kern, f=None, g=None, n=None):
     """K_M,0 summed exactly in free space: sum_{s != t} (K - K_R(1)) rho_s
-    + K_M,1(0) f_t."""
-    from . import kernels3d as k3
+    + K_M,1(0) f_t.  kern: the window (3D) or a kernels2d.Kernel2D (2D)."""
+    d = tree.dim
     N = tree.N
     w = tree.w
-    u = np.zeros((N, 3))
+    Sres, Tres, self_c, Sfull, Tfull = _kernels(d, kern)
+    u = np.zeros((N, d))
     for t in range(N):
         m = np.ones(N, dtype=bool)
         m[t] = False
         dd = w[t][None, :] - w[m]
         if f is not None:
-            K = k3.stokeslet(dd) - k3.stokeslet_res(win, dd, 1.0)
-            u[t] += np.einsum("pjl,pl->j", K, f[m]) - k3.stokeslet_self_coeff(win, 1.0) * f[t]
+            K = Sfull(dd) - Sres(dd, 1.0)
+            u[t] += np.einsum("pjl,pl->j", K, f[m]) - self_c(1.0) * f[t]
         if g is not None:
-            K = k3.stresslet(dd) - k3.stresslet_res(win, dd, 1.0)
+            K = Tfull(dd) - Tres(dd, 1.0)
             u[t] += np.einsum("pjlm,pl,pm->j", K, g[m], n[m])
     return u

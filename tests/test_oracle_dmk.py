@@ -144,3 +144,65 @@ def test_periodic_total_matches_gaussian_ewald():
     ref = ewald.ewald_sum(x, f, g, n, split=ewald.gaussian_split_3d(0.1))
     # the stresslet at the Table 2 bandlimit reaches about 2 eps (a reading stated with the design)
     assert rel_l2(u, ref) < 3 * eps
+
+
+def test_truncated_biharmonic_2d_closed_form_matches_hankel_quadrature():
+    from scipy.special import j0
+    R = 1.0 + np.sqrt(2.0)
+
+    def BR(r):                                         # Eq. (Btrunc), d = 2
+        return (r * r * np.log(r) - r * r / 2 - r * r * np.log(R) + R * R / 2) / (8 * np.pi)
+
+    for k in [1e-4, 1e-3, 0.2, 1.0, 3.7, 11.0]:
+        # 2D transform of a radial function: 2 pi int_0^R B(r) J0(k r) r dr
+        val = 2 * np.pi * quad(lambda r: BR(r) * j0(k * r) * r, 0.0, R, limit=200, epsabs=1e-15, epsrel=1e-12)[0]
+        got = float(dmk.B_trunc_hat(np.array([k]), d=2)[0])
+        assert abs(got - val) <= 1e-9 * max(1.0, abs(val)), (k, got, val)
+
+
+def test_2d_levels_root_and_total_match_exact_sums():
+    """The same pins in 2D (App. B kernels): each level against the real-space
+    difference-kernel sum, the root against K - K_R(1), and near + far against the
+    2D direct sum, free space, Stokeslet + stresslet, eps 1e-3."""
+    from oracle import kernels2d as k2
+    eps = 1e-3
+    rng = np.random.default_rng(12)
+    N = 220
+    x = wl.gaussian_mixture_points(rng, N, 2, 3, 0.08)
+    f = wl.forces(rng, N, 2)
+    g = wl.stresslet_strengths(rng, N, 2)
+    n = wl.unit_normals(rng, N, 2)
+    tcp, p, n1, nper = dmk.dmk_params(eps, stokeslet=True, stresslet=True)
+    win = window.ProlateWindow(tcp * np.pi / 3)
+    kern = k2.Kernel2D(win)
+    T = otree.Tree(x, 12)
+    F = dmk.FarField(T, win, p, n1, nper)
+    assert F.maxlev >= 3 and len(np.unique(T.leaf_level)) >= 2
+    for lev in range(F.maxlev + 1):
+        a = F.far(f, g, n, levels=[lev], want_root=False)
+        b = dmk.level_exact(T, kern, lev, f, g, n)
+        if np.linalg.norm(b) > 0:
+            assert rel_l2(a, b) < 3e-2, (lev, rel_l2(a, b))
+    a = F.far(f, g, n, levels=[], want_root=True)
+    assert rel_l2(a, dmk.root_exact_free(T, kern, f, g, n)) < 1e-3
+    u = near.near_lists(T, dict(k2d=kern, stokeslet=True, stresslet=True), f, g, n) + F.far(f, g, n)
+    assert rel_l2(u, direct.direct_sum(x, f, g, n)) < 3 * eps
+
+
+def test_2d_periodic_total_matches_gaussian_ewald():
+    from oracle import kernels2d as k2
+    eps = 1e-3
+    rng = np.random.default_rng(13)
+    N = 300
+    x = wl.uniform_points(rng, N, 2)
+    f = wl.forces(rng, N, 2, zero_mean=True)
+    g = wl.stresslet_strengths(rng, N, 2)
+    n = wl.unit_normals(rng, N, 2)
+    tcp, p, n1, nper = dmk.dmk_params(eps, stokeslet=True, stresslet=True)
+    win = window.ProlateWindow(tcp * np.pi / 3)
+    kern = k2.Kernel2D(win)
+    T = otree.Tree(x, 12, periodic=True)
+    u = (near.near_lists(T, dict(k2d=kern, stokeslet=True, stresslet=True), f, g, n)
+         + direct.stresslet_zero_mode(T.w, g, n) + dmk.FarField(T, win, p, n1, nper).far(f, g, n))
+    ref = ewald.ewald_sum(x, f, g, n, split=ewald.gaussian_split_2d(0.08))
+    assert rel_l2(u, ref) < 3 * eps
