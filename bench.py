@@ -671,14 +671,27 @@ def run_ours(args):
     # point count (profiles/dram_traffic_clustered5e5.md)
     traffic_5e5 = TRAFFIC_5E5.get((dom, ns)) if args.eps == 1e-6 else None
     traffic = traffic_5e5 * args.n / 500_000 if traffic_5e5 else None
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+
+    def stage_dram(k):
+        # DRAM GB/s of a stage against the measured HBM copy bandwidth: the ncu bytes of
+        # the N = 5e5 capture at the same leaf capacity, scaled by the point count
+        t5 = TRAFFIC_5E5.get((k, ns)) if args.eps == 1e-6 else None
+        if not t5:
+            return {}
+        gbs = t5 * args.n / 500_000 / (mx["stage_ms"][k] / 1e3) / 1e9
+        return {"dram_gbs": gbs, "hbm_frac": gbs / hbm_peak}
+
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "traffic_note": "bytes per launch, ncu capture at N=5e5 (same leaf capacity) scaled by the point count",
                 "kernel": kern_of[dom], "stage_ms": mx["stage_ms"][dom], "flops_per_launch": stage_flops[dom],
                 "peak_basis": peak_basis, "fp32": bool(mx["far_info"]["fp32"]),
+                "hbm_peak_gbs": hbm_peak, "hbm_peak_basis": "hbm_gbs of MEASURED_PEAKS.json (measured copy)",
                 "all_stages": {k: {"ms": mx["stage_ms"][k],
                                    "tflops": stage_flops[k] / (mx["stage_ms"][k] / 1e3) / 1e12,
-                                   "frac": stage_flops[k] / (mx["stage_ms"][k] / 1e3) / 1e12 / peak_tflops}
+                                   "frac": stage_flops[k] / (mx["stage_ms"][k] / 1e3) / 1e12 / peak_tflops,
+                                   **stage_dram(k)}
                                for k in kern_of}}
     if near_tf is not None:
         roofline["near_field"] = {"kernel": kern_of["near"], "achieved": near_tf, "frac": near_tf / peak_tflops,

@@ -88,17 +88,18 @@ typedef struct {
   int32_t components;    /* DMK_COMPONENTS_NEAR: the near component (residual
                             pass + self term, + the periodic stresslet zero
                             mode).
-                            DMK_COMPONENTS_ALL: the whole DMK sum, 3D, one
-                            force column, free space or periodic, Stokeslet
-                            and/or stresslet, sources or separate targets:
-                            the near component plus the far field of Sec. 6
-                            (leaf proxy charges on p^3 Chebyshev grids, child
-                            merges, level-l plane waves with N1 modes a side
-                            for the colleague difference kernels, the root
-                            kernel K_M,0: periodic Fourier series with N_per
-                            modes a side, or the truncated kernel of Eq.
-                            (Bmollhat_trunc) in free space, interpolation to
-                            the leaves).  p, N1, N_per from Table 2 (p
+                            DMK_COMPONENTS_ALL: the whole DMK sum, 2D or 3D,
+                            one force column, free space or periodic,
+                            Stokeslet and/or stresslet, sources or separate
+                            targets: the near component plus the far field of
+                            Sec. 6 (leaf proxy charges on p^d Chebyshev grids,
+                            child merges, level-l plane waves with N1 modes a
+                            side for the colleague difference kernels, the
+                            root kernel K_M,0: periodic Fourier series with
+                            N_per modes a side, or the truncated kernel of
+                            Eq. (Bmollhat_trunc), R = 1 + sqrt(d), in free
+                            space, interpolation to the leaves; App. B
+                            kernels in 2D).  p, N1, N_per from Table 2 (p
                             interpolated in log10 eps, N1 = 2 (3c/pi) - 1,
                             N_per = 2 floor(c / 2pi) + 1).  The far field runs
                             in float32 where the pair terms do (MIXED, eps >=

@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdmk_stokes.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["tables.cpp", "partition.cpp", "tree.cu", "near.cu", "near_mixed.cu", "near_mixed2d.cu", "near_fp64.cu",
-           "near_fp64_2d.cu", "near_ff.cu", "near_adj.cu", "near_close.cu", "ewald.cu", "far.cu", "api.cu", "noalloc.cu"]
+           "near_fp64_2d.cu", "near_ff.cu", "near_adj.cu", "near_close.cu", "ewald.cu", "far.cu", "far2d.cu", "api.cu", "noalloc.cu"]
 
 
 def _nvcc():

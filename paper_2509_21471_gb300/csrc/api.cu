@@ -51,8 +51,8 @@ dmk_status_t validate_opts(const dmk_stokes_opts_t* o, std::string& msg) {
     msg = "components = DMK_COMPONENTS_EWALD is provided for the periodic 3D Stokeslet with one force column";
     return DMK_ERR_UNSUPPORTED;
   }
-  if (o->components == DMK_COMPONENTS_ALL && !(o->dim == 3 && o->n_rhs == 1)) {
-    msg = "components = DMK_COMPONENTS_ALL (the DMK far field) is provided in 3D with one force column";
+  if (o->components == DMK_COMPONENTS_ALL && o->n_rhs != 1) {
+    msg = "components = DMK_COMPONENTS_ALL (the DMK far field) takes one force column";
     return DMK_ERR_UNSUPPORTED;
   }
   if (o->n_rhs != 1 && (o->kernels & DMK_KERNEL_STRESSLET)) {

@@ -230,13 +230,14 @@ void pinned_release(int32_t* slot);
 
 struct EwaldState;
 struct FarState;
+struct Far2State;
 
 struct Plan {
   dmk_stokes_opts_t opts{};
   int leaf_capacity = 0;
   int uniform_level = 0;       // > 0: every leaf at this level (single-level Ewald split)
   EwaldState* ewald = nullptr; // far field of components = EWALD (periodic 3D Stokeslet)
-  FarState* far = nullptr;     // DMK far field of components = ALL (3D)
+  FarState* far = nullptr;     // DMK far field of components = ALL (2D and 3D)
   cudaStream_t stream = nullptr;
   int device = 0;
   KernelTables tables;
@@ -281,12 +282,20 @@ size_t aux_bytes_grad(const dmk_stokes_opts_t& o, int64_t N);
 size_t aux_bytes_adjoint(const dmk_stokes_opts_t& o, int64_t N);
 // Gauss-Legendre nodes and weights on [-1, 1]
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
-// far.cu: the DMK far field (components = ALL, 3D): proxy charges, plane waves, root, interpolation
+// far.cu: the DMK far field (components = ALL): proxy charges, plane waves, root, interpolation
+// (3D there; the 2D plans are handed to far2d.cu)
 void far_setup(Plan& p);
 void far_free(Plan& p);
 void far_run(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u, cudaStream_t s);
 void far_info(const Plan& p, int32_t info[8]);
 size_t far_bytes(const Plan& p);
+// far2d.cu: the same in 2D
+Far2State* far2d_setup(Plan& p);
+void far2d_free(Plan& p, Far2State* F);
+void far2d_run(const Plan& p, const Far2State& F, const double* d_f, const double* d_g, const double* d_n, double* d_u,
+               cudaStream_t s);
+void far2d_info(const Far2State& F, int32_t info[8]);
+size_t far2d_bytes(const Far2State& F);
 // ewald.cu: the single-level PSWF Ewald far field (components = EWALD, periodic 3D Stokeslet)
 int ewald_level(int64_t N, int ns);
 void ewald_setup(Plan& p, int L);

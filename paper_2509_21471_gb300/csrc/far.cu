@@ -31,8 +31,7 @@
 // m_0 >= 0 only (the potential is real).  Arithmetic is FP32 when the plan's
 // pair terms are FP32 (MIXED at eps >= 2e-7), FP64 otherwise; the target
 // velocities are accumulated in FP64.
-#include "common.cuh"
-#include "tables.h"
+#include "far_common.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -44,20 +43,13 @@
 
 namespace dmk {
 
+using namespace farc;
+
 namespace {
 
-constexpr int kMaxP = 64;          // proxy order and mode counts a side (Table 2 needs <= 63)
 constexpr int kRotTile = 64;       // rest columns per k_rot block
 constexpr int kRotThreads = 256;
 constexpr double kRTrunc = 2.7320508075688772;   // R = 1 + sqrt(3), Eq. (Btrunc_hat)
-
-struct BoxGeo {
-  double x, y, z, w;   // centre and half side, in-cell coordinates
-};
-
-template <typename R> struct Cplx;
-template <> struct Cplx<float> { using T = float2; };
-template <> struct Cplx<double> { using T = double2; };
 
 // one stage of a separable transform: Y[r][m] (=, +=) sum_j A[m][j] X[j][r] over the
 // job's one or two inputs (the second with the second matrix), r < rest; complex
@@ -70,31 +62,11 @@ struct RotJob {
 
 // shared memory of k_rot: A transposed [nmat][n_in][n4] (n4 = n_out rounded up to 4,
 // zero padded), X [nmat][n_in][kRotTile], Y [kRotTile][n_out]; each part 16-byte aligned
-__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 __host__ __device__ inline void rot_smem_layout(size_t bytesA, size_t bytesX, size_t* offX, size_t* offY) {
   *offX = align16(bytesA);
   *offY = *offX + align16(bytesX);
 }
 
-// four consecutive entries from 16-byte aligned shared memory
-__device__ __forceinline__ void ld4(const float* p, float* v) {
-  const float4 a = *reinterpret_cast<const float4*>(p);
-  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double* v) {
-  const double2 a = *reinterpret_cast<const double2*>(p);
-  const double2 b = *reinterpret_cast<const double2*>(p + 2);
-  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-}
-__device__ __forceinline__ void ld4(const float2* p, float2* v) {
-  const float4 a = *reinterpret_cast<const float4*>(p);
-  const float4 b = *reinterpret_cast<const float4*>(p + 2);
-  v[0] = make_float2(a.x, a.y); v[1] = make_float2(a.z, a.w);
-  v[2] = make_float2(b.x, b.y); v[3] = make_float2(b.z, b.w);
-}
-__device__ __forceinline__ void ld4(const double2* p, double2* v) {
-  v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
-}
 
 // MODE 0: write, 1: accumulate.  Each thread owns a 4 x 4 register tile: four
 // consecutive columns r and four consecutive rows m; blockDim = 16 * (n4 / 4)
@@ -211,25 +183,6 @@ __global__ void __launch_bounds__(kRotThreads) k_rot(const RotJob* __restrict__ 
   }
 }
 
-// Lagrange basis at the Chebyshev points of the first kind in barycentric form
-// (weights (-1)^j sin((2j+1) pi / 2p)), in the far field's precision; exact at a
-// node; out[j * stride] for j < pad (zero past p)
-template <typename R>
-__device__ inline void lagrange_row(R t, int p, const R* nodes, const R* bw, R* out, int stride, int pad) {
-  R s = R(0);
-  int hit = -1;
-  for (int j = 0; j < p; ++j) {
-    const R d = t - nodes[j];
-    if (d == R(0)) hit = j;
-    else s += bw[j] / d;
-  }
-  const R inv = hit >= 0 ? R(0) : R(1) / s;
-  for (int j = 0; j < pad; ++j) {
-    R v = R(0);
-    if (j < p) v = hit >= 0 ? (j == hit ? R(1) : R(0)) : (bw[j] / (t - nodes[j])) * inv;
-    out[j * stride] = v;
-  }
-}
 
 // padded proxy order: the Lagrange rows and grid rows of the leaf kernels are PB
 // long (zeros past p), PB a multiple of the c-chunk of the anterpolation (24 in
@@ -429,21 +382,6 @@ __global__ void k_far_contract(int njob, const int32_t* __restrict__ job_box, co
   }
 }
 
-// incoming expansions, phase e^{-2 pi i m.delta / 3} for a colleague at offset delta
-// (e = m.delta mod 3: 1, e^{-2 pi i/3}, e^{-4 pi i/3})
-template <typename R>
-__device__ __forceinline__ void add_phased(int e, R ox, R oy, R& sr, R& si) {
-  const R c120 = R(-0.5), s120 = R(0.86602540378443864676);
-  if (e == 0) {
-    sr += ox;
-    si += oy;
-  } else {
-    const R sn = e == 1 ? -s120 : s120;
-    sr += c120 * ox - sn * oy;
-    si += c120 * oy + sn * ox;
-  }
-}
-
 // listed target boxes from their 27 colleague slots (slot s: delta_a = ((s / 3^a) % 3) - 1):
 // I[tlist[i]][k][m] = sum_slots phase O[colleague][k][m]   (used for the root)
 template <typename R>
@@ -486,19 +424,6 @@ __global__ void k_far_colleague(int nlist, const int32_t* __restrict__ tlist, co
 // children are three passes of 3-term sums (axis 0, then 1, then 2).
 // win[g][64]: box id or -1; chl[g][8]: target index of child o (o_a = bit a) or -1.
 constexpr int kGrpThreads = 128;
-template <typename R>
-__device__ __forceinline__ void axis_phase(int m, R& c, R& s) {     // f(+1) = e^{-2 pi i m / 3}; f(-1) = conj
-  int e = m % 3;
-  if (e < 0) e += 3;
-  c = e == 0 ? R(1) : R(-0.5);
-  s = e == 0 ? R(0) : (e == 1 ? R(-0.86602540378443864676) : R(0.86602540378443864676));
-}
-template <typename R>
-__device__ __forceinline__ void sum3(R c, R s, R xr_m, R xi_m, R xr_0, R xi_0, R xr_p, R xi_p, R& yr, R& yi) {
-  // y = f(-1) x_{-1} + x_0 + f(+1) x_{+1},  f(+1) = c + i s, f(-1) = c - i s
-  yr = xr_0 + c * (xr_m + xr_p) + s * (xi_m - xi_p);
-  yi = xi_0 + c * (xi_m + xi_p) + s * (xr_p - xr_m);
-}
 template <typename R>
 __global__ void __launch_bounds__(kGrpThreads) k_far_colleague_grp(const int32_t* __restrict__ win, const int32_t* __restrict__ chl,
                                                                    const typename Cplx<R>::T* __restrict__ O,
@@ -1096,28 +1021,6 @@ __global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restri
 }
 
 // ------------------------------------------------------------------ host side
-// gamma-hat(kappa) = 2 int_0^1 phi(t) (cos(kappa t) + kappa t sin(kappa t) / 2) dt
-// (Eq. (gammaB_in_phi)), Gauss-Legendre on [0, 1]
-struct GammaHat {
-  std::vector<double> t, wphi;
-  explicit GammaHat(double c) {
-    ProlateSeries ser;
-    if (prolate_series(c, &ser) != 0) throw Error{DMK_ERR_CUDA, "prolate series failed"};
-    std::vector<double> x, w;
-    gauss_legendre(256, x, w);
-    t.resize(x.size());
-    wphi.resize(x.size());
-    for (size_t i = 0; i < x.size(); ++i) {
-      t[i] = 0.5 * (x[i] + 1.0);
-      wphi[i] = w[i] * series_phi(ser, t[i]);       // 2 * (1/2) w_i phi(t_i)
-    }
-  }
-  double operator()(double kap) const {
-    double s = 0.0;
-    for (size_t i = 0; i < t.size(); ++i) s += wphi[i] * (std::cos(kap * t[i]) + 0.5 * kap * t[i] * std::sin(kap * t[i]));
-    return s;
-  }
-};
 
 // B-hat^R(k) in 3D, Eq. (Btrunc_hat); Taylor series of the bracket near k = 0
 double b_trunc_hat(double k) {
@@ -1127,25 +1030,6 @@ double b_trunc_hat(double k) {
   return R4 * (1.0 / 120.0 - x * x / 2520.0 + x * x * x * x / 120960.0);
 }
 
-// Table 2 columns and the rules that reproduce them: N1 = 2 (3c/pi) - 1, N_per = 2 floor(c / 2pi) + 1;
-// p interpolated linearly in log10 eps between the rows and rounded up
-int table2_p(double eps, int kernels) {
-  static const double e_rows[4] = {-12, -9, -6, -3};
-  static const double p_s[4] = {44, 33, 23, 12}, p_t[4] = {44, 33, 22, 11};
-  const double e = std::log10(eps);
-  auto interp = [&](const double* v) {
-    for (int i = 0; i < 3; ++i)
-      if (e >= e_rows[i] - 1e-9 && e <= e_rows[i + 1] + 1e-9) {
-        const double tt = (e - e_rows[i]) / (e_rows[i + 1] - e_rows[i]);
-        return static_cast<int>(std::ceil(v[i] + tt * (v[i + 1] - v[i]) - 1e-9));
-      }
-    return static_cast<int>(v[0]);
-  };
-  int p = 0;
-  if (kernels & DMK_KERNEL_STOKESLET) p = std::max(p, interp(p_s));
-  if (kernels & DMK_KERNEL_STRESSLET) p = std::max(p, interp(p_t));
-  return p;
-}
 
 // matrix bank of a parameter set (Chebyshev points, child matrices, plane-wave
 // matrices, kernel tables): built once per process for each set
@@ -1179,12 +1063,6 @@ struct RotLaunch {
   int n = 0;
 };
 
-template <typename T>
-T* upload(Plan& p, const std::vector<T>& v) {
-  T* d = p.arena.alloc<T>(std::max<size_t>(v.size(), 1));
-  if (!v.empty()) DMK_CUDA_TRY(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, p.stream));
-  return d;
-}
 
 }  // namespace
 
@@ -1241,6 +1119,7 @@ struct FarState {
   std::vector<int> mf_n, if_n;
   RotLaunch out1, out2, out3, ev1, ev2, ev3, r1, r2, r3, rv1, rv2, rv3;
   size_t bytes = 0;
+  Far2State* d2 = nullptr;           // the 2D far field (far2d.cu) in place of all of the above
 };
 
 namespace {
@@ -1300,6 +1179,12 @@ RotLaunch make_launch(Plan& p, const std::vector<RotJob>& jobs) {
 }  // namespace
 
 void far_setup(Plan& p) {
+  if (p.opts.dim == 2) {
+    auto Fp = std::make_unique<FarState>();
+    Fp->d2 = far2d_setup(p);
+    p.far = Fp.release();
+    return;
+  }
   const DeviceTree& T = p.tree;
   const dmk_stokes_opts_t& o = p.opts;
   cudaStream_t s = p.stream;
@@ -1870,13 +1755,14 @@ void far_setup(Plan& p) {
 void far_free(Plan& p) {
   FarState* F = p.far;
   if (!F) return;
+  if (F->d2) far2d_free(p, F->d2);
   for (void** b : {&F->q, &F->pot, &F->O, &F->I, &F->s1, &F->s2, &F->rO, &F->W})
     if (*b) cudaFreeAsync(*b, p.stream);
   delete F;                                   // small arrays live in the plan's arena
   p.far = nullptr;
 }
 
-size_t far_bytes(const Plan& p) { return p.far ? p.far->bytes : 0; }
+size_t far_bytes(const Plan& p) { return p.far ? (p.far->d2 ? far2d_bytes(*p.far->d2) : p.far->bytes) : 0; }
 
 namespace {
 
@@ -2090,7 +1976,8 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
 
 void far_run(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u, cudaStream_t s) {
   if (!p.far || !d_u || p.tree.N == 0) return;
-  if (p.far->fp32) far_run_t<float>(p, d_f, d_g, d_n, d_u, s);
+  if (p.far->d2) far2d_run(p, *p.far->d2, d_f, d_g, d_n, d_u, s);
+  else if (p.far->fp32) far_run_t<float>(p, d_f, d_g, d_n, d_u, s);
   else far_run_t<double>(p, d_f, d_g, d_n, d_u, s);
 }
 
@@ -2098,6 +1985,10 @@ void far_info(const Plan& p, int32_t info[8]) {
   for (int i = 0; i < 8; ++i) info[i] = 0;
   const FarState* F = p.far;
   if (!F) return;
+  if (F->d2) {
+    far2d_info(*F->d2, info);
+    return;
+  }
   info[0] = F->p;
   info[1] = 2 * F->M + 1;
   info[2] = F->rnm;

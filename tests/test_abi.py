@@ -38,9 +38,10 @@ def test_invalid_arguments_rejected_without_gpu(dmk_lib):
     assert b"dim" in lib.dmk_stokes_last_error(None)
     o = dmk_lib.make_opts(eps=1e-14)
     assert lib.dmk_stokes_plan(ctypes.byref(o), 0, None, 0, None, None, ctypes.byref(h)) == 1
-    # the Ewald split is periodic-3D-Stokeslet only; the DMK far field is 3D with one column
+    # the Ewald split is periodic-3D-Stokeslet only; the DMK far field takes one column
     for kw in (dict(components=dmk_lib.EWALD), dict(components=dmk_lib.EWALD, periodic=True, kernels=3),
-               dict(components=dmk_lib.ALL, dim=2), dict(components=dmk_lib.ALL, n_rhs=4)):
+               dict(components=dmk_lib.EWALD, periodic=True, dim=2), dict(components=dmk_lib.ALL, n_rhs=4),
+               dict(components=dmk_lib.ALL, dim=2, n_rhs=2)):
         o = dmk_lib.make_opts(**kw)
         assert lib.dmk_stokes_plan(ctypes.byref(o), 0, None, 0, None, None, ctypes.byref(h)) == 3, kw
     o = dmk_lib.make_opts(components=3)
