@@ -358,6 +358,14 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
     r.update(workload="2d-periodic-stokeslet+stresslet-uniform", n_points=len(x), eps=1e-8,
              mixed_pair_arith="float-float (eps < 2e-7)")
     res["periodic_2d_eps1e-8"] = r
+    # the same workload as the whole DMK sum (near + the 2D far field; far field in
+    # float64 at eps 1e-8 in both precisions)
+    r = measure(lambda prec: dmk.Plan(xd, eps=1e-8, periodic=True, kernels=dmk.STOKESLET | dmk.STRESSLET,
+                                      precision=prec, components=dmk.ALL),
+                lambda p: p.eval(fd, gd, nd, out=ud), len(x), 2)
+    r.update(workload="2d-periodic-stokeslet+stresslet-uniform, whole DMK sum", n_points=len(x), eps=1e-8,
+             note="near_ms here is the whole evaluation (near + far) with the plan reused")
+    res["dmk_full_sum_periodic_2d_eps1e-8"] = r
     del xd, fd, gd, nd, ud
 
     # 256 independent 3D systems, 16 force columns, one plan and one launch

@@ -451,6 +451,7 @@ dmk_status_t dmk_stokes_sync_status(dmk_stokes_plan_t plan) {
   if (st & dmk::ST_OUT_OF_RANGE) return set_err(plan, DMK_ERR_OUT_OF_RANGE, "point outside the unit box");
   if (st & (dmk::ST_NEAR_OVERFLOW | dmk::ST_TREE_INCONSISTENT))
     return set_err(plan, DMK_ERR_CUDA, "internal tree inconsistency");
+  if (st & dmk::ST_TC_TIMEOUT) return set_err(plan, DMK_ERR_CUDA, "tensor-core wait timed out in the far field");
   return DMK_OK;
 }
 

@@ -34,7 +34,8 @@ enum : int {
   ST_OUT_OF_RANGE = 1,      // free-space point outside the unit box
   ST_NONFINITE = 2,         // NaN / Inf coordinate
   ST_NEAR_OVERFLOW = 4,     // near list longer than kMaxNear (tree not level-restricted)
-  ST_TREE_INCONSISTENT = 8  // a fine neighbour expected to be a leaf was not
+  ST_TREE_INCONSISTENT = 8, // a fine neighbour expected to be a leaf was not
+  ST_TC_TIMEOUT = 16        // a wait for tensor-core MMAs ran out (results of that evaluation invalid)
 };
 
 // ------------------------------------------------------------ Morton keys

@@ -32,9 +32,11 @@
 // pair terms are FP32 (MIXED at eps >= 2e-7), FP64 otherwise; the target
 // velocities are accumulated in FP64.
 #include "far_common.cuh"
+#include "tc.cuh"
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <type_traits>
 #include <memory>
 #include <mutex>
@@ -1020,6 +1022,426 @@ __global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restri
     }
 }
 
+// ------------------------------------------------------------------ tensor-core leaf kernels
+// The float32 far field's two per-point contractions on tcgen05 (kind::tf32, split
+// TF32 products, D in tensor memory; tc.cuh).  Several blocks share an SM (their MMAs
+// and their operand forming interleave); within a block the next stage's inputs
+// arrive by cp.async while the current one is formed and multiplied.  Warp 0 waits on
+// the MMAs' mbarrier while the other warps wait at the block barrier.  A wait that runs
+// out sets ST_TC_TIMEOUT in the plan's status word, ends the block's work, waits once
+// more for the MMAs in flight and frees the tensor memory.
+constexpr int kTcThreads = 256;
+constexpr int kTcK = 32;                            // sources per operand stage (four K = 8 steps)
+constexpr int kTcSbo = (kTcK / 4) * 128;            // 8-row group stride of those operands (bytes)
+constexpr long long kTcWaitCycles = 4000000000LL;   // about 2 s of SM clock
+constexpr size_t kSmemPerSM = 228 * 1024;
+
+// densities of the component groups per source in sorted point order, float32:
+// Vs[gi][s] = (v0, v1, v2, 0) for the gi-th present group (0: f; 1: rho_00, rho_11,
+// rho_22; 2: rho_01, rho_02, rho_12 of the symmetric part of g (x) n)
+__global__ void k_far_values(const int32_t* __restrict__ perm, const double* __restrict__ f, const double* __restrict__ g,
+                             const double* __restrict__ nrm, int64_t N, int grp0, int ng, float4* __restrict__ Vs) {
+  const int64_t s = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (s >= N) return;
+  const int64_t o = perm[s];
+  for (int gi = 0; gi < ng; ++gi) {
+    const int grp = grp0 + gi;
+    double v0, v1, v2;
+    if (grp == 0) {
+      v0 = f[o * 3];
+      v1 = f[o * 3 + 1];
+      v2 = f[o * 3 + 2];
+    } else {
+      const double g0 = g[o * 3], g1 = g[o * 3 + 1], g2 = g[o * 3 + 2];
+      const double n0 = nrm[o * 3], n1 = nrm[o * 3 + 1], n2 = nrm[o * 3 + 2];
+      if (grp == 1) {
+        v0 = g0 * n0;
+        v1 = g1 * n1;
+        v2 = g2 * n2;
+      } else {
+        v0 = 0.5 * (g0 * n1 + g1 * n0);
+        v1 = 0.5 * (g0 * n2 + g2 * n0);
+        v2 = 0.5 * (g1 * n2 + g2 * n1);
+      }
+    }
+    Vs[gi * N + s] = make_float4(static_cast<float>(v0), static_cast<float>(v1), static_cast<float>(v2), 0.f);
+  }
+}
+
+// shared memory of the leaf-charge kernel: one operand buffer (A hi/lo [128][kTcK],
+// B hi/lo [NP][kTcK]) and two source stages (weights [kTcK][3][PB], densities
+// [kTcK][4]); at least a quarter of the SM so that at most three blocks (384 TMEM
+// columns) share one
+inline size_t anterp_tc_op_bytes(int NP) { return 2 * 128 * kTcK * 4 + 2 * static_cast<size_t>(NP) * kTcK * 4; }
+inline size_t anterp_tc_stage_floats(int PB) { return static_cast<size_t>(kTcK) * 3 * PB + kTcK * 4; }
+inline size_t anterp_tc_smem(int NP, int PB) {
+  const size_t need = anterp_tc_op_bytes(NP) + 2 * anterp_tc_stage_floats(PB) * 4;
+  return std::max({need, kSmemPerSM / 4 + 1024, 128 * static_cast<size_t>(NP + 1) * 4});
+}
+
+// leaf proxy charges: per leaf and component group, Q[(a,b)][(k,c)] = sum_s A[(a,b)][s] B[(k,c)][s]
+// with A = L_a(x_s) L_b(y_s) and B = L_c(z_s) v_s,k.  A block owns 128 rows (a, b)
+// (blockIdx.z) and all 3p columns (padded to NP, a multiple of 16, <= 128) in tensor
+// memory.  Per stage of kTcK sources, warps 0-3 form row tid of A and warps 4-7 row
+// tid - 128 of B from the stage's weights and densities (which arrive by cp.async one
+// stage ahead).  The result leaves through shared memory in the layout
+// q[box][slot + k][a][b][c].
+__global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
+                                                              const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ leaf_count,
+                                                              const float* __restrict__ W, const float4* __restrict__ Vs, int64_t N,
+                                                              int slot_f, int slot_t, int ncomp, float* __restrict__ q, int p,
+                                                              int PB, int NP, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t opA = 128 * kTcK * 4, opB = static_cast<size_t>(NP) * kTcK * 4;
+  const int stW = kTcK * 3 * PB;                                       // weight floats of one stage
+  const int stF = stW + kTcK * 4;                                      // floats of one stage
+  unsigned char* sAh = smem;
+  unsigned char* sAl = sAh + opA;
+  unsigned char* sBh = sAl + opA;
+  unsigned char* sBl = sBh + opB;
+  float* stage0 = reinterpret_cast<float*>(sBl + opB);
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  __shared__ int fail;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int li = leaf_list[blockIdx.x], box = leaf_box[blockIdx.x];
+  const int gi = blockIdx.y;
+  const int grp = (slot_f >= 0 ? 0 : 1) + gi;
+  const int slot = grp == 0 ? slot_f : slot_t + 3 * (grp - 1);
+  const int s0 = leaf_start[li], ns = leaf_count[li];
+  const int p2 = p * p;
+  const int64_t p3 = static_cast<int64_t>(p2) * p;
+  const bool arole = tid < 128;
+  const int rr = arole ? tid : tid - 128;
+  const int R = blockIdx.z * 128 + rr;
+  // weight offsets of this thread's row within a source's [3][PB] block (zero row: none)
+  int w0 = -1, w1 = -1;
+  if (arole && R < p2) {                                               // row (a, b) of A: L_a(x) L_b(y)
+    w0 = R / p;
+    w1 = PB + (R - w0 * p);
+  } else if (!arole && rr < 3 * p) {                                   // row (k, c) of B: L_c(z) v_k
+    w0 = 2 * PB + rr % p;
+    w1 = rr / p;
+  }
+  const bool forms = arole || rr < NP;
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    fail = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase, 128);
+  const int nchunk = (ns + kTcK - 1) / kTcK;
+  const float* Vg = reinterpret_cast<const float*>(Vs + gi * N);
+  auto stage_in = [&](int ch) {                                        // weights and densities of stage ch
+    const int sc = ch * kTcK, ncnt = min(kTcK, ns - sc);
+    float* sw = stage0 + (ch & 1) * stF;
+    const float* srcw = W + (static_cast<int64_t>(s0) + sc) * 3 * PB;
+    for (int i = tid; i < ncnt * 3 * PB / 4; i += kTcThreads) tc::cp_async16(sw + 4 * i, srcw + 4 * i);
+    const float* srcv = Vg + (static_cast<int64_t>(s0) + sc) * 4;
+    for (int i = tid; i < ncnt; i += kTcThreads) tc::cp_async16(sw + stW + 4 * i, srcv + 4 * i);
+    for (int i = ncnt * 3 * PB + tid; i < stW; i += kTcThreads) sw[i] = 0.f;       // tail sources: zero
+    for (int i = ncnt * 4 + tid; i < kTcK * 4; i += kTcThreads) sw[stW + i] = 0.f;
+    tc::cp_async_commit();
+  };
+  if (nchunk > 0) stage_in(0);
+  tc::sync_tc();
+  const uint32_t tmem = tbase;
+  const uint32_t idesc = tc::idesc_tf32(128, NP);
+  unsigned char* dh = arole ? sAh : sBh;
+  unsigned char* dl = arole ? sAl : sBl;
+  int issued = 0;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    if (ch + 1 < nchunk) {
+      stage_in(ch + 1);                                                // its stage was last read while forming ch - 1
+      tc::cp_async_wait<1>();
+    } else {
+      tc::cp_async_wait<0>();
+    }
+    if (ch >= 1 && warp == 0)                                          // the operands were read by the MMAs of ch - 1
+      if (!tc::mbar_wait(&mbar, (ch - 1) & 1, kTcWaitCycles)) fail = 1;
+    __syncthreads();
+    if (fail) break;
+    const float* sw = stage0 + (ch & 1) * stF;
+    if (forms) {
+#pragma unroll 4
+      for (int s4 = 0; s4 < kTcK / 4; ++s4) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int sl = 4 * s4 + j;
+          const float* ws = sw + sl * 3 * PB;
+          const float v = w0 < 0 ? 0.f : ws[w0] * (arole ? ws[w1] : sw[stW + sl * 4 + w1]);
+          tc::split_tf32_fast(v, h[j], l[j]);
+        }
+        const int o = tc::kmajor_off(rr, 4 * s4, kTcSbo);
+        *reinterpret_cast<uint4*>(dh + o) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(dl + o) = make_uint4(l[0], l[1], l[2], l[3]);
+      }
+    }
+    tc::fence_async_smem();
+    tc::sync_tc();
+    if (tid == 0) {
+      const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+#pragma unroll
+      for (int kk = 0; kk < kTcK / 8; ++kk) {
+        const uint32_t ko = kk * 256;                                  // two core matrices along K per step
+        tc::mma_tf32x3(tmem, tc::smem_desc(ah + ko, kTcSbo), tc::smem_desc(al + ko, kTcSbo),
+                       tc::smem_desc(bh + ko, kTcSbo), tc::smem_desc(bl + ko, kTcSbo), idesc,
+                       (ch > 0 || kk > 0) ? 1u : 0u);
+      }
+      tc::commit(&mbar);
+    }
+    ++issued;
+  }
+  if (issued > 0 && !fail && warp == 0)
+    if (!tc::mbar_wait(&mbar, (issued - 1) & 1, kTcWaitCycles)) fail = 1;
+  tc::sync_tc();
+  if (!fail && issued > 0) {
+    // D rows (a, b) x columns (k, c) through shared memory (the operand buffer is free):
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 and the column blocks of parity w / 4
+    float* sD = reinterpret_cast<float*>(smem);                       // [128][NP + 1]
+    const int lanew = warp & 3, half = warp >> 2, row = 32 * lanew + (tid & 31);
+    for (int cb = half; cb < NP / 16; cb += 2) {
+      float v[16];
+      tc::ld16(tmem + (static_cast<uint32_t>(32 * lanew) << 16) + cb * 16, v);
+      tc::ld_wait();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) sD[row * (NP + 1) + cb * 16 + j] = v[j];
+    }
+    __syncthreads();
+    const int R0 = blockIdx.z * 128, nrow = min(128, p2 - R0);
+    float* qb = q + (static_cast<int64_t>(box) * ncomp + slot) * p3 + static_cast<int64_t>(R0) * p;
+    for (int i = tid; i < 3 * nrow * p; i += kTcThreads) {
+      const int k = i / (nrow * p), rem = i - k * nrow * p;
+      const int r = rem / p, c = rem - r * p;
+      qb[k * p3 + rem] = sD[r * (NP + 1) + k * p + c];
+    }
+  } else if (fail) {
+    if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+    if (issued > 0 && warp == 0) tc::mbar_wait(&mbar, (issued - 1) & 1, kTcWaitCycles);
+  }
+  tc::cp_async_wait<0>();
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// grid rows (k, a) of one MMA block of the leaf evaluation: RB rows of RW columns b,
+// N = RB RW <= 256 and a multiple of 16
+constexpr int eval_tc_rows(int rw) {
+  int rb = 256 / rw;
+  while ((rb * rw) % 16) --rb;
+  return rb;
+}
+// shared memory of the leaf evaluation: A hi/lo [128][RW], B hi/lo [NB][RW], the staged
+// grid rows [RB][p^2], the a-weights [p][128] and the partial sums [128][3]; at least a
+// third of the SM, so that at most two blocks (512 TMEM columns) share one
+template <int RW>
+size_t eval_tc_smem_t(int p) {
+  const size_t nb = static_cast<size_t>(eval_tc_rows(RW)) * RW;
+  const size_t need = 2 * 128 * RW * 4 + 2 * nb * RW * 4 + static_cast<size_t>(eval_tc_rows(RW)) * p * p * 4 +
+                      static_cast<size_t>(p) * 128 * 4 + 128 * 3 * 4;
+  return std::max(need, kSmemPerSM / 3 + 1024);
+}
+
+// leaf evaluation: a block takes one chunk of at most 128 targets of one leaf (item
+// it_leaf / it_off, target t in TMEM lane t).  For each block j of RB grid rows (k, a)
+// the MMA forms V[t][(k,a,b)] = sum_c L_c(z_t) P[k][a][b][c] (K = c and the b of each
+// row padded to RW), and the threads reduce u_k(t) += L_a(x_t) sum_b L_b(y_t) V[t][(k,a,b)]
+// (threads t and t + 128 split the block's rows); block j + 1's grid rows arrive by
+// cp.async during the MMAs of block j.
+template <int RW>
+__global__ void __launch_bounds__(kTcThreads) k_far_eval_tc(const int32_t* __restrict__ it_leaf, const int32_t* __restrict__ it_off,
+                                                            const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
+                                                            const int32_t* __restrict__ t_start, const int32_t* __restrict__ t_count,
+                                                            const double* __restrict__ tw, int64_t NT, const int32_t* __restrict__ tperm,
+                                                            const BoxGeo* __restrict__ box_geo, const float* __restrict__ pot, int p,
+                                                            const float* __restrict__ nodes, const float* __restrict__ bw,
+                                                            double* __restrict__ u, int* __restrict__ status) {
+  constexpr int KP = RW;                         // K = c padded like the rows
+  constexpr int SBO = (KP / 4) * 128;
+  constexpr int RB = eval_tc_rows(RW);
+  constexpr int NB = RB * RW;
+  constexpr int RH = (RB + 1) / 2;               // rows of a block reduced by threads 0..127
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr size_t opA = 128 * KP * 4, opB = static_cast<size_t>(NB) * KP * 4;
+  unsigned char* sAh = smem;                                  // [128][KP]: L_c(z_t)
+  unsigned char* sAl = sAh + opA;
+  unsigned char* sBh = sAl + opA;                             // [NB][KP]: grid rows
+  unsigned char* sBl = sBh + opB;
+  float* sP = reinterpret_cast<float*>(sBl + opB);            // [RB][p^2]: staged grid rows
+  const int p2 = p * p;
+  float* sLa = sP + RB * p2;                                  // [p][128]: L_a(x_t)
+  float* sRed = sLa + p * 128;                                // [128][3]
+  __shared__ float s_nodes[kMaxP], s_bw[kMaxP];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  __shared__ int fail;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int t = tid & 127, half = tid >> 7;
+  const int e = it_leaf[blockIdx.x];
+  const int li = leaf_list[e];
+  const int box = leaf_box[e];
+  const float* P = pot + static_cast<int64_t>(box) * 3 * p2 * p;
+  const int nrows = 3 * p;
+  const int nblk = (nrows + RB - 1) / RB;
+  auto stage_in = [&](int j) {                   // grid rows j RB .. of the leaf into sP
+    const int r0 = j * RB, nr = min(RB, nrows - r0);
+    const float* src = P + static_cast<int64_t>(r0) * p2;
+    for (int i = tid; i < nr * p2; i += kTcThreads) tc::cp_async4(sP + i, src + i);
+    tc::cp_async_commit();
+  };
+  stage_in(0);
+  for (int j = tid; j < p; j += kTcThreads) {
+    s_nodes[j] = nodes[j];
+    s_bw[j] = bw[j];
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    fail = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(&tbase, 256);
+  tc::sync_tc();
+  const BoxGeo geo = box_geo[box];
+  const double inv_half = 1.0 / geo.w;
+  const int lt0 = t_start[li], lnt = t_count ? t_count[li] : t_start[li + 1] - lt0;
+  const int t0 = lt0 + it_off[blockIdx.x];
+  const int nt = min(128, lnt - it_off[blockIdx.x]);
+  const bool on = t < nt;
+  // b-weights in registers (both halves); a-weights and the c-row of A from half 0
+  float lb[RW];
+#pragma unroll
+  for (int j = 0; j < RW; ++j) lb[j] = 0.f;
+  if (on) {
+    const float y = static_cast<float>((tw[NT + t0 + t] - geo.y) * inv_half);
+    float sy = 0.f;
+    int hy = -1;
+    for (int j = 0; j < p; ++j) {
+      const float dy = y - s_nodes[j];
+      if (dy == 0.f) hy = j;
+      else sy += s_bw[j] / dy;
+    }
+    const float iy = hy >= 0 ? 0.f : 1.f / sy;
+#pragma unroll
+    for (int j = 0; j < RW; ++j)
+      if (j < p) lb[j] = hy >= 0 ? (j == hy ? 1.f : 0.f) : (s_bw[j] / (y - s_nodes[j])) * iy;
+  }
+  if (half == 0) {
+    float lc[RW];
+#pragma unroll
+    for (int j = 0; j < RW; ++j) lc[j] = 0.f;
+    if (on) {
+      const float x = static_cast<float>((tw[t0 + t] - geo.x) * inv_half);
+      lagrange_row<float>(x, p, s_nodes, s_bw, sLa + t, 128, p);
+      const float z = static_cast<float>((tw[2 * NT + t0 + t] - geo.z) * inv_half);
+      float sz = 0.f;
+      int hz = -1;
+      for (int j = 0; j < p; ++j) {
+        const float dz = z - s_nodes[j];
+        if (dz == 0.f) hz = j;
+        else sz += s_bw[j] / dz;
+      }
+      const float iz = hz >= 0 ? 0.f : 1.f / sz;
+#pragma unroll
+      for (int j = 0; j < RW; ++j)
+        if (j < p) lc[j] = hz >= 0 ? (j == hz ? 1.f : 0.f) : (s_bw[j] / (z - s_nodes[j])) * iz;
+    } else {
+      for (int j = 0; j < p; ++j) sLa[j * 128 + t] = 0.f;
+    }
+#pragma unroll
+    for (int c4 = 0; c4 < KP / 4; ++c4) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) tc::split_tf32_fast(lc[4 * c4 + j], h[j], l[j]);
+      const int o = tc::kmajor_off(t, 4 * c4, SBO);
+      *reinterpret_cast<uint4*>(sAh + o) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(sAl + o) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  }
+  const uint32_t tmem = tbase;
+  const uint32_t idesc = tc::idesc_tf32(128, NB);
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+  float acc[3] = {0.f, 0.f, 0.f};
+  tc::cp_async_wait<0>();
+  __syncthreads();
+  int issued = 0;
+  for (int j = 0; j < nblk; ++j) {
+    const int r0 = j * RB;
+    // block j as the B operand: n = (row, b), K = c; consecutive threads take consecutive n
+    for (int i = tid; i < NB * (KP / 4); i += kTcThreads) {
+      const int c4 = i / NB, n = i - c4 * NB;
+      const int rl = n / RW, b = n - rl * RW;
+      const bool ok = r0 + rl < nrows && b < p;
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int c = 4 * c4 + jj;
+        tc::split_tf32_fast(ok && c < p ? sP[rl * p2 + b * p + c] : 0.f, h[jj], l[jj]);
+      }
+      const int o = tc::kmajor_off(n, 4 * c4, SBO);
+      *reinterpret_cast<uint4*>(sBh + o) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(sBl + o) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+    tc::fence_async_smem();
+    tc::sync_tc();                               // sP consumed, B visible, the previous D read
+    if (j + 1 < nblk) stage_in(j + 1);
+    if (tid == 0) {
+      const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+#pragma unroll
+      for (int kk = 0; kk < KP / 8; ++kk) {
+        const uint32_t ko = kk * 256;
+        tc::mma_tf32x3(tmem, tc::smem_desc(ah + ko, SBO), tc::smem_desc(al + ko, SBO), tc::smem_desc(bh + ko, SBO),
+                       tc::smem_desc(bl + ko, SBO), idesc, kk > 0 ? 1u : 0u);
+      }
+      tc::commit(&mbar);
+    }
+    ++issued;
+    if (warp == 0)
+      if (!tc::mbar_wait(&mbar, (issued - 1) & 1, kTcWaitCycles)) fail = 1;
+    tc::cp_async_wait<0>();
+    tc::sync_tc();
+    if (fail) break;
+    // reduce block j: rows [0, RH) by threads 0..127, [RH, RB) by 128..255
+    for (int rr = half * RH; rr < (half ? RB : RH); ++rr) {
+      const int r = r0 + rr;
+      if (r >= nrows) break;
+      float v[RW];
+#pragma unroll
+      for (int c = 0; c + 16 <= RW; c += 16) tc::ld16(lane_base + rr * RW + c, v + c);
+      if constexpr (RW % 16 != 0) tc::ld8(lane_base + rr * RW + (RW - 8), v + (RW - 8));
+      tc::ld_wait();
+      float s = 0.f;
+#pragma unroll
+      for (int b = 0; b < RW; ++b) s = fmaf(lb[b], v[b], s);
+      const int k = r / p, a = r - k * p;
+      const float w = sLa[a * 128 + t] * s;
+      if (k == 0) acc[0] += w;
+      else if (k == 1) acc[1] += w;
+      else acc[2] += w;
+    }
+  }
+  if (fail) {
+    if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
+    if (warp == 0 && issued > 0) tc::mbar_wait(&mbar, (issued - 1) & 1, kTcWaitCycles);
+  } else {
+    if (half == 1) {
+      sRed[t * 3] = acc[0];
+      sRed[t * 3 + 1] = acc[1];
+      sRed[t * 3 + 2] = acc[2];
+    }
+    __syncthreads();
+    if (half == 0 && on) {
+      const int64_t o = tperm[t0 + t];
+      u[o * 3] += static_cast<double>(acc[0] + sRed[t * 3]);
+      u[o * 3 + 1] += static_cast<double>(acc[1] + sRed[t * 3 + 1]);
+      u[o * 3 + 2] += static_cast<double>(acc[2] + sRed[t * 3 + 2]);
+    }
+  }
+  tc::cp_async_wait<0>();
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
 // ------------------------------------------------------------------ host side
 
 // B-hat^R(k) in 3D, Eq. (Btrunc_hat); Taylor series of the bracket near k = 0
@@ -1089,6 +1511,9 @@ struct FarState {
   int32_t* ev_item_leaf = nullptr;   // index into the target-leaf list
   int32_t* ev_item_off = nullptr;    // first target of the chunk within its leaf
   int fused = 0;                     // 1: float32 transforms of a box in one kernel (shared memory fits)
+  int tc = 0;                        // 1: float32 leaf charges and leaf evaluation on the tensor cores
+  int tc_NP = 0, tc_RW = 0;          // their padded column count (3p) and row width (p)
+  void* Vs = nullptr;                // [groups][N] float4 densities of the sources (tensor-core charges)
   size_t fused_out_bytes = 0, fused_ev_bytes = 0;
   int32_t* coll = nullptr;           // [27] colleague slots of the root
   int32_t* root_tlist = nullptr;     // {target index of the root}
@@ -1401,42 +1826,11 @@ void far_setup(Plan& p) {
     F.m_RFh = m[12]; F.m_RF = m[13]; F.m_tab = m[14]; F.m_rtab = m[15];
     F.sT_root = cached->sT_root;
   } else {
-    std::vector<double> nodes(P), bwt(P);
-    for (int j = 0; j < P; ++j) {
-      const double th = (2.0 * j + 1.0) * M_PI / (2.0 * P);
-      nodes[j] = std::cos(th);
-      bwt[j] = ((j & 1) ? -1.0 : 1.0) * std::sin(th);
-    }
-    auto lag = [&](double t, int j) {       // plain Lagrange product (host)
-      double v = 1.0;
-      for (int k = 0; k < P; ++k)
-        if (k != j) v *= (t - nodes[k]) / (nodes[j] - nodes[k]);
-      return v;
-    };
-    const bool f32 = F.fp32;
-    auto put_real = [&](const std::vector<double>& v) {
-      const size_t off = (bank.size() + 15) & ~size_t(15);
-      bank.resize(off + v.size() * (f32 ? 4 : 8));
-      for (size_t i = 0; i < v.size(); ++i) {
-        if (f32) reinterpret_cast<float*>(bank.data() + off)[i] = static_cast<float>(v[i]);
-        else reinterpret_cast<double*>(bank.data() + off)[i] = v[i];
-      }
-      return off;
-    };
-    auto put_cplx = [&](const std::vector<double>& re, const std::vector<double>& im) {
-      const size_t off = (bank.size() + 15) & ~size_t(15);
-      bank.resize(off + re.size() * (f32 ? 8 : 16));
-      for (size_t i = 0; i < re.size(); ++i) {
-        if (f32) {
-          reinterpret_cast<float*>(bank.data() + off)[2 * i] = static_cast<float>(re[i]);
-          reinterpret_cast<float*>(bank.data() + off)[2 * i + 1] = static_cast<float>(im[i]);
-        } else {
-          reinterpret_cast<double*>(bank.data() + off)[2 * i] = re[i];
-          reinterpret_cast<double*>(bank.data() + off)[2 * i + 1] = im[i];
-        }
-      }
-      return off;
-    };
+    MatBank mb;
+    mb.f32 = F.fp32;
+    std::vector<double> nodes, bwt;
+    cheb_nodes_bw(P, nodes, bwt);
+    auto put_real = [&](const std::vector<double>& v) { return mb.put_real(v); };
     F.m_nodes = put_real(nodes);
     F.m_bw = put_real(bwt);
     // child -> parent anterpolation T_o[a][i] = L_a(((2o - 1) + xi_i) / 2), and the transposes
@@ -1444,7 +1838,7 @@ void far_setup(Plan& p) {
       std::vector<double> Tm(P * P), Tt(P * P);
       for (int a = 0; a < P; ++a)
         for (int i = 0; i < P; ++i) {
-          const double v = lag(((2 * oo - 1) + nodes[i]) / 2.0, a);
+          const double v = lagrange_host(nodes, ((2 * oo - 1) + nodes[i]) / 2.0, a);
           Tm[a * P + i] = v;
           Tt[i * P + a] = v;
         }
@@ -1452,29 +1846,16 @@ void far_setup(Plan& p) {
       (oo == 0 ? F.m_T0t : F.m_T1t) = put_real(Tt);
     }
     // plane-wave matrices: E[m][j] = e^{-i theta m xi_j}; F[a][m] = w_m e^{+i theta m xi_a}
-    auto pw = [&](int lo, int n, double theta, bool eval, bool half, size_t* outm) {
-      std::vector<double> re(static_cast<size_t>(n) * P), im(re.size());
-      for (int mi = 0; mi < n; ++mi)
-        for (int j = 0; j < P; ++j) {
-          const int m = lo + mi;
-          const double ph = theta * m * nodes[j];
-          const double wgt = (eval && half && m > 0) ? 2.0 : 1.0;
-          const size_t e = eval ? static_cast<size_t>(j) * n + mi : static_cast<size_t>(mi) * P + j;
-          re[e] = wgt * std::cos(ph);
-          im[e] = (eval ? 1.0 : -1.0) * wgt * std::sin(ph);
-        }
-      *outm = put_cplx(re, im);
-    };
     const double th_l = M_PI / 3.0;
-    pw(0, F.nh, th_l, false, true, &F.m_Eh);
-    pw(-F.M, F.nm, th_l, false, false, &F.m_E);
-    pw(0, F.nh, th_l, true, true, &F.m_Fh);
-    pw(-F.M, F.nm, th_l, true, false, &F.m_F);
+    F.m_Eh = mb.plane_wave(nodes, 0, F.nh, th_l, false, true);
+    F.m_E = mb.plane_wave(nodes, -F.M, F.nm, th_l, false, false);
+    F.m_Fh = mb.plane_wave(nodes, 0, F.nh, th_l, true, true);
+    F.m_F = mb.plane_wave(nodes, -F.M, F.nm, th_l, true, false);
     const double th_r = o.periodic ? M_PI : 0.5 * h0;
-    pw(0, F.rnh, th_r, false, true, &F.m_REh);
-    pw(-F.rK, F.rnm, th_r, false, false, &F.m_RE);
-    pw(0, F.rnh, th_r, true, true, &F.m_RFh);
-    pw(-F.rK, F.rnm, th_r, true, false, &F.m_RF);
+    F.m_REh = mb.plane_wave(nodes, 0, F.rnh, th_r, false, true);
+    F.m_RE = mb.plane_wave(nodes, -F.rK, F.rnm, th_r, false, false);
+    F.m_RFh = mb.plane_wave(nodes, 0, F.rnh, th_r, true, true);
+    F.m_RF = mb.plane_wave(nodes, -F.rK, F.rnm, th_r, true, false);
     // kernel tables by q = |m|^2
     GammaHat gh(c);
     {
@@ -1501,6 +1882,7 @@ void far_setup(Plan& p) {
       F.sT_root = o.periodic ? 2.0 * M_PI : h0;
       if (std::fabs(gh(0.0) - 1.0) > 1e-12) throw Error{DMK_ERR_CUDA, "window normalisation check failed"};
     }
+    bank = std::move(mb.bytes);
     auto cb = std::make_shared<CachedBank>();
     cb->bank = bank;
     const size_t offs[16] = {F.m_nodes, F.m_bw, F.m_T0, F.m_T1, F.m_T0t, F.m_T1t, F.m_Eh, F.m_E,
@@ -1544,6 +1926,12 @@ void far_setup(Plan& p) {
     F.fused = (std::max(F.fused_out_bytes, F.fused_ev_bytes) <= static_cast<size_t>(dev_smem)) ? 1 : 0;
     F.fused_tree_bytes = fused_tree_smem(F.p, sizeof(float));
     F.fused_tree = F.fused_tree_bytes <= static_cast<size_t>(dev_smem) ? 1 : 0;
+    // tensor cores for the leaf kernels unless DMK_STOKES_FAR_TC=0 (the FP32-pipe kernels then run)
+    const char* env = std::getenv("DMK_STOKES_FAR_TC");
+    F.tc_NP = ((3 * F.p + 15) / 16) * 16;
+    F.tc_RW = std::max(16, ((F.p + 7) / 8) * 8);
+    F.tc = (!(env && env[0] == '0') && F.tc_NP <= 128 && F.tc_RW <= 40 &&
+            anterp_tc_smem(F.tc_NP, F.PB) <= static_cast<size_t>(dev_smem)) ? 1 : 0;
   }
   F.coll = upload(p, coll);
   F.root_box = upload(p, std::vector<int32_t>{0});
@@ -1748,6 +2136,7 @@ void far_setup(Plan& p) {
   F.s2 = big(static_cast<size_t>(max_jobs) * st * ec);
   F.rO = big(static_cast<size_t>(3) * F.rmodes * ec);
   F.W = big(static_cast<size_t>(std::max<int64_t>(T.N, 1)) * 3 * F.PB * er);
+  if (F.tc) F.Vs = big(static_cast<size_t>(std::max<int64_t>(T.N, 1)) * (F.ncomp / 3) * sizeof(float4));
   DMK_CUDA_TRY(cudaStreamSynchronize(s));
   p.far = Fp.release();
 }
@@ -1756,7 +2145,7 @@ void far_free(Plan& p) {
   FarState* F = p.far;
   if (!F) return;
   if (F->d2) far2d_free(p, F->d2);
-  for (void** b : {&F->q, &F->pot, &F->O, &F->I, &F->s1, &F->s2, &F->rO, &F->W})
+  for (void** b : {&F->q, &F->pot, &F->O, &F->I, &F->s1, &F->s2, &F->rO, &F->W, &F->Vs})
     if (*b) cudaFreeAsync(*b, p.stream);
   delete F;                                   // small arrays live in the plan's arena
   p.far = nullptr;
@@ -1793,6 +2182,29 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
     k_far_weights<R><<<F.nsrc_leaf, 256, 0, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, T.w,
                                                  T.N, F.box_geo, P, PB, nodes, bw, W);
     DMK_CUDA_TRY(cudaGetLastError());
+    ++p.launches;
+    const int g0 = F.slot_f >= 0 ? 0 : 1;
+    const int ng = (F.slot_f >= 0 ? 1 : 0) + (F.slot_t >= 0 ? 2 : 0);
+    if constexpr (sizeof(R) == 4) {
+      if (F.tc) {
+        float4* Vs = static_cast<float4*>(F.Vs);
+        k_far_values<<<grid_for(T.N, 256), 256, 0, s>>>(T.perm, d_f, d_g, d_n, T.N, g0, ng, Vs);
+        DMK_CUDA_TRY(cudaGetLastError());
+        ++p.launches;
+        const size_t shm_tc = anterp_tc_smem(F.tc_NP, PB);
+        DMK_CUDA_TRY(cudaFuncSetAttribute(k_far_anterp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(shm_tc)));
+        const unsigned nmt = static_cast<unsigned>((P * P + 127) / 128);
+        k_far_anterp_tc<<<dim3(F.nsrc_leaf, ng, nmt), kTcThreads, shm_tc, s>>>(
+            F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, W, Vs, T.N, F.slot_f,
+            F.slot_t, nc, q, P, PB, F.tc_NP, p.status);
+        DMK_CUDA_TRY(cudaGetLastError());
+        ++p.launches;
+      }
+    }
+  }
+  if (F.nsrc_leaf > 0 && !(F.tc && sizeof(R) == 4)) {
+    R* W = static_cast<R*>(F.W);
     const size_t shm = (static_cast<size_t>(kAntChunk) * 3 * PB + 4 * kAntChunk) * sizeof(R);
     auto kern = k_far_anterp<R>;
     DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm)));
@@ -1805,7 +2217,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
     kern<<<dim3(F.nsrc_leaf, ng, nz), nthr, shm, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, W,
                                                   T.perm, d_f, d_g, d_n, g0, F.slot_f, F.slot_t, nc, q, P, PB);
     DMK_CUDA_TRY(cudaGetLastError());
-    p.launches += 2;
+    p.launches += 1;
   }
   mark(2);
   // 2. upward merges, finest parents first
@@ -1955,7 +2367,25 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
                                                    nodes, bw, d_u);
     };
     if constexpr (sizeof(R) == 4) {
-      if (PB == 24) go(k_far_eval<R, 24, 2>, 2);
+      if (F.tc) {
+        auto go_tc = [&](auto kern, size_t shm_tc) {
+          DMK_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm_tc)));
+          if (T.sep)
+            kern<<<F.n_ev_items, kTcThreads, shm_tc, s>>>(F.ev_item_leaf, F.ev_item_off, F.trg_leaf, F.trg_leaf + F.ntrg_leaf,
+                                                   T.leaf_tstart, nullptr, T.tw, T.NT, T.tperm, F.box_geo, pot, P, nodes,
+                                                   bw, d_u, p.status);
+          else
+            kern<<<F.n_ev_items, kTcThreads, shm_tc, s>>>(F.ev_item_leaf, F.ev_item_off, F.trg_leaf, F.trg_leaf + F.ntrg_leaf,
+                                                   T.leaf_start, T.leaf_count, T.w, T.N, T.perm, F.box_geo, pot, P, nodes,
+                                                   bw, d_u, p.status);
+        };
+        switch (F.tc_RW) {
+          case 16: go_tc(k_far_eval_tc<16>, eval_tc_smem_t<16>(P)); break;
+          case 24: go_tc(k_far_eval_tc<24>, eval_tc_smem_t<24>(P)); break;
+          case 32: go_tc(k_far_eval_tc<32>, eval_tc_smem_t<32>(P)); break;
+          default: go_tc(k_far_eval_tc<40>, eval_tc_smem_t<40>(P)); break;
+        }
+      } else if (PB == 24) go(k_far_eval<R, 24, 2>, 2);
       else go(k_far_eval<R, 48, 1>, 1);
     } else {
       switch (PB) {

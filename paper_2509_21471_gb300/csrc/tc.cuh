@@ -1,0 +1,163 @@
+// Fifth-generation tensor cores (tcgen05) for the far field's dense contractions:
+// thin wrappers over the PTX instructions (sm_100a / sm_103a) and the operand
+// layout the kernels use.
+//
+//   * D (FP32, in tensor memory) += A B^T, A: M x K, B: N x K, both K-major in
+//     shared memory without swizzle, kind::tf32 (K = 8 per instruction), M = 128:
+//     row i of D sits in TMEM lane i, column j in TMEM column j.
+//   * Operand layout: 8-row x 16-byte core matrices of 128 contiguous bytes;
+//     core matrices adjacent along K are 128 B apart (the descriptor's leading
+//     byte offset), 8-row groups are `sbo` bytes apart (the stride byte offset).
+//   * FP32-level products from three TF32 products: x = hi + lo with hi, lo the
+//     TF32 roundings of x and of x - hi; a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi
+//     (the dropped a_lo b_lo and the residual of the split are ~2^-22 relative).
+//   * One thread issues the MMAs and commits them to an mbarrier; one warp waits on
+//     it with a bounded loop (a wait that runs out reports failure instead of
+//     spinning on) while the others wait at the block barrier.
+#pragma once
+#include <cstdint>
+
+namespace dmk {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// round to TF32 (nearest, ties away): the FP32 bit pattern with the low 13 mantissa bits clear
+__device__ __forceinline__ uint32_t tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32(x);
+  lo = tf32(x - __uint_as_float(hi));
+}
+// the same split by integer rounding of the bit patterns (half an ulp of the 10-bit
+// fraction added to the magnitude, the low 13 bits cleared): a few ALU operations
+// instead of two conversions; ties round away from zero like cvt.rna
+__device__ __forceinline__ uint32_t tf32_bits(uint32_t b) { return (b + 0x1000u) & 0xFFFFE000u; }
+__device__ __forceinline__ void split_tf32_fast(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_bits(__float_as_uint(x));
+  lo = tf32_bits(__float_as_uint(x - __uint_as_float(hi)));
+}
+
+// byte offset of element (row, k) of a K-major operand without swizzle (4-byte elements)
+__host__ __device__ constexpr int kmajor_off(int row, int k, int sbo) {
+  return (row >> 3) * sbo + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4;
+}
+
+// shared-memory matrix descriptor: start address, leading byte offset (128: K-adjacent
+// core matrices), stride byte offset, the fixed version bit (46), no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo) {
+  return static_cast<uint64_t>((addr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(128u >> 4) << 16) |
+         (static_cast<uint64_t>(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::tf32: D F32 (bits 4-5 = 1), A and B TF32 (bits 7-9,
+// 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// the three TF32 products of one K = 8 step: D (+)= Ah Bh + Ah Bl + Al Bh
+__device__ __forceinline__ void mma_tf32x3(uint32_t d_tmem, uint64_t ah, uint64_t al, uint64_t bh, uint64_t bl,
+                                           uint32_t idesc, uint32_t accumulate) {
+  mma_tf32(d_tmem, ah, bh, idesc, accumulate);
+  mma_tf32(d_tmem, ah, bl, idesc, 1u);
+  mma_tf32(d_tmem, al, bh, idesc, 1u);
+}
+
+// arrive once on the mbarrier when every MMA this thread issued so far has completed
+__device__ __forceinline__ void commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// wait for the phase of the given parity to complete; false if it has not after
+// about `max_cycles` SM cycles
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long max_cycles) {
+  const long long t0 = clock64();
+  uint32_t done = 0;
+  while (true) {
+    asm volatile(
+        "{\n.reg .pred P;\nmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\nselp.u32 %0, 1, 0, P;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > max_cycles) return false;
+  }
+}
+
+// tensor memory: allocated and freed by one whole warp; ncols a power of two >= 32
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 16 / 8 consecutive FP32 columns of this thread's lane (warp w reads lanes 32 (w % 4) ..);
+// the registers are valid after ld_wait()
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// thread stores to shared memory visible to the tensor cores (the async proxy)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// a barrier across which tcgen05 operations are ordered
+__device__ __forceinline__ void sync_tc() {
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+}
+
+// 16-byte asynchronous copies global -> shared (both 16-byte aligned), grouped per thread
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most N of this thread's groups are still in flight
+__device__ __forceinline__ void cp_async4(void* dst_smem, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+}  // namespace tc
+}  // namespace dmk
