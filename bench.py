@@ -38,8 +38,6 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the candidate dominant kernels at N = 5e5 (8-Gaussian recipe,
 # eps 1e-6, MIXED), keyed by (stage, leaf capacity); filled from ncu captures
 TRAFFIC_5E5 = {("near", 2048): 29.1e6, ("near", 4096): 29.0e6,
-               ("leaf_eval", 2048): 242.0e6, ("leaf_eval", 4096): 185.5e6,
-               ("leaf_charges", 2048): 643.0e6, ("leaf_charges", 4096): 577.2e6,
                ("outgoing", 2048): 1301.6e6, ("outgoing", 4096): 957.7e6,
                ("incoming", 2048): 1001.7e6, ("incoming", 4096): 744.3e6}
 
@@ -655,8 +653,8 @@ def run_ours(args):
     peak_basis = (f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
                   "(max SM clock of MEASURED_PEAKS.json)")
     mx = evals["mixed"]
-    kern_of = {"leaf_eval": "k_far_eval (leaf grids at the targets)",
-               "leaf_charges": "k_far_weights + k_far_anterp (leaf proxy charges)",
+    kern_of = {"leaf_eval": "k_far_eval_tc (leaf grids at the targets, tcgen05)",
+               "leaf_charges": "k_far_weights + k_far_values + k_far_anterp_tc (leaf proxy charges, tcgen05)",
                "outgoing": "k_far_out_fused (outgoing plane waves + kernel contraction)",
                "incoming": "k_far_ev_fused (incoming plane waves to the potential grids)"}
     stage_flops = {k: far_flops(k, mx["far_info"], N, N) for k in kern_of}
@@ -690,6 +688,29 @@ def run_ours(args):
         gbs = t5 * args.n / 500_000 / (mx["stage_ms"][k] / 1e3) / 1e9
         return {"dram_gbs": gbs, "hbm_frac": gbs / hbm_peak}
 
+    # the two tcgen05 stages against the TF32 tensor peak: measured bf16 x the nominal
+    # TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s dense); algorithmic flops, and the flops the
+    # MMAs issue (three split-TF32 products, M padded to 128-row tiles, N to 16 columns)
+    tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) * 1.1 / 2.25
+    fi = mx["far_info"]
+
+    def stage_tensor(k):
+        if k not in ("leaf_charges", "leaf_eval") or not fi["fp32"]:
+            return {}
+        p_ = fi["p"]
+        if k == "leaf_charges":     # per source and group: 128-row tiles of p^2 x NP columns x 2 (FMA) x 3
+            issued = N * ((p_ * p_ + 127) // 128 * 128) * ((3 * p_ + 15) // 16 * 16) * 2 * 3
+        else:                       # per target: 3p rows of RW columns in 240-column blocks x RW (K) x 2 x 3
+            rw = max(16, (p_ + 7) // 8 * 8)
+            rb = 256 // rw
+            while (rb * rw) % 16:
+                rb -= 1
+            issued = N * ((3 * p_ + rb - 1) // rb) * rb * rw * rw * 2 * 3
+        t = mx["stage_ms"][k] / 1e3
+        return {"engine": "tcgen05 kind::tf32, split-TF32 (3 MMAs per product)", "tf32_peak_tflops": tf32_peak,
+                "tensor_frac_algorithmic": stage_flops[k] / t / 1e12 / tf32_peak,
+                "tensor_frac_issued": issued / t / 1e12 / tf32_peak}
+
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
                 "traffic_note": "bytes per launch, ncu capture at N=5e5 (same leaf capacity) scaled by the point count",
@@ -699,8 +720,11 @@ def run_ours(args):
                 "all_stages": {k: {"ms": mx["stage_ms"][k],
                                    "tflops": stage_flops[k] / (mx["stage_ms"][k] / 1e3) / 1e12,
                                    "frac": stage_flops[k] / (mx["stage_ms"][k] / 1e3) / 1e12 / peak_tflops,
-                                   **stage_dram(k)}
+                                   **stage_dram(k), **stage_tensor(k)}
                                for k in kern_of}}
+    if stage_tensor(dom):           # a tensor-core stage dominates: its own peak
+        roofline.update(bound="tensor", peak=tf32_peak, frac=achieved / tf32_peak,
+                        peak_basis="bf16_tflops of MEASURED_PEAKS.json x 1.1 / 2.25 (nominal TF32 / bf16)")
     if near_tf is not None:
         roofline["near_field"] = {"kernel": kern_of["near"], "achieved": near_tf, "frac": near_tf / peak_tflops,
                                   "flops_per_useful_pair": flops_per_pair, "flops_one_side": flops_one_side,

@@ -194,28 +194,57 @@ constexpr int kAntChunk = 64;
 constexpr int kAntThreads = 320;
 
 // Lagrange weights of every point of the listed leaves, once per evaluation:
-// W[s][axis][PB] in sorted point order
+// W[s][axis][PB] in sorted point order.  A thread forms one row (s, axis) with one
+// reciprocal per node (L_j = (w_j / d_j) / sum_k w_k / d_k, exact at a node) into a
+// shared-memory tile of kWRows rows; the tile then leaves in consecutive addresses
+// (a leaf's rows are contiguous in W).
+constexpr int kWRows = 256;
 template <typename R>
-__global__ void k_far_weights(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
-                              const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ leaf_count,
-                              const double* __restrict__ w, int64_t N, const BoxGeo* __restrict__ box_geo, int p, int PB,
-                              const R* __restrict__ nodes, const R* __restrict__ bw, R* __restrict__ W) {
+__global__ void __launch_bounds__(kWRows) k_far_weights(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
+                                                        const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ leaf_count,
+                                                        const double* __restrict__ w, int64_t N, const BoxGeo* __restrict__ box_geo,
+                                                        int p, int PB, const R* __restrict__ nodes, const R* __restrict__ bw,
+                                                        R* __restrict__ W) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  R* sRow = reinterpret_cast<R*>(smem);                    // [kWRows][PB + 1]
   __shared__ R s_nodes[kMaxP], s_bw[kMaxP];
   for (int j = threadIdx.x; j < p; j += blockDim.x) {
     s_nodes[j] = nodes[j];
     s_bw[j] = bw[j];
   }
-  __syncthreads();
   const int li = leaf_list[blockIdx.x];
   const BoxGeo geo = box_geo[leaf_box[blockIdx.x]];
   const int s0 = leaf_start[li], ns = leaf_count[li];
   const double inv_half = 1.0 / geo.w;             // a power of two
-  for (int i = threadIdx.x; i < 3 * ns; i += blockDim.x) {
-    const int sl = i / 3, ax = i - 3 * sl;
-    const int64_t si = s0 + sl;
-    const double ctr = ax == 0 ? geo.x : (ax == 1 ? geo.y : geo.z);
-    const R t = static_cast<R>((w[ax * N + si] - ctr) * inv_half);
-    lagrange_row<R>(t, p, s_nodes, s_bw, W + (si * 3 + ax) * PB, 1, PB);
+  const int ld = PB + 1;
+  R* Wl = W + static_cast<int64_t>(s0) * 3 * PB;
+  for (int r0 = 0; r0 < 3 * ns; r0 += kWRows) {
+    const int nr = min(kWRows, 3 * ns - r0);
+    __syncthreads();                               // nodes loaded; the previous tile written out
+    if (threadIdx.x < nr) {
+      const int row = r0 + threadIdx.x;
+      const int sl = row / 3, ax = row - 3 * sl;
+      const double ctr = ax == 0 ? geo.x : (ax == 1 ? geo.y : geo.z);
+      const R t = static_cast<R>((w[ax * N + s0 + sl] - ctr) * inv_half);
+      R* out = sRow + threadIdx.x * ld;
+      R sum = R(0);
+      int hit = -1;
+      for (int j = 0; j < p; ++j) {
+        const R d = t - s_nodes[j];
+        R v = R(0);
+        if (d == R(0)) hit = j;
+        else v = s_bw[j] * recip<R>(d);
+        out[j] = v;
+        sum += v;
+      }
+      const R inv = hit >= 0 ? R(0) : recip<R>(sum);
+      for (int j = 0; j < PB; ++j) out[j] = j < p ? (hit >= 0 ? (j == hit ? R(1) : R(0)) : out[j] * inv) : R(0);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nr * PB; i += blockDim.x) {
+      const int r = i / PB, c = i - r * PB;
+      Wl[static_cast<int64_t>(r0) * PB + i] = sRow[r * ld + c];
+    }
   }
 }
 
@@ -934,15 +963,20 @@ __global__ void __launch_bounds__(kEvThreads) k_far_eval(const int32_t* __restri
       const R z = static_cast<R>((tw[2 * NT + t0 + t] - geo.z) * inv_half);
       R ssum = R(0);
       int hit = -1;
-      for (int j = 0; j < p; ++j) {
-        const R d = z - s_nodes[j];
-        if (d == R(0)) hit = j;
-        else ssum += s_bw[j] / d;
-      }
-      const R inv = hit >= 0 ? R(0) : R(1) / ssum;
 #pragma unroll
-      for (int j = 0; j < PB; ++j)
-        if (j < p) cw[uu][j] = hit >= 0 ? (j == hit ? R(1) : R(0)) : (s_bw[j] / (z - s_nodes[j])) * inv;
+      for (int j = 0; j < PB; ++j) {
+        R v = R(0);
+        if (j < p) {
+          const R d = z - s_nodes[j];
+          if (d == R(0)) hit = j;
+          else v = s_bw[j] * recip<R>(d);
+        }
+        cw[uu][j] = v;
+        ssum += v;
+      }
+      const R inv = hit >= 0 ? R(0) : recip<R>(ssum);
+#pragma unroll
+      for (int j = 0; j < PB; ++j) cw[uu][j] = hit >= 0 ? (j == hit ? R(1) : R(0)) : cw[uu][j] * inv;
     } else {
       for (int j = 0; j < p; ++j) sL[j * kEvThreads + t] = sL[(p + j) * kEvThreads + t] = R(0);
     }
@@ -1315,15 +1349,20 @@ __global__ void __launch_bounds__(kTcThreads) k_far_eval_tc(const int32_t* __res
     const float y = static_cast<float>((tw[NT + t0 + t] - geo.y) * inv_half);
     float sy = 0.f;
     int hy = -1;
-    for (int j = 0; j < p; ++j) {
-      const float dy = y - s_nodes[j];
-      if (dy == 0.f) hy = j;
-      else sy += s_bw[j] / dy;
-    }
-    const float iy = hy >= 0 ? 0.f : 1.f / sy;
 #pragma unroll
-    for (int j = 0; j < RW; ++j)
-      if (j < p) lb[j] = hy >= 0 ? (j == hy ? 1.f : 0.f) : (s_bw[j] / (y - s_nodes[j])) * iy;
+    for (int j = 0; j < RW; ++j) {
+      float v = 0.f;
+      if (j < p) {
+        const float d = y - s_nodes[j];
+        if (d == 0.f) hy = j;
+        else v = s_bw[j] * __frcp_rn(d);
+      }
+      lb[j] = v;
+      sy += v;
+    }
+    const float iy = hy >= 0 ? 0.f : __frcp_rn(sy);
+#pragma unroll
+    for (int j = 0; j < RW; ++j) lb[j] = hy >= 0 ? (j == hy ? 1.f : 0.f) : lb[j] * iy;
   }
   if (half == 0) {
     float lc[RW];
@@ -1335,15 +1374,20 @@ __global__ void __launch_bounds__(kTcThreads) k_far_eval_tc(const int32_t* __res
       const float z = static_cast<float>((tw[2 * NT + t0 + t] - geo.z) * inv_half);
       float sz = 0.f;
       int hz = -1;
-      for (int j = 0; j < p; ++j) {
-        const float dz = z - s_nodes[j];
-        if (dz == 0.f) hz = j;
-        else sz += s_bw[j] / dz;
-      }
-      const float iz = hz >= 0 ? 0.f : 1.f / sz;
 #pragma unroll
-      for (int j = 0; j < RW; ++j)
-        if (j < p) lc[j] = hz >= 0 ? (j == hz ? 1.f : 0.f) : (s_bw[j] / (z - s_nodes[j])) * iz;
+      for (int j = 0; j < RW; ++j) {
+        float v = 0.f;
+        if (j < p) {
+          const float d = z - s_nodes[j];
+          if (d == 0.f) hz = j;
+          else v = s_bw[j] * __frcp_rn(d);
+        }
+        lc[j] = v;
+        sz += v;
+      }
+      const float iz = hz >= 0 ? 0.f : __frcp_rn(sz);
+#pragma unroll
+      for (int j = 0; j < RW; ++j) lc[j] = hz >= 0 ? (j == hz ? 1.f : 0.f) : lc[j] * iz;
     } else {
       for (int j = 0; j < p; ++j) sLa[j * 128 + t] = 0.f;
     }
@@ -2179,7 +2223,9 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
   // 1. Lagrange weights of the sources, leaf proxy charges
   if (F.nsrc_leaf > 0) {
     R* W = static_cast<R*>(F.W);
-    k_far_weights<R><<<F.nsrc_leaf, 256, 0, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, T.w,
+    const size_t wshm = static_cast<size_t>(kWRows) * (PB + 1) * sizeof(R);
+    DMK_CUDA_TRY(cudaFuncSetAttribute(k_far_weights<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(wshm)));
+    k_far_weights<R><<<F.nsrc_leaf, kWRows, wshm, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, T.w,
                                                  T.N, F.box_geo, P, PB, nodes, bw, W);
     DMK_CUDA_TRY(cudaGetLastError());
     ++p.launches;

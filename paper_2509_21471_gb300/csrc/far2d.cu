@@ -577,15 +577,20 @@ __global__ void __launch_bounds__(kEv2Threads) k_far2_eval(const int32_t* __rest
     const R y = static_cast<R>((tw[NT + t0 + t] - geo.y) * inv_half);
     R ssum = R(0);
     int hit = -1;
-    for (int j = 0; j < p; ++j) {
-      const R d = y - s_nodes[j];
-      if (d == R(0)) hit = j;
-      else ssum += s_bw[j] / d;
-    }
-    const R inv = hit >= 0 ? R(0) : R(1) / ssum;
 #pragma unroll
-    for (int j = 0; j < PB; ++j)
-      if (j < p) cw[j] = hit >= 0 ? (j == hit ? R(1) : R(0)) : (s_bw[j] / (y - s_nodes[j])) * inv;
+    for (int j = 0; j < PB; ++j) {
+      R v = R(0);
+      if (j < p) {
+        const R d = y - s_nodes[j];
+        if (d == R(0)) hit = j;
+        else v = s_bw[j] * recip<R>(d);
+      }
+      cw[j] = v;
+      ssum += v;
+    }
+    const R inv = hit >= 0 ? R(0) : recip<R>(ssum);
+#pragma unroll
+    for (int j = 0; j < PB; ++j) cw[j] = hit >= 0 ? (j == hit ? R(1) : R(0)) : cw[j] * inv;
   } else {
     for (int j = 0; j < p; ++j) sL[j * kEv2Threads + t] = R(0);
   }

@@ -44,22 +44,33 @@ __device__ __forceinline__ void ld4(const double2* p, double2* v) {
   v[0] = p[0]; v[1] = p[1]; v[2] = p[2]; v[3] = p[3];
 }
 
+// 1 / d in the far field's precision: the correctly rounded reciprocal in float32
+// (one reciprocal per node serves the barycentric sum and the values), a division in
+// float64
+template <typename R> __device__ __forceinline__ R recip(R d);
+template <> __device__ __forceinline__ float recip<float>(float d) { return __frcp_rn(d); }
+template <> __device__ __forceinline__ double recip<double>(double d) { return 1.0 / d; }
+
 // Lagrange basis at the Chebyshev points of the first kind in barycentric form
-// (weights (-1)^j sin((2j+1) pi / 2p)), in the far field's precision; exact at a
-// node; out[j * stride] for j < pad (zero past p)
+// (weights (-1)^j sin((2j+1) pi / 2p)), in the far field's precision:
+// L_j(t) = (w_j / (t - x_j)) / sum_k w_k / (t - x_k), exact at a node;
+// out[j * stride] for j < pad (zero past p)
 template <typename R>
 __device__ inline void lagrange_row(R t, int p, const R* nodes, const R* bw, R* out, int stride, int pad) {
   R s = R(0);
   int hit = -1;
   for (int j = 0; j < p; ++j) {
     const R d = t - nodes[j];
+    R v = R(0);
     if (d == R(0)) hit = j;
-    else s += bw[j] / d;
+    else v = bw[j] * recip<R>(d);
+    out[j * stride] = v;
+    s += v;
   }
-  const R inv = hit >= 0 ? R(0) : R(1) / s;
+  const R inv = hit >= 0 ? R(0) : recip<R>(s);
   for (int j = 0; j < pad; ++j) {
     R v = R(0);
-    if (j < p) v = hit >= 0 ? (j == hit ? R(1) : R(0)) : (bw[j] / (t - nodes[j])) * inv;
+    if (j < p) v = hit >= 0 ? (j == hit ? R(1) : R(0)) : out[j * stride] * inv;
     out[j * stride] = v;
   }
 }

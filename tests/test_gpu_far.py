@@ -165,3 +165,24 @@ def test_traced_evaluation_matches_eval_and_times_every_stage(dmk):
         else:
             assert sum(v for k, v in ms.items() if k != "near") == 0.0
         p.close()
+
+
+@pytest.mark.parametrize("eps,kernels", [(1e-3, 1), (1e-5, 3), (1e-6, 1), (1e-6, 3), (2e-7, 1)])
+def test_tensor_core_leaf_kernels_match_fp32_pipe(dmk, monkeypatch, eps, kernels):
+    """MIXED: the tcgen05 leaf charges and leaf evaluation (split-TF32 products, row
+    widths 16 / 24 / 32, 48 / 64 / 80 charge columns) against the FP32-pipe kernels on
+    the same plan, and both against the direct sum."""
+    rng = np.random.default_rng(500 + kernels)
+    N = 5000
+    x = wl.gaussian_mixture_points(rng, N, 3, 8, 0.05)
+    f = wl.forces(rng, N, 3) if kernels & 1 else None
+    g = wl.stresslet_strengths(rng, N, 3) if kernels & 2 else None
+    nrm = wl.unit_normals(rng, N, 3) if kernels & 2 else None
+    monkeypatch.setenv("DMK_STOKES_FAR_TC", "1")
+    u_tc, info = _run(dmk, x, f, g, nrm, eps, 1, 150, False, dmk.ALL)
+    monkeypatch.setenv("DMK_STOKES_FAR_TC", "0")
+    u_pipe, _ = _run(dmk, x, f, g, nrm, eps, 1, 150, False, dmk.ALL)
+    assert info["fp32"] == 1
+    assert rel_l2(u_tc, u_pipe) < max(1e-5, eps), rel_l2(u_tc, u_pipe)
+    ref = direct.direct_sum(x, f, g, nrm)
+    assert rel_l2(u_tc, ref) < 10 * eps, rel_l2(u_tc, ref)
