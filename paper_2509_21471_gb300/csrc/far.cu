@@ -1114,9 +1114,11 @@ inline size_t anterp_tc_smem(int NP, int PB) {
 }
 
 // leaf proxy charges: per leaf and component group, Q[(a,b)][(k,c)] = sum_s A[(a,b)][s] B[(k,c)][s]
-// with A = L_a(x_s) L_b(y_s) and B = L_c(z_s) v_s,k.  A block owns 128 rows (a, b)
-// (blockIdx.z) and all 3p columns (padded to NP, a multiple of 16, <= 128) in tensor
-// memory.  Per stage of kTcK sources, warps 0-3 form row tid of A and warps 4-7 row
+// with A = L_a(x_s) L_b(y_s) and B = L_c(z_s) v_s,k.  A block owns one tile of 128
+// rows (a, b) and all 3p columns (padded to NP, a multiple of 16, <= 128) in tensor
+// memory; the tiles of one leaf are consecutive blocks, so they run side by side and
+// read the leaf's weights once from HBM (then from L2).  Per stage of kTcK
+// sources, warps 0-3 form row tid of A and warps 4-7 row
 // tid - 128 of B from the stage's weights and densities (which arrive by cp.async one
 // stage ahead).  The result leaves through shared memory in the layout
 // q[box][slot + k][a][b][c].
@@ -1138,7 +1140,9 @@ __global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const int32_t* __r
   __shared__ uint32_t tbase;
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int li = leaf_list[blockIdx.x], box = leaf_box[blockIdx.x];
+  const int nmt = (p * p + 127) / 128;
+  const int leaf = blockIdx.x / nmt, mt = blockIdx.x - leaf * nmt;   // a leaf's row tiles run side by side
+  const int li = leaf_list[leaf], box = leaf_box[leaf];
   const int gi = blockIdx.y;
   const int grp = (slot_f >= 0 ? 0 : 1) + gi;
   const int slot = grp == 0 ? slot_f : slot_t + 3 * (grp - 1);
@@ -1147,7 +1151,7 @@ __global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const int32_t* __r
   const int64_t p3 = static_cast<int64_t>(p2) * p;
   const bool arole = tid < 128;
   const int rr = arole ? tid : tid - 128;
-  const int R = blockIdx.z * 128 + rr;
+  const int R = mt * 128 + rr;
   // weight offsets of this thread's row within a source's [3][PB] block (zero row: none)
   int w0 = -1, w1 = -1;
   if (arole && R < p2) {                                               // row (a, b) of A: L_a(x) L_b(y)
@@ -1242,7 +1246,7 @@ __global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const int32_t* __r
       for (int j = 0; j < 16; ++j) sD[row * (NP + 1) + cb * 16 + j] = v[j];
     }
     __syncthreads();
-    const int R0 = blockIdx.z * 128, nrow = min(128, p2 - R0);
+    const int R0 = mt * 128, nrow = min(128, p2 - R0);
     float* qb = q + (static_cast<int64_t>(box) * ncomp + slot) * p3 + static_cast<int64_t>(R0) * p;
     for (int i = tid; i < 3 * nrow * p; i += kTcThreads) {
       const int k = i / (nrow * p), rem = i - k * nrow * p;
@@ -2241,7 +2245,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
         DMK_CUDA_TRY(cudaFuncSetAttribute(k_far_anterp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           static_cast<int>(shm_tc)));
         const unsigned nmt = static_cast<unsigned>((P * P + 127) / 128);
-        k_far_anterp_tc<<<dim3(F.nsrc_leaf, ng, nmt), kTcThreads, shm_tc, s>>>(
+        k_far_anterp_tc<<<dim3(F.nsrc_leaf * nmt, ng), kTcThreads, shm_tc, s>>>(
             F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, W, Vs, T.N, F.slot_f,
             F.slot_t, nc, q, P, PB, F.tc_NP, p.status);
         DMK_CUDA_TRY(cudaGetLastError());
