@@ -454,7 +454,7 @@ def run_extras(args, dmk, wl, timed, max_over_ranks, rank, k_mixed=3, k_fp64=2):
             ud = torch.empty((n, dim), dtype=torch.float64, device="cuda")
             levels = [0]
 
-            comp = dmk.ALL if dim == 3 else dmk.NEAR      # the far field is provided in 3D
+            comp = dmk.ALL                                # the whole DMK sum (near + far field)
 
             def step():
                 p = dmk.Plan(xsd, targets=xtd, eps=1e-6, kernels=kern, precision=dmk.MIXED, components=comp)
