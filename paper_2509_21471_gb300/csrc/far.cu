@@ -34,6 +34,9 @@
 #include "far_common.cuh"
 #include "tc.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -1104,12 +1107,12 @@ __global__ void k_far_values(const int32_t* __restrict__ perm, const double* __r
 
 // shared memory of the leaf-charge kernel: one operand buffer (A hi/lo [128][kTcK],
 // B hi/lo [NP][kTcK]) and two source stages (weights [kTcK][3][PB], densities
-// [kTcK][4]); at least a quarter of the SM so that at most three blocks (384 TMEM
-// columns) share one
+// [kTcK][4], 128-byte aligned); at least a quarter of the SM so that at most three
+// blocks (384 TMEM columns) share one
 inline size_t anterp_tc_op_bytes(int NP) { return 2 * 128 * kTcK * 4 + 2 * static_cast<size_t>(NP) * kTcK * 4; }
 inline size_t anterp_tc_stage_floats(int PB) { return static_cast<size_t>(kTcK) * 3 * PB + kTcK * 4; }
 inline size_t anterp_tc_smem(int NP, int PB) {
-  const size_t need = anterp_tc_op_bytes(NP) + 2 * anterp_tc_stage_floats(PB) * 4;
+  const size_t need = anterp_tc_op_bytes(NP) + 2 * anterp_tc_stage_floats(PB) * 4 + 128;
   return std::max({need, kSmemPerSM / 4 + 1024, 128 * static_cast<size_t>(NP + 1) * 4});
 }
 
@@ -1117,16 +1120,17 @@ inline size_t anterp_tc_smem(int NP, int PB) {
 // with A = L_a(x_s) L_b(y_s) and B = L_c(z_s) v_s,k.  A block owns one tile of 128
 // rows (a, b) and all 3p columns (padded to NP, a multiple of 16, <= 128) in tensor
 // memory; the tiles of one leaf are consecutive blocks, so they run side by side and
-// read the leaf's weights once from HBM (then from L2).  Per stage of kTcK
-// sources, warps 0-3 form row tid of A and warps 4-7 row
-// tid - 128 of B from the stage's weights and densities (which arrive by cp.async one
-// stage ahead).  The result leaves through shared memory in the layout
-// q[box][slot + k][a][b][c].
-__global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
+// read the leaf's weights once from HBM (then from L2).  Per stage of kTcK sources,
+// warps 0-3 form row tid of A and warps 4-7 row tid - 128 of B from the stage's
+// weights and densities, which arrive one stage ahead by two TMA tile loads
+// (tmW: W as [N][3 PB], tmV: Vs as [groups N][4]) on the stage's mbarrier.  The
+// result leaves through shared memory in the layout q[box][slot + k][a][b][c].
+__global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const __grid_constant__ CUtensorMap tmW,
+                                                              const __grid_constant__ CUtensorMap tmV,
+                                                              const int32_t* __restrict__ leaf_list, const int32_t* __restrict__ leaf_box,
                                                               const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ leaf_count,
-                                                              const float* __restrict__ W, const float4* __restrict__ Vs, int64_t N,
-                                                              int slot_f, int slot_t, int ncomp, float* __restrict__ q, int p,
-                                                              int PB, int NP, int* __restrict__ status) {
+                                                              int64_t N, int slot_f, int slot_t, int ncomp, float* __restrict__ q,
+                                                              int p, int PB, int NP, int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t opA = 128 * kTcK * 4, opB = static_cast<size_t>(NP) * kTcK * 4;
   const int stW = kTcK * 3 * PB;                                       // weight floats of one stage
@@ -1135,8 +1139,12 @@ __global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const int32_t* __r
   unsigned char* sAl = sAh + opA;
   unsigned char* sBh = sAl + opA;
   unsigned char* sBl = sBh + opB;
-  float* stage0 = reinterpret_cast<float*>(sBl + opB);
-  __shared__ __align__(8) uint64_t mbar;
+  float* stage0;
+  {
+    const uint32_t a = tc::smem_u32(sBl + opB);
+    stage0 = reinterpret_cast<float*>(sBl + opB + ((128u - (a & 127u)) & 127u));   // TMA destinations: 128-byte aligned
+  }
+  __shared__ __align__(8) uint64_t mbar, mbst[2];
   __shared__ uint32_t tbase;
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -1162,43 +1170,44 @@ __global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const int32_t* __r
     w1 = rr / p;
   }
   const bool forms = arole || rr < NP;
+  const int nchunk = (ns + kTcK - 1) / kTcK;
+  auto stage_in = [&](int ch) {                                        // thread 0: the TMA loads of stage ch
+    float* sw = stage0 + (ch & 1) * stF;
+    const int y = s0 + ch * kTcK;
+    tc::expect_tx(&mbst[ch & 1], static_cast<uint32_t>(stF) * 4u);
+    tc::tma_load_2d(sw, &tmW, 0, y, &mbst[ch & 1]);
+    tc::tma_load_2d(sw + stW, &tmV, 0, static_cast<int>(gi * N) + y, &mbst[ch & 1]);
+  };
   if (tid == 0) {
     tc::mbar_init(&mbar, 1);
+    tc::mbar_init(&mbst[0], 1);
+    tc::mbar_init(&mbst[1], 1);
     fail = 0;
+    if (nchunk > 0) stage_in(0);
   }
   if (warp == 0) tc::tmem_alloc(&tbase, 128);
-  const int nchunk = (ns + kTcK - 1) / kTcK;
-  const float* Vg = reinterpret_cast<const float*>(Vs + gi * N);
-  auto stage_in = [&](int ch) {                                        // weights and densities of stage ch
-    const int sc = ch * kTcK, ncnt = min(kTcK, ns - sc);
-    float* sw = stage0 + (ch & 1) * stF;
-    const float* srcw = W + (static_cast<int64_t>(s0) + sc) * 3 * PB;
-    for (int i = tid; i < ncnt * 3 * PB / 4; i += kTcThreads) tc::cp_async16(sw + 4 * i, srcw + 4 * i);
-    const float* srcv = Vg + (static_cast<int64_t>(s0) + sc) * 4;
-    for (int i = tid; i < ncnt; i += kTcThreads) tc::cp_async16(sw + stW + 4 * i, srcv + 4 * i);
-    for (int i = ncnt * 3 * PB + tid; i < stW; i += kTcThreads) sw[i] = 0.f;       // tail sources: zero
-    for (int i = ncnt * 4 + tid; i < kTcK * 4; i += kTcThreads) sw[stW + i] = 0.f;
-    tc::cp_async_commit();
-  };
-  if (nchunk > 0) stage_in(0);
   tc::sync_tc();
   const uint32_t tmem = tbase;
   const uint32_t idesc = tc::idesc_tf32(128, NP);
   unsigned char* dh = arole ? sAh : sBh;
   unsigned char* dl = arole ? sAl : sBl;
-  int issued = 0;
+  int issued = 0, staged = nchunk > 0 ? 1 : 0;
   for (int ch = 0; ch < nchunk; ++ch) {
-    if (ch + 1 < nchunk) {
-      stage_in(ch + 1);                                                // its stage was last read while forming ch - 1
-      tc::cp_async_wait<1>();
-    } else {
-      tc::cp_async_wait<0>();
+    if (ch + 1 < nchunk) {                                             // its stage was last read while forming ch - 1
+      if (tid == 0) stage_in(ch + 1);
+      ++staged;
     }
+    if (!tc::mbar_wait(&mbst[ch & 1], (ch >> 1) & 1, kTcWaitCycles)) fail = 1;
     if (ch >= 1 && warp == 0)                                          // the operands were read by the MMAs of ch - 1
       if (!tc::mbar_wait(&mbar, (ch - 1) & 1, kTcWaitCycles)) fail = 1;
+    const int ncnt = min(kTcK, ns - ch * kTcK);
+    float* sw = stage0 + (ch & 1) * stF;
+    if (ncnt < kTcK) {                                                 // a leaf's last stage: sources past it read as zero
+      for (int i = ncnt * 3 * PB + tid; i < stW; i += kTcThreads) sw[i] = 0.f;
+      for (int i = ncnt * 4 + tid; i < kTcK * 4; i += kTcThreads) sw[stW + i] = 0.f;
+    }
     __syncthreads();
     if (fail) break;
-    const float* sw = stage0 + (ch & 1) * stF;
     if (forms) {
 #pragma unroll 4
       for (int s4 = 0; s4 < kTcK / 4; ++s4) {
@@ -1256,8 +1265,8 @@ __global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const int32_t* __r
   } else if (fail) {
     if (tid == 0) atomicOr(status, ST_TC_TIMEOUT);
     if (issued > 0 && warp == 0) tc::mbar_wait(&mbar, (issued - 1) & 1, kTcWaitCycles);
+    if (staged > 0) tc::mbar_wait(&mbst[(staged - 1) & 1], ((staged - 1) >> 1) & 1, kTcWaitCycles);   // the last TMA load
   }
-  tc::cp_async_wait<0>();
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 128);
@@ -1562,6 +1571,7 @@ struct FarState {
   int tc = 0;                        // 1: float32 leaf charges and leaf evaluation on the tensor cores
   int tc_NP = 0, tc_RW = 0;          // their padded column count (3p) and row width (p)
   void* Vs = nullptr;                // [groups][N] float4 densities of the sources (tensor-core charges)
+  CUtensorMap tmW{}, tmV{};          // TMA maps of W as [N][3 PB] and of Vs as [groups N][4], 32-row boxes
   size_t fused_out_bytes = 0, fused_ev_bytes = 0;
   int32_t* coll = nullptr;           // [27] colleague slots of the root
   int32_t* root_tlist = nullptr;     // {target index of the root}
@@ -1642,13 +1652,42 @@ void launch_rot(const Plan& p, const RotLaunch& L, const void* X, void* Y, int64
   ++p.launches;
 }
 
-RotLaunch make_launch(Plan& p, const std::vector<RotJob>& jobs) {
+RotLaunch make_launch(Uploader& up, const std::vector<RotJob>& jobs) {
   RotLaunch L;
   L.n = static_cast<int>(jobs.size());
-  if (L.n) L.jobs = upload(p, jobs);
+  if (L.n) L.jobs = up.put(jobs);
   return L;
 }
 
+}  // namespace
+
+namespace {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to the
+// driver library); null when the driver does not provide it
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }();
+  return fn;
+}
+// a row-major float32 [rows][inner] array read in boxes of 32 rows (inner x 4 bytes a
+// multiple of 16, at most 256 elements)
+bool encode_rows(CUtensorMap* m, const void* base, uint64_t inner, uint64_t rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc || rows == 0 || inner > 256 || (inner * 4) % 16) return false;
+  const cuuint64_t dim[2] = {inner, rows};
+  const cuuint64_t stride[1] = {inner * 4};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(inner), static_cast<cuuint32_t>(kTcK)};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dim, stride, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 }  // namespace
 
 void far_setup(Plan& p) {
@@ -1663,6 +1702,7 @@ void far_setup(Plan& p) {
   cudaStream_t s = p.stream;
   auto Fp = std::make_unique<FarState>();
   FarState& F = *Fp;
+  Uploader up(p);
   F.fp32 = fp32_pair_terms(o) ? 1 : 0;
   const double c = p.tables.c;
   const int tcp = static_cast<int>(std::lround(3.0 * c / M_PI));
@@ -1850,9 +1890,9 @@ void far_setup(Plan& p) {
     for (int ch = 0; ch < 8; ++ch) gch.push_back(trg_index[b.child[ch]]);
   }
   F.ngrp = static_cast<int>(gch.size() / 8);
-  F.grp_win = upload(p, gwin);
-  F.grp_ch = upload(p, gch);
-  F.root_tlist = upload(p, std::vector<int32_t>{trg_index[0]});
+  F.grp_win = up.put(gwin);
+  F.grp_ch = up.put(gch);
+  F.root_tlist = up.put(std::vector<int32_t>{trg_index[0]});
   std::vector<BoxGeo> geo(nb);
   std::vector<int32_t> blev(nb);
   for (int i = 0; i < nb; ++i) {
@@ -1939,20 +1979,19 @@ void far_setup(Plan& p) {
     cb->sT_root = F.sT_root;
     store_bank(bkey, cb);
   }
-  F.mats = p.arena.alloc<char>(bank.size());
-  DMK_CUDA_TRY(cudaMemcpyAsync(F.mats, bank.data(), bank.size(), cudaMemcpyHostToDevice, s));
-  F.box_geo = upload(p, geo);
-  F.box_level = upload(p, blev);
+  F.mats = up.put(bank);
+  F.box_geo = up.put(geo);
+  F.box_level = up.put(blev);
   {
     std::vector<int32_t> sl(src_leaf);
     sl.insert(sl.end(), src_leaf_box.begin(), src_leaf_box.end());
-    F.src_leaf = upload(p, sl);
+    F.src_leaf = up.put(sl);
     std::vector<int32_t> tl(trg_leaf);
     tl.insert(tl.end(), trg_leaf_box.begin(), trg_leaf_box.end());
-    F.trg_leaf = upload(p, tl);
+    F.trg_leaf = up.put(tl);
   }
-  F.src_box_list = upload(p, src_boxes);
-  F.trg_box_list = upload(p, trg_boxes);
+  F.src_box_list = up.put(src_boxes);
+  F.trg_box_list = up.put(trg_boxes);
   {
     std::vector<int32_t> il, io;
     for (size_t e = 0; e < trg_leaf.size(); ++e) {
@@ -1963,8 +2002,8 @@ void far_setup(Plan& p) {
       }
     }
     F.n_ev_items = static_cast<int>(il.size());
-    F.ev_item_leaf = upload(p, il);
-    F.ev_item_off = upload(p, io);
+    F.ev_item_leaf = up.put(il);
+    F.ev_item_off = up.put(io);
   }
   if (F.fp32) {
     F.fused_out_bytes = fused_out_smem(F.p, F.nh, F.nm, sizeof(float));
@@ -1981,8 +2020,8 @@ void far_setup(Plan& p) {
     F.tc = (!(env && env[0] == '0') && F.tc_NP <= 128 && F.tc_RW <= 40 &&
             anterp_tc_smem(F.tc_NP, F.PB) <= static_cast<size_t>(dev_smem)) ? 1 : 0;
   }
-  F.coll = upload(p, coll);
-  F.root_box = upload(p, std::vector<int32_t>{0});
+  F.coll = up.put(coll);
+  F.root_box = up.put(std::vector<int32_t>{0});
 
   // ---- scratch strides and job lists ---------------------------------------------------
   const int64_t p2 = static_cast<int64_t>(P) * P;
@@ -2052,13 +2091,13 @@ void far_setup(Plan& p) {
       ++np;
     }
     if (np == 0) continue;
-    F.mf_par.push_back(upload(p, fpar));
-    F.mf_ch.push_back(upload(p, fch));
+    F.mf_par.push_back(up.put(fpar));
+    F.mf_ch.push_back(up.put(fch));
     F.mf_n.push_back(np);
     F.merge_level.push_back(l);
-    F.merge[0].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j1));
-    F.merge[1].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j2));
-    F.merge[2].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j3));
+    F.merge[0].push_back(F.fused_tree ? RotLaunch{} : make_launch(up, j1));
+    F.merge[1].push_back(F.fused_tree ? RotLaunch{} : make_launch(up, j2));
+    F.merge[2].push_back(F.fused_tree ? RotLaunch{} : make_launch(up, j3));
     if (!F.fused_tree)
       max_jobs = std::max<int64_t>(max_jobs, (static_cast<int64_t>(np) * nc * 4 * P3 + 2 * st - 1) / (2 * st) + 1);
   }
@@ -2111,13 +2150,13 @@ void far_setup(Plan& p) {
       ++np;
     }
     if (np == 0) continue;
-    F.if_par.push_back(upload(p, fpar));
-    F.if_ch.push_back(upload(p, fch));
+    F.if_par.push_back(up.put(fpar));
+    F.if_ch.push_back(up.put(fch));
     F.if_n.push_back(np);
     F.interp_level.push_back(l);
-    F.interp[0].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j1));
-    F.interp[1].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j2));
-    F.interp[2].push_back(F.fused_tree ? RotLaunch{} : make_launch(p, j3));
+    F.interp[0].push_back(F.fused_tree ? RotLaunch{} : make_launch(up, j1));
+    F.interp[1].push_back(F.fused_tree ? RotLaunch{} : make_launch(up, j2));
+    F.interp[2].push_back(F.fused_tree ? RotLaunch{} : make_launch(up, j3));
     if (!F.fused_tree)
       max_jobs = std::max<int64_t>(max_jobs, (static_cast<int64_t>(np) * 3 * 4 * P3 + 2 * st - 1) / (2 * st) + 1);
   }
@@ -2152,12 +2191,12 @@ void far_setup(Plan& p) {
       e3.push_back(J);
     }
     if (!F.fused) {
-      F.out1 = make_launch(p, a1);
-      F.out2 = make_launch(p, a2);
-      F.out3 = make_launch(p, a3);
-      F.ev1 = make_launch(p, e1);
-      F.ev2 = make_launch(p, e2);
-      F.ev3 = make_launch(p, e3);
+      F.out1 = make_launch(up, a1);
+      F.out2 = make_launch(up, a2);
+      F.out3 = make_launch(up, a3);
+      F.ev1 = make_launch(up, e1);
+      F.ev2 = make_launch(up, e2);
+      F.ev3 = make_launch(up, e3);
     }
     RotJob J;
     J.x1 = -1;
@@ -2165,9 +2204,10 @@ void far_setup(Plan& p) {
     J.x0 = 0;
     J.y = 0;
     // one job at offset 0 for every root stage: q[root], the scratch, pot[root] (+ component offsets)
-    const RotLaunch one = make_launch(p, std::vector<RotJob>{J});
+    const RotLaunch one = make_launch(up, std::vector<RotJob>{J});
     F.r1 = F.r2 = F.r3 = F.rv1 = F.rv2 = F.rv3 = one;
   }
+  up.flush();
   // ---- big buffers -------------------------------------------------------------------
   const size_t er = elem_r(F), ec = 2 * er;
   auto big = [&](size_t bytes) {
@@ -2184,7 +2224,12 @@ void far_setup(Plan& p) {
   F.s2 = big(static_cast<size_t>(max_jobs) * st * ec);
   F.rO = big(static_cast<size_t>(3) * F.rmodes * ec);
   F.W = big(static_cast<size_t>(std::max<int64_t>(T.N, 1)) * 3 * F.PB * er);
-  if (F.tc) F.Vs = big(static_cast<size_t>(std::max<int64_t>(T.N, 1)) * (F.ncomp / 3) * sizeof(float4));
+  if (F.tc) {
+    F.Vs = big(static_cast<size_t>(std::max<int64_t>(T.N, 1)) * (F.ncomp / 3) * sizeof(float4));
+    if (T.N > 0 && !(encode_rows(&F.tmW, F.W, 3 * static_cast<uint64_t>(F.PB), static_cast<uint64_t>(T.N)) &&
+                     encode_rows(&F.tmV, F.Vs, 4, static_cast<uint64_t>(T.N) * (F.ncomp / 3))))
+      F.tc = 0;                      // no tensor maps here: the FP32-pipe leaf kernels
+  }
   DMK_CUDA_TRY(cudaStreamSynchronize(s));
   p.far = Fp.release();
 }
@@ -2246,8 +2291,8 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
                                           static_cast<int>(shm_tc)));
         const unsigned nmt = static_cast<unsigned>((P * P + 127) / 128);
         k_far_anterp_tc<<<dim3(F.nsrc_leaf * nmt, ng), kTcThreads, shm_tc, s>>>(
-            F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, W, Vs, T.N, F.slot_f,
-            F.slot_t, nc, q, P, PB, F.tc_NP, p.status);
+            F.tmW, F.tmV, F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, T.N, F.slot_f, F.slot_t,
+            nc, q, P, PB, F.tc_NP, p.status);
         DMK_CUDA_TRY(cudaGetLastError());
         ++p.launches;
       }

@@ -700,6 +700,7 @@ Far2State* far2d_setup(Plan& p) {
   cudaStream_t s = p.stream;
   auto Fp = std::make_unique<Far2State>();
   Far2State& F = *Fp;
+  Uploader up(p);
   F.fp32 = fp32_pair_terms(o) ? 1 : 0;
   const double c = p.tables.c;
   const int tcp = static_cast<int>(std::lround(3.0 * c / M_PI));
@@ -883,8 +884,8 @@ Far2State* far2d_setup(Plan& p) {
       for (int k = 0; k < 4; ++k) ch.push_back(boxes[b.child[k]].src ? b.child[k] : -1);
     }
     if (par.empty()) continue;
-    F.mf_par.push_back(upload(p, par));
-    F.mf_ch.push_back(upload(p, ch));
+    F.mf_par.push_back(up.put(par));
+    F.mf_ch.push_back(up.put(ch));
     F.mf_n.push_back(static_cast<int>(par.size()));
   }
   for (int l = 0; l < maxlev; ++l) {
@@ -896,8 +897,8 @@ Far2State* far2d_setup(Plan& p) {
       for (int k = 0; k < 4; ++k) ch.push_back(boxes[b.child[k]].trg ? b.child[k] : -1);
     }
     if (par.empty()) continue;
-    F.if_par.push_back(upload(p, par));
-    F.if_ch.push_back(upload(p, ch));
+    F.if_par.push_back(up.put(par));
+    F.if_ch.push_back(up.put(ch));
     F.if_n.push_back(static_cast<int>(par.size()));
   }
 
@@ -958,20 +959,19 @@ Far2State* far2d_setup(Plan& p) {
     F.m_rtab = bank.put_real(rt);
     F.sT_root = o.periodic ? 2.0 * M_PI : h0;
   }
-  F.mats = p.arena.alloc<char>(bank.bytes.size());
-  DMK_CUDA_TRY(cudaMemcpyAsync(F.mats, bank.bytes.data(), bank.bytes.size(), cudaMemcpyHostToDevice, s));
-  F.box_geo = upload(p, geo);
-  F.box_level = upload(p, blev);
+  F.mats = up.put(bank.bytes);
+  F.box_geo = up.put(geo);
+  F.box_level = up.put(blev);
   {
     std::vector<int32_t> sl(src_leaf);
     sl.insert(sl.end(), src_leaf_box.begin(), src_leaf_box.end());
-    F.src_leaf = upload(p, sl);
+    F.src_leaf = up.put(sl);
     std::vector<int32_t> tl(trg_leaf);
     tl.insert(tl.end(), trg_leaf_box.begin(), trg_leaf_box.end());
-    F.trg_leaf = upload(p, tl);
+    F.trg_leaf = up.put(tl);
   }
-  F.src_box_list = upload(p, src_boxes);
-  F.trg_box_list = upload(p, trg_boxes);
+  F.src_box_list = up.put(src_boxes);
+  F.trg_box_list = up.put(trg_boxes);
   {
     std::vector<int32_t> il, io;
     for (size_t e = 0; e < trg_leaf.size(); ++e) {
@@ -982,13 +982,13 @@ Far2State* far2d_setup(Plan& p) {
       }
     }
     F.n_ev_items = static_cast<int>(il.size());
-    F.ev_item_leaf = upload(p, il);
-    F.ev_item_off = upload(p, io);
+    F.ev_item_leaf = up.put(il);
+    F.ev_item_off = up.put(io);
   }
-  F.coll = upload(p, coll);
-  F.grp_win = upload(p, gwin);
-  F.grp_ch = upload(p, gch);
-  F.root_box = upload(p, std::vector<int32_t>{0});
+  F.coll = up.put(coll);
+  F.grp_win = up.put(gwin);
+  F.grp_ch = up.put(gch);
+  F.root_box = up.put(std::vector<int32_t>{0});
   const size_t er = F.fp32 ? sizeof(float) : sizeof(double), ec = 2 * er;
   F.out_bytes = out2_smem(P, F.nh, F.nm, er);
   F.ev_bytes = ev2_smem(P, F.nh, F.nm, er);
@@ -1001,6 +1001,7 @@ Far2State* far2d_setup(Plan& p) {
     const size_t need = std::max({F.out_bytes, F.ev_bytes, F.rout_bytes, F.rev_bytes, F.tree_bytes});
     if (need > static_cast<size_t>(dev_smem)) throw Error{DMK_ERR_UNSUPPORTED, "2D far field: shared memory too small"};
   }
+  up.flush();
   // ---- big buffers -------------------------------------------------------------------
   auto big = [&](size_t bytes) {
     void* ptr = nullptr;

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 namespace dmk {
@@ -118,12 +119,54 @@ inline int table2_p(double eps, int kernels) {
   return p;
 }
 
-template <typename T>
-T* upload(Plan& p, const std::vector<T>& v) {
-  T* d = p.arena.alloc<T>(std::max<size_t>(v.size(), 1));
-  if (!v.empty()) DMK_CUDA_TRY(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, p.stream));
-  return d;
+namespace {
+// copies segment b of the packed upload: desc[b] = (source word offset, word count,
+// destination address as two 32-bit halves)
+__global__ void k_scatter_words(const uint32_t* __restrict__ packed, const int4* __restrict__ desc) {
+  const int4 d = desc[blockIdx.x];
+  uint32_t* dst = reinterpret_cast<uint32_t*>((static_cast<uint64_t>(static_cast<uint32_t>(d.w)) << 32) |
+                                              static_cast<uint32_t>(d.z));
+  const uint32_t* src = packed + d.x;
+  for (int i = threadIdx.x; i < d.y; i += blockDim.x) dst[i] = src[i];
 }
+}  // namespace
+
+// the plan's small device tables: put() takes each table's device place from the
+// plan's arena at once and keeps a packed host copy; flush() moves them all with one
+// host-to-device copy and one scatter launch (instead of one copy per table)
+struct Uploader {
+  Plan& p;
+  std::vector<uint32_t> packed;         // host words of every table, each 16-byte aligned
+  std::vector<int4> desc;
+  explicit Uploader(Plan& plan) : p(plan) {}
+  template <typename T>
+  T* put(const std::vector<T>& v) {
+    if ((v.size() * sizeof(T)) % 4) throw Error{DMK_ERR_CUDA, "device table not a whole number of words"};
+    T* d = p.arena.alloc<T>(std::max<size_t>(v.size(), 1));
+    if (v.empty()) return d;
+    const size_t off = (packed.size() + 3) & ~size_t(3);
+    const size_t words = v.size() * sizeof(T) / 4;
+    packed.resize(off + words);
+    std::memcpy(packed.data() + off, v.data(), v.size() * sizeof(T));
+    const uint64_t a = reinterpret_cast<uint64_t>(d);
+    desc.push_back(make_int4(static_cast<int>(off), static_cast<int>(words), static_cast<int>(a & 0xffffffffu),
+                             static_cast<int>(a >> 32)));
+    return d;
+  }
+  void flush() {
+    if (desc.empty()) return;
+    const size_t doff = (packed.size() + 3) & ~size_t(3);
+    packed.resize(doff + desc.size() * 4);
+    std::memcpy(packed.data() + doff, desc.data(), desc.size() * sizeof(int4));
+    uint32_t* d = p.arena.alloc<uint32_t>(packed.size());
+    DMK_CUDA_TRY(cudaMemcpyAsync(d, packed.data(), packed.size() * 4, cudaMemcpyHostToDevice, p.stream));
+    k_scatter_words<<<static_cast<unsigned>(desc.size()), 256, 0, p.stream>>>(d, reinterpret_cast<const int4*>(d + doff));
+    DMK_CUDA_TRY(cudaGetLastError());
+    ++p.launches;
+    packed.clear();
+    desc.clear();
+  }
+};
 
 // incoming expansions, phase e^{-2 pi i m.delta / 3} for a colleague at offset delta
 // (e = m.delta mod 3: 1, e^{-2 pi i/3}, e^{-4 pi i/3})
