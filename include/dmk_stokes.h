@@ -103,7 +103,11 @@ typedef struct {
                             interpolated in log10 eps, N1 = 2 (3c/pi) - 1,
                             N_per = 2 floor(c / 2pi) + 1).  The far field runs
                             in float32 where the pair terms do (MIXED, eps >=
-                            2e-7) and in float64 otherwise.  Single system;
+                            2e-7) and in float64 otherwise; in 3D float32 its
+                            leaf charges and leaf evaluation run on the
+                            tensor cores (split-TF32 products), or on the
+                            FP32 pipe when the environment variable
+                            DMK_STOKES_FAR_TC=0 is set at plan time.  Single system;
                             eval_grad / adjoint / noalloc: UNSUPPORTED.
                             DMK_COMPONENTS_EWALD: the periodic 3D Stokeslet
                             summed by a single-level prolate Ewald split on a
