@@ -37,11 +37,11 @@ N_SM = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes per launch of the candidate dominant kernels at N = 5e5 (8-Gaussian recipe,
 # eps 1e-6, MIXED), keyed by (stage, leaf capacity); filled from ncu captures
-TRAFFIC_5E5 = {("near", 2048): 29.1e6, ("near", 3072): 29.1e6, ("near", 4096): 29.1e6,
-               ("leaf_charges", 2048): 428.2e6, ("leaf_charges", 3072): 407.7e6, ("leaf_charges", 4096): 383.6e6,
-               ("outgoing", 2048): 1302.1e6, ("outgoing", 3072): 1160.7e6, ("outgoing", 4096): 957.4e6,
-               ("incoming", 2048): 1001.0e6, ("incoming", 3072): 893.2e6, ("incoming", 4096): 744.4e6,
-               ("leaf_eval", 2048): 242.5e6, ("leaf_eval", 3072): 217.6e6, ("leaf_eval", 4096): 185.5e6}
+TRAFFIC_5E5 = {("near", 2048): 29.1e6, ("near", 3072): 29.1e6, ("near", 4096): 29.0e6,
+               ("leaf_charges", 2048): 428.8e6, ("leaf_charges", 3072): 408.7e6, ("leaf_charges", 4096): 384.7e6,
+               ("outgoing", 2048): 1299.4e6, ("outgoing", 3072): 1162.2e6, ("outgoing", 4096): 957.5e6,
+               ("incoming", 2048): 1001.5e6, ("incoming", 3072): 892.7e6, ("incoming", 4096): 744.4e6,
+               ("leaf_eval", 2048): 242.7e6, ("leaf_eval", 3072): 217.5e6, ("leaf_eval", 4096): 185.7e6}
 
 
 def parse():

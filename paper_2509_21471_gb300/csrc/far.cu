@@ -1197,9 +1197,9 @@ __global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const __grid_const
       if (tid == 0) stage_in(ch + 1);
       ++staged;
     }
-    if (!tc::mbar_wait(&mbst[ch & 1], (ch >> 1) & 1, kTcWaitCycles)) fail = 1;
+    if (!tc::mbar_wait(&mbst[ch & 1], (ch >> 1) & 1, kTcWaitCycles)) atomicExch(&fail, 1);
     if (ch >= 1 && warp == 0)                                          // the operands were read by the MMAs of ch - 1
-      if (!tc::mbar_wait(&mbar, (ch - 1) & 1, kTcWaitCycles)) fail = 1;
+      if (!tc::mbar_wait(&mbar, (ch - 1) & 1, kTcWaitCycles)) atomicExch(&fail, 1);
     const int ncnt = min(kTcK, ns - ch * kTcK);
     float* sw = stage0 + (ch & 1) * stF;
     if (ncnt < kTcK) {                                                 // a leaf's last stage: sources past it read as zero
@@ -1240,7 +1240,7 @@ __global__ void __launch_bounds__(kTcThreads) k_far_anterp_tc(const __grid_const
     ++issued;
   }
   if (issued > 0 && !fail && warp == 0)
-    if (!tc::mbar_wait(&mbar, (issued - 1) & 1, kTcWaitCycles)) fail = 1;
+    if (!tc::mbar_wait(&mbar, (issued - 1) & 1, kTcWaitCycles)) atomicExch(&fail, 1);
   tc::sync_tc();
   if (!fail && issued > 0) {
     // D rows (a, b) x columns (k, c) through shared memory (the operand buffer is free):
@@ -1453,7 +1453,7 @@ __global__ void __launch_bounds__(kTcThreads) k_far_eval_tc(const int32_t* __res
     }
     ++issued;
     if (warp == 0)
-      if (!tc::mbar_wait(&mbar, (issued - 1) & 1, kTcWaitCycles)) fail = 1;
+      if (!tc::mbar_wait(&mbar, (issued - 1) & 1, kTcWaitCycles)) atomicExch(&fail, 1);
     tc::cp_async_wait<0>();
     tc::sync_tc();
     if (fail) break;
