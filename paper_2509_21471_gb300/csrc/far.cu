@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kWRows) k_far_weights(const int32_t* __restric
   const double inv_half = 1.0 / geo.w;             // a power of two
   const int ld = PB + 1;
   R* Wl = W + static_cast<int64_t>(s0) * 3 * PB;
-  for (int r0 = 0; r0 < 3 * ns; r0 += kWRows) {
+  for (int r0 = blockIdx.y * kWRows; r0 < 3 * ns; r0 += gridDim.y * kWRows) {   // a leaf's tiles over blockIdx.y
     const int nr = min(kWRows, 3 * ns - r0);
     __syncthreads();                               // nodes loaded; the previous tile written out
     if (threadIdx.x < nr) {
@@ -1571,6 +1571,7 @@ struct FarState {
   int tc = 0;                        // 1: float32 leaf charges and leaf evaluation on the tensor cores
   int tc_NP = 0, tc_RW = 0;          // their padded column count (3p) and row width (p)
   void* Vs = nullptr;                // [groups][N] float4 densities of the sources (tensor-core charges)
+  int w_tiles = 1;                   // tiles of kWRows weight rows of the largest source leaf
   CUtensorMap tmW{}, tmV{};          // TMA maps of W as [N][3 PB] and of Vs as [groups N][4], 32-row boxes
   size_t fused_out_bytes = 0, fused_ev_bytes = 0;
   int32_t* coll = nullptr;           // [27] colleague slots of the root
@@ -1842,6 +1843,11 @@ void far_setup(Plan& p) {
   F.nsrc_box = static_cast<int>(src_boxes.size());
   F.ntrg_box = static_cast<int>(trg_boxes.size());
   F.nsrc_leaf = static_cast<int>(src_leaf.size());
+  {
+    int64_t mx = 1;
+    for (int32_t li : src_leaf) mx = std::max<int64_t>(mx, cnt[li]);
+    F.w_tiles = static_cast<int>(std::min<int64_t>((3 * mx + kWRows - 1) / kWRows, 65535));
+  }
   F.ntrg_leaf = static_cast<int>(trg_leaf.size());
   // 27 colleague slots of the root (target index 0: boxes are sorted by level); the
   // other boxes take their colleagues from their parent's window below
@@ -2274,7 +2280,7 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
     R* W = static_cast<R*>(F.W);
     const size_t wshm = static_cast<size_t>(kWRows) * (PB + 1) * sizeof(R);
     DMK_CUDA_TRY(cudaFuncSetAttribute(k_far_weights<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(wshm)));
-    k_far_weights<R><<<F.nsrc_leaf, kWRows, wshm, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, T.w,
+    k_far_weights<R><<<dim3(F.nsrc_leaf, F.w_tiles), kWRows, wshm, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, T.w,
                                                  T.N, F.box_geo, P, PB, nodes, bw, W);
     DMK_CUDA_TRY(cudaGetLastError());
     ++p.launches;

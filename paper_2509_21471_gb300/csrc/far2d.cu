@@ -61,7 +61,7 @@ __global__ void k_far2_weights(const int32_t* __restrict__ leaf_list, const int3
   const BoxGeo geo = box_geo[leaf_box[blockIdx.x]];
   const int s0 = leaf_start[li], ns = leaf_count[li];
   const double inv_half = 1.0 / geo.w;
-  for (int i = threadIdx.x; i < 2 * ns; i += blockDim.x) {
+  for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < 2 * ns; i += gridDim.y * blockDim.x) {   // rows over blockIdx.y
     const int sl = i >> 1, ax = i & 1;
     const int64_t si = s0 + sl;
     const R t = static_cast<R>((w[ax * N + si] - (ax == 0 ? geo.x : geo.y)) * inv_half);
@@ -665,6 +665,7 @@ struct Far2State {
   int ncomp = 0, slot_f = -1, slot_t = -1;
   int nbox = 0, maxlev = 0, nsrc_box = 0, ntrg_box = 0, nsrc_leaf = 0, ntrg_leaf = 0;
   int ngrp = 0, n_ev_items = 0;
+  int w_tiles = 1;                   // blocks of 128 weight rows of the largest source leaf
   int64_t p2 = 0, modes = 0, rmodes = 0;
   double sT_root = 1.0;
   BoxGeo* box_geo = nullptr;
@@ -832,6 +833,11 @@ Far2State* far2d_setup(Plan& p) {
   F.ntrg_box = static_cast<int>(trg_boxes.size());
   F.nsrc_leaf = static_cast<int>(src_leaf.size());
   F.ntrg_leaf = static_cast<int>(trg_leaf.size());
+  {
+    int64_t mx = 1;
+    for (int32_t li : src_leaf) mx = std::max<int64_t>(mx, cnt[li]);
+    F.w_tiles = static_cast<int>(std::min<int64_t>((2 * mx + 127) / 128, 65535));
+  }
   auto lookup = [&](int l, const int64_t* raw, int* id) {
     const int64_t n = int64_t(1) << l;
     int64_t cc[2];
@@ -1067,7 +1073,7 @@ void far2d_run_t(const Plan& p, const Far2State& F, const double* d_f, const dou
   // 1. Lagrange weights of the sources, leaf proxy charges
   if (F.nsrc_leaf > 0) {
     R* W = static_cast<R*>(F.W);
-    k_far2_weights<R><<<F.nsrc_leaf, 128, 0, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, T.w,
+    k_far2_weights<R><<<dim3(F.nsrc_leaf, F.w_tiles), 128, 0, s>>>(F.src_leaf, F.src_leaf + F.nsrc_leaf, T.leaf_start, T.leaf_count, T.w,
                                                   T.N, F.box_geo, P, PB, nodes, bw, W);
     check();
     const size_t shm = (static_cast<size_t>(kAnt2Chunk) * 2 * PB + 4 * kAnt2Chunk) * sizeof(R);
