@@ -24,13 +24,16 @@
 //
 // GPU layout.  The box hierarchy and every job list are built on the host when
 // the plan is made.  The separable tensor-product transforms (child merges,
-// interpolation, outgoing and incoming plane waves, the root) all run in one
-// kernel, k_rot, which contracts the slowest axis of a [n_in][rest] tensor with
-// a small matrix and writes the result as [rest][n_out] (the contracted axis
-// moves last, so three stages return the original axis order).  Spectra keep
-// m_0 >= 0 only (the potential is real).  Arithmetic is FP32 when the plan's
-// pair terms are FP32 (MIXED at eps >= 2e-7), FP64 otherwise; the target
-// velocities are accumulated in FP64.
+// interpolation, outgoing and incoming plane waves, the root) run in the generic
+// kernel k_rot, which contracts the slowest axis of a [n_in][rest] tensor with a
+// small matrix and writes the result as [rest][n_out] (the contracted axis moves
+// last, so three stages return the original axis order), or, in float32, in
+// kernels that keep one box's (or one parent's) stages in shared memory.  Spectra
+// keep m_0 >= 0 only (the potential is real).  Arithmetic is FP32 when the plan's
+// pair terms are FP32 (MIXED at eps >= 2e-7), FP64 otherwise; in FP32 the two
+// per-point contractions (leaf charges, leaf evaluation) run on the tcgen05
+// tensor cores with split-TF32 products (tc.cuh).  The target velocities are
+// accumulated in FP64.
 #include "far_common.cuh"
 #include "tc.cuh"
 
