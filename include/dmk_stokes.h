@@ -279,6 +279,14 @@ dmk_status_t dmk_stokes_eval_traced(dmk_stokes_plan_t plan, const double* d_f, c
  *   in float32, 0 in float64.  All zero for other plans. */
 dmk_status_t dmk_stokes_far_info(dmk_stokes_plan_t plan, int32_t info[8]);
 
+/* Diagnostics of the far field's tensor-core kernels (no paper counterpart): runs
+ * on `stream` one block that allocates tensor memory and waits on an mbarrier that
+ * nothing completes, with a limit of ~1 ms of SM clock instead of the kernels' ~2 s,
+ * and sets *h_timed_out = 1 when the wait ran out and was reported in the status
+ * word the way the kernels report it (then freeing the tensor memory).  The device
+ * stays usable afterwards.  Host-synchronises. */
+dmk_status_t dmk_stokes_tc_wait_selftest(void* stream, int32_t* h_timed_out);
+
 /* Synchronises the plan's last stream and returns the latched device status
  * (DMK_OK, DMK_ERR_OUT_OF_RANGE, DMK_ERR_INVALID_ARG for a non-finite point). */
 dmk_status_t dmk_stokes_sync_status(dmk_stokes_plan_t plan);

@@ -438,6 +438,16 @@ dmk_status_t dmk_stokes_far_info(dmk_stokes_plan_t plan, int32_t info[8]) {
   return DMK_OK;
 }
 
+dmk_status_t dmk_stokes_tc_wait_selftest(void* stream, int32_t* h_timed_out) {
+  if (!h_timed_out) return set_err(nullptr, DMK_ERR_INVALID_ARG, "h_timed_out is NULL");
+  try {
+    *h_timed_out = dmk::tc_wait_selftest(static_cast<cudaStream_t>(stream)) ? 1 : 0;
+  } catch (const dmk::Error& e) {
+    return set_err(nullptr, e.code, e.msg);
+  }
+  return DMK_OK;
+}
+
 dmk_status_t dmk_stokes_sync_status(dmk_stokes_plan_t plan) {
   if (!valid_plan(plan)) return set_err(nullptr, DMK_ERR_BAD_PLAN, "invalid plan handle");
   dmk::Plan& p = plan->p;

@@ -290,6 +290,8 @@ void far_free(Plan& p);
 void far_run(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u, cudaStream_t s);
 void far_info(const Plan& p, int32_t info[8]);
 size_t far_bytes(const Plan& p);
+// the tensor-core wait limit exercised on purpose (true when the wait ran out and was reported)
+bool tc_wait_selftest(cudaStream_t s);
 // far2d.cu: the same in 2D
 Far2State* far2d_setup(Plan& p);
 void far2d_free(Plan& p, Far2State* F);

@@ -1502,6 +1502,22 @@ __global__ void __launch_bounds__(kTcThreads) k_far_eval_tc(const int32_t* __res
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+// the failure path of the tensor-core kernels on purpose, without a fault: tensor
+// memory allocated, an mbarrier that nothing arrives on, the bounded wait running
+// out after max_cycles, the status bit, the tensor memory freed
+__global__ void k_tc_wait_selftest(int* __restrict__ status, long long max_cycles) {
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) tc::mbar_init(&mbar, 1);
+  if (warp == 0) tc::tmem_alloc(&tbase, 32);
+  tc::sync_tc();
+  if (warp == 0 && !tc::mbar_wait(&mbar, 0, max_cycles) && threadIdx.x == 0) atomicOr(status, ST_TC_TIMEOUT);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 32);
+}
+
 // ------------------------------------------------------------------ host side
 
 // B-hat^R(k) in 3D, Eq. (Btrunc_hat); Taylor series of the bracket near k = 0
@@ -2507,6 +2523,19 @@ void far_run_t(const Plan& p, const double* d_f, const double* d_g, const double
 }
 
 }  // namespace
+
+bool tc_wait_selftest(cudaStream_t s) {
+  int* d = nullptr;
+  int h = 0;
+  DMK_CUDA_TRY(cudaMallocAsync(&d, sizeof(int), s));
+  DMK_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(int), s));
+  k_tc_wait_selftest<<<1, 128, 0, s>>>(d, 2000000LL);      // about 1 ms of SM clock
+  DMK_CUDA_TRY(cudaGetLastError());
+  DMK_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  DMK_CUDA_TRY(cudaFreeAsync(d, s));
+  DMK_CUDA_TRY(cudaStreamSynchronize(s));
+  return (h & ST_TC_TIMEOUT) != 0;
+}
 
 void far_run(const Plan& p, const double* d_f, const double* d_g, const double* d_n, double* d_u, cudaStream_t s) {
   if (!p.far || !d_u || p.tree.N == 0) return;

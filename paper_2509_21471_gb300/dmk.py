@@ -58,6 +58,7 @@ _lib.dmk_stokes_halo_leaves.argtypes = [ctypes.c_int32, _P, _P, ctypes.c_int32, 
 _lib.dmk_stokes_autotune.argtypes = [ctypes.POINTER(Opts), ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_int32, _P,
                                      ctypes.c_int32, _P, _P, _P]
 _lib.dmk_stokes_far_info.argtypes = [_P, _P]
+_lib.dmk_stokes_tc_wait_selftest.argtypes = [_P, _P]
 _lib.dmk_stokes_eval_traced.argtypes = [_P, _P, _P, _P, _P, _P, _P, ctypes.c_int32]
 _lib.dmk_stokes_destroy.argtypes = [_P]
 _lib.dmk_stokes_destroy.restype = None
@@ -73,7 +74,7 @@ for _name in ("dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "
 EXPORTED = ["dmk_stokes_plan", "dmk_stokes_plan_batched", "dmk_stokes_eval", "dmk_stokes_eval_noalloc",
             "dmk_stokes_eval_grad", "dmk_stokes_eval_adjoint",
             "dmk_stokes_sync_status", "dmk_stokes_plan_stats", "dmk_stokes_plan_tree", "dmk_stokes_kernel_table",
-            "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves", "dmk_stokes_autotune", "dmk_stokes_far_info", "dmk_stokes_eval_traced",
+            "dmk_stokes_partition_leaves", "dmk_stokes_halo_leaves", "dmk_stokes_autotune", "dmk_stokes_far_info", "dmk_stokes_eval_traced", "dmk_stokes_tc_wait_selftest",
             "dmk_stokes_destroy", "dmk_stokes_last_error"]
 
 
@@ -287,6 +288,14 @@ def autotune(x, f=None, g=None, n=None, candidates=(600, 1200, 2400), repeats=3,
                                         _stream_ptr(stream), ms.ctypes.data_as(ctypes.c_void_p),
                                         ctypes.byref(best)))
     return int(cand[best.value]), {int(c): float(t) for c, t in zip(cand, ms)}
+
+
+def tc_wait_selftest(stream=None):
+    """dmk_stokes_tc_wait_selftest: True when a tensor-core wait that nothing
+    completes ran out and was reported (the far field's failure path)."""
+    out = ctypes.c_int32(0)
+    _check(_lib.dmk_stokes_tc_wait_selftest(_stream_ptr(stream), ctypes.byref(out)), None)
+    return bool(out.value)
 
 
 def _i32(a):

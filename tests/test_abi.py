@@ -47,6 +47,7 @@ def test_invalid_arguments_rejected_without_gpu(dmk_lib):
     o = dmk_lib.make_opts(components=3)
     assert lib.dmk_stokes_plan(ctypes.byref(o), 0, None, 0, None, None, ctypes.byref(h)) == 1
     assert lib.dmk_stokes_far_info(None, None) == 7
+    assert lib.dmk_stokes_tc_wait_selftest(None, None) == 1        # no output pointer: rejected before the GPU
     o = dmk_lib.make_opts()
     assert lib.dmk_stokes_plan(ctypes.byref(o), 10, None, 10, None, None, ctypes.byref(h)) == 1
     # targets are the sources (d_trg NULL) but n_trg != n_src

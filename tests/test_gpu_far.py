@@ -186,3 +186,14 @@ def test_tensor_core_leaf_kernels_match_fp32_pipe(dmk, monkeypatch, eps, kernels
     assert rel_l2(u_tc, u_pipe) < max(1e-5, eps), rel_l2(u_tc, u_pipe)
     ref = direct.direct_sum(x, f, g, nrm)
     assert rel_l2(u_tc, ref) < 10 * eps, rel_l2(u_tc, ref)
+
+
+def test_tensor_core_wait_limit_is_reported_and_the_device_stays_usable(dmk):
+    """The bounded wait of the tensor-core kernels run out on purpose (an mbarrier
+    that nothing completes, ~1 ms limit): reported as the kernels report it, tensor
+    memory freed, and the device still evaluates a plan correctly afterwards."""
+    assert dmk.tc_wait_selftest() is True
+    x, f = wl.small_uniform_3d()
+    u, info = _run(dmk, x, f, None, None, 1e-6, 1, 64, False, dmk.ALL)
+    assert info["fp32"] == 1
+    assert rel_l2(u, direct.direct_sum(x, f)) < 1e-5
