@@ -676,7 +676,7 @@ def run_ours(args):
     achieved = stage_flops[dom] / (mx["stage_ms"][dom] / 1e3) / 1e12
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
     # capture of the same recipe at N = 5e5 and the same leaf capacity, scaled by the
-    # point count (profiles/dram_traffic_clustered5e5.md)
+    # point count
     traffic_5e5 = TRAFFIC_5E5.get((dom, ns)) if args.eps == 1e-6 else None
     traffic = traffic_5e5 * args.n / 500_000 if traffic_5e5 else None
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
