@@ -419,15 +419,20 @@ def level_exact(tree, kern, lev, f=None, g=None, n=None):
     images = list(itertools.product((-1, 0, 1), repeat=d)) if tree.periodic else [(0,) * d]
     KS = _kernels(d, kern)
     for t in idx:
+        # every (source, image) pair of t, evaluated in one call
+        dds, Ss, sames = [], [], []
         for img in images:
             im = np.array(img, dtype=np.int64)
             bs = box[idx] + im[None, :] * n_side
             S = idx[np.all(np.abs(bs - box[t][None, :]) <= 1, axis=1)]
             if len(S) == 0:
                 continue
-            dd = (tree.w[t][None, :] - tree.w[S]) - im[None, :].astype(np.float64)
-            same = (S == t) & (not any(img))
-            u[t] += _diff_pairs(KS, d, dd, r0, r1, same, f, g, n, S)
+            dds.append((tree.w[t][None, :] - tree.w[S]) - im[None, :].astype(np.float64))
+            Ss.append(S)
+            sames.append((S == t) & (not any(img)))
+        if Ss:
+            u[t] += _diff_pairs(KS, d, np.concatenate(dds), r0, r1, np.concatenate(sames), f, g, n,
+                                np.concatenate(Ss))
     return u
 
 
